@@ -1,0 +1,360 @@
+#!/usr/bin/env python
+"""Benchmark of the QPAT reconstruction hot path on GB300.
+
+Workload: 40 mm Kuhn cube, 64^3 nodes (262,144 nodes, 1,500,282 tets), six
+seeded spherical inclusions, 4 boundary-patch illuminations.  One step is one
+Jv + J^T w pair at the phantom's linearisation point -- K = 4 forward-type
+and 4 adjoint solves, run as one 8-RHS block PCG -- followed by one
+lagged-diffusivity prior solve M_delta^-1 (both blocks), i.e. the operator
+work of one priorconditioned LSQR round.  value = pairs/s.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--precision mixed|fp64]
+  python bench.py --impl reference ...   (CPU oracle, bounded sample)
+
+Prints one JSON line (rank 0).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import qpat_synth as S  # noqa: E402
+
+WORKLOAD = "c1_cube64"
+METRIC = "Jv+JTw pairs/s (64^3-node cube, K=4, + one M_delta solve per pair)"
+UNIT = "pairs/s"
+
+
+def env_rank():
+    return int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), int(
+        os.environ.get("LOCAL_RANK", "0"))
+
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            p = json.load(fh)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle samples during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_bench_{os.getpid()}.csv")
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = max(mx, float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def pcg_bytes_per_iter(N: int, E: int, R: int, s: int) -> float:
+    """Algorithmic (unique) bytes of one fused PCG iteration on a general tet
+    mesh: 16 B of connectivity per tet, coordinates + two coefficients +
+    the inverse diagonal per node (6 s), and per right-hand side x, r, p read
+    and written once (6 s)."""
+    return 16.0 * E + 6.0 * s * N + 6.0 * s * R * N
+
+
+def setup_problem(Q, torch, precision: int):
+    cfg = S.config(WORKLOAD)
+    xyz, tets = cfg.mesh()
+    kappa, mu = cfg.coefficients(xyz)
+    mesh = Q.qpat_mesh(xyz, tets)
+    flux = np.stack([Q.qpat_flux_patch(mesh, p.center, p.normal, p.half_w, p.amp) for p in cfg.patches])
+    dev = torch.device("cuda")
+    T = lambda a: torch.tensor(np.ascontiguousarray(a), device=dev)
+    d = {"cfg": cfg, "mesh": mesh, "N": mesh.N, "E": mesh.E, "K": cfg.K}
+    d["kappa"], d["mu"], d["flux"] = T(kappa), T(mu), T(flux)
+    phi = torch.empty((cfg.K, mesh.N), dtype=torch.float64, device=dev)
+    h = torch.empty_like(phi)
+    Q.qpat_forward_dev(mesh, d["kappa"], d["mu"], d["flux"], phi, h, Q.qpat_default_params(precision=0))
+    torch.cuda.synchronize()
+    d["phi"] = phi
+    hmax = float(h.abs().max())
+    d["w"] = 1.0 / (0.01 * h.abs() + 1e-3 * hmax)
+    rng = np.random.default_rng(123)
+    d["s"] = T(0.1 * rng.standard_normal(2 * mesh.N))
+    d["t"] = T(rng.standard_normal((cfg.K, mesh.N)))
+    k0, m0 = float(np.median(kappa)), float(np.median(mu))
+    d["kt"] = T(np.log(kappa / k0))
+    d["mt"] = T(np.log(mu / m0))
+    d["prior_rhs"] = T(rng.standard_normal(2 * mesh.N))
+    d["oj"] = torch.empty((cfg.K, mesh.N), dtype=torch.float64, device=dev)
+    d["ov"] = torch.empty(2 * mesh.N, dtype=torch.float64, device=dev)
+    d["op"] = torch.empty(2 * mesh.N, dtype=torch.float64, device=dev)
+    d["host"] = {k: np.ascontiguousarray(d[k].cpu().numpy()) for k in
+                 ("kappa", "mu", "phi", "w", "s", "t", "kt", "mt", "prior_rhs")}
+    return d
+
+
+def run_ours(args):
+    import torch
+    import paper_1512_02796_gb300 as Q
+    rank, world, local = env_rank()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    precision = 1 if args.precision == "mixed" else 0
+    prm = Q.qpat_default_params(precision=precision)
+    d = setup_problem(Q, torch, precision)
+    mesh = d["mesh"]
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")  # 256 MB > L2
+
+    def step():
+        Q.qpat_jvp_vjp_pair_dev(mesh, d["kappa"], d["mu"], d["phi"], d["w"], d["s"], d["t"], d["oj"], d["ov"], prm)
+        Q.qpat_prior_solve_dev(mesh, d["kt"], d["mt"], d["prior_rhs"], d["op"], prm)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    mesh.set_timing(True)
+    mesh.reset_stats()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    pair_ms, pair_iters, pair_launches = 0.0, 0, 0
+    clk = ClockSampler(local)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    clk.start()
+    wall0 = time.perf_counter()
+    for i in range(args.steps):
+        flush.fill_(float(i))
+        a, b = ev[i]
+        a.record()
+        mesh.reset_stats()
+        Q.qpat_jvp_vjp_pair_dev(mesh, d["kappa"], d["mu"], d["phi"], d["w"], d["s"], d["t"], d["oj"], d["ov"], prm)
+        st = mesh.stats()
+        pair_ms += mesh.pcg_time_ms()
+        pair_iters += st["pcg_iters"]
+        pair_launches += st["launches"]
+        Q.qpat_prior_solve_dev(mesh, d["kt"], d["mt"], d["prior_rhs"], d["op"], prm)
+        b.record()
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - wall0
+    clocks = clk.stop()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    tot_ms = sum(step_ms)
+    if world > 1:
+        t = torch.tensor([tot_ms], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        tot_ms = float(t.item())
+    value = world * args.steps / (tot_ms / 1e3)
+
+    # ---- end to end through the host-pointer ABI (copies inside the timed region)
+    H = d["host"]
+    e2e_steps = max(1, min(args.steps, 5))
+    hk = H["kappa"]
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        oj = Q.qpat_jvp(mesh, H["kappa"], H["mu"], H["phi"], H["s"], H["w"], prm)
+        ov = Q.qpat_vjp(mesh, H["kappa"], H["mu"], H["phi"], H["t"], H["w"], prm)
+        op = Q.qpat_prior_solve(mesh, H["kt"], H["mt"], H["prior_rhs"], prm)
+    e2e_s = time.perf_counter() - t0
+    N, K = d["N"], d["K"]
+    # inputs of qpat_jvp (kappa, mu, phi, w, s), qpat_vjp (kappa, mu, phi, w, t), qpat_prior_solve (kt, mt, rhs)
+    h2d = 8 *((N + N + K * N + K * N + 2 * N) + (N + N + K * N + K * N + K * N) + (N + N + 2 * N))
+    d2h = 8 * (K * N + 2 * N + 2 * N)
+
+    # ---- roofline of the dominant kernel (fused PCG of the pair launch)
+    s_bytes = 4 if precision == 1 else 8
+    R = 2 * (1 << max(0, math.ceil(math.log2(K))))
+    bpi = pcg_bytes_per_iter(N, d["E"], R, s_bytes)
+    peak, peak_kind = load_peaks()
+    achieved = bpi * pair_iters / (pair_ms / 1e3) / 1e9 if pair_ms > 0 else 0.0
+    traffic = None
+    tf = os.path.join(ROOT, "profiles", "pcg_traffic_c1.json")
+    if os.path.exists(tf):
+        try:
+            tr = json.load(open(tf))
+            if tr.get("precision") == args.precision:
+                traffic = tr.get("dram_bytes_per_launch")
+        except Exception:
+            traffic = None
+
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": tot_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak" if world > 1 else "none", "vs_baseline": None,
+        "dtype": "f32+f64-refine" if precision == 1 else "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "nodes": N, "tets": d["E"], "illuminations": K,
+                   "pair_rhs": R, "precision": args.precision, "pcg_rtol": prm.pcg_rtol,
+                   "l2": "flushed between steps (256 MB write outside the per-step events)",
+                   "parallelism": "replicas" if world > 1 else "single"},
+        "e2e": {"value": e2e_steps / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "roofline": {"bound": "hbm", "kernel": "k_pcg (fused persistent PCG, pair launch)",
+                     "achieved": achieved, "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
+                     "frac": achieved / peak if peak else None, "traffic": traffic,
+                     "bytes_per_iter": bpi, "pcg_iters_per_step": pair_iters / args.steps,
+                     "pcg_launches_per_step": pair_launches / args.steps,
+                     "pcg_ms_per_step": pair_ms / args.steps},
+        "clocks": clocks,
+        "wall_s": wall,
+    }
+    if rank == 0 and args.cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(steps=2)
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def cpu_baseline(steps: int = 2):
+    """The CPU oracle (assembled CSR + SuperLU) on a bounded sample of the
+    workload: a 32^3-node cube of the same family with K = 4.  One pair =
+    J s and J^T t with the factorisation reused, plus its 1/50 share of the
+    factorisation (one per linearisation of 50 LSQR rounds); the pairs/s
+    figure is scaled by the node ratio to the 64^3 workload (a lower bound
+    on the oracle's cost there, since sparse LU grows faster than N)."""
+    import oracle as O
+    cfg = S.small_config(32, 40.0, 4, 5)
+    xyz, tets = cfg.mesh()
+    m = O.Mesh(xyz, tets)
+    kap, mu = cfg.coefficients(xyz)
+    fl = np.stack([O.flux_patch(m, p.center, p.normal, p.half_w) for p in cfg.patches])
+    t0 = time.perf_counter()
+    fac = O.Factor(O.system_matrix(m, kap, mu))
+    t_fac = time.perf_counter() - t0
+    phi, h = O.forward(m, kap, mu, fl, fac)
+    rng = np.random.default_rng(0)
+    s = rng.standard_normal(2 * m.N)
+    t = rng.standard_normal((4, m.N))
+    kt = np.log(kap / np.median(kap))
+    mt = np.log(mu / np.median(mu))
+    Pf = O.Factor(O.prior_matrix(m, kt, mt, 1e-2, 1.0, 1e-6))
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        O.jvp(m, kap, mu, phi, s, None, fac)
+        O.vjp(m, kap, mu, phi, t, None, fac)
+        Pf.solve(rng.standard_normal(2 * m.N))
+    t_pair = (time.perf_counter() - t0) / steps
+    per_pair = t_pair + t_fac / 50.0
+    scale = (64 ** 3) / float(m.N)
+    try:
+        cores = len(os.sched_getaffinity(0))
+    except Exception:
+        cores = os.cpu_count()
+    return {"value": 1.0 / (per_pair * scale), "unit": UNIT, "cores": 1, "cores_available": cores,
+            "kind": "oracle",
+            "sample": f"32^3-node cube (N={m.N}), K=4: {steps} pairs + M_delta solves with reused SuperLU "
+                      f"factors ({t_pair:.2f} s/pair) + 1/50 of the K factorisation ({t_fac:.2f} s); "
+                      f"pairs/s scaled by N ratio x{scale:.0f} to 64^3; single-threaded SuperLU"}
+
+
+def run_reference(args):
+    """Reference arm: the CPU oracle timed as it stands, rank 0 only."""
+    rank, world, _ = env_rank()
+    if rank != 0:
+        return
+    import oracle as O
+    cfg = S.small_config(32, 40.0, 4, 5)
+    xyz, tets = cfg.mesh()
+    m = O.Mesh(xyz, tets)
+    kap, mu = cfg.coefficients(xyz)
+    fl = np.stack([O.flux_patch(m, p.center, p.normal, p.half_w) for p in cfg.patches])
+    fac = O.Factor(O.system_matrix(m, kap, mu))
+    phi, _ = O.forward(m, kap, mu, fl, fac)
+    rng = np.random.default_rng(0)
+    kt = np.log(kap / np.median(kap))
+    mt = np.log(mu / np.median(mu))
+    Pf = O.Factor(O.prior_matrix(m, kt, mt, 1e-2, 1.0, 1e-6))
+    scale = (64 ** 3) / float(m.N)
+
+    def step():
+        s = rng.standard_normal(2 * m.N)
+        t = rng.standard_normal((4, m.N))
+        O.jvp(m, kap, mu, phi, s, None, fac)
+        O.vjp(m, kap, mu, phi, t, None, fac)
+        Pf.solve(rng.standard_normal(2 * m.N))
+
+    for _ in range(args.warmup):
+        step()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        step()
+    dt = (time.perf_counter() - t0) / args.steps * scale
+    value = 1.0 / dt
+    sample = (f"32^3-node cube (N={m.N}), K=4, reused SuperLU factors; per-pair time scaled by the node "
+              f"ratio x{scale:.0f} to 64^3")
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3, "higher_is_better": True,
+        "dtype": "f64", "data": "synthetic", "config": {"workload": WORKLOAD, "sample": sample},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,236 @@
+/*
+ * qpat.h -- C ABI of the GB300 hot path of QPAT reconstruction with
+ * total-variation-type priors (priorconditioned LSQR, lagged diffusivity,
+ * matrix-free Jacobians of the diffusion approximation).
+ *
+ * Paper references below are to its sections, equations, Algorithm 1 and
+ * Appendix.  Conventions common to every call:
+ *
+ *  - Units follow the caller (the paper uses mm and mm^-1).
+ *  - Node vectors have length N and are in the CALLER's node order; the
+ *    library permutes to its own locality order internally.  Stacked
+ *    per-illumination vectors are K x N row-major (illumination k is the
+ *    contiguous row k), as in the stacking rule of Sec. 4.
+ *  - Parameter vectors of the derivative calls are beta = [kappa_tilde; mu_tilde]
+ *    in R^{2N} (log parameters, Eq. (4)); kappa, mu are the nodal (P1)
+ *    coefficients kappa_n = kappa_0 exp(kappa_tilde_n), mu_n = mu_0 exp(mu_tilde_n).
+ *  - Boundary faces are numbered in the canonical order: each face written
+ *    with its three caller node ids ascending, faces sorted lexicographically.
+ *    Per-face flux arrays (K x F) use this order.
+ *  - Plain calls take HOST pointers, copy in, compute on the GPU and copy
+ *    out before returning.  *_dev calls take DEVICE pointers (any CUDA
+ *    allocation of the current device) and a cudaStream_t passed as void*;
+ *    they are asynchronous with respect to the host except where noted.
+ *  - The caller owns every array it passes.  The mesh handle owns the device
+ *    copy of the mesh and a workspace that grows on demand (cudaMalloc);
+ *    both are released by qpat_mesh_free.
+ *  - Every int-returning call returns QPAT_OK (0) or a negative code; the
+ *    outputs are then undefined and qpat_last_error() (thread-local) says why.
+ *  - A mesh handle must not be used by two host threads at once.
+ */
+#ifndef QPAT_H
+#define QPAT_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+    QPAT_OK = 0,
+    QPAT_EINVAL = -1,      /* bad argument: sizes, NULL, degenerate tet, ... */
+    QPAT_ENOCONV = -2,     /* a linear solve hit its iteration cap */
+    QPAT_EBREAKDOWN = -3,  /* PCG breakdown: p.Ap <= 0 or a NaN/Inf scalar */
+    QPAT_ETIMEOUT = -4,    /* a bounded grid barrier gave up waiting */
+    QPAT_ECUDA = -5,       /* a CUDA runtime call failed */
+    QPAT_ENOMEM = -6
+};
+
+typedef struct qpat_mesh_s* qpat_mesh_t;
+
+/* Solver and Algorithm 1 parameters.  Defaults (qpat_default_params):
+ * T = 5e-3, b/a = 1, delta = 1e-6, m0 = 10, tau = 1e-2 (Sec. 4, end),
+ * 5 linearisations including step 0 and 50 LSQR rounds as caps,
+ * FP64 PCG to a relative residual of 1e-13. */
+typedef struct {
+    double T;              /* Perona-Malik edge scale, Eq. (10) */
+    double b_over_a;       /* prior weight ratio, Eq. (16) */
+    double delta;          /* M_delta = M + delta I, Eq. (19) */
+    double tau;            /* stopping threshold, Eq. (22) */
+    int m0;                /* stopping window, Eq. (22) */
+    int max_lin;           /* linearisations, step 0 counted (Sec. 5) */
+    int max_lsqr;          /* LSQR rounds per linearisation */
+    int fixed_counts;      /* 1: run exactly max_lin x max_lsqr, no Eq. (22) stop
+                              (the step-4 acceptance of Algorithm 1 stays active) */
+    int precision;         /* 0: FP64 PCG; 1: FP32 PCG inside FP64 refinement */
+    int max_pcg_iter;      /* cap per PCG run (inner run for precision 1) */
+    double pcg_rtol;       /* |b - A x| / |b| target of every K and M_delta solve */
+    int fit_grid;          /* (kappa_0, mu_0) search grid per axis (Algorithm 1) */
+    int fit_gn_steps;      /* Gauss-Newton polish steps of that search */
+    int patch_nodes;       /* owned nodes per CTA patch (0 = library choice) */
+    int reserved[7];
+} qpat_params;
+
+/* Report of qpat_reconstruct (Algorithm 1). */
+typedef struct {
+    double kappa0, mu0;            /* background fit or the given values */
+    int linearisations;            /* step 0 counted */
+    int accepted_last;             /* 0 if step 4 rejected the last LSQR result */
+    int lsqr_iters[32];            /* rounds run in each linearisation */
+    double residuals[33];          /* |Gamma^-1/2 (chi - h)| after each accepted step */
+    int64_t pcg_iters;             /* total PCG iterations (all solves) */
+    int64_t solves;                /* total linear solves (RHS counted) */
+    int64_t refinements;           /* FP64 refinement sweeps (precision 1) */
+    double ms_total;               /* device wall time of the call */
+} qpat_report;
+
+void qpat_default_params(qpat_params* p);
+
+/* Thread-local message describing the last error of this thread. */
+const char* qpat_last_error(void);
+
+/* ---------------------------------------------------------------- mesh */
+
+/* Builds a mesh handle from N node coordinates (xyz, N x 3, row-major) and
+ * E tetrahedra (tets, E x 4, 0-based caller node ids, any orientation).
+ * The P1 basis of Eq. (5) lives on this mesh.  Copies both arrays; extracts
+ * the boundary faces (faces owned by one tet), orders nodes for locality,
+ * splits them into CTA patches and uploads everything to the current
+ * device.  Fails with QPAT_EINVAL on ids out of range or a degenerate tet. */
+int qpat_mesh(const double* xyz, int64_t N, const int32_t* tets, int64_t E,
+              qpat_mesh_t* out);
+
+/* Same, with the owned-node patch size chosen by the caller (>= 32). */
+int qpat_mesh_ex(const double* xyz, int64_t N, const int32_t* tets, int64_t E,
+                 int patch_nodes, qpat_mesh_t* out);
+
+void qpat_mesh_free(qpat_mesh_t mesh);
+
+/* Host-only preparation check (needs no GPU): builds the mesh structures of
+ * qpat_mesh_ex and verifies them.  info8 receives F, patches, max touched
+ * nodes per patch, max owned nodes, max tets per patch, max faces per patch,
+ * total patch-tet entries (>= E; the excess is the tets duplicated on patch
+ * borders) and total patch-face entries.  faces (F x 3) and perm (N) are
+ * filled when not NULL.  Returns QPAT_EINVAL with a message if a check fails. */
+int qpat_mesh_host_info(const double* xyz, int64_t N, const int32_t* tets, int64_t E,
+                        int patch_nodes, int64_t* info8, int32_t* faces, int32_t* perm);
+
+/* Counters of the linear solves run with this mesh since creation or the
+ * last reset: out4 = {PCG iterations, solves (RHS), FP64 refinement sweeps,
+ * PCG launches}. */
+int qpat_mesh_stats(qpat_mesh_t mesh, int64_t* out4);
+int qpat_mesh_reset_stats(qpat_mesh_t mesh);
+
+/* When on, every PCG launch is bracketed by CUDA events recorded on the
+ * stream it is launched on; qpat_mesh_pcg_time returns the summed device
+ * time (ms) of those launches since the last reset. */
+int qpat_mesh_set_timing(qpat_mesh_t mesh, int on);
+int qpat_mesh_pcg_time(qpat_mesh_t mesh, double* ms);
+
+int64_t qpat_mesh_num_nodes(qpat_mesh_t mesh);
+int64_t qpat_mesh_num_tets(qpat_mesh_t mesh);
+int64_t qpat_mesh_num_faces(qpat_mesh_t mesh);
+int64_t qpat_mesh_num_patches(qpat_mesh_t mesh);
+
+/* Boundary faces in canonical order (F x 3 caller node ids, ascending). */
+int qpat_mesh_faces(qpat_mesh_t mesh, int32_t* faces);
+
+/* Library node order: perm[i] = caller id of library node i (N entries). */
+int qpat_mesh_permutation(qpat_mesh_t mesh, int32_t* perm);
+
+/* Face-constant flux of a square boundary patch (Sec. 5, Test 2 uses such
+ * characteristic functions): flux_face[f] = amp if all three vertices of
+ * face f lie on the plane through c with unit normal n (to 1e-9 of the mesh
+ * extent) and its centroid lies in the closed square of half width half_w
+ * about c (infinity norm over the in-plane axes), else 0.  F entries. */
+int qpat_flux_patch(qpat_mesh_t mesh, const double c[3], const double n[3],
+                    double half_w, double amp, double* flux_face);
+
+/* ------------------------------------------------------- operator apply */
+
+/* y = K(kappa, mu) x for R right-hand sides: the FE matrix of the weak form
+ * of Eq. (1) (Appendix): integral kappa grad x . grad v + mu x v plus
+ * 1/2 integral over the boundary of x v, with P1 nodal kappa and mu.
+ * x, y: N x R node-major (x[n*R + r]), caller order, device pointers.
+ * precision 0 computes in FP64, 1 in FP32 (inputs and outputs stay FP64). */
+int qpat_apply_K_dev(qpat_mesh_t mesh, int precision, const double* kappa,
+                     const double* mu, int R, const double* x, double* y,
+                     void* stream);
+
+/* -------------------------------------------------------- forward model */
+
+/* phi^(k) = K^{-1} f^(k), h^(k) = mu * phi^(k) for K illuminations
+ * (Appendix; Eq. (2) and (7)), f_i = 2 integral Phi lambda_i over the
+ * boundary with face-constant Phi.  flux_face: K x F; phi, h: K x N.
+ * Either output may be NULL.  Solved as one K-RHS block PCG. */
+int qpat_forward(qpat_mesh_t mesh, const qpat_params* prm, const double* kappa,
+                 const double* mu, int K, const double* flux_face,
+                 double* phi, double* h);
+int qpat_forward_dev(qpat_mesh_t mesh, const qpat_params* prm, const double* kappa,
+                     const double* mu, int K, const double* flux_face,
+                     double* phi, double* h, void* stream);
+
+/* out = w o (J s), stacked over K illuminations (Appendix):
+ *   J s = diag(mu) K^{-1} (G1 diag(kappa) s1 + G2 diag(mu) s2) + diag(phi) diag(mu) s2
+ * with G1_ij = -integral phi_j grad(varphi).grad(phi_i), G2_ij = -integral phi_j varphi phi_i.
+ * phi: K x N forward solutions at (kappa, mu); w: K x N whitening weights
+ * Gamma^{-1/2} (NULL = 1); s: 2N; out: K x N.  The G matrices are never formed. */
+int qpat_jvp(qpat_mesh_t mesh, const qpat_params* prm, const double* kappa,
+             const double* mu, int K, const double* phi, const double* w,
+             const double* s, double* out);
+int qpat_jvp_dev(qpat_mesh_t mesh, const qpat_params* prm, const double* kappa,
+                 const double* mu, int K, const double* phi, const double* w,
+                 const double* s, double* out, void* stream);
+
+/* out = J^T (w o t) summed over the K illuminations (Appendix):
+ *   J^T t = blkdiag(kappa, mu) ([G1^T; G2] K^{-1} diag(mu) t + [0; diag(phi) t]).
+ * t: K x N; out: 2N. */
+int qpat_vjp(qpat_mesh_t mesh, const qpat_params* prm, const double* kappa,
+             const double* mu, int K, const double* phi, const double* w,
+             const double* t, double* out);
+int qpat_vjp_dev(qpat_mesh_t mesh, const qpat_params* prm, const double* kappa,
+                 const double* mu, int K, const double* phi, const double* w,
+                 const double* t, double* out, void* stream);
+
+/* One Jv and one J^T w of independent inputs solved together as a single
+ * 2K-RHS block PCG (the K solves of each are independent): out_jv = w o (J s)
+ * (K x N) and out_vjp = J^T (w o t) (2N). */
+int qpat_jvp_vjp_pair_dev(qpat_mesh_t mesh, const qpat_params* prm,
+                          const double* kappa, const double* mu, int K,
+                          const double* phi, const double* w, const double* s,
+                          const double* t, double* out_jv, double* out_vjp,
+                          void* stream);
+
+/* ------------------------------------------------------------- prior */
+
+/* out = M_delta^{-1} rhs with M_delta = blkdiag(M(kt), (b/a) M(mt)) + delta I
+ * (Eqs. (14), (16), (19)); M(u) is the FE matrix of -div(c_u grad) with
+ * natural boundary condition and the Perona-Malik lagged diffusivity
+ * c_u = r'(|grad u|)/|grad u| = 1/(1 + |grad u|^2/T^2) per tet (Eq. (10)).
+ * kt, mt: N; rhs, out: 2N.  Uses prm->T, b_over_a, delta. */
+int qpat_prior_solve(qpat_mesh_t mesh, const qpat_params* prm, const double* kt,
+                     const double* mt, const double* rhs, double* out);
+int qpat_prior_solve_dev(qpat_mesh_t mesh, const qpat_params* prm, const double* kt,
+                         const double* mt, const double* rhs, double* out,
+                         void* stream);
+
+/* ------------------------------------------------------- Algorithm 1 */
+
+/* Algorithm 1 with step 0 (Sec. 5) and K stacked illuminations (Sec. 4):
+ * background fit (unless kappa0_mu0 != NULL), mu_tilde initialisation,
+ * step 0 (kappa-only LSQR), then linearise / lagged diffusivity /
+ * priorconditioned LSQR (Eqs. (21)-(22)) / acceptance until max_lin
+ * linearisations or a rejected step.  flux_face: K x F; chi, sigma: K x N
+ * (Gamma = diag(sigma^2)); kappa, mu: N outputs; rep may be NULL.
+ * Host pointers; blocks until done. */
+int qpat_reconstruct(qpat_mesh_t mesh, const qpat_params* prm, int K,
+                     const double* flux_face, const double* chi,
+                     const double* sigma, const double* kappa0_mu0,
+                     double* kappa, double* mu, qpat_report* rep);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* QPAT_H */

@@ -40,7 +40,7 @@ __all__ = [
     "assemble_robin", "load_vector", "load_vector_nodal", "flux_patch", "system_matrix", "Factor",
     "forward", "G1_matrix", "G2_matrix", "jvp", "vjp", "lagged_weights",
     "prior_matrix", "prior_solve", "lsqr_prior", "fit_background", "init_mu",
-    "reconstruct", "measure", "nonlinear_residual",
+    "reconstruct", "measure", "nonlinear_residual", "simulate_data",
 ]
 
 
@@ -533,10 +533,32 @@ def fit_background(mesh: Mesh, flux, chi, w, grid: int = 9, gn_steps: int = 10):
 def init_mu(chi, phi0, mu0):
     """mu_init = (1/K) sum_k chi^(k) / phi0^(k) (Algorithm 1 with the
     multi-illumination rule of Sec. 4); mu_tilde = log(mu_init / mu0).
-    Reading: mu_init is clamped below at 1e-12 mu0 before the logarithm."""
+    Reading (the paper assumes phi0 > 0): a P1 solution can undershoot to
+    phi0 <= 0 far from the sources, so where the average is not positive
+    mu_init = mu0, and mu_init is then clipped into [mu0 / 10, 10 mu0]."""
     mu_init = np.mean(chi / phi0, axis=0)
-    mu_init = np.maximum(mu_init, 1e-12 * mu0)
+    mu_init = np.where(mu_init > 0, mu_init, mu0)
+    mu_init = np.clip(mu_init, 0.1 * mu0, 10.0 * mu0)
     return np.log(mu_init / mu0)
+
+
+def simulate_data(cfg, noise_seed: int, floor: float = 1e-3):
+    """Synthetic measurement of Sec. 5 (Test 1): h on the nested 2x finer
+    mesh, injected onto the coarse nodes (the interpolation P), plus Gaussian
+    noise eta_i ~ N(0, sigma_i^2) with sigma_i = 0.01 |h_i|.  Reading: sigma
+    gets a floor of `floor` x max|h| so that Gamma stays positive definite
+    where the P1 data is ~0.  cfg is a qpat_synth.Config.
+    Returns (chi, sigma, h), each K x N on the coarse nodes."""
+    import qpat_synth as S
+    xf, tf = S.kuhn_cube(2 * cfg.n - 1, cfg.L)
+    mf = Mesh(xf, tf)
+    kf, muf = cfg.coefficients(xf)
+    flf = np.stack([flux_patch(mf, p.center, p.normal, p.half_w, p.amp) for p in cfg.patches])
+    hf = measure(mf, kf, muf, flf)
+    h = hf[:, S.fine_to_coarse_index(cfg.n)]
+    sig = 0.01 * np.abs(h) + floor * np.abs(h).max()
+    chi = h + sig * S.noise_draws(noise_seed, h.shape)
+    return chi, sig, h
 
 
 @dataclasses.dataclass

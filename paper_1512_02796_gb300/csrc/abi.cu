@@ -1,0 +1,514 @@
+// C ABI: mesh handles, workspace, the linear-solve drivers (FP64 PCG and
+// FP32 PCG inside FP64 iterative refinement) and the forward / Jacobian /
+// prior entry points.  Algorithm 1 lives in recon.cu.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <map>
+#include <string>
+#include <vector>
+
+#include "abi_internal.h"
+
+namespace qpat {
+
+thread_local std::string g_err;
+
+int fail(int code, const std::string& msg) {
+    g_err = msg;
+    return code;
+}
+
+int cuda_fail(cudaError_t e, const char* where) {
+    return fail(QPAT_ECUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+void* Workspace::get_bytes(const std::string& name, size_t bytes, cudaStream_t s, cudaError_t* err) {
+    *err = cudaSuccess;
+    auto it = bufs.find(name);
+    if (it != bufs.end() && it->second.second >= bytes) return it->second.first;
+    if (it != bufs.end()) {
+        cudaStreamSynchronize(s);
+        cudaFree(it->second.first);
+        bufs.erase(it);
+    }
+    void* p = nullptr;
+    size_t alloc = std::max<size_t>(bytes, 256);
+    *err = cudaMalloc(&p, alloc);
+    if (*err != cudaSuccess) return nullptr;
+    bufs[name] = {p, alloc};
+    return p;
+}
+
+void Workspace::release() {
+    for (auto& kv : bufs) cudaFree(kv.second.first);
+    bufs.clear();
+}
+
+int round_rhs(int K) {
+    if (K <= 1) return 1;
+    if (K <= 2) return 2;
+    if (K <= 4) return 4;
+    if (K <= 8) return 8;
+    if (K <= 16) return 16;
+    return -1;
+}
+
+namespace {
+
+__global__ void k_mul(int64_t n, const double* a, const double* b, double* out) {
+    for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x)
+        out[i] = a[i] * b[i];
+}
+
+__global__ void k_exp_scale(int64_t n, double c0, const double* u, double* out) {
+    for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x)
+        out[i] = c0 * exp(u[i]);
+}
+
+// out[l*R + r] = d[l] * x[l*R + r]
+__global__ void k_rowscale(int64_t N, int R, const double* d, const double* x, double* out) {
+    for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < N * R; i += int64_t(gridDim.x) * blockDim.x)
+        out[i] = d[i / R] * x[i];
+}
+
+// Jv epilogue: out = w o (mu o x + phi o (mu o s2))      (Appendix)
+__global__ void k_jv_out(int64_t N, int R, const double* mu, const double* b, const double* x, const double* phi,
+                         const double* w, double* out) {
+    for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < N * R; i += int64_t(gridDim.x) * blockDim.x) {
+        const int64_t l = i / R;
+        const double v = mu[l] * x[i] + phi[i] * b[l];
+        out[i] = w ? w[i] * v : v;
+    }
+}
+
+// J^T epilogue: ok = kappa o y0 ; om = mu o (y1 + sum_r phi_r tw_r)     (Appendix)
+__global__ void k_jt_out(int64_t N, int R, const double* kappa, const double* mu, const double* y,
+                         const double* phi, const double* tw, double* ok, double* om) {
+    for (int64_t l = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; l < N; l += int64_t(gridDim.x) * blockDim.x) {
+        double s = 0.0;
+        for (int r = 0; r < R; ++r) s += phi[l * R + r] * tw[l * R + r];
+        ok[l] = kappa[l] * y[2 * l];
+        om[l] = mu[l] * (y[2 * l + 1] + s);
+    }
+}
+
+__global__ void k_sqrt_vec(int n, const double* in, double* out) {
+    if (threadIdx.x < n) out[threadIdx.x] = sqrt(in[threadIdx.x]);
+}
+
+int grid_of(int64_t n) {
+    int64_t g = (n + 255) / 256;
+    return int(std::max<int64_t>(1, std::min<int64_t>(g, 152 * 16)));
+}
+
+}  // namespace
+
+void k_mul_launch(int64_t n, const double* a, const double* b, double* out, cudaStream_t s) {
+    k_mul<<<grid_of(n), 256, 0, s>>>(n, a, b, out);
+}
+void k_exp_scale_launch(int64_t n, double c0, const double* u, double* out, cudaStream_t s) {
+    k_exp_scale<<<grid_of(n), 256, 0, s>>>(n, c0, u, out);
+}
+void k_rowscale_launch(int64_t N, int R, const double* d, const double* x, double* out, cudaStream_t s) {
+    k_rowscale<<<grid_of(N * R), 256, 0, s>>>(N, R, d, x, out);
+}
+void k_jv_out_launch(int64_t N, int R, const double* mu, const double* b, const double* x, const double* phi,
+                     const double* w, double* out, cudaStream_t s) {
+    k_jv_out<<<grid_of(N * R), 256, 0, s>>>(N, R, mu, b, x, phi, w, out);
+}
+void k_jt_out_launch(int64_t N, int R, const double* kappa, const double* mu, const double* y, const double* phi,
+                     const double* tw, double* ok, double* om, cudaStream_t s) {
+    k_jt_out<<<grid_of(N), 256, 0, s>>>(N, R, kappa, mu, y, phi, tw, ok, om);
+}
+
+// --------------------------------------------------------------------------
+// Linear-solve drivers
+// --------------------------------------------------------------------------
+
+// Operator state of one K(kappa, mu) or M_delta(kt, mt), library order.
+int prepare_K(qpat_mesh_s* M, const double* kap_l, const double* mu_l, OpState& st, cudaStream_t s,
+              const char* tag) {
+    const int64_t N = M->h.N;
+    cudaError_t e = cudaSuccess;
+    const std::string t(tag);
+    st.kind = OP_K;
+    st.c1_64 = kap_l;
+    st.c2_64 = mu_l;
+    st.c1_32 = M->ws.get<float>(t + ".c1_32", N, s, &e);
+    st.c2_32 = M->ws.get<float>(t + ".c2_32", N, s, &e);
+    st.inv64 = M->ws.get<double>(t + ".inv64", N, s, &e);
+    st.inv32 = M->ws.get<float>(t + ".inv32", N, s, &e);
+    if (e != cudaSuccess) return cuda_fail(e, "workspace");
+    if ((e = launch_cast_d2f(N, kap_l, st.c1_32, s)) != cudaSuccess) return cuda_fail(e, "cast");
+    if ((e = launch_cast_d2f(N, mu_l, st.c2_32, s)) != cudaSuccess) return cuda_fail(e, "cast");
+    if ((e = launch_invdiag_K(M->d, kap_l, mu_l, st.inv64, st.inv32, s)) != cudaSuccess)
+        return cuda_fail(e, "invdiag_K");
+    return QPAT_OK;
+}
+
+int prepare_prior(qpat_mesh_s* M, const double* kt_l, const double* mt_l, double T, double b_over_a, double delta,
+                  OpState& st, cudaStream_t s) {
+    const int64_t N = M->h.N;
+    cudaError_t e = cudaSuccess;
+    st.kind = OP_PRIOR;
+    st.c1_64 = kt_l;
+    st.c2_64 = mt_l;
+    st.inv_T2 = 1.0 / (T * T);
+    st.scale1 = b_over_a;
+    st.delta = delta;
+    st.c1_32 = M->ws.get<float>("opP.c1_32", N, s, &e);
+    st.c2_32 = M->ws.get<float>("opP.c2_32", N, s, &e);
+    st.inv64 = M->ws.get<double>("opP.inv64", 2 * N, s, &e);
+    st.inv32 = M->ws.get<float>("opP.inv32", 2 * N, s, &e);
+    if (e != cudaSuccess) return cuda_fail(e, "workspace");
+    if ((e = launch_cast_d2f(N, kt_l, st.c1_32, s)) != cudaSuccess) return cuda_fail(e, "cast");
+    if ((e = launch_cast_d2f(N, mt_l, st.c2_32, s)) != cudaSuccess) return cuda_fail(e, "cast");
+    if ((e = launch_invdiag_prior(M->d, kt_l, mt_l, st.inv_T2, b_over_a, delta, st.inv64, st.inv32, s)) !=
+        cudaSuccess)
+        return cuda_fail(e, "invdiag_prior");
+    return QPAT_OK;
+}
+
+static cudaError_t apply_op64(qpat_mesh_s* M, const OpState& st, int R, const double* x, double* y,
+                              cudaStream_t s) {
+    if (st.kind == OP_K) return launch_apply_K<double>(M->d, R, st.c1_64, st.c2_64, 1, 1.0, x, y, s);
+    return launch_apply_prior<double>(M->d, st.c1_64, st.c2_64, st.inv_T2, st.scale1, st.delta, x, y, s);
+}
+
+static int pcg_status(int st, const char* what) {
+    if (st == QPAT_OK) return QPAT_OK;
+    if (st == QPAT_ETIMEOUT) return fail(st, std::string(what) + ": grid barrier timed out");
+    if (st == QPAT_EBREAKDOWN) return fail(st, std::string(what) + ": PCG breakdown (p.Ap <= 0 or not finite)");
+    if (st == QPAT_ENOCONV) return fail(st, std::string(what) + ": PCG iteration cap reached");
+    return fail(st, std::string(what) + ": PCG failed");
+}
+
+// Solves A X = B for R right-hand sides (library order, N x R node-major,
+// FP64 in and out).  precision 0: FP64 PCG to rtol.  precision 1: X = 0,
+// then sweeps of  r = B - A X (FP64 element apply), d = A32^-1 (r / |r|)
+// (FP32 PCG to a loose tolerance), X += |r| d,  until |r_j| <= rtol |B_j|.
+int solve(qpat_mesh_s* M, const OpState& st, const SolveOpts& so, int R, const double* B, double* X,
+          cudaStream_t s) {
+    const int64_t N = M->h.N;
+    const int64_t n = N * R;
+    cudaError_t e = cudaSuccess;
+    PcgWork w{};
+    const char* pfx = st.kind == OP_K ? "pcg" : "pcgP";
+    auto nm = [&](const char* a) { return std::string(pfx) + "." + a; };
+    const size_t esz = so.precision == 0 ? sizeof(double) : sizeof(float);
+    w.r = M->ws.get_bytes(nm("r"), n * esz, s, &e);
+    w.p0 = M->ws.get_bytes(nm("p0"), n * esz, s, &e);
+    w.p1 = M->ws.get_bytes(nm("p1"), n * esz, s, &e);
+    w.q = M->ws.get_bytes(nm("q"), n * esz, s, &e);
+    w.partials = M->ws.get<double>("pcg.partials", size_t(2) * pcg_max_grid() * 3 * 16, s, &e);
+    w.bar = M->ws.get<unsigned>("pcg.bar", 2, s, &e);
+    w.status = M->ws.get<int>("pcg.status", 1, s, &e);
+    w.iters = M->ws.get<int>("pcg.iters", 1, s, &e);
+    w.stats = M->ws.get<double>("pcg.stats", 32, s, &e);
+    double* hpin = M->host_scratch;  // pinned, >= 64 doubles
+    if (e != cudaSuccess) return cuda_fail(e, "workspace");
+    const int OP = st.kind;
+
+    if (so.precision == 0) {
+        w.b = const_cast<double*>(B);
+        w.x = X;
+        OpParams<double> op{st.c1_64, st.c2_64, st.inv_T2, st.scale1, st.delta, 1};
+        if (M->timing) cudaEventRecord(M->ev0, s);
+        if ((e = launch_pcg<double>(M->d, OP, R, op, st.inv64, w, so.rtol, so.maxit, s, nullptr)) != cudaSuccess)
+            return cuda_fail(e, "pcg launch");
+        if (M->timing) cudaEventRecord(M->ev1, s);
+        int hst[2];
+        if ((e = cudaMemcpyAsync(hst, w.status, sizeof(int), cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
+            (e = cudaMemcpyAsync(hst + 1, w.iters, sizeof(int), cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
+            (e = cudaStreamSynchronize(s)) != cudaSuccess)
+            return cuda_fail(e, "pcg sync");
+        if (M->timing) {
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, M->ev0, M->ev1);
+            M->pcg_ms += ms;
+        }
+        M->stats.pcg_iters += hst[1];
+        M->stats.solves += R;
+        M->stats.launches += 1;
+        return pcg_status(hst[0], pfx);
+    }
+
+    // ---- FP32 PCG inside FP64 refinement
+    double* Rres = M->ws.get<double>(nm("res64"), n, s, &e);
+    double* tmp = M->ws.get<double>(nm("tmp64"), n, s, &e);
+    float* b32 = M->ws.get<float>(nm("b32"), n, s, &e);
+    float* x32 = M->ws.get<float>(nm("x32"), n, s, &e);
+    double* dpart = M->ws.get<double>("dots.partial", 608 * 16, s, &e);
+    double* dnorm = M->ws.get<double>(nm("norms"), 64, s, &e);  // [0,R): |r|^2, [16,16+R): |B|^2, [32,..): |r|
+    if (e != cudaSuccess) return cuda_fail(e, "workspace");
+    w.b = b32;
+    w.x = x32;
+    OpParams<float> op{st.c1_32, st.c2_32, float(st.inv_T2), float(st.scale1), float(st.delta), 1};
+    if ((e = cudaMemsetAsync(X, 0, n * sizeof(double), s)) != cudaSuccess) return cuda_fail(e, "memset");
+    if ((e = cudaMemcpyAsync(Rres, B, n * sizeof(double), cudaMemcpyDeviceToDevice, s)) != cudaSuccess)
+        return cuda_fail(e, "copy");
+    if ((e = launch_dots<double>(N, R, B, B, dpart, dnorm + 16, s)) != cudaSuccess) return cuda_fail(e, "dots");
+    if ((e = cudaMemcpyAsync(hpin + 16, dnorm + 16, R * sizeof(double), cudaMemcpyDeviceToHost, s)) != cudaSuccess)
+        return cuda_fail(e, "copy");
+    int sweeps = 0;
+    for (;;) {
+        if ((e = launch_dots<double>(N, R, Rres, Rres, dpart, dnorm, s)) != cudaSuccess) return cuda_fail(e, "dots");
+        if ((e = cudaMemcpyAsync(hpin, dnorm, R * sizeof(double), cudaMemcpyDeviceToHost, s)) != cudaSuccess)
+            return cuda_fail(e, "copy");
+        if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return cuda_fail(e, "sync");
+        bool done = true;
+        for (int r = 0; r < R; ++r) {
+            if (!std::isfinite(hpin[r])) return fail(QPAT_EBREAKDOWN, "refinement: residual not finite");
+            if (hpin[r] > so.rtol * so.rtol * hpin[16 + r]) done = false;
+        }
+        if (done) break;
+        if (sweeps >= so.max_sweeps) return fail(QPAT_ENOCONV, "refinement: sweep cap reached");
+        ++sweeps;
+        k_sqrt_vec<<<1, 32, 0, s>>>(R, dnorm, dnorm + 32);
+        if ((e = launch_cast_d2f_scaled(N, R, Rres, dnorm + 32, b32, s)) != cudaSuccess) return cuda_fail(e, "cast");
+        if (M->timing) cudaEventRecord(M->ev0, s);
+        if ((e = launch_pcg<float>(M->d, OP, R, op, st.inv32, w, so.inner_rtol, so.maxit, s, nullptr)) !=
+            cudaSuccess)
+            return cuda_fail(e, "pcg32 launch");
+        if (M->timing) cudaEventRecord(M->ev1, s);
+        int hst[2];
+        if ((e = cudaMemcpyAsync(hst, w.status, sizeof(int), cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
+            (e = cudaMemcpyAsync(hst + 1, w.iters, sizeof(int), cudaMemcpyDeviceToHost, s)) != cudaSuccess)
+            return cuda_fail(e, "copy");
+        if ((e = launch_axpy_f2d_scaled(N, R, x32, dnorm + 32, X, s)) != cudaSuccess) return cuda_fail(e, "axpy");
+        if ((e = apply_op64(M, st, R, X, tmp, s)) != cudaSuccess) return cuda_fail(e, "apply64");
+        if ((e = launch_sub(n, B, tmp, Rres, s)) != cudaSuccess) return cuda_fail(e, "sub");
+        if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return cuda_fail(e, "sync");
+        if (M->timing) {
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, M->ev0, M->ev1);
+            M->pcg_ms += ms;
+        }
+        M->stats.pcg_iters += hst[1];
+        M->stats.launches += 1;
+        M->stats.refinements += 1;
+        // an inner run that stops at its cap still improves x; breakdown or timeout is fatal
+        if (hst[0] == QPAT_ETIMEOUT || hst[0] == QPAT_EBREAKDOWN) return pcg_status(hst[0], "pcg32");
+    }
+    M->stats.solves += R;
+    return QPAT_OK;
+}
+
+}  // namespace qpat
+
+using namespace qpat;
+
+// --------------------------------------------------------------------------
+// Public entry points
+// --------------------------------------------------------------------------
+
+extern "C" {
+
+const char* qpat_last_error(void) { return g_err.c_str(); }
+
+void qpat_default_params(qpat_params* p) {
+    if (!p) return;
+    std::memset(p, 0, sizeof(*p));
+    p->T = 5e-3;
+    p->b_over_a = 1.0;
+    p->delta = 1e-6;
+    p->tau = 1e-2;
+    p->m0 = 10;
+    p->max_lin = 5;
+    p->max_lsqr = 50;
+    p->fixed_counts = 0;
+    p->precision = 0;
+    p->max_pcg_iter = 20000;
+    p->pcg_rtol = 1e-13;
+    p->fit_grid = 9;
+    p->fit_gn_steps = 10;
+    p->patch_nodes = 0;
+}
+
+int qpat_mesh_ex(const double* xyz, int64_t N, const int32_t* tets, int64_t E, int patch_nodes, qpat_mesh_t* out) {
+    if (!out) return fail(QPAT_EINVAL, "qpat_mesh: out is NULL");
+    *out = nullptr;
+    auto* M = new qpat_mesh_s();
+    std::string msg = build_host_mesh(xyz, N, tets, E, patch_nodes, M->h);
+    if (!msg.empty()) {
+        delete M;
+        return fail(QPAT_EINVAL, msg);
+    }
+    int rc = upload_mesh(M);
+    if (rc != QPAT_OK) {
+        qpat_mesh_free(M);
+        return rc;
+    }
+    *out = M;
+    return QPAT_OK;
+}
+
+int qpat_mesh_host_info(const double* xyz, int64_t N, const int32_t* tets, int64_t E, int patch_nodes,
+                        int64_t* info8, int32_t* faces, int32_t* perm) {
+    if (!info8) return fail(QPAT_EINVAL, "qpat_mesh_host_info: info is NULL");
+    HostMesh h;
+    std::string msg = build_host_mesh(xyz, N, tets, E, patch_nodes, h);
+    if (!msg.empty()) return fail(QPAT_EINVAL, msg);
+    // self-check of the patch structure: owned ranges tile [0, N); every tet
+    // that touches an owned node is listed; local ids map back to the tets
+    int64_t dup = 0;
+    for (int p = 0; p < h.P; ++p) {
+        const int ob = h.own_begin[p], oe = h.own_begin[p + 1], nb = h.node_ptr[p];
+        for (int t = h.tet_ptr[p]; t < h.tet_ptr[p + 1]; ++t) {
+            int owned = 0;
+            for (int a = 0; a < 4; ++a) {
+                const int li = h.tet_loc[4 * t + a];
+                if (li >= h.node_ptr[p + 1] - nb) return fail(QPAT_EINVAL, "host check: local id out of range");
+                const int g = h.nodes[nb + li];
+                if ((li < oe - ob) != (g >= ob && g < oe)) return fail(QPAT_EINVAL, "host check: owned flag wrong");
+                owned |= (g >= ob && g < oe);
+            }
+            if (!owned) return fail(QPAT_EINVAL, "host check: patch tet without owned node");
+        }
+        dup += h.tet_ptr[p + 1] - h.tet_ptr[p];
+    }
+    info8[0] = h.F;
+    info8[1] = h.P;
+    info8[2] = h.max_touched;
+    info8[3] = h.max_own;
+    info8[4] = h.max_ptets;
+    info8[5] = h.max_pfaces;
+    info8[6] = dup;  // sum over patches of listed tets (>= E; the excess is border duplication)
+    info8[7] = int64_t(h.face_ptr[h.P]);
+    if (faces) std::memcpy(faces, h.faces_caller.data(), sizeof(int32_t) * 3 * h.F);
+    if (perm) std::memcpy(perm, h.perm.data(), sizeof(int32_t) * h.N);
+    // every tet must be listed once per distinct patch owning one of its
+    // vertices (node g belongs to patch g / patch_nodes)
+    int64_t expect = 0;
+    for (int64_t e = 0; e < h.E; ++e) {
+        int pid[4];
+        for (int a = 0; a < 4; ++a) pid[a] = h.tets[4 * e + a] / h.patch_nodes;
+        std::sort(pid, pid + 4);
+        expect += 1 + (pid[1] != pid[0]) + (pid[2] != pid[1]) + (pid[3] != pid[2]);
+    }
+    if (expect != dup) return fail(QPAT_EINVAL, "host check: patch tet lists do not cover the mesh");
+    return QPAT_OK;
+}
+
+int qpat_mesh(const double* xyz, int64_t N, const int32_t* tets, int64_t E, qpat_mesh_t* out) {
+    return qpat_mesh_ex(xyz, N, tets, E, 512, out);
+}
+
+void qpat_mesh_free(qpat_mesh_t M) {
+    if (!M) return;
+    int cur = 0;
+    cudaGetDevice(&cur);
+    cudaSetDevice(M->device);
+    if (M->stream) cudaStreamSynchronize(M->stream);
+    M->ws.release();
+    if (M->ev0) cudaEventDestroy(M->ev0);
+    if (M->ev1) cudaEventDestroy(M->ev1);
+    for (void* p : M->dev_allocs) cudaFree(p);
+    if (M->host_scratch) cudaFreeHost(M->host_scratch);
+    if (M->stream) cudaStreamDestroy(M->stream);
+    cudaSetDevice(cur);
+    delete M;
+}
+
+int64_t qpat_mesh_num_nodes(qpat_mesh_t M) { return M ? M->h.N : -1; }
+int64_t qpat_mesh_num_tets(qpat_mesh_t M) { return M ? M->h.E : -1; }
+int64_t qpat_mesh_num_faces(qpat_mesh_t M) { return M ? M->h.F : -1; }
+int64_t qpat_mesh_num_patches(qpat_mesh_t M) { return M ? M->h.P : -1; }
+
+int qpat_mesh_faces(qpat_mesh_t M, int32_t* faces) {
+    if (!M || !faces) return fail(QPAT_EINVAL, "qpat_mesh_faces: NULL argument");
+    std::memcpy(faces, M->h.faces_caller.data(), sizeof(int32_t) * 3 * M->h.F);
+    return QPAT_OK;
+}
+
+int qpat_mesh_permutation(qpat_mesh_t M, int32_t* perm) {
+    if (!M || !perm) return fail(QPAT_EINVAL, "qpat_mesh_permutation: NULL argument");
+    std::memcpy(perm, M->h.perm.data(), sizeof(int32_t) * M->h.N);
+    return QPAT_OK;
+}
+
+int qpat_mesh_stats(qpat_mesh_t M, int64_t* out4) {
+    if (!M || !out4) return fail(QPAT_EINVAL, "qpat_mesh_stats: NULL argument");
+    out4[0] = M->stats.pcg_iters;
+    out4[1] = M->stats.solves;
+    out4[2] = M->stats.refinements;
+    out4[3] = M->stats.launches;
+    return QPAT_OK;
+}
+
+int qpat_mesh_reset_stats(qpat_mesh_t M) {
+    if (!M) return fail(QPAT_EINVAL, "qpat_mesh_reset_stats: NULL mesh");
+    M->stats = SolveStats();
+    M->pcg_ms = 0.0;
+    return QPAT_OK;
+}
+
+int qpat_mesh_set_timing(qpat_mesh_t M, int on) {
+    if (!M) return fail(QPAT_EINVAL, "qpat_mesh_set_timing: NULL mesh");
+    DeviceGuard dg(M->device);
+    if (on && !M->ev0) {
+        cudaError_t e = cudaEventCreate(&M->ev0);
+        if (e == cudaSuccess) e = cudaEventCreate(&M->ev1);
+        if (e != cudaSuccess) return cuda_fail(e, "qpat_mesh_set_timing");
+    }
+    M->timing = on ? 1 : 0;
+    return QPAT_OK;
+}
+
+int qpat_mesh_pcg_time(qpat_mesh_t M, double* ms) {
+    if (!M || !ms) return fail(QPAT_EINVAL, "qpat_mesh_pcg_time: NULL argument");
+    *ms = M->pcg_ms;
+    return QPAT_OK;
+}
+
+int qpat_flux_patch(qpat_mesh_t M, const double c[3], const double n[3], double half_w, double amp,
+                    double* flux_face) {
+    if (!M || !c || !n || !flux_face) return fail(QPAT_EINVAL, "qpat_flux_patch: NULL argument");
+    if (!(half_w >= 0.0) || (n[0] == 0 && n[1] == 0 && n[2] == 0))
+        return fail(QPAT_EINVAL, "qpat_flux_patch: bad half width or zero normal");
+    flux_patch_host(M->h, c, n, half_w, amp, flux_face);
+    return QPAT_OK;
+}
+
+int qpat_apply_K_dev(qpat_mesh_t M, int precision, const double* kappa, const double* mu, int R, const double* x,
+                     double* y, void* stream) {
+    if (!M || !kappa || !mu || !x || !y) return fail(QPAT_EINVAL, "qpat_apply_K_dev: NULL argument");
+    const int Rp = round_rhs(R);
+    if (R < 1 || Rp < 0) return fail(QPAT_EINVAL, "qpat_apply_K_dev: R must be in [1, 16]");
+    if (precision != 0 && precision != 1) return fail(QPAT_EINVAL, "qpat_apply_K_dev: precision must be 0 or 1");
+    DeviceGuard dg(M->device);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const int64_t N = M->h.N;
+    cudaError_t e = cudaSuccess;
+    double* kl = M->ws.get<double>("ak.k", N, s, &e);
+    double* ml = M->ws.get<double>("ak.m", N, s, &e);
+    double* xl = M->ws.get<double>("ak.x", N * Rp, s, &e);
+    double* yl = M->ws.get<double>("ak.y", N * Rp, s, &e);
+    if (e != cudaSuccess) return cuda_fail(e, "workspace");
+    // x, y are N x R node-major in caller order: treat as R rows of a "K x N"? no --
+    // gather row-wise: node-major caller layout means in[c*R + r]; use the K=1 helper per column.
+    if ((e = launch_to_lib<double, double>(M->d, 1, 1, kappa, kl, s)) != cudaSuccess) return cuda_fail(e, "to_lib");
+    if ((e = launch_to_lib<double, double>(M->d, 1, 1, mu, ml, s)) != cudaSuccess) return cuda_fail(e, "to_lib");
+    if ((e = launch_nodemajor_to_lib(M->d, R, Rp, x, xl, s)) != cudaSuccess) return cuda_fail(e, "to_lib");
+    if (precision == 0) {
+        if ((e = launch_apply_K<double>(M->d, Rp, kl, ml, 1, 1.0, xl, yl, s)) != cudaSuccess)
+            return cuda_fail(e, "apply_K");
+    } else {
+        float* k32 = M->ws.get<float>("ak.k32", N, s, &e);
+        float* m32 = M->ws.get<float>("ak.m32", N, s, &e);
+        float* x32 = M->ws.get<float>("ak.x32", N * Rp, s, &e);
+        float* y32 = M->ws.get<float>("ak.y32", N * Rp, s, &e);
+        if (e != cudaSuccess) return cuda_fail(e, "workspace");
+        launch_cast_d2f(N, kl, k32, s);
+        launch_cast_d2f(N, ml, m32, s);
+        launch_cast_d2f(N * Rp, xl, x32, s);
+        if ((e = launch_apply_K<float>(M->d, Rp, k32, m32, 1, 1.0f, x32, y32, s)) != cudaSuccess)
+            return cuda_fail(e, "apply_K32");
+        if ((e = launch_cast_f2d(N * Rp, y32, yl, s)) != cudaSuccess) return cuda_fail(e, "cast");
+    }
+    if ((e = launch_nodemajor_from_lib(M->d, R, Rp, yl, y, s)) != cudaSuccess) return cuda_fail(e, "from_lib");
+    return QPAT_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,133 @@
+// Internal state behind the C ABI (mesh handle, workspace, solve drivers).
+#pragma once
+
+#include <map>
+#include <string>
+#include <utility>
+#include <vector>
+
+#include "launch.h"
+
+namespace qpat {
+
+struct Workspace {
+    std::map<std::string, std::pair<void*, size_t>> bufs;
+    void* get_bytes(const std::string& name, size_t bytes, cudaStream_t s, cudaError_t* err);
+    template <typename T>
+    T* get(const std::string& name, size_t count, cudaStream_t s, cudaError_t* err) {
+        cudaError_t e = cudaSuccess;
+        T* p = static_cast<T*>(get_bytes(name, count * sizeof(T), s, &e));
+        if (e != cudaSuccess) *err = e;
+        return p;
+    }
+    void release();
+};
+
+struct SolveStats {
+    int64_t pcg_iters = 0;
+    int64_t solves = 0;
+    int64_t refinements = 0;
+    int64_t launches = 0;
+};
+
+struct OpState {
+    int kind = OP_K;
+    const double* c1_64 = nullptr;  // kappa (OP_K) or kappa_tilde (OP_PRIOR), library order
+    const double* c2_64 = nullptr;  // mu or mu_tilde
+    float* c1_32 = nullptr;
+    float* c2_32 = nullptr;
+    double* inv64 = nullptr;        // inverse diagonal (N, or N x 2 for the prior)
+    float* inv32 = nullptr;
+    double inv_T2 = 0, scale1 = 1, delta = 0;
+};
+
+struct SolveOpts {
+    int precision = 0;        // 0 FP64 PCG, 1 FP32 PCG + FP64 refinement
+    double rtol = 1e-13;
+    int maxit = 20000;
+    double inner_rtol = 1e-4;
+    int max_sweeps = 30;
+};
+
+struct DeviceGuard {
+    int prev = 0;
+    explicit DeviceGuard(int dev) {
+        cudaGetDevice(&prev);
+        if (prev != dev) cudaSetDevice(dev);
+    }
+    ~DeviceGuard() {
+        int cur = 0;
+        cudaGetDevice(&cur);
+        if (cur != prev) cudaSetDevice(prev);
+    }
+};
+
+}  // namespace qpat
+
+struct qpat_mesh_s {
+    qpat::HostMesh h;
+    qpat::MeshDev d{};
+    std::vector<void*> dev_allocs;
+    int device = 0;
+    cudaStream_t stream = nullptr;   // used by the host-pointer entry points
+    double* host_scratch = nullptr;  // pinned, 256 doubles
+    qpat::Workspace ws;
+    qpat::SolveStats stats;
+    // optional CUDA-event timing of every PCG launch (on the launching stream)
+    int timing = 0;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    double pcg_ms = 0.0;
+};
+
+namespace qpat {
+
+extern thread_local std::string g_err;
+int fail(int code, const std::string& msg);
+int cuda_fail(cudaError_t e, const char* where);
+int round_rhs(int K);
+
+int upload_mesh(qpat_mesh_s* M);
+int prepare_K(qpat_mesh_s* M, const double* kap_l, const double* mu_l, OpState& st, cudaStream_t s,
+              const char* tag = "opK");
+int prepare_prior(qpat_mesh_s* M, const double* kt_l, const double* mt_l, double T, double b_over_a, double delta,
+                  OpState& st, cudaStream_t s);
+int solve(qpat_mesh_s* M, const OpState& st, const SolveOpts& so, int R, const double* B, double* X,
+          cudaStream_t s);
+SolveOpts solve_opts(const qpat_params* prm);
+
+// node-major caller layout (x[c*R + r], r < R) <-> library N x Rp (zero padding)
+cudaError_t launch_nodemajor_to_lib(const MeshDev& m, int R, int Rp, const double* in, double* out, cudaStream_t s);
+cudaError_t launch_nodemajor_from_lib(const MeshDev& m, int R, int Rp, const double* in, double* out,
+                                      cudaStream_t s);
+cudaError_t launch_cast_f2d(int64_t n, const float* in, double* out, cudaStream_t s);
+
+void k_mul_launch(int64_t n, const double* a, const double* b, double* out, cudaStream_t s);
+void k_exp_scale_launch(int64_t n, double c0, const double* u, double* out, cudaStream_t s);
+void k_rowscale_launch(int64_t N, int R, const double* d, const double* x, double* out, cudaStream_t s);
+void k_jv_out_launch(int64_t N, int R, const double* mu, const double* b, const double* x, const double* phi,
+                     const double* w, double* out, cudaStream_t s);
+void k_jt_out_launch(int64_t N, int R, const double* kappa, const double* mu, const double* y, const double* phi,
+                     const double* tw, double* ok, double* om, cudaStream_t s);
+
+// Linearisation state on the device (library order): the coefficients,
+// the forward solutions and the K operator (recon.cu and ops.cu).
+struct LinState {
+    int K = 0, R = 0;
+    double* kap = nullptr;   // N
+    double* mu = nullptr;    // N
+    double* phi = nullptr;   // N x R
+    double* w = nullptr;     // N x R whitening (nullptr = 1)
+    OpState opK;
+};
+
+// J s and J^T t on library-order device data (ops.cu).
+int jvp_lib(qpat_mesh_s* M, const SolveOpts& so, LinState& L, const double* s1, const double* s2, double* out,
+            cudaStream_t s);
+int vjp_lib(qpat_mesh_s* M, const SolveOpts& so, LinState& L, const double* t, double* o1, double* o2,
+            cudaStream_t s);
+int forward_lib(qpat_mesh_s* M, const SolveOpts& so, LinState& L, const double* flux_dev, cudaStream_t s);
+
+}  // namespace qpat
+
+extern "C" int qpat_mesh_stats(qpat_mesh_t M, int64_t* out4);
+extern "C" int qpat_mesh_reset_stats(qpat_mesh_t M);

@@ -1,0 +1,259 @@
+// Element-level device code shared by every patch kernel.
+//
+// All element operators are written with the cofactor vectors of a tet:
+// with edges e_j = p_j - p_0 (j = 1..3), c_1 = e_2 x e_3, c_2 = e_3 x e_1,
+// c_3 = e_1 x e_2, c_0 = -(c_1 + c_2 + c_3) and det = e_1 . c_1, the P1
+// barycentric gradients are grad(lambda_i) = c_i / det and |T| = |det| / 6.
+// For a P1 field x_h on the tet, G_x = sum_j x_j c_j = sum_{j>=1} (x_j - x_0) c_j
+// is det * grad(x_h), so |T| grad(lambda_i) . grad(x_h) = (c_i . G_x) / (6 |det|).
+//
+// The mass term with a P1 coefficient mu uses the exact integral of
+// lambda_i lambda_j lambda_k (|T|/20, /60, /120 for 3, 2, 1 distinct
+// indices), summed in closed form:
+//   (M(mu) x)_i = |T|/120 [ (S_mu + mu_i)(S_x + x_i) + mu.x + mu_i x_i ],
+// S_mu, S_x the sums over the 4 vertices.  The Robin boundary term
+// 1/2 integral x v (Appendix weak form) on a face F adds |F|/24 (S_x^F + x_i).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "qpat_internal.h"
+
+namespace qpat {
+
+enum OpKind { OP_K = 0, OP_PRIOR = 1 };
+
+constexpr int kThreads = 256;
+
+template <typename T>
+struct OpParams {
+    const T* c1;     // OP_K: nodal kappa (or kappa o s1); OP_PRIOR: u for block 0 (kappa_tilde)
+    const T* c2;     // OP_K: nodal mu (or mu o s2);      OP_PRIOR: u for block 1 (mu_tilde)
+    T inv_T2;        // OP_PRIOR: 1 / T^2 of the Perona-Malik weight (Eq. (10), (14))
+    T scale1;        // OP_PRIOR: b / a on block 1 (Eq. (16))
+    T delta;         // OP_PRIOR: delta of M_delta (Eq. (19))
+    int robin;       // OP_K: include the Robin boundary term
+};
+
+template <typename T>
+__device__ __forceinline__ void tet_cofactors(const T p[4][3], T c[4][3], T& ad) {
+    T e1[3], e2[3], e3[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        e1[k] = p[1][k] - p[0][k];
+        e2[k] = p[2][k] - p[0][k];
+        e3[k] = p[3][k] - p[0][k];
+    }
+    c[1][0] = e2[1] * e3[2] - e2[2] * e3[1];
+    c[1][1] = e2[2] * e3[0] - e2[0] * e3[2];
+    c[1][2] = e2[0] * e3[1] - e2[1] * e3[0];
+    c[2][0] = e3[1] * e1[2] - e3[2] * e1[1];
+    c[2][1] = e3[2] * e1[0] - e3[0] * e1[2];
+    c[2][2] = e3[0] * e1[1] - e3[1] * e1[0];
+    c[3][0] = e1[1] * e2[2] - e1[2] * e2[1];
+    c[3][1] = e1[2] * e2[0] - e1[0] * e2[2];
+    c[3][2] = e1[0] * e2[1] - e1[1] * e2[0];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) c[0][k] = -(c[1][k] + c[2][k] + c[3][k]);
+    T det = e1[0] * c[1][0] + e1[1] * c[1][1] + e1[2] * c[1][2];
+    ad = fabs(det);
+}
+
+// G_x = sum_{j>=1} (x_j - x_0) c_j
+template <typename T>
+__device__ __forceinline__ void grad_vec(const T c[4][3], const T x[4], T G[3]) {
+    const T d1 = x[1] - x[0], d2 = x[2] - x[0], d3 = x[3] - x[0];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) G[k] = d1 * c[1][k] + d2 * c[2][k] + d3 * c[3][k];
+}
+
+// y_i = sk (c_i . G) for i = 0..3 (c_0 term from the others)
+template <typename T>
+__device__ __forceinline__ void stiff_rows(const T c[4][3], const T G[3], T sk, T y[4]) {
+    T s1 = sk * (c[1][0] * G[0] + c[1][1] * G[1] + c[1][2] * G[2]);
+    T s2 = sk * (c[2][0] * G[0] + c[2][1] * G[1] + c[2][2] * G[2]);
+    T s3 = sk * (c[3][0] * G[0] + c[3][1] * G[1] + c[3][2] * G[2]);
+    y[0] = -(s1 + s2 + s3);
+    y[1] = s1;
+    y[2] = s2;
+    y[3] = s3;
+}
+
+// y_i += vm [ (S_m + m_i)(S_x + x_i) + m.x + m_i x_i ],  vm = |T| / 120
+template <typename T>
+__device__ __forceinline__ void mass_rows_add(const T m[4], T Sm, const T x[4], T vm, T y[4]) {
+    const T Sx = x[0] + x[1] + x[2] + x[3];
+    const T mx = m[0] * x[0] + m[1] * x[1] + m[2] * x[2] + m[3] * x[3];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) y[i] += vm * ((Sm + m[i]) * (Sx + x[i]) + mx + m[i] * x[i]);
+}
+
+// Shared-memory staging of one patch.  Strides use the mesh-wide maxima so
+// that the layout is fixed for the kernel.
+template <typename T, int R>
+struct PatchSmem {
+    T* px;
+    T* py;
+    T* pz;
+    T* c1;
+    T* c2;
+    T* xin;   // touched x R, node-major
+    T* yout;  // owned x R, node-major
+    __device__ void carve(T* base, int MT, int MO) {
+        px = base;
+        py = px + MT;
+        pz = py + MT;
+        c1 = pz + MT;
+        c2 = c1 + MT;
+        xin = c2 + MT;
+        yout = xin + size_t(MT) * R;
+        (void)MO;
+    }
+    static size_t bytes(int MT, int MO) { return sizeof(T) * (size_t(MT) * (5 + R) + size_t(MO) * R); }
+};
+
+template <typename T>
+__device__ __forceinline__ const T* xyz_of(const MeshDev& m);
+template <>
+__device__ __forceinline__ const double* xyz_of<double>(const MeshDev& m) { return m.xyz64; }
+template <>
+__device__ __forceinline__ const float* xyz_of<float>(const MeshDev& m) { return m.xyz32; }
+
+template <typename T>
+__device__ __forceinline__ T face_area_of(const MeshDev& m, int i);
+template <>
+__device__ __forceinline__ double face_area_of<double>(const MeshDev& m, int i) { return __ldg(m.pface_area64 + i); }
+template <>
+__device__ __forceinline__ float face_area_of<float>(const MeshDev& m, int i) { return __ldg(m.pface_area32 + i); }
+
+// Stage coordinates and the two nodal coefficients of the touched nodes.
+template <typename T, int R>
+__device__ __forceinline__ void stage_static(const MeshDev& m, int nb, int nt, const PatchSmem<T, R>& s,
+                                             const OpParams<T>& op) {
+    const T* xyz = xyz_of<T>(m);
+    for (int i = threadIdx.x; i < nt; i += blockDim.x) {
+        const int g = __ldg(m.nodes + nb + i);
+        s.px[i] = __ldg(xyz + 3 * g + 0);
+        s.py[i] = __ldg(xyz + 3 * g + 1);
+        s.pz[i] = __ldg(xyz + 3 * g + 2);
+        s.c1[i] = __ldg(op.c1 + g);
+        s.c2[i] = __ldg(op.c2 + g);
+    }
+}
+
+template <typename T, int R>
+__device__ __forceinline__ void load_tet(const PatchSmem<T, R>& s, const ushort4 lv, T p[4][3]) {
+    const int v[4] = {lv.x, lv.y, lv.z, lv.w};
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+        p[a][0] = s.px[v[a]];
+        p[a][1] = s.py[v[a]];
+        p[a][2] = s.pz[v[a]];
+    }
+}
+
+// Element loop of one patch: yout[owned] += (operator) xin.  xin, the
+// coordinates and the coefficients must be staged and yout zeroed.
+template <typename T, int R, int OP>
+__device__ __forceinline__ void patch_elements(const MeshDev& m, int p, int nown, const PatchSmem<T, R>& s,
+                                               const OpParams<T>& op) {
+    const int tb = __ldg(m.tet_ptr + p), te = __ldg(m.tet_ptr + p + 1);
+    for (int t = tb + threadIdx.x; t < te; t += blockDim.x) {
+        const ushort4 lv = m.tet_loc[t];
+        const int v[4] = {lv.x, lv.y, lv.z, lv.w};
+        T pc[4][3], c[4][3], ad;
+        load_tet(s, lv, pc);
+        tet_cofactors(pc, c, ad);
+        if constexpr (OP == OP_K) {
+            T mu[4], Sm = T(0), ks = T(0);
+#pragma unroll
+            for (int a = 0; a < 4; ++a) {
+                ks += s.c1[v[a]];
+                mu[a] = s.c2[v[a]];
+                Sm += mu[a];
+            }
+            const T sk = ks / (T(24) * ad);  // (S_kappa / 4) / (6 |det|)
+            const T vm = ad / T(720);        // |T| / 120
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                T x[4], G[3], y[4];
+#pragma unroll
+                for (int a = 0; a < 4; ++a) x[a] = s.xin[v[a] * R + r];
+                grad_vec(c, x, G);
+                stiff_rows(c, G, sk, y);
+                mass_rows_add(mu, Sm, x, vm, y);
+#pragma unroll
+                for (int a = 0; a < 4; ++a)
+                    if (v[a] < nown) atomicAdd(&s.yout[v[a] * R + r], y[a]);
+            }
+        } else {
+            static_assert(R == 2, "the prior operator has two blocks");
+            const T inv6ad = T(1) / (T(6) * ad);
+#pragma unroll
+            for (int r = 0; r < 2; ++r) {
+                const T* uc = r == 0 ? s.c1 : s.c2;
+                T u[4], Gu[3], x[4], G[3], y[4];
+#pragma unroll
+                for (int a = 0; a < 4; ++a) {
+                    u[a] = uc[v[a]];
+                    x[a] = s.xin[v[a] * 2 + r];
+                }
+                grad_vec(c, u, Gu);
+                // |grad u|^2 = |G_u|^2 / det^2 ; c_T = 1 / (1 + |grad u|^2 / T^2)
+                const T g2 = (Gu[0] * Gu[0] + Gu[1] * Gu[1] + Gu[2] * Gu[2]) / (ad * ad);
+                const T cT = T(1) / (T(1) + g2 * op.inv_T2);
+                const T sk = (r == 0 ? T(1) : op.scale1) * cT * inv6ad;
+                grad_vec(c, x, G);
+                stiff_rows(c, G, sk, y);
+#pragma unroll
+                for (int a = 0; a < 4; ++a)
+                    if (v[a] < nown) atomicAdd(&s.yout[v[a] * 2 + r], y[a]);
+            }
+        }
+    }
+    if constexpr (OP == OP_K) {
+        if (op.robin) {
+            const int fb = __ldg(m.face_ptr + p), fe = __ldg(m.face_ptr + p + 1);
+            for (int f = fb + threadIdx.x; f < fe; f += blockDim.x) {
+                const ushort4 lv = m.face_loc[f];
+                const int v[3] = {lv.x, lv.y, lv.z};
+                const T w = face_area_of<T>(m, f) / T(24);
+#pragma unroll
+                for (int r = 0; r < R; ++r) {
+                    T x[3];
+#pragma unroll
+                    for (int a = 0; a < 3; ++a) x[a] = s.xin[v[a] * R + r];
+                    const T Sx = x[0] + x[1] + x[2];
+#pragma unroll
+                    for (int a = 0; a < 3; ++a)
+                        if (v[a] < nown) atomicAdd(&s.yout[v[a] * R + r], w * (Sx + x[a]));
+                }
+            }
+        }
+    }
+}
+
+// Deterministic block reduction of NS doubles per thread; result valid in
+// thread 0 (out[s]).  scratch: at least 32 * NS doubles of shared memory.
+template <int NS>
+__device__ __forceinline__ void block_reduce(double (&v)[NS], double* scratch) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+    for (int s = 0; s < NS; ++s) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v[s] += __shfl_down_sync(0xffffffffu, v[s], o);
+    }
+    if (lane == 0)
+        for (int s = 0; s < NS; ++s) scratch[warp * NS + s] = v[s];
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < NS; ++s) {
+            double a = 0.0;
+            for (int w = 0; w < nw; ++w) a += scratch[w * NS + s];
+            v[s] = a;
+        }
+    }
+    __syncthreads();
+}
+
+}  // namespace qpat

@@ -1,0 +1,421 @@
+// One-pass patch kernels (operator applies, diagonals, Jacobian pieces),
+// the load vector, layout conversions and reductions.
+#include "launch.h"
+
+namespace qpat {
+
+namespace {
+
+constexpr int kRedBlocks = 608;  // 4 x 152 SMs
+
+// ---------------------------------------------------------------- operator apply
+// One CTA per patch: stage, element loop, write the owned rows.
+template <typename T, int R, int OP>
+__global__ void __launch_bounds__(kThreads) k_apply(MeshDev m, OpParams<T> op, T sign, const T* __restrict__ x,
+                                                    T* __restrict__ y) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    PatchSmem<T, R> s;
+    s.carve(reinterpret_cast<T*>(smem_raw), m.max_touched, m.max_own);
+    const int p = blockIdx.x;
+    const int nb = m.node_ptr[p], nt = m.node_ptr[p + 1] - nb;
+    const int ob = m.own_begin[p], nown = m.own_begin[p + 1] - ob;
+    stage_static<T, R>(m, nb, nt, s, op);
+    for (int i = threadIdx.x; i < nt * R; i += blockDim.x) {
+        const int g = __ldg(m.nodes + nb + i / R);
+        s.xin[i] = __ldg(x + size_t(g) * R + (i % R));
+    }
+    for (int i = threadIdx.x; i < nown * R; i += blockDim.x) s.yout[i] = T(0);
+    __syncthreads();
+    patch_elements<T, R, OP>(m, p, nown, s, op);
+    __syncthreads();
+    for (int i = threadIdx.x; i < nown * R; i += blockDim.x) {
+        T v = s.yout[i];
+        if (OP == OP_PRIOR) v += op.delta * s.xin[i];
+        y[size_t(ob) * R + i] = sign * v;
+    }
+}
+
+template <typename T, int R, int OP>
+cudaError_t apply_t(const MeshDev& m, const OpParams<T>& op, T sign, const T* x, T* y, cudaStream_t st) {
+    const size_t smem = PatchSmem<T, R>::bytes(m.max_touched, m.max_own);
+    auto kern = k_apply<T, R, OP>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+    if (e != cudaSuccess) return e;
+    kern<<<m.P, kThreads, smem, st>>>(m, op, sign, x, y);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- diagonals (FP64)
+// diag K_ii = sum_T [ S_kappa/4 |c_i|^2/(6|det|) + |T|/120 (2 S_mu + 4 mu_i) ] + sum_F |F|/12
+__global__ void __launch_bounds__(kThreads) k_diag_K(MeshDev m, const double* __restrict__ kappa,
+                                                     const double* __restrict__ mu, double* inv64, float* inv32) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    PatchSmem<double, 1> s;
+    s.carve(reinterpret_cast<double*>(smem_raw), m.max_touched, m.max_own);
+    const int p = blockIdx.x;
+    const int nb = m.node_ptr[p], nt = m.node_ptr[p + 1] - nb;
+    const int ob = m.own_begin[p], nown = m.own_begin[p + 1] - ob;
+    OpParams<double> op{kappa, mu, 0, 0, 0, 1};
+    stage_static<double, 1>(m, nb, nt, s, op);
+    for (int i = threadIdx.x; i < nown; i += blockDim.x) s.yout[i] = 0.0;
+    __syncthreads();
+    for (int t = m.tet_ptr[p] + threadIdx.x; t < m.tet_ptr[p + 1]; t += blockDim.x) {
+        const ushort4 lv = m.tet_loc[t];
+        const int v[4] = {lv.x, lv.y, lv.z, lv.w};
+        double pc[4][3], c[4][3], ad;
+        load_tet(s, lv, pc);
+        tet_cofactors(pc, c, ad);
+        double ks = 0, Sm = 0;
+        for (int a = 0; a < 4; ++a) {
+            ks += s.c1[v[a]];
+            Sm += s.c2[v[a]];
+        }
+        const double sk = ks / (24.0 * ad), vm = ad / 720.0;
+        for (int a = 0; a < 4; ++a)
+            if (v[a] < nown) {
+                const double c2 = c[a][0] * c[a][0] + c[a][1] * c[a][1] + c[a][2] * c[a][2];
+                atomicAdd(&s.yout[v[a]], sk * c2 + vm * (2.0 * Sm + 4.0 * s.c2[v[a]]));
+            }
+    }
+    for (int f = m.face_ptr[p] + threadIdx.x; f < m.face_ptr[p + 1]; f += blockDim.x) {
+        const ushort4 lv = m.face_loc[f];
+        const int v[3] = {lv.x, lv.y, lv.z};
+        const double w = m.pface_area64[f] / 12.0;
+        for (int a = 0; a < 3; ++a)
+            if (v[a] < nown) atomicAdd(&s.yout[v[a]], w);
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < nown; i += blockDim.x) {
+        const double d = 1.0 / s.yout[i];
+        inv64[ob + i] = d;
+        if (inv32) inv32[ob + i] = float(d);
+    }
+}
+
+// diag M_delta: block r: scale_r c_T |c_i|^2 / (6 |det|) + delta
+__global__ void __launch_bounds__(kThreads) k_diag_prior(MeshDev m, const double* __restrict__ u1,
+                                                         const double* __restrict__ u2, double inv_T2,
+                                                         double scale1, double delta, double* inv64,
+                                                         float* inv32) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    PatchSmem<double, 2> s;
+    s.carve(reinterpret_cast<double*>(smem_raw), m.max_touched, m.max_own);
+    const int p = blockIdx.x;
+    const int nb = m.node_ptr[p], nt = m.node_ptr[p + 1] - nb;
+    const int ob = m.own_begin[p], nown = m.own_begin[p + 1] - ob;
+    OpParams<double> op{u1, u2, inv_T2, scale1, delta, 0};
+    stage_static<double, 2>(m, nb, nt, s, op);
+    for (int i = threadIdx.x; i < 2 * nown; i += blockDim.x) s.yout[i] = 0.0;
+    __syncthreads();
+    for (int t = m.tet_ptr[p] + threadIdx.x; t < m.tet_ptr[p + 1]; t += blockDim.x) {
+        const ushort4 lv = m.tet_loc[t];
+        const int v[4] = {lv.x, lv.y, lv.z, lv.w};
+        double pc[4][3], c[4][3], ad;
+        load_tet(s, lv, pc);
+        tet_cofactors(pc, c, ad);
+        for (int r = 0; r < 2; ++r) {
+            const double* uc = r == 0 ? s.c1 : s.c2;
+            double u[4], Gu[3];
+            for (int a = 0; a < 4; ++a) u[a] = uc[v[a]];
+            grad_vec(c, u, Gu);
+            const double g2 = (Gu[0] * Gu[0] + Gu[1] * Gu[1] + Gu[2] * Gu[2]) / (ad * ad);
+            const double cT = 1.0 / (1.0 + g2 * inv_T2);
+            const double sk = (r == 0 ? 1.0 : scale1) * cT / (6.0 * ad);
+            for (int a = 0; a < 4; ++a)
+                if (v[a] < nown)
+                    atomicAdd(&s.yout[2 * v[a] + r], sk * (c[a][0] * c[a][0] + c[a][1] * c[a][1] + c[a][2] * c[a][2]));
+        }
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < 2 * nown; i += blockDim.x) {
+        const double d = 1.0 / (s.yout[i] + delta);
+        inv64[2 * ob + i] = d;
+        if (inv32) inv32[2 * ob + i] = float(d);
+    }
+}
+
+// ---------------------------------------------------------------- J^T pieces
+// y[g][0] = -sum_k sum_{T ni g} (|T|/4) grad(phi_k) . grad(z_k)       ( = sum_k G1^T z_k )
+// y[g][1] = -sum_k (M(phi_k) z_k)_g                                    ( = sum_k G2 z_k )
+template <typename T, int K>
+__global__ void __launch_bounds__(kThreads) k_vjp_accum(MeshDev m, const T* __restrict__ phi,
+                                                        const T* __restrict__ z, T* __restrict__ y) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int MT = m.max_touched;
+    T* px = reinterpret_cast<T*>(smem_raw);
+    T* py = px + MT;
+    T* pz = py + MT;
+    T* sphi = pz + MT;                 // MT x K
+    T* sz = sphi + size_t(MT) * K;     // MT x K
+    T* sy = sz + size_t(MT) * K;       // owned x 2
+    const T* xyz = xyz_of<T>(m);
+    const int p = blockIdx.x;
+    const int nb = m.node_ptr[p], nt = m.node_ptr[p + 1] - nb;
+    const int ob = m.own_begin[p], nown = m.own_begin[p + 1] - ob;
+    for (int i = threadIdx.x; i < nt; i += blockDim.x) {
+        const int g = m.nodes[nb + i];
+        px[i] = xyz[3 * g];
+        py[i] = xyz[3 * g + 1];
+        pz[i] = xyz[3 * g + 2];
+    }
+    for (int i = threadIdx.x; i < nt * K; i += blockDim.x) {
+        const int g = m.nodes[nb + i / K];
+        sphi[i] = phi[size_t(g) * K + i % K];
+        sz[i] = z[size_t(g) * K + i % K];
+    }
+    for (int i = threadIdx.x; i < 2 * nown; i += blockDim.x) sy[i] = T(0);
+    __syncthreads();
+    for (int t = m.tet_ptr[p] + threadIdx.x; t < m.tet_ptr[p + 1]; t += blockDim.x) {
+        const ushort4 lv = m.tet_loc[t];
+        const int v[4] = {lv.x, lv.y, lv.z, lv.w};
+        T pc[4][3], c[4][3], ad;
+        for (int a = 0; a < 4; ++a) {
+            pc[a][0] = px[v[a]];
+            pc[a][1] = py[v[a]];
+            pc[a][2] = pz[v[a]];
+        }
+        tet_cofactors(pc, c, ad);
+        const T s1 = T(1) / (T(24) * ad), vm = ad / T(720);
+        T g1 = T(0), m4[4] = {T(0), T(0), T(0), T(0)};
+        for (int k = 0; k < K; ++k) {
+            T f[4], zz[4], Gf[3], Gz[3];
+            for (int a = 0; a < 4; ++a) {
+                f[a] = sphi[v[a] * K + k];
+                zz[a] = sz[v[a] * K + k];
+            }
+            grad_vec(c, f, Gf);
+            grad_vec(c, zz, Gz);
+            g1 += Gf[0] * Gz[0] + Gf[1] * Gz[1] + Gf[2] * Gz[2];
+            mass_rows_add(f, f[0] + f[1] + f[2] + f[3], zz, vm, m4);
+        }
+        g1 *= s1;
+        for (int a = 0; a < 4; ++a)
+            if (v[a] < nown) {
+                atomicAdd(&sy[2 * v[a]], -g1);
+                atomicAdd(&sy[2 * v[a] + 1], -m4[a]);
+            }
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < 2 * nown; i += blockDim.x) y[size_t(ob) * 2 + i] = sy[i];
+}
+
+template <typename T, int K>
+cudaError_t vjp_t(const MeshDev& m, const T* phi, const T* z, T* y, cudaStream_t st) {
+    const size_t smem = sizeof(T) * (size_t(m.max_touched) * (3 + 2 * K) + size_t(m.max_own) * 2);
+    auto kern = k_vjp_accum<T, K>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+    if (e != cudaSuccess) return e;
+    kern<<<m.P, kThreads, smem, st>>>(m, phi, z, y);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- load vector
+// f_i += 2 Phi_F |F| / 3 for the three vertices of every lit face
+__global__ void k_load(MeshDev m, int K, int R, const double* __restrict__ flux, double* f) {
+    const int64_t total = int64_t(m.F) * K;
+    for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < total; i += int64_t(gridDim.x) * blockDim.x) {
+        const int k = int(i / m.F), fi = int(i % m.F);
+        const double v = flux[i];
+        if (v == 0.0) continue;
+        const double c = 2.0 * v * m.farea[fi] / 3.0;
+        for (int a = 0; a < 3; ++a) atomicAdd(&f[size_t(m.faces_lib[3 * fi + a]) * R + k], c);
+    }
+}
+
+// ---------------------------------------------------------------- layout helpers
+// out[l*R + r] = in[r*N + perm[l]] for r < K, 0 for K <= r < R
+template <typename Tin, typename Tout>
+__global__ void k_to_lib(int N, int K, int R, const int* __restrict__ perm, const Tin* __restrict__ in,
+                         Tout* __restrict__ out) {
+    const int64_t total = int64_t(N) * R;
+    for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < total; i += int64_t(gridDim.x) * blockDim.x) {
+        const int l = int(i / R), r = int(i % R);
+        out[i] = r < K ? Tout(in[int64_t(r) * N + perm[l]]) : Tout(0);
+    }
+}
+
+// out[r*N + perm[l]] = in[l*R + r] for r < K
+template <typename Tin, typename Tout>
+__global__ void k_from_lib(int N, int K, int R, const int* __restrict__ perm, const Tin* __restrict__ in,
+                           Tout* __restrict__ out) {
+    const int64_t total = int64_t(N) * K;
+    for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < total; i += int64_t(gridDim.x) * blockDim.x) {
+        const int l = int(i / K), r = int(i % K);
+        out[int64_t(r) * N + perm[l]] = Tout(in[int64_t(l) * R + r]);
+    }
+}
+
+int grid_for(int64_t n) {
+    int64_t g = (n + 255) / 256;
+    if (g > 152 * 16) g = 152 * 16;
+    if (g < 1) g = 1;
+    return int(g);
+}
+
+// ---------------------------------------------------------------- reductions
+template <typename T>
+__global__ void k_dot_partial(int64_t n, int R, const T* __restrict__ a, const T* __restrict__ b, double* partial) {
+    // thread t handles entries i with i % R == t % R (blockDim multiple of R)
+    __shared__ double sm[256];
+    double acc = 0.0;
+    const int64_t total = n * R;
+    for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < total; i += int64_t(gridDim.x) * blockDim.x)
+        acc += double(a[i]) * double(b[i]);
+    sm[threadIdx.x] = acc;
+    __syncthreads();
+    if (threadIdx.x < R) {
+        double s = 0.0;
+        for (int j = threadIdx.x; j < blockDim.x; j += R) s += sm[j];
+        partial[size_t(blockIdx.x) * R + threadIdx.x] = s;
+    }
+}
+
+__global__ void k_dot_final(int nblk, int R, const double* partial, double* out) {
+    const int r = threadIdx.x;
+    if (r < R) {
+        double s = 0.0;
+        for (int j = 0; j < nblk; ++j) s += partial[size_t(j) * R + r];
+        out[r] = s;
+    }
+}
+
+__global__ void k_cast_d2f_scaled(int64_t n, int R, const double* in, const double* scale, float* out) {
+    for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n * R; i += int64_t(gridDim.x) * blockDim.x) {
+        const double s = scale[i % R];
+        out[i] = s > 0.0 ? float(in[i] / s) : 0.0f;
+    }
+}
+
+__global__ void k_axpy_f2d_scaled(int64_t n, int R, const float* d, const double* scale, double* x) {
+    for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n * R; i += int64_t(gridDim.x) * blockDim.x)
+        x[i] += scale[i % R] * double(d[i]);
+}
+
+__global__ void k_sub(int64_t n, const double* a, const double* b, double* out) {
+    for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x)
+        out[i] = a[i] - b[i];
+}
+
+__global__ void k_cast_d2f(int64_t n, const double* in, float* out) {
+    for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x)
+        out[i] = float(in[i]);
+}
+
+}  // namespace
+
+template <typename T>
+cudaError_t launch_apply_K(const MeshDev& m, int R, const T* c1, const T* c2, int robin, T sign, const T* x, T* y,
+                           cudaStream_t s) {
+    OpParams<T> op{c1, c2, T(0), T(0), T(0), robin};
+    switch (R) {
+        case 1: return apply_t<T, 1, OP_K>(m, op, sign, x, y, s);
+        case 2: return apply_t<T, 2, OP_K>(m, op, sign, x, y, s);
+        case 4: return apply_t<T, 4, OP_K>(m, op, sign, x, y, s);
+        case 8: return apply_t<T, 8, OP_K>(m, op, sign, x, y, s);
+        case 16: return apply_t<T, 16, OP_K>(m, op, sign, x, y, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+template <typename T>
+cudaError_t launch_apply_prior(const MeshDev& m, const T* u1, const T* u2, T inv_T2, T scale1, T delta, const T* x,
+                               T* y, cudaStream_t s) {
+    OpParams<T> op{u1, u2, inv_T2, scale1, delta, 0};
+    return apply_t<T, 2, OP_PRIOR>(m, op, T(1), x, y, s);
+}
+
+cudaError_t launch_invdiag_K(const MeshDev& m, const double* kappa, const double* mu, double* inv64, float* inv32,
+                             cudaStream_t s) {
+    const size_t smem = PatchSmem<double, 1>::bytes(m.max_touched, m.max_own);
+    cudaError_t e = cudaFuncSetAttribute(k_diag_K, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+    if (e != cudaSuccess) return e;
+    k_diag_K<<<m.P, kThreads, smem, s>>>(m, kappa, mu, inv64, inv32);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_invdiag_prior(const MeshDev& m, const double* u1, const double* u2, double inv_T2, double scale1,
+                                 double delta, double* inv64, float* inv32, cudaStream_t s) {
+    const size_t smem = PatchSmem<double, 2>::bytes(m.max_touched, m.max_own);
+    cudaError_t e = cudaFuncSetAttribute(k_diag_prior, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+    if (e != cudaSuccess) return e;
+    k_diag_prior<<<m.P, kThreads, smem, s>>>(m, u1, u2, inv_T2, scale1, delta, inv64, inv32);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_vjp_accum(const MeshDev& m, int K, const T* phi, const T* z, T* y, cudaStream_t s) {
+    switch (K) {
+        case 1: return vjp_t<T, 1>(m, phi, z, y, s);
+        case 2: return vjp_t<T, 2>(m, phi, z, y, s);
+        case 4: return vjp_t<T, 4>(m, phi, z, y, s);
+        case 8: return vjp_t<T, 8>(m, phi, z, y, s);
+        case 16: return vjp_t<T, 16>(m, phi, z, y, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t launch_load(const MeshDev& m, int K, int R, const double* flux, double* f, cudaStream_t s) {
+    k_load<<<grid_for(int64_t(m.F) * K), 256, 0, s>>>(m, K, R, flux, f);
+    return cudaGetLastError();
+}
+
+template <typename Tin, typename Tout>
+cudaError_t launch_to_lib(const MeshDev& m, int K, int R, const Tin* in, Tout* out, cudaStream_t s) {
+    k_to_lib<Tin, Tout><<<grid_for(int64_t(m.N) * R), 256, 0, s>>>(m.N, K, R, m.perm, in, out);
+    return cudaGetLastError();
+}
+
+template <typename Tin, typename Tout>
+cudaError_t launch_from_lib(const MeshDev& m, int K, int R, const Tin* in, Tout* out, cudaStream_t s) {
+    k_from_lib<Tin, Tout><<<grid_for(int64_t(m.N) * K), 256, 0, s>>>(m.N, K, R, m.perm, in, out);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_dots(int64_t n, int R, const T* a, const T* b, double* partial, double* out, cudaStream_t s) {
+    k_dot_partial<T><<<kRedBlocks, 256, 0, s>>>(n, R, a, b, partial);
+    k_dot_final<<<1, 32, 0, s>>>(kRedBlocks, R, partial, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_cast_d2f_scaled(int64_t n, int R, const double* in, const double* scale, float* out,
+                                   cudaStream_t s) {
+    k_cast_d2f_scaled<<<grid_for(n * R), 256, 0, s>>>(n, R, in, scale, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_axpy_f2d_scaled(int64_t n, int R, const float* d, const double* scale, double* x,
+                                   cudaStream_t s) {
+    k_axpy_f2d_scaled<<<grid_for(n * R), 256, 0, s>>>(n, R, d, scale, x);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sub(int64_t n, const double* a, const double* b, double* out, cudaStream_t s) {
+    k_sub<<<grid_for(n), 256, 0, s>>>(n, a, b, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_cast_d2f(int64_t n, const double* in, float* out, cudaStream_t s) {
+    k_cast_d2f<<<grid_for(n), 256, 0, s>>>(n, in, out);
+    return cudaGetLastError();
+}
+
+template cudaError_t launch_apply_K<double>(const MeshDev&, int, const double*, const double*, int, double,
+                                            const double*, double*, cudaStream_t);
+template cudaError_t launch_apply_K<float>(const MeshDev&, int, const float*, const float*, int, float, const float*,
+                                           float*, cudaStream_t);
+template cudaError_t launch_apply_prior<double>(const MeshDev&, const double*, const double*, double, double, double,
+                                                const double*, double*, cudaStream_t);
+template cudaError_t launch_apply_prior<float>(const MeshDev&, const float*, const float*, float, float, float,
+                                               const float*, float*, cudaStream_t);
+template cudaError_t launch_vjp_accum<double>(const MeshDev&, int, const double*, const double*, double*,
+                                              cudaStream_t);
+template cudaError_t launch_vjp_accum<float>(const MeshDev&, int, const float*, const float*, float*, cudaStream_t);
+template cudaError_t launch_to_lib<double, double>(const MeshDev&, int, int, const double*, double*, cudaStream_t);
+template cudaError_t launch_to_lib<double, float>(const MeshDev&, int, int, const double*, float*, cudaStream_t);
+template cudaError_t launch_from_lib<double, double>(const MeshDev&, int, int, const double*, double*, cudaStream_t);
+template cudaError_t launch_from_lib<float, double>(const MeshDev&, int, int, const float*, double*, cudaStream_t);
+template cudaError_t launch_dots<double>(int64_t, int, const double*, const double*, double*, double*, cudaStream_t);
+template cudaError_t launch_dots<float>(int64_t, int, const float*, const float*, double*, double*, cudaStream_t);
+
+}  // namespace qpat

@@ -1,0 +1,73 @@
+// Host-side launchers of the CUDA kernels (internal).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "fem.cuh"
+#include "qpat_internal.h"
+
+namespace qpat {
+
+// ---------------------------------------------------------------- kernels.cu
+// y = sign * (S(c1) + M(c2) + robin * B) x for R RHS, library order, N x R node-major.
+template <typename T>
+cudaError_t launch_apply_K(const MeshDev& m, int R, const T* c1, const T* c2, int robin, T sign,
+                           const T* x, T* y, cudaStream_t s);
+// y = (blkdiag(M(u1), scale1 M(u2)) + delta I) x, x and y N x 2 node-major.
+template <typename T>
+cudaError_t launch_apply_prior(const MeshDev& m, const T* u1, const T* u2, T inv_T2, T scale1, T delta,
+                               const T* x, T* y, cudaStream_t s);
+// inverse diagonal of K(kappa, mu) (N) and of M_delta (N x 2), computed in FP64.
+cudaError_t launch_invdiag_K(const MeshDev& m, const double* kappa, const double* mu, double* inv64,
+                             float* inv32, cudaStream_t s);
+cudaError_t launch_invdiag_prior(const MeshDev& m, const double* u1, const double* u2, double inv_T2,
+                                 double scale1, double delta, double* inv64, float* inv32, cudaStream_t s);
+// y (N x 2) = [ -sum_k G1-transpose-type term ; -sum_k M(phi_k) z_k ] (see kernels.cu)
+template <typename T>
+cudaError_t launch_vjp_accum(const MeshDev& m, int K, const T* phi, const T* z, T* y, cudaStream_t s);
+// f (N x R node-major, library order, column k < K) += 2 Phi_F |F| / 3 at the
+// vertices of every face (flux: K x F canonical order); f must be zeroed.
+cudaError_t launch_load(const MeshDev& m, int K, int R, const double* flux, double* f, cudaStream_t s);
+
+// layout helpers: caller K x N rows  <->  library N x R node-major
+template <typename Tin, typename Tout>
+cudaError_t launch_to_lib(const MeshDev& m, int K, int R, const Tin* in, Tout* out, cudaStream_t s);
+template <typename Tin, typename Tout>
+cudaError_t launch_from_lib(const MeshDev& m, int K, int R, const Tin* in, Tout* out, cudaStream_t s);
+
+// per-RHS dot products of N x R node-major arrays, out[r] (double, device)
+template <typename T>
+cudaError_t launch_dots(int64_t n, int R, const T* a, const T* b, double* partial, double* out, cudaStream_t s);
+
+// elementwise helpers (see kernels.cu for the formulas)
+cudaError_t launch_cast_d2f_scaled(int64_t n, int R, const double* in, const double* scale, float* out,
+                                   cudaStream_t s);
+cudaError_t launch_axpy_f2d_scaled(int64_t n, int R, const float* d, const double* scale, double* x,
+                                   cudaStream_t s);
+cudaError_t launch_sub(int64_t n, const double* a, const double* b, double* out, cudaStream_t s);
+cudaError_t launch_cast_d2f(int64_t n, const double* in, float* out, cudaStream_t s);
+
+// ---------------------------------------------------------------- pcg.cu
+struct PcgWork {
+    void* b;  // N x R (T)
+    void* x;
+    void* r;
+    void* p0;
+    void* p1;
+    void* q;
+    double* partials;   // 2 x max_grid x 3R
+    unsigned* bar;      // 2
+    int* status;        // 1
+    int* iters;         // 1
+    double* stats;      // 2R: final r.r, b.b
+};
+
+// Persistent fused Jacobi-PCG on R right-hand sides (see pcg.cu).  b is
+// read from w.b; the solution is left in w.x.  Asynchronous.
+template <typename T>
+cudaError_t launch_pcg(const MeshDev& m, int OP, int R, const OpParams<T>& op, const T* invdiag,
+                       const PcgWork& w, double rtol, int maxit, cudaStream_t s, int* grid_used);
+
+int pcg_max_grid();  // upper bound of the cooperative grid (for sizing partials)
+
+}  // namespace qpat

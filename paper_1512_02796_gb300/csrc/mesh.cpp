@@ -1,0 +1,254 @@
+// Host-side mesh preparation: boundary faces in canonical order, Morton
+// locality order of the nodes and the owned-node CTA patches used by every
+// element kernel.  The P1 basis of Eq. (5) lives on this mesh; the boundary
+// faces carry the Robin term and the illumination of Eq. (1).
+#include <algorithm>
+#include <array>
+#include <cmath>
+#include <cstring>
+#include <numeric>
+
+#include "qpat_internal.h"
+
+namespace qpat {
+
+namespace {
+
+uint64_t spread3(uint64_t v) {
+    // spread the low 21 bits of v to every third bit
+    v &= 0x1fffff;
+    v = (v | v << 32) & 0x1f00000000ffffULL;
+    v = (v | v << 16) & 0x1f0000ff0000ffULL;
+    v = (v | v << 8) & 0x100f00f00f00f00fULL;
+    v = (v | v << 4) & 0x10c30c30c30c30c3ULL;
+    v = (v | v << 2) & 0x1249249249249249ULL;
+    return v;
+}
+
+struct Face {
+    int32_t v[3];
+    int32_t tet;
+};
+
+}  // namespace
+
+std::string build_host_mesh(const double* xyz, int64_t N, const int32_t* tets,
+                            int64_t E, int patch_nodes, HostMesh& m) {
+    if (N <= 0 || E <= 0 || xyz == nullptr || tets == nullptr)
+        return "qpat_mesh: empty mesh or NULL array";
+    if (N >= (int64_t(1) << 31) || E >= (int64_t(1) << 29))
+        return "qpat_mesh: mesh too large for 32-bit ids";
+    if (patch_nodes < 32 || patch_nodes > 8192)
+        return "qpat_mesh: patch_nodes must be in [32, 8192]";
+    for (int64_t i = 0; i < 4 * E; ++i)
+        if (tets[i] < 0 || tets[i] >= N) return "qpat_mesh: tet node id out of range";
+    for (int64_t i = 0; i < 3 * N; ++i)
+        if (!std::isfinite(xyz[i])) return "qpat_mesh: non-finite coordinate";
+
+    m = HostMesh();
+    m.N = N;
+    m.E = E;
+    m.patch_nodes = patch_nodes;
+
+    // ---- degenerate tets
+    for (int64_t e = 0; e < E; ++e) {
+        const int32_t* t = tets + 4 * e;
+        double d[3][3];
+        for (int a = 0; a < 3; ++a)
+            for (int c = 0; c < 3; ++c) d[a][c] = xyz[3 * t[a + 1] + c] - xyz[3 * t[0] + c];
+        double det = d[0][0] * (d[1][1] * d[2][2] - d[1][2] * d[2][1]) -
+                     d[0][1] * (d[1][0] * d[2][2] - d[1][2] * d[2][0]) +
+                     d[0][2] * (d[1][0] * d[2][1] - d[1][1] * d[2][0]);
+        double scale = 0.0;
+        for (int a = 0; a < 3; ++a)
+            for (int c = 0; c < 3; ++c) scale = std::max(scale, std::fabs(d[a][c]));
+        if (!(std::fabs(det) > 1e-12 * scale * scale * scale))
+            return "qpat_mesh: degenerate tetrahedron " + std::to_string(e);
+    }
+
+    // ---- boundary faces, canonical order (sorted caller triples, lexicographic)
+    {
+        std::vector<Face> f(4 * E);
+        static const int omit[4][3] = {{1, 2, 3}, {0, 2, 3}, {0, 1, 3}, {0, 1, 2}};
+        for (int64_t e = 0; e < E; ++e)
+            for (int k = 0; k < 4; ++k) {
+                Face& q = f[4 * e + k];
+                for (int a = 0; a < 3; ++a) q.v[a] = tets[4 * e + omit[k][a]];
+                std::sort(q.v, q.v + 3);
+                q.tet = int32_t(e);
+            }
+        std::sort(f.begin(), f.end(), [](const Face& a, const Face& b) {
+            if (a.v[0] != b.v[0]) return a.v[0] < b.v[0];
+            if (a.v[1] != b.v[1]) return a.v[1] < b.v[1];
+            return a.v[2] < b.v[2];
+        });
+        auto same = [](const Face& a, const Face& b) {
+            return a.v[0] == b.v[0] && a.v[1] == b.v[1] && a.v[2] == b.v[2];
+        };
+        for (size_t i = 0; i < f.size();) {
+            size_t j = i + 1;
+            while (j < f.size() && same(f[i], f[j])) ++j;
+            if (j - i > 2) return "qpat_mesh: a face is shared by more than two tets";
+            if (j - i == 1)
+                for (int a = 0; a < 3; ++a) m.faces_caller.push_back(f[i].v[a]);
+            i = j;
+        }
+        m.F = int64_t(m.faces_caller.size() / 3);
+    }
+
+    // ---- Morton order of the nodes
+    double lo[3] = {xyz[0], xyz[1], xyz[2]}, hi[3] = {xyz[0], xyz[1], xyz[2]};
+    for (int64_t i = 0; i < N; ++i)
+        for (int c = 0; c < 3; ++c) {
+            lo[c] = std::min(lo[c], xyz[3 * i + c]);
+            hi[c] = std::max(hi[c], xyz[3 * i + c]);
+        }
+    double ext = std::max({hi[0] - lo[0], hi[1] - lo[1], hi[2] - lo[2], 1e-300});
+    m.extent = ext;
+    std::vector<std::pair<uint64_t, int32_t>> key(N);
+    for (int64_t i = 0; i < N; ++i) {
+        uint64_t code = 0;
+        for (int c = 0; c < 3; ++c) {
+            double s = (xyz[3 * i + c] - lo[c]) / ext;
+            uint64_t q = uint64_t(std::min(std::max(s, 0.0), 1.0) * double((1u << 21) - 1) + 0.5);
+            code |= spread3(q) << c;
+        }
+        key[i] = {code, int32_t(i)};
+    }
+    std::sort(key.begin(), key.end());
+    m.perm.resize(N);
+    m.iperm.resize(N);
+    for (int64_t i = 0; i < N; ++i) {
+        m.perm[i] = key[i].second;
+        m.iperm[key[i].second] = int32_t(i);
+    }
+    m.xyz.resize(3 * N);
+    for (int64_t i = 0; i < N; ++i)
+        for (int c = 0; c < 3; ++c) m.xyz[3 * i + c] = xyz[3 * m.perm[i] + c];
+    m.tets.resize(4 * E);
+    for (int64_t i = 0; i < 4 * E; ++i) m.tets[i] = m.iperm[tets[i]];
+    m.faces_lib.resize(3 * m.F);
+    m.farea.resize(m.F);
+    for (int64_t f = 0; f < m.F; ++f) {
+        for (int a = 0; a < 3; ++a) m.faces_lib[3 * f + a] = m.iperm[m.faces_caller[3 * f + a]];
+        const double* p0 = &m.xyz[3 * m.faces_lib[3 * f + 0]];
+        const double* p1 = &m.xyz[3 * m.faces_lib[3 * f + 1]];
+        const double* p2 = &m.xyz[3 * m.faces_lib[3 * f + 2]];
+        double a[3], b[3];
+        for (int c = 0; c < 3; ++c) {
+            a[c] = p1[c] - p0[c];
+            b[c] = p2[c] - p0[c];
+        }
+        double cx = a[1] * b[2] - a[2] * b[1], cy = a[2] * b[0] - a[0] * b[2],
+               cz = a[0] * b[1] - a[1] * b[0];
+        m.farea[f] = 0.5 * std::sqrt(cx * cx + cy * cy + cz * cz);
+    }
+
+    // ---- node -> incident tets, node -> incident boundary faces
+    std::vector<int32_t> nt_ptr(N + 1, 0), nt(4 * E);
+    for (int64_t i = 0; i < 4 * E; ++i) nt_ptr[m.tets[i] + 1]++;
+    for (int64_t i = 0; i < N; ++i) nt_ptr[i + 1] += nt_ptr[i];
+    {
+        std::vector<int32_t> fill(nt_ptr.begin(), nt_ptr.end() - 1);
+        for (int64_t e = 0; e < E; ++e)
+            for (int k = 0; k < 4; ++k) nt[fill[m.tets[4 * e + k]]++] = int32_t(e);
+    }
+    std::vector<int32_t> nf_ptr(N + 1, 0), nf(3 * m.F);
+    for (int64_t i = 0; i < 3 * m.F; ++i) nf_ptr[m.faces_lib[i] + 1]++;
+    for (int64_t i = 0; i < N; ++i) nf_ptr[i + 1] += nf_ptr[i];
+    {
+        std::vector<int32_t> fill(nf_ptr.begin(), nf_ptr.end() - 1);
+        for (int64_t f = 0; f < m.F; ++f)
+            for (int k = 0; k < 3; ++k) nf[fill[m.faces_lib[3 * f + k]]++] = int32_t(f);
+    }
+
+    // ---- patches
+    const int P = int((N + patch_nodes - 1) / patch_nodes);
+    m.P = P;
+    m.own_begin.resize(P + 1);
+    for (int p = 0; p <= P; ++p) m.own_begin[p] = int32_t(std::min<int64_t>(int64_t(p) * patch_nodes, N));
+    m.node_ptr.assign(1, 0);
+    m.tet_ptr.assign(1, 0);
+    m.face_ptr.assign(1, 0);
+    std::vector<int32_t> tet_stamp(E, -1), face_stamp(m.F, -1), node_local(N, -1);
+    std::vector<int32_t> ptets, pfaces, halo;
+    for (int p = 0; p < P; ++p) {
+        const int32_t b = m.own_begin[p], e = m.own_begin[p + 1];
+        const int nown = e - b;
+        ptets.clear();
+        pfaces.clear();
+        halo.clear();
+        for (int32_t g = b; g < e; ++g) {
+            for (int32_t q = nt_ptr[g]; q < nt_ptr[g + 1]; ++q) {
+                int32_t t = nt[q];
+                if (tet_stamp[t] != p) {
+                    tet_stamp[t] = p;
+                    ptets.push_back(t);
+                }
+            }
+            for (int32_t q = nf_ptr[g]; q < nf_ptr[g + 1]; ++q) {
+                int32_t f = nf[q];
+                if (face_stamp[f] != p) {
+                    face_stamp[f] = p;
+                    pfaces.push_back(f);
+                }
+            }
+        }
+        for (int32_t g = b; g < e; ++g) node_local[g] = g - b;
+        for (int32_t t : ptets)
+            for (int k = 0; k < 4; ++k) {
+                int32_t g = m.tets[4 * t + k];
+                if ((g < b || g >= e) && node_local[g] < 0) {
+                    node_local[g] = -2;  // seen
+                    halo.push_back(g);
+                }
+            }
+        std::sort(halo.begin(), halo.end());
+        for (size_t i = 0; i < halo.size(); ++i) node_local[halo[i]] = int32_t(nown + i);
+        const int ntouch = nown + int(halo.size());
+        if (ntouch > 65535) return "qpat_mesh: a patch touches more than 65535 nodes";
+        for (int32_t g = b; g < e; ++g) m.nodes.push_back(g);
+        for (int32_t g : halo) m.nodes.push_back(g);
+        for (int32_t t : ptets)
+            for (int k = 0; k < 4; ++k) m.tet_loc.push_back(uint16_t(node_local[m.tets[4 * t + k]]));
+        for (int32_t f : pfaces) {
+            for (int k = 0; k < 3; ++k) m.face_loc.push_back(uint16_t(node_local[m.faces_lib[3 * f + k]]));
+            m.face_loc.push_back(0);
+            m.pface_area.push_back(m.farea[f]);
+        }
+        m.node_ptr.push_back(int32_t(m.nodes.size()));
+        m.tet_ptr.push_back(int32_t(m.tet_loc.size() / 4));
+        m.face_ptr.push_back(int32_t(m.face_loc.size() / 4));
+        m.max_touched = std::max(m.max_touched, ntouch);
+        m.max_own = std::max(m.max_own, nown);
+        m.max_ptets = std::max(m.max_ptets, int(ptets.size()));
+        m.max_pfaces = std::max(m.max_pfaces, int(pfaces.size()));
+        for (int32_t g = b; g < e; ++g) node_local[g] = -1;
+        for (int32_t g : halo) node_local[g] = -1;
+    }
+    return "";
+}
+
+void flux_patch_host(const HostMesh& m, const double c[3], const double n[3],
+                     double half_w, double amp, double* flux_face) {
+    const double tol = 1e-9 * m.extent;
+    double nn = std::sqrt(n[0] * n[0] + n[1] * n[1] + n[2] * n[2]);
+    double u[3] = {n[0] / nn, n[1] / nn, n[2] / nn};
+    for (int64_t f = 0; f < m.F; ++f) {
+        bool on = true;
+        double cen[3] = {0, 0, 0};
+        for (int a = 0; a < 3; ++a) {
+            const double* p = &m.xyz[3 * m.faces_lib[3 * f + a]];
+            double d = (p[0] - c[0]) * u[0] + (p[1] - c[1]) * u[1] + (p[2] - c[2]) * u[2];
+            if (std::fabs(d) > tol) on = false;
+            for (int k = 0; k < 3; ++k) cen[k] += p[k] / 3.0;
+        }
+        double r[3] = {cen[0] - c[0], cen[1] - c[1], cen[2] - c[2]};
+        double rn = r[0] * u[0] + r[1] * u[1] + r[2] * u[2];
+        double inf = 0.0;
+        for (int k = 0; k < 3; ++k) inf = std::max(inf, std::fabs(r[k] - rn * u[k]));
+        flux_face[f] = (on && inf <= half_w + tol) ? amp : 0.0;
+    }
+}
+
+}  // namespace qpat

@@ -1,0 +1,74 @@
+// Internal data structures shared by the host mesh preparation, the CUDA
+// kernels and the C ABI layer.  Nothing here is part of the public ABI.
+#pragma once
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "../../include/qpat.h"
+
+namespace qpat {
+
+// Host-side mesh after preparation.  Node ids inside are LIBRARY ids: nodes
+// are sorted by the Morton code of their coordinates, so that a contiguous
+// range of library ids is a spatially compact block.  The ranges of
+// `patch_nodes` consecutive library nodes are the CTA patches: a patch owns
+// its range, lists every tet that touches an owned node (tets on a patch
+// border appear in several patches) and the halo nodes those tets reach.
+struct HostMesh {
+    int64_t N = 0, E = 0, F = 0;
+    int P = 0;                        // number of patches
+    int patch_nodes = 0;              // owned nodes per patch (last may be fewer)
+    std::vector<double> xyz;          // N x 3, library order
+    std::vector<int32_t> tets;        // E x 4, library ids
+    std::vector<int32_t> perm;        // library id -> caller id
+    std::vector<int32_t> iperm;       // caller id -> library id
+    std::vector<int32_t> faces_caller;  // F x 3 canonical order, caller ids ascending
+    std::vector<int32_t> faces_lib;     // F x 3 same faces, library ids
+    std::vector<double> farea;          // F
+    // patches (CSR-style offsets, P + 1 entries each)
+    std::vector<int32_t> own_begin;     // owned library range [own_begin[p], own_begin[p+1])
+    std::vector<int32_t> node_ptr;      // touched nodes of patch p: nodes[node_ptr[p] ..)
+    std::vector<int32_t> nodes;         //   owned ones first (in order), then halo ascending
+    std::vector<int32_t> tet_ptr;
+    std::vector<uint16_t> tet_loc;      // 4 local vertex ids per patch tet
+    std::vector<int32_t> face_ptr;
+    std::vector<uint16_t> face_loc;     // 4 per patch face: 3 local ids + 0 pad
+    std::vector<double> pface_area;     // per patch face
+    int max_touched = 0, max_own = 0, max_ptets = 0, max_pfaces = 0;
+    double extent = 0.0;                // largest bounding-box side
+};
+
+// Builds a HostMesh; returns "" on success or an error message.
+std::string build_host_mesh(const double* xyz, int64_t N, const int32_t* tets,
+                            int64_t E, int patch_nodes, HostMesh& out);
+
+// Flux of a square boundary patch in canonical face order (see qpat.h).
+void flux_patch_host(const HostMesh& m, const double c[3], const double n[3],
+                     double half_w, double amp, double* flux_face);
+
+// Plain-old-data view of the device copy of a mesh, passed to kernels by value.
+struct MeshDev {
+    int N, E, F, P;
+    int max_touched, max_own, max_ptets, max_pfaces;
+    const double* xyz64;        // N x 3 library order
+    const float* xyz32;
+    const int* own_begin;       // P + 1
+    const int* node_ptr;        // P + 1
+    const int* nodes;
+    const int* tet_ptr;         // P + 1
+    const ushort4* tet_loc;
+    const int* face_ptr;        // P + 1
+    const ushort4* face_loc;
+    const double* pface_area64;
+    const float* pface_area32;
+    const int* faces_lib;       // F x 3 canonical order
+    const double* farea;        // F
+    const int* perm;            // library -> caller
+    const int* iperm;           // caller -> library
+};
+
+}  // namespace qpat

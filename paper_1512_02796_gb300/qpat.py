@@ -1,0 +1,351 @@
+"""Thin Python binding of the C ABI in include/qpat.h (argument marshalling only).
+
+Every function keeps the C name.  Host-pointer calls take numpy arrays and
+return numpy arrays; `*_dev` calls take CUDA torch tensors (float64,
+contiguous) and run on the current torch stream.  All computation happens in
+libqpat.so; there is no fallback: a missing library or a failing call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional, Sequence
+
+import numpy as np
+
+from . import build as _build
+
+_c_double_p = ctypes.POINTER(ctypes.c_double)
+_c_int32_p = ctypes.POINTER(ctypes.c_int32)
+_c_int64_p = ctypes.POINTER(ctypes.c_int64)
+
+QPAT_OK, QPAT_EINVAL, QPAT_ENOCONV, QPAT_EBREAKDOWN, QPAT_ETIMEOUT, QPAT_ECUDA, QPAT_ENOMEM = 0, -1, -2, -3, -4, -5, -6
+
+
+class qpat_params(ctypes.Structure):
+    _fields_ = [
+        ("T", ctypes.c_double), ("b_over_a", ctypes.c_double), ("delta", ctypes.c_double),
+        ("tau", ctypes.c_double), ("m0", ctypes.c_int), ("max_lin", ctypes.c_int),
+        ("max_lsqr", ctypes.c_int), ("fixed_counts", ctypes.c_int), ("precision", ctypes.c_int),
+        ("max_pcg_iter", ctypes.c_int), ("pcg_rtol", ctypes.c_double), ("fit_grid", ctypes.c_int),
+        ("fit_gn_steps", ctypes.c_int), ("patch_nodes", ctypes.c_int), ("reserved", ctypes.c_int * 7),
+    ]
+
+
+class qpat_report(ctypes.Structure):
+    _fields_ = [
+        ("kappa0", ctypes.c_double), ("mu0", ctypes.c_double), ("linearisations", ctypes.c_int),
+        ("accepted_last", ctypes.c_int), ("lsqr_iters", ctypes.c_int * 32),
+        ("residuals", ctypes.c_double * 33), ("pcg_iters", ctypes.c_int64), ("solves", ctypes.c_int64),
+        ("refinements", ctypes.c_int64), ("ms_total", ctypes.c_double),
+    ]
+
+
+class QpatError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"qpat error {code}: {msg}")
+        self.code = code
+
+
+_LIB = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True) -> ctypes.CDLL:
+    """Loads libqpat.so (building it first if it is missing)."""
+    global _LIB
+    if _LIB is not None:
+        return _LIB
+    path = _build.LIB
+    if not os.path.exists(path):
+        if not build_if_missing:
+            raise RuntimeError(f"libqpat.so not built at {path}")
+        _build.build()
+    lib = ctypes.CDLL(path)
+    vp = ctypes.c_void_p
+    sig = {
+        "qpat_default_params": (None, [ctypes.POINTER(qpat_params)]),
+        "qpat_last_error": (ctypes.c_char_p, []),
+        "qpat_mesh": (ctypes.c_int, [_c_double_p, ctypes.c_int64, _c_int32_p, ctypes.c_int64, ctypes.POINTER(vp)]),
+        "qpat_mesh_ex": (ctypes.c_int, [_c_double_p, ctypes.c_int64, _c_int32_p, ctypes.c_int64, ctypes.c_int,
+                                        ctypes.POINTER(vp)]),
+        "qpat_mesh_free": (None, [vp]),
+        "qpat_mesh_host_info": (ctypes.c_int, [_c_double_p, ctypes.c_int64, _c_int32_p, ctypes.c_int64,
+                                               ctypes.c_int, _c_int64_p, _c_int32_p, _c_int32_p]),
+        "qpat_mesh_num_nodes": (ctypes.c_int64, [vp]),
+        "qpat_mesh_num_tets": (ctypes.c_int64, [vp]),
+        "qpat_mesh_num_faces": (ctypes.c_int64, [vp]),
+        "qpat_mesh_num_patches": (ctypes.c_int64, [vp]),
+        "qpat_mesh_faces": (ctypes.c_int, [vp, _c_int32_p]),
+        "qpat_mesh_permutation": (ctypes.c_int, [vp, _c_int32_p]),
+        "qpat_mesh_stats": (ctypes.c_int, [vp, _c_int64_p]),
+        "qpat_mesh_reset_stats": (ctypes.c_int, [vp]),
+        "qpat_mesh_set_timing": (ctypes.c_int, [vp, ctypes.c_int]),
+        "qpat_mesh_pcg_time": (ctypes.c_int, [vp, _c_double_p]),
+        "qpat_flux_patch": (ctypes.c_int, [vp, _c_double_p, _c_double_p, ctypes.c_double, ctypes.c_double,
+                                           _c_double_p]),
+        "qpat_apply_K_dev": (ctypes.c_int, [vp, ctypes.c_int, vp, vp, ctypes.c_int, vp, vp, vp]),
+        "qpat_forward": (ctypes.c_int, [vp, ctypes.POINTER(qpat_params), _c_double_p, _c_double_p, ctypes.c_int,
+                                        _c_double_p, _c_double_p, _c_double_p]),
+        "qpat_forward_dev": (ctypes.c_int, [vp, ctypes.POINTER(qpat_params), vp, vp, ctypes.c_int, vp, vp, vp, vp]),
+        "qpat_jvp": (ctypes.c_int, [vp, ctypes.POINTER(qpat_params), _c_double_p, _c_double_p, ctypes.c_int,
+                                    _c_double_p, _c_double_p, _c_double_p, _c_double_p]),
+        "qpat_jvp_dev": (ctypes.c_int, [vp, ctypes.POINTER(qpat_params), vp, vp, ctypes.c_int, vp, vp, vp, vp, vp]),
+        "qpat_vjp": (ctypes.c_int, [vp, ctypes.POINTER(qpat_params), _c_double_p, _c_double_p, ctypes.c_int,
+                                    _c_double_p, _c_double_p, _c_double_p, _c_double_p]),
+        "qpat_vjp_dev": (ctypes.c_int, [vp, ctypes.POINTER(qpat_params), vp, vp, ctypes.c_int, vp, vp, vp, vp, vp]),
+        "qpat_jvp_vjp_pair_dev": (ctypes.c_int, [vp, ctypes.POINTER(qpat_params), vp, vp, ctypes.c_int, vp, vp, vp,
+                                                 vp, vp, vp, vp]),
+        "qpat_prior_solve": (ctypes.c_int, [vp, ctypes.POINTER(qpat_params), _c_double_p, _c_double_p, _c_double_p,
+                                            _c_double_p]),
+        "qpat_prior_solve_dev": (ctypes.c_int, [vp, ctypes.POINTER(qpat_params), vp, vp, vp, vp, vp]),
+        "qpat_reconstruct": (ctypes.c_int, [vp, ctypes.POINTER(qpat_params), ctypes.c_int, _c_double_p,
+                                            _c_double_p, _c_double_p, _c_double_p, _c_double_p, _c_double_p,
+                                            ctypes.POINTER(qpat_report)]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _LIB = lib
+    return lib
+
+
+def exported_names() -> Sequence[str]:
+    return [
+        "qpat_default_params", "qpat_last_error", "qpat_mesh", "qpat_mesh_ex", "qpat_mesh_free",
+        "qpat_mesh_host_info", "qpat_mesh_num_nodes", "qpat_mesh_num_tets", "qpat_mesh_num_faces", "qpat_mesh_num_patches",
+        "qpat_mesh_faces", "qpat_mesh_permutation", "qpat_mesh_stats", "qpat_mesh_reset_stats",
+        "qpat_mesh_set_timing", "qpat_mesh_pcg_time",
+        "qpat_flux_patch", "qpat_apply_K_dev", "qpat_forward", "qpat_forward_dev", "qpat_jvp", "qpat_jvp_dev",
+        "qpat_vjp", "qpat_vjp_dev", "qpat_jvp_vjp_pair_dev", "qpat_prior_solve", "qpat_prior_solve_dev",
+        "qpat_reconstruct",
+    ]
+
+
+def _check(rc: int):
+    if rc != QPAT_OK:
+        msg = load().qpat_last_error().decode(errors="replace")
+        raise QpatError(rc, msg)
+
+
+def _dp(a: Optional[np.ndarray]):
+    if a is None:
+        return None
+    return a.ctypes.data_as(_c_double_p)
+
+
+def _f64(a) -> np.ndarray:
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def qpat_default_params(**overrides) -> qpat_params:
+    p = qpat_params()
+    load().qpat_default_params(ctypes.byref(p))
+    for k, v in overrides.items():
+        if not hasattr(p, k):
+            raise KeyError(k)
+        setattr(p, k, v)
+    return p
+
+
+class Mesh:
+    """Owning wrapper of a qpat_mesh_t handle."""
+
+    def __init__(self, xyz, tets, patch_nodes: int = 512):
+        lib = load()
+        xyz = _f64(xyz)
+        tets = np.ascontiguousarray(tets, dtype=np.int32)
+        h = ctypes.c_void_p()
+        _check(lib.qpat_mesh_ex(_dp(xyz), xyz.shape[0], tets.ctypes.data_as(_c_int32_p), tets.shape[0],
+                                patch_nodes, ctypes.byref(h)))
+        self.handle = h
+        self.N = int(lib.qpat_mesh_num_nodes(h))
+        self.E = int(lib.qpat_mesh_num_tets(h))
+        self.F = int(lib.qpat_mesh_num_faces(h))
+        self.P = int(lib.qpat_mesh_num_patches(h))
+
+    def close(self):
+        if getattr(self, "handle", None):
+            load().qpat_mesh_free(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def faces(self) -> np.ndarray:
+        out = np.empty((self.F, 3), dtype=np.int32)
+        _check(load().qpat_mesh_faces(self.handle, out.ctypes.data_as(_c_int32_p)))
+        return out
+
+    def permutation(self) -> np.ndarray:
+        out = np.empty(self.N, dtype=np.int32)
+        _check(load().qpat_mesh_permutation(self.handle, out.ctypes.data_as(_c_int32_p)))
+        return out
+
+    def stats(self) -> dict:
+        out = np.zeros(4, dtype=np.int64)
+        _check(load().qpat_mesh_stats(self.handle, out.ctypes.data_as(_c_int64_p)))
+        return {"pcg_iters": int(out[0]), "solves": int(out[1]), "refinements": int(out[2]),
+                "launches": int(out[3])}
+
+    def reset_stats(self):
+        _check(load().qpat_mesh_reset_stats(self.handle))
+
+    def set_timing(self, on: bool = True):
+        _check(load().qpat_mesh_set_timing(self.handle, 1 if on else 0))
+
+    def pcg_time_ms(self) -> float:
+        v = ctypes.c_double()
+        _check(load().qpat_mesh_pcg_time(self.handle, ctypes.byref(v)))
+        return float(v.value)
+
+
+def qpat_mesh(xyz, tets, patch_nodes: int = 512) -> Mesh:
+    return Mesh(xyz, tets, patch_nodes)
+
+
+def qpat_mesh_host_info(xyz, tets, patch_nodes: int = 512):
+    """Host-only mesh preparation check; returns (info dict, faces, perm)."""
+    xyz = _f64(xyz)
+    tets = np.ascontiguousarray(tets, dtype=np.int32)
+    info = np.zeros(8, dtype=np.int64)
+    lib = load()
+    # first call sizes the face array
+    _check(lib.qpat_mesh_host_info(_dp(xyz), xyz.shape[0], tets.ctypes.data_as(_c_int32_p), tets.shape[0],
+                                   patch_nodes, info.ctypes.data_as(_c_int64_p), None, None))
+    faces = np.empty((int(info[0]), 3), dtype=np.int32)
+    perm = np.empty(xyz.shape[0], dtype=np.int32)
+    _check(lib.qpat_mesh_host_info(_dp(xyz), xyz.shape[0], tets.ctypes.data_as(_c_int32_p), tets.shape[0],
+                                   patch_nodes, info.ctypes.data_as(_c_int64_p), faces.ctypes.data_as(_c_int32_p),
+                                   perm.ctypes.data_as(_c_int32_p)))
+    keys = ["F", "P", "max_touched", "max_own", "max_ptets", "max_pfaces", "patch_tets", "patch_faces"]
+    return dict(zip(keys, (int(v) for v in info))), faces, perm
+
+
+def qpat_flux_patch(mesh: Mesh, center, normal, half_w: float, amp: float = 1.0) -> np.ndarray:
+    c = _f64(center)
+    n = _f64(normal)
+    out = np.empty(mesh.F)
+    _check(load().qpat_flux_patch(mesh.handle, _dp(c), _dp(n), float(half_w), float(amp), _dp(out)))
+    return out
+
+
+def _pp(params):
+    return ctypes.byref(params) if params is not None else None
+
+
+# ------------------------------------------------------------------ host calls
+
+def qpat_forward(mesh: Mesh, kappa, mu, flux, params: Optional[qpat_params] = None):
+    flux = _f64(np.atleast_2d(flux))
+    K = flux.shape[0]
+    kappa, mu = _f64(kappa), _f64(mu)
+    phi = np.empty((K, mesh.N))
+    h = np.empty((K, mesh.N))
+    _check(load().qpat_forward(mesh.handle, _pp(params), _dp(kappa), _dp(mu), K, _dp(flux), _dp(phi), _dp(h)))
+    return phi, h
+
+
+def qpat_jvp(mesh: Mesh, kappa, mu, phi, s, w=None, params: Optional[qpat_params] = None):
+    phi = _f64(np.atleast_2d(phi))
+    K = phi.shape[0]
+    w = None if w is None else _f64(np.broadcast_to(w, phi.shape))
+    out = np.empty((K, mesh.N))
+    _check(load().qpat_jvp(mesh.handle, _pp(params), _dp(_f64(kappa)), _dp(_f64(mu)), K, _dp(phi), _dp(w),
+                           _dp(_f64(s)), _dp(out)))
+    return out
+
+
+def qpat_vjp(mesh: Mesh, kappa, mu, phi, t, w=None, params: Optional[qpat_params] = None):
+    phi = _f64(np.atleast_2d(phi))
+    K = phi.shape[0]
+    t = _f64(np.broadcast_to(t, phi.shape))
+    w = None if w is None else _f64(np.broadcast_to(w, phi.shape))
+    out = np.empty(2 * mesh.N)
+    _check(load().qpat_vjp(mesh.handle, _pp(params), _dp(_f64(kappa)), _dp(_f64(mu)), K, _dp(phi), _dp(w),
+                           _dp(t), _dp(out)))
+    return out
+
+
+def qpat_prior_solve(mesh: Mesh, kt, mt, rhs, params: Optional[qpat_params] = None):
+    out = np.empty(2 * mesh.N)
+    _check(load().qpat_prior_solve(mesh.handle, _pp(params), _dp(_f64(kt)), _dp(_f64(mt)), _dp(_f64(rhs)),
+                                   _dp(out)))
+    return out
+
+
+def qpat_reconstruct(mesh: Mesh, flux, chi, sigma, params: Optional[qpat_params] = None, kappa0_mu0=None):
+    flux = _f64(np.atleast_2d(flux))
+    K = flux.shape[0]
+    chi = _f64(np.atleast_2d(chi))
+    sigma = _f64(np.broadcast_to(sigma, chi.shape))
+    k0 = None if kappa0_mu0 is None else _f64(kappa0_mu0)
+    kappa = np.empty(mesh.N)
+    mu = np.empty(mesh.N)
+    rep = qpat_report()
+    _check(load().qpat_reconstruct(mesh.handle, _pp(params), K, _dp(flux), _dp(chi), _dp(sigma), _dp(k0),
+                                   _dp(kappa), _dp(mu), ctypes.byref(rep)))
+    return kappa, mu, rep
+
+
+# ------------------------------------------------------------------ device calls (torch)
+
+def _tp(t):
+    if t is None:
+        return None
+    if not (t.is_cuda and t.dtype.itemsize == 8 and t.is_contiguous()):
+        raise ValueError("device calls take contiguous float64 CUDA tensors")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream():
+    import torch
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def qpat_apply_K_dev(mesh: Mesh, kappa, mu, x, y, precision: int = 0):
+    R = 1 if x.dim() == 1 else x.shape[1]
+    _check(load().qpat_apply_K_dev(mesh.handle, precision, _tp(kappa), _tp(mu), R, _tp(x), _tp(y), _stream()))
+    return y
+
+
+def qpat_forward_dev(mesh: Mesh, kappa, mu, flux, phi, h, params: Optional[qpat_params] = None):
+    K = flux.shape[0]
+    _check(load().qpat_forward_dev(mesh.handle, _pp(params), _tp(kappa), _tp(mu), K, _tp(flux), _tp(phi), _tp(h),
+                                   _stream()))
+    return phi, h
+
+
+def qpat_jvp_dev(mesh: Mesh, kappa, mu, phi, w, s, out, params: Optional[qpat_params] = None):
+    K = phi.shape[0]
+    _check(load().qpat_jvp_dev(mesh.handle, _pp(params), _tp(kappa), _tp(mu), K, _tp(phi), _tp(w), _tp(s),
+                               _tp(out), _stream()))
+    return out
+
+
+def qpat_vjp_dev(mesh: Mesh, kappa, mu, phi, w, t, out, params: Optional[qpat_params] = None):
+    K = phi.shape[0]
+    _check(load().qpat_vjp_dev(mesh.handle, _pp(params), _tp(kappa), _tp(mu), K, _tp(phi), _tp(w), _tp(t),
+                               _tp(out), _stream()))
+    return out
+
+
+def qpat_jvp_vjp_pair_dev(mesh: Mesh, kappa, mu, phi, w, s, t, out_jv, out_vjp,
+                          params: Optional[qpat_params] = None):
+    K = phi.shape[0]
+    _check(load().qpat_jvp_vjp_pair_dev(mesh.handle, _pp(params), _tp(kappa), _tp(mu), K, _tp(phi), _tp(w),
+                                        _tp(s), _tp(t), _tp(out_jv), _tp(out_vjp), _stream()))
+    return out_jv, out_vjp
+
+
+def qpat_prior_solve_dev(mesh: Mesh, kt, mt, rhs, out, params: Optional[qpat_params] = None):
+    _check(load().qpat_prior_solve_dev(mesh.handle, _pp(params), _tp(kt), _tp(mt), _tp(rhs), _tp(out),
+                                       _stream()))
+    return out

@@ -1,0 +1,78 @@
+"""CPU-side checks of the C ABI: the library builds for sm_103a, loads, exports
+every entry point declared in include/qpat.h, and its host mesh preparation
+(boundary faces in canonical order, locality permutation, CTA patches)
+agrees with the oracle's mesh processing.  No GPU compute is called."""
+import os
+import re
+
+import numpy as np
+import pytest
+
+import oracle as O
+import qpat_synth as S
+import paper_1512_02796_gb300 as Q
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_symbols():
+    txt = open(os.path.join(ROOT, "include", "qpat.h")).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(qpat_[A-Za-z0-9_]+)\s*\(", txt)))
+
+
+def test_library_exports_every_declared_symbol():
+    lib = Q.load()
+    names = declared_symbols()
+    assert len(names) >= 20
+    for n in names:
+        assert hasattr(lib, n), n
+    assert set(Q.exported_names()) == set(names)
+
+
+def test_default_params_follow_the_paper():
+    p = Q.qpat_default_params()
+    assert p.T == 5e-3 and p.delta == 1e-6 and p.b_over_a == 1.0
+    assert p.m0 == 10 and p.tau == 1e-2
+
+
+@pytest.mark.parametrize("n,L,pn", [(2, 1.0, 32), (5, 2.0, 32), (11, 20.0, 64), (11, 20.0, 512), (17, 4.0, 100)])
+def test_host_mesh_faces_match_oracle_and_patches_verify(n, L, pn):
+    xyz, tets = S.kuhn_cube(n, L)
+    info, faces, perm = Q.qpat_mesh_host_info(xyz, tets, pn)
+    of = O.boundary_faces(tets)
+    assert info["F"] == of.shape[0] == 12 * (n - 1) ** 2
+    np.testing.assert_array_equal(faces, of)
+    assert np.array_equal(np.sort(perm), np.arange(n ** 3))
+    assert info["P"] == -(-n ** 3 // pn)
+    assert info["patch_tets"] >= 6 * (n - 1) ** 3
+    assert info["max_own"] <= pn
+
+
+def test_host_mesh_random_relabelled_mesh():
+    """Faces are canonical in caller ids whatever the node numbering and tet
+    orientation."""
+    xyz, tets = S.kuhn_cube(6, 3.0)
+    rng = np.random.default_rng(0)
+    p = rng.permutation(xyz.shape[0])
+    inv = np.argsort(p)
+    xyz2 = xyz[p]
+    tets2 = inv[tets]
+    for e in range(tets2.shape[0]):
+        tets2[e] = tets2[e][rng.permutation(4)]
+    info, faces, _ = Q.qpat_mesh_host_info(xyz2, tets2.astype(np.int32), 40)
+    np.testing.assert_array_equal(faces, O.boundary_faces(tets2))
+
+
+def test_host_mesh_rejects_bad_input():
+    xyz, tets = S.kuhn_cube(3, 1.0)
+    bad = tets.copy()
+    bad[0, 0] = xyz.shape[0]
+    with pytest.raises(Q.QpatError):
+        Q.qpat_mesh_host_info(xyz, bad, 32)
+    flat = tets.copy()
+    flat[0] = [0, 1, 2, 2]        # degenerate tet
+    with pytest.raises(Q.QpatError):
+        Q.qpat_mesh_host_info(xyz, flat, 32)
+    with pytest.raises(Q.QpatError):
+        Q.qpat_mesh_host_info(xyz, tets, 8)   # patch size below the minimum

@@ -1,0 +1,91 @@
+"""Parity at the benchmark's full size (40 mm cube, 64^3 nodes, 4 illuminations)
+in the launch configuration bench.py times.  The oracle's sparse
+factorisation is too slow here, so each result is checked through a property
+that holds at any size, using only the oracle's assembled matrices:
+  K x against the oracle CSR product (sampled rows and the full vector),
+  the forward residual |K phi - f| / |f| with the oracle K and f,
+  the J s solve residual |K x - (G1 kappa s1 + G2 mu s2)| with the oracle G,
+  and the adjoint identity <J s, t> = <s, J^T t> of the paired launch.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+import qpat_synth as S
+from tests.gpu_common import Case, rel
+
+torch = pytest.importorskip("torch")
+Q = pytest.importorskip("paper_1512_02796_gb300")
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def big():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    c = Case(S.config("c1_cube64"), solve=False)
+    c.lib = Q.qpat_mesh(c.xyz, c.tets)
+    dev = torch.device("cuda")
+    c.T = lambda a: torch.tensor(np.ascontiguousarray(a), device=dev)
+    phi, _ = Q.qpat_forward(c.lib, c.kappa, c.mu, c.flux)
+    c.phi = phi
+    yield c
+    c.lib.close()
+
+
+def test_apply_full_size(big):
+    rng = np.random.default_rng(1)
+    x = rng.standard_normal((big.N, 4))
+    y = torch.empty((big.N, 4), dtype=torch.float64, device="cuda")
+    Q.qpat_apply_K_dev(big.lib, big.T(big.kappa), big.T(big.mu), big.T(x), y, 0)
+    torch.cuda.synchronize()
+    assert rel(y.cpu().numpy(), big.Kmat @ x) < 1e-13
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_forward_residual_full_size(big, precision):
+    dev = "cuda"
+    phi = torch.empty((big.K, big.N), dtype=torch.float64, device=dev)
+    h = torch.empty_like(phi)
+    Q.qpat_forward_dev(big.lib, big.T(big.kappa), big.T(big.mu), big.T(big.flux), phi, h,
+                       Q.qpat_default_params(precision=precision))
+    torch.cuda.synchronize()
+    ph = phi.cpu().numpy()
+    for k in range(big.K):
+        f = O.load_vector(big.om, big.flux[k])
+        assert np.linalg.norm(big.Kmat @ ph[k] - f) / np.linalg.norm(f) < 1e-12
+    np.testing.assert_allclose(h.cpu().numpy(), big.mu * ph, rtol=1e-15)
+    assert rel(ph, big.phi) < 1e-10
+
+
+def test_jvp_solve_residual_full_size(big):
+    rng = np.random.default_rng(2)
+    s = 0.1 * rng.standard_normal(2 * big.N)
+    N = big.N
+    out = torch.empty((big.K, N), dtype=torch.float64, device="cuda")
+    Q.qpat_jvp_dev(big.lib, big.T(big.kappa), big.T(big.mu), big.T(big.phi), None, big.T(s), out)
+    torch.cuda.synchronize()
+    Js = out.cpu().numpy()
+    for k in range(big.K):
+        x = (Js[k] - big.phi[k] * big.mu * s[N:]) / big.mu
+        rhs = (O.G1_matrix(big.om, big.phi[k]) @ (big.kappa * s[:N])
+               + O.G2_matrix(big.om, big.phi[k]) @ (big.mu * s[N:]))
+        assert np.linalg.norm(big.Kmat @ x - rhs) / np.linalg.norm(rhs) < 1e-11
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_pair_adjoint_identity_full_size(big, precision):
+    rng = np.random.default_rng(3)
+    N = big.N
+    s = rng.standard_normal(2 * N)
+    t = rng.standard_normal((big.K, N))
+    w = 1.0 / (0.01 * np.abs(big.mu * big.phi) + 1e-6)
+    oj = torch.empty((big.K, N), dtype=torch.float64, device="cuda")
+    ov = torch.empty(2 * N, dtype=torch.float64, device="cuda")
+    Q.qpat_jvp_vjp_pair_dev(big.lib, big.T(big.kappa), big.T(big.mu), big.T(big.phi), big.T(w), big.T(s), big.T(t),
+                            oj, ov, Q.qpat_default_params(precision=precision))
+    torch.cuda.synchronize()
+    a = float(np.sum(oj.cpu().numpy() * t))
+    b = float(s @ ov.cpu().numpy())
+    assert abs(a - b) <= 1e-10 * abs(a)

@@ -1,0 +1,148 @@
+"""GPU parity of the CUDA path (through the C ABI) against the CPU FP64 oracle.
+
+Tolerances (relative L2 per field):
+  operator apply FP64      1e-13  (summation order only)
+  operator apply FP32      2e-6   (FP32 coordinates and arithmetic)
+  forward, J s, J^T t      1e-10  (FP64 PCG and FP32 PCG + FP64 refinement,
+                                   both to a relative residual of 1e-13;
+                                   error <= cond(K) * 1e-13 with cond(K) < 1e3)
+  M_delta^-1               bounded by cond(M_delta) * 1e-12 (computed per case)
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+import qpat_synth as S
+from tests.gpu_common import Case, rel, small_cases
+
+torch = pytest.importorskip("torch")
+Q = pytest.importorskip("paper_1512_02796_gb300")
+
+pytestmark = pytest.mark.gpu
+
+CASES = small_cases()
+
+
+def _need_gpu():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+
+
+@pytest.fixture(scope="module", params=list(CASES))
+def case(request):
+    _need_gpu()
+    c = Case(CASES[request.param])
+    c.lib = Q.qpat_mesh(c.xyz, c.tets, patch_nodes=64 if c.N > 64 else 32)
+    yield c
+    c.lib.close()
+
+
+def _params(precision=0, **kw):
+    return Q.qpat_default_params(precision=precision, **kw)
+
+
+def test_mesh_faces_and_flux(case):
+    np.testing.assert_array_equal(case.lib.faces(), case.om.faces)
+    for k, p in enumerate(case.cfg.patches):
+        f = Q.qpat_flux_patch(case.lib, p.center, p.normal, p.half_w, p.amp)
+        np.testing.assert_array_equal(f, case.flux[k])
+
+
+@pytest.mark.parametrize("precision,tol", [(0, 1e-13), (1, 2e-6)])
+@pytest.mark.parametrize("R", [1, 3, 4, 8])
+def test_apply_K(case, precision, tol, R):
+    rng = np.random.default_rng(R)
+    x = rng.standard_normal((case.N, R))
+    y_ref = case.Kmat @ x
+    dev = torch.device("cuda")
+    xt = torch.tensor(x, device=dev)
+    yt = torch.empty_like(xt)
+    Q.qpat_apply_K_dev(case.lib, torch.tensor(case.kappa, device=dev), torch.tensor(case.mu, device=dev), xt, yt,
+                       precision)
+    torch.cuda.synchronize()
+    assert rel(yt.cpu().numpy(), y_ref) < tol
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_forward(case, precision):
+    phi, h = Q.qpat_forward(case.lib, case.kappa, case.mu, case.flux, _params(precision))
+    assert rel(phi, case.phi) < 1e-10
+    assert rel(h, case.h) < 1e-10
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_jvp(case, precision):
+    rng = np.random.default_rng(5)
+    s = rng.standard_normal(2 * case.N)
+    ref = O.jvp(case.om, case.kappa, case.mu, case.phi, s, case.w, case.fac)
+    out = Q.qpat_jvp(case.lib, case.kappa, case.mu, case.phi, s, case.w, _params(precision))
+    assert rel(out, ref) < 1e-10
+    out1 = Q.qpat_jvp(case.lib, case.kappa, case.mu, case.phi, s, None, _params(precision))
+    assert rel(out1, O.jvp(case.om, case.kappa, case.mu, case.phi, s, None, case.fac)) < 1e-10
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_vjp(case, precision):
+    rng = np.random.default_rng(6)
+    t = rng.standard_normal((case.K, case.N))
+    ref = O.vjp(case.om, case.kappa, case.mu, case.phi, t, case.w, case.fac)
+    out = Q.qpat_vjp(case.lib, case.kappa, case.mu, case.phi, t, case.w, _params(precision))
+    assert rel(out[:case.N], ref[:case.N]) < 1e-10
+    assert rel(out[case.N:], ref[case.N:]) < 1e-10
+
+
+def test_adjoint_identity_on_gpu(case):
+    rng = np.random.default_rng(7)
+    v = rng.standard_normal(2 * case.N)
+    t = rng.standard_normal((case.K, case.N))
+    a = np.sum(Q.qpat_jvp(case.lib, case.kappa, case.mu, case.phi, v, case.w) * t)
+    b = v @ Q.qpat_vjp(case.lib, case.kappa, case.mu, case.phi, t, case.w)
+    assert abs(a - b) <= 1e-10 * abs(a)
+
+
+def test_pair_matches_separate_calls(case):
+    if case.K > 8:
+        pytest.skip("pair needs K <= 8")
+    dev = torch.device("cuda")
+    rng = np.random.default_rng(8)
+    s = rng.standard_normal(2 * case.N)
+    t = rng.standard_normal((case.K, case.N))
+    T = lambda a: torch.tensor(np.ascontiguousarray(a), device=dev)
+    oj = torch.empty((case.K, case.N), dtype=torch.float64, device=dev)
+    ov = torch.empty(2 * case.N, dtype=torch.float64, device=dev)
+    Q.qpat_jvp_vjp_pair_dev(case.lib, T(case.kappa), T(case.mu), T(case.phi), T(case.w), T(s), T(t), oj, ov)
+    torch.cuda.synchronize()
+    assert rel(oj.cpu().numpy(), O.jvp(case.om, case.kappa, case.mu, case.phi, s, case.w, case.fac)) < 1e-10
+    assert rel(ov.cpu().numpy(), O.vjp(case.om, case.kappa, case.mu, case.phi, t, case.w, case.fac)) < 1e-10
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_prior_solve(case, precision):
+    rng = np.random.default_rng(9)
+    N = case.N
+    kt = 0.3 * rng.standard_normal(N)
+    mt = np.log(case.mu / case.mu.mean())
+    rhs = rng.standard_normal(2 * N)
+    T, ba, delta = 1e-2, 0.7, 1e-6
+    Md = O.prior_matrix(case.om, kt, mt, T, ba, delta)
+    ref = O.Factor(Md).solve(rhs)
+    p = _params(precision, T=T, b_over_a=ba, delta=delta, pcg_rtol=1e-13)
+    out = Q.qpat_prior_solve(case.lib, kt, mt, rhs, p)
+    res = np.linalg.norm(Md @ out - rhs) / np.linalg.norm(rhs)
+    assert res < 1e-12
+    if N <= 800:
+        ev = np.linalg.eigvalsh(Md.toarray())
+        tol = 10 * (ev[-1] / ev[0]) * 1e-13
+    else:
+        tol = 1e-4
+    assert rel(out, ref) < max(tol, 1e-10)
+
+
+def test_forward_k_padding_and_zero_flux(case):
+    # a zero illumination next to real ones: padded / inactive RHS stay exactly 0
+    fl = np.vstack([case.flux, np.zeros_like(case.flux[:1])])
+    if fl.shape[0] > 16:
+        pytest.skip("K too large")
+    phi, _ = Q.qpat_forward(case.lib, case.kappa, case.mu, fl)
+    assert np.all(phi[-1] == 0.0)
+    assert rel(phi[:-1], case.phi) < 1e-10
