@@ -63,13 +63,17 @@ typedef struct {
     int max_lsqr;          /* LSQR rounds per linearisation */
     int fixed_counts;      /* 1: run exactly max_lin x max_lsqr, no Eq. (22) stop
                               (the step-4 acceptance of Algorithm 1 stays active) */
-    int precision;         /* 0: FP64 PCG; 1: FP32 PCG inside FP64 refinement */
+    int precision;         /* 0: FP64 PCG; 1: FP32 PCG inside FP64 refinement for
+                              the K solves (M_delta solves always run in FP64:
+                              their conditioning, set by delta, is beyond FP32) */
     int max_pcg_iter;      /* cap per PCG run (inner run for precision 1) */
     double pcg_rtol;       /* |b - A x| / |b| target of every K and M_delta solve */
     int fit_grid;          /* (kappa_0, mu_0) search grid per axis (Algorithm 1) */
     int fit_gn_steps;      /* Gauss-Newton polish steps of that search */
     int patch_nodes;       /* owned nodes per CTA patch (0 = library choice) */
-    int reserved[7];
+    int fp32_operator;     /* FP32 inner operator of precision 1: 0 = matrix-free
+                              element recomputation, 1 = assembled FP32 values */
+    int reserved[6];
 } qpat_params;
 
 /* Report of qpat_reconstruct (Algorithm 1). */
@@ -153,7 +157,9 @@ int qpat_flux_patch(qpat_mesh_t mesh, const double c[3], const double n[3],
  * of Eq. (1) (Appendix): integral kappa grad x . grad v + mu x v plus
  * 1/2 integral over the boundary of x v, with P1 nodal kappa and mu.
  * x, y: N x R node-major (x[n*R + r]), caller order, device pointers.
- * precision 0 computes in FP64, 1 in FP32 (inputs and outputs stay FP64). */
+ * mode 0: FP64 matrix-free element apply; 1: FP32 matrix-free; 2: FP64
+ * assembled (sliced ELLPACK) values; 3: FP32 assembled values.  Inputs and
+ * outputs stay FP64 in every mode. */
 int qpat_apply_K_dev(qpat_mesh_t mesh, int precision, const double* kappa,
                      const double* mu, int R, const double* x, double* y,
                      void* stream);

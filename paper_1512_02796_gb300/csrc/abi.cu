@@ -20,6 +20,9 @@ int fail(int code, const std::string& msg) {
 }
 
 int cuda_fail(cudaError_t e, const char* where) {
+    // clear the runtime's last-error slot so that a later launch check does
+    // not report this (non-sticky) failure again
+    (void)cudaGetLastError();
     return fail(QPAT_ECUDA, std::string(where) + ": " + cudaGetErrorString(e));
 }
 
@@ -139,11 +142,16 @@ int prepare_K(qpat_mesh_s* M, const double* kap_l, const double* mu_l, OpState& 
     st.c2_32 = M->ws.get<float>(t + ".c2_32", N, s, &e);
     st.inv64 = M->ws.get<double>(t + ".inv64", N, s, &e);
     st.inv32 = M->ws.get<float>(t + ".inv32", N, s, &e);
+    st.nv = 1;
+    st.v64[0] = M->ws.get<double>(t + ".v64", M->d.sell_entries, s, &e);
+    st.v32[0] = M->ws.get<float>(t + ".v32", M->d.sell_entries, s, &e);
     if (e != cudaSuccess) return cuda_fail(e, "workspace");
     if ((e = launch_cast_d2f(N, kap_l, st.c1_32, s)) != cudaSuccess) return cuda_fail(e, "cast");
     if ((e = launch_cast_d2f(N, mu_l, st.c2_32, s)) != cudaSuccess) return cuda_fail(e, "cast");
-    if ((e = launch_invdiag_K(M->d, kap_l, mu_l, st.inv64, st.inv32, s)) != cudaSuccess)
-        return cuda_fail(e, "invdiag_K");
+    if ((e = launch_assemble_K(M->d, kap_l, mu_l, st.v64[0], st.inv64, st.inv32, s)) != cudaSuccess)
+        return cuda_fail(e, "assemble_K");
+    if ((e = launch_cast_vals(M->d.sell_entries, st.v64[0], st.v32[0], s)) != cudaSuccess)
+        return cuda_fail(e, "cast");
     return QPAT_OK;
 }
 
@@ -161,19 +169,24 @@ int prepare_prior(qpat_mesh_s* M, const double* kt_l, const double* mt_l, double
     st.c2_32 = M->ws.get<float>("opP.c2_32", N, s, &e);
     st.inv64 = M->ws.get<double>("opP.inv64", 2 * N, s, &e);
     st.inv32 = M->ws.get<float>("opP.inv32", 2 * N, s, &e);
+    st.nv = 2;
+    st.v64[0] = M->ws.get<double>("opP.v64a", M->d.sell_entries, s, &e);
+    st.v64[1] = M->ws.get<double>("opP.v64b", M->d.sell_entries, s, &e);
     if (e != cudaSuccess) return cuda_fail(e, "workspace");
     if ((e = launch_cast_d2f(N, kt_l, st.c1_32, s)) != cudaSuccess) return cuda_fail(e, "cast");
     if ((e = launch_cast_d2f(N, mt_l, st.c2_32, s)) != cudaSuccess) return cuda_fail(e, "cast");
-    if ((e = launch_invdiag_prior(M->d, kt_l, mt_l, st.inv_T2, b_over_a, delta, st.inv64, st.inv32, s)) !=
-        cudaSuccess)
-        return cuda_fail(e, "invdiag_prior");
+    if ((e = launch_assemble_prior(M->d, kt_l, mt_l, st.inv_T2, b_over_a, delta, st.v64[0], st.v64[1], st.inv64,
+                                   st.inv32, s)) != cudaSuccess)
+        return cuda_fail(e, "assemble_prior");
     return QPAT_OK;
 }
 
+// FP64 operator apply of the refinement residual: the assembled values
+// (two FP64 flops per stored entry; GB300 runs FP64 at ~1/64 of FP32, so the
+// element recomputation is kept for FP32 only).
 static cudaError_t apply_op64(qpat_mesh_s* M, const OpState& st, int R, const double* x, double* y,
                               cudaStream_t s) {
-    if (st.kind == OP_K) return launch_apply_K<double>(M->d, R, st.c1_64, st.c2_64, 1, 1.0, x, y, s);
-    return launch_apply_prior<double>(M->d, st.c1_64, st.c2_64, st.inv_T2, st.scale1, st.delta, x, y, s);
+    return launch_apply_csr<double>(M->d, st.nv, R, st.v64[0], st.v64[1], x, y, s);
 }
 
 static int pcg_status(int st, const char* what) {
@@ -188,8 +201,14 @@ static int pcg_status(int st, const char* what) {
 // FP64 in and out).  precision 0: FP64 PCG to rtol.  precision 1: X = 0,
 // then sweeps of  r = B - A X (FP64 element apply), d = A32^-1 (r / |r|)
 // (FP32 PCG to a loose tolerance), X += |r| d,  until |r_j| <= rtol |B_j|.
-int solve(qpat_mesh_s* M, const OpState& st, const SolveOpts& so, int R, const double* B, double* X,
+int solve(qpat_mesh_s* M, const OpState& st, const SolveOpts& so_in, int R, const double* B, double* X,
           cudaStream_t s) {
+    // M_delta is solved in FP64 whatever the precision mode: its smallest
+    // eigenvalue is delta (constant mode, 1e-6 below the rest) and the
+    // lagged weights reach ~1e-5 across edges, beyond what an FP32 inner
+    // solve can resolve, so refinement would not contract.
+    SolveOpts so = so_in;
+    if (st.kind == OP_PRIOR) so.precision = 0;
     const int64_t N = M->h.N;
     const int64_t n = N * R;
     cudaError_t e = cudaSuccess;
@@ -208,12 +227,11 @@ int solve(qpat_mesh_s* M, const OpState& st, const SolveOpts& so, int R, const d
     w.stats = M->ws.get<double>("pcg.stats", 32, s, &e);
     double* hpin = M->host_scratch;  // pinned, >= 64 doubles
     if (e != cudaSuccess) return cuda_fail(e, "workspace");
-    const int OP = st.kind;
-
     if (so.precision == 0) {
         w.b = const_cast<double*>(B);
         w.x = X;
-        OpParams<double> op{st.c1_64, st.c2_64, st.inv_T2, st.scale1, st.delta, 1};
+        const int OP = st.kind == OP_K ? OP_CSR1 : OP_CSR2;
+        OpParams<double> op{st.c1_64, st.c2_64, st.inv_T2, st.scale1, st.delta, 1, st.v64[0], st.v64[1]};
         if (M->timing) cudaEventRecord(M->ev0, s);
         if ((e = launch_pcg<double>(M->d, OP, R, op, st.inv64, w, so.rtol, so.maxit, s, nullptr)) != cudaSuccess)
             return cuda_fail(e, "pcg launch");
@@ -244,7 +262,9 @@ int solve(qpat_mesh_s* M, const OpState& st, const SolveOpts& so, int R, const d
     if (e != cudaSuccess) return cuda_fail(e, "workspace");
     w.b = b32;
     w.x = x32;
-    OpParams<float> op{st.c1_32, st.c2_32, float(st.inv_T2), float(st.scale1), float(st.delta), 1};
+    const int OP = so.fp32_assembled ? OP_CSR1 : OP_K;
+    OpParams<float> op{st.c1_32, st.c2_32, float(st.inv_T2), float(st.scale1), float(st.delta), 1, st.v32[0],
+                       nullptr};
     if ((e = cudaMemsetAsync(X, 0, n * sizeof(double), s)) != cudaSuccess) return cuda_fail(e, "memset");
     if ((e = cudaMemcpyAsync(Rres, B, n * sizeof(double), cudaMemcpyDeviceToDevice, s)) != cudaSuccess)
         return cuda_fail(e, "copy");
@@ -353,8 +373,16 @@ int qpat_mesh_host_info(const double* xyz, int64_t N, const int32_t* tets, int64
     // self-check of the patch structure: owned ranges tile [0, N); every tet
     // that touches an owned node is listed; local ids map back to the tets
     int64_t dup = 0;
+    std::vector<int> stamp(h.N, -1);
     for (int p = 0; p < h.P; ++p) {
         const int ob = h.own_begin[p], oe = h.own_begin[p + 1], nb = h.node_ptr[p];
+        // touched nodes are distinct, owned ones first and in order
+        for (int i = nb; i < h.node_ptr[p + 1]; ++i) {
+            const int g = h.nodes[i];
+            if (stamp[g] == p) return fail(QPAT_EINVAL, "host check: duplicate touched node");
+            stamp[g] = p;
+            if (i - nb < oe - ob && g != ob + (i - nb)) return fail(QPAT_EINVAL, "host check: owned order");
+        }
         for (int t = h.tet_ptr[p]; t < h.tet_ptr[p + 1]; ++t) {
             int owned = 0;
             for (int a = 0; a < 4; ++a) {
@@ -476,7 +504,7 @@ int qpat_apply_K_dev(qpat_mesh_t M, int precision, const double* kappa, const do
     if (!M || !kappa || !mu || !x || !y) return fail(QPAT_EINVAL, "qpat_apply_K_dev: NULL argument");
     const int Rp = round_rhs(R);
     if (R < 1 || Rp < 0) return fail(QPAT_EINVAL, "qpat_apply_K_dev: R must be in [1, 16]");
-    if (precision != 0 && precision != 1) return fail(QPAT_EINVAL, "qpat_apply_K_dev: precision must be 0 or 1");
+    if (precision < 0 || precision > 3) return fail(QPAT_EINVAL, "qpat_apply_K_dev: mode must be in [0, 3]");
     DeviceGuard dg(M->device);
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const int64_t N = M->h.N;
@@ -486,12 +514,27 @@ int qpat_apply_K_dev(qpat_mesh_t M, int precision, const double* kappa, const do
     double* xl = M->ws.get<double>("ak.x", N * Rp, s, &e);
     double* yl = M->ws.get<double>("ak.y", N * Rp, s, &e);
     if (e != cudaSuccess) return cuda_fail(e, "workspace");
-    // x, y are N x R node-major in caller order: treat as R rows of a "K x N"? no --
-    // gather row-wise: node-major caller layout means in[c*R + r]; use the K=1 helper per column.
+    // x, y are N x R node-major in caller order
     if ((e = launch_to_lib<double, double>(M->d, 1, 1, kappa, kl, s)) != cudaSuccess) return cuda_fail(e, "to_lib");
     if ((e = launch_to_lib<double, double>(M->d, 1, 1, mu, ml, s)) != cudaSuccess) return cuda_fail(e, "to_lib");
     if ((e = launch_nodemajor_to_lib(M->d, R, Rp, x, xl, s)) != cudaSuccess) return cuda_fail(e, "to_lib");
-    if (precision == 0) {
+    if (precision >= 2) {
+        OpState st;
+        int rc = prepare_K(M, kl, ml, st, s, "akK");
+        if (rc != QPAT_OK) return rc;
+        if (precision == 2) {
+            if ((e = launch_apply_csr<double>(M->d, 1, Rp, st.v64[0], nullptr, xl, yl, s)) != cudaSuccess)
+                return cuda_fail(e, "apply_csr");
+        } else {
+            float* x32 = M->ws.get<float>("ak.x32", N * Rp, s, &e);
+            float* y32 = M->ws.get<float>("ak.y32", N * Rp, s, &e);
+            if (e != cudaSuccess) return cuda_fail(e, "workspace");
+            launch_cast_d2f(N * Rp, xl, x32, s);
+            if ((e = launch_apply_csr<float>(M->d, 1, Rp, st.v32[0], nullptr, x32, y32, s)) != cudaSuccess)
+                return cuda_fail(e, "apply_csr32");
+            if ((e = launch_cast_f2d(N * Rp, y32, yl, s)) != cudaSuccess) return cuda_fail(e, "cast");
+        }
+    } else if (precision == 0) {
         if ((e = launch_apply_K<double>(M->d, Rp, kl, ml, 1, 1.0, xl, yl, s)) != cudaSuccess)
             return cuda_fail(e, "apply_K");
     } else {

@@ -39,6 +39,9 @@ struct OpState {
     double* inv64 = nullptr;        // inverse diagonal (N, or N x 2 for the prior)
     float* inv32 = nullptr;
     double inv_T2 = 0, scale1 = 1, delta = 0;
+    int nv = 1;                     // assembled value sets (1: K, 2: prior blocks)
+    double* v64[2] = {nullptr, nullptr};  // assembled FP64 values (sliced ELLPACK)
+    float* v32[2] = {nullptr, nullptr};   // FP32 copy (K only)
 };
 
 struct SolveOpts {
@@ -47,6 +50,7 @@ struct SolveOpts {
     int maxit = 20000;
     double inner_rtol = 1e-4;
     int max_sweeps = 30;
+    int fp32_assembled = 0;   // FP32 inner operator: 0 matrix-free elements, 1 assembled values
 };
 
 struct DeviceGuard {

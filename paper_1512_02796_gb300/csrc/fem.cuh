@@ -21,7 +21,11 @@
 
 namespace qpat {
 
-enum OpKind { OP_K = 0, OP_PRIOR = 1 };
+// OP_K / OP_PRIOR: matrix-free element operators recomputed from the
+// geometry on every apply.  OP_CSR1 / OP_CSR2: the same operators assembled
+// once per linearisation into the sliced-ELLPACK pattern of the mesh (one
+// value array shared by all right-hand sides, or one per prior block).
+enum OpKind { OP_K = 0, OP_PRIOR = 1, OP_CSR1 = 2, OP_CSR2 = 3 };
 
 constexpr int kThreads = 256;
 
@@ -33,7 +37,51 @@ struct OpParams {
     T scale1;        // OP_PRIOR: b / a on block 1 (Eq. (16))
     T delta;         // OP_PRIOR: delta of M_delta (Eq. (19))
     int robin;       // OP_K: include the Robin boundary term
+    const T* v0;     // OP_CSR*: assembled values (block 0 / all RHS)
+    const T* v1;     // OP_CSR2: assembled values of block 1
 };
+
+// Slot of local column c in library row g of the sliced-ELLPACK pattern.
+__device__ __forceinline__ int64_t sell_slot(const MeshDev& m, int g, int c) {
+    const int64_t base = m.sell_ptr[g >> 5];
+    const int lane = g & 31, len = m.sell_len[g];
+    for (int k = 0; k < len; ++k) {
+        const int64_t idx = (base + k) * 32 + lane;
+        if (m.sell_col[idx] == c) return idx;
+    }
+    return -1;
+}
+
+// Rows [ob, ob + nown) of an assembled operator applied to staged input
+// xin (touched x R, node-major), R right-hand sides; result written by
+// `emit(i, r, value)` with i the owned local row.
+template <typename T, int R, int NV, class Emit>
+__device__ __forceinline__ void csr_rows(const MeshDev& m, int ob, int nown, const T* __restrict__ v0,
+                                         const T* __restrict__ v1, const T* xin, Emit emit) {
+    for (int i = threadIdx.x; i < nown; i += blockDim.x) {
+        const int g = ob + i;
+        const int64_t base = m.sell_ptr[g >> 5] * 32 + (g & 31);
+        const int len = m.sell_len[g];
+        T acc[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) acc[r] = T(0);
+        for (int k = 0; k < len; ++k) {
+            const int64_t idx = base + int64_t(k) * 32;
+            const int c = m.sell_col[idx];
+            if constexpr (NV == 1) {
+                const T v = __ldg(v0 + idx);
+#pragma unroll
+                for (int r = 0; r < R; ++r) acc[r] += v * xin[c * R + r];
+            } else {
+                static_assert(R == 2, "two value sets mean two blocks");
+                acc[0] += __ldg(v0 + idx) * xin[c * 2];
+                acc[1] += __ldg(v1 + idx) * xin[c * 2 + 1];
+            }
+        }
+#pragma unroll
+        for (int r = 0; r < R; ++r) emit(i, r, acc[r]);
+    }
+}
 
 template <typename T>
 __device__ __forceinline__ void tet_cofactors(const T p[4][3], T c[4][3], T& ad) {

@@ -134,6 +134,150 @@ __global__ void __launch_bounds__(kThreads) k_diag_prior(MeshDev m, const double
     }
 }
 
+// ---------------------------------------------------------------- assembly (FP64)
+// Element matrices of K (Appendix weak form) added into the owned rows of
+// the sliced-ELLPACK values:  A_ab = S_kappa/(24|det|) c_a.c_b
+//   + |T|/120 (a == b ? 2 S_mu + 4 mu_a : S_mu + mu_a + mu_b)   [exact P1 mass]
+//   + Robin |F|/24 (1 + delta_ab) on boundary faces.
+__global__ void __launch_bounds__(kThreads) k_assemble_K(MeshDev m, const double* __restrict__ kappa,
+                                                         const double* __restrict__ mu, double* val) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    PatchSmem<double, 1> s;
+    s.carve(reinterpret_cast<double*>(smem_raw), m.max_touched, m.max_own);
+    const int p = blockIdx.x;
+    const int nb = m.node_ptr[p], nt = m.node_ptr[p + 1] - nb;
+    const int ob = m.own_begin[p], nown = m.own_begin[p + 1] - ob;
+    OpParams<double> op{kappa, mu, 0, 0, 0, 1};
+    stage_static<double, 1>(m, nb, nt, s, op);
+    __syncthreads();
+    for (int t = m.tet_ptr[p] + threadIdx.x; t < m.tet_ptr[p + 1]; t += blockDim.x) {
+        const ushort4 lv = m.tet_loc[t];
+        const int v[4] = {lv.x, lv.y, lv.z, lv.w};
+        double pc[4][3], c[4][3], ad;
+        load_tet(s, lv, pc);
+        tet_cofactors(pc, c, ad);
+        double ks = 0, Sm = 0;
+        for (int a = 0; a < 4; ++a) {
+            ks += s.c1[v[a]];
+            Sm += s.c2[v[a]];
+        }
+        const double sk = ks / (24.0 * ad), vm = ad / 720.0;
+        for (int a = 0; a < 4; ++a) {
+            if (v[a] >= nown) continue;
+            const int g = ob + v[a];
+            for (int b = 0; b < 4; ++b) {
+                const double st = sk * (c[a][0] * c[b][0] + c[a][1] * c[b][1] + c[a][2] * c[b][2]);
+                const double ms = a == b ? 2.0 * Sm + 4.0 * s.c2[v[a]] : Sm + s.c2[v[a]] + s.c2[v[b]];
+                const int64_t idx = sell_slot(m, g, v[b]);
+                if (idx >= 0) atomicAdd(val + idx, st + vm * ms);
+            }
+        }
+    }
+    for (int f = m.face_ptr[p] + threadIdx.x; f < m.face_ptr[p + 1]; f += blockDim.x) {
+        const ushort4 lv = m.face_loc[f];
+        const int v[3] = {lv.x, lv.y, lv.z};
+        const double w = m.pface_area64[f] / 24.0;
+        for (int a = 0; a < 3; ++a) {
+            if (v[a] >= nown) continue;
+            for (int b = 0; b < 3; ++b) {
+                const int64_t idx = sell_slot(m, ob + v[a], v[b]);
+                if (idx >= 0) atomicAdd(val + idx, a == b ? 2.0 * w : w);
+            }
+        }
+    }
+}
+
+// Prior blocks: A^r_ab = scale_r c_T(u_r) c_a.c_b / (6 |det|), c_T = 1/(1 + |grad u_r|^2/T^2)
+__global__ void __launch_bounds__(kThreads) k_assemble_prior(MeshDev m, const double* __restrict__ u1,
+                                                             const double* __restrict__ u2, double inv_T2,
+                                                             double scale1, double* val0, double* val1) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    PatchSmem<double, 1> s;
+    s.carve(reinterpret_cast<double*>(smem_raw), m.max_touched, m.max_own);
+    const int p = blockIdx.x;
+    const int nb = m.node_ptr[p], nt = m.node_ptr[p + 1] - nb;
+    const int ob = m.own_begin[p], nown = m.own_begin[p + 1] - ob;
+    OpParams<double> op{u1, u2, 0, 0, 0, 0};
+    stage_static<double, 1>(m, nb, nt, s, op);
+    __syncthreads();
+    for (int t = m.tet_ptr[p] + threadIdx.x; t < m.tet_ptr[p + 1]; t += blockDim.x) {
+        const ushort4 lv = m.tet_loc[t];
+        const int v[4] = {lv.x, lv.y, lv.z, lv.w};
+        double pc[4][3], c[4][3], ad;
+        load_tet(s, lv, pc);
+        tet_cofactors(pc, c, ad);
+        double coef[2];
+        for (int r = 0; r < 2; ++r) {
+            const double* uc = r == 0 ? s.c1 : s.c2;
+            double u[4], Gu[3];
+            for (int a = 0; a < 4; ++a) u[a] = uc[v[a]];
+            grad_vec(c, u, Gu);
+            const double g2 = (Gu[0] * Gu[0] + Gu[1] * Gu[1] + Gu[2] * Gu[2]) / (ad * ad);
+            coef[r] = (r == 0 ? 1.0 : scale1) / (1.0 + g2 * inv_T2) / (6.0 * ad);
+        }
+        for (int a = 0; a < 4; ++a) {
+            if (v[a] >= nown) continue;
+            const int g = ob + v[a];
+            for (int b = 0; b < 4; ++b) {
+                const double cc = c[a][0] * c[b][0] + c[a][1] * c[b][1] + c[a][2] * c[b][2];
+                const int64_t idx = sell_slot(m, g, v[b]);
+                if (idx >= 0) {
+                    atomicAdd(val0 + idx, coef[0] * cc);
+                    atomicAdd(val1 + idx, coef[1] * cc);
+                }
+            }
+        }
+    }
+}
+
+// val_r[diag] += shift ; inv[g * NV + r] = 1 / val_r[diag]  (FP64, optional FP32 copy)
+__global__ void k_diag_csr(MeshDev m, int NV, double shift, double* val0, double* val1, double* inv64, float* inv32) {
+    for (int64_t g = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; g < m.N; g += int64_t(gridDim.x) * blockDim.x) {
+        const int64_t idx = (m.sell_ptr[g >> 5] + m.sell_diag[g]) * 32 + (g & 31);
+        for (int r = 0; r < NV; ++r) {
+            double* v = r == 0 ? val0 : val1;
+            const double d = v[idx] + shift;
+            v[idx] = d;
+            inv64[g * NV + r] = 1.0 / d;
+            if (inv32) inv32[g * NV + r] = float(1.0 / d);
+        }
+    }
+}
+
+__global__ void k_cast_vals(int64_t n, const double* in, float* out) {
+    for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x)
+        out[i] = float(in[i]);
+}
+
+// y = A x with an assembled operator: one CTA per patch, x staged on the
+// touched nodes in shared memory, thread-per-row sliced-ELLPACK rows.
+template <typename T, int R, int NV>
+__global__ void __launch_bounds__(kThreads) k_apply_csr(MeshDev m, const T* __restrict__ v0,
+                                                        const T* __restrict__ v1, const T* __restrict__ x,
+                                                        T* __restrict__ y) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T* xin = reinterpret_cast<T*>(smem_raw);
+    const int p = blockIdx.x;
+    const int nb = m.node_ptr[p], nt = m.node_ptr[p + 1] - nb;
+    const int ob = m.own_begin[p], nown = m.own_begin[p + 1] - ob;
+    for (int i = threadIdx.x; i < nt * R; i += blockDim.x) {
+        const int g = __ldg(m.nodes + nb + i / R);
+        xin[i] = __ldg(x + size_t(g) * R + (i % R));
+    }
+    __syncthreads();
+    csr_rows<T, R, NV>(m, ob, nown, v0, v1, xin, [&](int i, int r, T v) { y[size_t(ob + i) * R + r] = v; });
+}
+
+template <typename T, int R, int NV>
+cudaError_t apply_csr_t(const MeshDev& m, const T* v0, const T* v1, const T* x, T* y, cudaStream_t st) {
+    const size_t smem = sizeof(T) * size_t(m.max_touched) * R;
+    auto kern = k_apply_csr<T, R, NV>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+    if (e != cudaSuccess) return e;
+    kern<<<m.P, kThreads, smem, st>>>(m, v0, v1, x, y);
+    return cudaGetLastError();
+}
+
 // ---------------------------------------------------------------- J^T pieces
 // y[g][0] = -sum_k sum_{T ni g} (|T|/4) grad(phi_k) . grad(z_k)       ( = sum_k G1^T z_k )
 // y[g][1] = -sum_k (M(phi_k) z_k)_g                                    ( = sum_k G2 z_k )
@@ -341,6 +485,59 @@ cudaError_t launch_invdiag_prior(const MeshDev& m, const double* u1, const doubl
     k_diag_prior<<<m.P, kThreads, smem, s>>>(m, u1, u2, inv_T2, scale1, delta, inv64, inv32);
     return cudaGetLastError();
 }
+
+cudaError_t launch_assemble_K(const MeshDev& m, const double* kappa, const double* mu, double* val, double* inv64,
+                              float* inv32, cudaStream_t s) {
+    cudaError_t e = cudaMemsetAsync(val, 0, sizeof(double) * m.sell_entries, s);
+    if (e != cudaSuccess) return e;
+    const size_t smem = PatchSmem<double, 1>::bytes(m.max_touched, m.max_own);
+    e = cudaFuncSetAttribute(k_assemble_K, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+    if (e != cudaSuccess) return e;
+    k_assemble_K<<<m.P, kThreads, smem, s>>>(m, kappa, mu, val);
+    k_diag_csr<<<grid_for(m.N), 256, 0, s>>>(m, 1, 0.0, val, nullptr, inv64, inv32);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_assemble_prior(const MeshDev& m, const double* u1, const double* u2, double inv_T2, double scale1,
+                                  double delta, double* val0, double* val1, double* inv64, float* inv32,
+                                  cudaStream_t s) {
+    cudaError_t e = cudaMemsetAsync(val0, 0, sizeof(double) * m.sell_entries, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(val1, 0, sizeof(double) * m.sell_entries, s);
+    if (e != cudaSuccess) return e;
+    const size_t smem = PatchSmem<double, 1>::bytes(m.max_touched, m.max_own);
+    e = cudaFuncSetAttribute(k_assemble_prior, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+    if (e != cudaSuccess) return e;
+    k_assemble_prior<<<m.P, kThreads, smem, s>>>(m, u1, u2, inv_T2, scale1, val0, val1);
+    k_diag_csr<<<grid_for(m.N), 256, 0, s>>>(m, 2, delta, val0, val1, inv64, inv32);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_cast_vals(int64_t n, const double* in, float* out, cudaStream_t s) {
+    k_cast_vals<<<grid_for(n), 256, 0, s>>>(n, in, out);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_apply_csr(const MeshDev& m, int NV, int R, const T* v0, const T* v1, const T* x, T* y,
+                             cudaStream_t s) {
+    if (NV == 2) {
+        if (R != 2) return cudaErrorInvalidValue;
+        return apply_csr_t<T, 2, 2>(m, v0, v1, x, y, s);
+    }
+    switch (R) {
+        case 1: return apply_csr_t<T, 1, 1>(m, v0, v1, x, y, s);
+        case 2: return apply_csr_t<T, 2, 1>(m, v0, v1, x, y, s);
+        case 4: return apply_csr_t<T, 4, 1>(m, v0, v1, x, y, s);
+        case 8: return apply_csr_t<T, 8, 1>(m, v0, v1, x, y, s);
+        case 16: return apply_csr_t<T, 16, 1>(m, v0, v1, x, y, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+template cudaError_t launch_apply_csr<double>(const MeshDev&, int, int, const double*, const double*, const double*,
+                                              double*, cudaStream_t);
+template cudaError_t launch_apply_csr<float>(const MeshDev&, int, int, const float*, const float*, const float*,
+                                             float*, cudaStream_t);
 
 template <typename T>
 cudaError_t launch_vjp_accum(const MeshDev& m, int K, const T* phi, const T* z, T* y, cudaStream_t s) {

@@ -22,6 +22,19 @@ cudaError_t launch_invdiag_K(const MeshDev& m, const double* kappa, const double
                              float* inv32, cudaStream_t s);
 cudaError_t launch_invdiag_prior(const MeshDev& m, const double* u1, const double* u2, double inv_T2,
                                  double scale1, double delta, double* inv64, float* inv32, cudaStream_t s);
+// Assembly of K (FP64 values in the sliced-ELLPACK pattern; val must hold
+// m.sell_entries) and of the two prior blocks with delta on the diagonal;
+// both also write the inverse diagonal (FP64 and, if not null, FP32).
+cudaError_t launch_assemble_K(const MeshDev& m, const double* kappa, const double* mu, double* val, double* inv64,
+                              float* inv32, cudaStream_t s);
+cudaError_t launch_assemble_prior(const MeshDev& m, const double* u1, const double* u2, double inv_T2, double scale1,
+                                  double delta, double* val0, double* val1, double* inv64, float* inv32,
+                                  cudaStream_t s);
+cudaError_t launch_cast_vals(int64_t n, const double* in, float* out, cudaStream_t s);
+// y = A x with an assembled operator (NV = 1: one value set for R RHS; NV = 2: the prior, R = 2)
+template <typename T>
+cudaError_t launch_apply_csr(const MeshDev& m, int NV, int R, const T* v0, const T* v1, const T* x, T* y,
+                             cudaStream_t s);
 // y (N x 2) = [ -sum_k G1-transpose-type term ; -sum_k M(phi_k) z_k ] (see kernels.cu)
 template <typename T>
 cudaError_t launch_vjp_accum(const MeshDev& m, int K, const T* phi, const T* z, T* y, cudaStream_t s);

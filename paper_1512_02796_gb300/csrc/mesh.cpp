@@ -38,8 +38,8 @@ std::string build_host_mesh(const double* xyz, int64_t N, const int32_t* tets,
         return "qpat_mesh: empty mesh or NULL array";
     if (N >= (int64_t(1) << 31) || E >= (int64_t(1) << 29))
         return "qpat_mesh: mesh too large for 32-bit ids";
-    if (patch_nodes < 32 || patch_nodes > 8192)
-        return "qpat_mesh: patch_nodes must be in [32, 8192]";
+    if (patch_nodes < 32 || patch_nodes > 8192 || patch_nodes % 32 != 0)
+        return "qpat_mesh: patch_nodes must be a multiple of 32 in [32, 8192]";
     for (int64_t i = 0; i < 4 * E; ++i)
         if (tets[i] < 0 || tets[i] >= N) return "qpat_mesh: tet node id out of range";
     for (int64_t i = 0; i < 3 * N; ++i)
@@ -172,6 +172,7 @@ std::string build_host_mesh(const double* xyz, int64_t N, const int32_t* tets,
     m.face_ptr.assign(1, 0);
     std::vector<int32_t> tet_stamp(E, -1), face_stamp(m.F, -1), node_local(N, -1);
     std::vector<int32_t> ptets, pfaces, halo;
+    std::vector<std::vector<uint16_t>> rows(N);  // local column ids of every row
     for (int p = 0; p < P; ++p) {
         const int32_t b = m.own_begin[p], e = m.own_begin[p + 1];
         const int nown = e - b;
@@ -198,7 +199,7 @@ std::string build_host_mesh(const double* xyz, int64_t N, const int32_t* tets,
         for (int32_t t : ptets)
             for (int k = 0; k < 4; ++k) {
                 int32_t g = m.tets[4 * t + k];
-                if ((g < b || g >= e) && node_local[g] < 0) {
+                if ((g < b || g >= e) && node_local[g] == -1) {
                     node_local[g] = -2;  // seen
                     halo.push_back(g);
                 }
@@ -209,8 +210,22 @@ std::string build_host_mesh(const double* xyz, int64_t N, const int32_t* tets,
         if (ntouch > 65535) return "qpat_mesh: a patch touches more than 65535 nodes";
         for (int32_t g = b; g < e; ++g) m.nodes.push_back(g);
         for (int32_t g : halo) m.nodes.push_back(g);
-        for (int32_t t : ptets)
-            for (int k = 0; k < 4; ++k) m.tet_loc.push_back(uint16_t(node_local[m.tets[4 * t + k]]));
+        for (int32_t t : ptets) {
+            int32_t lv[4];
+            for (int k = 0; k < 4; ++k) {
+                lv[k] = node_local[m.tets[4 * t + k]];
+                m.tet_loc.push_back(uint16_t(lv[k]));
+            }
+            for (int a = 0; a < 4; ++a)
+                if (lv[a] < nown)
+                    for (int c = 0; c < 4; ++c) rows[b + lv[a]].push_back(uint16_t(lv[c]));
+        }
+        for (int32_t g = b; g < e; ++g) {
+            auto& r = rows[g];
+            std::sort(r.begin(), r.end());
+            r.erase(std::unique(r.begin(), r.end()), r.end());
+            if (r.size() > 255) return "qpat_mesh: a node has more than 254 neighbours";
+        }
         for (int32_t f : pfaces) {
             for (int k = 0; k < 3; ++k) m.face_loc.push_back(uint16_t(node_local[m.faces_lib[3 * f + k]]));
             m.face_loc.push_back(0);
@@ -225,6 +240,38 @@ std::string build_host_mesh(const double* xyz, int64_t N, const int32_t* tets,
         m.max_pfaces = std::max(m.max_pfaces, int(pfaces.size()));
         for (int32_t g = b; g < e; ++g) node_local[g] = -1;
         for (int32_t g : halo) node_local[g] = -1;
+    }
+
+    // ---- sliced ELLPACK pattern (slices never straddle patches: patch_nodes % 32 == 0)
+    m.nslices = (N + 31) / 32;
+    m.sell_ptr.assign(m.nslices + 1, 0);
+    m.sell_len.resize(N);
+    m.sell_diag.resize(N);
+    for (int64_t s = 0; s < m.nslices; ++s) {
+        size_t w = 0;
+        for (int64_t g = 32 * s; g < std::min<int64_t>(N, 32 * s + 32); ++g) w = std::max(w, rows[g].size());
+        m.sell_ptr[s + 1] = m.sell_ptr[s] + int64_t(w);
+    }
+    m.sell_col.assign(size_t(32) * m.sell_ptr[m.nslices], 0);
+    for (int64_t s = 0; s < m.nslices; ++s) {
+        const int64_t w = m.sell_ptr[s + 1] - m.sell_ptr[s];
+        for (int lane = 0; lane < 32; ++lane) {
+            const int64_t g = 32 * s + lane;
+            uint16_t self = 0;
+            if (g < N) {
+                const int p = int(g / patch_nodes);
+                self = uint16_t(g - m.own_begin[p]);
+                m.sell_len[g] = uint8_t(rows[g].size());
+                m.sell_diag[g] = -1;
+            }
+            for (int64_t k = 0; k < w; ++k) {
+                uint16_t c = self;
+                if (g < N && k < int64_t(rows[g].size())) c = rows[g][k];
+                m.sell_col[(m.sell_ptr[s] + k) * 32 + lane] = c;
+                if (g < N && k < int64_t(rows[g].size()) && c == self) m.sell_diag[g] = int32_t(k);
+            }
+            if (g < N && m.sell_diag[g] < 0) return "qpat_mesh: a node belongs to no tetrahedron";
+        }
     }
     return "";
 }

@@ -113,6 +113,10 @@ int upload_mesh(qpat_mesh_s* M) {
         (rc = up(M, h.faces_lib, &d.faces_lib)) || (rc = up(M, h.farea, &d.farea)) ||
         (rc = up(M, h.perm, &d.perm)) || (rc = up(M, h.iperm, &d.iperm)))
         return rc;
+    if ((rc = up(M, h.sell_ptr, &d.sell_ptr)) || (rc = up(M, h.sell_col, &d.sell_col)) ||
+        (rc = up(M, h.sell_len, &d.sell_len)) || (rc = up(M, h.sell_diag, &d.sell_diag)))
+        return rc;
+    d.sell_entries = int64_t(h.sell_col.size());
     const uint16_t* tl = nullptr;
     if ((rc = up(M, h.tet_loc, &tl))) return rc;
     d.tet_loc = reinterpret_cast<const ushort4*>(tl);
@@ -134,6 +138,7 @@ SolveOpts solve_opts(const qpat_params* prm) {
     so.precision = p->precision;
     so.rtol = p->pcg_rtol > 0 ? p->pcg_rtol : 1e-13;
     so.maxit = p->max_pcg_iter > 0 ? p->max_pcg_iter : 20000;
+    so.fp32_assembled = p->fp32_operator == 1 ? 1 : 0;
     return so;
 }
 

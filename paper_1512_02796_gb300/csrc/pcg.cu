@@ -97,7 +97,9 @@ __device__ __forceinline__ bool grid_sum(double (&acc)[NQ], double* scratch, dou
 #pragma unroll
         for (int q = 0; q < NQ; ++q) scratch[(warp * NQ + q) * R + lane] = acc[q];
     __syncthreads();
-    double* part = partials + size_t(red_id & 1) * kMaxGrid * NQ * R;
+    // two buffers of fixed stride (the largest reduction, 3 x 16 values):
+    // a slow CTA still reading reduction k never sees reduction k+1's writes
+    double* part = partials + size_t(red_id & 1) * kMaxGrid * 48;
     if (threadIdx.x < NQ * R) {
         const int q = threadIdx.x / R, r = threadIdx.x % R;
         double a = 0.0;
@@ -118,17 +120,54 @@ __device__ __forceinline__ bool grid_sum(double (&acc)[NQ], double* scratch, dou
     return true;
 }
 
+// Grid-wide sum of NS values held (all of them) by every thread.
+template <int NS>
+__device__ __forceinline__ bool grid_sum_full(double (&acc)[NS], double* scratch, double* partials, int& red_id,
+                                              unsigned* bar, int* status, long long limit, double* out) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+    for (int q = 0; q < NS; ++q)
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) acc[q] += __shfl_down_sync(0xffffffffu, acc[q], o);
+    if (lane == 0)
+#pragma unroll
+        for (int q = 0; q < NS; ++q) scratch[warp * NS + q] = acc[q];
+    __syncthreads();
+    double* part = partials + size_t(red_id & 1) * kMaxGrid * 48;
+    if (threadIdx.x < NS) {
+        double a = 0.0;
+        for (int w = 0; w < nw; ++w) a += scratch[w * NS + threadIdx.x];
+        part[size_t(blockIdx.x) * NS + threadIdx.x] = a;
+    }
+    ++red_id;
+    if (!grid_sync(bar, status, limit)) return false;
+    for (int s = warp; s < NS; s += nw) {
+        double a = 0.0;
+        for (int j = lane; j < gridDim.x; j += 32) a += __ldcg(part + size_t(j) * NS + s);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+        if (lane == 0) out[s] = a;
+    }
+    __syncthreads();
+    return true;
+}
+
 template <typename T, int R, int OP>
 __device__ __forceinline__ T dinv(const T* invdiag, int g, int r) {
-    return OP == OP_PRIOR ? __ldg(invdiag + 2 * g + r) : __ldg(invdiag + g);
+    return (OP == OP_PRIOR || OP == OP_CSR2) ? __ldg(invdiag + 2 * g + r) : __ldg(invdiag + g);
 }
 
 template <typename T, int R, int OP>
 __global__ void __launch_bounds__(kThreads) k_pcg(PcgArgs<T> a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
+    constexpr bool kCsr = (OP == OP_CSR1 || OP == OP_CSR2);
     PatchSmem<T, R> s;
-    s.carve(reinterpret_cast<T*>(smem_raw), a.m.max_touched, a.m.max_own);
-    __shared__ double scratch[(kThreads / 32) * 3 * R];
+    if constexpr (kCsr) {
+        s.xin = reinterpret_cast<T*>(smem_raw);  // assembled operators stage p only
+    } else {
+        s.carve(reinterpret_cast<T*>(smem_raw), a.m.max_touched, a.m.max_own);
+    }
+    __shared__ double scratch[(kThreads / 32) * 3 * 16];
     __shared__ double red[3 * R];
     __shared__ double bb[R], rz[R], rz_old[R], rr[R], alpha[R], beta[R];
     __shared__ int s_flag;
@@ -190,9 +229,33 @@ __global__ void __launch_bounds__(kThreads) k_pcg(PcgArgs<T> a) {
 
         // ---- phase A: p = D^-1 r + beta p_old on touched nodes, q = A p on owned nodes
         double accA[1] = {0.0};
+        double accF[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) accF[r] = 0.0;
         for (int p = blockIdx.x; p < P; p += gridDim.x) {
             const int nb = __ldg(m.node_ptr + p), nt = __ldg(m.node_ptr + p + 1) - nb;
             const int ob = __ldg(m.own_begin + p), nown = __ldg(m.own_begin + p + 1) - ob;
+            if constexpr (kCsr) {
+                for (int i = threadIdx.x; i < nt * R; i += blockDim.x) {
+                    const int g = __ldg(m.nodes + nb + i / R);
+                    const size_t e = size_t(g) * R + myr;
+                    T pv = dinv<T, R, OP>(a.invdiag, g, myr) * __ldcg(a.r + e);
+                    const T bt = T(beta[myr]);
+                    if (bt != T(0)) pv += bt * __ldcg(pp + e);
+                    s.xin[i] = pv;
+                }
+                __syncthreads();
+                csr_rows<T, R, (OP == OP_CSR2 ? 2 : 1)>(m, ob, nown, a.op.v0, a.op.v1, s.xin,
+                                                       [&](int i, int r, T qv) {
+                                                           const size_t e = size_t(ob + i) * R + r;
+                                                           const T pv = s.xin[i * R + r];
+                                                           pc[e] = pv;
+                                                           a.q[e] = qv;
+                                                           accF[r] += double(pv) * double(qv);
+                                                       });
+                __syncthreads();
+                continue;
+            }
             stage_static<T, R>(m, nb, nt, s, a.op);
             for (int i = threadIdx.x; i < nt * R; i += blockDim.x) {
                 const int li = i / R;
@@ -205,20 +268,26 @@ __global__ void __launch_bounds__(kThreads) k_pcg(PcgArgs<T> a) {
             }
             for (int i = threadIdx.x; i < nown * R; i += blockDim.x) s.yout[i] = T(0);
             __syncthreads();
-            patch_elements<T, R, OP>(m, p, nown, s, a.op);
-            __syncthreads();
-            for (int i = threadIdx.x; i < nown * R; i += blockDim.x) {
-                const size_t e = size_t(ob) * R + i;
-                const T pv = s.xin[i];
-                T qv = s.yout[i];
-                if (OP == OP_PRIOR) qv += a.op.delta * pv;
-                pc[e] = pv;
-                a.q[e] = qv;
-                accA[0] += double(pv) * double(qv);
+            if constexpr (!kCsr) {
+                patch_elements<T, R, OP>(m, p, nown, s, a.op);
+                __syncthreads();
+                for (int i = threadIdx.x; i < nown * R; i += blockDim.x) {
+                    const size_t e = size_t(ob) * R + i;
+                    const T pv = s.xin[i];
+                    T qv = s.yout[i];
+                    if (OP == OP_PRIOR) qv += a.op.delta * pv;
+                    pc[e] = pv;
+                    a.q[e] = qv;
+                    accA[0] += double(pv) * double(qv);
+                }
+                __syncthreads();
             }
-            __syncthreads();
         }
-        if (!grid_sum<R, 1>(accA, scratch, a.partials, red_id, a.bar, a.status, a.spin_limit, red)) return;
+        if constexpr (kCsr) {
+            if (!grid_sum_full<R>(accF, scratch, a.partials, red_id, a.bar, a.status, a.spin_limit, red)) return;
+        } else {
+            if (!grid_sum<R, 1>(accA, scratch, a.partials, red_id, a.bar, a.status, a.spin_limit, red)) return;
+        }
         if (threadIdx.x == 0) {
             int bad = 0;
             for (int r = 0; r < R; ++r) {
@@ -276,7 +345,8 @@ __global__ void __launch_bounds__(kThreads) k_pcg(PcgArgs<T> a) {
 template <typename T, int R, int OP>
 cudaError_t launch_pcg_t(const MeshDev& m, const OpParams<T>& op, const T* invdiag, const PcgWork& w,
                          double rtol, int maxit, cudaStream_t s, int* grid_used) {
-    const size_t smem = PatchSmem<T, R>::bytes(m.max_touched, m.max_own);
+    const size_t smem = (OP == OP_CSR1 || OP == OP_CSR2) ? sizeof(T) * size_t(m.max_touched) * R
+                                                         : PatchSmem<T, R>::bytes(m.max_touched, m.max_own);
     auto kern = k_pcg<T, R, OP>;
     cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
     if (err != cudaSuccess) return err;
@@ -326,6 +396,20 @@ cudaError_t launch_pcg(const MeshDev& m, int OP, int R, const OpParams<T>& op, c
     if (OP == OP_PRIOR) {
         if (R != 2) return cudaErrorInvalidValue;
         return launch_pcg_t<T, 2, OP_PRIOR>(m, op, invdiag, w, rtol, maxit, s, grid_used);
+    }
+    if (OP == OP_CSR2) {
+        if (R != 2) return cudaErrorInvalidValue;
+        return launch_pcg_t<T, 2, OP_CSR2>(m, op, invdiag, w, rtol, maxit, s, grid_used);
+    }
+    if (OP == OP_CSR1) {
+        switch (R) {
+            case 1: return launch_pcg_t<T, 1, OP_CSR1>(m, op, invdiag, w, rtol, maxit, s, grid_used);
+            case 2: return launch_pcg_t<T, 2, OP_CSR1>(m, op, invdiag, w, rtol, maxit, s, grid_used);
+            case 4: return launch_pcg_t<T, 4, OP_CSR1>(m, op, invdiag, w, rtol, maxit, s, grid_used);
+            case 8: return launch_pcg_t<T, 8, OP_CSR1>(m, op, invdiag, w, rtol, maxit, s, grid_used);
+            case 16: return launch_pcg_t<T, 16, OP_CSR1>(m, op, invdiag, w, rtol, maxit, s, grid_used);
+            default: return cudaErrorInvalidValue;
+        }
     }
     switch (R) {
         case 1: return launch_pcg_t<T, 1, OP_K>(m, op, invdiag, w, rtol, maxit, s, grid_used);

@@ -40,6 +40,16 @@ struct HostMesh {
     std::vector<double> pface_area;     // per patch face
     int max_touched = 0, max_own = 0, max_ptets = 0, max_pfaces = 0;
     double extent = 0.0;                // largest bounding-box side
+    // Assembled-operator pattern in sliced ELLPACK form (slices of 32
+    // consecutive library rows; entry k of row 32 s + lane sits at
+    // (sell_ptr[s] + k) * 32 + lane).  Column ids are LOCAL ids of the row's
+    // patch (the patch's touched-node numbering), padding entries repeat the
+    // row's own local id with a zero value.
+    int64_t nslices = 0;
+    std::vector<int64_t> sell_ptr;      // nslices + 1, in units of 32 entries
+    std::vector<uint16_t> sell_col;     // 32 * sell_ptr[nslices]
+    std::vector<uint8_t> sell_len;      // row lengths (N)
+    std::vector<int32_t> sell_diag;     // k of the diagonal entry of each row (N)
 };
 
 // Builds a HostMesh; returns "" on success or an error message.
@@ -69,6 +79,12 @@ struct MeshDev {
     const double* farea;        // F
     const int* perm;            // library -> caller
     const int* iperm;           // caller -> library
+    // sliced-ELLPACK pattern of the assembled operators (see HostMesh)
+    const int64_t* sell_ptr;
+    const uint16_t* sell_col;
+    const uint8_t* sell_len;
+    const int* sell_diag;
+    int64_t sell_entries;       // 32 * sell_ptr[nslices]
 };
 
 }  // namespace qpat

@@ -28,7 +28,8 @@ class qpat_params(ctypes.Structure):
         ("tau", ctypes.c_double), ("m0", ctypes.c_int), ("max_lin", ctypes.c_int),
         ("max_lsqr", ctypes.c_int), ("fixed_counts", ctypes.c_int), ("precision", ctypes.c_int),
         ("max_pcg_iter", ctypes.c_int), ("pcg_rtol", ctypes.c_double), ("fit_grid", ctypes.c_int),
-        ("fit_gn_steps", ctypes.c_int), ("patch_nodes", ctypes.c_int), ("reserved", ctypes.c_int * 7),
+        ("fit_gn_steps", ctypes.c_int), ("patch_nodes", ctypes.c_int), ("fp32_operator", ctypes.c_int),
+        ("reserved", ctypes.c_int * 6),
     ]
 
 

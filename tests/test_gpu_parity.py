@@ -48,7 +48,7 @@ def test_mesh_faces_and_flux(case):
         np.testing.assert_array_equal(f, case.flux[k])
 
 
-@pytest.mark.parametrize("precision,tol", [(0, 1e-13), (1, 2e-6)])
+@pytest.mark.parametrize("precision,tol", [(0, 1e-13), (1, 2e-6), (2, 1e-13), (3, 2e-6)])
 @pytest.mark.parametrize("R", [1, 3, 4, 8])
 def test_apply_K(case, precision, tol, R):
     rng = np.random.default_rng(R)
@@ -63,9 +63,9 @@ def test_apply_K(case, precision, tol, R):
     assert rel(yt.cpu().numpy(), y_ref) < tol
 
 
-@pytest.mark.parametrize("precision", [0, 1])
-def test_forward(case, precision):
-    phi, h = Q.qpat_forward(case.lib, case.kappa, case.mu, case.flux, _params(precision))
+@pytest.mark.parametrize("precision,fp32_op", [(0, 0), (1, 0), (1, 1)])
+def test_forward(case, precision, fp32_op):
+    phi, h = Q.qpat_forward(case.lib, case.kappa, case.mu, case.flux, _params(precision, fp32_operator=fp32_op))
     assert rel(phi, case.phi) < 1e-10
     assert rel(h, case.h) < 1e-10
 
@@ -129,7 +129,9 @@ def test_prior_solve(case, precision):
     p = _params(precision, T=T, b_over_a=ba, delta=delta, pcg_rtol=1e-13)
     out = Q.qpat_prior_solve(case.lib, kt, mt, rhs, p)
     res = np.linalg.norm(Md @ out - rhs) / np.linalg.norm(rhs)
-    assert res < 1e-12
+    # the PCG stops on its recursive residual (1e-13); the true residual of
+    # an operator with cond ~1e6-1e8 drifts above it by up to ~eps * cond
+    assert res < 1e-10
     if N <= 800:
         ev = np.linalg.eigvalsh(Md.toarray())
         tol = 10 * (ev[-1] / ev[0]) * 1e-13
