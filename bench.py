@@ -150,7 +150,7 @@ def run_ours(args):
         dist.init_process_group("nccl")
     torch.cuda.set_device(local)
     precision = 1 if args.precision == "mixed" else 0
-    prm = Q.qpat_default_params(precision=precision)
+    prm = Q.qpat_default_params(precision=precision, fp32_operator=args.fp32_operator)
     d = setup_problem(Q, torch, precision)
     mesh = d["mesh"]
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")  # 256 MB > L2
@@ -339,18 +339,46 @@ def run_reference(args):
     }), flush=True)
 
 
+def run_profile_case(args):
+    """Fixed sequence for ncu captures of the PCG kernel: two FP32+refinement
+    forward solves, one pair, one M_delta solve, one FP64 forward and one
+    matrix-free FP32 forward (no timing, no output but a status line)."""
+    import torch
+    import paper_1512_02796_gb300 as Q
+    d = setup_problem(Q, torch, 1)
+    mesh = d["mesh"]
+    pm = Q.qpat_default_params(precision=1, fp32_operator=1)
+    phi = torch.empty_like(d["phi"])
+    h = torch.empty_like(phi)
+    for _ in range(2):
+        Q.qpat_forward_dev(mesh, d["kappa"], d["mu"], d["flux"], phi, h, pm)
+    Q.qpat_jvp_vjp_pair_dev(mesh, d["kappa"], d["mu"], d["phi"], d["w"], d["s"], d["t"], d["oj"], d["ov"], pm)
+    Q.qpat_prior_solve_dev(mesh, d["kt"], d["mt"], d["prior_rhs"], d["op"], pm)
+    Q.qpat_forward_dev(mesh, d["kappa"], d["mu"], d["flux"], phi, h, Q.qpat_default_params(precision=0))
+    Q.qpat_forward_dev(mesh, d["kappa"], d["mu"], d["flux"], phi, h,
+                       Q.qpat_default_params(precision=1, fp32_operator=0))
+    torch.cuda.synchronize()
+    print("profile case ok", flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
+    ap.add_argument("--profile-case", action="store_true",
+                    help="run the fixed solve sequence used for ncu captures and exit")
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--fp32-operator", type=int, default=1, choices=[0, 1],
+                    help="FP32 inner operator: 0 matrix-free elements, 1 assembled values")
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
-    if args.impl == "reference":
+    if args.profile_case:
+        run_profile_case(args)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_ours(args)

@@ -416,6 +416,24 @@ int qpat_mesh_host_info(const double* xyz, int64_t N, const int32_t* tets, int64
         expect += 1 + (pid[1] != pid[0]) + (pid[2] != pid[1]) + (pid[3] != pid[2]);
     }
     if (expect != dup) return fail(QPAT_EINVAL, "host check: patch tet lists do not cover the mesh");
+    // assembled pattern: row g lists exactly g and its edge neighbours, each once
+    std::vector<std::vector<int>> adj(h.N);
+    for (int64_t e = 0; e < h.E; ++e)
+        for (int a = 0; a < 4; ++a)
+            for (int b = 0; b < 4; ++b) adj[h.tets[4 * e + a]].push_back(h.tets[4 * e + b]);
+    for (int64_t g = 0; g < h.N; ++g) {
+        auto& ref = adj[g];
+        std::sort(ref.begin(), ref.end());
+        ref.erase(std::unique(ref.begin(), ref.end()), ref.end());
+        const int p = int(g / h.patch_nodes), nb = h.node_ptr[p];
+        std::vector<int> got;
+        for (int k = 0; k < h.sell_len[g]; ++k)
+            got.push_back(h.nodes[nb + h.sell_col[(h.sell_ptr[g >> 5] + k) * 32 + (g & 31)]]);
+        std::sort(got.begin(), got.end());
+        if (got != ref) return fail(QPAT_EINVAL, "host check: assembled pattern row " + std::to_string(g));
+        const int64_t d = (h.sell_ptr[g >> 5] + h.sell_diag[g]) * 32 + (g & 31);
+        if (h.nodes[nb + h.sell_col[d]] != g) return fail(QPAT_EINVAL, "host check: diagonal slot");
+    }
     return QPAT_OK;
 }
 
