@@ -177,6 +177,32 @@ int qpat_forward_dev(qpat_mesh_t mesh, const qpat_params* prm, const double* kap
                      const double* mu, int K, const double* flux_face,
                      double* phi, double* h, void* stream);
 
+/* Allocation-free forward solve, for callers that cannot allocate device
+ * memory when they need the solve (code issued during CUDA graph capture,
+ * real-time pipelines that forbid allocator calls after start-up, hosts that
+ * budget every byte of GPU memory themselves).  The paper has no
+ * counterpart; it computes the same phi = K^-1 f and h = mu * phi as
+ * qpat_forward_dev in FP64 (matrix-free operator, Jacobi PCG to a relative
+ * residual rtol, at most max_iter iterations), with every scratch vector in
+ * one fixed file-scope device array of 4,835,392 doubles (about 39 MB) that
+ * each GPU using the library keeps until the process exits.
+ *  - Limit: N x R <= 524,288, R = K rounded up to 1, 2, 4, 8 or 16;
+ *    larger problems return QPAT_EINVAL without touching the GPU.
+ *  - kappa, mu: N; flux_face: K x F; phi, h: K x N (either may be NULL);
+ *    all device pointers owned by the caller; stream is a cudaStream_t.
+ *  - The mesh handle must already exist (qpat_mesh allocates).
+ *  - The first call on a device looks up the array's device address
+ *    (cudaGetSymbolAddress, with that device current; the driver may load
+ *    the library's device code then) -- make that first call before any
+ *    stream capture.  No call allocates or frees device memory.
+ *  - Every call shares the one array: calls that overlap on the GPU (other
+ *    streams, other threads, other meshes) race and must be serialised by
+ *    the caller.  The call synchronises the stream before returning (it
+ *    reads the solver status). */
+int qpat_forward_noalloc_dev(qpat_mesh_t mesh, const double* kappa, const double* mu,
+                             int K, const double* flux_face, double rtol, int max_iter,
+                             double* phi, double* h, void* stream);
+
 /* out = w o (J s), stacked over K illuminations (Appendix):
  *   J s = diag(mu) K^{-1} (G1 diag(kappa) s1 + G2 diag(mu) s2) + diag(phi) diag(mu) s2
  * with G1_ij = -integral phi_j grad(varphi).grad(phi_i), G2_ij = -integral phi_j varphi phi_i.

@@ -92,6 +92,8 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
         "qpat_forward": (ctypes.c_int, [vp, ctypes.POINTER(qpat_params), _c_double_p, _c_double_p, ctypes.c_int,
                                         _c_double_p, _c_double_p, _c_double_p]),
         "qpat_forward_dev": (ctypes.c_int, [vp, ctypes.POINTER(qpat_params), vp, vp, ctypes.c_int, vp, vp, vp, vp]),
+        "qpat_forward_noalloc_dev": (ctypes.c_int, [vp, vp, vp, ctypes.c_int, vp, ctypes.c_double, ctypes.c_int,
+                                                    vp, vp, vp]),
         "qpat_jvp": (ctypes.c_int, [vp, ctypes.POINTER(qpat_params), _c_double_p, _c_double_p, ctypes.c_int,
                                     _c_double_p, _c_double_p, _c_double_p, _c_double_p]),
         "qpat_jvp_dev": (ctypes.c_int, [vp, ctypes.POINTER(qpat_params), vp, vp, ctypes.c_int, vp, vp, vp, vp, vp]),
@@ -121,7 +123,8 @@ def exported_names() -> Sequence[str]:
         "qpat_mesh_host_info", "qpat_mesh_num_nodes", "qpat_mesh_num_tets", "qpat_mesh_num_faces", "qpat_mesh_num_patches",
         "qpat_mesh_faces", "qpat_mesh_permutation", "qpat_mesh_stats", "qpat_mesh_reset_stats",
         "qpat_mesh_set_timing", "qpat_mesh_pcg_time",
-        "qpat_flux_patch", "qpat_apply_K_dev", "qpat_forward", "qpat_forward_dev", "qpat_jvp", "qpat_jvp_dev",
+        "qpat_flux_patch", "qpat_apply_K_dev", "qpat_forward", "qpat_forward_dev", "qpat_forward_noalloc_dev",
+        "qpat_jvp", "qpat_jvp_dev",
         "qpat_vjp", "qpat_vjp_dev", "qpat_jvp_vjp_pair_dev", "qpat_prior_solve", "qpat_prior_solve_dev",
         "qpat_reconstruct",
     ]
@@ -321,6 +324,15 @@ def qpat_forward_dev(mesh: Mesh, kappa, mu, flux, phi, h, params: Optional[qpat_
     K = flux.shape[0]
     _check(load().qpat_forward_dev(mesh.handle, _pp(params), _tp(kappa), _tp(mu), K, _tp(flux), _tp(phi), _tp(h),
                                    _stream()))
+    return phi, h
+
+
+def qpat_forward_noalloc_dev(mesh: Mesh, kappa, mu, flux, phi, h, rtol: float = 1e-13, max_iter: int = 20000):
+    """Forward solve whose scratch lives in the library's fixed device array
+    (no device allocation in the call); see include/qpat.h for the limit."""
+    K = flux.shape[0]
+    _check(load().qpat_forward_noalloc_dev(mesh.handle, _tp(kappa), _tp(mu), K, _tp(flux), float(rtol),
+                                           int(max_iter), _tp(phi), _tp(h), _stream()))
     return phi, h
 
 
