@@ -41,6 +41,17 @@ def env_rank():
         os.environ.get("LOCAL_RANK", "0"))
 
 
+def kernel_source_sha1() -> str:
+    """Hash of the PCG kernel sources (a stored ncu traffic figure is only
+    reported while these are unchanged)."""
+    import hashlib
+    h = hashlib.sha1()
+    for f in ("pcg.cu", "fem.cuh"):
+        with open(os.path.join(ROOT, "paper_1512_02796_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
 def load_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
@@ -102,11 +113,19 @@ class ClockSampler:
 
 
 def pcg_bytes_per_iter(N: int, E: int, R: int, s: int) -> float:
-    """Algorithmic (unique) bytes of one fused PCG iteration on a general tet
-    mesh: 16 B of connectivity per tet, coordinates + two coefficients +
-    the inverse diagonal per node (6 s), and per right-hand side x, r, p read
-    and written once (6 s)."""
+    """Algorithmic (unique) bytes of one fused matrix-free PCG iteration on a
+    general tet mesh: 16 B of connectivity per tet, coordinates + two
+    coefficients + the inverse diagonal per node (6 s), and per right-hand
+    side x, r, p read and written once (6 s)."""
     return 16.0 * E + 6.0 * s * N + 6.0 * s * R * N
+
+
+def pcg_asm_bytes_per_iter(N: int, entries: int, R: int, s: int, nv: int) -> float:
+    """Algorithmic bytes of one fused PCG iteration with an assembled
+    operator: every stored entry read once (nv value sets of s bytes and a
+    2-byte column id), the inverse diagonal (one per value set) and per
+    right-hand side x, r, p read and written once (6 s)."""
+    return entries * (nv * s + 2.0) + nv * s * N + 6.0 * s * R * N
 
 
 def setup_problem(Q, torch, precision: int):
@@ -166,6 +185,7 @@ def run_ours(args):
     mesh.reset_stats()
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     pair_ms, pair_iters, pair_launches = 0.0, 0, 0
+    prior_ms, prior_iters, prior_launches = 0.0, 0, 0
     clk = ClockSampler(local)
     if world > 1:
         torch.distributed.barrier()
@@ -182,7 +202,12 @@ def run_ours(args):
         pair_ms += mesh.pcg_time_ms()
         pair_iters += st["pcg_iters"]
         pair_launches += st["launches"]
+        mesh.reset_stats()
         Q.qpat_prior_solve_dev(mesh, d["kt"], d["mt"], d["prior_rhs"], d["op"], prm)
+        st = mesh.stats()
+        prior_ms += mesh.pcg_time_ms()
+        prior_iters += st["pcg_iters"]
+        prior_launches += st["launches"]
         b.record()
     torch.cuda.synchronize()
     wall = time.perf_counter() - wall0
@@ -210,19 +235,43 @@ def run_ours(args):
     h2d = 8 *((N + N + K * N + K * N + 2 * N) + (N + N + K * N + K * N + K * N) + (N + N + 2 * N))
     d2h = 8 * (K * N + 2 * N + 2 * N)
 
-    # ---- roofline of the dominant kernel (fused PCG of the pair launch)
+    # ---- roofline of the dominant kernel: the fused PCG launch (pair or prior)
+    # with the larger share of the step's device time
     s_bytes = 4 if precision == 1 else 8
     R = 2 * (1 << max(0, math.ceil(math.log2(K))))
-    bpi = pcg_bytes_per_iter(N, d["E"], R, s_bytes)
+    if precision == 1 and args.fp32_operator == 0:
+        bpi_pair = pcg_bytes_per_iter(N, d["E"], R, 4)
+    else:
+        bpi_pair = pcg_asm_bytes_per_iter(N, mesh.entries, R, s_bytes, 1)
+    bpi_prior = pcg_asm_bytes_per_iter(N, mesh.entries, 2, 8, 2)
+    kernels = {
+        "pair": {"kernel": f"k_pcg<{'float' if precision == 1 else 'double'}, {R}, "
+                           f"{0 if (precision == 1 and args.fp32_operator == 0) else 2}> (J s + J^T w, {R} RHS)",
+                 "ms": pair_ms, "iters": pair_iters, "launches": pair_launches, "bytes_per_iter": bpi_pair},
+        "prior": {"kernel": "k_pcg<double, 2, 3> (M_delta^-1, two blocks)",
+                  "ms": prior_ms, "iters": prior_iters, "launches": prior_launches, "bytes_per_iter": bpi_prior},
+    }
+    for v in kernels.values():
+        v["achieved_gbs"] = v["bytes_per_iter"] * v["iters"] / (v["ms"] / 1e3) / 1e9 if v["ms"] > 0 else 0.0
+        v["us_per_iter"] = 1e3 * v["ms"] / max(v["iters"], 1)
+        v["share_of_step"] = v["ms"] / tot_ms if tot_ms > 0 else None
+    dom = max(kernels, key=lambda k: kernels[k]["ms"])
+    bpi = kernels[dom]["bytes_per_iter"]
     peak, peak_kind = load_peaks()
-    achieved = bpi * pair_iters / (pair_ms / 1e3) / 1e9 if pair_ms > 0 else 0.0
+    achieved = kernels[dom]["achieved_gbs"]
+    # DRAM traffic per launch from the committed ncu capture, valid only
+    # while the kernel sources are unchanged since the capture
     traffic = None
-    tf = os.path.join(ROOT, "profiles", "pcg_traffic_c1.json")
+    tf = os.path.join(ROOT, "profiles", "k_pcg_c1_cube64_traffic.json")
     if os.path.exists(tf):
         try:
             tr = json.load(open(tf))
-            if tr.get("precision") == args.precision:
-                traffic = tr.get("dram_bytes_per_launch")
+            ent = tr.get("kernels", {}).get(dom)
+            if ent and tr.get("source_sha1") == kernel_source_sha1():
+                traffic = ent.get("dram_bytes_per_launch")
+                kernels[dom]["dram_bytes_per_iter_ncu"] = ent.get("dram_bytes_per_iter")
+                kernels[dom]["algorithmic_bytes_per_launch"] = bpi * kernels[dom]["iters"] / max(
+                    kernels[dom]["launches"], 1)
         except Exception:
             traffic = None
 
@@ -236,12 +285,12 @@ def run_ours(args):
                    "l2": "flushed between steps (256 MB write outside the per-step events)",
                    "parallelism": "replicas" if world > 1 else "single"},
         "e2e": {"value": e2e_steps / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
-        "roofline": {"bound": "hbm", "kernel": "k_pcg (fused persistent PCG, pair launch)",
+        "roofline": {"bound": "hbm", "kernel": kernels[dom]["kernel"],
                      "achieved": achieved, "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
                      "frac": achieved / peak if peak else None, "traffic": traffic,
-                     "bytes_per_iter": bpi, "pcg_iters_per_step": pair_iters / args.steps,
-                     "pcg_launches_per_step": pair_launches / args.steps,
-                     "pcg_ms_per_step": pair_ms / args.steps},
+                     "bytes_per_iter": bpi,
+                     "note": "64^3 operands are L2-resident (126 MB L2): achieved is algorithmic bytes / time",
+                     "kernels": kernels},
         "clocks": clocks,
         "wall_s": wall,
     }

@@ -136,6 +136,9 @@ int64_t qpat_mesh_num_nodes(qpat_mesh_t mesh);
 int64_t qpat_mesh_num_tets(qpat_mesh_t mesh);
 int64_t qpat_mesh_num_faces(qpat_mesh_t mesh);
 int64_t qpat_mesh_num_patches(qpat_mesh_t mesh);
+/* Stored entries of the assembled operators (node pairs sharing a tet,
+ * the diagonal included), without the sliced-ELLPACK padding. */
+int64_t qpat_mesh_num_entries(qpat_mesh_t mesh);
 
 /* Boundary faces in canonical order (F x 3 caller node ids, ascending). */
 int qpat_mesh_faces(qpat_mesh_t mesh, int32_t* faces);
@@ -184,7 +187,7 @@ int qpat_forward_dev(qpat_mesh_t mesh, const qpat_params* prm, const double* kap
  * counterpart; it computes the same phi = K^-1 f and h = mu * phi as
  * qpat_forward_dev in FP64 (matrix-free operator, Jacobi PCG to a relative
  * residual rtol, at most max_iter iterations), with every scratch vector in
- * one fixed file-scope device array of 4,835,392 doubles (about 39 MB) that
+ * one fixed file-scope device array of 4,835,488 doubles (about 39 MB) that
  * each GPU using the library keeps until the process exits.
  *  - Limit: N x R <= 524,288, R = K rounded up to 1, 2, 4, 8 or 16;
  *    larger problems return QPAT_EINVAL without touching the GPU.

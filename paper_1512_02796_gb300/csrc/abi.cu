@@ -220,7 +220,7 @@ int solve(qpat_mesh_s* M, const OpState& st, const SolveOpts& so_in, int R, cons
     w.p0 = M->ws.get_bytes(nm("p0"), n * esz, s, &e);
     w.p1 = M->ws.get_bytes(nm("p1"), n * esz, s, &e);
     w.q = M->ws.get_bytes(nm("q"), n * esz, s, &e);
-    w.partials = M->ws.get<double>("pcg.partials", size_t(2) * pcg_max_grid() * 3 * 16, s, &e);
+    w.partials = M->ws.get<double>("pcg.partials", pcg_partials_doubles(), s, &e);
     w.bar = M->ws.get<unsigned>("pcg.bar", 2, s, &e);
     w.status = M->ws.get<int>("pcg.status", 1, s, &e);
     w.iters = M->ws.get<int>("pcg.iters", 1, s, &e);
@@ -346,11 +346,12 @@ void qpat_default_params(qpat_params* p) {
     p->patch_nodes = 0;
 }
 
-int qpat_mesh_ex(const double* xyz, int64_t N, const int32_t* tets, int64_t E, int patch_nodes, qpat_mesh_t* out) {
+static int mesh_create(const double* xyz, int64_t N, const int32_t* tets, int64_t E, int patch_nodes,
+                       int patch_multiple, qpat_mesh_t* out) {
     if (!out) return fail(QPAT_EINVAL, "qpat_mesh: out is NULL");
     *out = nullptr;
     auto* M = new qpat_mesh_s();
-    std::string msg = build_host_mesh(xyz, N, tets, E, patch_nodes, M->h);
+    std::string msg = build_host_mesh(xyz, N, tets, E, patch_nodes, patch_multiple, M->h);
     if (!msg.empty()) {
         delete M;
         return fail(QPAT_EINVAL, msg);
@@ -368,7 +369,7 @@ int qpat_mesh_host_info(const double* xyz, int64_t N, const int32_t* tets, int64
                         int64_t* info8, int32_t* faces, int32_t* perm) {
     if (!info8) return fail(QPAT_EINVAL, "qpat_mesh_host_info: info is NULL");
     HostMesh h;
-    std::string msg = build_host_mesh(xyz, N, tets, E, patch_nodes, h);
+    std::string msg = build_host_mesh(xyz, N, tets, E, patch_nodes, 0, h);
     if (!msg.empty()) return fail(QPAT_EINVAL, msg);
     // self-check of the patch structure: owned ranges tile [0, N); every tet
     // that touches an owned node is listed; local ids map back to the tets
@@ -407,11 +408,11 @@ int qpat_mesh_host_info(const double* xyz, int64_t N, const int32_t* tets, int64
     if (faces) std::memcpy(faces, h.faces_caller.data(), sizeof(int32_t) * 3 * h.F);
     if (perm) std::memcpy(perm, h.perm.data(), sizeof(int32_t) * h.N);
     // every tet must be listed once per distinct patch owning one of its
-    // vertices (node g belongs to patch g / patch_nodes)
+    // vertices (node g belongs to the patch of its 32-node slice)
     int64_t expect = 0;
     for (int64_t e = 0; e < h.E; ++e) {
         int pid[4];
-        for (int a = 0; a < 4; ++a) pid[a] = h.tets[4 * e + a] / h.patch_nodes;
+        for (int a = 0; a < 4; ++a) pid[a] = h.patch_of_slice[h.tets[4 * e + a] >> 5];
         std::sort(pid, pid + 4);
         expect += 1 + (pid[1] != pid[0]) + (pid[2] != pid[1]) + (pid[3] != pid[2]);
     }
@@ -425,7 +426,7 @@ int qpat_mesh_host_info(const double* xyz, int64_t N, const int32_t* tets, int64
         auto& ref = adj[g];
         std::sort(ref.begin(), ref.end());
         ref.erase(std::unique(ref.begin(), ref.end()), ref.end());
-        const int p = int(g / h.patch_nodes), nb = h.node_ptr[p];
+        const int p = h.patch_of_slice[g >> 5], nb = h.node_ptr[p];
         std::vector<int> got;
         for (int k = 0; k < h.sell_len[g]; ++k)
             got.push_back(h.nodes[nb + h.sell_col[(h.sell_ptr[g >> 5] + k) * 32 + (g & 31)]]);
@@ -438,7 +439,20 @@ int qpat_mesh_host_info(const double* xyz, int64_t N, const int32_t* tets, int64
 }
 
 int qpat_mesh(const double* xyz, int64_t N, const int32_t* tets, int64_t E, qpat_mesh_t* out) {
-    return qpat_mesh_ex(xyz, N, tets, E, 512, out);
+    // default patching: at most 1024 owned nodes per patch and a patch count
+    // that is a multiple of 4 CTAs per SM, so that every resident CTA of the
+    // persistent solver owns the same number of patches
+    int dev = 0, nsm = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) !=
+                                                   cudaSuccess || nsm < 1) {
+        (void)cudaGetLastError();
+        nsm = 152;
+    }
+    return mesh_create(xyz, N, tets, E, 1024, 4 * nsm, out);
+}
+
+int qpat_mesh_ex(const double* xyz, int64_t N, const int32_t* tets, int64_t E, int patch_nodes, qpat_mesh_t* out) {
+    return mesh_create(xyz, N, tets, E, patch_nodes, 0, out);
 }
 
 void qpat_mesh_free(qpat_mesh_t M) {
@@ -461,6 +475,13 @@ int64_t qpat_mesh_num_nodes(qpat_mesh_t M) { return M ? M->h.N : -1; }
 int64_t qpat_mesh_num_tets(qpat_mesh_t M) { return M ? M->h.E : -1; }
 int64_t qpat_mesh_num_faces(qpat_mesh_t M) { return M ? M->h.F : -1; }
 int64_t qpat_mesh_num_patches(qpat_mesh_t M) { return M ? M->h.P : -1; }
+
+int64_t qpat_mesh_num_entries(qpat_mesh_t M) {
+    if (!M) return -1;
+    int64_t n = 0;
+    for (uint8_t l : M->h.sell_len) n += l;
+    return n;
+}
 
 int qpat_mesh_faces(qpat_mesh_t M, int32_t* faces) {
     if (!M || !faces) return fail(QPAT_EINVAL, "qpat_mesh_faces: NULL argument");

@@ -9,10 +9,12 @@ namespace {
 constexpr int kRedBlocks = 608;  // 4 x 152 SMs
 
 // ---------------------------------------------------------------- operator apply
-// One CTA per patch: stage, element loop, write the owned rows.
+// One CTA per patch: stage, element loop, write the owned rows.  Columns
+// [c0, c0 + R) of N x ldx node-major x and y (large RHS counts are applied in
+// column chunks so that the staging fits in shared memory).
 template <typename T, int R, int OP>
 __global__ void __launch_bounds__(kThreads) k_apply(MeshDev m, OpParams<T> op, T sign, const T* __restrict__ x,
-                                                    T* __restrict__ y) {
+                                                    T* __restrict__ y, int ldx, int c0) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     PatchSmem<T, R> s;
     s.carve(reinterpret_cast<T*>(smem_raw), m.max_touched, m.max_own);
@@ -22,7 +24,7 @@ __global__ void __launch_bounds__(kThreads) k_apply(MeshDev m, OpParams<T> op, T
     stage_static<T, R>(m, nb, nt, s, op);
     for (int i = threadIdx.x; i < nt * R; i += blockDim.x) {
         const int g = __ldg(m.nodes + nb + i / R);
-        s.xin[i] = __ldg(x + size_t(g) * R + (i % R));
+        s.xin[i] = __ldg(x + size_t(g) * ldx + c0 + (i % R));
     }
     for (int i = threadIdx.x; i < nown * R; i += blockDim.x) s.yout[i] = T(0);
     __syncthreads();
@@ -31,18 +33,33 @@ __global__ void __launch_bounds__(kThreads) k_apply(MeshDev m, OpParams<T> op, T
     for (int i = threadIdx.x; i < nown * R; i += blockDim.x) {
         T v = s.yout[i];
         if (OP == OP_PRIOR) v += op.delta * s.xin[i];
-        y[size_t(ob) * R + i] = sign * v;
+        y[size_t(ob + i / R) * ldx + c0 + (i % R)] = sign * v;
     }
 }
 
+constexpr size_t kSmemBudget = 200 * 1024;
+
 template <typename T, int R, int OP>
-cudaError_t apply_t(const MeshDev& m, const OpParams<T>& op, T sign, const T* x, T* y, cudaStream_t st) {
+cudaError_t apply_t(const MeshDev& m, const OpParams<T>& op, T sign, const T* x, T* y, int ldx, int c0,
+                    cudaStream_t st) {
     const size_t smem = PatchSmem<T, R>::bytes(m.max_touched, m.max_own);
     auto kern = k_apply<T, R, OP>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
     if (e != cudaSuccess) return e;
-    kern<<<m.P, kThreads, smem, st>>>(m, op, sign, x, y);
+    kern<<<m.P, kThreads, smem, st>>>(m, op, sign, x, y, ldx, c0);
     return cudaGetLastError();
+}
+
+// largest chunk of {16, 8, 4, 2, 1} dividing R whose staging fits the budget
+template <typename T>
+int apply_chunk(const MeshDev& m, int R, size_t per_node_extra) {
+    for (int c : {16, 8, 4, 2, 1}) {
+        if (c > R || R % c) continue;
+        const size_t bytes = sizeof(T) * (size_t(m.max_touched) * (per_node_extra + size_t(c)) +
+                                          size_t(m.max_own) * c);
+        if (bytes <= kSmemBudget) return c;
+    }
+    return 1;
 }
 
 // ---------------------------------------------------------------- diagonals (FP64)
@@ -279,11 +296,13 @@ cudaError_t apply_csr_t(const MeshDev& m, const T* v0, const T* v1, const T* x, 
 }
 
 // ---------------------------------------------------------------- J^T pieces
-// y[g][0] = -sum_k sum_{T ni g} (|T|/4) grad(phi_k) . grad(z_k)       ( = sum_k G1^T z_k )
-// y[g][1] = -sum_k (M(phi_k) z_k)_g                                    ( = sum_k G2 z_k )
+// y[g][0] (+)= -sum_k sum_{T ni g} (|T|/4) grad(phi_k) . grad(z_k)   ( = sum_k G1^T z_k )
+// y[g][1] (+)= -sum_k (M(phi_k) z_k)_g                               ( = sum_k G2 z_k )
+// over the columns [c0, c0 + K) of N x ldk node-major phi and z.
 template <typename T, int K>
 __global__ void __launch_bounds__(kThreads) k_vjp_accum(MeshDev m, const T* __restrict__ phi,
-                                                        const T* __restrict__ z, T* __restrict__ y) {
+                                                        const T* __restrict__ z, T* __restrict__ y, int ldk,
+                                                        int c0, int accumulate) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int MT = m.max_touched;
     T* px = reinterpret_cast<T*>(smem_raw);
@@ -304,8 +323,8 @@ __global__ void __launch_bounds__(kThreads) k_vjp_accum(MeshDev m, const T* __re
     }
     for (int i = threadIdx.x; i < nt * K; i += blockDim.x) {
         const int g = m.nodes[nb + i / K];
-        sphi[i] = phi[size_t(g) * K + i % K];
-        sz[i] = z[size_t(g) * K + i % K];
+        sphi[i] = phi[size_t(g) * ldk + c0 + i % K];
+        sz[i] = z[size_t(g) * ldk + c0 + i % K];
     }
     for (int i = threadIdx.x; i < 2 * nown; i += blockDim.x) sy[i] = T(0);
     __syncthreads();
@@ -340,16 +359,19 @@ __global__ void __launch_bounds__(kThreads) k_vjp_accum(MeshDev m, const T* __re
             }
     }
     __syncthreads();
-    for (int i = threadIdx.x; i < 2 * nown; i += blockDim.x) y[size_t(ob) * 2 + i] = sy[i];
+    for (int i = threadIdx.x; i < 2 * nown; i += blockDim.x) {
+        T* dst = y + size_t(ob) * 2 + i;
+        *dst = accumulate ? *dst + sy[i] : sy[i];
+    }
 }
 
 template <typename T, int K>
-cudaError_t vjp_t(const MeshDev& m, const T* phi, const T* z, T* y, cudaStream_t st) {
+cudaError_t vjp_t(const MeshDev& m, const T* phi, const T* z, T* y, int ldk, int c0, int acc, cudaStream_t st) {
     const size_t smem = sizeof(T) * (size_t(m.max_touched) * (3 + 2 * K) + size_t(m.max_own) * 2);
     auto kern = k_vjp_accum<T, K>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
     if (e != cudaSuccess) return e;
-    kern<<<m.P, kThreads, smem, st>>>(m, phi, z, y);
+    kern<<<m.P, kThreads, smem, st>>>(m, phi, z, y, ldk, c0, acc);
     return cudaGetLastError();
 }
 
@@ -451,21 +473,27 @@ template <typename T>
 cudaError_t launch_apply_K(const MeshDev& m, int R, const T* c1, const T* c2, int robin, T sign, const T* x, T* y,
                            cudaStream_t s) {
     OpParams<T> op{c1, c2, T(0), T(0), T(0), robin};
-    switch (R) {
-        case 1: return apply_t<T, 1, OP_K>(m, op, sign, x, y, s);
-        case 2: return apply_t<T, 2, OP_K>(m, op, sign, x, y, s);
-        case 4: return apply_t<T, 4, OP_K>(m, op, sign, x, y, s);
-        case 8: return apply_t<T, 8, OP_K>(m, op, sign, x, y, s);
-        case 16: return apply_t<T, 16, OP_K>(m, op, sign, x, y, s);
-        default: return cudaErrorInvalidValue;
+    if (R != 1 && R != 2 && R != 4 && R != 8 && R != 16) return cudaErrorInvalidValue;
+    const int C = apply_chunk<T>(m, R, 5);
+    for (int c0 = 0; c0 < R; c0 += C) {
+        cudaError_t e = cudaErrorInvalidValue;
+        switch (C) {
+            case 1: e = apply_t<T, 1, OP_K>(m, op, sign, x, y, R, c0, s); break;
+            case 2: e = apply_t<T, 2, OP_K>(m, op, sign, x, y, R, c0, s); break;
+            case 4: e = apply_t<T, 4, OP_K>(m, op, sign, x, y, R, c0, s); break;
+            case 8: e = apply_t<T, 8, OP_K>(m, op, sign, x, y, R, c0, s); break;
+            case 16: e = apply_t<T, 16, OP_K>(m, op, sign, x, y, R, c0, s); break;
+        }
+        if (e != cudaSuccess) return e;
     }
+    return cudaSuccess;
 }
 
 template <typename T>
 cudaError_t launch_apply_prior(const MeshDev& m, const T* u1, const T* u2, T inv_T2, T scale1, T delta, const T* x,
                                T* y, cudaStream_t s) {
     OpParams<T> op{u1, u2, inv_T2, scale1, delta, 0};
-    return apply_t<T, 2, OP_PRIOR>(m, op, T(1), x, y, s);
+    return apply_t<T, 2, OP_PRIOR>(m, op, T(1), x, y, 2, 0, s);
 }
 
 cudaError_t launch_invdiag_K(const MeshDev& m, const double* kappa, const double* mu, double* inv64, float* inv32,
@@ -541,14 +569,28 @@ template cudaError_t launch_apply_csr<float>(const MeshDev&, int, int, const flo
 
 template <typename T>
 cudaError_t launch_vjp_accum(const MeshDev& m, int K, const T* phi, const T* z, T* y, cudaStream_t s) {
-    switch (K) {
-        case 1: return vjp_t<T, 1>(m, phi, z, y, s);
-        case 2: return vjp_t<T, 2>(m, phi, z, y, s);
-        case 4: return vjp_t<T, 4>(m, phi, z, y, s);
-        case 8: return vjp_t<T, 8>(m, phi, z, y, s);
-        case 16: return vjp_t<T, 16>(m, phi, z, y, s);
-        default: return cudaErrorInvalidValue;
+    if (K != 1 && K != 2 && K != 4 && K != 8 && K != 16) return cudaErrorInvalidValue;
+    int C = 1;
+    for (int c : {16, 8, 4, 2, 1}) {
+        if (c > K || K % c) continue;
+        if (sizeof(T) * (size_t(m.max_touched) * (3 + 2 * c) + size_t(m.max_own) * 2) <= kSmemBudget) {
+            C = c;
+            break;
+        }
     }
+    for (int c0 = 0; c0 < K; c0 += C) {
+        const int acc = c0 > 0;
+        cudaError_t e = cudaErrorInvalidValue;
+        switch (C) {
+            case 1: e = vjp_t<T, 1>(m, phi, z, y, K, c0, acc, s); break;
+            case 2: e = vjp_t<T, 2>(m, phi, z, y, K, c0, acc, s); break;
+            case 4: e = vjp_t<T, 4>(m, phi, z, y, K, c0, acc, s); break;
+            case 8: e = vjp_t<T, 8>(m, phi, z, y, K, c0, acc, s); break;
+            case 16: e = vjp_t<T, 16>(m, phi, z, y, K, c0, acc, s); break;
+        }
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
 }
 
 cudaError_t launch_load(const MeshDev& m, int K, int R, const double* flux, double* f, cudaStream_t s) {

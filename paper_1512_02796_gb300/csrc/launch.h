@@ -81,6 +81,7 @@ template <typename T>
 cudaError_t launch_pcg(const MeshDev& m, int OP, int R, const OpParams<T>& op, const T* invdiag,
                        const PcgWork& w, double rtol, int maxit, cudaStream_t s, int* grid_used);
 
-int pcg_max_grid();  // upper bound of the cooperative grid (for sizing partials)
+int pcg_max_grid();            // upper bound of the cooperative grid
+size_t pcg_partials_doubles();  // size of PcgWork::partials (per-CTA partials + totals)
 
 }  // namespace qpat

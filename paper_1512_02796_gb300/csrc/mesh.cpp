@@ -33,7 +33,7 @@ struct Face {
 }  // namespace
 
 std::string build_host_mesh(const double* xyz, int64_t N, const int32_t* tets,
-                            int64_t E, int patch_nodes, HostMesh& m) {
+                            int64_t E, int patch_nodes, int patch_multiple, HostMesh& m) {
     if (N <= 0 || E <= 0 || xyz == nullptr || tets == nullptr)
         return "qpat_mesh: empty mesh or NULL array";
     if (N >= (int64_t(1) << 31) || E >= (int64_t(1) << 29))
@@ -162,11 +162,21 @@ std::string build_host_mesh(const double* xyz, int64_t N, const int32_t* tets,
             for (int k = 0; k < 3; ++k) nf[fill[m.faces_lib[3 * f + k]]++] = int32_t(f);
     }
 
-    // ---- patches
-    const int P = int((N + patch_nodes - 1) / patch_nodes);
+    // ---- patches: P balanced ranges of whole 32-node slices.  With
+    // patch_multiple > 0 the count is rounded up to a multiple of it (the
+    // resident CTA count of the persistent solver) so that every CTA owns the
+    // same number of patches and the patches differ by at most one slice.
+    const int64_t S = (N + 31) / 32;
+    int64_t Pl = (N + patch_nodes - 1) / patch_nodes;
+    if (patch_multiple > 0) Pl = ((Pl + patch_multiple - 1) / patch_multiple) * patch_multiple;
+    Pl = std::max<int64_t>(1, std::min(Pl, S));
+    const int P = int(Pl);
     m.P = P;
     m.own_begin.resize(P + 1);
-    for (int p = 0; p <= P; ++p) m.own_begin[p] = int32_t(std::min<int64_t>(int64_t(p) * patch_nodes, N));
+    m.patch_of_slice.resize(S);
+    for (int p = 0; p <= P; ++p) m.own_begin[p] = int32_t(std::min<int64_t>(32 * ((S * p) / P), N));
+    for (int p = 0; p < P; ++p)
+        for (int64_t s = (S * p) / P; s < (S * (p + 1)) / P; ++s) m.patch_of_slice[s] = p;
     m.node_ptr.assign(1, 0);
     m.tet_ptr.assign(1, 0);
     m.face_ptr.assign(1, 0);
@@ -259,7 +269,7 @@ std::string build_host_mesh(const double* xyz, int64_t N, const int32_t* tets,
             const int64_t g = 32 * s + lane;
             uint16_t self = 0;
             if (g < N) {
-                const int p = int(g / patch_nodes);
+                const int p = m.patch_of_slice[g >> 5];
                 self = uint16_t(g - m.own_begin[p]);
                 m.sell_len[g] = uint8_t(rows[g].size());
                 m.sell_diag[g] = -1;

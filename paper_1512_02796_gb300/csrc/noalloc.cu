@@ -22,7 +22,7 @@ constexpr int64_t kNoallocMaxNR = int64_t(1) << 19;
 // Scratch layout in doubles: kappa, mu, inverse diagonal (N each, N <= max),
 // then six N x R vectors (f, x, r, p0, p1, q), two reduction buffers and a
 // small control block (barrier, status, iteration count, statistics).
-constexpr int64_t kPartials = int64_t(2) * 1216 * 48;
+constexpr int64_t kPartials = int64_t(2) * 1216 * 48 + 2 * 48;
 constexpr int64_t kCtl = 64;
 constexpr int64_t kNoallocDoubles = 3 * kNoallocMaxNR + 6 * kNoallocMaxNR + kPartials + kCtl;
 

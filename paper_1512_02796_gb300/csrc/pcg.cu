@@ -7,16 +7,20 @@
 // node patches and, per iteration,
 //   phase A: forms p = D^-1 r + beta p_old on its touched nodes in shared
 //            memory (the z = D^-1 r vector is never stored), writes p on its
-//            owned nodes, applies the matrix-free element operator and keeps
-//            q = A p on its owned nodes, accumulating p.q;
+//            owned nodes, applies the operator and keeps q = A p on its
+//            owned nodes, accumulating p.q;
 //   phase B: x += alpha p, r -= alpha q on its owned nodes, accumulating
 //            r.D^-1 r and r.r.
-// Each phase ends with a grid-wide deterministic reduction (per-CTA
-// partials, summed in the same order by every CTA, so every CTA takes the
-// same decisions) behind a bounded grid barrier.  R right-hand sides share
-// one launch with their own alpha and beta (block form of the stacked
-// illuminations of Sec. 4).  Scalars are accumulated in FP64 for either T.
+// Each phase ends with a grid-wide reduction behind a bounded grid barrier:
+// every CTA writes its partial sums, the last CTA to arrive adds all of them
+// in a fixed order, publishes the totals and releases the others, so every
+// CTA takes the same decisions from bit-identical scalars.  R right-hand
+// sides share one launch with their own alpha and beta (block form of the
+// stacked illuminations of Sec. 4); node vectors are N x R node-major and
+// are moved as 16-byte vectors (4 floats or 2 doubles of consecutive RHS)
+// wherever R allows.  Scalars are accumulated in FP64 for either T.
 #include <cuda/atomic>
+#include <cstring>
 
 #include "launch.h"
 
@@ -46,154 +50,204 @@ struct PcgArgs {
 };
 
 constexpr int kMaxGrid = 152 * 8;
+constexpr int kMaxNS = 48;  // largest reduction: 3 quantities x 16 RHS
 
-// Bounded grid barrier: arrive on a counter, the last arrival bumps the
-// generation; the others spin (with a limit) until it changes.  On timeout
-// the CTA records QPAT_ETIMEOUT and every CTA leaves at its next check.
-__device__ __forceinline__ bool grid_sync(unsigned* bar, int* status, long long limit) {
-    __shared__ int s_ok;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        cuda::atomic_ref<unsigned, cuda::thread_scope_device> cnt(bar[0]);
-        cuda::atomic_ref<unsigned, cuda::thread_scope_device> gen(bar[1]);
-        const unsigned g = gen.load(cuda::memory_order_acquire);
-        __threadfence();
-        const unsigned old = cnt.fetch_add(1u, cuda::memory_order_acq_rel);
-        int ok = 1;
-        if (old == gridDim.x - 1) {
-            cnt.store(0u, cuda::memory_order_relaxed);
-            gen.fetch_add(1u, cuda::memory_order_release);
-        } else {
-            long long spins = 0;
-            while (gen.load(cuda::memory_order_acquire) == g) {
-                if (++spins > limit) {
-                    atomicExch(status, QPAT_ETIMEOUT);
-                    ok = 0;
-                    break;
-                }
-                __nanosleep(100);
-            }
-        }
-        __threadfence();
-        cuda::atomic_ref<int, cuda::thread_scope_device> st(*status);
-        if (st.load(cuda::memory_order_relaxed) == QPAT_ETIMEOUT) ok = 0;
-        s_ok = ok;
-    }
-    __syncthreads();
-    return s_ok != 0;
+// ---------------------------------------------------------------- vectors
+template <typename T, int VW>
+struct VecT;
+template <>
+struct VecT<float, 4> {
+    using type = float4;
+};
+template <>
+struct VecT<double, 2> {
+    using type = double2;
+};
+template <typename T>
+struct VecT<T, 1> {
+    using type = T;
+};
+
+template <typename T, int R, bool kVec>
+__host__ __device__ constexpr int vec_width() {
+    if (!kVec) return 1;
+    if (sizeof(T) == 4) return R % 4 == 0 ? 4 : 1;
+    return R % 2 == 0 ? 2 : 1;
 }
 
-// Grid-wide sum of NQ*R values.  acc[q] belongs to RHS (threadIdx.x % R).
-// Result in out[q * R + r] (shared memory) in every CTA.
-template <int R, int NQ>
-__device__ __forceinline__ bool grid_sum(double (&acc)[NQ], double* scratch, double* partials, int& red_id,
-                                         unsigned* bar, int* status, long long limit, double* out) {
+template <typename T, int VW>
+__device__ __forceinline__ void vld_cg(const T* p, T (&v)[VW]) {
+    if constexpr (VW == 1) {
+        v[0] = __ldcg(p);
+    } else {
+        const auto t = __ldcg(reinterpret_cast<const typename VecT<T, VW>::type*>(p));
+        memcpy(v, &t, sizeof(t));
+    }
+}
+template <typename T, int VW>
+__device__ __forceinline__ void vld(const T* p, T (&v)[VW]) {
+    if constexpr (VW == 1) {
+        v[0] = *p;
+    } else {
+        const auto t = *reinterpret_cast<const typename VecT<T, VW>::type*>(p);
+        memcpy(v, &t, sizeof(t));
+    }
+}
+template <typename T, int VW>
+__device__ __forceinline__ void vst(T* p, const T (&v)[VW]) {
+    if constexpr (VW == 1) {
+        *p = v[0];
+    } else {
+        typename VecT<T, VW>::type t;
+        memcpy(&t, v, sizeof(t));
+        *reinterpret_cast<typename VecT<T, VW>::type*>(p) = t;
+    }
+}
+
+// inverse diagonal of the VW right-hand sides [r0, r0 + VW) of node g
+template <typename T, int VW, int OP>
+__device__ __forceinline__ void dinv_vec(const T* invdiag, int g, int r0, T (&d)[VW]) {
+    if constexpr (OP == OP_PRIOR || OP == OP_CSR2) {
+        if constexpr (VW == 1) {
+            d[0] = __ldg(invdiag + 2 * g + r0);
+        } else {
+            const auto t = __ldg(reinterpret_cast<const typename VecT<T, VW>::type*>(invdiag + 2 * g + r0));
+            memcpy(d, &t, sizeof(t));
+        }
+    } else {
+        const T v = __ldg(invdiag + g);
+#pragma unroll
+        for (int c = 0; c < VW; ++c) d[c] = v;
+    }
+}
+
+// ---------------------------------------------------------------- grid reduction
+// Sum over the grid of NQ x R values; thread t holds acc[q][c] for RHS
+// (t % NP) * VW + c.  Totals land in out[q * R + r] (shared) in every CTA.
+template <int NQ, int VW, int NP>
+__device__ __forceinline__ bool grid_reduce(double (&acc)[NQ][VW], double* scratch, double* partials, int& red_id,
+                                            unsigned* bar, int* status, long long limit, double* out) {
+    constexpr int R = VW * NP, NS = NQ * R;
+    __shared__ int s_last;
+    __shared__ int s_ok;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
 #pragma unroll
     for (int q = 0; q < NQ; ++q)
 #pragma unroll
-        for (int o = 16; o >= R; o >>= 1) acc[q] += __shfl_down_sync(0xffffffffu, acc[q], o);
-    if (lane < R)
+        for (int c = 0; c < VW; ++c)
 #pragma unroll
-        for (int q = 0; q < NQ; ++q) scratch[(warp * NQ + q) * R + lane] = acc[q];
+            for (int o = 16; o >= NP; o >>= 1) acc[q][c] += __shfl_down_sync(0xffffffffu, acc[q][c], o);
+    if (lane < NP)
+#pragma unroll
+        for (int q = 0; q < NQ; ++q)
+#pragma unroll
+            for (int c = 0; c < VW; ++c) scratch[warp * NS + q * R + lane * VW + c] = acc[q][c];
     __syncthreads();
-    // two buffers of fixed stride (the largest reduction, 3 x 16 values):
-    // a slow CTA still reading reduction k never sees reduction k+1's writes
-    double* part = partials + size_t(red_id & 1) * kMaxGrid * 48;
-    if (threadIdx.x < NQ * R) {
-        const int q = threadIdx.x / R, r = threadIdx.x % R;
-        double a = 0.0;
-        for (int w = 0; w < nw; ++w) a += scratch[(w * NQ + q) * R + r];
-        part[size_t(blockIdx.x) * NQ * R + threadIdx.x] = a;
-    }
+    double* part = partials + size_t(red_id & 1) * kMaxGrid * kMaxNS;
+    double* res = partials + size_t(2) * kMaxGrid * kMaxNS + (red_id & 1) * kMaxNS;
     ++red_id;
-    if (!grid_sync(bar, status, limit)) return false;
-    // every CTA sums the partials in the same order
-    for (int s = warp; s < NQ * R; s += nw) {
-        double a = 0.0;
-        for (int j = lane; j < gridDim.x; j += 32) a += __ldcg(part + size_t(j) * NQ * R + s);
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
-        if (lane == 0) out[s] = a;
-    }
-    __syncthreads();
-    return true;
-}
-
-// Grid-wide sum of NS values held (all of them) by every thread.
-template <int NS>
-__device__ __forceinline__ bool grid_sum_full(double (&acc)[NS], double* scratch, double* partials, int& red_id,
-                                              unsigned* bar, int* status, long long limit, double* out) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-#pragma unroll
-    for (int q = 0; q < NS; ++q)
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) acc[q] += __shfl_down_sync(0xffffffffu, acc[q], o);
-    if (lane == 0)
-#pragma unroll
-        for (int q = 0; q < NS; ++q) scratch[warp * NS + q] = acc[q];
-    __syncthreads();
-    double* part = partials + size_t(red_id & 1) * kMaxGrid * 48;
     if (threadIdx.x < NS) {
         double a = 0.0;
         for (int w = 0; w < nw; ++w) a += scratch[w * NS + threadIdx.x];
         part[size_t(blockIdx.x) * NS + threadIdx.x] = a;
     }
-    ++red_id;
-    if (!grid_sync(bar, status, limit)) return false;
-    for (int s = warp; s < NS; s += nw) {
-        double a = 0.0;
-        for (int j = lane; j < gridDim.x; j += 32) a += __ldcg(part + size_t(j) * NS + s);
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
-        if (lane == 0) out[s] = a;
+    __syncthreads();
+    cuda::atomic_ref<unsigned, cuda::thread_scope_device> cnt(bar[0]);
+    cuda::atomic_ref<unsigned, cuda::thread_scope_device> gen(bar[1]);
+    unsigned g = 0;
+    if (threadIdx.x == 0) {
+        g = gen.load(cuda::memory_order_acquire);
+        __threadfence();
+        const unsigned old = cnt.fetch_add(1u, cuda::memory_order_acq_rel);
+        s_last = old == gridDim.x - 1;
+        s_ok = 1;
     }
+    __syncthreads();
+    if (s_last) {
+        // the last CTA adds the partials of every CTA in a fixed order
+        __threadfence();
+        for (int s = warp; s < NS; s += nw) {
+            double a = 0.0;
+            for (int j = lane; j < gridDim.x; j += 32) a += __ldcg(part + size_t(j) * NS + s);
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+            if (lane == 0) res[s] = a;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            __threadfence();
+            cnt.store(0u, cuda::memory_order_relaxed);
+            gen.fetch_add(1u, cuda::memory_order_release);
+        }
+    } else if (threadIdx.x == 0) {
+        long long spins = 0;
+        while (gen.load(cuda::memory_order_acquire) == g) {
+            if (++spins > limit) {
+                atomicExch(status, QPAT_ETIMEOUT);
+                s_ok = 0;
+                break;
+            }
+            __nanosleep(32);
+        }
+        __threadfence();
+    }
+    __syncthreads();
+    if (!s_ok) return false;
+    if (threadIdx.x < NS) out[threadIdx.x] = __ldcg(res + threadIdx.x);
     __syncthreads();
     return true;
 }
 
-template <typename T, int R, int OP>
-__device__ __forceinline__ T dinv(const T* invdiag, int g, int r) {
-    return (OP == OP_PRIOR || OP == OP_CSR2) ? __ldg(invdiag + 2 * g + r) : __ldg(invdiag + g);
-}
-
+// ---------------------------------------------------------------- the solver
 template <typename T, int R, int OP>
 __global__ void __launch_bounds__(kThreads) k_pcg(PcgArgs<T> a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     constexpr bool kCsr = (OP == OP_CSR1 || OP == OP_CSR2);
+    constexpr int VW = vec_width<T, R, kCsr>();
+    constexpr int NP = R / VW;
     PatchSmem<T, R> s;
     if constexpr (kCsr) {
         s.xin = reinterpret_cast<T*>(smem_raw);  // assembled operators stage p only
     } else {
         s.carve(reinterpret_cast<T*>(smem_raw), a.m.max_touched, a.m.max_own);
     }
-    __shared__ double scratch[(kThreads / 32) * 3 * 16];
-    __shared__ double red[3 * R];
+    __shared__ double scratch[(kThreads / 32) * kMaxNS];
+    __shared__ double red[kMaxNS];
     __shared__ double bb[R], rz[R], rz_old[R], rr[R], alpha[R], beta[R];
     __shared__ int s_flag;
 
     const MeshDev& m = a.m;
     const int P = m.P;
-    const int myr = threadIdx.x % R;
+    const int part = threadIdx.x % NP;  // this thread's RHS block [part*VW, part*VW + VW)
+    const int r0 = part * VW;
     int red_id = 0;
 
     // ---- initial residual r = b (x0 = 0)
     {
-        double acc[3] = {0.0, 0.0, 0.0};
+        double acc[3][VW];
+#pragma unroll
+        for (int c = 0; c < VW; ++c) acc[0][c] = acc[1][c] = acc[2][c] = 0.0;
         for (int p = blockIdx.x; p < P; p += gridDim.x) {
-            const int ob = __ldg(m.own_begin + p), oe = __ldg(m.own_begin + p + 1);
-            for (int i = threadIdx.x; i < (oe - ob) * R; i += blockDim.x) {
-                const size_t e = size_t(ob) * R + i;
-                const T bv = a.b[e];
-                a.x[e] = T(0);
-                a.r[e] = bv;
-                const T z = dinv<T, R, OP>(a.invdiag, ob + i / R, myr) * bv;
-                acc[0] += double(bv) * double(bv);
-                acc[1] += double(bv) * double(z);
+            const int ob = __ldg(m.own_begin + p), nown = __ldg(m.own_begin + p + 1) - ob;
+            for (int i = threadIdx.x; i < nown * NP; i += blockDim.x) {
+                const int g = ob + i / NP;
+                const size_t e = size_t(g) * R + r0;
+                T bv[VW], d[VW], zero[VW];
+                vld(a.b + e, bv);
+                dinv_vec<T, VW, OP>(a.invdiag, g, r0, d);
+#pragma unroll
+                for (int c = 0; c < VW; ++c) {
+                    zero[c] = T(0);
+                    acc[0][c] += double(bv[c]) * double(bv[c]);
+                    acc[1][c] += double(bv[c]) * double(d[c] * bv[c]);
+                }
+                vst(a.x + e, zero);
+                vst(a.r + e, bv);
             }
         }
-        acc[2] = acc[0];
-        if (!grid_sum<R, 3>(acc, scratch, a.partials, red_id, a.bar, a.status, a.spin_limit, red)) return;
+#pragma unroll
+        for (int c = 0; c < VW; ++c) acc[2][c] = acc[0][c];
+        if (!grid_reduce<3, VW, NP>(acc, scratch, a.partials, red_id, a.bar, a.status, a.spin_limit, red)) return;
         if (threadIdx.x < R) {
             bb[threadIdx.x] = red[threadIdx.x];
             rz[threadIdx.x] = red[R + threadIdx.x];
@@ -226,49 +280,75 @@ __global__ void __launch_bounds__(kThreads) k_pcg(PcgArgs<T> a) {
 
         T* pc = (it & 1) ? a.p1 : a.p0;
         const T* pp = (it & 1) ? a.p0 : a.p1;
+        T bt[VW];
+#pragma unroll
+        for (int c = 0; c < VW; ++c) bt[c] = T(beta[r0 + c]);
 
         // ---- phase A: p = D^-1 r + beta p_old on touched nodes, q = A p on owned nodes
-        double accA[1] = {0.0};
-        double accF[R];
+        double accA[1][VW];
 #pragma unroll
-        for (int r = 0; r < R; ++r) accF[r] = 0.0;
+        for (int c = 0; c < VW; ++c) accA[0][c] = 0.0;
         for (int p = blockIdx.x; p < P; p += gridDim.x) {
             const int nb = __ldg(m.node_ptr + p), nt = __ldg(m.node_ptr + p + 1) - nb;
             const int ob = __ldg(m.own_begin + p), nown = __ldg(m.own_begin + p + 1) - ob;
+            if constexpr (!kCsr) stage_static<T, R>(m, nb, nt, s, a.op);
+            for (int i = threadIdx.x; i < nt * NP; i += blockDim.x) {
+                const int li = i / NP;
+                const int g = __ldg(m.nodes + nb + li);
+                const size_t e = size_t(g) * R + r0;
+                T rv[VW], d[VW], pv[VW];
+                vld_cg(a.r + e, rv);
+                dinv_vec<T, VW, OP>(a.invdiag, g, r0, d);
+                if (it > 0) {
+                    T po[VW];
+                    vld_cg(pp + e, po);
+#pragma unroll
+                    for (int c = 0; c < VW; ++c) pv[c] = d[c] * rv[c] + bt[c] * po[c];
+                } else {
+#pragma unroll
+                    for (int c = 0; c < VW; ++c) pv[c] = d[c] * rv[c];
+                }
+                vst(s.xin + li * R + r0, pv);
+            }
+            if constexpr (!kCsr)
+                for (int i = threadIdx.x; i < nown * R; i += blockDim.x) s.yout[i] = T(0);
+            __syncthreads();
             if constexpr (kCsr) {
-                for (int i = threadIdx.x; i < nt * R; i += blockDim.x) {
-                    const int g = __ldg(m.nodes + nb + i / R);
-                    const size_t e = size_t(g) * R + myr;
-                    T pv = dinv<T, R, OP>(a.invdiag, g, myr) * __ldcg(a.r + e);
-                    const T bt = T(beta[myr]);
-                    if (bt != T(0)) pv += bt * __ldcg(pp + e);
-                    s.xin[i] = pv;
+                // thread per (owned row, RHS block): sliced-ELLPACK row from shared p
+                for (int i = threadIdx.x; i < nown * NP; i += blockDim.x) {
+                    const int li = i / NP;
+                    const int g = ob + li;
+                    const int64_t base = m.sell_ptr[g >> 5] * 32 + (g & 31);
+                    const int len = m.sell_len[g];
+                    T acc[VW];
+#pragma unroll
+                    for (int c = 0; c < VW; ++c) acc[c] = T(0);
+                    for (int k = 0; k < len; ++k) {
+                        const int64_t idx = base + int64_t(k) * 32;
+                        const int col = m.sell_col[idx];
+                        T xv[VW];
+                        vld(s.xin + col * R + r0, xv);
+                        if constexpr (OP == OP_CSR1) {
+                            const T v = __ldg(a.op.v0 + idx);
+#pragma unroll
+                            for (int c = 0; c < VW; ++c) acc[c] += v * xv[c];
+                        } else {
+                            // two blocks, one value set each (R = 2)
+#pragma unroll
+                            for (int c = 0; c < VW; ++c)
+                                acc[c] += __ldg(((r0 + c) == 0 ? a.op.v0 : a.op.v1) + idx) * xv[c];
+                        }
+                    }
+                    T pv[VW];
+                    vld(s.xin + li * R + r0, pv);
+                    const size_t e = size_t(g) * R + r0;
+                    vst(pc + e, pv);
+                    vst(a.q + e, acc);
+#pragma unroll
+                    for (int c = 0; c < VW; ++c) accA[0][c] += double(pv[c]) * double(acc[c]);
                 }
                 __syncthreads();
-                csr_rows<T, R, (OP == OP_CSR2 ? 2 : 1)>(m, ob, nown, a.op.v0, a.op.v1, s.xin,
-                                                       [&](int i, int r, T qv) {
-                                                           const size_t e = size_t(ob + i) * R + r;
-                                                           const T pv = s.xin[i * R + r];
-                                                           pc[e] = pv;
-                                                           a.q[e] = qv;
-                                                           accF[r] += double(pv) * double(qv);
-                                                       });
-                __syncthreads();
-                continue;
-            }
-            stage_static<T, R>(m, nb, nt, s, a.op);
-            for (int i = threadIdx.x; i < nt * R; i += blockDim.x) {
-                const int li = i / R;
-                const int g = __ldg(m.nodes + nb + li);
-                const size_t e = size_t(g) * R + myr;
-                T pv = dinv<T, R, OP>(a.invdiag, g, myr) * __ldcg(a.r + e);
-                const T bt = T(beta[myr]);
-                if (bt != T(0)) pv += bt * __ldcg(pp + e);
-                s.xin[i] = pv;
-            }
-            for (int i = threadIdx.x; i < nown * R; i += blockDim.x) s.yout[i] = T(0);
-            __syncthreads();
-            if constexpr (!kCsr) {
+            } else {
                 patch_elements<T, R, OP>(m, p, nown, s, a.op);
                 __syncthreads();
                 for (int i = threadIdx.x; i < nown * R; i += blockDim.x) {
@@ -278,16 +358,12 @@ __global__ void __launch_bounds__(kThreads) k_pcg(PcgArgs<T> a) {
                     if (OP == OP_PRIOR) qv += a.op.delta * pv;
                     pc[e] = pv;
                     a.q[e] = qv;
-                    accA[0] += double(pv) * double(qv);
+                    accA[0][0] += double(pv) * double(qv);
                 }
                 __syncthreads();
             }
         }
-        if constexpr (kCsr) {
-            if (!grid_sum_full<R>(accF, scratch, a.partials, red_id, a.bar, a.status, a.spin_limit, red)) return;
-        } else {
-            if (!grid_sum<R, 1>(accA, scratch, a.partials, red_id, a.bar, a.status, a.spin_limit, red)) return;
-        }
+        if (!grid_reduce<1, VW, NP>(accA, scratch, a.partials, red_id, a.bar, a.status, a.spin_limit, red)) return;
         if (threadIdx.x == 0) {
             int bad = 0;
             for (int r = 0; r < R; ++r) {
@@ -305,24 +381,37 @@ __global__ void __launch_bounds__(kThreads) k_pcg(PcgArgs<T> a) {
         }
 
         // ---- phase B: x += alpha p, r -= alpha q; r.D^-1 r and r.r
-        double accB[2] = {0.0, 0.0};
+        double accB[2][VW];
+#pragma unroll
+        for (int c = 0; c < VW; ++c) accB[0][c] = accB[1][c] = 0.0;
         {
-            const T al = T(alpha[myr]);
+            T al[VW];
+#pragma unroll
+            for (int c = 0; c < VW; ++c) al[c] = T(alpha[r0 + c]);
             for (int p = blockIdx.x; p < P; p += gridDim.x) {
-                const int ob = __ldg(m.own_begin + p), oe = __ldg(m.own_begin + p + 1);
-                for (int i = threadIdx.x; i < (oe - ob) * R; i += blockDim.x) {
-                    const size_t e = size_t(ob) * R + i;
-                    const T pv = pc[e], qv = a.q[e];
-                    a.x[e] += al * pv;
-                    const T rv = a.r[e] - al * qv;
-                    a.r[e] = rv;
-                    const T z = dinv<T, R, OP>(a.invdiag, ob + i / R, myr) * rv;
-                    accB[0] += double(rv) * double(z);
-                    accB[1] += double(rv) * double(rv);
+                const int ob = __ldg(m.own_begin + p), nown = __ldg(m.own_begin + p + 1) - ob;
+                for (int i = threadIdx.x; i < nown * NP; i += blockDim.x) {
+                    const int g = ob + i / NP;
+                    const size_t e = size_t(g) * R + r0;
+                    T pv[VW], qv[VW], xv[VW], rv[VW], d[VW];
+                    vld(pc + e, pv);
+                    vld(a.q + e, qv);
+                    vld(a.x + e, xv);
+                    vld(a.r + e, rv);
+                    dinv_vec<T, VW, OP>(a.invdiag, g, r0, d);
+#pragma unroll
+                    for (int c = 0; c < VW; ++c) {
+                        xv[c] += al[c] * pv[c];
+                        rv[c] -= al[c] * qv[c];
+                        accB[0][c] += double(rv[c]) * double(d[c] * rv[c]);
+                        accB[1][c] += double(rv[c]) * double(rv[c]);
+                    }
+                    vst(a.x + e, xv);
+                    vst(a.r + e, rv);
                 }
             }
         }
-        if (!grid_sum<R, 2>(accB, scratch, a.partials, red_id, a.bar, a.status, a.spin_limit, red)) return;
+        if (!grid_reduce<2, VW, NP>(accB, scratch, a.partials, red_id, a.bar, a.status, a.spin_limit, red)) return;
         if (threadIdx.x < R) {
             const int r = threadIdx.x;
             const bool act = rr[r] > a.rtol2 * bb[r];
@@ -356,9 +445,11 @@ cudaError_t launch_pcg_t(const MeshDev& m, const OpParams<T>& op, const T* invdi
     err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, smem);
     if (err != cudaSuccess) return err;
     if (per_sm < 1) return cudaErrorInvalidConfiguration;
-    int grid = per_sm * nsm;
-    if (grid > kMaxGrid) grid = kMaxGrid;
-    if (grid > m.P) grid = m.P;
+    int maxres = per_sm * nsm;
+    if (maxres > kMaxGrid) maxres = kMaxGrid;
+    // equal patch counts per CTA: k = ceil(P / resident), grid = ceil(P / k)
+    const int k = (m.P + maxres - 1) / maxres;
+    const int grid = (m.P + k - 1) / k;
     if (grid_used) *grid_used = grid;
     PcgArgs<T> a;
     a.m = m;
@@ -377,7 +468,7 @@ cudaError_t launch_pcg_t(const MeshDev& m, const OpParams<T>& op, const T* invdi
     a.stats = w.stats;
     a.rtol2 = rtol * rtol;
     a.maxit = maxit;
-    a.spin_limit = 20000000LL;  // about 2 s of __nanosleep(100) spins
+    a.spin_limit = 40000000LL;  // about 2 s of __nanosleep(32) spins
     err = cudaMemsetAsync(w.bar, 0, 2 * sizeof(unsigned), s);
     if (err != cudaSuccess) return err;
     err = cudaMemsetAsync(w.status, 0, sizeof(int), s);
@@ -389,6 +480,8 @@ cudaError_t launch_pcg_t(const MeshDev& m, const OpParams<T>& op, const T* invdi
 }  // namespace
 
 int pcg_max_grid() { return kMaxGrid; }
+
+size_t pcg_partials_doubles() { return size_t(2) * kMaxGrid * kMaxNS + 2 * kMaxNS; }
 
 template <typename T>
 cudaError_t launch_pcg(const MeshDev& m, int OP, int R, const OpParams<T>& op, const T* invdiag,

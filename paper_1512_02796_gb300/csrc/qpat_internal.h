@@ -21,7 +21,8 @@ namespace qpat {
 struct HostMesh {
     int64_t N = 0, E = 0, F = 0;
     int P = 0;                        // number of patches
-    int patch_nodes = 0;              // owned nodes per patch (last may be fewer)
+    int patch_nodes = 0;              // target owned nodes per patch (multiple of 32)
+    std::vector<int32_t> patch_of_slice;  // patch owning each 32-node slice
     std::vector<double> xyz;          // N x 3, library order
     std::vector<int32_t> tets;        // E x 4, library ids
     std::vector<int32_t> perm;        // library id -> caller id
@@ -54,7 +55,7 @@ struct HostMesh {
 
 // Builds a HostMesh; returns "" on success or an error message.
 std::string build_host_mesh(const double* xyz, int64_t N, const int32_t* tets,
-                            int64_t E, int patch_nodes, HostMesh& out);
+                            int64_t E, int patch_nodes, int patch_multiple, HostMesh& out);
 
 // Flux of a square boundary patch in canonical face order (see qpat.h).
 void flux_patch_host(const HostMesh& m, const double c[3], const double n[3],

@@ -80,6 +80,7 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
         "qpat_mesh_num_tets": (ctypes.c_int64, [vp]),
         "qpat_mesh_num_faces": (ctypes.c_int64, [vp]),
         "qpat_mesh_num_patches": (ctypes.c_int64, [vp]),
+        "qpat_mesh_num_entries": (ctypes.c_int64, [vp]),
         "qpat_mesh_faces": (ctypes.c_int, [vp, _c_int32_p]),
         "qpat_mesh_permutation": (ctypes.c_int, [vp, _c_int32_p]),
         "qpat_mesh_stats": (ctypes.c_int, [vp, _c_int64_p]),
@@ -121,6 +122,7 @@ def exported_names() -> Sequence[str]:
     return [
         "qpat_default_params", "qpat_last_error", "qpat_mesh", "qpat_mesh_ex", "qpat_mesh_free",
         "qpat_mesh_host_info", "qpat_mesh_num_nodes", "qpat_mesh_num_tets", "qpat_mesh_num_faces", "qpat_mesh_num_patches",
+        "qpat_mesh_num_entries",
         "qpat_mesh_faces", "qpat_mesh_permutation", "qpat_mesh_stats", "qpat_mesh_reset_stats",
         "qpat_mesh_set_timing", "qpat_mesh_pcg_time",
         "qpat_flux_patch", "qpat_apply_K_dev", "qpat_forward", "qpat_forward_dev", "qpat_forward_noalloc_dev",
@@ -159,18 +161,23 @@ def qpat_default_params(**overrides) -> qpat_params:
 class Mesh:
     """Owning wrapper of a qpat_mesh_t handle."""
 
-    def __init__(self, xyz, tets, patch_nodes: int = 512):
+    def __init__(self, xyz, tets, patch_nodes: Optional[int] = None):
         lib = load()
         xyz = _f64(xyz)
         tets = np.ascontiguousarray(tets, dtype=np.int32)
         h = ctypes.c_void_p()
-        _check(lib.qpat_mesh_ex(_dp(xyz), xyz.shape[0], tets.ctypes.data_as(_c_int32_p), tets.shape[0],
-                                patch_nodes, ctypes.byref(h)))
+        if patch_nodes is None:
+            _check(lib.qpat_mesh(_dp(xyz), xyz.shape[0], tets.ctypes.data_as(_c_int32_p), tets.shape[0],
+                                 ctypes.byref(h)))
+        else:
+            _check(lib.qpat_mesh_ex(_dp(xyz), xyz.shape[0], tets.ctypes.data_as(_c_int32_p), tets.shape[0],
+                                    patch_nodes, ctypes.byref(h)))
         self.handle = h
         self.N = int(lib.qpat_mesh_num_nodes(h))
         self.E = int(lib.qpat_mesh_num_tets(h))
         self.F = int(lib.qpat_mesh_num_faces(h))
         self.P = int(lib.qpat_mesh_num_patches(h))
+        self.entries = int(lib.qpat_mesh_num_entries(h))
 
     def close(self):
         if getattr(self, "handle", None):
@@ -211,7 +218,9 @@ class Mesh:
         return float(v.value)
 
 
-def qpat_mesh(xyz, tets, patch_nodes: int = 512) -> Mesh:
+def qpat_mesh(xyz, tets, patch_nodes: Optional[int] = None) -> Mesh:
+    """Mesh handle; patch_nodes=None lets the library balance the patches
+    over the GPU's resident CTAs (qpat_mesh), an int calls qpat_mesh_ex."""
     return Mesh(xyz, tets, patch_nodes)
 
 

@@ -46,7 +46,7 @@ def test_host_mesh_faces_match_oracle_and_patches_verify(n, L, pn):
     assert np.array_equal(np.sort(perm), np.arange(n ** 3))
     assert info["P"] == -(-n ** 3 // pn)
     assert info["patch_tets"] >= 6 * (n - 1) ** 3
-    assert info["max_own"] <= pn
+    assert info["max_own"] <= pn + 32     # balanced whole 32-node slices
 
 
 def test_host_mesh_random_relabelled_mesh():
