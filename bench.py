@@ -294,12 +294,81 @@ def run_ours(args):
         "clocks": clocks,
         "wall_s": wall,
     }
+    if rank == 0 and args.extras:
+        out["uneven_batch"] = uneven_batch_leg(Q, torch)
+        out["autotune"] = autotune_leg(Q)
     if rank == 0 and args.cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(steps=2)
     if rank == 0:
         print(json.dumps(out), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()
+
+
+def uneven_batch_leg(Q, torch, reps: int = 5):
+    """32 forward problems on cubes of 16^3-48^3 nodes with 1-4 illuminations:
+    one batched cooperative launch replayed as a CUDA graph, against the same
+    solves issued one mesh after the other (FP64, rtol 1e-13 both)."""
+    cfgs = S.uneven_batch(32)
+    meshes, ins = [], []
+    for cfg in cfgs:
+        xyz, tets = cfg.mesh()
+        kap, mu = cfg.coefficients(xyz)
+        m = Q.qpat_mesh(xyz, tets, patch_nodes=256)
+        flux = np.stack([Q.qpat_flux_patch(m, p.center, p.normal, p.half_w, p.amp) for p in cfg.patches])
+        meshes.append(m)
+        ins.append(tuple(torch.tensor(a, device="cuda") for a in (kap, mu, flux)))
+    batch = Q.qpat_batch_create(meshes, [c.K for c in cfgs])
+    for j, (k, mu, f) in enumerate(ins):
+        bk, bm, bf = batch.inputs(j)
+        bk.copy_(k)
+        bm.copy_(mu)
+        bf.copy_(f)
+    batch.forward()                      # records the graph
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    for _ in range(reps):
+        batch.forward()
+    b.record()
+    torch.cuda.synchronize()
+    t_batch = a.elapsed_time(b) / reps
+    st, it, ct = batch.status()
+    outs = [torch.empty((c.K, m.N), dtype=torch.float64, device="cuda") for c, m in zip(cfgs, meshes)]
+    hs = [torch.empty_like(o) for o in outs]
+    p0 = Q.qpat_default_params(precision=0)
+    for j, (k, mu, f) in enumerate(ins):
+        Q.qpat_forward_dev(meshes[j], k, mu, f, outs[j], hs[j], p0)
+    torch.cuda.synchronize()
+    a.record()
+    for _ in range(reps):
+        for j, (k, mu, f) in enumerate(ins):
+            Q.qpat_forward_dev(meshes[j], k, mu, f, outs[j], hs[j], p0)
+    b.record()
+    torch.cuda.synchronize()
+    t_seq = a.elapsed_time(b) / reps
+    err = max(float(torch.linalg.norm(batch.phi(j) - outs[j]) / torch.linalg.norm(outs[j]))
+              for j in range(len(cfgs)))
+    res = {"problems": len(cfgs), "nodes_total": int(sum(m.N for m in meshes)),
+           "sizes_n": [c.n for c in cfgs], "illuminations": [c.K for c in cfgs],
+           "batched_graph_ms": t_batch, "sequential_ms": t_seq, "speedup": t_seq / t_batch,
+           "max_rel_diff_vs_sequential": err, "ctas": ct, "pcg_iters": it,
+           "all_converged": all(s == 0 for s in st)}
+    batch.close()
+    for m in meshes:
+        m.close()
+    return res
+
+
+def autotune_leg(Q):
+    """Autotuner on the benchmark mesh for the pair launch (8 RHS)."""
+    cfg = S.config(WORKLOAD)
+    xyz, tets = cfg.mesh()
+    kap, mu = cfg.coefficients(xyz)
+    (pn, op), table = Q.qpat_autotune(xyz, tets, kap, mu, 2 * cfg.K, iters=30)
+    return {"rhs": 2 * cfg.K, "best_patch_nodes": pn, "best_fp32_operator": op,
+            "us_per_fp32_iteration": {f"{'default' if c == 0 else c}/{'assembled' if o else 'matrix-free'}": v
+                                      for (c, o), v in table.items()}}
 
 
 def cpu_baseline(steps: int = 2):
@@ -422,6 +491,8 @@ def main():
     ap.add_argument("--fp32-operator", type=int, default=1, choices=[0, 1],
                     help="FP32 inner operator: 0 matrix-free elements, 1 assembled values")
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
+    ap.add_argument("--no-extras", dest="extras", action="store_false",
+                    help="skip the uneven-batch and autotuner legs")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -237,6 +237,49 @@ int qpat_jvp_vjp_pair_dev(qpat_mesh_t mesh, const qpat_params* prm,
                           const double* t, double* out_jv, double* out_vjp,
                           void* stream);
 
+/* ---------------------------------------------------------- autotuner */
+
+/* Times `iters` FP32 PCG iterations (K right-hand sides, host kappa and mu
+ * in caller order) for each candidate patch size {library default, 128,
+ * 256, 512, 1024 owned nodes per CTA} and each FP32 operator form
+ * {matrix-free, assembled}, building a mesh per candidate; returns the
+ * fastest pair (best_patch_nodes 0 = the default of qpat_mesh) and, if not
+ * NULL, the microseconds per iteration of all candidates in that order
+ * (us_per_iter needs 10 entries; *ncand receives the count).  Pass the
+ * winners to qpat_mesh_ex / qpat_params.fp32_operator.  Not in the paper. */
+int qpat_autotune(const double* xyz, int64_t N, const int32_t* tets, int64_t E,
+                  const double* kappa, const double* mu, int K, int iters,
+                  int* best_patch_nodes, int* best_fp32_operator,
+                  double* us_per_iter, int* ncand);
+
+/* ---------------------------------------------------- uneven batches */
+
+/* A batch of forward solves (as qpat_forward_dev, FP64, assembled K) on
+ * several meshes of different sizes.  All solves run in ONE cooperative
+ * launch: each problem gets CTAs in proportion to its node count (at least
+ * one, at most one per patch) and synchronises only those.  The whole
+ * sequence (layout changes, assembly of K, load vectors, the batched PCG,
+ * the output layout) is recorded into a CUDA graph on the first
+ * qpat_batch_forward and replayed afterwards.  Illuminations are padded to
+ * a common R = K_max rounded up to 1, 2, 4 or 8 (K_j <= 8).  Stacked
+ * illuminations follow Sec. 4; the solve is the Appendix's K^-1 f.
+ * Ownership: the batch allocates (at creation) and owns per problem j the
+ * device buffers kappa_j, mu_j (N_j), flux_j (K_j x F_j, canonical faces)
+ * and phi_j (K_j x N_j) returned by qpat_batch_buffers; the caller fills
+ * the inputs, runs qpat_batch_forward(stream) and reads phi_j after the
+ * stream completes.  The meshes must outlive the batch. */
+typedef struct qpat_batch_s* qpat_batch_t;
+int qpat_batch_create(int nprob, const qpat_mesh_t* meshes, const int* K,
+                      const qpat_params* prm, qpat_batch_t* out);
+int qpat_batch_buffers(qpat_batch_t batch, int j, double** kappa, double** mu,
+                       double** flux, double** phi);
+/* Asynchronous on `stream` (a cudaStream_t); the first call records the graph. */
+int qpat_batch_forward(qpat_batch_t batch, void* stream);
+/* Per problem: PCG status (QPAT_OK, QPAT_ENOCONV, ...), iterations and CTAs
+ * of the last run (synchronous; any array may be NULL). */
+int qpat_batch_status(qpat_batch_t batch, int* status, int* iters, int* ctas);
+void qpat_batch_free(qpat_batch_t batch);
+
 /* ------------------------------------------------------------- prior */
 
 /* out = M_delta^{-1} rhs with M_delta = blkdiag(M(kt), (b/a) M(mt)) + delta I

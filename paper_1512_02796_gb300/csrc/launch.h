@@ -3,6 +3,8 @@
 
 #include <cuda_runtime.h>
 
+#include <vector>
+
 #include "fem.cuh"
 #include "qpat_internal.h"
 
@@ -80,6 +82,27 @@ struct PcgWork {
 template <typename T>
 cudaError_t launch_pcg(const MeshDev& m, int OP, int R, const OpParams<T>& op, const T* invdiag,
                        const PcgWork& w, double rtol, int maxit, cudaStream_t s, int* grid_used);
+
+// Many independent FP64 assembled-K solves (different meshes) in one
+// cooperative launch; see k_pcg_batch in pcg.cu.
+struct PcgBatchProblem {
+    MeshDev m;
+    const double* vals;     // assembled K values
+    const double* invdiag;  // N
+    PcgWork w;              // b, x, r, p0, p1, q, partials, bar, status, iters, stats
+    double rtol;
+    int maxit;
+};
+struct PcgBatchPlan {
+    void* dev_args = nullptr;
+    int* dev_cta_begin = nullptr;
+    int R = 0, nprob = 0, grid = 0;
+    size_t smem = 0;
+    std::vector<int> cta_count;
+};
+cudaError_t pcg_batch_prepare(int R, const std::vector<PcgBatchProblem>& probs, PcgBatchPlan& plan);
+cudaError_t pcg_batch_launch(const PcgBatchPlan& plan, cudaStream_t s);
+void pcg_batch_release(PcgBatchPlan& plan);
 
 int pcg_max_grid();            // upper bound of the cooperative grid
 size_t pcg_partials_doubles();  // size of PcgWork::partials (per-CTA partials + totals)

@@ -20,7 +20,9 @@
 // are moved as 16-byte vectors (4 floats or 2 doubles of consecutive RHS)
 // wherever R allows.  Scalars are accumulated in FP64 for either T.
 #include <cuda/atomic>
+#include <algorithm>
 #include <cstring>
+#include <vector>
 
 #include "launch.h"
 
@@ -126,7 +128,8 @@ __device__ __forceinline__ void dinv_vec(const T* invdiag, int g, int r0, T (&d)
 // (t % NP) * VW + c.  Totals land in out[q * R + r] (shared) in every CTA.
 template <int NQ, int VW, int NP>
 __device__ __forceinline__ bool grid_reduce(double (&acc)[NQ][VW], double* scratch, double* partials, int& red_id,
-                                            unsigned* bar, int* status, long long limit, double* out) {
+                                            unsigned* bar, int* status, long long limit, double* out, int cta,
+                                            int ncta) {
     constexpr int R = VW * NP, NS = NQ * R;
     __shared__ int s_last;
     __shared__ int s_ok;
@@ -149,7 +152,7 @@ __device__ __forceinline__ bool grid_reduce(double (&acc)[NQ][VW], double* scrat
     if (threadIdx.x < NS) {
         double a = 0.0;
         for (int w = 0; w < nw; ++w) a += scratch[w * NS + threadIdx.x];
-        part[size_t(blockIdx.x) * NS + threadIdx.x] = a;
+        part[size_t(cta) * NS + threadIdx.x] = a;
     }
     __syncthreads();
     cuda::atomic_ref<unsigned, cuda::thread_scope_device> cnt(bar[0]);
@@ -159,7 +162,7 @@ __device__ __forceinline__ bool grid_reduce(double (&acc)[NQ][VW], double* scrat
         g = gen.load(cuda::memory_order_acquire);
         __threadfence();
         const unsigned old = cnt.fetch_add(1u, cuda::memory_order_acq_rel);
-        s_last = old == gridDim.x - 1;
+        s_last = old == unsigned(ncta) - 1;
         s_ok = 1;
     }
     __syncthreads();
@@ -168,7 +171,7 @@ __device__ __forceinline__ bool grid_reduce(double (&acc)[NQ][VW], double* scrat
         __threadfence();
         for (int s = warp; s < NS; s += nw) {
             double a = 0.0;
-            for (int j = lane; j < gridDim.x; j += 32) a += __ldcg(part + size_t(j) * NS + s);
+            for (int j = lane; j < ncta; j += 32) a += __ldcg(part + size_t(j) * NS + s);
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
             if (lane == 0) res[s] = a;
@@ -200,7 +203,7 @@ __device__ __forceinline__ bool grid_reduce(double (&acc)[NQ][VW], double* scrat
 
 // ---------------------------------------------------------------- the solver
 template <typename T, int R, int OP>
-__global__ void __launch_bounds__(kThreads) k_pcg(PcgArgs<T> a) {
+__device__ __forceinline__ void pcg_body(const PcgArgs<T>& a, const int cta, const int ncta) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     constexpr bool kCsr = (OP == OP_CSR1 || OP == OP_CSR2);
     constexpr int VW = vec_width<T, R, kCsr>();
@@ -227,7 +230,7 @@ __global__ void __launch_bounds__(kThreads) k_pcg(PcgArgs<T> a) {
         double acc[3][VW];
 #pragma unroll
         for (int c = 0; c < VW; ++c) acc[0][c] = acc[1][c] = acc[2][c] = 0.0;
-        for (int p = blockIdx.x; p < P; p += gridDim.x) {
+        for (int p = cta; p < P; p += ncta) {
             const int ob = __ldg(m.own_begin + p), nown = __ldg(m.own_begin + p + 1) - ob;
             for (int i = threadIdx.x; i < nown * NP; i += blockDim.x) {
                 const int g = ob + i / NP;
@@ -247,7 +250,9 @@ __global__ void __launch_bounds__(kThreads) k_pcg(PcgArgs<T> a) {
         }
 #pragma unroll
         for (int c = 0; c < VW; ++c) acc[2][c] = acc[0][c];
-        if (!grid_reduce<3, VW, NP>(acc, scratch, a.partials, red_id, a.bar, a.status, a.spin_limit, red)) return;
+        if (!grid_reduce<3, VW, NP>(acc, scratch, a.partials, red_id, a.bar, a.status, a.spin_limit, red, cta,
+                                    ncta))
+            return;
         if (threadIdx.x < R) {
             bb[threadIdx.x] = red[threadIdx.x];
             rz[threadIdx.x] = red[R + threadIdx.x];
@@ -268,7 +273,7 @@ __global__ void __launch_bounds__(kThreads) k_pcg(PcgArgs<T> a) {
         __syncthreads();
         if (!s_flag) break;
         if (it >= a.maxit) {
-            if (blockIdx.x == 0 && threadIdx.x == 0) atomicCAS(a.status, 0, QPAT_ENOCONV);
+            if (cta == 0 && threadIdx.x == 0) atomicCAS(a.status, 0, QPAT_ENOCONV);
             break;
         }
         if (threadIdx.x < R) {
@@ -288,7 +293,7 @@ __global__ void __launch_bounds__(kThreads) k_pcg(PcgArgs<T> a) {
         double accA[1][VW];
 #pragma unroll
         for (int c = 0; c < VW; ++c) accA[0][c] = 0.0;
-        for (int p = blockIdx.x; p < P; p += gridDim.x) {
+        for (int p = cta; p < P; p += ncta) {
             const int nb = __ldg(m.node_ptr + p), nt = __ldg(m.node_ptr + p + 1) - nb;
             const int ob = __ldg(m.own_begin + p), nown = __ldg(m.own_begin + p + 1) - ob;
             if constexpr (!kCsr) stage_static<T, R>(m, nb, nt, s, a.op);
@@ -363,7 +368,9 @@ __global__ void __launch_bounds__(kThreads) k_pcg(PcgArgs<T> a) {
                 __syncthreads();
             }
         }
-        if (!grid_reduce<1, VW, NP>(accA, scratch, a.partials, red_id, a.bar, a.status, a.spin_limit, red)) return;
+        if (!grid_reduce<1, VW, NP>(accA, scratch, a.partials, red_id, a.bar, a.status, a.spin_limit, red, cta,
+                                    ncta))
+            return;
         if (threadIdx.x == 0) {
             int bad = 0;
             for (int r = 0; r < R; ++r) {
@@ -376,7 +383,7 @@ __global__ void __launch_bounds__(kThreads) k_pcg(PcgArgs<T> a) {
         }
         __syncthreads();
         if (s_flag) {
-            if (blockIdx.x == 0 && threadIdx.x == 0) atomicCAS(a.status, 0, QPAT_EBREAKDOWN);
+            if (cta == 0 && threadIdx.x == 0) atomicCAS(a.status, 0, QPAT_EBREAKDOWN);
             break;
         }
 
@@ -388,7 +395,7 @@ __global__ void __launch_bounds__(kThreads) k_pcg(PcgArgs<T> a) {
             T al[VW];
 #pragma unroll
             for (int c = 0; c < VW; ++c) al[c] = T(alpha[r0 + c]);
-            for (int p = blockIdx.x; p < P; p += gridDim.x) {
+            for (int p = cta; p < P; p += ncta) {
                 const int ob = __ldg(m.own_begin + p), nown = __ldg(m.own_begin + p + 1) - ob;
                 for (int i = threadIdx.x; i < nown * NP; i += blockDim.x) {
                     const int g = ob + i / NP;
@@ -411,7 +418,9 @@ __global__ void __launch_bounds__(kThreads) k_pcg(PcgArgs<T> a) {
                 }
             }
         }
-        if (!grid_reduce<2, VW, NP>(accB, scratch, a.partials, red_id, a.bar, a.status, a.spin_limit, red)) return;
+        if (!grid_reduce<2, VW, NP>(accB, scratch, a.partials, red_id, a.bar, a.status, a.spin_limit, red, cta,
+                                    ncta))
+            return;
         if (threadIdx.x < R) {
             const int r = threadIdx.x;
             const bool act = rr[r] > a.rtol2 * bb[r];
@@ -424,11 +433,127 @@ __global__ void __launch_bounds__(kThreads) k_pcg(PcgArgs<T> a) {
         __syncthreads();
         ++it;
     }
-    if (blockIdx.x == 0 && threadIdx.x < R) {
+    if (cta == 0 && threadIdx.x < R) {
         a.stats[threadIdx.x] = rr[threadIdx.x];
         a.stats[R + threadIdx.x] = bb[threadIdx.x];
         if (threadIdx.x == 0) *a.iters = it;
     }
+}
+
+template <typename T, int R, int OP>
+__global__ void __launch_bounds__(kThreads) k_pcg(PcgArgs<T> a) {
+    pcg_body<T, R, OP>(a, blockIdx.x, gridDim.x);
+}
+
+// Independent problems (meshes of different sizes) in one cooperative
+// launch: CTAs [cta_begin[j], cta_begin[j+1]) solve problem j, and each
+// problem's barriers and reductions involve only its own CTAs.
+template <typename T, int R, int OP>
+__global__ void __launch_bounds__(kThreads) k_pcg_batch(const PcgArgs<T>* __restrict__ probs,
+                                                        const int* __restrict__ cta_begin, int nprob) {
+    int lo = 0, hi = nprob - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) / 2;
+        if (cta_begin[mid] <= int(blockIdx.x))
+            lo = mid;
+        else
+            hi = mid - 1;
+    }
+    const int b0 = cta_begin[lo];
+    const PcgArgs<T> a = probs[lo];
+    pcg_body<T, R, OP>(a, int(blockIdx.x) - b0, cta_begin[lo + 1] - b0);
+}
+
+template <int R>
+cudaError_t batch_prepare_t(const std::vector<PcgBatchProblem>& probs, PcgBatchPlan& plan) {
+    size_t smem = 0;
+    for (const auto& p : probs) smem = std::max(smem, sizeof(double) * size_t(p.m.max_touched) * R);
+    auto kern = k_pcg_batch<double, R, OP_CSR1>;
+    cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+    if (err != cudaSuccess) return err;
+    int dev = 0, nsm = 0, per_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, smem);
+    if (err != cudaSuccess) return err;
+    if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    const int nprob = int(probs.size());
+    int resident = std::min(per_sm * nsm, kMaxGrid);
+    if (resident < nprob) return cudaErrorInvalidConfiguration;
+    // CTAs proportional to the work (nodes), at least one per problem and at
+    // most one per patch
+    double total = 0;
+    for (const auto& p : probs) total += double(p.m.N);
+    std::vector<int> cnt(nprob);
+    int used = 0;
+    for (int j = 0; j < nprob; ++j) {
+        int c = int(double(resident - nprob) * double(probs[j].m.N) / total) + 1;
+        c = std::min(c, probs[j].m.P);
+        cnt[j] = c;
+        used += c;
+    }
+    // hand the remaining CTAs to the problems with the most nodes per CTA
+    for (int guard = 0; used < resident && guard < resident; ++guard) {
+        int best = -1;
+        double load = 0;
+        for (int j = 0; j < nprob; ++j)
+            if (cnt[j] < probs[j].m.P && double(probs[j].m.N) / cnt[j] > load) {
+                load = double(probs[j].m.N) / cnt[j];
+                best = j;
+            }
+        if (best < 0) break;
+        ++cnt[best];
+        ++used;
+    }
+    std::vector<int> begin(nprob + 1, 0);
+    for (int j = 0; j < nprob; ++j) begin[j + 1] = begin[j] + cnt[j];
+    std::vector<PcgArgs<double>> args(nprob);
+    for (int j = 0; j < nprob; ++j) {
+        const auto& p = probs[j];
+        PcgArgs<double>& a = args[j];
+        a.m = p.m;
+        a.op = OpParams<double>{nullptr, nullptr, 0.0, 0.0, 0.0, 1, p.vals, nullptr};
+        a.invdiag = p.invdiag;
+        a.b = static_cast<const double*>(p.w.b);
+        a.x = static_cast<double*>(p.w.x);
+        a.r = static_cast<double*>(p.w.r);
+        a.p0 = static_cast<double*>(p.w.p0);
+        a.p1 = static_cast<double*>(p.w.p1);
+        a.q = static_cast<double*>(p.w.q);
+        a.partials = p.w.partials;
+        a.bar = p.w.bar;
+        a.status = p.w.status;
+        a.iters = p.w.iters;
+        a.stats = p.w.stats;
+        a.rtol2 = p.rtol * p.rtol;
+        a.maxit = p.maxit;
+        a.spin_limit = 40000000LL;
+    }
+    if ((err = cudaMalloc(&plan.dev_args, sizeof(PcgArgs<double>) * nprob)) != cudaSuccess) return err;
+    if ((err = cudaMalloc(reinterpret_cast<void**>(&plan.dev_cta_begin), sizeof(int) * (nprob + 1))) != cudaSuccess)
+        return err;
+    if ((err = cudaMemcpy(plan.dev_args, args.data(), sizeof(PcgArgs<double>) * nprob, cudaMemcpyHostToDevice)) !=
+        cudaSuccess)
+        return err;
+    if ((err = cudaMemcpy(plan.dev_cta_begin, begin.data(), sizeof(int) * (nprob + 1), cudaMemcpyHostToDevice)) !=
+        cudaSuccess)
+        return err;
+    plan.R = R;
+    plan.nprob = nprob;
+    plan.grid = begin[nprob];
+    plan.smem = smem;
+    plan.cta_count = cnt;
+    return cudaSuccess;
+}
+
+template <int R>
+cudaError_t batch_launch_t(const PcgBatchPlan& plan, cudaStream_t s) {
+    auto kern = k_pcg_batch<double, R, OP_CSR1>;
+    const PcgArgs<double>* pa = static_cast<const PcgArgs<double>*>(plan.dev_args);
+    const int* cb = plan.dev_cta_begin;
+    int np = plan.nprob;
+    void* args[] = {&pa, &cb, &np};
+    return cudaLaunchCooperativeKernel((void*)kern, dim3(plan.grid), dim3(kThreads), args, plan.smem, s);
 }
 
 template <typename T, int R, int OP>
@@ -480,6 +605,33 @@ cudaError_t launch_pcg_t(const MeshDev& m, const OpParams<T>& op, const T* invdi
 }  // namespace
 
 int pcg_max_grid() { return kMaxGrid; }
+
+cudaError_t pcg_batch_prepare(int R, const std::vector<PcgBatchProblem>& probs, PcgBatchPlan& plan) {
+    switch (R) {
+        case 1: return batch_prepare_t<1>(probs, plan);
+        case 2: return batch_prepare_t<2>(probs, plan);
+        case 4: return batch_prepare_t<4>(probs, plan);
+        case 8: return batch_prepare_t<8>(probs, plan);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t pcg_batch_launch(const PcgBatchPlan& plan, cudaStream_t s) {
+    switch (plan.R) {
+        case 1: return batch_launch_t<1>(plan, s);
+        case 2: return batch_launch_t<2>(plan, s);
+        case 4: return batch_launch_t<4>(plan, s);
+        case 8: return batch_launch_t<8>(plan, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+void pcg_batch_release(PcgBatchPlan& plan) {
+    if (plan.dev_args) cudaFree(plan.dev_args);
+    if (plan.dev_cta_begin) cudaFree(plan.dev_cta_begin);
+    plan.dev_args = nullptr;
+    plan.dev_cta_begin = nullptr;
+}
 
 size_t pcg_partials_doubles() { return size_t(2) * kMaxGrid * kMaxNS + 2 * kMaxNS; }
 

@@ -105,6 +105,17 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
                                                  vp, vp, vp, vp]),
         "qpat_prior_solve": (ctypes.c_int, [vp, ctypes.POINTER(qpat_params), _c_double_p, _c_double_p, _c_double_p,
                                             _c_double_p]),
+        "qpat_batch_create": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(vp), ctypes.POINTER(ctypes.c_int),
+                                             ctypes.POINTER(qpat_params), ctypes.POINTER(vp)]),
+        "qpat_batch_buffers": (ctypes.c_int, [vp, ctypes.c_int, ctypes.POINTER(vp), ctypes.POINTER(vp),
+                                              ctypes.POINTER(vp), ctypes.POINTER(vp)]),
+        "qpat_batch_forward": (ctypes.c_int, [vp, vp]),
+        "qpat_batch_status": (ctypes.c_int, [vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                                             ctypes.POINTER(ctypes.c_int)]),
+        "qpat_batch_free": (None, [vp]),
+        "qpat_autotune": (ctypes.c_int, [_c_double_p, ctypes.c_int64, _c_int32_p, ctypes.c_int64, _c_double_p,
+                                         _c_double_p, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
+                                         ctypes.POINTER(ctypes.c_int), _c_double_p, ctypes.POINTER(ctypes.c_int)]),
         "qpat_prior_solve_dev": (ctypes.c_int, [vp, ctypes.POINTER(qpat_params), vp, vp, vp, vp, vp]),
         "qpat_reconstruct": (ctypes.c_int, [vp, ctypes.POINTER(qpat_params), ctypes.c_int, _c_double_p,
                                             _c_double_p, _c_double_p, _c_double_p, _c_double_p, _c_double_p,
@@ -128,8 +139,24 @@ def exported_names() -> Sequence[str]:
         "qpat_flux_patch", "qpat_apply_K_dev", "qpat_forward", "qpat_forward_dev", "qpat_forward_noalloc_dev",
         "qpat_jvp", "qpat_jvp_dev",
         "qpat_vjp", "qpat_vjp_dev", "qpat_jvp_vjp_pair_dev", "qpat_prior_solve", "qpat_prior_solve_dev",
-        "qpat_reconstruct",
+        "qpat_batch_create", "qpat_batch_buffers", "qpat_batch_forward", "qpat_batch_status", "qpat_batch_free",
+        "qpat_autotune", "qpat_reconstruct",
     ]
+
+
+def qpat_autotune(xyz, tets, kappa, mu, K: int, iters: int = 30):
+    """Best (patch_nodes, fp32_operator) for this mesh and K, and the timing
+    table {(patch_nodes, fp32_operator): microseconds per FP32 PCG iteration}."""
+    xyz = _f64(xyz)
+    tets = np.ascontiguousarray(tets, dtype=np.int32)
+    bp, bo, nc = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    us = np.zeros(16)
+    _check(load().qpat_autotune(_dp(xyz), xyz.shape[0], tets.ctypes.data_as(_c_int32_p), tets.shape[0],
+                                _dp(_f64(kappa)), _dp(_f64(mu)), int(K), int(iters), ctypes.byref(bp),
+                                ctypes.byref(bo), _dp(us), ctypes.byref(nc)))
+    cands = [0, 128, 256, 512, 1024]
+    table = {(c, op): float(us[2 * i + op]) for i, c in enumerate(cands) for op in (0, 1)}
+    return (bp.value, bo.value), table
 
 
 def _check(rc: int):
@@ -371,3 +398,68 @@ def qpat_prior_solve_dev(mesh: Mesh, kt, mt, rhs, out, params: Optional[qpat_par
     _check(load().qpat_prior_solve_dev(mesh.handle, _pp(params), _tp(kt), _tp(mt), _tp(rhs), _tp(out),
                                        _stream()))
     return out
+
+
+# ------------------------------------------------------------------ uneven batches
+
+class _DevArray:
+    """Zero-copy view of a library-owned float64 device buffer."""
+
+    def __init__(self, ptr: int, shape):
+        self.__cuda_array_interface__ = {"shape": tuple(shape), "typestr": "<f8", "data": (ptr, False),
+                                         "version": 3, "strides": None}
+
+
+class Batch:
+    """Owning wrapper of a qpat_batch_t: forward solves of several meshes in
+    one cooperative launch, replayed as a CUDA graph (see include/qpat.h)."""
+
+    def __init__(self, meshes, K, params: Optional[qpat_params] = None):
+        import torch
+        lib = load()
+        n = len(meshes)
+        arr = (ctypes.c_void_p * n)(*[m.handle for m in meshes])
+        ks = (ctypes.c_int * n)(*[int(k) for k in K])
+        h = ctypes.c_void_p()
+        _check(lib.qpat_batch_create(n, arr, ks, _pp(params), ctypes.byref(h)))
+        self.handle = h
+        self.meshes = list(meshes)
+        self.K = [int(k) for k in K]
+        self.views = []
+        for j, m in enumerate(meshes):
+            p = [ctypes.c_void_p() for _ in range(4)]
+            _check(lib.qpat_batch_buffers(h, j, *[ctypes.byref(x) for x in p]))
+            shapes = [(m.N,), (m.N,), (self.K[j], m.F), (self.K[j], m.N)]
+            self.views.append([torch.as_tensor(_DevArray(x.value, s), device="cuda") for x, s in zip(p, shapes)])
+
+    def inputs(self, j):
+        """(kappa, mu, flux) device tensors of problem j, to be filled in place."""
+        return tuple(self.views[j][:3])
+
+    def phi(self, j):
+        return self.views[j][3]
+
+    def forward(self):
+        _check(load().qpat_batch_forward(self.handle, _stream()))
+
+    def status(self):
+        n = len(self.meshes)
+        st, it, ct = (ctypes.c_int * n)(), (ctypes.c_int * n)(), (ctypes.c_int * n)()
+        _check(load().qpat_batch_status(self.handle, st, it, ct))
+        return list(st), list(it), list(ct)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            self.views = []
+            load().qpat_batch_free(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def qpat_batch_create(meshes, K, params: Optional[qpat_params] = None) -> Batch:
+    return Batch(meshes, K, params)

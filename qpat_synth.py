@@ -273,6 +273,22 @@ def small_config(n: int, L: float, K: int, seed: int) -> Config:
     return Config(f"cube{n}_K{K}", n, L, patches, spheres, seed=seed)
 
 
+def uneven_batch(count: int = 32, seed: int = 3000, nmin: int = 16, nmax: int = 48) -> List[Config]:
+    """Independent problems of uneven size: cubes of n ~ U{nmin..nmax} nodes
+    per side (L = 20 mm), K ~ U{1..4} face patches, 2-5 random spheres."""
+    rng = np.random.default_rng(seed)
+    faces = [(2, 1), (2, 0), (0, 1), (0, 0)]
+    out = []
+    for i in range(count):
+        n = int(rng.integers(nmin, nmax + 1))
+        K = int(rng.integers(1, 5))
+        L = 20.0
+        spheres = _random_spheres(rng, L, int(rng.integers(2, 6)), 2.0, 4.0)
+        out.append(Config(f"batch{i}_n{n}_K{K}", n, L, _face_patches(L, 5.0, faces[:K]), spheres,
+                          seed=seed + i))
+    return out
+
+
 def noise_draws(seed: int, shape) -> np.ndarray:
     """Standard normal draws for the measurement noise eta (Sec. 5, Test 1):
     chi = h + 0.01 |h| * xi with xi from here."""

@@ -1,0 +1,67 @@
+"""Uneven batch: forward solves of meshes of different sizes (and different
+illumination counts) in one cooperative launch replayed as a CUDA graph,
+against the per-mesh entry point and the oracle."""
+import numpy as np
+import pytest
+
+import oracle as O
+import qpat_synth as S
+from tests.gpu_common import rel
+
+torch = pytest.importorskip("torch")
+Q = pytest.importorskip("paper_1512_02796_gb300")
+
+pytestmark = pytest.mark.gpu
+
+SIZES = [(5, 1), (9, 3), (12, 2), (7, 4), (16, 1), (10, 4), (13, 3)]
+
+
+def test_uneven_batch_matches_single_solves():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    cfgs = [S.small_config(n, 2.0 * n, K, 100 + i) for i, (n, K) in enumerate(SIZES)]
+    meshes, data = [], []
+    for cfg in cfgs:
+        xyz, tets = cfg.mesh()
+        kap, mu = cfg.coefficients(xyz)
+        m = Q.qpat_mesh(xyz, tets, patch_nodes=64)
+        flux = np.stack([Q.qpat_flux_patch(m, p.center, p.normal, p.half_w, p.amp) for p in cfg.patches])
+        meshes.append(m)
+        data.append((xyz, tets, kap, mu, flux))
+    batch = Q.qpat_batch_create(meshes, [c.K for c in cfgs])
+    try:
+        for rep in range(3):
+            scale = 1.0 + 0.1 * rep          # new inputs on every replay of the same graph
+            for j, (xyz, tets, kap, mu, flux) in enumerate(data):
+                k, m_, f = batch.inputs(j)
+                k.copy_(torch.tensor(kap * scale))
+                m_.copy_(torch.tensor(mu))
+                f.copy_(torch.tensor(flux))
+            batch.forward()
+            torch.cuda.synchronize()
+            st, it, ct = batch.status()
+            assert all(s == 0 for s in st), st
+            assert all(c >= 1 for c in ct)
+            for j, (xyz, tets, kap, mu, flux) in enumerate(data):
+                ref, _ = Q.qpat_forward(meshes[j], kap * scale, mu, flux)
+                assert rel(batch.phi(j).cpu().numpy(), ref) < 1e-10
+                if rep == 0 and j < 3:
+                    om = O.Mesh(xyz, tets)
+                    phi_o, _ = O.forward(om, kap, mu, flux)
+                    assert rel(batch.phi(j).cpu().numpy(), phi_o) < 1e-10
+    finally:
+        batch.close()
+        for m in meshes:
+            m.close()
+
+
+def test_autotune_picks_a_measured_candidate():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    cfg = S.small_config(20, 20.0, 4, 7)
+    xyz, tets = cfg.mesh()
+    kap, mu = cfg.coefficients(xyz)
+    (pn, op), table = Q.qpat_autotune(xyz, tets, kap, mu, 4, iters=20)
+    finite = {k: v for k, v in table.items() if np.isfinite(v)}
+    assert len(finite) >= 6
+    assert (pn, op) in finite and finite[(pn, op)] == min(finite.values())
