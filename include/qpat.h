@@ -180,6 +180,14 @@ int qpat_forward_dev(qpat_mesh_t mesh, const qpat_params* prm, const double* kap
                      const double* mu, int K, const double* flux_face,
                      double* phi, double* h, void* stream);
 
+/* qpat_forward_dev started from an initial guess phi0 (K x N, caller order,
+ * device; NULL = zero), e.g. a learned prediction.  The solve stops at the
+ * same absolute residual |f - K phi| <= pcg_rtol |f| as from zero, so the
+ * guess changes only the work, not the accuracy. */
+int qpat_forward_guess_dev(qpat_mesh_t mesh, const qpat_params* prm, const double* kappa,
+                           const double* mu, int K, const double* flux_face,
+                           const double* phi0, double* phi, double* h, void* stream);
+
 /* Allocation-free forward solve, for callers that cannot allocate device
  * memory when they need the solve (code issued during CUDA graph capture,
  * real-time pipelines that forbid allocator calls after start-up, hosts that
@@ -236,6 +244,53 @@ int qpat_jvp_vjp_pair_dev(qpat_mesh_t mesh, const qpat_params* prm,
                           const double* phi, const double* w, const double* s,
                           const double* t, double* out_jv, double* out_vjp,
                           void* stream);
+
+/* ------------------------------------------------ learned initial guess */
+
+/* A 3D U-Net that predicts the fluence of one illumination on an n^3 Kuhn
+ * grid (node index = voxel index), used as the initial guess of
+ * qpat_forward_guess_dev.  Not in the paper: the forward solve it feeds is
+ * the Appendix's K^-1 f and still runs to the same tolerance.  Four levels
+ * with 16, 32, 64, 128 channels, two 3x3x3 ReLU convolutions per level,
+ * 2x2x2 average pooling, nearest upsampling with skip concatenation and a
+ * linear output convolution.  Every convolution, forward and backward, runs
+ * on hand-written BF16 tensor-core kernels (fp32 accumulation); Adam keeps
+ * fp32 master weights.  n must be a multiple of 16 in [32, 512].
+ * Features (qpat_unet_features_dev): per voxel [log(mu/0.01),
+ * log(kappa/0.33), f_k / h^2] with f_k the load vector of illumination k
+ * (2 integral Phi_k lambda_i) -- x is K x N x 3 float.
+ * predict: x (B x n^3 x 3 float) -> y (B x n^3 float).
+ * train: one Adam step on the mean-squared error of B samples (targets t,
+ * B x n^3 float, e.g. forward solutions); *loss (host, may be NULL) gets the
+ * mean loss before the step.  Device pointers, asynchronous on stream except
+ * when loss is requested.  Parameters: per convolution the fp32 weights
+ * [27][c_out][c_in] then the bias [c_out]. */
+typedef struct qpat_unet_s* qpat_unet_t;
+int qpat_unet_create(int n, uint64_t seed, qpat_unet_t* out);
+void qpat_unet_free(qpat_unet_t unet);
+int64_t qpat_unet_num_params(qpat_unet_t unet);
+int qpat_unet_get_params(qpat_unet_t unet, float* host);
+int qpat_unet_set_params(qpat_unet_t unet, const float* host);
+int qpat_unet_features_dev(qpat_mesh_t mesh, const double* kappa, const double* mu, int K,
+                           const double* flux_face, double h, float* x, void* stream);
+int qpat_unet_predict_dev(qpat_unet_t unet, const float* x, int B, float* y, void* stream);
+int qpat_unet_train_dev(qpat_unet_t unet, const float* x, const float* t, int B, float lr,
+                        float* loss, void* stream);
+/* y (float) -> out (double), count entries (the guess handed to the solve). */
+int qpat_unet_to_double_dev(const float* y, int64_t count, double* out, void* stream);
+
+/* The BF16 tensor-core 3x3x3 convolution of the U-Net on its own (tests and
+ * users of the kernels): in [n^3][Cin] bf16 (Cin % 16 == 0), w
+ * [27][Cout][Cin] bf16 (Cout % 8 == 0), bias fp32 (NULL = 0), zero padding;
+ * out bf16 [n^3][Cout], out_f32 (optional) the fp32 values before rounding.
+ * wgrad: dw [27][Cout][Cin] and db [Cout] (fp32) of that convolution for an
+ * output gradient dy [n^3][Cout] bf16 (Cin % 8 == 0, Cout % 16 == 0,
+ * n^3 % 16 == 0); partial: scratch of qpat_conv3d_bf16_wgrad_scratch floats. */
+int qpat_conv3d_bf16_dev(const void* in, int Cin, const void* w, const float* bias, int Cout,
+                         int relu, int n, void* out, float* out_f32, void* stream);
+int qpat_conv3d_bf16_wgrad_dev(const void* in, int Cin, const void* dy, int Cout, int n,
+                               float* dw, float* db, float* partial, void* stream);
+int64_t qpat_conv3d_bf16_wgrad_scratch(int n, int Cin, int Cout);
 
 /* ---------------------------------------------------------- autotuner */
 

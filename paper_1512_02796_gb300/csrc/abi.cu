@@ -107,6 +107,18 @@ int grid_of(int64_t n) {
 
 }  // namespace
 
+namespace {
+__global__ void k_add(int64_t n, const double* a, double* y) {
+    for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x)
+        y[i] += a[i];
+}
+}  // namespace
+
+cudaError_t launch_add(int64_t n, const double* a, double* y, cudaStream_t s) {
+    k_add<<<grid_of(n), 256, 0, s>>>(n, a, y);
+    return cudaGetLastError();
+}
+
 void k_mul_launch(int64_t n, const double* a, const double* b, double* out, cudaStream_t s) {
     k_mul<<<grid_of(n), 256, 0, s>>>(n, a, b, out);
 }
@@ -202,7 +214,7 @@ static int pcg_status(int st, const char* what) {
 // then sweeps of  r = B - A X (FP64 element apply), d = A32^-1 (r / |r|)
 // (FP32 PCG to a loose tolerance), X += |r| d,  until |r_j| <= rtol |B_j|.
 int solve(qpat_mesh_s* M, const OpState& st, const SolveOpts& so_in, int R, const double* B, double* X,
-          cudaStream_t s) {
+          cudaStream_t s, const double* X0) {
     // M_delta is solved in FP64 whatever the precision mode: its smallest
     // eigenvalue is delta (constant mode, 1e-6 below the rest) and the
     // lagged weights reach ~1e-5 across edges, beyond what an FP32 inner
@@ -227,6 +239,33 @@ int solve(qpat_mesh_s* M, const OpState& st, const SolveOpts& so_in, int R, cons
     w.stats = M->ws.get<double>("pcg.stats", 32, s, &e);
     double* hpin = M->host_scratch;  // pinned, >= 64 doubles
     if (e != cudaSuccess) return cuda_fail(e, "workspace");
+    if (so.precision == 0 && X0) {
+        // initial guess: solve A D = B - A X0 with D0 = 0 to the same absolute
+        // target |B - A X| <= rtol |B| (per RHS), then X = X0 + D
+        double* Bp = M->ws.get<double>(std::string(pfx) + ".b0", n, s, &e);
+        double* tmp = M->ws.get<double>(std::string(pfx) + ".t0", n, s, &e);
+        double* dpart = M->ws.get<double>("dots.partial", 608 * 16, s, &e);
+        double* dn = M->ws.get<double>(std::string(pfx) + ".n0", 64, s, &e);
+        if (e != cudaSuccess) return cuda_fail(e, "workspace");
+        if ((e = apply_op64(M, st, R, X0, tmp, s)) != cudaSuccess) return cuda_fail(e, "apply64");
+        if ((e = launch_sub(n, B, tmp, Bp, s)) != cudaSuccess) return cuda_fail(e, "sub");
+        if ((e = launch_dots<double>(N, R, B, B, dpart, dn, s)) != cudaSuccess ||
+            (e = launch_dots<double>(N, R, Bp, Bp, dpart, dn + 16, s)) != cudaSuccess)
+            return cuda_fail(e, "dots");
+        if ((e = cudaMemcpyAsync(hpin, dn, 32 * sizeof(double), cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
+            (e = cudaStreamSynchronize(s)) != cudaSuccess)
+            return cuda_fail(e, "copy");
+        double scale = INFINITY;
+        for (int r = 0; r < R; ++r)
+            if (hpin[16 + r] > 0.0) scale = std::min(scale, std::sqrt(hpin[r] / hpin[16 + r]));
+        if (!std::isfinite(scale)) scale = 1.0;
+        SolveOpts s2 = so;
+        s2.rtol = so.rtol * std::max(scale, 1.0);
+        int rc = solve(M, st, s2, R, Bp, X, s, nullptr);
+        if (rc != QPAT_OK) return rc;
+        if ((e = launch_add(n, X0, X, s)) != cudaSuccess) return cuda_fail(e, "add");
+        return QPAT_OK;
+    }
     if (so.precision == 0) {
         w.b = const_cast<double*>(B);
         w.x = X;
@@ -265,9 +304,17 @@ int solve(qpat_mesh_s* M, const OpState& st, const SolveOpts& so_in, int R, cons
     const int OP = so.fp32_assembled ? OP_CSR1 : OP_K;
     OpParams<float> op{st.c1_32, st.c2_32, float(st.inv_T2), float(st.scale1), float(st.delta), 1, st.v32[0],
                        nullptr};
-    if ((e = cudaMemsetAsync(X, 0, n * sizeof(double), s)) != cudaSuccess) return cuda_fail(e, "memset");
-    if ((e = cudaMemcpyAsync(Rres, B, n * sizeof(double), cudaMemcpyDeviceToDevice, s)) != cudaSuccess)
-        return cuda_fail(e, "copy");
+    if (X0) {
+        // start from the initial guess: X = X0, r = B - A X0
+        if ((e = cudaMemcpyAsync(X, X0, n * sizeof(double), cudaMemcpyDeviceToDevice, s)) != cudaSuccess)
+            return cuda_fail(e, "copy");
+        if ((e = apply_op64(M, st, R, X, tmp, s)) != cudaSuccess) return cuda_fail(e, "apply64");
+        if ((e = launch_sub(n, B, tmp, Rres, s)) != cudaSuccess) return cuda_fail(e, "sub");
+    } else {
+        if ((e = cudaMemsetAsync(X, 0, n * sizeof(double), s)) != cudaSuccess) return cuda_fail(e, "memset");
+        if ((e = cudaMemcpyAsync(Rres, B, n * sizeof(double), cudaMemcpyDeviceToDevice, s)) != cudaSuccess)
+            return cuda_fail(e, "copy");
+    }
     if ((e = launch_dots<double>(N, R, B, B, dpart, dnorm + 16, s)) != cudaSuccess) return cuda_fail(e, "dots");
     if ((e = cudaMemcpyAsync(hpin + 16, dnorm + 16, R * sizeof(double), cudaMemcpyDeviceToHost, s)) != cudaSuccess)
         return cuda_fail(e, "copy");

@@ -95,8 +95,11 @@ int prepare_K(qpat_mesh_s* M, const double* kap_l, const double* mu_l, OpState& 
               const char* tag = "opK");
 int prepare_prior(qpat_mesh_s* M, const double* kt_l, const double* mt_l, double T, double b_over_a, double delta,
                   OpState& st, cudaStream_t s);
+// X0 (optional): initial guess; the solve then stops at the same absolute
+// residual |B - A X| <= rtol |B| as from zero.
 int solve(qpat_mesh_s* M, const OpState& st, const SolveOpts& so, int R, const double* B, double* X,
-          cudaStream_t s);
+          cudaStream_t s, const double* X0 = nullptr);
+cudaError_t launch_add(int64_t n, const double* a, double* y, cudaStream_t s);  // y += a
 SolveOpts solve_opts(const qpat_params* prm);
 
 // node-major caller layout (x[c*R + r], r < R) <-> library N x Rp (zero padding)
@@ -129,7 +132,8 @@ int jvp_lib(qpat_mesh_s* M, const SolveOpts& so, LinState& L, const double* s1, 
             cudaStream_t s);
 int vjp_lib(qpat_mesh_s* M, const SolveOpts& so, LinState& L, const double* t, double* o1, double* o2,
             cudaStream_t s);
-int forward_lib(qpat_mesh_s* M, const SolveOpts& so, LinState& L, const double* flux_dev, cudaStream_t s);
+int forward_lib(qpat_mesh_s* M, const SolveOpts& so, LinState& L, const double* flux_dev, cudaStream_t s,
+                const double* x0 = nullptr);
 
 }  // namespace qpat
 

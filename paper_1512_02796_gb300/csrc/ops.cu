@@ -149,14 +149,15 @@ static int check_params(const qpat_params* prm, const char* who) {
     return QPAT_OK;
 }
 
-int forward_lib(qpat_mesh_s* M, const SolveOpts& so, LinState& L, const double* flux_dev, cudaStream_t s) {
+int forward_lib(qpat_mesh_s* M, const SolveOpts& so, LinState& L, const double* flux_dev, cudaStream_t s,
+                const double* x0) {
     const int64_t N = M->h.N;
     cudaError_t e = cudaSuccess;
     double* f = M->ws.get<double>("fw.f", N * L.R, s, &e);
     if (e != cudaSuccess) return cuda_fail(e, "workspace");
     if ((e = cudaMemsetAsync(f, 0, N * L.R * sizeof(double), s)) != cudaSuccess) return cuda_fail(e, "memset");
     if ((e = launch_load(M->d, L.K, L.R, flux_dev, f, s)) != cudaSuccess) return cuda_fail(e, "load");
-    return solve(M, L.opK, so, L.R, f, L.phi, s);
+    return solve(M, L.opK, so, L.R, f, L.phi, s, x0);
 }
 
 int jvp_lib(qpat_mesh_s* M, const SolveOpts& so, LinState& L, const double* s1, const double* s2, double* out,
@@ -268,6 +269,11 @@ extern "C" {
 
 int qpat_forward_dev(qpat_mesh_t M, const qpat_params* prm, const double* kappa, const double* mu, int K,
                      const double* flux_face, double* phi, double* h, void* stream) {
+    return qpat_forward_guess_dev(M, prm, kappa, mu, K, flux_face, nullptr, phi, h, stream);
+}
+
+int qpat_forward_guess_dev(qpat_mesh_t M, const qpat_params* prm, const double* kappa, const double* mu, int K,
+                           const double* flux_face, const double* phi0, double* phi, double* h, void* stream) {
     if (!M || !kappa || !mu || !flux_face) return fail(QPAT_EINVAL, "qpat_forward: NULL argument");
     if (K < 1 || round_rhs(K) < 0) return fail(QPAT_EINVAL, "qpat_forward: K must be in [1, 16]");
     int rc = check_params(prm, "qpat_forward");
@@ -277,7 +283,15 @@ int qpat_forward_dev(qpat_mesh_t M, const qpat_params* prm, const double* kappa,
     LinState L;
     if ((rc = lin_from_caller(M, kappa, mu, K, nullptr, nullptr, L, s))) return rc;
     SolveOpts so = solve_opts(prm);
-    if ((rc = forward_lib(M, so, L, flux_face, s))) return rc;
+    double* x0 = nullptr;
+    if (phi0) {
+        cudaError_t e0 = cudaSuccess;
+        x0 = M->ws.get<double>("fw.x0", M->h.N * L.R, s, &e0);
+        if (e0 != cudaSuccess) return cuda_fail(e0, "workspace");
+        if ((e0 = launch_to_lib<double, double>(M->d, K, L.R, phi0, x0, s)) != cudaSuccess)
+            return cuda_fail(e0, "to_lib");
+    }
+    if ((rc = forward_lib(M, so, L, flux_face, s, x0))) return rc;
     cudaError_t e = cudaSuccess;
     if (phi && (e = launch_from_lib<double, double>(M->d, K, L.R, L.phi, phi, s)) != cudaSuccess)
         return cuda_fail(e, "from_lib");

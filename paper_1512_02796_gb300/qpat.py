@@ -95,6 +95,8 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
         "qpat_forward_dev": (ctypes.c_int, [vp, ctypes.POINTER(qpat_params), vp, vp, ctypes.c_int, vp, vp, vp, vp]),
         "qpat_forward_noalloc_dev": (ctypes.c_int, [vp, vp, vp, ctypes.c_int, vp, ctypes.c_double, ctypes.c_int,
                                                     vp, vp, vp]),
+        "qpat_forward_guess_dev": (ctypes.c_int, [vp, ctypes.POINTER(qpat_params), vp, vp, ctypes.c_int, vp, vp,
+                                                  vp, vp, vp]),
         "qpat_jvp": (ctypes.c_int, [vp, ctypes.POINTER(qpat_params), _c_double_p, _c_double_p, ctypes.c_int,
                                     _c_double_p, _c_double_p, _c_double_p, _c_double_p]),
         "qpat_jvp_dev": (ctypes.c_int, [vp, ctypes.POINTER(qpat_params), vp, vp, ctypes.c_int, vp, vp, vp, vp, vp]),
@@ -113,6 +115,21 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
         "qpat_batch_status": (ctypes.c_int, [vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
                                              ctypes.POINTER(ctypes.c_int)]),
         "qpat_batch_free": (None, [vp]),
+        "qpat_unet_create": (ctypes.c_int, [ctypes.c_int, ctypes.c_uint64, ctypes.POINTER(vp)]),
+        "qpat_unet_free": (None, [vp]),
+        "qpat_unet_num_params": (ctypes.c_int64, [vp]),
+        "qpat_unet_get_params": (ctypes.c_int, [vp, ctypes.POINTER(ctypes.c_float)]),
+        "qpat_unet_set_params": (ctypes.c_int, [vp, ctypes.POINTER(ctypes.c_float)]),
+        "qpat_unet_features_dev": (ctypes.c_int, [vp, vp, vp, ctypes.c_int, vp, ctypes.c_double, vp, vp]),
+        "qpat_unet_predict_dev": (ctypes.c_int, [vp, vp, ctypes.c_int, vp, vp]),
+        "qpat_unet_train_dev": (ctypes.c_int, [vp, vp, vp, ctypes.c_int, ctypes.c_float,
+                                               ctypes.POINTER(ctypes.c_float), vp]),
+        "qpat_unet_to_double_dev": (ctypes.c_int, [vp, ctypes.c_int64, vp, vp]),
+        "qpat_conv3d_bf16_dev": (ctypes.c_int, [vp, ctypes.c_int, vp, vp, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                                vp, vp, vp]),
+        "qpat_conv3d_bf16_wgrad_dev": (ctypes.c_int, [vp, ctypes.c_int, vp, ctypes.c_int, ctypes.c_int, vp, vp, vp,
+                                                      vp]),
+        "qpat_conv3d_bf16_wgrad_scratch": (ctypes.c_int64, [ctypes.c_int, ctypes.c_int, ctypes.c_int]),
         "qpat_autotune": (ctypes.c_int, [_c_double_p, ctypes.c_int64, _c_int32_p, ctypes.c_int64, _c_double_p,
                                          _c_double_p, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
                                          ctypes.POINTER(ctypes.c_int), _c_double_p, ctypes.POINTER(ctypes.c_int)]),
@@ -137,11 +154,97 @@ def exported_names() -> Sequence[str]:
         "qpat_mesh_faces", "qpat_mesh_permutation", "qpat_mesh_stats", "qpat_mesh_reset_stats",
         "qpat_mesh_set_timing", "qpat_mesh_pcg_time",
         "qpat_flux_patch", "qpat_apply_K_dev", "qpat_forward", "qpat_forward_dev", "qpat_forward_noalloc_dev",
+        "qpat_forward_guess_dev",
         "qpat_jvp", "qpat_jvp_dev",
         "qpat_vjp", "qpat_vjp_dev", "qpat_jvp_vjp_pair_dev", "qpat_prior_solve", "qpat_prior_solve_dev",
         "qpat_batch_create", "qpat_batch_buffers", "qpat_batch_forward", "qpat_batch_status", "qpat_batch_free",
         "qpat_autotune", "qpat_reconstruct",
+        "qpat_unet_create", "qpat_unet_free", "qpat_unet_num_params", "qpat_unet_get_params", "qpat_unet_set_params",
+        "qpat_unet_features_dev", "qpat_unet_predict_dev", "qpat_unet_train_dev", "qpat_unet_to_double_dev",
+        "qpat_conv3d_bf16_dev", "qpat_conv3d_bf16_wgrad_dev", "qpat_conv3d_bf16_wgrad_scratch",
     ]
+
+
+class UNet:
+    """Owning wrapper of qpat_unet_t (see include/qpat.h)."""
+
+    def __init__(self, n: int, seed: int = 0):
+        h = ctypes.c_void_p()
+        _check(load().qpat_unet_create(int(n), int(seed), ctypes.byref(h)))
+        self.handle = h
+        self.n = int(n)
+
+    def num_params(self) -> int:
+        return int(load().qpat_unet_num_params(self.handle))
+
+    def get_params(self) -> np.ndarray:
+        out = np.empty(self.num_params(), dtype=np.float32)
+        _check(load().qpat_unet_get_params(self.handle, out.ctypes.data_as(ctypes.POINTER(ctypes.c_float))))
+        return out
+
+    def set_params(self, p):
+        p = np.ascontiguousarray(p, dtype=np.float32)
+        _check(load().qpat_unet_set_params(self.handle, p.ctypes.data_as(ctypes.POINTER(ctypes.c_float))))
+
+    def predict(self, x, y):
+        """x: (B, n^3, 3) float32 CUDA tensor -> y (B, n^3) float32."""
+        _check(load().qpat_unet_predict_dev(self.handle, _tpf(x), x.shape[0], _tpf(y), _stream()))
+        return y
+
+    def train_step(self, x, t, lr: float) -> float:
+        loss = ctypes.c_float()
+        _check(load().qpat_unet_train_dev(self.handle, _tpf(x), _tpf(t), x.shape[0], float(lr), ctypes.byref(loss),
+                                          _stream()))
+        return float(loss.value)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            load().qpat_unet_free(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _tpf(t):
+    """float32 / bf16 contiguous CUDA tensor pointer."""
+    if t is None:
+        return None
+    if not (t.is_cuda and t.is_contiguous()):
+        raise ValueError("device calls take contiguous CUDA tensors")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def qpat_unet_features_dev(mesh: Mesh, kappa, mu, flux, h: float, x):
+    K = flux.shape[0]
+    _check(load().qpat_unet_features_dev(mesh.handle, _tp(kappa), _tp(mu), K, _tp(flux), float(h), _tpf(x),
+                                         _stream()))
+    return x
+
+
+def qpat_unet_to_double_dev(y, out):
+    _check(load().qpat_unet_to_double_dev(_tpf(y), int(y.numel()), _tp(out), _stream()))
+    return out
+
+
+def qpat_conv3d_bf16_dev(x, w, bias, cout: int, relu: bool, n: int, out, out_f32=None):
+    cin = x.shape[-1]
+    _check(load().qpat_conv3d_bf16_dev(_tpf(x), int(cin), _tpf(w), _tpf(bias), int(cout), 1 if relu else 0, int(n),
+                                       _tpf(out), _tpf(out_f32), _stream()))
+    return out
+
+
+def qpat_conv3d_bf16_wgrad_dev(x, dy, n: int, dw, db, partial):
+    _check(load().qpat_conv3d_bf16_wgrad_dev(_tpf(x), int(x.shape[-1]), _tpf(dy), int(dy.shape[-1]), int(n),
+                                             _tpf(dw), _tpf(db), _tpf(partial), _stream()))
+    return dw, db
+
+
+def qpat_conv3d_bf16_wgrad_scratch(n: int, cin: int, cout: int) -> int:
+    return int(load().qpat_conv3d_bf16_wgrad_scratch(int(n), int(cin), int(cout)))
 
 
 def qpat_autotune(xyz, tets, kappa, mu, K: int, iters: int = 30):
@@ -360,6 +463,13 @@ def qpat_forward_dev(mesh: Mesh, kappa, mu, flux, phi, h, params: Optional[qpat_
     K = flux.shape[0]
     _check(load().qpat_forward_dev(mesh.handle, _pp(params), _tp(kappa), _tp(mu), K, _tp(flux), _tp(phi), _tp(h),
                                    _stream()))
+    return phi, h
+
+
+def qpat_forward_guess_dev(mesh: Mesh, kappa, mu, flux, phi0, phi, h, params: Optional[qpat_params] = None):
+    K = flux.shape[0]
+    _check(load().qpat_forward_guess_dev(mesh.handle, _pp(params), _tp(kappa), _tp(mu), K, _tp(flux), _tp(phi0),
+                                         _tp(phi), _tp(h), _stream()))
     return phi, h
 
 
