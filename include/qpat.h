@@ -73,7 +73,13 @@ typedef struct {
     int patch_nodes;       /* owned nodes per CTA patch (0 = library choice) */
     int fp32_operator;     /* FP32 inner operator of precision 1: 0 = matrix-free
                               element recomputation, 1 = assembled FP32 values */
-    int reserved[6];
+    int pcg_variant;       /* PCG on assembled operators: 0 = library choice (1),
+                              1 = two grid reductions per iteration (textbook
+                              order), 2 = one grid reduction per iteration
+                              (Chronopoulos-Gear recurrences; the same iterates
+                              in exact arithmetic, more vector traffic).
+                              Matrix-free FP32 runs always use 1. */
+    int reserved[5];
 } qpat_params;
 
 /* Report of qpat_reconstruct (Algorithm 1). */

@@ -237,6 +237,14 @@ int solve(qpat_mesh_s* M, const OpState& st, const SolveOpts& so_in, int R, cons
     w.status = M->ws.get<int>("pcg.status", 1, s, &e);
     w.iters = M->ws.get<int>("pcg.iters", 1, s, &e);
     w.stats = M->ws.get<double>("pcg.stats", 32, s, &e);
+    // single-reduction variant on the assembled operators
+    const bool single = so.single_reduction && (so.precision == 0 || so.fp32_assembled);
+    if (single) {
+        w.r1 = M->ws.get_bytes(nm("r1"), n * esz, s, &e);
+        w.s0 = M->ws.get_bytes(nm("s0"), n * esz, s, &e);
+        w.s1 = M->ws.get_bytes(nm("s1"), n * esz, s, &e);
+        w.w1 = M->ws.get_bytes(nm("w1"), n * esz, s, &e);
+    }
     double* hpin = M->host_scratch;  // pinned, >= 64 doubles
     if (e != cudaSuccess) return cuda_fail(e, "workspace");
     if (so.precision == 0 && X0) {
@@ -272,8 +280,9 @@ int solve(qpat_mesh_s* M, const OpState& st, const SolveOpts& so_in, int R, cons
         const int OP = st.kind == OP_K ? OP_CSR1 : OP_CSR2;
         OpParams<double> op{st.c1_64, st.c2_64, st.inv_T2, st.scale1, st.delta, 1, st.v64[0], st.v64[1]};
         if (M->timing) cudaEventRecord(M->ev0, s);
-        if ((e = launch_pcg<double>(M->d, OP, R, op, st.inv64, w, so.rtol, so.maxit, s, nullptr)) != cudaSuccess)
-            return cuda_fail(e, "pcg launch");
+        e = single ? launch_pcg1<double>(M->d, OP, R, op, st.inv64, w, so.rtol, so.maxit, s, nullptr)
+                   : launch_pcg<double>(M->d, OP, R, op, st.inv64, w, so.rtol, so.maxit, s, nullptr);
+        if (e != cudaSuccess) return cuda_fail(e, "pcg launch");
         if (M->timing) cudaEventRecord(M->ev1, s);
         int hst[2];
         if ((e = cudaMemcpyAsync(hst, w.status, sizeof(int), cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
@@ -335,9 +344,9 @@ int solve(qpat_mesh_s* M, const OpState& st, const SolveOpts& so_in, int R, cons
         k_sqrt_vec<<<1, 32, 0, s>>>(R, dnorm, dnorm + 32);
         if ((e = launch_cast_d2f_scaled(N, R, Rres, dnorm + 32, b32, s)) != cudaSuccess) return cuda_fail(e, "cast");
         if (M->timing) cudaEventRecord(M->ev0, s);
-        if ((e = launch_pcg<float>(M->d, OP, R, op, st.inv32, w, so.inner_rtol, so.maxit, s, nullptr)) !=
-            cudaSuccess)
-            return cuda_fail(e, "pcg32 launch");
+        e = single ? launch_pcg1<float>(M->d, OP, R, op, st.inv32, w, so.inner_rtol, so.maxit, s, nullptr)
+                   : launch_pcg<float>(M->d, OP, R, op, st.inv32, w, so.inner_rtol, so.maxit, s, nullptr);
+        if (e != cudaSuccess) return cuda_fail(e, "pcg32 launch");
         if (M->timing) cudaEventRecord(M->ev1, s);
         int hst[2];
         if ((e = cudaMemcpyAsync(hst, w.status, sizeof(int), cudaMemcpyDeviceToHost, s)) != cudaSuccess ||

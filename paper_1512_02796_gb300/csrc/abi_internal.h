@@ -51,6 +51,7 @@ struct SolveOpts {
     double inner_rtol = 1e-4;
     int max_sweeps = 30;
     int fp32_assembled = 0;   // FP32 inner operator: 0 matrix-free elements, 1 assembled values
+    int single_reduction = 0; // assembled operators: Chronopoulos-Gear PCG (one grid reduction)
 };
 
 struct DeviceGuard {

@@ -70,6 +70,11 @@ struct PcgWork {
     void* p0;
     void* p1;
     void* q;
+    // extra vectors of the single-reduction variant (see pcg.cu)
+    void* r1 = nullptr;
+    void* s0 = nullptr;
+    void* s1 = nullptr;
+    void* w1 = nullptr;
     double* partials;   // 2 x max_grid x 3R
     unsigned* bar;      // 2
     int* status;        // 1
@@ -82,6 +87,11 @@ struct PcgWork {
 template <typename T>
 cudaError_t launch_pcg(const MeshDev& m, int OP, int R, const OpParams<T>& op, const T* invdiag,
                        const PcgWork& w, double rtol, int maxit, cudaStream_t s, int* grid_used);
+// Single-reduction (Chronopoulos-Gear) PCG for the assembled operators
+// (OP_CSR1 / OP_CSR2): one grid barrier per iteration; needs w.r1, s0, s1, w1.
+template <typename T>
+cudaError_t launch_pcg1(const MeshDev& m, int OP, int R, const OpParams<T>& op, const T* invdiag,
+                        const PcgWork& w, double rtol, int maxit, cudaStream_t s, int* grid_used);
 
 // Many independent FP64 assembled-K solves (different meshes) in one
 // cooperative launch; see k_pcg_batch in pcg.cu.

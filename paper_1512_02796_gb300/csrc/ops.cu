@@ -139,6 +139,7 @@ SolveOpts solve_opts(const qpat_params* prm) {
     so.rtol = p->pcg_rtol > 0 ? p->pcg_rtol : 1e-13;
     so.maxit = p->max_pcg_iter > 0 ? p->max_pcg_iter : 20000;
     so.fp32_assembled = p->fp32_operator == 1 ? 1 : 0;
+    so.single_reduction = p->pcg_variant == 2 ? 1 : 0;
     return so;
 }
 
@@ -146,6 +147,8 @@ static int check_params(const qpat_params* prm, const char* who) {
     if (!prm) return QPAT_OK;
     if (prm->precision != 0 && prm->precision != 1)
         return fail(QPAT_EINVAL, std::string(who) + ": precision must be 0 or 1");
+    if (prm->pcg_variant < 0 || prm->pcg_variant > 2)
+        return fail(QPAT_EINVAL, std::string(who) + ": pcg_variant must be 0, 1 or 2");
     return QPAT_OK;
 }
 

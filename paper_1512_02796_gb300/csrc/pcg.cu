@@ -49,6 +49,10 @@ struct PcgArgs {
     double rtol2;
     int maxit;
     long long spin_limit;
+    T* r1;  // single-reduction variant
+    T* s0;
+    T* s1;
+    T* w1;
 };
 
 constexpr int kMaxGrid = 152 * 8;
@@ -123,6 +127,46 @@ __device__ __forceinline__ void dinv_vec(const T* invdiag, int g, int r0, T (&d)
     }
 }
 
+// (A x) of owned row g for this thread's right-hand sides [r0, r0 + VW),
+// x staged in shared memory (touched x R).  The row's column ids and values
+// are fetched kChunk at a time into registers before any is used, so that
+// kChunk independent loads per thread are in flight at once (a thread-per-row
+// loop that consumes each entry as it arrives waits one memory latency per
+// entry).  Entries past the row length are not loaded.
+constexpr int kChunk = 8;
+constexpr int kUnroll = 2;  // touched nodes a thread stages at once
+template <typename T, int R, int VW, int OP>
+__device__ __forceinline__ void sell_row(const MeshDev& m, const OpParams<T>& op, const T* xs, int g, int r0,
+                                         T (&acc)[VW]) {
+    constexpr int NL = OP == OP_CSR2 ? VW : 1;  // distinct value sets this thread reads
+    const int64_t base = m.sell_ptr[g >> 5] * 32 + (g & 31);
+    const int len = m.sell_len[g];
+    const T* vp[NL];
+#pragma unroll
+    for (int q = 0; q < NL; ++q) vp[q] = (OP == OP_CSR2 && r0 + q == 1) ? op.v1 : op.v0;
+#pragma unroll
+    for (int c = 0; c < VW; ++c) acc[c] = T(0);
+    for (int k0 = 0; k0 < len; k0 += kChunk) {
+        int col[kChunk];
+        T v[kChunk][NL];
+#pragma unroll
+        for (int j = 0; j < kChunk; ++j) {
+            const int64_t idx = base + int64_t(k0 + j) * 32;
+            const bool ok = k0 + j < len;
+            col[j] = ok ? int(__ldg(m.sell_col + idx)) : 0;
+#pragma unroll
+            for (int q = 0; q < NL; ++q) v[j][q] = ok ? __ldg(vp[q] + idx) : T(0);
+        }
+#pragma unroll
+        for (int j = 0; j < kChunk; ++j) {
+            T xv[VW];
+            vld(xs + col[j] * R + r0, xv);
+#pragma unroll
+            for (int c = 0; c < VW; ++c) acc[c] += v[j][NL == 1 ? 0 : c] * xv[c];
+        }
+    }
+}
+
 // ---------------------------------------------------------------- grid reduction
 // Sum over the grid of NQ x R values; thread t holds acc[q][c] for RHS
 // (t % NP) * VW + c.  Totals land in out[q * R + r] (shared) in every CTA.
@@ -170,8 +214,17 @@ __device__ __forceinline__ bool grid_reduce(double (&acc)[NQ][VW], double* scrat
         // the last CTA adds the partials of every CTA in a fixed order
         __threadfence();
         for (int s = warp; s < NS; s += nw) {
-            double a = 0.0;
-            for (int j = lane; j < ncta; j += 32) a += __ldcg(part + size_t(j) * NS + s);
+            // four independent chains keep four loads per lane in flight
+            double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+            int j = lane;
+            for (; j + 96 < ncta; j += 128) {
+                a0 += __ldcg(part + size_t(j) * NS + s);
+                a1 += __ldcg(part + size_t(j + 32) * NS + s);
+                a2 += __ldcg(part + size_t(j + 64) * NS + s);
+                a3 += __ldcg(part + size_t(j + 96) * NS + s);
+            }
+            for (; j < ncta; j += 32) a0 += __ldcg(part + size_t(j) * NS + s);
+            double a = (a0 + a1) + (a2 + a3);
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
             if (lane == 0) res[s] = a;
@@ -297,23 +350,27 @@ __device__ __forceinline__ void pcg_body(const PcgArgs<T>& a, const int cta, con
             const int nb = __ldg(m.node_ptr + p), nt = __ldg(m.node_ptr + p + 1) - nb;
             const int ob = __ldg(m.own_begin + p), nown = __ldg(m.own_begin + p + 1) - ob;
             if constexpr (!kCsr) stage_static<T, R>(m, nb, nt, s, a.op);
-            for (int i = threadIdx.x; i < nt * NP; i += blockDim.x) {
-                const int li = i / NP;
-                const int g = __ldg(m.nodes + nb + li);
-                const size_t e = size_t(g) * R + r0;
-                T rv[VW], d[VW], pv[VW];
-                vld_cg(a.r + e, rv);
-                dinv_vec<T, VW, OP>(a.invdiag, g, r0, d);
-                if (it > 0) {
-                    T po[VW];
-                    vld_cg(pp + e, po);
+            // kUnroll touched nodes per thread in flight (a spare slot repeats the first node)
+            for (int i0 = threadIdx.x; i0 < nt * NP; i0 += kUnroll * blockDim.x) {
+                int li[kUnroll];
+                T rv[kUnroll][VW], d[kUnroll][VW], po[kUnroll][VW];
 #pragma unroll
-                    for (int c = 0; c < VW; ++c) pv[c] = d[c] * rv[c] + bt[c] * po[c];
-                } else {
-#pragma unroll
-                    for (int c = 0; c < VW; ++c) pv[c] = d[c] * rv[c];
+                for (int u = 0; u < kUnroll; ++u) {
+                    const int i = i0 + u * blockDim.x;
+                    li[u] = (i < nt * NP ? i : i0) / NP;
+                    const int g = __ldg(m.nodes + nb + li[u]);
+                    const size_t e = size_t(g) * R + r0;
+                    vld_cg(a.r + e, rv[u]);
+                    dinv_vec<T, VW, OP>(a.invdiag, g, r0, d[u]);
+                    if (it > 0) vld_cg(pp + e, po[u]);
                 }
-                vst(s.xin + li * R + r0, pv);
+#pragma unroll
+                for (int u = 0; u < kUnroll; ++u) {
+                    T pv[VW];
+#pragma unroll
+                    for (int c = 0; c < VW; ++c) pv[c] = d[u][c] * rv[u][c] + (it > 0 ? bt[c] * po[u][c] : T(0));
+                    if (u == 0 || i0 + u * int(blockDim.x) < nt * NP) vst(s.xin + li[u] * R + r0, pv);
+                }
             }
             if constexpr (!kCsr)
                 for (int i = threadIdx.x; i < nown * R; i += blockDim.x) s.yout[i] = T(0);
@@ -323,27 +380,8 @@ __device__ __forceinline__ void pcg_body(const PcgArgs<T>& a, const int cta, con
                 for (int i = threadIdx.x; i < nown * NP; i += blockDim.x) {
                     const int li = i / NP;
                     const int g = ob + li;
-                    const int64_t base = m.sell_ptr[g >> 5] * 32 + (g & 31);
-                    const int len = m.sell_len[g];
                     T acc[VW];
-#pragma unroll
-                    for (int c = 0; c < VW; ++c) acc[c] = T(0);
-                    for (int k = 0; k < len; ++k) {
-                        const int64_t idx = base + int64_t(k) * 32;
-                        const int col = m.sell_col[idx];
-                        T xv[VW];
-                        vld(s.xin + col * R + r0, xv);
-                        if constexpr (OP == OP_CSR1) {
-                            const T v = __ldg(a.op.v0 + idx);
-#pragma unroll
-                            for (int c = 0; c < VW; ++c) acc[c] += v * xv[c];
-                        } else {
-                            // two blocks, one value set each (R = 2)
-#pragma unroll
-                            for (int c = 0; c < VW; ++c)
-                                acc[c] += __ldg(((r0 + c) == 0 ? a.op.v0 : a.op.v1) + idx) * xv[c];
-                        }
-                    }
+                    sell_row<T, R, VW, OP>(m, a.op, s.xin, g, r0, acc);
                     T pv[VW];
                     vld(s.xin + li * R + r0, pv);
                     const size_t e = size_t(g) * R + r0;
@@ -440,9 +478,254 @@ __device__ __forceinline__ void pcg_body(const PcgArgs<T>& a, const int cta, con
     }
 }
 
+// single-reduction kernel on assembled operators: at least 4 resident CTAs
+// per SM (a 64-register cap; uncapped it needs ~100 and halves the grid)
+template <int OP>
+constexpr int min_ctas() {
+    return (OP == OP_CSR1 || OP == OP_CSR2) ? 4 : 1;
+}
+
 template <typename T, int R, int OP>
 __global__ void __launch_bounds__(kThreads) k_pcg(PcgArgs<T> a) {
     pcg_body<T, R, OP>(a, blockIdx.x, gridDim.x);
+}
+
+// ---------------------------------------------------------------- single-reduction variant
+// Chronopoulos-Gear form of the same Jacobi-PCG (assembled operators only):
+// with u = D^-1 r, w = A u and s = A p kept by recurrence,
+//   x += alpha p,  r -= alpha s,  u = D^-1 r,  w = A u,
+//   gamma = r.u,  delta = w.u   (one grid reduction per iteration),
+//   beta = gamma / gamma_old,  alpha = gamma / (delta - beta gamma / alpha_old),
+//   p = u + beta p,  s = w + beta s.
+// r, s and w are read on the halo and double-buffered; every CTA updates s
+// and r redundantly on its touched nodes from the previous w, s and r, so the
+// new u is staged without a second barrier.  In exact arithmetic the iterates
+// equal those of pcg_body.
+template <typename T, int R, int OP>
+__device__ __forceinline__ void pcg1_body(const PcgArgs<T>& a, const int cta, const int ncta) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    constexpr int VW = vec_width<T, R, true>();
+    constexpr int NP = R / VW;
+    T* su = reinterpret_cast<T*>(smem_raw);  // touched x R: the new u
+    __shared__ double scratch[(kThreads / 32) * kMaxNS];
+    __shared__ double red[kMaxNS];
+    __shared__ double bb[R], gam[R], alpha[R], beta[R], rr[R];
+    __shared__ int s_flag;
+
+    const MeshDev& m = a.m;
+    const int P = m.P;
+    const int part = threadIdx.x % NP;
+    const int r0 = part * VW;
+    int red_id = 0;
+    T* const u = a.p1;  // owned u
+    T* const p = a.p0;  // owned p
+
+    // ---- start: x = 0, r = b, u = D^-1 b, w = A u; gamma, delta, |b|^2
+    {
+        double acc[3][VW];
+#pragma unroll
+        for (int c = 0; c < VW; ++c) acc[0][c] = acc[1][c] = acc[2][c] = 0.0;
+        for (int pt = cta; pt < P; pt += ncta) {
+            const int nb = __ldg(m.node_ptr + pt), nt = __ldg(m.node_ptr + pt + 1) - nb;
+            const int ob = __ldg(m.own_begin + pt), nown = __ldg(m.own_begin + pt + 1) - ob;
+            for (int i = threadIdx.x; i < nt * NP; i += blockDim.x) {
+                const int li = i / NP;
+                const int g = __ldg(m.nodes + nb + li);
+                T bv[VW], d[VW], uv[VW];
+                vld(a.b + size_t(g) * R + r0, bv);
+                dinv_vec<T, VW, OP>(a.invdiag, g, r0, d);
+#pragma unroll
+                for (int c = 0; c < VW; ++c) uv[c] = d[c] * bv[c];
+                vst(su + li * R + r0, uv);
+            }
+            __syncthreads();
+            for (int i = threadIdx.x; i < nown * NP; i += blockDim.x) {
+                const int li = i / NP, g = ob + li;
+                const size_t e = size_t(g) * R + r0;
+                T wv[VW], uv[VW], bv[VW], zero[VW];
+                sell_row<T, R, VW, OP>(m, a.op, su, g, r0, wv);
+                vld(su + li * R + r0, uv);
+                vld(a.b + e, bv);
+#pragma unroll
+                for (int c = 0; c < VW; ++c) {
+                    zero[c] = T(0);
+                    acc[0][c] += double(bv[c]) * double(uv[c]);
+                    acc[1][c] += double(wv[c]) * double(uv[c]);
+                    acc[2][c] += double(bv[c]) * double(bv[c]);
+                }
+                vst(a.q + e, wv);
+                vst(u + e, uv);
+                vst(a.r + e, bv);
+                vst(a.x + e, zero);
+            }
+            __syncthreads();
+        }
+        // r = b, so |r|^2 = |b|^2
+        if (!grid_reduce<3, VW, NP>(acc, scratch, a.partials, red_id, a.bar, a.status, a.spin_limit, red, cta, ncta))
+            return;
+        if (threadIdx.x == 0) {
+            int bad = 0;
+            for (int r = 0; r < R; ++r) {
+                gam[r] = red[r];
+                rr[r] = red[2 * R + r];
+                bb[r] = rr[r];
+                const bool act = rr[r] > a.rtol2 * bb[r];
+                const double dl = red[R + r];
+                if (act && !(dl > 0.0 && isfinite(dl))) bad = 1;
+                alpha[r] = act && dl > 0.0 ? gam[r] / dl : 0.0;
+                beta[r] = 0.0;
+            }
+            s_flag = bad;
+        }
+        __syncthreads();
+        if (s_flag) {
+            if (cta == 0 && threadIdx.x == 0) atomicCAS(a.status, 0, QPAT_EBREAKDOWN);
+            return;
+        }
+    }
+
+    int it = 0;
+    for (;;) {
+        if (threadIdx.x == 0) {
+            int any = 0;
+            for (int r = 0; r < R; ++r) any |= (rr[r] > a.rtol2 * bb[r]) ? 1 : 0;
+            s_flag = any;
+        }
+        __syncthreads();
+        if (!s_flag) break;
+        if (it >= a.maxit) {
+            if (cta == 0 && threadIdx.x == 0) atomicCAS(a.status, 0, QPAT_ENOCONV);
+            break;
+        }
+        // double buffers by iteration parity (r, w: current / next; s: current / previous)
+        const bool odd = it & 1;
+        const T* rcur = odd ? a.r1 : a.r;
+        T* rnew = odd ? a.r : a.r1;
+        const T* wcur = odd ? a.w1 : a.q;
+        T* wnew = odd ? a.q : a.w1;
+        const T* sold = odd ? a.s0 : a.s1;
+        T* scur = odd ? a.s1 : a.s0;
+        T al[VW], bt[VW];
+#pragma unroll
+        for (int c = 0; c < VW; ++c) {
+            al[c] = T(alpha[r0 + c]);
+            bt[c] = T(beta[r0 + c]);
+        }
+        double acc[3][VW];
+#pragma unroll
+        for (int c = 0; c < VW; ++c) acc[0][c] = acc[1][c] = acc[2][c] = 0.0;
+        for (int pt = cta; pt < P; pt += ncta) {
+            const int nb = __ldg(m.node_ptr + pt), nt = __ldg(m.node_ptr + pt + 1) - nb;
+            const int ob = __ldg(m.own_begin + pt), nown = __ldg(m.own_begin + pt + 1) - ob;
+            // s = w + beta s_old, r_new = r - alpha s, u_new = D^-1 r_new on the touched nodes
+            for (int i0 = threadIdx.x; i0 < nt * NP; i0 += kUnroll * blockDim.x) {
+                int li[kUnroll];
+                size_t e[kUnroll];
+                T wv[kUnroll][VW], rv[kUnroll][VW], sv[kUnroll][VW], d[kUnroll][VW];
+#pragma unroll
+                for (int u = 0; u < kUnroll; ++u) {
+                    const int i = i0 + u * blockDim.x;
+                    li[u] = (i < nt * NP ? i : i0) / NP;
+                    const int g = __ldg(m.nodes + nb + li[u]);
+                    e[u] = size_t(g) * R + r0;
+                    vld_cg(wcur + e[u], wv[u]);
+                    vld_cg(rcur + e[u], rv[u]);
+                    if (it > 0) vld_cg(sold + e[u], sv[u]);
+                    dinv_vec<T, VW, OP>(a.invdiag, g, r0, d[u]);
+                }
+#pragma unroll
+                for (int u = 0; u < kUnroll; ++u) {
+                    if (u > 0 && i0 + u * int(blockDim.x) >= nt * NP) break;
+                    T un[VW];
+#pragma unroll
+                    for (int c = 0; c < VW; ++c) {
+                        sv[u][c] = wv[u][c] + (it > 0 ? bt[c] * sv[u][c] : T(0));
+                        rv[u][c] -= al[c] * sv[u][c];
+                        un[c] = d[u][c] * rv[u][c];
+                    }
+                    vst(su + li[u] * R + r0, un);
+                    if (li[u] < nown) {
+                        vst(scur + e[u], sv[u]);
+                        vst(rnew + e[u], rv[u]);
+                    }
+                }
+            }
+            __syncthreads();
+            // owned rows: w_new = A u_new; p = u + beta p; x += alpha p
+            for (int i = threadIdx.x; i < nown * NP; i += blockDim.x) {
+                const int li = i / NP, g = ob + li;
+                const size_t e = size_t(g) * R + r0;
+                T wv[VW], un[VW], rn[VW], uo[VW], pv[VW], xv[VW];
+                sell_row<T, R, VW, OP>(m, a.op, su, g, r0, wv);
+                vld(su + li * R + r0, un);
+                vld(rnew + e, rn);
+                vld(u + e, uo);
+                vld(a.x + e, xv);
+                if (it > 0) {
+                    vld(p + e, pv);
+#pragma unroll
+                    for (int c = 0; c < VW; ++c) pv[c] = uo[c] + bt[c] * pv[c];
+                } else {
+#pragma unroll
+                    for (int c = 0; c < VW; ++c) pv[c] = uo[c];
+                }
+#pragma unroll
+                for (int c = 0; c < VW; ++c) {
+                    xv[c] += al[c] * pv[c];
+                    acc[0][c] += double(rn[c]) * double(un[c]);
+                    acc[1][c] += double(wv[c]) * double(un[c]);
+                    acc[2][c] += double(rn[c]) * double(rn[c]);
+                }
+                vst(p + e, pv);
+                vst(a.x + e, xv);
+                vst(u + e, un);
+                vst(wnew + e, wv);
+            }
+            __syncthreads();
+        }
+        if (!grid_reduce<3, VW, NP>(acc, scratch, a.partials, red_id, a.bar, a.status, a.spin_limit, red, cta, ncta))
+            return;
+        if (threadIdx.x == 0) {
+            int bad = 0;
+            for (int r = 0; r < R; ++r) {
+                const bool act = rr[r] > a.rtol2 * bb[r];
+                if (!act) {
+                    alpha[r] = beta[r] = 0.0;
+                    continue;
+                }
+                rr[r] = red[2 * R + r];
+                if (!(rr[r] > a.rtol2 * bb[r])) {
+                    // converged now: x holds the final iterate, freeze it
+                    alpha[r] = beta[r] = 0.0;
+                    continue;
+                }
+                const double gn = red[r], dn = red[R + r];
+                const double b_ = gn / gam[r];
+                const double den = dn - b_ * gn / alpha[r];
+                if (!(den > 0.0 && isfinite(den) && isfinite(gn))) bad = 1;
+                beta[r] = b_;
+                alpha[r] = den > 0.0 ? gn / den : 0.0;
+                gam[r] = gn;
+            }
+            s_flag = bad;
+        }
+        __syncthreads();
+        if (s_flag) {
+            if (cta == 0 && threadIdx.x == 0) atomicCAS(a.status, 0, QPAT_EBREAKDOWN);
+            break;
+        }
+        ++it;
+    }
+    if (cta == 0 && threadIdx.x < R) {
+        a.stats[threadIdx.x] = rr[threadIdx.x];
+        a.stats[R + threadIdx.x] = bb[threadIdx.x];
+        if (threadIdx.x == 0) *a.iters = it;
+    }
+}
+
+template <typename T, int R, int OP>
+__global__ void __launch_bounds__(kThreads, min_ctas<OP>()) k_pcg1(PcgArgs<T> a) {
+    pcg1_body<T, R, OP>(a, blockIdx.x, gridDim.x);
 }
 
 // Independent problems (meshes of different sizes) in one cooperative
@@ -556,12 +839,16 @@ cudaError_t batch_launch_t(const PcgBatchPlan& plan, cudaStream_t s) {
     return cudaLaunchCooperativeKernel((void*)kern, dim3(plan.grid), dim3(kThreads), args, plan.smem, s);
 }
 
-template <typename T, int R, int OP>
+template <typename T, int R, int OP, bool kSingle = false>
 cudaError_t launch_pcg_t(const MeshDev& m, const OpParams<T>& op, const T* invdiag, const PcgWork& w,
                          double rtol, int maxit, cudaStream_t s, int* grid_used) {
     const size_t smem = (OP == OP_CSR1 || OP == OP_CSR2) ? sizeof(T) * size_t(m.max_touched) * R
                                                          : PatchSmem<T, R>::bytes(m.max_touched, m.max_own);
-    auto kern = k_pcg<T, R, OP>;
+    void (*kern)(PcgArgs<T>) = nullptr;
+    if constexpr (kSingle)
+        kern = k_pcg1<T, R, OP>;
+    else
+        kern = k_pcg<T, R, OP>;
     cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
     if (err != cudaSuccess) return err;
     int dev = 0, nsm = 0, per_sm = 0;
@@ -594,6 +881,11 @@ cudaError_t launch_pcg_t(const MeshDev& m, const OpParams<T>& op, const T* invdi
     a.rtol2 = rtol * rtol;
     a.maxit = maxit;
     a.spin_limit = 40000000LL;  // about 2 s of __nanosleep(32) spins
+    a.r1 = static_cast<T*>(w.r1);
+    a.s0 = static_cast<T*>(w.s0);
+    a.s1 = static_cast<T*>(w.s1);
+    a.w1 = static_cast<T*>(w.w1);
+    if (kSingle && !(a.r1 && a.s0 && a.s1 && a.w1)) return cudaErrorInvalidValue;
     err = cudaMemsetAsync(w.bar, 0, 2 * sizeof(unsigned), s);
     if (err != cudaSuccess) return err;
     err = cudaMemsetAsync(w.status, 0, sizeof(int), s);
@@ -666,6 +958,28 @@ cudaError_t launch_pcg(const MeshDev& m, int OP, int R, const OpParams<T>& op, c
     }
 }
 
+template <typename T>
+cudaError_t launch_pcg1(const MeshDev& m, int OP, int R, const OpParams<T>& op, const T* invdiag,
+                        const PcgWork& w, double rtol, int maxit, cudaStream_t s, int* grid_used) {
+    if (OP == OP_CSR2) {
+        if (R != 2) return cudaErrorInvalidValue;
+        return launch_pcg_t<T, 2, OP_CSR2, true>(m, op, invdiag, w, rtol, maxit, s, grid_used);
+    }
+    if (OP != OP_CSR1) return cudaErrorInvalidValue;
+    switch (R) {
+        case 1: return launch_pcg_t<T, 1, OP_CSR1, true>(m, op, invdiag, w, rtol, maxit, s, grid_used);
+        case 2: return launch_pcg_t<T, 2, OP_CSR1, true>(m, op, invdiag, w, rtol, maxit, s, grid_used);
+        case 4: return launch_pcg_t<T, 4, OP_CSR1, true>(m, op, invdiag, w, rtol, maxit, s, grid_used);
+        case 8: return launch_pcg_t<T, 8, OP_CSR1, true>(m, op, invdiag, w, rtol, maxit, s, grid_used);
+        case 16: return launch_pcg_t<T, 16, OP_CSR1, true>(m, op, invdiag, w, rtol, maxit, s, grid_used);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+template cudaError_t launch_pcg1<double>(const MeshDev&, int, int, const OpParams<double>&, const double*,
+                                         const PcgWork&, double, int, cudaStream_t, int*);
+template cudaError_t launch_pcg1<float>(const MeshDev&, int, int, const OpParams<float>&, const float*,
+                                        const PcgWork&, double, int, cudaStream_t, int*);
 template cudaError_t launch_pcg<double>(const MeshDev&, int, int, const OpParams<double>&, const double*,
                                         const PcgWork&, double, int, cudaStream_t, int*);
 template cudaError_t launch_pcg<float>(const MeshDev&, int, int, const OpParams<float>&, const float*,

@@ -63,9 +63,11 @@ def test_apply_K(case, precision, tol, R):
     assert rel(yt.cpu().numpy(), y_ref) < tol
 
 
-@pytest.mark.parametrize("precision,fp32_op", [(0, 0), (1, 0), (1, 1)])
-def test_forward(case, precision, fp32_op):
-    phi, h = Q.qpat_forward(case.lib, case.kappa, case.mu, case.flux, _params(precision, fp32_operator=fp32_op))
+# pcg_variant 1: two grid reductions per PCG iteration, 2: one (Chronopoulos-Gear)
+@pytest.mark.parametrize("precision,fp32_op,variant", [(0, 0, 1), (0, 0, 2), (1, 0, 1), (1, 1, 1), (1, 1, 2)])
+def test_forward(case, precision, fp32_op, variant):
+    phi, h = Q.qpat_forward(case.lib, case.kappa, case.mu, case.flux,
+                            _params(precision, fp32_operator=fp32_op, pcg_variant=variant))
     assert rel(phi, case.phi) < 1e-10
     assert rel(h, case.h) < 1e-10
 
@@ -116,8 +118,9 @@ def test_pair_matches_separate_calls(case):
     assert rel(ov.cpu().numpy(), O.vjp(case.om, case.kappa, case.mu, case.phi, t, case.w, case.fac)) < 1e-10
 
 
+@pytest.mark.parametrize("variant", [1, 2])
 @pytest.mark.parametrize("precision", [0, 1])
-def test_prior_solve(case, precision):
+def test_prior_solve(case, precision, variant):
     rng = np.random.default_rng(9)
     N = case.N
     kt = 0.3 * rng.standard_normal(N)
@@ -126,7 +129,7 @@ def test_prior_solve(case, precision):
     T, ba, delta = 1e-2, 0.7, 1e-6
     Md = O.prior_matrix(case.om, kt, mt, T, ba, delta)
     ref = O.Factor(Md).solve(rhs)
-    p = _params(precision, T=T, b_over_a=ba, delta=delta, pcg_rtol=1e-13)
+    p = _params(precision, T=T, b_over_a=ba, delta=delta, pcg_rtol=1e-13, pcg_variant=variant)
     out = Q.qpat_prior_solve(case.lib, kt, mt, rhs, p)
     res = np.linalg.norm(Md @ out - rhs) / np.linalg.norm(rhs)
     # the PCG stops on its recursive residual (1e-13); the true residual of
@@ -140,11 +143,12 @@ def test_prior_solve(case, precision):
     assert rel(out, ref) < max(tol, 1e-10)
 
 
-def test_forward_k_padding_and_zero_flux(case):
+@pytest.mark.parametrize("variant", [1, 2])
+def test_forward_k_padding_and_zero_flux(case, variant):
     # a zero illumination next to real ones: padded / inactive RHS stay exactly 0
     fl = np.vstack([case.flux, np.zeros_like(case.flux[:1])])
     if fl.shape[0] > 16:
         pytest.skip("K too large")
-    phi, _ = Q.qpat_forward(case.lib, case.kappa, case.mu, fl)
+    phi, _ = Q.qpat_forward(case.lib, case.kappa, case.mu, fl, _params(0, pcg_variant=variant))
     assert np.all(phi[-1] == 0.0)
     assert rel(phi[:-1], case.phi) < 1e-10
