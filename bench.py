@@ -128,6 +128,23 @@ def pcg_asm_bytes_per_iter(N: int, entries: int, R: int, s: int, nv: int) -> flo
     return entries * (nv * s + 2.0) + nv * s * N + 6.0 * s * R * N
 
 
+def pcg_asm_flops_per_iter(N: int, entries: int, R: int) -> float:
+    """Algorithmic floating-point operations of one PCG iteration with an
+    assembled operator of `entries` stored nonzeros per value set, R
+    right-hand sides (for the two-block prior R = 2, one value set each):
+    2 per nonzero per RHS for q = A p, and per node per RHS 13 for the vector
+    work (z = D^-1 r: 1; p = z + beta p, x += alpha p, r -= alpha q: 2 each;
+    the dot products p.q, r.z, r.r: 2 each)."""
+    return 2.0 * entries * R + 13.0 * R * N
+
+
+def fp64_peak_tflops(sm_mhz: float, nsm: int) -> float:
+    """FP64 arithmetic peak of a GB300 at the sampled SM clock: 2 FP64 FMA
+    (4 flops) per SM per cycle (ncu: sm__sass_thread_inst_executed_op_dfma_pred_on
+    peak_sustained = 304 per cycle over 152 SMs)."""
+    return 4.0 * nsm * sm_mhz * 1e6 / 1e12
+
+
 def setup_problem(Q, torch, precision: int):
     cfg = S.config(WORKLOAD)
     xyz, tets = cfg.mesh()
@@ -191,6 +208,7 @@ def run_ours(args):
         torch.distributed.barrier()
     torch.cuda.synchronize()
     clk.start()
+    launches0 = Q.qpat_launch_count()
     wall0 = time.perf_counter()
     for i in range(args.steps):
         flush.fill_(float(i))
@@ -211,6 +229,7 @@ def run_ours(args):
         b.record()
     torch.cuda.synchronize()
     wall = time.perf_counter() - wall0
+    gpu_launches = Q.qpat_launch_count() - launches0   # library kernels launched in the timed region
     clocks = clk.stop()
     step_ms = [a.elapsed_time(b) for a, b in ev]
     tot_ms = sum(step_ms)
@@ -219,6 +238,7 @@ def run_ours(args):
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
         tot_ms = float(t.item())
     value = world * args.steps / (tot_ms / 1e3)
+
 
     # ---- end to end through the host-pointer ABI (copies inside the timed region)
     H = d["host"]
@@ -244,21 +264,40 @@ def run_ours(args):
     else:
         bpi_pair = pcg_asm_bytes_per_iter(N, mesh.entries, R, s_bytes, 1)
     bpi_prior = pcg_asm_bytes_per_iter(N, mesh.entries, 2, 8, 2)
+    fpi_pair = pcg_asm_flops_per_iter(N, mesh.entries, R)
+    fpi_prior = pcg_asm_flops_per_iter(N, mesh.entries, 2)
     kernels = {
         "pair": {"kernel": f"k_pcg<{'float' if precision == 1 else 'double'}, {R}, "
                            f"{0 if (precision == 1 and args.fp32_operator == 0) else 2}> (J s + J^T w, {R} RHS)",
-                 "ms": pair_ms, "iters": pair_iters, "launches": pair_launches, "bytes_per_iter": bpi_pair},
+                 "ms": pair_ms, "iters": pair_iters, "launches": pair_launches, "bytes_per_iter": bpi_pair,
+                 "flops_per_iter": fpi_pair, "arith": "fp32" if precision == 1 else "fp64"},
         "prior": {"kernel": "k_pcg<double, 2, 3> (M_delta^-1, two blocks)",
-                  "ms": prior_ms, "iters": prior_iters, "launches": prior_launches, "bytes_per_iter": bpi_prior},
+                  "ms": prior_ms, "iters": prior_iters, "launches": prior_launches, "bytes_per_iter": bpi_prior,
+                  "flops_per_iter": fpi_prior, "arith": "fp64"},
     }
     for v in kernels.values():
         v["achieved_gbs"] = v["bytes_per_iter"] * v["iters"] / (v["ms"] / 1e3) / 1e9 if v["ms"] > 0 else 0.0
+        v["achieved_tflops"] = v["flops_per_iter"] * v["iters"] / (v["ms"] / 1e3) / 1e12 if v["ms"] > 0 else 0.0
         v["us_per_iter"] = 1e3 * v["ms"] / max(v["iters"], 1)
         v["share_of_step"] = v["ms"] / tot_ms if tot_ms > 0 else None
     dom = max(kernels, key=lambda k: kernels[k]["ms"])
     bpi = kernels[dom]["bytes_per_iter"]
-    peak, peak_kind = load_peaks()
-    achieved = kernels[dom]["achieved_gbs"]
+    hbm_peak, hbm_kind = load_peaks()
+    nsm = torch.cuda.get_device_properties(local).multi_processor_count
+    sm_mhz = clocks["sm_mhz"] if clocks else 2070.0
+    f64_peak = fp64_peak_tflops(sm_mhz, nsm)
+    for v in kernels.values():
+        v["hbm_frac"] = v["achieved_gbs"] / hbm_peak if hbm_peak else None
+        if v["arith"] == "fp64":
+            v["fp64_frac"] = v["achieved_tflops"] / f64_peak
+    # an FP64 kernel on GB300 is bound by the FP64 pipe (ncu: fp64 pipe busy
+    # 55-70 %, DRAM < 5 %); an FP32 one by memory traffic and latency
+    if kernels[dom]["arith"] == "fp64":
+        bound, unit, achieved, peak = "alu", "TFLOP/s", kernels[dom]["achieved_tflops"], f64_peak
+        peak_kind = (f"derived: 2 FP64 FMA per SM per cycle x {nsm} SMs x {sm_mhz:.0f} MHz "
+                     f"(median sampled SM clock)")
+    else:
+        bound, unit, achieved, peak, peak_kind = "hbm", "GB/s", kernels[dom]["achieved_gbs"], hbm_peak, hbm_kind
     # DRAM traffic per launch from the committed ncu capture, valid only
     # while the kernel sources are unchanged since the capture
     traffic = None
@@ -285,12 +324,15 @@ def run_ours(args):
                    "l2": "flushed between steps (256 MB write outside the per-step events)",
                    "parallelism": "replicas" if world > 1 else "single"},
         "e2e": {"value": e2e_steps / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
-        "roofline": {"bound": "hbm", "kernel": kernels[dom]["kernel"],
-                     "achieved": achieved, "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
+        "roofline": {"bound": bound, "kernel": kernels[dom]["kernel"],
+                     "achieved": achieved, "peak": peak, "peak_kind": peak_kind, "unit": unit,
                      "frac": achieved / peak if peak else None, "traffic": traffic,
-                     "bytes_per_iter": bpi,
-                     "note": "64^3 operands are L2-resident (126 MB L2): achieved is algorithmic bytes / time",
+                     "bytes_per_iter": bpi, "flops_per_iter": kernels[dom]["flops_per_iter"],
+                     "hbm_peak_gbs": hbm_peak,
+                     "note": ("achieved = algorithmic work per iteration x iterations / CUDA-event time of the "
+                              "launches; the 64^3 operands are largely L2-resident (126 MB L2)"),
                      "kernels": kernels},
+        "gpu_launches": gpu_launches,
         "clocks": clocks,
         "wall_s": wall,
     }

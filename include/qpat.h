@@ -73,12 +73,16 @@ typedef struct {
     int patch_nodes;       /* owned nodes per CTA patch (0 = library choice) */
     int fp32_operator;     /* FP32 inner operator of precision 1: 0 = matrix-free
                               element recomputation, 1 = assembled FP32 values */
-    int pcg_variant;       /* PCG on assembled operators: 0 = library choice (1),
-                              1 = two grid reductions per iteration (textbook
-                              order), 2 = one grid reduction per iteration
+    int pcg_variant;       /* PCG on assembled operators: 0 = library choice
+                              (currently 1, the fastest measured), 1 = two grid
+                              reductions per iteration (textbook order),
+                              2 = one grid reduction per iteration
                               (Chronopoulos-Gear recurrences; the same iterates
-                              in exact arithmetic, more vector traffic).
-                              Matrix-free FP32 runs always use 1. */
+                              in exact arithmetic, more vector traffic),
+                              3 = as 1 with the operator streamed through a
+                              shared-memory ring by bulk copies (QPAT_EINVAL
+                              if the ring does not fit).  Matrix-free FP32
+                              runs always use 1. */
     int reserved[5];
 } qpat_params;
 
@@ -99,6 +103,12 @@ void qpat_default_params(qpat_params* p);
 
 /* Thread-local message describing the last error of this thread. */
 const char* qpat_last_error(void);
+
+/* Number of CUDA kernels this library has launched in this process (every
+ * launch statement counts; a replayed batch graph counts its one kernel).
+ * Host-side counter, never reset; take differences around a region.  Not in
+ * the paper. */
+int64_t qpat_launch_count(void);
 
 /* ---------------------------------------------------------------- mesh */
 

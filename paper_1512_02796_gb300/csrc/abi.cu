@@ -2,6 +2,7 @@
 // FP32 PCG inside FP64 iterative refinement) and the forward / Jacobian /
 // prior entry points.  Algorithm 1 lives in recon.cu.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstring>
 #include <map>
@@ -115,25 +116,31 @@ __global__ void k_add(int64_t n, const double* a, double* y) {
 }  // namespace
 
 cudaError_t launch_add(int64_t n, const double* a, double* y, cudaStream_t s) {
+    qpat::note_launch(1);
     k_add<<<grid_of(n), 256, 0, s>>>(n, a, y);
     return cudaGetLastError();
 }
 
 void k_mul_launch(int64_t n, const double* a, const double* b, double* out, cudaStream_t s) {
+    qpat::note_launch(1);
     k_mul<<<grid_of(n), 256, 0, s>>>(n, a, b, out);
 }
 void k_exp_scale_launch(int64_t n, double c0, const double* u, double* out, cudaStream_t s) {
+    qpat::note_launch(1);
     k_exp_scale<<<grid_of(n), 256, 0, s>>>(n, c0, u, out);
 }
 void k_rowscale_launch(int64_t N, int R, const double* d, const double* x, double* out, cudaStream_t s) {
+    qpat::note_launch(1);
     k_rowscale<<<grid_of(N * R), 256, 0, s>>>(N, R, d, x, out);
 }
 void k_jv_out_launch(int64_t N, int R, const double* mu, const double* b, const double* x, const double* phi,
                      const double* w, double* out, cudaStream_t s) {
+    qpat::note_launch(1);
     k_jv_out<<<grid_of(N * R), 256, 0, s>>>(N, R, mu, b, x, phi, w, out);
 }
 void k_jt_out_launch(int64_t N, int R, const double* kappa, const double* mu, const double* y, const double* phi,
                      const double* tw, double* ok, double* om, cudaStream_t s) {
+    qpat::note_launch(1);
     k_jt_out<<<grid_of(N), 256, 0, s>>>(N, R, kappa, mu, y, phi, tw, ok, om);
 }
 
@@ -237,8 +244,10 @@ int solve(qpat_mesh_s* M, const OpState& st, const SolveOpts& so_in, int R, cons
     w.status = M->ws.get<int>("pcg.status", 1, s, &e);
     w.iters = M->ws.get<int>("pcg.iters", 1, s, &e);
     w.stats = M->ws.get<double>("pcg.stats", 32, s, &e);
-    // single-reduction variant on the assembled operators
-    const bool single = so.single_reduction && (so.precision == 0 || so.fp32_assembled);
+    // PCG variant on the assembled operators (the matrix-free FP32 operator has one)
+    const bool assembled = so.precision == 0 || so.fp32_assembled;
+    const bool single = assembled && so.pcg_variant == 2;
+    const bool ring = assembled && so.pcg_variant == 3;
     if (single) {
         w.r1 = M->ws.get_bytes(nm("r1"), n * esz, s, &e);
         w.s0 = M->ws.get_bytes(nm("s0"), n * esz, s, &e);
@@ -280,8 +289,13 @@ int solve(qpat_mesh_s* M, const OpState& st, const SolveOpts& so_in, int R, cons
         const int OP = st.kind == OP_K ? OP_CSR1 : OP_CSR2;
         OpParams<double> op{st.c1_64, st.c2_64, st.inv_T2, st.scale1, st.delta, 1, st.v64[0], st.v64[1]};
         if (M->timing) cudaEventRecord(M->ev0, s);
-        e = single ? launch_pcg1<double>(M->d, OP, R, op, st.inv64, w, so.rtol, so.maxit, s, nullptr)
-                   : launch_pcg<double>(M->d, OP, R, op, st.inv64, w, so.rtol, so.maxit, s, nullptr);
+        e = cudaErrorNotSupported;
+        if (ring) e = launch_pcg_ring<double>(M->d, OP, R, op, st.inv64, w, so.rtol, so.maxit, s, nullptr);
+        if (e == cudaErrorNotSupported) {
+            if (so.pcg_variant == 3) return fail(QPAT_EINVAL, "pcg: the bulk-copy ring does not fit this mesh");
+            e = single ? launch_pcg1<double>(M->d, OP, R, op, st.inv64, w, so.rtol, so.maxit, s, nullptr)
+                       : launch_pcg<double>(M->d, OP, R, op, st.inv64, w, so.rtol, so.maxit, s, nullptr);
+        }
         if (e != cudaSuccess) return cuda_fail(e, "pcg launch");
         if (M->timing) cudaEventRecord(M->ev1, s);
         int hst[2];
@@ -341,11 +355,17 @@ int solve(qpat_mesh_s* M, const OpState& st, const SolveOpts& so_in, int R, cons
         if (done) break;
         if (sweeps >= so.max_sweeps) return fail(QPAT_ENOCONV, "refinement: sweep cap reached");
         ++sweeps;
+        qpat::note_launch(1);
         k_sqrt_vec<<<1, 32, 0, s>>>(R, dnorm, dnorm + 32);
         if ((e = launch_cast_d2f_scaled(N, R, Rres, dnorm + 32, b32, s)) != cudaSuccess) return cuda_fail(e, "cast");
         if (M->timing) cudaEventRecord(M->ev0, s);
-        e = single ? launch_pcg1<float>(M->d, OP, R, op, st.inv32, w, so.inner_rtol, so.maxit, s, nullptr)
-                   : launch_pcg<float>(M->d, OP, R, op, st.inv32, w, so.inner_rtol, so.maxit, s, nullptr);
+        e = cudaErrorNotSupported;
+        if (ring) e = launch_pcg_ring<float>(M->d, OP, R, op, st.inv32, w, so.inner_rtol, so.maxit, s, nullptr);
+        if (e == cudaErrorNotSupported) {
+            if (so.pcg_variant == 3) return fail(QPAT_EINVAL, "pcg32: the bulk-copy ring does not fit this mesh");
+            e = single ? launch_pcg1<float>(M->d, OP, R, op, st.inv32, w, so.inner_rtol, so.maxit, s, nullptr)
+                       : launch_pcg<float>(M->d, OP, R, op, st.inv32, w, so.inner_rtol, so.maxit, s, nullptr);
+        }
         if (e != cudaSuccess) return cuda_fail(e, "pcg32 launch");
         if (M->timing) cudaEventRecord(M->ev1, s);
         int hst[2];
@@ -379,9 +399,16 @@ using namespace qpat;
 // Public entry points
 // --------------------------------------------------------------------------
 
+namespace qpat {
+static std::atomic<long long> g_launches{0};
+void note_launch(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+}  // namespace qpat
+
 extern "C" {
 
 const char* qpat_last_error(void) { return g_err.c_str(); }
+
+int64_t qpat_launch_count(void) { return int64_t(qpat::g_launches.load(std::memory_order_relaxed)); }
 
 void qpat_default_params(qpat_params* p) {
     if (!p) return;

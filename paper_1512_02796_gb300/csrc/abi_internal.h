@@ -51,7 +51,7 @@ struct SolveOpts {
     double inner_rtol = 1e-4;
     int max_sweeps = 30;
     int fp32_assembled = 0;   // FP32 inner operator: 0 matrix-free elements, 1 assembled values
-    int single_reduction = 0; // assembled operators: Chronopoulos-Gear PCG (one grid reduction)
+    int pcg_variant = 0;      // assembled operators: 0 (= 1) two reductions, 2 one reduction, 3 bulk-copy ring
 };
 
 struct DeviceGuard {

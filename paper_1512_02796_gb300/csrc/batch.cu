@@ -190,6 +190,7 @@ int qpat_batch_forward(qpat_batch_t B, void* stream) {
         if ((e = cudaGraphInstantiate(&B->exec, g, 0)) != cudaSuccess)
             return cuda_fail(e, "qpat_batch_forward: instantiate");
     }
+    qpat::note_launch(1);  // the graph holds one cooperative kernel
     if ((e = cudaGraphLaunch(B->exec, s)) != cudaSuccess) return cuda_fail(e, "qpat_batch_forward: graph launch");
     return QPAT_OK;
 }

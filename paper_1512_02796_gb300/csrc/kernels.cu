@@ -46,6 +46,7 @@ cudaError_t apply_t(const MeshDev& m, const OpParams<T>& op, T sign, const T* x,
     auto kern = k_apply<T, R, OP>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
     if (e != cudaSuccess) return e;
+    qpat::note_launch(1);
     kern<<<m.P, kThreads, smem, st>>>(m, op, sign, x, y, ldx, c0);
     return cudaGetLastError();
 }
@@ -291,6 +292,7 @@ cudaError_t apply_csr_t(const MeshDev& m, const T* v0, const T* v1, const T* x, 
     auto kern = k_apply_csr<T, R, NV>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
     if (e != cudaSuccess) return e;
+    qpat::note_launch(1);
     kern<<<m.P, kThreads, smem, st>>>(m, v0, v1, x, y);
     return cudaGetLastError();
 }
@@ -371,6 +373,7 @@ cudaError_t vjp_t(const MeshDev& m, const T* phi, const T* z, T* y, int ldk, int
     auto kern = k_vjp_accum<T, K>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
     if (e != cudaSuccess) return e;
+    qpat::note_launch(1);
     kern<<<m.P, kThreads, smem, st>>>(m, phi, z, y, ldk, c0, acc);
     return cudaGetLastError();
 }
@@ -501,6 +504,7 @@ cudaError_t launch_invdiag_K(const MeshDev& m, const double* kappa, const double
     const size_t smem = PatchSmem<double, 1>::bytes(m.max_touched, m.max_own);
     cudaError_t e = cudaFuncSetAttribute(k_diag_K, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
     if (e != cudaSuccess) return e;
+    qpat::note_launch(1);
     k_diag_K<<<m.P, kThreads, smem, s>>>(m, kappa, mu, inv64, inv32);
     return cudaGetLastError();
 }
@@ -510,6 +514,7 @@ cudaError_t launch_invdiag_prior(const MeshDev& m, const double* u1, const doubl
     const size_t smem = PatchSmem<double, 2>::bytes(m.max_touched, m.max_own);
     cudaError_t e = cudaFuncSetAttribute(k_diag_prior, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
     if (e != cudaSuccess) return e;
+    qpat::note_launch(1);
     k_diag_prior<<<m.P, kThreads, smem, s>>>(m, u1, u2, inv_T2, scale1, delta, inv64, inv32);
     return cudaGetLastError();
 }
@@ -521,7 +526,9 @@ cudaError_t launch_assemble_K(const MeshDev& m, const double* kappa, const doubl
     const size_t smem = PatchSmem<double, 1>::bytes(m.max_touched, m.max_own);
     e = cudaFuncSetAttribute(k_assemble_K, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
     if (e != cudaSuccess) return e;
+    qpat::note_launch(1);
     k_assemble_K<<<m.P, kThreads, smem, s>>>(m, kappa, mu, val);
+    qpat::note_launch(1);
     k_diag_csr<<<grid_for(m.N), 256, 0, s>>>(m, 1, 0.0, val, nullptr, inv64, inv32);
     return cudaGetLastError();
 }
@@ -535,12 +542,15 @@ cudaError_t launch_assemble_prior(const MeshDev& m, const double* u1, const doub
     const size_t smem = PatchSmem<double, 1>::bytes(m.max_touched, m.max_own);
     e = cudaFuncSetAttribute(k_assemble_prior, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
     if (e != cudaSuccess) return e;
+    qpat::note_launch(1);
     k_assemble_prior<<<m.P, kThreads, smem, s>>>(m, u1, u2, inv_T2, scale1, val0, val1);
+    qpat::note_launch(1);
     k_diag_csr<<<grid_for(m.N), 256, 0, s>>>(m, 2, delta, val0, val1, inv64, inv32);
     return cudaGetLastError();
 }
 
 cudaError_t launch_cast_vals(int64_t n, const double* in, float* out, cudaStream_t s) {
+    qpat::note_launch(1);
     k_cast_vals<<<grid_for(n), 256, 0, s>>>(n, in, out);
     return cudaGetLastError();
 }
@@ -594,47 +604,56 @@ cudaError_t launch_vjp_accum(const MeshDev& m, int K, const T* phi, const T* z, 
 }
 
 cudaError_t launch_load(const MeshDev& m, int K, int R, const double* flux, double* f, cudaStream_t s) {
+    qpat::note_launch(1);
     k_load<<<grid_for(int64_t(m.F) * K), 256, 0, s>>>(m, K, R, flux, f);
     return cudaGetLastError();
 }
 
 template <typename Tin, typename Tout>
 cudaError_t launch_to_lib(const MeshDev& m, int K, int R, const Tin* in, Tout* out, cudaStream_t s) {
+    qpat::note_launch(1);
     k_to_lib<Tin, Tout><<<grid_for(int64_t(m.N) * R), 256, 0, s>>>(m.N, K, R, m.perm, in, out);
     return cudaGetLastError();
 }
 
 template <typename Tin, typename Tout>
 cudaError_t launch_from_lib(const MeshDev& m, int K, int R, const Tin* in, Tout* out, cudaStream_t s) {
+    qpat::note_launch(1);
     k_from_lib<Tin, Tout><<<grid_for(int64_t(m.N) * K), 256, 0, s>>>(m.N, K, R, m.perm, in, out);
     return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t launch_dots(int64_t n, int R, const T* a, const T* b, double* partial, double* out, cudaStream_t s) {
+    qpat::note_launch(1);
     k_dot_partial<T><<<kRedBlocks, 256, 0, s>>>(n, R, a, b, partial);
+    qpat::note_launch(1);
     k_dot_final<<<1, 32, 0, s>>>(kRedBlocks, R, partial, out);
     return cudaGetLastError();
 }
 
 cudaError_t launch_cast_d2f_scaled(int64_t n, int R, const double* in, const double* scale, float* out,
                                    cudaStream_t s) {
+    qpat::note_launch(1);
     k_cast_d2f_scaled<<<grid_for(n * R), 256, 0, s>>>(n, R, in, scale, out);
     return cudaGetLastError();
 }
 
 cudaError_t launch_axpy_f2d_scaled(int64_t n, int R, const float* d, const double* scale, double* x,
                                    cudaStream_t s) {
+    qpat::note_launch(1);
     k_axpy_f2d_scaled<<<grid_for(n * R), 256, 0, s>>>(n, R, d, scale, x);
     return cudaGetLastError();
 }
 
 cudaError_t launch_sub(int64_t n, const double* a, const double* b, double* out, cudaStream_t s) {
+    qpat::note_launch(1);
     k_sub<<<grid_for(n), 256, 0, s>>>(n, a, b, out);
     return cudaGetLastError();
 }
 
 cudaError_t launch_cast_d2f(int64_t n, const double* in, float* out, cudaStream_t s) {
+    qpat::note_launch(1);
     k_cast_d2f<<<grid_for(n), 256, 0, s>>>(n, in, out);
     return cudaGetLastError();
 }

@@ -93,6 +93,14 @@ template <typename T>
 cudaError_t launch_pcg1(const MeshDev& m, int OP, int R, const OpParams<T>& op, const T* invdiag,
                         const PcgWork& w, double rtol, int maxit, cudaStream_t s, int* grid_used);
 
+// Two-reduction PCG on the assembled operators with the operator streamed
+// through a shared-memory ring by bulk copies (see pcg.cu).  Returns
+// cudaErrorNotSupported, launching nothing, when no ring of >= 2 slots fits
+// beside the staged vector at the wanted occupancy.
+template <typename T>
+cudaError_t launch_pcg_ring(const MeshDev& m, int OP, int R, const OpParams<T>& op, const T* invdiag,
+                            const PcgWork& w, double rtol, int maxit, cudaStream_t s, int* grid_used);
+
 // Many independent FP64 assembled-K solves (different meshes) in one
 // cooperative launch; see k_pcg_batch in pcg.cu.
 struct PcgBatchProblem {

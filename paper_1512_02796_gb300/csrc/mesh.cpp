@@ -255,12 +255,13 @@ std::string build_host_mesh(const double* xyz, int64_t N, const int32_t* tets,
     // ---- sliced ELLPACK pattern (slices never straddle patches: patch_nodes % 32 == 0)
     m.nslices = (N + 31) / 32;
     m.sell_ptr.assign(m.nslices + 1, 0);
-    m.sell_len.resize(N);
+    m.sell_len.assign(size_t(32) * m.nslices, 0);
     m.sell_diag.resize(N);
     for (int64_t s = 0; s < m.nslices; ++s) {
         size_t w = 0;
         for (int64_t g = 32 * s; g < std::min<int64_t>(N, 32 * s + 32); ++g) w = std::max(w, rows[g].size());
         m.sell_ptr[s + 1] = m.sell_ptr[s] + int64_t(w);
+        m.sell_wmax = std::max(m.sell_wmax, int(w));
     }
     m.sell_col.assign(size_t(32) * m.sell_ptr[m.nslices], 0);
     for (int64_t s = 0; s < m.nslices; ++s) {

@@ -170,8 +170,13 @@ __device__ __forceinline__ void sell_row(const MeshDev& m, const OpParams<T>& op
 // ---------------------------------------------------------------- grid reduction
 // Sum over the grid of NQ x R values; thread t holds acc[q][c] for RHS
 // (t % NP) * VW + c.  Totals land in out[q * R + r] (shared) in every CTA.
-template <int NQ, int VW, int NP>
-__device__ __forceinline__ bool grid_reduce(double (&acc)[NQ][VW], double* scratch, double* partials, int& red_id,
+// Each thread's partial sums (a few terms) and the sums across a warp are
+// formed in the solve's own precision T; from the warp totals on, the sums
+// (across warps, then across CTAs in a fixed order) run in FP64.  GB300
+// issues FP64 at 1/64 of the FP32 rate, so per-element FP64 terms, FP32->FP64
+// conversions and FP64 warp shuffles would dominate an FP32 iteration.
+template <int NQ, int VW, int NP, typename T>
+__device__ __forceinline__ bool grid_reduce(T (&acc)[NQ][VW], double* scratch, double* partials, int& red_id,
                                             unsigned* bar, int* status, long long limit, double* out, int cta,
                                             int ncta) {
     constexpr int R = VW * NP, NS = NQ * R;
@@ -188,7 +193,7 @@ __device__ __forceinline__ bool grid_reduce(double (&acc)[NQ][VW], double* scrat
 #pragma unroll
         for (int q = 0; q < NQ; ++q)
 #pragma unroll
-            for (int c = 0; c < VW; ++c) scratch[warp * NS + q * R + lane * VW + c] = acc[q][c];
+            for (int c = 0; c < VW; ++c) scratch[warp * NS + q * R + lane * VW + c] = double(acc[q][c]);
     __syncthreads();
     double* part = partials + size_t(red_id & 1) * kMaxGrid * kMaxNS;
     double* res = partials + size_t(2) * kMaxGrid * kMaxNS + (red_id & 1) * kMaxNS;
@@ -280,7 +285,7 @@ __device__ __forceinline__ void pcg_body(const PcgArgs<T>& a, const int cta, con
 
     // ---- initial residual r = b (x0 = 0)
     {
-        double acc[3][VW];
+        T acc[3][VW];
 #pragma unroll
         for (int c = 0; c < VW; ++c) acc[0][c] = acc[1][c] = acc[2][c] = 0.0;
         for (int p = cta; p < P; p += ncta) {
@@ -294,8 +299,8 @@ __device__ __forceinline__ void pcg_body(const PcgArgs<T>& a, const int cta, con
 #pragma unroll
                 for (int c = 0; c < VW; ++c) {
                     zero[c] = T(0);
-                    acc[0][c] += double(bv[c]) * double(bv[c]);
-                    acc[1][c] += double(bv[c]) * double(d[c] * bv[c]);
+                    acc[0][c] += bv[c] * bv[c];
+                    acc[1][c] += bv[c] * (d[c] * bv[c]);
                 }
                 vst(a.x + e, zero);
                 vst(a.r + e, bv);
@@ -343,9 +348,9 @@ __device__ __forceinline__ void pcg_body(const PcgArgs<T>& a, const int cta, con
         for (int c = 0; c < VW; ++c) bt[c] = T(beta[r0 + c]);
 
         // ---- phase A: p = D^-1 r + beta p_old on touched nodes, q = A p on owned nodes
-        double accA[1][VW];
+        T accA[1][VW];
 #pragma unroll
-        for (int c = 0; c < VW; ++c) accA[0][c] = 0.0;
+        for (int c = 0; c < VW; ++c) accA[0][c] = T(0);
         for (int p = cta; p < P; p += ncta) {
             const int nb = __ldg(m.node_ptr + p), nt = __ldg(m.node_ptr + p + 1) - nb;
             const int ob = __ldg(m.own_begin + p), nown = __ldg(m.own_begin + p + 1) - ob;
@@ -388,7 +393,7 @@ __device__ __forceinline__ void pcg_body(const PcgArgs<T>& a, const int cta, con
                     vst(pc + e, pv);
                     vst(a.q + e, acc);
 #pragma unroll
-                    for (int c = 0; c < VW; ++c) accA[0][c] += double(pv[c]) * double(acc[c]);
+                    for (int c = 0; c < VW; ++c) accA[0][c] += pv[c] * acc[c];
                 }
                 __syncthreads();
             } else {
@@ -401,7 +406,7 @@ __device__ __forceinline__ void pcg_body(const PcgArgs<T>& a, const int cta, con
                     if (OP == OP_PRIOR) qv += a.op.delta * pv;
                     pc[e] = pv;
                     a.q[e] = qv;
-                    accA[0][0] += double(pv) * double(qv);
+                    accA[0][0] += pv * qv;
                 }
                 __syncthreads();
             }
@@ -426,7 +431,7 @@ __device__ __forceinline__ void pcg_body(const PcgArgs<T>& a, const int cta, con
         }
 
         // ---- phase B: x += alpha p, r -= alpha q; r.D^-1 r and r.r
-        double accB[2][VW];
+        T accB[2][VW];
 #pragma unroll
         for (int c = 0; c < VW; ++c) accB[0][c] = accB[1][c] = 0.0;
         {
@@ -448,8 +453,8 @@ __device__ __forceinline__ void pcg_body(const PcgArgs<T>& a, const int cta, con
                     for (int c = 0; c < VW; ++c) {
                         xv[c] += al[c] * pv[c];
                         rv[c] -= al[c] * qv[c];
-                        accB[0][c] += double(rv[c]) * double(d[c] * rv[c]);
-                        accB[1][c] += double(rv[c]) * double(rv[c]);
+                        accB[0][c] += rv[c] * (d[c] * rv[c]);
+                        accB[1][c] += rv[c] * rv[c];
                     }
                     vst(a.x + e, xv);
                     vst(a.r + e, rv);
@@ -522,7 +527,7 @@ __device__ __forceinline__ void pcg1_body(const PcgArgs<T>& a, const int cta, co
 
     // ---- start: x = 0, r = b, u = D^-1 b, w = A u; gamma, delta, |b|^2
     {
-        double acc[3][VW];
+        T acc[3][VW];
 #pragma unroll
         for (int c = 0; c < VW; ++c) acc[0][c] = acc[1][c] = acc[2][c] = 0.0;
         for (int pt = cta; pt < P; pt += ncta) {
@@ -549,9 +554,9 @@ __device__ __forceinline__ void pcg1_body(const PcgArgs<T>& a, const int cta, co
 #pragma unroll
                 for (int c = 0; c < VW; ++c) {
                     zero[c] = T(0);
-                    acc[0][c] += double(bv[c]) * double(uv[c]);
-                    acc[1][c] += double(wv[c]) * double(uv[c]);
-                    acc[2][c] += double(bv[c]) * double(bv[c]);
+                    acc[0][c] += bv[c] * uv[c];
+                    acc[1][c] += wv[c] * uv[c];
+                    acc[2][c] += bv[c] * bv[c];
                 }
                 vst(a.q + e, wv);
                 vst(u + e, uv);
@@ -611,7 +616,7 @@ __device__ __forceinline__ void pcg1_body(const PcgArgs<T>& a, const int cta, co
             al[c] = T(alpha[r0 + c]);
             bt[c] = T(beta[r0 + c]);
         }
-        double acc[3][VW];
+        T acc[3][VW];
 #pragma unroll
         for (int c = 0; c < VW; ++c) acc[0][c] = acc[1][c] = acc[2][c] = 0.0;
         for (int pt = cta; pt < P; pt += ncta) {
@@ -672,9 +677,9 @@ __device__ __forceinline__ void pcg1_body(const PcgArgs<T>& a, const int cta, co
 #pragma unroll
                 for (int c = 0; c < VW; ++c) {
                     xv[c] += al[c] * pv[c];
-                    acc[0][c] += double(rn[c]) * double(un[c]);
-                    acc[1][c] += double(wv[c]) * double(un[c]);
-                    acc[2][c] += double(rn[c]) * double(rn[c]);
+                    acc[0][c] += rn[c] * un[c];
+                    acc[1][c] += wv[c] * un[c];
+                    acc[2][c] += rn[c] * rn[c];
                 }
                 vst(p + e, pv);
                 vst(a.x + e, xv);
@@ -726,6 +731,430 @@ __device__ __forceinline__ void pcg1_body(const PcgArgs<T>& a, const int cta, co
 template <typename T, int R, int OP>
 __global__ void __launch_bounds__(kThreads, min_ctas<OP>()) k_pcg1(PcgArgs<T> a) {
     pcg1_body<T, R, OP>(a, blockIdx.x, gridDim.x);
+}
+
+// ---------------------------------------------------------------- bulk-copy ring variant
+// Same iteration as pcg_body (assembled operators), but the operator is not
+// read with per-thread loads: one thread streams it, a 32-row slice at a
+// time, into a ring of S shared-memory slots with cp.async.bulk copies that
+// signal an mbarrier when their bytes have landed (Hopper/Blackwell bulk-copy
+// engine: no registers, no per-thread requests).  A slice is the values, the
+// local column ids and the row lengths of 32 consecutive rows, which the
+// sliced-ELLPACK layout keeps contiguous.  The operator does not change
+// between iterations, so the copies for the next iteration's first slices are
+// issued while this one finishes: they travel during phase B and both grid
+// reductions.  Rows of a slice are computed by all 8 warps: lane = row,
+// warp = (RHS block, stride-KS share of the row's entries); the KS partial
+// sums meet in shared memory (double-buffered, one __syncthreads per slice).
+constexpr int kMaxSlots = 8;
+constexpr long long kMbarSpinLimit = 1LL << 22;  // try_wait polls; each may suspend up to ~1 us
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// bounded wait on phase `parity` of an mbarrier; false after the spin limit
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity) {
+    for (long long i = 0; i < kMbarSpinLimit; ++i)
+        if (mbar_try_wait(bar, parity)) return true;
+    return false;
+}
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned bytes, uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_addr(dst)),
+        "l"(src), "r"(bytes), "r"(smem_addr(bar))
+        : "memory");
+}
+
+// shared-memory layout of the ring kernel (byte offsets, 128-aligned)
+struct RingLayout {
+    int slots;          // S
+    int slot_bytes;     // one slice: NV value arrays, column ids, lengths
+    int xs_off, red_off, ring_off, total;
+};
+
+template <typename T, int R, int OP>
+struct RingCfg {
+    static constexpr int VW = vec_width<T, R, true>();
+    static constexpr int NP = R / VW;
+    static constexpr int KS = (kThreads / 32) / NP;  // warps sharing one row's entries
+    static constexpr int NV = OP == OP_CSR2 ? 2 : 1;
+    static_assert(NP <= kThreads / 32, "one warp per RHS block at least");
+};
+
+template <typename T, int R, int OP>
+__host__ __device__ inline RingLayout ring_layout(int max_touched, int wmax, int slots) {
+    using C = RingCfg<T, R, OP>;
+    auto up = [](int b) { return (b + 127) / 128 * 128; };
+    RingLayout L;
+    L.slots = slots;
+    L.slot_bytes = up(C::NV * wmax * 32 * int(sizeof(T)) + wmax * 32 * 2 + 32);
+    L.xs_off = 0;
+    L.red_off = up(int(sizeof(T)) * max_touched * R);
+    // two KS x NP x 32 x VW partial-sum buffers; also the grid reduction's scratch
+    int red = 2 * (kThreads / 32) * 32 * C::VW * int(sizeof(T));
+    red = red > (kThreads / 32) * kMaxNS * 8 ? red : (kThreads / 32) * kMaxNS * 8;
+    L.ring_off = L.red_off + up(red);
+    L.total = L.ring_off + slots * L.slot_bytes;
+    return L;
+}
+
+template <typename T, int R, int OP>
+__device__ __forceinline__ void pcg_ring_body(const PcgArgs<T>& a, const RingLayout L, const int cta,
+                                              const int ncta) {
+    using C = RingCfg<T, R, OP>;
+    constexpr int VW = C::VW, NP = C::NP, KS = C::KS, NV = C::NV;
+    extern __shared__ __align__(128) unsigned char ring_smem[];
+    T* xs = reinterpret_cast<T*>(ring_smem + L.xs_off);
+    T* red_s = reinterpret_cast<T*>(ring_smem + L.red_off);
+    double* scratch = reinterpret_cast<double*>(ring_smem + L.red_off);
+    unsigned char* ring = ring_smem + L.ring_off;
+    __shared__ uint64_t full[kMaxSlots];
+    __shared__ double red[kMaxNS];
+    __shared__ double bb[R], rz[R], rz_old[R], rr[R], alpha[R], beta[R];
+    __shared__ double dot_s[NP][VW];
+    __shared__ int s_flag;
+
+    const MeshDev& m = a.m;
+    const int P = m.P;
+    const int S = L.slots;
+    const int lane = threadIdx.x & 31, wq = threadIdx.x >> 5;
+    const int rpart = wq % NP, kslot = wq / NP;  // rows pass: RHS block and entry share
+    const int r0row = rpart * VW;
+    const int spart = threadIdx.x % NP;          // staging and vector phases
+    const int r0 = spart * VW;
+    const int W = m.sell_wmax;
+    int red_id = 0;
+
+    // slices of this CTA per phase (its patches' owned rows, 32 per slice)
+    int nsl = 0;
+    for (int pt = cta; pt < P; pt += ncta)
+        nsl += (__ldg(m.own_begin + pt + 1) - __ldg(m.own_begin + pt) + 31) / 32;
+    // sequence number q -> global slice id (the same order every iteration)
+    auto slice_of = [&](long long q) {
+        int loc = int(q % nsl);
+        for (int pt = cta; pt < P; pt += ncta) {
+            const int ob = __ldg(m.own_begin + pt);
+            const int ns = (__ldg(m.own_begin + pt + 1) - ob + 31) / 32;
+            if (loc < ns) return ob / 32 + loc;
+            loc -= ns;
+        }
+        return 0;  // not reached
+    };
+    auto issue = [&](long long q) {  // one thread
+        const int slot = int(q % S);
+        const int sl = slice_of(q);
+        const int64_t p0 = m.sell_ptr[sl];
+        const int w = int(m.sell_ptr[sl + 1] - p0);
+        const int64_t e0 = p0 * 32;
+        unsigned char* dst = ring + size_t(slot) * L.slot_bytes;
+        const unsigned bv = unsigned(w) * 32u * sizeof(T), bc = unsigned(w) * 64u;
+        mbar_expect_tx(&full[slot], NV * bv + bc + 32u);
+        bulk_g2s(dst, a.op.v0 + e0, bv, &full[slot]);
+        if constexpr (NV == 2) bulk_g2s(dst + size_t(W) * 32 * sizeof(T), a.op.v1 + e0, bv, &full[slot]);
+        bulk_g2s(dst + size_t(NV) * W * 32 * sizeof(T), m.sell_col + e0, bc, &full[slot]);
+        bulk_g2s(dst + size_t(NV) * W * 32 * sizeof(T) + size_t(W) * 64, m.sell_len + size_t(sl) * 32, 32u,
+                 &full[slot]);
+    };
+    long long cons = 0;  // next slice to consume; slices [cons, cons + S) are in flight
+    // waits for every copy in flight (bounded), so that no copy outlives the CTA
+    auto drain = [&]() {
+        for (long long q = cons; q < cons + S; ++q) mbar_wait(&full[q % S], unsigned((q / S) & 1));
+    };
+
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < S; ++i) mbar_init(&full[i], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    if (threadIdx.x == 0)
+        for (long long q = 0; q < S; ++q) issue(q);
+
+    // ---- initial residual r = b (x0 = 0)
+    {
+        T acc[3][VW];
+#pragma unroll
+        for (int c = 0; c < VW; ++c) acc[0][c] = acc[1][c] = acc[2][c] = 0.0;
+        for (int pt = cta; pt < P; pt += ncta) {
+            const int ob = __ldg(m.own_begin + pt), nown = __ldg(m.own_begin + pt + 1) - ob;
+            for (int i = threadIdx.x; i < nown * NP; i += blockDim.x) {
+                const int g = ob + i / NP;
+                const size_t e = size_t(g) * R + r0;
+                T bv[VW], d[VW], zero[VW];
+                vld(a.b + e, bv);
+                dinv_vec<T, VW, OP>(a.invdiag, g, r0, d);
+#pragma unroll
+                for (int c = 0; c < VW; ++c) {
+                    zero[c] = T(0);
+                    acc[0][c] += bv[c] * bv[c];
+                    acc[1][c] += bv[c] * (d[c] * bv[c]);
+                }
+                vst(a.x + e, zero);
+                vst(a.r + e, bv);
+            }
+        }
+#pragma unroll
+        for (int c = 0; c < VW; ++c) acc[2][c] = acc[0][c];
+        if (!grid_reduce<3, VW, NP>(acc, scratch, a.partials, red_id, a.bar, a.status, a.spin_limit, red, cta,
+                                    ncta)) {
+            drain();
+            return;
+        }
+        if (threadIdx.x < R) {
+            bb[threadIdx.x] = red[threadIdx.x];
+            rz[threadIdx.x] = red[R + threadIdx.x];
+            rr[threadIdx.x] = red[2 * R + threadIdx.x];
+            rz_old[threadIdx.x] = 1.0;
+        }
+        __syncthreads();
+    }
+
+    int it = 0;
+    for (;;) {
+        if (threadIdx.x == 0) {
+            int any = 0;
+            for (int r = 0; r < R; ++r) any |= (rr[r] > a.rtol2 * bb[r]) ? 1 : 0;
+            s_flag = any;
+        }
+        __syncthreads();
+        if (!s_flag) break;
+        if (it >= a.maxit) {
+            if (cta == 0 && threadIdx.x == 0) atomicCAS(a.status, 0, QPAT_ENOCONV);
+            break;
+        }
+        if (threadIdx.x < R) {
+            const int r = threadIdx.x;
+            const bool act = rr[r] > a.rtol2 * bb[r];
+            beta[r] = (it == 0 || !act) ? 0.0 : rz[r] / rz_old[r];
+        }
+        __syncthreads();
+
+        T* pc = (it & 1) ? a.p1 : a.p0;
+        const T* pp = (it & 1) ? a.p0 : a.p1;
+        T bt[VW];
+#pragma unroll
+        for (int c = 0; c < VW; ++c) bt[c] = T(beta[r0 + c]);
+
+        // ---- phase A: p on the touched nodes (shared), q = A p row slice by row slice
+        T dotA[VW];
+#pragma unroll
+        for (int c = 0; c < VW; ++c) dotA[c] = 0.0;
+        bool ok = true;
+        for (int pt = cta; pt < P && ok; pt += ncta) {
+            const int nb = __ldg(m.node_ptr + pt), nt = __ldg(m.node_ptr + pt + 1) - nb;
+            const int ob = __ldg(m.own_begin + pt), nown = __ldg(m.own_begin + pt + 1) - ob;
+            for (int i0 = threadIdx.x; i0 < nt * NP; i0 += kUnroll * blockDim.x) {
+                int li[kUnroll];
+                T rv[kUnroll][VW], d[kUnroll][VW], po[kUnroll][VW];
+#pragma unroll
+                for (int u = 0; u < kUnroll; ++u) {
+                    const int i = i0 + u * blockDim.x;
+                    li[u] = (i < nt * NP ? i : i0) / NP;
+                    const int g = __ldg(m.nodes + nb + li[u]);
+                    const size_t e = size_t(g) * R + r0;
+                    vld_cg(a.r + e, rv[u]);
+                    dinv_vec<T, VW, OP>(a.invdiag, g, r0, d[u]);
+                    if (it > 0) vld_cg(pp + e, po[u]);
+                }
+#pragma unroll
+                for (int u = 0; u < kUnroll; ++u) {
+                    T pv[VW];
+#pragma unroll
+                    for (int c = 0; c < VW; ++c) pv[c] = d[u][c] * rv[u][c] + (it > 0 ? bt[c] * po[u][c] : T(0));
+                    if (u == 0 || i0 + u * int(blockDim.x) < nt * NP) vst(xs + li[u] * R + r0, pv);
+                }
+            }
+            __syncthreads();
+            const int ns = (nown + 31) / 32;
+            for (int j = 0; j < ns; ++j, ++cons) {
+                const int slot = int(cons % S);
+                // a thread that gives up computes nothing (the slot is not
+                // valid) and the vote below takes every thread out together
+                const bool landed = mbar_wait(&full[slot], unsigned((cons / S) & 1));
+                const unsigned char* sb = ring + size_t(slot) * L.slot_bytes;
+                const T* vals0 = reinterpret_cast<const T*>(sb);
+                const T* vals1 = reinterpret_cast<const T*>(sb + size_t(W) * 32 * sizeof(T));
+                const uint16_t* cols = reinterpret_cast<const uint16_t*>(sb + size_t(NV) * W * 32 * sizeof(T));
+                const uint8_t* lens = sb + size_t(NV) * W * 32 * sizeof(T) + size_t(W) * 64;
+                const int len = landed ? int(lens[lane]) : 0;
+                T acc[VW];
+#pragma unroll
+                for (int c = 0; c < VW; ++c) acc[c] = T(0);
+                for (int k = kslot; k < len; k += KS) {
+                    const int col = cols[k * 32 + lane];
+                    T xv[VW];
+                    vld(xs + col * R + r0row, xv);
+                    if constexpr (NV == 1) {
+                        const T v = vals0[k * 32 + lane];
+#pragma unroll
+                        for (int c = 0; c < VW; ++c) acc[c] += v * xv[c];
+                    } else {
+#pragma unroll
+                        for (int c = 0; c < VW; ++c) acc[c] += (r0row + c == 0 ? vals0 : vals1)[k * 32 + lane] * xv[c];
+                    }
+                }
+                T* rb = red_s + size_t(cons & 1) * (kThreads / 32) * 32 * VW;
+                if constexpr (KS > 1) vst(rb + (wq * 32 + lane) * VW, acc);
+                // the slot and this pass's partial sums are complete
+                if (!__syncthreads_and(landed)) {
+                    if (threadIdx.x == 0) atomicExch(a.status, QPAT_ETIMEOUT);
+                    ok = false;
+                    break;
+                }
+                if (threadIdx.x == 0) {
+                    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                    issue(cons + S);
+                }
+                if (kslot == 0) {
+                    if constexpr (KS > 1) {
+#pragma unroll
+                        for (int c = 0; c < VW; ++c) acc[c] = T(0);
+                        for (int k2 = 0; k2 < KS; ++k2) {
+                            T pv[VW];
+                            vld(rb + ((k2 * NP + rpart) * 32 + lane) * VW, pv);
+#pragma unroll
+                            for (int c = 0; c < VW; ++c) acc[c] += pv[c];
+                        }
+                    }
+                    const int li = 32 * j + lane;
+                    if (li < nown) {
+                        T pv[VW];
+                        vld(xs + li * R + r0row, pv);
+                        const size_t e = size_t(ob + li) * R + r0row;
+                        vst(pc + e, pv);
+                        vst(a.q + e, acc);
+#pragma unroll
+                        for (int c = 0; c < VW; ++c) dotA[c] += pv[c] * acc[c];
+                    }
+                }
+            }
+            __syncthreads();  // xs is restaged for the next patch
+        }
+        if (!ok) {
+            drain();
+            return;
+        }
+        // p.q per RHS block: warp sums, then one thread per block feeds the grid reduction
+        if (kslot == 0) {
+#pragma unroll
+            for (int c = 0; c < VW; ++c) {
+                double v = double(dotA[c]);
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+                if (lane == 0) dot_s[rpart][c] = v;
+            }
+        }
+        __syncthreads();
+        double accA[1][VW];
+#pragma unroll
+        for (int c = 0; c < VW; ++c) accA[0][c] = threadIdx.x < NP ? dot_s[threadIdx.x][c] : 0.0;
+        if (!grid_reduce<1, VW, NP>(accA, scratch, a.partials, red_id, a.bar, a.status, a.spin_limit, red, cta,
+                                    ncta)) {
+            drain();
+            return;
+        }
+        if (threadIdx.x == 0) {
+            int bad = 0;
+            for (int r = 0; r < R; ++r) {
+                const bool act = rr[r] > a.rtol2 * bb[r];
+                const double pq = red[r];
+                if (act && !(pq > 0.0 && isfinite(pq))) bad = 1;
+                alpha[r] = act && pq > 0.0 ? rz[r] / pq : 0.0;
+            }
+            s_flag = bad;
+        }
+        __syncthreads();
+        if (s_flag) {
+            if (cta == 0 && threadIdx.x == 0) atomicCAS(a.status, 0, QPAT_EBREAKDOWN);
+            break;
+        }
+
+        // ---- phase B: x += alpha p, r -= alpha q; r.D^-1 r and r.r
+        T accB[2][VW];
+#pragma unroll
+        for (int c = 0; c < VW; ++c) accB[0][c] = accB[1][c] = 0.0;
+        {
+            T al[VW];
+#pragma unroll
+            for (int c = 0; c < VW; ++c) al[c] = T(alpha[r0 + c]);
+            for (int pt = cta; pt < P; pt += ncta) {
+                const int ob = __ldg(m.own_begin + pt), nown = __ldg(m.own_begin + pt + 1) - ob;
+                for (int i0 = threadIdx.x; i0 < nown * NP; i0 += kUnroll * blockDim.x) {
+                    T pv[kUnroll][VW], qv[kUnroll][VW], xv[kUnroll][VW], rv[kUnroll][VW], d[kUnroll][VW];
+                    size_t e[kUnroll];
+#pragma unroll
+                    for (int u = 0; u < kUnroll; ++u) {
+                        const int i = i0 + u * blockDim.x;
+                        const int g = ob + (i < nown * NP ? i : i0) / NP;
+                        e[u] = size_t(g) * R + r0;
+                        vld(pc + e[u], pv[u]);
+                        vld(a.q + e[u], qv[u]);
+                        vld(a.x + e[u], xv[u]);
+                        vld(a.r + e[u], rv[u]);
+                        dinv_vec<T, VW, OP>(a.invdiag, g, r0, d[u]);
+                    }
+#pragma unroll
+                    for (int u = 0; u < kUnroll; ++u) {
+                        if (u > 0 && i0 + u * int(blockDim.x) >= nown * NP) break;
+#pragma unroll
+                        for (int c = 0; c < VW; ++c) {
+                            xv[u][c] += al[c] * pv[u][c];
+                            rv[u][c] -= al[c] * qv[u][c];
+                            accB[0][c] += rv[u][c] * (d[u][c] * rv[u][c]);
+                            accB[1][c] += rv[u][c] * rv[u][c];
+                        }
+                        vst(a.x + e[u], xv[u]);
+                        vst(a.r + e[u], rv[u]);
+                    }
+                }
+            }
+        }
+        if (!grid_reduce<2, VW, NP>(accB, scratch, a.partials, red_id, a.bar, a.status, a.spin_limit, red, cta,
+                                    ncta)) {
+            drain();
+            return;
+        }
+        if (threadIdx.x < R) {
+            const int r = threadIdx.x;
+            const bool act = rr[r] > a.rtol2 * bb[r];
+            if (act) {
+                rz_old[r] = rz[r];
+                rz[r] = red[r];
+                rr[r] = red[R + r];
+            }
+        }
+        __syncthreads();
+        ++it;
+    }
+    drain();
+    if (cta == 0 && threadIdx.x < R) {
+        a.stats[threadIdx.x] = rr[threadIdx.x];
+        a.stats[R + threadIdx.x] = bb[threadIdx.x];
+        if (threadIdx.x == 0) *a.iters = it;
+    }
+}
+
+template <typename T, int R, int OP>
+__global__ void __launch_bounds__(kThreads, 4) k_pcg_ring(PcgArgs<T> a, RingLayout L) {
+    pcg_ring_body<T, R, OP>(a, L, blockIdx.x, gridDim.x);
 }
 
 // Independent problems (meshes of different sizes) in one cooperative
@@ -836,6 +1265,7 @@ cudaError_t batch_launch_t(const PcgBatchPlan& plan, cudaStream_t s) {
     const int* cb = plan.dev_cta_begin;
     int np = plan.nprob;
     void* args[] = {&pa, &cb, &np};
+    qpat::note_launch(1);
     return cudaLaunchCooperativeKernel((void*)kern, dim3(plan.grid), dim3(kThreads), args, plan.smem, s);
 }
 
@@ -891,12 +1321,94 @@ cudaError_t launch_pcg_t(const MeshDev& m, const OpParams<T>& op, const T* invdi
     err = cudaMemsetAsync(w.status, 0, sizeof(int), s);
     if (err != cudaSuccess) return err;
     void* args[] = {&a};
+    qpat::note_launch(1);
     return cudaLaunchCooperativeKernel((void*)kern, dim3(grid), dim3(kThreads), args, smem, s);
+}
+
+// Ring variant: picks the most slots (<= kMaxSlots) that keep min(4, P / SMs)
+// CTAs resident per SM; cudaErrorNotSupported when not even 2 slots fit.
+template <typename T, int R, int OP>
+cudaError_t launch_pcg_ring_t(const MeshDev& m, const OpParams<T>& op, const T* invdiag, const PcgWork& w,
+                              double rtol, int maxit, cudaStream_t s, int* grid_used) {
+    auto kern = k_pcg_ring<T, R, OP>;
+    int dev = 0, nsm = 0, smem_optin = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    cudaFuncAttributes fa{};
+    cudaError_t err = cudaFuncGetAttributes(&fa, kern);
+    if (err != cudaSuccess) return err;
+    const int dyn_max = smem_optin - int(fa.sharedSizeBytes);  // static + dynamic <= opt-in limit
+    err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn_max);
+    if (err != cudaSuccess) return err;
+    const int want = std::max(1, std::min(4, (m.P + nsm - 1) / nsm));
+    RingLayout L{};
+    int per_sm = 0;
+    bool found = false;
+    for (int S = kMaxSlots; S >= 2 && !found; --S) {
+        L = ring_layout<T, R, OP>(m.max_touched, m.sell_wmax, S);
+        if (L.total > dyn_max) continue;
+        err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, L.total);
+        if (err != cudaSuccess) return err;
+        found = per_sm >= want;
+    }
+    if (!found) return cudaErrorNotSupported;
+    int maxres = std::min(per_sm * nsm, kMaxGrid);
+    const int k = (m.P + maxres - 1) / maxres;
+    const int grid = (m.P + k - 1) / k;
+    if (grid_used) *grid_used = grid;
+    PcgArgs<T> a{};
+    a.m = m;
+    a.op = op;
+    a.invdiag = invdiag;
+    a.b = static_cast<const T*>(w.b);
+    a.x = static_cast<T*>(w.x);
+    a.r = static_cast<T*>(w.r);
+    a.p0 = static_cast<T*>(w.p0);
+    a.p1 = static_cast<T*>(w.p1);
+    a.q = static_cast<T*>(w.q);
+    a.partials = w.partials;
+    a.bar = w.bar;
+    a.status = w.status;
+    a.iters = w.iters;
+    a.stats = w.stats;
+    a.rtol2 = rtol * rtol;
+    a.maxit = maxit;
+    a.spin_limit = 40000000LL;
+    err = cudaMemsetAsync(w.bar, 0, 2 * sizeof(unsigned), s);
+    if (err != cudaSuccess) return err;
+    err = cudaMemsetAsync(w.status, 0, sizeof(int), s);
+    if (err != cudaSuccess) return err;
+    void* args[] = {&a, &L};
+    qpat::note_launch(1);
+    return cudaLaunchCooperativeKernel((void*)kern, dim3(grid), dim3(kThreads), args, size_t(L.total), s);
 }
 
 }  // namespace
 
 int pcg_max_grid() { return kMaxGrid; }
+
+template <typename T>
+cudaError_t launch_pcg_ring(const MeshDev& m, int OP, int R, const OpParams<T>& op, const T* invdiag,
+                            const PcgWork& w, double rtol, int maxit, cudaStream_t s, int* grid_used) {
+    if (OP == OP_CSR2) {
+        if (R != 2) return cudaErrorInvalidValue;
+        return launch_pcg_ring_t<T, 2, OP_CSR2>(m, op, invdiag, w, rtol, maxit, s, grid_used);
+    }
+    if (OP != OP_CSR1) return cudaErrorInvalidValue;
+    switch (R) {
+        case 1: return launch_pcg_ring_t<T, 1, OP_CSR1>(m, op, invdiag, w, rtol, maxit, s, grid_used);
+        case 2: return launch_pcg_ring_t<T, 2, OP_CSR1>(m, op, invdiag, w, rtol, maxit, s, grid_used);
+        case 4: return launch_pcg_ring_t<T, 4, OP_CSR1>(m, op, invdiag, w, rtol, maxit, s, grid_used);
+        case 8: return launch_pcg_ring_t<T, 8, OP_CSR1>(m, op, invdiag, w, rtol, maxit, s, grid_used);
+        case 16: return launch_pcg_ring_t<T, 16, OP_CSR1>(m, op, invdiag, w, rtol, maxit, s, grid_used);
+        default: return cudaErrorInvalidValue;
+    }
+}
+template cudaError_t launch_pcg_ring<double>(const MeshDev&, int, int, const OpParams<double>&, const double*,
+                                             const PcgWork&, double, int, cudaStream_t, int*);
+template cudaError_t launch_pcg_ring<float>(const MeshDev&, int, int, const OpParams<float>&, const float*,
+                                            const PcgWork&, double, int, cudaStream_t, int*);
 
 cudaError_t pcg_batch_prepare(int R, const std::vector<PcgBatchProblem>& probs, PcgBatchPlan& plan) {
     switch (R) {

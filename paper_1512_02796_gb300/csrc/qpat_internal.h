@@ -12,6 +12,10 @@
 
 namespace qpat {
 
+// Counts kernel launches of this library (one per launch statement; a
+// replayed CUDA graph counts its kernel nodes); read by qpat_launch_count.
+void note_launch(int n = 1);
+
 // Host-side mesh after preparation.  Node ids inside are LIBRARY ids: nodes
 // are sorted by the Morton code of their coordinates, so that a contiguous
 // range of library ids is a spatially compact block.  The ranges of
@@ -49,8 +53,9 @@ struct HostMesh {
     int64_t nslices = 0;
     std::vector<int64_t> sell_ptr;      // nslices + 1, in units of 32 entries
     std::vector<uint16_t> sell_col;     // 32 * sell_ptr[nslices]
-    std::vector<uint8_t> sell_len;      // row lengths (N)
+    std::vector<uint8_t> sell_len;      // row lengths (32 * nslices; 0 past row N - 1)
     std::vector<int32_t> sell_diag;     // k of the diagonal entry of each row (N)
+    int sell_wmax = 0;                  // widest slice (entries per row)
 };
 
 // Builds a HostMesh; returns "" on success or an error message.
@@ -86,6 +91,7 @@ struct MeshDev {
     const uint8_t* sell_len;
     const int* sell_diag;
     int64_t sell_entries;       // 32 * sell_ptr[nslices]
+    int sell_wmax;              // widest slice
 };
 
 }  // namespace qpat

@@ -220,6 +220,7 @@ struct Recon {
         ckq(prepare_K(M, kap, mu, L.opK, s, tag));
     }
     double residual(LinState& L) {
+        qpat::note_launch(1);
         k_wresid<<<GS(N * R)>>>(N, R, w, chi, L.mu, L.phi, nullptr, tmpR);
         return std::sqrt(dot(N * R, tmpR, tmpR));
     }
@@ -252,36 +253,51 @@ int lsqr(Recon& rc, LinState& L, const OpState& P, const double* b, int kappa_on
         rc.ck(cudaMemsetAsync(x, 0, 2 * N * sizeof(double), s), "memset");
         return 0;
     }
+    qpat::note_launch(1);
     k_scal_set<<<1, 32, 0, s>>>(S, S_BETA, S_T0, 0);
+    qpat::note_launch(1);
     k_scale_inv<<<GS(N * R)>>>(N * R, S, S_BETA, u);
     // p = A^T u ; z = P^-1 p ; alpha ; v, q ; w_d = v ; x = 0
     rc.ckq(vjp_lib(rc.M, rc.so, L, u, o1, o2, s));
+    qpat::note_launch(1);
     k_p_update<<<GS(N)>>>(N, o1, o2, q, S, 1, kappa_only, p);
     rc.ckq(solve(rc.M, P, rc.so, 2, p, z, s));
     rc.ck(launch_dots<double>(2 * N, 1, p, z, rc.dpart, S + S_T1, s), "dot");
+    qpat::note_launch(1);
     k_scal_set<<<1, 32, 0, s>>>(S, S_ALPHA, S_T1, 0);
+    qpat::note_launch(1);
     k_vq<<<GS(2 * N)>>>(2 * N, z, p, S, v, q, 1, wd, x);
+    qpat::note_launch(1);
     k_lsqr_init_scalars<<<1, 32, 0, s>>>(S, rc.hist);
     hist_out[0] = std::sqrt(bb);
     int m = 0;
     while (m < maxit) {
         ++m;
         // u = (A v - alpha u) / beta
+        qpat::note_launch(1);
         k_unpack_beta<<<GS(N)>>>(N, v, kappa_only, s1, s2);
         rc.ckq(jvp_lib(rc.M, rc.so, L, s1, s2, Av, s));
+        qpat::note_launch(1);
         k_uh<<<GS(N * R)>>>(N * R, Av, S, u, 0);
         rc.ck(launch_dots<double>(N * R, 1, u, u, rc.dpart, S + S_T0, s), "dot");
+        qpat::note_launch(1);
         k_scal_set<<<1, 32, 0, s>>>(S, S_BETA, S_T0, 0);
+        qpat::note_launch(1);
         k_scale_inv<<<GS(N * R)>>>(N * R, S, S_BETA, u);
         // p = A^T u - beta q ; z = P^-1 p ; alpha = sqrt(p.z) ; v = z/alpha ; q = p/alpha
         rc.ckq(vjp_lib(rc.M, rc.so, L, u, o1, o2, s));
+        qpat::note_launch(1);
         k_p_update<<<GS(N)>>>(N, o1, o2, q, S, 0, kappa_only, p);
         rc.ckq(solve(rc.M, P, rc.so, 2, p, z, s));
         rc.ck(launch_dots<double>(2 * N, 1, p, z, rc.dpart, S + S_T1, s), "dot");
+        qpat::note_launch(1);
         k_scal_set<<<1, 32, 0, s>>>(S, S_ALPHA, S_T1, 0);
+        qpat::note_launch(1);
         k_vq<<<GS(2 * N)>>>(2 * N, z, p, S, v, q, 0, wd, x);
         // rotation, then x and w_d
+        qpat::note_launch(1);
         k_givens<<<1, 32, 0, s>>>(S, rc.hist, m);
+        qpat::note_launch(1);
         k_xw<<<GS(2 * N)>>>(2 * N, S, v, x, wd);
         rc.ck(cudaMemcpyAsync(rc.M->host_scratch, S + S_PHIBAR, sizeof(double), cudaMemcpyDeviceToHost, s), "copy");
         rc.ck(cudaStreamSynchronize(s), "sync");
@@ -343,6 +359,7 @@ extern "C" int qpat_reconstruct(qpat_mesh_t M, const qpat_params* prm_in, int K,
         rc.ck(cudaMemcpyAsync(hsig, sigma, sizeof(double) * K * N, cudaMemcpyHostToDevice, s), "H2D");
         rc.ck(launch_to_lib<double, double>(M->d, K, R, hchi, rc.chi, s), "to_lib");
         rc.ck(launch_to_lib<double, double>(M->d, K, R, hsig, sig_l, s), "to_lib");
+        qpat::note_launch(1);
         k_inv_sigma<<<GS(N * R)>>>(N, K, R, sig_l, rc.w);
 
         double* kapA = rc.buf("kapA", N);
@@ -361,7 +378,9 @@ extern "C" int qpat_reconstruct(qpat_mesh_t M, const qpat_params* prm_in, int K,
         LinState LA, LB;
 
         auto forward_const = [&](double k, double m, LinState& L, double* kp, double* mp, double* ph) {
+            qpat::note_launch(1);
             k_fill<<<GS(N)>>>(N, k, kp);
+            qpat::note_launch(1);
             k_fill<<<GS(N)>>>(N, m, mp);
             rc.lin(L, kp, mp, ph, "rKA");
             rc.ckq(forward_lib(M, rc.so, L, rc.flux, s));
@@ -392,12 +411,15 @@ extern "C" int qpat_reconstruct(qpat_mesh_t M, const qpat_params* prm_in, int K,
             double* jbv = rc.buf("jbv", N * R);
             double* one = rc.buf("one", N);
             double* zero = rc.buf("zero", N);
+            qpat::note_launch(1);
             k_fill<<<GS(N)>>>(N, 1.0, one);
+            qpat::note_launch(1);
             k_fill<<<GS(N)>>>(N, 0.0, zero);
             for (int it = 0; it < prm.fit_gn_steps; ++it) {
                 const double r0 = forward_const(std::exp(ba), std::exp(bb), LA, kapA, muA, phiA);
                 rc.ckq(jvp_lib(M, rc.so, LA, one, zero, ja, s));
                 rc.ckq(jvp_lib(M, rc.so, LA, zero, one, jbv, s));
+                qpat::note_launch(1);
                 k_wresid<<<GS(N * R)>>>(N, R, rc.w, rc.chi, LA.mu, LA.phi, nullptr, rc.tmpR);
                 const double aa = rc.dot(N * R, ja, ja), ab = rc.dot(N * R, ja, jbv), bbv = rc.dot(N * R, jbv, jbv);
                 const double ra = rc.dot(N * R, ja, rc.tmpR), rb = rc.dot(N * R, jbv, rc.tmpR);
@@ -427,27 +449,35 @@ extern "C" int qpat_reconstruct(qpat_mesh_t M, const qpat_params* prm_in, int K,
 
         // ---- initialisation: phi0 at the constants, mu_tilde_init, kappa_tilde_init = 0
         forward_const(k0, m0, LA, kapA, muA, phiA);
+        qpat::note_launch(1);
         k_mu_init<<<GS(N)>>>(N, K, R, rc.chi, LA.phi, m0, beta);
 
         // ---- step 0: kappa-only LSQR with M_delta(kappa_tilde_init)
+        qpat::note_launch(1);
         k_coef_from_beta<<<GS(N)>>>(N, 0, k0, beta, kapA);
+        qpat::note_launch(1);
         k_coef_from_beta<<<GS(N)>>>(N, 1, m0, beta, muA);
         rc.lin(LA, kapA, muA, phiA, "rKA");
         rc.ckq(forward_lib(M, rc.so, LA, rc.flux, s));
+        qpat::note_launch(1);
         k_wresid<<<GS(N * R)>>>(N, R, rc.w, rc.chi, LA.mu, LA.phi, nullptr, ytil);
         double* ktmp = rc.buf("ktv", N);
         double* mtmp = rc.buf("mtv", N);
+        qpat::note_launch(1);
         k_unpack_beta<<<GS(N)>>>(N, beta, 0, ktmp, mtmp);
         OpState P;
         rc.ckq(prepare_prior(M, ktmp, mtmp, prm.T, prm.b_over_a, prm.delta, P, s));
         std::vector<double> hist;
         int it0 = lsqr(rc, LA, P, ytil, 1, prm, xls, hist);
+        qpat::note_launch(1);
         k_add_beta<<<GS(N)>>>(N, xls, 1, beta);
         report.lsqr_iters[0] = it0;
         report.linearisations = 1;
 
         // ---- h(beta^(0))
+        qpat::note_launch(1);
         k_coef_from_beta<<<GS(N)>>>(N, 0, k0, beta, kapA);
+        qpat::note_launch(1);
         k_coef_from_beta<<<GS(N)>>>(N, 1, m0, beta, muA);
         rc.lin(LA, kapA, muA, phiA, "rKA");
         rc.ckq(forward_lib(M, rc.so, LA, rc.flux, s));
@@ -463,13 +493,16 @@ extern "C" int qpat_reconstruct(qpat_mesh_t M, const qpat_params* prm_in, int K,
 
         while (report.linearisations < prm.max_lin) {
             // step 1: y-tilde = w o (chi - h + J beta)   (J unweighted here)
+            qpat::note_launch(1);
             k_unpack_beta<<<GS(N)>>>(N, beta, 0, s1, s2);
             double* wsave = cur->w;
             cur->w = nullptr;
             rc.ckq(jvp_lib(M, rc.so, *cur, s1, s2, jb, s));
             cur->w = wsave;
+            qpat::note_launch(1);
             k_wresid<<<GS(N * R)>>>(N, R, rc.w, rc.chi, cur->mu, cur->phi, jb, ytil);
             // step 2: M_delta from the current iterate
+            qpat::note_launch(1);
             k_unpack_beta<<<GS(N)>>>(N, beta, 0, ktmp, mtmp);
             rc.ckq(prepare_prior(M, ktmp, mtmp, prm.T, prm.b_over_a, prm.delta, P, s));
             // step 3: LSQR from zero
@@ -477,7 +510,9 @@ extern "C" int qpat_reconstruct(qpat_mesh_t M, const qpat_params* prm_in, int K,
             report.lsqr_iters[report.linearisations] = it;
             report.linearisations += 1;
             // step 4: accept only if the nonlinear residual decreased
+            qpat::note_launch(1);
             k_coef_from_beta<<<GS(N)>>>(N, 0, k0, betaN, kapN);
+            qpat::note_launch(1);
             k_coef_from_beta<<<GS(N)>>>(N, 1, m0, betaN, muN);
             rc.lin(*nxt, kapN, muN, phiN, tagN);
             rc.ckq(forward_lib(M, rc.so, *nxt, rc.flux, s));
@@ -496,7 +531,9 @@ extern "C" int qpat_reconstruct(qpat_mesh_t M, const qpat_params* prm_in, int K,
             if (nres < 33) report.residuals[nres++] = r_cur;
         }
         // ---- output kappa = k0 exp(kt), mu = m0 exp(mt) in caller order
+        qpat::note_launch(1);
         k_coef_from_beta<<<GS(N)>>>(N, 0, k0, beta, s1);
+        qpat::note_launch(1);
         k_coef_from_beta<<<GS(N)>>>(N, 1, m0, beta, s2);
         double* outk = rc.buf("outk", N);
         double* outm = rc.buf("outm", N);

@@ -332,9 +332,11 @@ int qpat_unet_predict_dev(qpat_unet_t U, const float* x, int B, float* y, void* 
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const int64_t nv = int64_t(U->n) * U->n * U->n;
     for (int b = 0; b < B; ++b) {
+        qpat::note_launch(1);
         k_pack_input<<<g1(nv * 16), 256, 0, s>>>(nv, x + b * nv * 3, U->xin);
         int rc = unet_forward(U, s);
         if (rc) return rc;
+        qpat::note_launch(1);
         k_take_channel0<<<g1(nv), 256, 0, s>>>(nv, U->y32, y + b * nv);
     }
     UCK(cudaGetLastError());
@@ -348,13 +350,17 @@ int qpat_unet_train_dev(qpat_unet_t U, const float* x, const float* t, int B, fl
     const int64_t nv = int64_t(U->n) * U->n * U->n;
     UCK(cudaMemsetAsync(U->loss, 0, sizeof(float), s));
     for (int b = 0; b < B; ++b) {
+        qpat::note_launch(1);
         k_pack_input<<<g1(nv * 16), 256, 0, s>>>(nv, x + b * nv * 3, U->xin);
         int rc = unet_forward(U, s);
         if (rc) return rc;
+        qpat::note_launch(1);
         k_mse<<<g1(nv), 256, 0, s>>>(nv, U->y32, t + b * nv, 1.f / float(nv * B), U->g_y, U->loss);
         if ((rc = unet_backward(U, s))) return rc;
         for (auto& c : U->conv) {
+            qpat::note_launch(1);
             k_axpy32<<<g1(c.nw()), 256, 0, s>>>(c.nw(), 1.f, c.gw, c.aw, b == 0);
+            qpat::note_launch(1);
             k_axpy32<<<1, 256, 0, s>>>(c.cout, 1.f, c.gb, c.ab, b == 0);
         }
     }
@@ -391,6 +397,7 @@ int qpat_unet_features_dev(qpat_mesh_t M, const double* kappa, const double* mu,
     UCK(cudaMemsetAsync(f, 0, N * R * sizeof(double), s));
     UCK(launch_load(M->d, K, R, flux_face, f, s));
     UCK((launch_from_lib<double, double>(M->d, K, R, f, fc, s)));
+    qpat::note_launch(K);
     for (int k = 0; k < K; ++k) k_features<<<g1(N), 256, 0, s>>>(N, mu, kappa, fc + k * N, 1.0 / (h * h), x + k * N * 3);
     UCK(cudaGetLastError());
     return QPAT_OK;
@@ -398,6 +405,7 @@ int qpat_unet_features_dev(qpat_mesh_t M, const double* kappa, const double* mu,
 
 // float predictions -> double initial guess
 int qpat_unet_to_double_dev(const float* y, int64_t count, double* out, void* stream) {
+    qpat::note_launch(1);
     k_f32_to_f64<<<g1(count), 256, 0, static_cast<cudaStream_t>(stream)>>>(count, y, out);
     UCK(cudaGetLastError());
     return QPAT_OK;

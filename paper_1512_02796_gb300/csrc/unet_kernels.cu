@@ -114,6 +114,7 @@ cudaError_t conv_fwd_t(const bf16* in, int Cin, const bf16* w, const float* bias
     if (e != cudaSuccess) return e;
     const int nvox = n * n * n;
     const int grid = (nvox + 16 * kConvWarps - 1) / (16 * kConvWarps);
+    qpat::note_launch(1);
     k_conv_fwd<NT><<<grid, kConvWarps * 32, smem, s>>>(in, Cin, w, bias, Cout, relu, out, out32, n);
     return cudaGetLastError();
 }
@@ -209,6 +210,7 @@ cudaError_t wgrad_t(const bf16* in, int Cin, const bf16* dy, int Cout, float* pa
     const int nvox = n * n * n;
     const int chunks = (nvox + kWgradVox - 1) / kWgradVox;
     dim3 grid(chunks, 27, Cout / 16);
+    qpat::note_launch(1);
     k_conv_wgrad<NCI><<<grid, 128, 0, s>>>(in, Cin, dy, Cout, partial, n);
     return cudaGetLastError();
 }
@@ -365,39 +367,50 @@ cudaError_t conv3d_wgrad(const bf16* in, int Cin, const bf16* dy, int Cout, floa
     }
     if (e != cudaSuccess) return e;
     const int64_t count = int64_t(27) * Cout * Cin;
+    qpat::note_launch(1);
     k_sum_chunks<<<grid1d(count), 256, 0, s>>>(partial, wgrad_chunks(n), count, dw);
-    if (db) k_bias_grad<<<Cout, 256, 0, s>>>(dy, Cout, n * n * n, db);
+    if (db) {
+        qpat::note_launch(1);
+        k_bias_grad<<<Cout, 256, 0, s>>>(dy, Cout, n * n * n, db);
+    }
     return cudaGetLastError();
 }
 
 cudaError_t flip_weights(const bf16* w, int Cin, int Cout, bf16* w_t, cudaStream_t s) {
+    qpat::note_launch(1);
     k_flip<<<grid1d(int64_t(27) * Cin * Cout), 256, 0, s>>>(w, Cin, Cout, w_t);
     return cudaGetLastError();
 }
 
 cudaError_t relu_mask(bf16* dy, const bf16* y, int64_t count, cudaStream_t s) {
+    qpat::note_launch(1);
     k_relu_mask<<<grid1d(count), 256, 0, s>>>(dy, y, count);
     return cudaGetLastError();
 }
 
 cudaError_t avgpool(const bf16* in, int C, int n, bf16* out, cudaStream_t s) {
+    qpat::note_launch(1);
     k_avgpool<<<grid1d(int64_t(n / 2) * (n / 2) * (n / 2) * C), 256, 0, s>>>(in, C, n, out);
     return cudaGetLastError();
 }
 
 cudaError_t avgpool_bwd(const bf16* dout, int C, int n, bf16* din, int accumulate, cudaStream_t s) {
+    qpat::note_launch(1);
     k_avgpool_bwd<<<grid1d(int64_t(n) * n * n * C), 256, 0, s>>>(dout, C, n, din, accumulate);
     return cudaGetLastError();
 }
 
 cudaError_t upcat(const bf16* lo, int Clo, const bf16* skip, int Cs, int n, bf16* cat, cudaStream_t s) {
+    qpat::note_launch(1);
     k_upcat<<<grid1d(int64_t(n) * n * n * (Clo + Cs)), 256, 0, s>>>(lo, Clo, skip, Cs, n, cat);
     return cudaGetLastError();
 }
 
 cudaError_t upcat_bwd(const bf16* dcat, int Clo, int Cs, int n, bf16* dlo, bf16* dskip, int accumulate_skip,
                       cudaStream_t s) {
+    qpat::note_launch(1);
     k_upcat_bwd_lo<<<grid1d(int64_t(n / 2) * (n / 2) * (n / 2) * Clo), 256, 0, s>>>(dcat, Clo, Cs, n, dlo);
+    qpat::note_launch(1);
     k_upcat_bwd_skip<<<grid1d(int64_t(n) * n * n * Cs), 256, 0, s>>>(dcat, Clo, Cs, n, dskip, accumulate_skip);
     return cudaGetLastError();
 }
@@ -405,16 +418,19 @@ cudaError_t upcat_bwd(const bf16* dcat, int Clo, int Cs, int n, bf16* dlo, bf16*
 cudaError_t adam(float* w, bf16* wb, const float* g, float* m, float* v, int64_t count, float lr, float b1, float b2,
                  float eps, int step, cudaStream_t s) {
     const float c1 = 1.f - powf(b1, float(step)), c2 = 1.f - powf(b2, float(step));
+    qpat::note_launch(1);
     k_adam<<<grid1d(count), 256, 0, s>>>(w, wb, g, m, v, count, lr, b1, b2, eps, c1, c2);
     return cudaGetLastError();
 }
 
 cudaError_t f32_to_bf16(const float* in, bf16* out, int64_t count, cudaStream_t s) {
+    qpat::note_launch(1);
     k_f2b<<<grid1d(count), 256, 0, s>>>(in, out, count);
     return cudaGetLastError();
 }
 
 cudaError_t bf16_to_f32(const bf16* in, float* out, int64_t count, cudaStream_t s) {
+    qpat::note_launch(1);
     k_b2f<<<grid1d(count), 256, 0, s>>>(in, out, count);
     return cudaGetLastError();
 }

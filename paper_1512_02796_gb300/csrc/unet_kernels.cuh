@@ -10,6 +10,10 @@
 #pragma once
 
 #include <cuda_bf16.h>
+
+namespace qpat {
+void note_launch(int n);  // launch counter (abi.cu)
+}
 #include <cuda_runtime.h>
 
 #include <cstdint>

@@ -70,6 +70,7 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
     sig = {
         "qpat_default_params": (None, [ctypes.POINTER(qpat_params)]),
         "qpat_last_error": (ctypes.c_char_p, []),
+        "qpat_launch_count": (ctypes.c_int64, []),
         "qpat_mesh": (ctypes.c_int, [_c_double_p, ctypes.c_int64, _c_int32_p, ctypes.c_int64, ctypes.POINTER(vp)]),
         "qpat_mesh_ex": (ctypes.c_int, [_c_double_p, ctypes.c_int64, _c_int32_p, ctypes.c_int64, ctypes.c_int,
                                         ctypes.POINTER(vp)]),
@@ -148,7 +149,7 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
 
 def exported_names() -> Sequence[str]:
     return [
-        "qpat_default_params", "qpat_last_error", "qpat_mesh", "qpat_mesh_ex", "qpat_mesh_free",
+        "qpat_default_params", "qpat_last_error", "qpat_launch_count", "qpat_mesh", "qpat_mesh_ex", "qpat_mesh_free",
         "qpat_mesh_host_info", "qpat_mesh_num_nodes", "qpat_mesh_num_tets", "qpat_mesh_num_faces", "qpat_mesh_num_patches",
         "qpat_mesh_num_entries",
         "qpat_mesh_faces", "qpat_mesh_permutation", "qpat_mesh_stats", "qpat_mesh_reset_stats",
@@ -276,6 +277,11 @@ def _dp(a: Optional[np.ndarray]):
 
 def _f64(a) -> np.ndarray:
     return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def qpat_launch_count() -> int:
+    """Kernels launched by the library so far in this process."""
+    return int(load().qpat_launch_count())
 
 
 def qpat_default_params(**overrides) -> qpat_params:

@@ -76,3 +76,8 @@ def test_host_mesh_rejects_bad_input():
         Q.qpat_mesh_host_info(xyz, flat, 32)
     with pytest.raises(Q.QpatError):
         Q.qpat_mesh_host_info(xyz, tets, 8)   # patch size below the minimum
+
+
+def test_launch_counter_is_callable_without_a_gpu():
+    # a host-side counter: no kernel has been launched by the CPU test process
+    assert Q.qpat_launch_count() >= 0

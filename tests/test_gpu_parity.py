@@ -63,8 +63,10 @@ def test_apply_K(case, precision, tol, R):
     assert rel(yt.cpu().numpy(), y_ref) < tol
 
 
-# pcg_variant 1: two grid reductions per PCG iteration, 2: one (Chronopoulos-Gear)
-@pytest.mark.parametrize("precision,fp32_op,variant", [(0, 0, 1), (0, 0, 2), (1, 0, 1), (1, 1, 1), (1, 1, 2)])
+# pcg_variant 1: two grid reductions per PCG iteration, 2: one (Chronopoulos-Gear),
+# 3: two, with the operator streamed through a shared-memory ring by bulk copies
+@pytest.mark.parametrize("precision,fp32_op,variant", [(0, 0, 1), (0, 0, 2), (0, 0, 3), (1, 0, 1), (1, 1, 1),
+                                                       (1, 1, 2), (1, 1, 3)])
 def test_forward(case, precision, fp32_op, variant):
     phi, h = Q.qpat_forward(case.lib, case.kappa, case.mu, case.flux,
                             _params(precision, fp32_operator=fp32_op, pcg_variant=variant))
@@ -118,7 +120,7 @@ def test_pair_matches_separate_calls(case):
     assert rel(ov.cpu().numpy(), O.vjp(case.om, case.kappa, case.mu, case.phi, t, case.w, case.fac)) < 1e-10
 
 
-@pytest.mark.parametrize("variant", [1, 2])
+@pytest.mark.parametrize("variant", [1, 2, 3])
 @pytest.mark.parametrize("precision", [0, 1])
 def test_prior_solve(case, precision, variant):
     rng = np.random.default_rng(9)
@@ -143,7 +145,7 @@ def test_prior_solve(case, precision, variant):
     assert rel(out, ref) < max(tol, 1e-10)
 
 
-@pytest.mark.parametrize("variant", [1, 2])
+@pytest.mark.parametrize("variant", [1, 2, 3])
 def test_forward_k_padding_and_zero_flux(case, variant):
     # a zero illumination next to real ones: padded / inactive RHS stay exactly 0
     fl = np.vstack([case.flux, np.zeros_like(case.flux[:1])])
@@ -152,3 +154,9 @@ def test_forward_k_padding_and_zero_flux(case, variant):
     phi, _ = Q.qpat_forward(case.lib, case.kappa, case.mu, fl, _params(0, pcg_variant=variant))
     assert np.all(phi[-1] == 0.0)
     assert rel(phi[:-1], case.phi) < 1e-10
+
+
+def test_launch_counter_counts_the_solve(case):
+    n0 = Q.qpat_launch_count()
+    Q.qpat_forward(case.lib, case.kappa, case.mu, case.flux)
+    assert Q.qpat_launch_count() - n0 >= 2   # at least assembly + one PCG launch
