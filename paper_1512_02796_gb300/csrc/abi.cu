@@ -286,6 +286,10 @@ int solve(qpat_mesh_s* M, const OpState& st, const SolveOpts& so_in, int R, cons
     if (so.precision == 0) {
         w.b = const_cast<double*>(B);
         w.x = X;
+        // z = D^-1 r kept by the owner: the halo staging then needs one FP64
+        // FMA per value instead of a multiply and an FMA
+        w.z = M->ws.get_bytes(nm("z"), n * esz, s, &e);
+        if (e != cudaSuccess) return cuda_fail(e, "workspace");
         const int OP = st.kind == OP_K ? OP_CSR1 : OP_CSR2;
         OpParams<double> op{st.c1_64, st.c2_64, st.inv_T2, st.scale1, st.delta, 1, st.v64[0], st.v64[1]};
         if (M->timing) cudaEventRecord(M->ev0, s);

@@ -70,6 +70,7 @@ struct PcgWork {
     void* p0;
     void* p1;
     void* q;
+    void* z = nullptr;  // optional N x R: D^-1 r kept by the owner (saves a multiply per halo node)
     // extra vectors of the single-reduction variant (see pcg.cu)
     void* r1 = nullptr;
     void* s0 = nullptr;

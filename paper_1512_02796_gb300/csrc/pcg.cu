@@ -49,6 +49,7 @@ struct PcgArgs {
     double rtol2;
     int maxit;
     long long spin_limit;
+    T* z;   // optional: z = D^-1 r stored by the owner (two-reduction kernel)
     T* r1;  // single-reduction variant
     T* s0;
     T* s1;
@@ -183,17 +184,45 @@ __device__ __forceinline__ bool grid_reduce(T (&acc)[NQ][VW], double* scratch, d
     __shared__ int s_last;
     __shared__ int s_ok;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    // Warp sums by reduce-scatter: the NQ x VW values of a thread are padded
+    // to P2 (a power of two); at each shuffle level the lanes whose level bit
+    // is clear keep the lower half of their set and the others the upper
+    // half, each adding its partner's copy, so the set halves instead of
+    // every lane adding every value at every level.  Lanes that differ in a
+    // bit below NP hold different RHS blocks and are never paired.
+    constexpr int V = NQ * VW;
+    constexpr int P2 = V <= 1 ? 1 : V <= 2 ? 2 : V <= 4 ? 4 : V <= 8 ? 8 : 16;
+    static_assert(V <= 16, "at most 16 values per thread");
+    T v[P2];
 #pragma unroll
-    for (int q = 0; q < NQ; ++q)
+    for (int f = 0; f < P2; ++f) v[f] = f < V ? acc[f / VW][f % VW] : T(0);
+    int base = 0, nkeep = P2, dup_mask = 0;
 #pragma unroll
-        for (int c = 0; c < VW; ++c)
+    for (int o = 16; o >= NP; o >>= 1) {
+        if (nkeep > 1) {
+            const int h = nkeep / 2;
+            const bool up = (lane & o) != 0;
 #pragma unroll
-            for (int o = 16; o >= NP; o >>= 1) acc[q][c] += __shfl_down_sync(0xffffffffu, acc[q][c], o);
-    if (lane < NP)
+            for (int i = 0; i < h; ++i) {
+                const T send = up ? v[i] : v[h + i];
+                const T recv = __shfl_xor_sync(0xffffffffu, send, o);
+                v[i] = (up ? v[h + i] : v[i]) + recv;
+            }
+            if (up) base += h;
+            nkeep = h;
+        } else {
+            v[0] += __shfl_xor_sync(0xffffffffu, v[0], o);
+            dup_mask |= o;  // both partners now hold the same sum
+        }
+    }
+    if ((lane & dup_mask) == 0) {
+        const int part = lane & (NP - 1);
 #pragma unroll
-        for (int q = 0; q < NQ; ++q)
-#pragma unroll
-            for (int c = 0; c < VW; ++c) scratch[warp * NS + q * R + lane * VW + c] = double(acc[q][c]);
+        for (int i = 0; i < nkeep; ++i) {
+            const int f = base + i;
+            if (f < V) scratch[warp * NS + (f / VW) * R + part * VW + (f % VW)] = double(v[i]);
+        }
+    }
     __syncthreads();
     double* part = partials + size_t(red_id & 1) * kMaxGrid * kMaxNS;
     double* res = partials + size_t(2) * kMaxGrid * kMaxNS + (red_id & 1) * kMaxNS;
@@ -281,6 +310,7 @@ __device__ __forceinline__ void pcg_body(const PcgArgs<T>& a, const int cta, con
     const int P = m.P;
     const int part = threadIdx.x % NP;  // this thread's RHS block [part*VW, part*VW + VW)
     const int r0 = part * VW;
+    const bool zs = a.z != nullptr;
     int red_id = 0;
 
     // ---- initial residual r = b (x0 = 0)
@@ -293,17 +323,19 @@ __device__ __forceinline__ void pcg_body(const PcgArgs<T>& a, const int cta, con
             for (int i = threadIdx.x; i < nown * NP; i += blockDim.x) {
                 const int g = ob + i / NP;
                 const size_t e = size_t(g) * R + r0;
-                T bv[VW], d[VW], zero[VW];
+                T bv[VW], d[VW], zero[VW], zv[VW];
                 vld(a.b + e, bv);
                 dinv_vec<T, VW, OP>(a.invdiag, g, r0, d);
 #pragma unroll
                 for (int c = 0; c < VW; ++c) {
                     zero[c] = T(0);
+                    zv[c] = d[c] * bv[c];
                     acc[0][c] += bv[c] * bv[c];
-                    acc[1][c] += bv[c] * (d[c] * bv[c]);
+                    acc[1][c] += bv[c] * zv[c];
                 }
                 vst(a.x + e, zero);
                 vst(a.r + e, bv);
+                if (a.z) vst(a.z + e, zv);
             }
         }
 #pragma unroll
@@ -365,15 +397,20 @@ __device__ __forceinline__ void pcg_body(const PcgArgs<T>& a, const int cta, con
                     li[u] = (i < nt * NP ? i : i0) / NP;
                     const int g = __ldg(m.nodes + nb + li[u]);
                     const size_t e = size_t(g) * R + r0;
-                    vld_cg(a.r + e, rv[u]);
-                    dinv_vec<T, VW, OP>(a.invdiag, g, r0, d[u]);
+                    if (zs) {
+                        vld_cg(a.z + e, rv[u]);  // z = D^-1 r from its owner
+                    } else {
+                        vld_cg(a.r + e, rv[u]);
+                        dinv_vec<T, VW, OP>(a.invdiag, g, r0, d[u]);
+                    }
                     if (it > 0) vld_cg(pp + e, po[u]);
                 }
 #pragma unroll
                 for (int u = 0; u < kUnroll; ++u) {
                     T pv[VW];
 #pragma unroll
-                    for (int c = 0; c < VW; ++c) pv[c] = d[u][c] * rv[u][c] + (it > 0 ? bt[c] * po[u][c] : T(0));
+                    for (int c = 0; c < VW; ++c)
+                        pv[c] = (zs ? rv[u][c] : d[u][c] * rv[u][c]) + (it > 0 ? bt[c] * po[u][c] : T(0));
                     if (u == 0 || i0 + u * int(blockDim.x) < nt * NP) vst(s.xin + li[u] * R + r0, pv);
                 }
             }
@@ -449,15 +486,18 @@ __device__ __forceinline__ void pcg_body(const PcgArgs<T>& a, const int cta, con
                     vld(a.x + e, xv);
                     vld(a.r + e, rv);
                     dinv_vec<T, VW, OP>(a.invdiag, g, r0, d);
+                    T zv[VW];
 #pragma unroll
                     for (int c = 0; c < VW; ++c) {
                         xv[c] += al[c] * pv[c];
                         rv[c] -= al[c] * qv[c];
-                        accB[0][c] += rv[c] * (d[c] * rv[c]);
+                        zv[c] = d[c] * rv[c];
+                        accB[0][c] += rv[c] * zv[c];
                         accB[1][c] += rv[c] * rv[c];
                     }
                     vst(a.x + e, xv);
                     vst(a.r + e, rv);
+                    if (zs) vst(a.z + e, zv);
                 }
             }
         }
@@ -1311,6 +1351,7 @@ cudaError_t launch_pcg_t(const MeshDev& m, const OpParams<T>& op, const T* invdi
     a.rtol2 = rtol * rtol;
     a.maxit = maxit;
     a.spin_limit = 40000000LL;  // about 2 s of __nanosleep(32) spins
+    a.z = static_cast<T*>(w.z);
     a.r1 = static_cast<T*>(w.r1);
     a.s0 = static_cast<T*>(w.s0);
     a.s1 = static_cast<T*>(w.s1);
