@@ -83,7 +83,14 @@ typedef struct {
                               shared-memory ring by bulk copies (QPAT_EINVAL
                               if the ring does not fit).  Matrix-free FP32
                               runs always use 1. */
-    int reserved[5];
+    int prior;             /* r(t) of the prior R(u) = integral r(|grad u|), Eq. (9):
+                              0 = Perona-Malik, Eq. (10) (the paper's examples);
+                              1 = smoothed TV^q, r(t) = (t^2 + T^2)^(q/2) / q, one
+                              of the alternatives named after Eq. (10) (q = 1:
+                              smoothed total variation).  The lagged step
+                              weights each tet by r'(t)/t (Eq. (14)). */
+    int reserved[4];
+    double prior_q;        /* q of prior 1, in (0, 2] */
 } qpat_params;
 
 /* Report of qpat_reconstruct (Algorithm 1). */

@@ -38,7 +38,7 @@ __all__ = [
     "Mesh", "QpatParams", "tet_geometry", "boundary_faces", "face_areas",
     "int_bary_tet", "int_bary_tri", "assemble_stiffness", "assemble_weighted_mass",
     "assemble_robin", "load_vector", "load_vector_nodal", "flux_patch", "system_matrix", "Factor",
-    "forward", "G1_matrix", "G2_matrix", "jvp", "vjp", "lagged_weights",
+    "forward", "G1_matrix", "G2_matrix", "jvp", "vjp", "lagged_weights", "tvq_r", "tvq_rprime",
     "prior_matrix", "prior_solve", "lsqr_prior", "fit_background", "init_mu",
     "reconstruct", "measure", "nonlinear_residual", "simulate_data",
 ]
@@ -350,30 +350,49 @@ def pm_rprime(t, T):
     return t / (1.0 + (t / T) ** 2)
 
 
-def lagged_weights(mesh: Mesh, u: np.ndarray, T: float) -> np.ndarray:
+def tvq_r(t, T, q):
+    """Smoothed TV^q, one of the alternatives to Eq. (10) named in Sec. 3:
+    r(t) = (t^2 + T^2)^(q/2) / q (q = 1: smoothed total variation; the
+    smoothing T makes r continuously differentiable at t = 0, as Eq. (9)
+    requires)."""
+    return (t * t + T * T) ** (q / 2.0) / q
+
+
+def tvq_rprime(t, T, q):
+    """d/dt of tvq_r: t (t^2 + T^2)^(q/2 - 1)."""
+    return t * (t * t + T * T) ** (q / 2.0 - 1.0)
+
+
+def lagged_weights(mesh: Mesh, u: np.ndarray, T: float, prior: int = 0, q: float = 1.0) -> np.ndarray:
     """c_u = r'(|grad u|) / |grad u| on every tet (Eq. (14)); grad u is
-    constant on a tet for P1 u.  At |grad u| = 0 the limit value 1 is used."""
+    constant on a tet for P1 u.  prior 0: Perona-Malik (Eq. (10)); prior 1:
+    smoothed TV^q (tvq_r).  At |grad u| = 0 the limit value is used: 1 for
+    Perona-Malik, T^(q-2) for TV^q."""
     g = np.einsum("ek,ekd->ed", u[mesh.tets], mesh.grads)
     t = np.linalg.norm(g, axis=1)
-    c = np.ones_like(t)
     nz = t > 0
-    c[nz] = pm_rprime(t[nz], T) / t[nz]
+    if prior == 0:
+        c = np.ones_like(t)
+        c[nz] = pm_rprime(t[nz], T) / t[nz]
+    else:
+        c = np.full_like(t, T ** (q - 2.0))
+        c[nz] = tvq_rprime(t[nz], T, q) / t[nz]
     return c
 
 
-def prior_matrix(mesh: Mesh, kt, mt, T: float, b_over_a: float, delta: float):
+def prior_matrix(mesh: Mesh, kt, mt, T: float, b_over_a: float, delta: float, prior: int = 0, q: float = 1.0):
     """M_delta = blkdiag(M(kt), (b/a) M(mt)) + delta I (Eqs. (16), (19)), with
     M(u) the FE matrix of -div(c_u grad) with natural boundary condition."""
-    Mk = assemble_stiffness(mesh, lagged_weights(mesh, kt, T))
-    Mm = assemble_stiffness(mesh, lagged_weights(mesh, mt, T))
+    Mk = assemble_stiffness(mesh, lagged_weights(mesh, kt, T, prior, q))
+    Mm = assemble_stiffness(mesh, lagged_weights(mesh, mt, T, prior, q))
     M = sp.block_diag([Mk, b_over_a * Mm], format="csr")
     return (M + delta * sp.identity(2 * mesh.N, format="csr")).tocsr()
 
 
 def prior_solve(mesh: Mesh, kt, mt, rhs, T: float, b_over_a: float = 1.0,
-                delta: float = 1e-6):
+                delta: float = 1e-6, prior: int = 0, q: float = 1.0):
     """x = M_delta^{-1} rhs (the one prior solve of each LSQR round, Sec. 4)."""
-    return Factor(prior_matrix(mesh, kt, mt, T, b_over_a, delta)).solve(rhs)
+    return Factor(prior_matrix(mesh, kt, mt, T, b_over_a, delta, prior, q)).solve(rhs)
 
 
 # --------------------------------------------------------------------------
@@ -470,6 +489,8 @@ class QpatParams:
     fixed_counts: bool = False
     fit_grid: int = 9
     fit_gn_steps: int = 10
+    prior: int = 0            # 0: Perona-Malik (Eq. (10)); 1: smoothed TV^q (tvq_r)
+    prior_q: float = 1.0
 
 
 def nonlinear_residual(chi, h, w) -> float:
@@ -606,7 +627,7 @@ def reconstruct(mesh: Mesh, flux, chi, sigma, params: QpatParams,
     phi, h = forward(mesh, kap, mu, flux, fac)
     zeros = np.zeros(N)
     yhat = (w * (chi - h)).ravel()          # J kt_init = 0 as kt_init = 0
-    Mk = Factor(assemble_stiffness(mesh, lagged_weights(mesh, kt, P.T))
+    Mk = Factor(assemble_stiffness(mesh, lagged_weights(mesh, kt, P.T, P.prior, P.prior_q))
                 + P.delta * sp.identity(N, format="csr"))
     A0 = lambda v: jvp(mesh, kap, mu, phi, np.concatenate([v, zeros]), w, fac).ravel()
     AT0 = lambda u: vjp(mesh, kap, mu, phi, u.reshape(K, N), w, fac)[:N]
@@ -629,7 +650,7 @@ def reconstruct(mesh: Mesh, flux, chi, sigma, params: QpatParams,
         Jb = jvp(mesh, kap, mu, phi, beta, None, fac)
         ytil = (w * (chi - h + Jb)).ravel()
         # step 2: M_delta from the current iterate
-        Pfac = Factor(prior_matrix(mesh, beta[:N], beta[N:], P.T, P.b_over_a, P.delta))
+        Pfac = Factor(prior_matrix(mesh, beta[:N], beta[N:], P.T, P.b_over_a, P.delta, P.prior, P.prior_q))
         # step 3: priorconditioned LSQR from zero
         A = lambda v: jvp(mesh, kap, mu, phi, v, w, fac).ravel()
         AT = lambda u: vjp(mesh, kap, mu, phi, u.reshape(K, N), w, fac)

@@ -174,7 +174,8 @@ int prepare_K(qpat_mesh_s* M, const double* kap_l, const double* mu_l, OpState& 
     return QPAT_OK;
 }
 
-int prepare_prior(qpat_mesh_s* M, const double* kt_l, const double* mt_l, double T, double b_over_a, double delta,
+int prepare_prior(qpat_mesh_s* M, const double* kt_l, const double* mt_l, double T, int kind, double q,
+                  double b_over_a, double delta,
                   OpState& st, cudaStream_t s) {
     const int64_t N = M->h.N;
     cudaError_t e = cudaSuccess;
@@ -182,6 +183,8 @@ int prepare_prior(qpat_mesh_s* M, const double* kt_l, const double* mt_l, double
     st.c1_64 = kt_l;
     st.c2_64 = mt_l;
     st.inv_T2 = 1.0 / (T * T);
+    st.prior_kind = kind;
+    st.prior_q = q;
     st.scale1 = b_over_a;
     st.delta = delta;
     st.c1_32 = M->ws.get<float>("opP.c1_32", N, s, &e);
@@ -194,8 +197,8 @@ int prepare_prior(qpat_mesh_s* M, const double* kt_l, const double* mt_l, double
     if (e != cudaSuccess) return cuda_fail(e, "workspace");
     if ((e = launch_cast_d2f(N, kt_l, st.c1_32, s)) != cudaSuccess) return cuda_fail(e, "cast");
     if ((e = launch_cast_d2f(N, mt_l, st.c2_32, s)) != cudaSuccess) return cuda_fail(e, "cast");
-    if ((e = launch_assemble_prior(M->d, kt_l, mt_l, st.inv_T2, b_over_a, delta, st.v64[0], st.v64[1], st.inv64,
-                                   st.inv32, s)) != cudaSuccess)
+    if ((e = launch_assemble_prior(M->d, kt_l, mt_l, st.inv_T2, kind, q, b_over_a, delta, st.v64[0], st.v64[1],
+                                   st.inv64, st.inv32, s)) != cudaSuccess)
         return cuda_fail(e, "assemble_prior");
     return QPAT_OK;
 }
@@ -431,6 +434,8 @@ void qpat_default_params(qpat_params* p) {
     p->fit_grid = 9;
     p->fit_gn_steps = 10;
     p->patch_nodes = 0;
+    p->prior = 0;
+    p->prior_q = 1.0;
 }
 
 static int mesh_create(const double* xyz, int64_t N, const int32_t* tets, int64_t E, int patch_nodes,

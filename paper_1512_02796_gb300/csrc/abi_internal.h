@@ -39,6 +39,8 @@ struct OpState {
     double* inv64 = nullptr;        // inverse diagonal (N, or N x 2 for the prior)
     float* inv32 = nullptr;
     double inv_T2 = 0, scale1 = 1, delta = 0;
+    int prior_kind = 0;             // r(t) of the prior (prior_weight in fem.cuh)
+    double prior_q = 1;
     int nv = 1;                     // assembled value sets (1: K, 2: prior blocks)
     double* v64[2] = {nullptr, nullptr};  // assembled FP64 values (sliced ELLPACK)
     float* v32[2] = {nullptr, nullptr};   // FP32 copy (K only)
@@ -94,7 +96,8 @@ int round_rhs(int K);
 int upload_mesh(qpat_mesh_s* M);
 int prepare_K(qpat_mesh_s* M, const double* kap_l, const double* mu_l, OpState& st, cudaStream_t s,
               const char* tag = "opK");
-int prepare_prior(qpat_mesh_s* M, const double* kt_l, const double* mt_l, double T, double b_over_a, double delta,
+int prepare_prior(qpat_mesh_s* M, const double* kt_l, const double* mt_l, double T, int kind, double q,
+                  double b_over_a, double delta,
                   OpState& st, cudaStream_t s);
 // X0 (optional): initial guess; the solve then stops at the same absolute
 // residual |B - A X| <= rtol |B| as from zero.

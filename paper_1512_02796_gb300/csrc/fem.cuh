@@ -39,7 +39,22 @@ struct OpParams {
     int robin;       // OP_K: include the Robin boundary term
     const T* v0;     // OP_CSR*: assembled values (block 0 / all RHS)
     const T* v1;     // OP_CSR2: assembled values of block 1
+    int prior_kind = 0;   // OP_PRIOR: r(t) of the prior (see prior_weight)
+    T prior_q = T(1);     // OP_PRIOR: exponent q of the smoothed TV^q prior
 };
+
+// Lagged-diffusivity weight r'(t)/t of the prior R(u) = integral r(|grad u|)
+// (Eq. (9)) at t^2 = g2; the lagged step (Eq. (14)) uses it per tet.
+//   kind 0, Perona-Malik (Eq. (10)): r(t) = T^2/2 log(1 + t^2/T^2)  ->  1 / (1 + t^2/T^2)
+//   kind 1, smoothed TV^q (named after Eq. (10)): r(t) = (t^2 + T^2)^(q/2) / q
+//                                              ->  (t^2 + T^2)^(q/2 - 1)
+// (q = 1 is smoothed total variation; q = 2 gives weight 1, the plain Laplacian.)
+template <typename T>
+__host__ __device__ inline T prior_weight(int kind, T g2, T inv_T2, T q) {
+    if (kind == 0) return T(1) / (T(1) + g2 * inv_T2);
+    const T e = q * T(0.5) - T(1);
+    return e == T(0) ? T(1) : pow(g2 + T(1) / inv_T2, e);
+}
 
 // Slot of local column c in library row g of the sliced-ELLPACK pattern.
 __device__ __forceinline__ int64_t sell_slot(const MeshDev& m, int g, int c) {
@@ -247,9 +262,9 @@ __device__ __forceinline__ void patch_elements(const MeshDev& m, int p, int nown
                     x[a] = s.xin[v[a] * 2 + r];
                 }
                 grad_vec(c, u, Gu);
-                // |grad u|^2 = |G_u|^2 / det^2 ; c_T = 1 / (1 + |grad u|^2 / T^2)
+                // |grad u|^2 = |G_u|^2 / det^2 ; c_T = r'(|grad u|) / |grad u|
                 const T g2 = (Gu[0] * Gu[0] + Gu[1] * Gu[1] + Gu[2] * Gu[2]) / (ad * ad);
-                const T cT = T(1) / (T(1) + g2 * op.inv_T2);
+                const T cT = prior_weight<T>(op.prior_kind, g2, op.inv_T2, op.prior_q);
                 const T sk = (r == 0 ? T(1) : op.scale1) * cT * inv6ad;
                 grad_vec(c, x, G);
                 stiff_rows(c, G, sk, y);

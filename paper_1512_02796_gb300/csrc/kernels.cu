@@ -113,15 +113,15 @@ __global__ void __launch_bounds__(kThreads) k_diag_K(MeshDev m, const double* __
 // diag M_delta: block r: scale_r c_T |c_i|^2 / (6 |det|) + delta
 __global__ void __launch_bounds__(kThreads) k_diag_prior(MeshDev m, const double* __restrict__ u1,
                                                          const double* __restrict__ u2, double inv_T2,
-                                                         double scale1, double delta, double* inv64,
-                                                         float* inv32) {
+                                                         int kind, double q, double scale1, double delta,
+                                                         double* inv64, float* inv32) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     PatchSmem<double, 2> s;
     s.carve(reinterpret_cast<double*>(smem_raw), m.max_touched, m.max_own);
     const int p = blockIdx.x;
     const int nb = m.node_ptr[p], nt = m.node_ptr[p + 1] - nb;
     const int ob = m.own_begin[p], nown = m.own_begin[p + 1] - ob;
-    OpParams<double> op{u1, u2, inv_T2, scale1, delta, 0};
+    OpParams<double> op{u1, u2, inv_T2, scale1, delta, 0, nullptr, nullptr, kind, q};
     stage_static<double, 2>(m, nb, nt, s, op);
     for (int i = threadIdx.x; i < 2 * nown; i += blockDim.x) s.yout[i] = 0.0;
     __syncthreads();
@@ -137,7 +137,7 @@ __global__ void __launch_bounds__(kThreads) k_diag_prior(MeshDev m, const double
             for (int a = 0; a < 4; ++a) u[a] = uc[v[a]];
             grad_vec(c, u, Gu);
             const double g2 = (Gu[0] * Gu[0] + Gu[1] * Gu[1] + Gu[2] * Gu[2]) / (ad * ad);
-            const double cT = 1.0 / (1.0 + g2 * inv_T2);
+            const double cT = prior_weight<double>(kind, g2, inv_T2, q);
             const double sk = (r == 0 ? 1.0 : scale1) * cT / (6.0 * ad);
             for (int a = 0; a < 4; ++a)
                 if (v[a] < nown)
@@ -205,10 +205,11 @@ __global__ void __launch_bounds__(kThreads) k_assemble_K(MeshDev m, const double
     }
 }
 
-// Prior blocks: A^r_ab = scale_r c_T(u_r) c_a.c_b / (6 |det|), c_T = 1/(1 + |grad u_r|^2/T^2)
+// Prior blocks: A^r_ab = scale_r c_T(u_r) c_a.c_b / (6 |det|), c_T = r'(t)/t at t = |grad u_r| (prior_weight)
 __global__ void __launch_bounds__(kThreads) k_assemble_prior(MeshDev m, const double* __restrict__ u1,
                                                              const double* __restrict__ u2, double inv_T2,
-                                                             double scale1, double* val0, double* val1) {
+                                                             int kind, double q, double scale1, double* val0,
+                                                             double* val1) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     PatchSmem<double, 1> s;
     s.carve(reinterpret_cast<double*>(smem_raw), m.max_touched, m.max_own);
@@ -231,7 +232,7 @@ __global__ void __launch_bounds__(kThreads) k_assemble_prior(MeshDev m, const do
             for (int a = 0; a < 4; ++a) u[a] = uc[v[a]];
             grad_vec(c, u, Gu);
             const double g2 = (Gu[0] * Gu[0] + Gu[1] * Gu[1] + Gu[2] * Gu[2]) / (ad * ad);
-            coef[r] = (r == 0 ? 1.0 : scale1) / (1.0 + g2 * inv_T2) / (6.0 * ad);
+            coef[r] = (r == 0 ? 1.0 : scale1) * prior_weight<double>(kind, g2, inv_T2, q) / (6.0 * ad);
         }
         for (int a = 0; a < 4; ++a) {
             if (v[a] >= nown) continue;
@@ -493,9 +494,9 @@ cudaError_t launch_apply_K(const MeshDev& m, int R, const T* c1, const T* c2, in
 }
 
 template <typename T>
-cudaError_t launch_apply_prior(const MeshDev& m, const T* u1, const T* u2, T inv_T2, T scale1, T delta, const T* x,
-                               T* y, cudaStream_t s) {
-    OpParams<T> op{u1, u2, inv_T2, scale1, delta, 0};
+cudaError_t launch_apply_prior(const MeshDev& m, const T* u1, const T* u2, T inv_T2, int kind, T q, T scale1,
+                               T delta, const T* x, T* y, cudaStream_t s) {
+    OpParams<T> op{u1, u2, inv_T2, scale1, delta, 0, nullptr, nullptr, kind, q};
     return apply_t<T, 2, OP_PRIOR>(m, op, T(1), x, y, 2, 0, s);
 }
 
@@ -509,13 +510,14 @@ cudaError_t launch_invdiag_K(const MeshDev& m, const double* kappa, const double
     return cudaGetLastError();
 }
 
-cudaError_t launch_invdiag_prior(const MeshDev& m, const double* u1, const double* u2, double inv_T2, double scale1,
-                                 double delta, double* inv64, float* inv32, cudaStream_t s) {
+cudaError_t launch_invdiag_prior(const MeshDev& m, const double* u1, const double* u2, double inv_T2, int kind,
+                                 double q, double scale1, double delta, double* inv64, float* inv32,
+                                 cudaStream_t s) {
     const size_t smem = PatchSmem<double, 2>::bytes(m.max_touched, m.max_own);
     cudaError_t e = cudaFuncSetAttribute(k_diag_prior, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
     if (e != cudaSuccess) return e;
     qpat::note_launch(1);
-    k_diag_prior<<<m.P, kThreads, smem, s>>>(m, u1, u2, inv_T2, scale1, delta, inv64, inv32);
+    k_diag_prior<<<m.P, kThreads, smem, s>>>(m, u1, u2, inv_T2, kind, q, scale1, delta, inv64, inv32);
     return cudaGetLastError();
 }
 
@@ -533,9 +535,9 @@ cudaError_t launch_assemble_K(const MeshDev& m, const double* kappa, const doubl
     return cudaGetLastError();
 }
 
-cudaError_t launch_assemble_prior(const MeshDev& m, const double* u1, const double* u2, double inv_T2, double scale1,
-                                  double delta, double* val0, double* val1, double* inv64, float* inv32,
-                                  cudaStream_t s) {
+cudaError_t launch_assemble_prior(const MeshDev& m, const double* u1, const double* u2, double inv_T2, int kind,
+                                  double q, double scale1, double delta, double* val0, double* val1, double* inv64,
+                                  float* inv32, cudaStream_t s) {
     cudaError_t e = cudaMemsetAsync(val0, 0, sizeof(double) * m.sell_entries, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(val1, 0, sizeof(double) * m.sell_entries, s);
     if (e != cudaSuccess) return e;
@@ -543,7 +545,7 @@ cudaError_t launch_assemble_prior(const MeshDev& m, const double* u1, const doub
     e = cudaFuncSetAttribute(k_assemble_prior, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
     if (e != cudaSuccess) return e;
     qpat::note_launch(1);
-    k_assemble_prior<<<m.P, kThreads, smem, s>>>(m, u1, u2, inv_T2, scale1, val0, val1);
+    k_assemble_prior<<<m.P, kThreads, smem, s>>>(m, u1, u2, inv_T2, kind, q, scale1, val0, val1);
     qpat::note_launch(1);
     k_diag_csr<<<grid_for(m.N), 256, 0, s>>>(m, 2, delta, val0, val1, inv64, inv32);
     return cudaGetLastError();
@@ -662,10 +664,10 @@ template cudaError_t launch_apply_K<double>(const MeshDev&, int, const double*, 
                                             const double*, double*, cudaStream_t);
 template cudaError_t launch_apply_K<float>(const MeshDev&, int, const float*, const float*, int, float, const float*,
                                            float*, cudaStream_t);
-template cudaError_t launch_apply_prior<double>(const MeshDev&, const double*, const double*, double, double, double,
-                                                const double*, double*, cudaStream_t);
-template cudaError_t launch_apply_prior<float>(const MeshDev&, const float*, const float*, float, float, float,
-                                               const float*, float*, cudaStream_t);
+template cudaError_t launch_apply_prior<double>(const MeshDev&, const double*, const double*, double, int, double,
+                                                double, double, const double*, double*, cudaStream_t);
+template cudaError_t launch_apply_prior<float>(const MeshDev&, const float*, const float*, float, int, float, float,
+                                               float, const float*, float*, cudaStream_t);
 template cudaError_t launch_vjp_accum<double>(const MeshDev&, int, const double*, const double*, double*,
                                               cudaStream_t);
 template cudaError_t launch_vjp_accum<float>(const MeshDev&, int, const float*, const float*, float*, cudaStream_t);

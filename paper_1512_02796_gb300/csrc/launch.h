@@ -15,23 +15,25 @@ namespace qpat {
 template <typename T>
 cudaError_t launch_apply_K(const MeshDev& m, int R, const T* c1, const T* c2, int robin, T sign,
                            const T* x, T* y, cudaStream_t s);
-// y = (blkdiag(M(u1), scale1 M(u2)) + delta I) x, x and y N x 2 node-major.
+// y = (blkdiag(M(u1), scale1 M(u2)) + delta I) x, x and y N x 2 node-major;
+// kind, q select the prior's r(t) (prior_weight in fem.cuh).
 template <typename T>
-cudaError_t launch_apply_prior(const MeshDev& m, const T* u1, const T* u2, T inv_T2, T scale1, T delta,
-                               const T* x, T* y, cudaStream_t s);
+cudaError_t launch_apply_prior(const MeshDev& m, const T* u1, const T* u2, T inv_T2, int kind, T q, T scale1,
+                               T delta, const T* x, T* y, cudaStream_t s);
 // inverse diagonal of K(kappa, mu) (N) and of M_delta (N x 2), computed in FP64.
 cudaError_t launch_invdiag_K(const MeshDev& m, const double* kappa, const double* mu, double* inv64,
                              float* inv32, cudaStream_t s);
-cudaError_t launch_invdiag_prior(const MeshDev& m, const double* u1, const double* u2, double inv_T2,
-                                 double scale1, double delta, double* inv64, float* inv32, cudaStream_t s);
+cudaError_t launch_invdiag_prior(const MeshDev& m, const double* u1, const double* u2, double inv_T2, int kind,
+                                 double q, double scale1, double delta, double* inv64, float* inv32,
+                                 cudaStream_t s);
 // Assembly of K (FP64 values in the sliced-ELLPACK pattern; val must hold
 // m.sell_entries) and of the two prior blocks with delta on the diagonal;
 // both also write the inverse diagonal (FP64 and, if not null, FP32).
 cudaError_t launch_assemble_K(const MeshDev& m, const double* kappa, const double* mu, double* val, double* inv64,
                               float* inv32, cudaStream_t s);
-cudaError_t launch_assemble_prior(const MeshDev& m, const double* u1, const double* u2, double inv_T2, double scale1,
-                                  double delta, double* val0, double* val1, double* inv64, float* inv32,
-                                  cudaStream_t s);
+cudaError_t launch_assemble_prior(const MeshDev& m, const double* u1, const double* u2, double inv_T2, int kind,
+                                  double q, double scale1, double delta, double* val0, double* val1, double* inv64,
+                                  float* inv32, cudaStream_t s);
 cudaError_t launch_cast_vals(int64_t n, const double* in, float* out, cudaStream_t s);
 // y = A x with an assembled operator (NV = 1: one value set for R RHS; NV = 2: the prior, R = 2)
 template <typename T>

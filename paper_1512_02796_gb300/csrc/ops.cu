@@ -153,6 +153,9 @@ static int check_params(const qpat_params* prm, const char* who) {
         return fail(QPAT_EINVAL, std::string(who) + ": precision must be 0 or 1");
     if (prm->pcg_variant < 0 || prm->pcg_variant > 3)
         return fail(QPAT_EINVAL, std::string(who) + ": pcg_variant must be 0, 1, 2 or 3");
+    if (prm->prior != 0 && prm->prior != 1) return fail(QPAT_EINVAL, std::string(who) + ": prior must be 0 or 1");
+    if (prm->prior == 1 && !(prm->prior_q > 0.0 && prm->prior_q <= 2.0))
+        return fail(QPAT_EINVAL, std::string(who) + ": prior_q must lie in (0, 2]");
     return QPAT_OK;
 }
 
@@ -506,7 +509,7 @@ int qpat_prior_solve_dev(qpat_mesh_t M, const qpat_params* prm, const double* kt
         (e = launch_to_lib<double, double>(M->d, 2, 2, rhs, bl, s)) != cudaSuccess)
         return cuda_fail(e, "to_lib");
     OpState st;
-    if ((rc = prepare_prior(M, ktl, mtl, p->T, p->b_over_a, p->delta, st, s))) return rc;
+    if ((rc = prepare_prior(M, ktl, mtl, p->T, p->prior, p->prior_q, p->b_over_a, p->delta, st, s))) return rc;
     if ((rc = solve(M, st, solve_opts(prm), 2, bl, xl, s))) return rc;
     if ((e = launch_from_lib<double, double>(M->d, 2, 2, xl, out, s)) != cudaSuccess)
         return cuda_fail(e, "from_lib");

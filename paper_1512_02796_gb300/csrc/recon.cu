@@ -325,6 +325,9 @@ extern "C" int qpat_reconstruct(qpat_mesh_t M, const qpat_params* prm_in, int K,
     qpat_default_params(&prm);
     if (prm_in) prm = *prm_in;
     if (prm.precision != 0 && prm.precision != 1) return fail(QPAT_EINVAL, "qpat_reconstruct: bad precision");
+    if (prm.prior != 0 && prm.prior != 1) return fail(QPAT_EINVAL, "qpat_reconstruct: prior must be 0 or 1");
+    if (prm.prior == 1 && !(prm.prior_q > 0.0 && prm.prior_q <= 2.0))
+        return fail(QPAT_EINVAL, "qpat_reconstruct: prior_q must lie in (0, 2]");
     if (prm.max_lin < 1 || prm.max_lin > 32 || prm.max_lsqr < 0 || prm.m0 < 1)
         return fail(QPAT_EINVAL, "qpat_reconstruct: max_lin must be in [1, 32], max_lsqr >= 0, m0 >= 1");
     if (!(prm.T > 0) || !(prm.delta > 0) || !(prm.b_over_a > 0))
@@ -466,7 +469,7 @@ extern "C" int qpat_reconstruct(qpat_mesh_t M, const qpat_params* prm_in, int K,
         qpat::note_launch(1);
         k_unpack_beta<<<GS(N)>>>(N, beta, 0, ktmp, mtmp);
         OpState P;
-        rc.ckq(prepare_prior(M, ktmp, mtmp, prm.T, prm.b_over_a, prm.delta, P, s));
+        rc.ckq(prepare_prior(M, ktmp, mtmp, prm.T, prm.prior, prm.prior_q, prm.b_over_a, prm.delta, P, s));
         std::vector<double> hist;
         int it0 = lsqr(rc, LA, P, ytil, 1, prm, xls, hist);
         qpat::note_launch(1);
@@ -504,7 +507,7 @@ extern "C" int qpat_reconstruct(qpat_mesh_t M, const qpat_params* prm_in, int K,
             // step 2: M_delta from the current iterate
             qpat::note_launch(1);
             k_unpack_beta<<<GS(N)>>>(N, beta, 0, ktmp, mtmp);
-            rc.ckq(prepare_prior(M, ktmp, mtmp, prm.T, prm.b_over_a, prm.delta, P, s));
+            rc.ckq(prepare_prior(M, ktmp, mtmp, prm.T, prm.prior, prm.prior_q, prm.b_over_a, prm.delta, P, s));
             // step 3: LSQR from zero
             const int it = lsqr(rc, *cur, P, ytil, 0, prm, betaN, hist);
             report.lsqr_iters[report.linearisations] = it;

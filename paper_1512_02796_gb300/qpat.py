@@ -29,7 +29,8 @@ class qpat_params(ctypes.Structure):
         ("max_lsqr", ctypes.c_int), ("fixed_counts", ctypes.c_int), ("precision", ctypes.c_int),
         ("max_pcg_iter", ctypes.c_int), ("pcg_rtol", ctypes.c_double), ("fit_grid", ctypes.c_int),
         ("fit_gn_steps", ctypes.c_int), ("patch_nodes", ctypes.c_int), ("fp32_operator", ctypes.c_int),
-        ("pcg_variant", ctypes.c_int), ("reserved", ctypes.c_int * 5),
+        ("pcg_variant", ctypes.c_int), ("prior", ctypes.c_int), ("reserved", ctypes.c_int * 4),
+        ("prior_q", ctypes.c_double),
     ]
 
 

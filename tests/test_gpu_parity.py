@@ -160,3 +160,37 @@ def test_launch_counter_counts_the_solve(case):
     n0 = Q.qpat_launch_count()
     Q.qpat_forward(case.lib, case.kappa, case.mu, case.flux)
     assert Q.qpat_launch_count() - n0 >= 2   # at least assembly + one PCG launch
+
+
+@pytest.mark.parametrize("q", [1.0, 0.5, 2.0])
+def test_prior_solve_tvq(case, q):
+    """M_delta of the smoothed TV^q prior (Sec. 3's alternative r(t)) solved on
+    the GPU against the oracle's sparse LU; q = 2 is the plain Laplacian."""
+    rng = np.random.default_rng(11)
+    N = case.N
+    kt = 0.3 * rng.standard_normal(N)
+    mt = np.log(case.mu / case.mu.mean())
+    rhs = rng.standard_normal(2 * N)
+    T, ba, delta = 1e-2, 0.7, 1e-6
+    Md = O.prior_matrix(case.om, kt, mt, T, ba, delta, prior=1, q=q)
+    ref = O.Factor(Md).solve(rhs)
+    out = Q.qpat_prior_solve(case.lib, kt, mt, rhs,
+                             _params(0, T=T, b_over_a=ba, delta=delta, pcg_rtol=1e-13, prior=1, prior_q=q))
+    # TV^q weights reach T^(q-2) (up to 1e3 here), so cond(M_delta) ~ 1e9-1e10
+    # and the true residual of a solve stopped on its recursive residual sits
+    # ~eps cond above it; the bar is the normwise backward error instead
+    Anorm = abs(Md).sum(axis=0).max()
+    eta = np.linalg.norm(Md @ out - rhs, 1) / (Anorm * np.linalg.norm(out, 1) + np.linalg.norm(rhs, 1))
+    assert eta < 1e-13
+    if N <= 800:
+        ev = np.linalg.eigvalsh(Md.toarray())
+        tol = 10 * (ev[-1] / ev[0]) * 1e-13
+    else:
+        tol = 1e-4
+    assert rel(out, ref) < max(tol, 1e-10)
+
+
+def test_prior_parameter_checks(case):
+    with pytest.raises(Q.QpatError):
+        Q.qpat_prior_solve(case.lib, np.zeros(case.N), np.zeros(case.N), np.ones(2 * case.N),
+                           _params(0, prior=1, prior_q=2.5))

@@ -111,3 +111,29 @@ def test_background_fit_matches_oracle(c0):
     # so the minimiser is fixed only to ~sqrt(eps) relative
     assert abs(rep.kappa0 / k_o - 1) < 1e-6
     assert abs(rep.mu0 / m_o - 1) < 1e-6
+
+
+@pytest.mark.parametrize("q,nlin,nlsqr", [(1.0, 2, 2), (0.6, 2, 2), (1.0, 3, 3)])
+def test_reconstruct_with_tvq_prior_matches_oracle(c0, q, nlin, nlsqr):
+    """Algorithm 1 with the smoothed TV^q prior (the alternative r(t) of
+    Sec. 3) instead of Perona-Malik, FP64, within max(1e-10, 10 x the
+    oracle's own spread under 1e-13 solve perturbations).  Short sweeps pin
+    the path tightly; at 3 x 3 the oracle's own spread is already ~3e-2 for
+    kappa (TV^q weights up to T^(q-2) make M_delta far worse conditioned)."""
+    par = O.QpatParams(T=1e-2, max_lin=nlin, max_lsqr=nlsqr, fixed_counts=True, prior=1, prior_q=q)
+    k0m0 = (0.32, 0.011)
+    kap_o, mu_o, _ = _oracle(c0, par, k0m0)
+    kap_p, mu_p, _ = _oracle(c0, par, k0m0, perturb=1e-13, seed=2)
+    floor = max(rel(kap_p, kap_o), rel(mu_p, mu_o))
+    prm = Q.qpat_default_params(T=1e-2, max_lin=nlin, max_lsqr=nlsqr, fixed_counts=1, precision=0, prior=1,
+                                prior_q=q)
+    kap_g, mu_g, _ = Q.qpat_reconstruct(c0["lib"], c0["flux"], c0["chi"], c0["sig"], prm, k0m0)
+    tol = max(1e-10, 10 * floor)
+    print(f"TV^q q={q} {nlin}x{nlsqr}: floor {floor:.2e}  kappa {rel(kap_g, kap_o):.2e}  mu {rel(mu_g, mu_o):.2e}")
+    assert rel(kap_g, kap_o) < tol
+    assert rel(mu_g, mu_o) < tol
+    # the prior changed the result (it is not silently Perona-Malik)
+    kap_pm, _, _ = Q.qpat_reconstruct(c0["lib"], c0["flux"], c0["chi"], c0["sig"],
+                                      Q.qpat_default_params(T=1e-2, max_lin=nlin, max_lsqr=nlsqr,
+                                                            fixed_counts=1, precision=0), k0m0)
+    assert rel(kap_pm, kap_g) > 1e-6

@@ -80,3 +80,15 @@ def test_wrong_gradient_index_is_caught(monkeypatch):
         return vol, g[:, [0, 2, 1, 3], :]        # swapped local indices
     monkeypatch.setattr(Q, "tet_geometry", bad)
     assert _fails(P.test_kuhn_laplacian_is_seven_point_stencil)
+
+
+def test_tvq_exponent_off_by_one_is_caught(monkeypatch):
+    # r'(t)/t computed as (t^2 + T^2)^(q/2) instead of (t^2 + T^2)^(q/2 - 1)
+    monkeypatch.setattr(Q, "tvq_rprime", lambda t, T, q: t * (t * t + T * T) ** (q / 2.0))
+    assert _fails(P.test_tvq_weights_closed_forms_and_derivative)
+
+
+def test_tvq_missing_chain_rule_factor_is_caught(monkeypatch):
+    # d/dt (t^2 + T^2)^(q/2) / q taken without the inner derivative 2t / 2 = t
+    monkeypatch.setattr(Q, "tvq_rprime", lambda t, T, q: (t * t + T * T) ** (q / 2.0 - 1.0))
+    assert _fails(P.test_tvq_weights_closed_forms_and_derivative)

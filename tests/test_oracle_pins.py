@@ -305,6 +305,42 @@ def test_prior_operator_psd_kernel_and_delta():
         O.assemble_stiffness(m, np.ones(m.E)).toarray(), atol=1e-14)
 
 
+def test_tvq_weights_closed_forms_and_derivative():
+    """Smoothed TV^q (the alternative priors named in Sec. 3): q = 1 gives the
+    lagged-diffusivity weight of smoothed total variation, 1/sqrt(t^2 + T^2)
+    (the fixed-point weight of Vogel and Oman); q = 2 gives weight 1 for any u
+    (the plain P1 Laplacian stiffness, a textbook case); for every q the weight
+    times t is the derivative of r (central differences), and the t = 0
+    value is T^(q - 2)."""
+    m = small_mesh(4, 3.0)
+    T = 5e-3
+    rng = np.random.default_rng(4)
+    u = 0.2 * rng.standard_normal(m.N)
+    g = np.einsum("ek,ekd->ed", u[m.tets], m.grads)
+    t = np.linalg.norm(g, axis=1)
+    np.testing.assert_allclose(O.lagged_weights(m, u, T, prior=1, q=1.0), 1.0 / np.sqrt(t ** 2 + T ** 2),
+                               rtol=1e-13)
+    np.testing.assert_allclose(O.lagged_weights(m, u, T, prior=1, q=2.0), 1.0, rtol=1e-15)
+    np.testing.assert_allclose(
+        O.prior_matrix(m, u, -u, T, 1.0, 0.0, prior=1, q=2.0).toarray()[:m.N, :m.N],
+        O.assemble_stiffness(m, np.ones(m.E)).toarray(), atol=1e-14)
+    for q in (0.5, 1.0, 1.5):
+        assert np.all(O.lagged_weights(m, np.zeros(m.N), T, prior=1, q=q) == T ** (q - 2.0))
+        for gnorm in (1e-4, 5e-3, 0.2):
+            gv = gnorm * np.array([2.0, -1.0, 2.0]) / 3.0
+            c = O.lagged_weights(m, m.xyz @ gv, T, prior=1, q=q)
+            e = 1e-4 * gnorm          # truncation O(e^2) vs roundoff eps r / e
+            rp = (O.tvq_r(gnorm + e, T, q) - O.tvq_r(gnorm - e, T, q)) / (2 * e)
+            np.testing.assert_allclose(c * gnorm, rp, rtol=1e-6)
+    # the lagged operator keeps M 1 = 0, PSD with a 1-D kernel, and M_delta >= delta
+    Mu = O.assemble_stiffness(m, O.lagged_weights(m, u, T, prior=1, q=0.7)).toarray()
+    assert np.abs(Mu @ np.ones(m.N)).max() < 1e-9 * np.abs(Mu).max()
+    ev = np.linalg.eigvalsh(Mu)
+    assert ev.min() >= -1e-13 * ev.max() and np.sum(ev < 1e-12 * ev.max()) == 1
+    evd = np.linalg.eigvalsh(O.prior_matrix(m, u, -u, T, 0.7, 1e-6, prior=1, q=0.7).toarray())
+    assert evd.min() >= 1e-6 * (1 - 1e-6)
+
+
 # ---------------------------------------------------------------- LSQR
 
 def _dense_problem(mrows=40, ncols=12, seed=0):
