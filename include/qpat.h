@@ -177,6 +177,19 @@ int qpat_mesh_permutation(qpat_mesh_t mesh, int32_t* perm);
 int qpat_flux_patch(qpat_mesh_t mesh, const double c[3], const double n[3],
                     double half_w, double amp, double* flux_face);
 
+/* Face-constant flux through the curved side of a cylinder (Sec. 5, Test 1),
+ * canonical face order: Phi = amp cos(pi/2 (theta - theta0) / half_w) for
+ * |theta - theta0| <= half_w, else 0 (half_w = pi/8 gives the paper's
+ * cos(4 (theta - theta0))), homogeneous along the axis.  A face is on the
+ * side iff its three vertices lie at distance `radius` (within 1e-9 of the
+ * mesh extent) from the axis line through c along `axis`; it takes Phi at
+ * the polar angle of its centroid, measured about the axis from `ref`
+ * (projected off the axis).  flux_face: F doubles, caller-owned.
+ * QPAT_EINVAL for NULL pointers, a zero axis, ref parallel to the axis, or
+ * radius, half_w <= 0. */
+int qpat_flux_side(qpat_mesh_t mesh, const double c[3], const double axis[3], const double ref[3],
+                   double radius, double theta0, double half_w, double amp, double* flux_face);
+
 /* ------------------------------------------------------- operator apply */
 
 /* y = K(kappa, mu) x for R right-hand sides: the FE matrix of the weak form

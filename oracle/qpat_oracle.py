@@ -37,7 +37,7 @@ import scipy.sparse.linalg as spla
 __all__ = [
     "Mesh", "QpatParams", "tet_geometry", "boundary_faces", "face_areas",
     "int_bary_tet", "int_bary_tri", "assemble_stiffness", "assemble_weighted_mass",
-    "assemble_robin", "load_vector", "load_vector_nodal", "flux_patch", "system_matrix", "Factor",
+    "assemble_robin", "load_vector", "load_vector_nodal", "flux_patch", "flux_side", "system_matrix", "Factor",
     "forward", "G1_matrix", "G2_matrix", "jvp", "vjp", "lagged_weights", "tvq_r", "tvq_rprime",
     "prior_matrix", "prior_solve", "lsqr_prior", "fit_background", "init_mu",
     "reconstruct", "measure", "nonlinear_residual", "simulate_data",
@@ -243,6 +243,34 @@ def flux_patch(mesh: Mesh, center, normal, half_w: float, amp: float = 1.0,
     tang = cen - np.outer(cen @ nv, nv)
     inside = np.max(np.abs(tang), axis=1) <= half_w + tol * scale
     return np.where(on_plane & inside, amp, 0.0)
+
+
+def flux_side(mesh: Mesh, center, axis, ref, radius: float, theta0: float,
+              half_w: float = np.pi / 8, amp: float = 1.0, tol: float = 1e-9) -> np.ndarray:
+    """Face-constant flux through the curved side of a cylinder (Sec. 5,
+    Test 1): Phi(theta) = amp cos(pi/2 (theta - theta0) / half_w) for
+    |theta - theta0| <= half_w (the paper's cos(4 (theta - theta0)) on
+    [theta0 - pi/8, theta0 + pi/8]), homogeneous along the axis.  Reading: a
+    boundary face belongs to the side iff its three vertices lie at distance
+    `radius` from the axis (line through `center` along `axis`); it takes
+    the value of Phi at the polar angle of its centroid, measured about the
+    axis from the direction `ref` (projected off the axis)."""
+    c = np.asarray(center, dtype=np.float64)
+    a = np.asarray(axis, dtype=np.float64)
+    a = a / np.linalg.norm(a)
+    e1 = np.asarray(ref, dtype=np.float64)
+    e1 = e1 - (e1 @ a) * a
+    e1 = e1 / np.linalg.norm(e1)
+    e2 = np.cross(a, e1)
+    scale = np.max(np.ptp(mesh.xyz, axis=0))
+    p = mesh.xyz[mesh.faces] - c                     # F x 3 x 3
+    radial = p - (p @ a)[..., None] * a
+    on_side = np.all(np.abs(np.linalg.norm(radial, axis=2) - radius) <= tol * scale, axis=1)
+    cen = p.mean(axis=1)
+    theta = np.arctan2(cen @ e2, cen @ e1)
+    d = np.angle(np.exp(1j * (theta - theta0)))      # wrapped to (-pi, pi]
+    lit = on_side & (np.abs(d) <= half_w)
+    return np.where(lit, amp * np.cos(0.5 * np.pi * d / half_w), 0.0)
 
 
 def system_matrix(mesh: Mesh, kappa: np.ndarray, mu: np.ndarray) -> sp.csr_matrix:

@@ -630,6 +630,19 @@ int qpat_flux_patch(qpat_mesh_t M, const double c[3], const double n[3], double 
     return QPAT_OK;
 }
 
+int qpat_flux_side(qpat_mesh_t M, const double c[3], const double axis[3], const double ref[3], double radius,
+                   double theta0, double half_w, double amp, double* flux_face) {
+    if (!M || !c || !axis || !ref || !flux_face) return fail(QPAT_EINVAL, "qpat_flux_side: NULL argument");
+    const double an = std::sqrt(axis[0] * axis[0] + axis[1] * axis[1] + axis[2] * axis[2]);
+    if (!(an > 0) || !(radius > 0) || !(half_w > 0)) return fail(QPAT_EINVAL, "qpat_flux_side: bad axis, radius or width");
+    const double ra = (ref[0] * axis[0] + ref[1] * axis[1] + ref[2] * axis[2]) / an;
+    const double rn2 = ref[0] * ref[0] + ref[1] * ref[1] + ref[2] * ref[2] - ra * ra;
+    if (!(rn2 > 1e-24 * (ref[0] * ref[0] + ref[1] * ref[1] + ref[2] * ref[2])))
+        return fail(QPAT_EINVAL, "qpat_flux_side: ref is parallel to the axis");
+    flux_side_host(M->h, c, axis, ref, radius, theta0, half_w, amp, flux_face);
+    return QPAT_OK;
+}
+
 int qpat_apply_K_dev(qpat_mesh_t M, int precision, const double* kappa, const double* mu, int R, const double* x,
                      double* y, void* stream) {
     if (!M || !kappa || !mu || !x || !y) return fail(QPAT_EINVAL, "qpat_apply_K_dev: NULL argument");

@@ -309,4 +309,40 @@ void flux_patch_host(const HostMesh& m, const double c[3], const double n[3],
     }
 }
 
+void flux_side_host(const HostMesh& m, const double c[3], const double axis[3], const double ref[3],
+                    double radius, double theta0, double half_w, double amp, double* flux_face) {
+    const double tol = 1e-9 * m.extent;
+    const double pi = 3.14159265358979323846;
+    auto dot = [](const double* x, const double* y) { return x[0] * y[0] + x[1] * y[1] + x[2] * y[2]; };
+    // orthonormal frame: u along the axis, e1 = ref without its axial part, e2 = u x e1
+    const double an = std::sqrt(dot(axis, axis));
+    const double u[3] = {axis[0] / an, axis[1] / an, axis[2] / an};
+    const double ru = dot(ref, u);
+    double e1[3] = {ref[0] - ru * u[0], ref[1] - ru * u[1], ref[2] - ru * u[2]};
+    const double e1n = std::sqrt(dot(e1, e1));
+    for (double& v : e1) v /= e1n;
+    const double e2[3] = {u[1] * e1[2] - u[2] * e1[1], u[2] * e1[0] - u[0] * e1[2], u[0] * e1[1] - u[1] * e1[0]};
+    for (int64_t f = 0; f < m.F; ++f) {
+        bool side = true;
+        double cen[3] = {0, 0, 0};
+        for (int a = 0; a < 3; ++a) {
+            const double* p = &m.xyz[3 * m.faces_lib[3 * f + a]];
+            const double d[3] = {p[0] - c[0], p[1] - c[1], p[2] - c[2]};
+            const double t = dot(d, u);
+            const double rr[3] = {d[0] - t * u[0], d[1] - t * u[1], d[2] - t * u[2]};
+            if (std::fabs(std::sqrt(dot(rr, rr)) - radius) > tol) side = false;
+            for (int k = 0; k < 3; ++k) cen[k] += d[k] / 3.0;
+        }
+        double val = 0.0;
+        if (side) {
+            // polar angle of the centroid, its offset from theta0 wrapped to (-pi, pi]
+            double dth = std::atan2(dot(cen, e2), dot(cen, e1)) - theta0;
+            dth = std::remainder(dth, 2.0 * pi);
+            if (dth <= -pi) dth += 2.0 * pi;
+            if (std::fabs(dth) <= half_w) val = amp * std::cos(0.5 * pi * dth / half_w);
+        }
+        flux_face[f] = val;
+    }
+}
+
 }  // namespace qpat

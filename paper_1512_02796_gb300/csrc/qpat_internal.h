@@ -65,6 +65,9 @@ std::string build_host_mesh(const double* xyz, int64_t N, const int32_t* tets,
 // Flux of a square boundary patch in canonical face order (see qpat.h).
 void flux_patch_host(const HostMesh& m, const double c[3], const double n[3],
                      double half_w, double amp, double* flux_face);
+// Flux through the curved side of a cylinder in canonical face order (see qpat.h).
+void flux_side_host(const HostMesh& m, const double c[3], const double axis[3], const double ref[3],
+                    double radius, double theta0, double half_w, double amp, double* flux_face);
 
 // Plain-old-data view of the device copy of a mesh, passed to kernels by value.
 struct MeshDev {

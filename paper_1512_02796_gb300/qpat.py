@@ -8,6 +8,7 @@ libqpat.so; there is no fallback: a missing library or a failing call raises.
 from __future__ import annotations
 
 import ctypes
+import math
 import os
 from typing import Optional, Sequence
 
@@ -89,6 +90,8 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
         "qpat_mesh_reset_stats": (ctypes.c_int, [vp]),
         "qpat_mesh_set_timing": (ctypes.c_int, [vp, ctypes.c_int]),
         "qpat_mesh_pcg_time": (ctypes.c_int, [vp, _c_double_p]),
+        "qpat_flux_side": (ctypes.c_int, [vp, _c_double_p, _c_double_p, _c_double_p, ctypes.c_double,
+                                          ctypes.c_double, ctypes.c_double, ctypes.c_double, _c_double_p]),
         "qpat_flux_patch": (ctypes.c_int, [vp, _c_double_p, _c_double_p, ctypes.c_double, ctypes.c_double,
                                            _c_double_p]),
         "qpat_apply_K_dev": (ctypes.c_int, [vp, ctypes.c_int, vp, vp, ctypes.c_int, vp, vp, vp]),
@@ -155,7 +158,7 @@ def exported_names() -> Sequence[str]:
         "qpat_mesh_num_entries",
         "qpat_mesh_faces", "qpat_mesh_permutation", "qpat_mesh_stats", "qpat_mesh_reset_stats",
         "qpat_mesh_set_timing", "qpat_mesh_pcg_time",
-        "qpat_flux_patch", "qpat_apply_K_dev", "qpat_forward", "qpat_forward_dev", "qpat_forward_noalloc_dev",
+        "qpat_flux_patch", "qpat_flux_side", "qpat_apply_K_dev", "qpat_forward", "qpat_forward_dev", "qpat_forward_noalloc_dev",
         "qpat_forward_guess_dev",
         "qpat_jvp", "qpat_jvp_dev",
         "qpat_vjp", "qpat_vjp_dev", "qpat_jvp_vjp_pair_dev", "qpat_prior_solve", "qpat_prior_solve_dev",
@@ -377,6 +380,16 @@ def qpat_mesh_host_info(xyz, tets, patch_nodes: int = 512):
                                    perm.ctypes.data_as(_c_int32_p)))
     keys = ["F", "P", "max_touched", "max_own", "max_ptets", "max_pfaces", "patch_tets", "patch_faces"]
     return dict(zip(keys, (int(v) for v in info))), faces, perm
+
+
+def qpat_flux_side(mesh: Mesh, center, axis, ref, radius: float, theta0: float, half_w: float = math.pi / 8,
+                   amp: float = 1.0) -> np.ndarray:
+    """Per-face flux (canonical face order) through the curved side of a
+    cylinder, cos(pi/2 (theta - theta0) / half_w) on |theta - theta0| <= half_w."""
+    out = np.empty(mesh.F)
+    _check(load().qpat_flux_side(mesh.handle, _dp(_f64(center)), _dp(_f64(axis)), _dp(_f64(ref)), float(radius),
+                                 float(theta0), float(half_w), float(amp), _dp(out)))
+    return out
 
 
 def qpat_flux_patch(mesh: Mesh, center, normal, half_w: float, amp: float = 1.0) -> np.ndarray:

@@ -25,6 +25,7 @@ __all__ = [
     "kuhn_cube", "fine_to_coarse_index", "Sphere", "Patch", "Config",
     "spheres_phantom", "blob_phantom", "config", "noise_draws",
     "random_vector", "kappa_from_optics", "CONFIG_NAMES",
+    "cylinder_mesh", "SideIllumination", "CylinderConfig", "cylinder_config",
 ]
 
 
@@ -298,3 +299,103 @@ def noise_draws(seed: int, shape) -> np.ndarray:
 def random_vector(seed: int, shape) -> np.ndarray:
     """Seeded standard-normal test vector."""
     return np.random.default_rng(seed).standard_normal(shape)
+
+
+# ------------------------------------------------------------------ cylinder (Test 1 geometry)
+
+def cylinder_mesh(n: int, nz: int, R: float, H: float) -> Tuple[np.ndarray, np.ndarray]:
+    """Tetrahedral mesh of the cylinder {x^2 + y^2 <= R^2, 0 <= z <= H}.
+
+    A Kuhn grid with n x n x nz nodes on [-1, 1]^2 x [0, H] is mapped onto
+    the cylinder by sending each square ring max(|x|, |y|) = s to the circle
+    of radius s R along rays from the axis: (x, y) -> R s (x, y) / |(x, y)|.
+    The map is a homeomorphism, so the mesh stays conforming; tets take many
+    shapes and the side is a polygonal approximation of the circle whose
+    boundary nodes lie exactly at radius R.  Node and tet numbering follow
+    the Kuhn grid (x fastest).  Orientation is left as generated.
+    """
+    if n < 3 or nz < 2:
+        raise ValueError("cylinder_mesh needs n >= 3 and nz >= 2")
+    g = np.linspace(-1.0, 1.0, n)
+    gz = np.linspace(0.0, H, nz)
+    zz, yy, xx = np.meshgrid(gz, g, g, indexing="ij")
+    x, y = xx.ravel(), yy.ravel()
+    s = np.maximum(np.abs(x), np.abs(y))
+    rho = np.hypot(x, y)
+    f = np.where(rho > 0, s / np.where(rho > 0, rho, 1.0), 0.0) * R
+    xyz = np.stack([x * f, y * f, zz.ravel()], axis=1)
+    m, mz = n - 1, nz - 1
+    kk, jj, ii = np.meshgrid(np.arange(mz), np.arange(m), np.arange(m), indexing="ij")
+    base = (ii + n * (jj + n * kk)).ravel().astype(np.int64)
+    stride = np.array([1, n, n * n], dtype=np.int64)
+    tets = []
+    for perm in itertools.permutations(range(3)):
+        a, b, _ = perm
+        v1 = base + stride[a]
+        tets.append(np.stack([base, v1, v1 + stride[b], base + stride.sum()], axis=1))
+    tets = np.stack(tets, axis=1).reshape(-1, 4)
+    return xyz, tets.astype(np.int32)
+
+
+@dataclasses.dataclass
+class SideIllumination:
+    """Photon flux through the curved side of the cylinder (Sec. 5, Test 1):
+    homogeneous along the axis, centred at polar angle theta0, non-zero for
+    |theta - theta0| <= half_w with amplitude amp cos(pi/2 (theta - theta0) /
+    half_w) (half_w = pi/8 gives the paper's cos(4 (theta - theta0))).  The
+    polar angle is measured about `axis` through `center`, from `ref`."""
+    theta0: float
+    half_w: float = np.pi / 8
+    amp: float = 1.0
+    center: Tuple[float, float, float] = (0.0, 0.0, 0.0)
+    axis: Tuple[float, float, float] = (0.0, 0.0, 1.0)
+    ref: Tuple[float, float, float] = (1.0, 0.0, 0.0)
+
+
+@dataclasses.dataclass
+class CylinderConfig:
+    name: str
+    n: int
+    nz: int
+    R: float
+    H: float
+    illuminations: List[SideIllumination]
+    spheres: List[Sphere]
+    mua_bg: float = 0.01
+    mus_bg: float = 1.0
+    seed: int = 0
+
+    @property
+    def N(self) -> int:
+        return self.n * self.n * self.nz
+
+    @property
+    def K(self) -> int:
+        return len(self.illuminations)
+
+    def mesh(self):
+        return cylinder_mesh(self.n, self.nz, self.R, self.H)
+
+    def optics(self, xyz: np.ndarray):
+        return spheres_phantom(xyz, self.spheres, self.mua_bg, self.mus_bg)
+
+    def coefficients(self, xyz: np.ndarray):
+        mua, mus = self.optics(xyz)
+        return kappa_from_optics(mua, mus), mua
+
+
+def cylinder_config(n: int, nz: int, R: float, H: float, K: int, seed: int) -> CylinderConfig:
+    """Test 1 stand-in: cylinder of radius R and height H, K side
+    illuminations at theta0 = (k - 1) pi / 2 (k = 1..K, cycling), two random
+    spherical inclusions inside radius R/2 (the paper's Test 1 targets are
+    not available)."""
+    rng = np.random.default_rng(seed)
+    spheres = []
+    for i in range(2):
+        r0 = rng.uniform(0.0, 0.5 * R)
+        t0 = rng.uniform(0.0, 2 * np.pi)
+        c = (r0 * np.cos(t0), r0 * np.sin(t0), rng.uniform(0.3 * H, 0.7 * H))
+        spheres.append(Sphere(c, rng.uniform(0.15, 0.25) * R, mua=rng.uniform(0.02, 0.03),
+                              mus=2.0 if i == 0 else None))
+    ill = [SideIllumination(theta0=(k % 4) * np.pi / 2) for k in range(K)]
+    return CylinderConfig(f"cyl{n}x{nz}_K{K}", n, nz, R, H, ill, spheres, seed=seed)

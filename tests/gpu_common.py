@@ -15,7 +15,12 @@ class Case:
         self.xyz, self.tets = cfg.mesh()
         self.om = O.Mesh(self.xyz, self.tets)
         self.kappa, self.mu = cfg.coefficients(self.xyz)
-        self.flux = np.stack([O.flux_patch(self.om, p.center, p.normal, p.half_w, p.amp) for p in cfg.patches])
+        if hasattr(cfg, "illuminations"):     # cylinder: curved-side fluxes (Test 1)
+            self.flux = np.stack([O.flux_side(self.om, il.center, il.axis, il.ref, cfg.R, il.theta0, il.half_w,
+                                              il.amp) for il in cfg.illuminations])
+        else:
+            self.flux = np.stack([O.flux_patch(self.om, p.center, p.normal, p.half_w, p.amp)
+                                  for p in cfg.patches])
         self.K = self.flux.shape[0]
         self.N = self.om.N
         self.patch_nodes = patch_nodes
@@ -40,4 +45,5 @@ def small_cases():
         "cube9_K3": S.small_config(9, 10.0, 3, 2),
         "c0_cube11": S.config("c0_cube11"),
         "cube13_K5": S.small_config(13, 12.0, 5, 3),
+        "cyl9x6_K4": S.cylinder_config(9, 6, 10.0, 8.0, 4, 21),
     }

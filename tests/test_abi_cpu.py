@@ -49,6 +49,20 @@ def test_host_mesh_faces_match_oracle_and_patches_verify(n, L, pn):
     assert info["max_own"] <= pn + 32     # balanced whole 32-node slices
 
 
+@pytest.mark.parametrize("n,nz,pn", [(5, 4, 32), (9, 6, 64), (17, 9, 256)])
+def test_host_mesh_cylinder_faces_match_oracle_and_patches_verify(n, nz, pn):
+    """The mapped cylinder (Test 1 geometry): tets of many shapes, a curved
+    side; the host preparation (faces, order, patches, assembled pattern) is
+    checked by the library's structure validator and against the oracle."""
+    xyz, tets = S.cylinder_mesh(n, nz, 10.0, 8.0)
+    info, faces, perm = Q.qpat_mesh_host_info(xyz, tets, pn)
+    of = O.boundary_faces(tets)
+    np.testing.assert_array_equal(faces, of)
+    assert info["F"] == of.shape[0] == 4 * (n - 1) * (nz - 1) * 2 + 2 * 2 * (n - 1) ** 2
+    assert np.array_equal(np.sort(perm), np.arange(xyz.shape[0]))
+    assert info["max_own"] <= pn + 32
+
+
 def test_host_mesh_random_relabelled_mesh():
     """Faces are canonical in caller ids whatever the node numbering and tet
     orientation."""

@@ -199,6 +199,66 @@ def test_manufactured_solution_second_order():
     assert abs(ratios[-1] - 4.0) < 0.1, ratios
 
 
+def _manufactured_error_cylinder(n, R=1.0, H=2.0, kap=0.3, mu=0.05):
+    """As _manufactured_error on the mapped cylinder mesh (Test 1 geometry):
+    the Robin data is exact on the polygonal domain the mesh covers, so the
+    P1 error must still fall as h^2."""
+    m = O.Mesh(*S.cylinder_mesh(n, n, R, H))
+    a = math.sqrt(mu / kap) * np.array([1.0, 2.0, 2.0]) / 3.0
+    exact = np.exp(m.xyz @ a)
+    W = np.array([[2, 1, 1], [1, 2, 1], [1, 1, 2]]) / 12.0
+    f = np.zeros(m.N)
+    p = m.xyz[m.faces]
+    nrm = np.cross(p[:, 1] - p[:, 0], p[:, 2] - p[:, 0])
+    nrm /= np.linalg.norm(nrm, axis=1)[:, None]
+    cen = p.mean(axis=1)
+    out = np.sign(((cen - np.array([0.0, 0.0, H / 2])) * nrm).sum(1))   # convex body
+    nrm *= out[:, None]
+    for fi in range(m.F):
+        vals = exact[m.faces[fi]] * (0.25 + 0.5 * kap * (nrm[fi] @ a))
+        f[m.faces[fi]] += 2.0 * m.farea[fi] * (W @ vals)
+    K = O.system_matrix(m, np.full(m.N, kap), np.full(m.N, mu))
+    e = O.Factor(K).solve(f) - exact
+    return math.sqrt(e @ (O.assemble_weighted_mass(m, np.ones(m.N)) @ e))
+
+
+def test_manufactured_solution_second_order_on_cylinder():
+    errs = [_manufactured_error_cylinder(n) for n in (5, 9, 17, 33)]
+    ratios = [errs[i] / errs[i + 1] for i in range(3)]
+    assert all(3.3 < r < 4.7 for r in ratios), ratios
+    assert abs(ratios[-1] - 4.0) < 0.3, ratios
+
+
+def test_cylinder_mesh_measures_and_side_flux_converge():
+    """Volume -> pi R^2 H (error O(h^2)), side area -> 2 pi R H (inscribed
+    polygons); the side illumination's total flux sum Phi_F |F| -> R H / 2, the
+    integral of cos(4 (theta - theta0)) over [theta0 - pi/8, theta0 + pi/8]
+    times R H; faces outside the lit band or on the caps carry no flux."""
+    R, H = 10.0, 8.0
+    prev = None
+    for n in (9, 17, 33):
+        m = O.Mesh(*S.cylinder_mesh(n, 5, R, H))
+        vol_err = abs(m.vol.sum() - np.pi * R * R * H) / (np.pi * R * R * H)
+        radial = np.linalg.norm(m.xyz[m.faces][..., :2], axis=2)
+        side = np.all(np.abs(radial - R) <= 1e-9 * R, axis=1)
+        area_err = abs(m.farea[side].sum() - 2 * np.pi * R * H) / (2 * np.pi * R * H)
+        errs = []
+        for k in range(4):
+            fl = O.flux_side(m, (0, 0, 0), (0, 0, 1), (1, 0, 0), R, k * np.pi / 2)
+            assert np.all(fl[~side] == 0.0) and fl.min() >= 0.0 and fl.max() <= 1.0
+            errs.append(abs((fl * m.farea).sum() - R * H / 2) / (R * H / 2))
+        cur = (vol_err, area_err, max(errs))
+        if prev is not None:
+            # volume O(h^2); side nodes are not equally spaced in angle
+            # (square rings), so the side area and flux fall less regularly
+            assert cur[0] < prev[0] / 3.5 and cur[1] < prev[1] / 1.8 and cur[2] < prev[2] / 1.9, (prev, cur)
+        prev = cur
+    assert prev[0] < 2e-3 and prev[1] < 2e-3 and prev[2] < 1e-2
+    # the four illuminations are rotations of each other: equal totals
+    tot = [(O.flux_side(m, (0, 0, 0), (0, 0, 1), (1, 0, 0), R, k * np.pi / 2) * m.farea).sum() for k in range(4)]
+    np.testing.assert_allclose(tot, tot[0], rtol=1e-12)
+
+
 def test_load_vector_nodal_matches_face_constant_for_constant_flux():
     m = small_mesh(5, 2.0)
     nod = np.ones(m.N)
