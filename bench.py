@@ -339,6 +339,8 @@ def run_ours(args):
     if rank == 0 and args.extras:
         out["uneven_batch"] = uneven_batch_leg(Q, torch)
         out["autotune"] = autotune_leg(Q)
+        out["reconstruction"] = recon_leg(Q, torch, n=args.recon_n)
+        out["learned_guess"] = learned_leg(Q, torch)
     if rank == 0 and args.cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(steps=2)
     if rank == 0:
@@ -400,6 +402,118 @@ def uneven_batch_leg(Q, torch, reps: int = 5):
     for m in meshes:
         m.close()
     return res
+
+
+def recon_leg(Q, torch, n: int = 64, seed: int = 7, nlin: int = 5, nlsqr: int = 20):
+    """Algorithm 1 end to end (qpat_reconstruct: background fit, step 0 and
+    nlin linearisations of nlsqr LSQR rounds each, fixed counts so that both
+    precisions do the same work; T = 1e-2) on an n^3 cube with 4 patches,
+    FP64 against FP32 + FP64 refinement: wall time of the host call and the
+    reconstruction error of each.  Data: the library's own
+    FP64 forward on the nested (2n-1)^3 mesh, injected onto the coarse nodes,
+    plus seeded 1 % noise (sigma floor 1e-3 max|h|)."""
+    cfg = S.small_config(n, 40.0, 4, seed)
+    xf, tf = S.kuhn_cube(2 * n - 1, cfg.L)
+    mf = Q.qpat_mesh(xf, tf)
+    kf, mfu = cfg.coefficients(xf)
+    flf = np.stack([Q.qpat_flux_patch(mf, p.center, p.normal, p.half_w, p.amp) for p in cfg.patches])
+    _, hf = Q.qpat_forward(mf, kf, mfu, flf, Q.qpat_default_params(precision=0))
+    mf.close()
+    h = hf[:, S.fine_to_coarse_index(n)]
+    sig = 0.01 * np.abs(h) + 1e-3 * np.abs(h).max()
+    chi = h + sig * S.noise_draws(seed + 1, h.shape)
+    xyz, tets = cfg.mesh()
+    kap_t, mu_t = cfg.coefficients(xyz)
+    mesh = Q.qpat_mesh(xyz, tets)
+    flux = np.stack([Q.qpat_flux_patch(mesh, p.center, p.normal, p.half_w, p.amp) for p in cfg.patches])
+    out = {"n": n, "nodes": mesh.N, "illuminations": cfg.K}
+    res = {}
+    common = dict(T=1e-2, max_lin=nlin, max_lsqr=nlsqr, fixed_counts=1)
+    out["params"] = dict(common)
+    for name, prm in (("fp64", Q.qpat_default_params(precision=0, **common)),
+                      ("mixed", Q.qpat_default_params(precision=1, fp32_operator=1, **common))):
+        warm = Q.qpat_default_params(precision=prm.precision, fp32_operator=1, T=1e-2, max_lin=1, max_lsqr=2,
+                                     fixed_counts=1)
+        Q.qpat_reconstruct(mesh, flux, chi, sig, warm)         # warm-up (workspace, kernels)
+        t0 = time.perf_counter()
+        kap, mu, rep = Q.qpat_reconstruct(mesh, flux, chi, sig, prm)
+        dt = time.perf_counter() - t0
+        res[name] = (kap, mu)
+        out[name] = {"wall_s": dt, "e_mu": float(np.linalg.norm(mu - mu_t) / np.linalg.norm(mu_t)),
+                     "e_kappa": float(np.linalg.norm(kap - kap_t) / np.linalg.norm(kap_t)),
+                     "linearisations": int(rep.linearisations),
+                     "lsqr_rounds": [int(v) for v in rep.lsqr_iters[:rep.linearisations]],
+                     "pcg_iters": int(rep.pcg_iters)}
+    f, m = out["fp64"], out["mixed"]
+    out["speedup_mixed_vs_fp64"] = f["wall_s"] / m["wall_s"]
+    out["field_rel_diff"] = max(float(np.linalg.norm(res["mixed"][i] - res["fp64"][i]) / np.linalg.norm(res["fp64"][i]))
+                                for i in range(2))
+    # equal error (survey 8(d)): errors within 1 % of the FP64 form's and fields within 1e-6 of them
+    out["equal_error"] = bool(abs(m["e_mu"] - f["e_mu"]) <= 0.01 * f["e_mu"]
+                              and abs(m["e_kappa"] - f["e_kappa"]) <= 0.01 * f["e_kappa"]
+                              and out["field_rel_diff"] <= 1e-6)
+    mesh.close()
+    return out
+
+
+def learned_leg(Q, torch, n: int = 32, train_phantoms: int = 18, steps: int = 150):
+    """Learned initial guess: the BF16 U-Net trained on the library's own
+    FP32 + refinement forward solves of `train_phantoms` seeded phantoms on an
+    n^3 cube (1 illumination each), then FP64 forward solves of held-out
+    phantoms from zero and from the network's guess, both to the same
+    tolerance: PCG iterations, device time (CUDA events) and the difference
+    of the two solutions."""
+    from paper_1512_02796_gb300 import learned as LG
+    cfgs = [S.small_config(n, 20.0, 1, 500 + i) for i in range(train_phantoms + 2)]
+    xyz, tets = cfgs[0].mesh()
+    mesh = Q.qpat_mesh(xyz, tets)
+    net = Q.UNet(n, seed=1)
+    try:
+        X, T = [], []
+        for cfg in cfgs[:train_phantoms]:
+            kap, mu = cfg.coefficients(xyz)
+            flux = np.stack([Q.qpat_flux_patch(mesh, p.center, p.normal, p.half_w, p.amp) for p in cfg.patches])
+            x, t = LG.sample(mesh, cfg, kap, mu, flux)
+            X.append(x)
+            T.append(t)
+        t0 = time.perf_counter()
+        losses = LG.train(net, torch.cat(X), torch.cat(T), steps=steps, lr=3e-3, batch=4)
+        torch.cuda.synchronize()
+        train_s = time.perf_counter() - t0
+        dev = torch.device("cuda")
+        prm = Q.qpat_default_params(precision=0)
+        rows = []
+        for cfg in cfgs[train_phantoms:]:
+            kap, mu = cfg.coefficients(xyz)
+            flux = np.stack([Q.qpat_flux_patch(mesh, p.center, p.normal, p.half_w, p.amp) for p in cfg.patches])
+            k, m, f = (torch.tensor(a, device=dev) for a in (kap, mu, flux))
+            x, _ = LG.sample(mesh, cfg, kap, mu, flux)
+            phi0 = LG.guess(net, x)
+            pa = torch.empty((1, mesh.N), dtype=torch.float64, device=dev)
+            pb = torch.empty_like(pa)
+            hh = torch.empty_like(pa)
+            e = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+            Q.qpat_forward_dev(mesh, k, m, f, pa, hh, prm)            # warm-up
+            mesh.reset_stats()
+            e[0].record()
+            Q.qpat_forward_dev(mesh, k, m, f, pa, hh, prm)
+            e[1].record()
+            torch.cuda.synchronize()
+            it_plain = mesh.stats()["pcg_iters"]
+            mesh.reset_stats()
+            e[2].record()
+            Q.qpat_forward_guess_dev(mesh, k, m, f, phi0, pb, hh, prm)
+            e[3].record()
+            torch.cuda.synchronize()
+            it_guess = mesh.stats()["pcg_iters"]
+            rows.append({"pcg_iters_plain": it_plain, "pcg_iters_guess": it_guess,
+                         "ms_plain": e[0].elapsed_time(e[1]), "ms_guess": e[2].elapsed_time(e[3]),
+                         "solution_rel_diff": float(torch.linalg.norm(pb - pa) / torch.linalg.norm(pa))})
+        return {"n": n, "train_phantoms": train_phantoms, "adam_steps": steps, "train_s": train_s,
+                "loss_first": float(losses[0]), "loss_last": float(np.mean(losses[-10:])), "held_out": rows}
+    finally:
+        net.close()
+        mesh.close()
 
 
 def autotune_leg(Q):
@@ -534,7 +648,9 @@ def main():
                     help="FP32 inner operator: 0 matrix-free elements, 1 assembled values")
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
     ap.add_argument("--no-extras", dest="extras", action="store_false",
-                    help="skip the uneven-batch and autotuner legs")
+                    help="skip the uneven-batch, autotuner, reconstruction and learned-guess legs")
+    ap.add_argument("--recon-n", type=int, default=64,
+                    help="nodes per side of the cube of the reconstruction leg (FP64 vs mixed)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -89,7 +89,11 @@ typedef struct {
                               of the alternatives named after Eq. (10) (q = 1:
                               smoothed total variation).  The lagged step
                               weights each tet by r'(t)/t (Eq. (14)). */
-    int reserved[4];
+    int mixed_restart;     /* precision 1: 0 = reliable updates (each FP32 inner run
+                              continues the previous search direction, rescaled,
+                              after r is replaced by the true FP64 residual);
+                              1 = restart the inner PCG at every refinement sweep */
+    int reserved[3];
     double prior_q;        /* q of prior 1, in (0, 2] */
 } qpat_params;
 
@@ -147,6 +151,10 @@ int qpat_mesh_host_info(const double* xyz, int64_t N, const int32_t* tets, int64
  * last reset: out4 = {PCG iterations, solves (RHS), FP64 refinement sweeps,
  * PCG launches}. */
 int qpat_mesh_stats(qpat_mesh_t mesh, int64_t* out4);
+/* Precision-1 solves of K whose FP32 inner PCG broke down, or whose FP64
+ * refinement stalled, and that were therefore solved again by the FP64 PCG
+ * (since the last reset); -1 for a NULL mesh. */
+int64_t qpat_mesh_fp64_fallbacks(qpat_mesh_t mesh);
 int qpat_mesh_reset_stats(qpat_mesh_t mesh);
 
 /* When on, every PCG launch is bracketed by CUDA events recorded on the

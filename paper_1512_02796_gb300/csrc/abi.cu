@@ -321,81 +321,130 @@ int solve(qpat_mesh_s* M, const OpState& st, const SolveOpts& so_in, int R, cons
         return pcg_status(hst[0], pfx);
     }
 
-    // ---- FP32 PCG inside FP64 refinement
-    double* Rres = M->ws.get<double>(nm("res64"), n, s, &e);
-    double* tmp = M->ws.get<double>(nm("tmp64"), n, s, &e);
-    float* b32 = M->ws.get<float>(nm("b32"), n, s, &e);
-    float* x32 = M->ws.get<float>(nm("x32"), n, s, &e);
-    double* dpart = M->ws.get<double>("dots.partial", 608 * 16, s, &e);
-    double* dnorm = M->ws.get<double>(nm("norms"), 64, s, &e);  // [0,R): |r|^2, [16,16+R): |B|^2, [32,..): |r|
-    if (e != cudaSuccess) return cuda_fail(e, "workspace");
-    w.b = b32;
-    w.x = x32;
-    const int OP = so.fp32_assembled ? OP_CSR1 : OP_K;
-    OpParams<float> op{st.c1_32, st.c2_32, float(st.inv_T2), float(st.scale1), float(st.delta), 1, st.v32[0],
-                       nullptr};
-    if (X0) {
-        // start from the initial guess: X = X0, r = B - A X0
-        if ((e = cudaMemcpyAsync(X, X0, n * sizeof(double), cudaMemcpyDeviceToDevice, s)) != cudaSuccess)
-            return cuda_fail(e, "copy");
-        if ((e = apply_op64(M, st, R, X, tmp, s)) != cudaSuccess) return cuda_fail(e, "apply64");
-        if ((e = launch_sub(n, B, tmp, Rres, s)) != cudaSuccess) return cuda_fail(e, "sub");
-    } else {
-        if ((e = cudaMemsetAsync(X, 0, n * sizeof(double), s)) != cudaSuccess) return cuda_fail(e, "memset");
-        if ((e = cudaMemcpyAsync(Rres, B, n * sizeof(double), cudaMemcpyDeviceToDevice, s)) != cudaSuccess)
-            return cuda_fail(e, "copy");
-    }
-    if ((e = launch_dots<double>(N, R, B, B, dpart, dnorm + 16, s)) != cudaSuccess) return cuda_fail(e, "dots");
-    if ((e = cudaMemcpyAsync(hpin + 16, dnorm + 16, R * sizeof(double), cudaMemcpyDeviceToHost, s)) != cudaSuccess)
-        return cuda_fail(e, "copy");
-    int sweeps = 0;
-    for (;;) {
-        if ((e = launch_dots<double>(N, R, Rres, Rres, dpart, dnorm, s)) != cudaSuccess) return cuda_fail(e, "dots");
-        if ((e = cudaMemcpyAsync(hpin, dnorm, R * sizeof(double), cudaMemcpyDeviceToHost, s)) != cudaSuccess)
-            return cuda_fail(e, "copy");
-        if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return cuda_fail(e, "sync");
-        bool done = true;
-        for (int r = 0; r < R; ++r) {
-            if (!std::isfinite(hpin[r])) return fail(QPAT_EBREAKDOWN, "refinement: residual not finite");
-            if (hpin[r] > so.rtol * so.rtol * hpin[16 + r]) done = false;
+    // ---- FP32 PCG inside FP64 refinement.  If the FP32 inner solve breaks
+    // down or the refinement stalls (an iterate's coefficients outside the
+    // range FP32 resolves), this system is solved again by the FP64 PCG.
+    auto refine = [&]() -> int {
+        double* Rres = M->ws.get<double>(nm("res64"), n, s, &e);
+        double* tmp = M->ws.get<double>(nm("tmp64"), n, s, &e);
+        float* b32 = M->ws.get<float>(nm("b32"), n, s, &e);
+        float* x32 = M->ws.get<float>(nm("x32"), n, s, &e);
+        double* dpart = M->ws.get<double>("dots.partial", 608 * 16, s, &e);
+        double* dnorm = M->ws.get<double>(nm("norms"), 64, s, &e);  // [0,R): |r|^2, [16,16+R): |B|^2, [32,..): |r|
+        if (e != cudaSuccess) return cuda_fail(e, "workspace");
+        w.b = b32;
+        w.x = x32;
+        const int OP = so.fp32_assembled ? OP_CSR1 : OP_K;
+        OpParams<float> op{st.c1_32, st.c2_32, float(st.inv_T2), float(st.scale1), float(st.delta), 1, st.v32[0],
+                           nullptr};
+        if (X0) {
+            // start from the initial guess: X = X0, r = B - A X0
+            if ((e = cudaMemcpyAsync(X, X0, n * sizeof(double), cudaMemcpyDeviceToDevice, s)) != cudaSuccess)
+                return cuda_fail(e, "copy");
+            if ((e = apply_op64(M, st, R, X, tmp, s)) != cudaSuccess) return cuda_fail(e, "apply64");
+            if ((e = launch_sub(n, B, tmp, Rres, s)) != cudaSuccess) return cuda_fail(e, "sub");
+        } else {
+            if ((e = cudaMemsetAsync(X, 0, n * sizeof(double), s)) != cudaSuccess) return cuda_fail(e, "memset");
+            if ((e = cudaMemcpyAsync(Rres, B, n * sizeof(double), cudaMemcpyDeviceToDevice, s)) != cudaSuccess)
+                return cuda_fail(e, "copy");
         }
-        if (done) break;
-        if (sweeps >= so.max_sweeps) return fail(QPAT_ENOCONV, "refinement: sweep cap reached");
-        ++sweeps;
-        qpat::note_launch(1);
-        k_sqrt_vec<<<1, 32, 0, s>>>(R, dnorm, dnorm + 32);
-        if ((e = launch_cast_d2f_scaled(N, R, Rres, dnorm + 32, b32, s)) != cudaSuccess) return cuda_fail(e, "cast");
-        if (M->timing) cudaEventRecord(M->ev0, s);
-        e = cudaErrorNotSupported;
-        if (ring) e = launch_pcg_ring<float>(M->d, OP, R, op, st.inv32, w, so.inner_rtol, so.maxit, s, nullptr);
-        if (e == cudaErrorNotSupported) {
-            if (so.pcg_variant == 3) return fail(QPAT_EINVAL, "pcg32: the bulk-copy ring does not fit this mesh");
-            e = single ? launch_pcg1<float>(M->d, OP, R, op, st.inv32, w, so.inner_rtol, so.maxit, s, nullptr)
-                       : launch_pcg<float>(M->d, OP, R, op, st.inv32, w, so.inner_rtol, so.maxit, s, nullptr);
-        }
-        if (e != cudaSuccess) return cuda_fail(e, "pcg32 launch");
-        if (M->timing) cudaEventRecord(M->ev1, s);
-        int hst[2];
-        if ((e = cudaMemcpyAsync(hst, w.status, sizeof(int), cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
-            (e = cudaMemcpyAsync(hst + 1, w.iters, sizeof(int), cudaMemcpyDeviceToHost, s)) != cudaSuccess)
+        if ((e = launch_dots<double>(N, R, B, B, dpart, dnorm + 16, s)) != cudaSuccess) return cuda_fail(e, "dots");
+        if ((e = cudaMemcpyAsync(hpin + 16, dnorm + 16, R * sizeof(double), cudaMemcpyDeviceToHost, s)) != cudaSuccess)
             return cuda_fail(e, "copy");
-        if ((e = launch_axpy_f2d_scaled(N, R, x32, dnorm + 32, X, s)) != cudaSuccess) return cuda_fail(e, "axpy");
-        if ((e = apply_op64(M, st, R, X, tmp, s)) != cudaSuccess) return cuda_fail(e, "apply64");
-        if ((e = launch_sub(n, B, tmp, Rres, s)) != cudaSuccess) return cuda_fail(e, "sub");
-        if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return cuda_fail(e, "sync");
-        if (M->timing) {
-            float ms = 0.f;
-            cudaEventElapsedTime(&ms, M->ev0, M->ev1);
-            M->pcg_ms += ms;
+        // Reliable updates: each inner run continues the previous one's search
+        // direction (rescaled to the new RHS scaling) instead of restarting,
+        // with r replaced by the true FP64 residual; the Krylov space built in
+        // FP32 is kept across the FP64 corrections.
+        const bool reliable = !so.mixed_restart && !single && !ring;
+        double* gam = M->ws.get<double>(nm("gamma"), 16, s, &e);
+        double* rzst = M->ws.get<double>(nm("rzstate"), 16, s, &e);
+        int* pbufp = M->ws.get<int>(nm("pbuf"), 1, s, &e);
+        if (e != cudaSuccess) return cuda_fail(e, "workspace");
+        double prev_scale[16];
+        w.rz_state = reliable ? rzst : nullptr;
+        w.pbuf = reliable ? pbufp : nullptr;
+        bool resume_next = false;  // set when the last inner run ended normally
+        int first_iters = 0;       // iterations of this solve's first inner run
+        int sweeps = 0;
+        for (;;) {
+            if ((e = launch_dots<double>(N, R, Rres, Rres, dpart, dnorm, s)) != cudaSuccess) return cuda_fail(e, "dots");
+            if ((e = cudaMemcpyAsync(hpin, dnorm, R * sizeof(double), cudaMemcpyDeviceToHost, s)) != cudaSuccess)
+                return cuda_fail(e, "copy");
+            if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return cuda_fail(e, "sync");
+            bool done = true;
+            for (int r = 0; r < R; ++r) {
+                if (!std::isfinite(hpin[r])) return fail(QPAT_EBREAKDOWN, "refinement: residual not finite");
+                if (hpin[r] > so.rtol * so.rtol * hpin[16 + r]) done = false;
+            }
+            if (done) break;
+            if (sweeps >= so.max_sweeps) return fail(QPAT_ENOCONV, "refinement: sweep cap reached");
+            w.resume_gamma = nullptr;
+            if (reliable && sweeps > 0 && resume_next) {
+                // safeguard: continue the previous direction only while the
+                // last run cut every residual that was not converged by 10x;
+                // otherwise the FP32 recurrence has drifted and a fresh start
+                // is better
+                bool progress = true;
+                for (int r = 0; r < R; ++r) {
+                    const double nr = std::sqrt(hpin[r]);
+                    if (hpin[r] > so.rtol * so.rtol * hpin[16 + r] && nr > 0.1 * prev_scale[r]) progress = false;
+                    hpin[48 + r] = nr > 0.0 ? prev_scale[r] / nr : 0.0;
+                }
+                if (progress) {
+                if ((e = cudaMemcpyAsync(gam, hpin + 48, R * sizeof(double), cudaMemcpyHostToDevice, s)) != cudaSuccess)
+                    return cuda_fail(e, "copy");
+                w.resume_gamma = gam;
+                }
+            }
+            for (int r = 0; r < R; ++r) prev_scale[r] = std::sqrt(hpin[r]);
+            ++sweeps;
+            qpat::note_launch(1);
+            k_sqrt_vec<<<1, 32, 0, s>>>(R, dnorm, dnorm + 32);
+            if ((e = launch_cast_d2f_scaled(N, R, Rres, dnorm + 32, b32, s)) != cudaSuccess) return cuda_fail(e, "cast");
+            if (M->timing) cudaEventRecord(M->ev0, s);
+            // a resumed run that needs far more iterations than the first run
+            // has stagnated in FP32: it is cut short and the next run restarts
+            const int seg_maxit = w.resume_gamma ? std::min(so.maxit, std::max(100, 2 * first_iters)) : so.maxit;
+            e = cudaErrorNotSupported;
+            if (ring) e = launch_pcg_ring<float>(M->d, OP, R, op, st.inv32, w, so.inner_rtol, seg_maxit, s, nullptr);
+            if (e == cudaErrorNotSupported) {
+                if (so.pcg_variant == 3) return fail(QPAT_EINVAL, "pcg32: the bulk-copy ring does not fit this mesh");
+                e = single ? launch_pcg1<float>(M->d, OP, R, op, st.inv32, w, so.inner_rtol, seg_maxit, s, nullptr)
+                           : launch_pcg<float>(M->d, OP, R, op, st.inv32, w, so.inner_rtol, seg_maxit, s, nullptr);
+            }
+            if (e != cudaSuccess) return cuda_fail(e, "pcg32 launch");
+            if (M->timing) cudaEventRecord(M->ev1, s);
+            int hst[2];
+            if ((e = cudaMemcpyAsync(hst, w.status, sizeof(int), cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
+                (e = cudaMemcpyAsync(hst + 1, w.iters, sizeof(int), cudaMemcpyDeviceToHost, s)) != cudaSuccess)
+                return cuda_fail(e, "copy");
+            if ((e = launch_axpy_f2d_scaled(N, R, x32, dnorm + 32, X, s)) != cudaSuccess) return cuda_fail(e, "axpy");
+            if ((e = apply_op64(M, st, R, X, tmp, s)) != cudaSuccess) return cuda_fail(e, "apply64");
+            if ((e = launch_sub(n, B, tmp, Rres, s)) != cudaSuccess) return cuda_fail(e, "sub");
+            if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return cuda_fail(e, "sync");
+            if (M->timing) {
+                float ms = 0.f;
+                cudaEventElapsedTime(&ms, M->ev0, M->ev1);
+                M->pcg_ms += ms;
+            }
+            M->stats.pcg_iters += hst[1];
+            M->stats.launches += 1;
+            M->stats.refinements += 1;
+            // an inner run that stops at its cap still improves x (the next
+            // one then starts afresh); breakdown or timeout is fatal
+            if (hst[0] == QPAT_ETIMEOUT || hst[0] == QPAT_EBREAKDOWN) return pcg_status(hst[0], "pcg32");
+            resume_next = hst[0] == QPAT_OK;
+            if (sweeps == 1) first_iters = hst[1];
         }
-        M->stats.pcg_iters += hst[1];
-        M->stats.launches += 1;
-        M->stats.refinements += 1;
-        // an inner run that stops at its cap still improves x; breakdown or timeout is fatal
-        if (hst[0] == QPAT_ETIMEOUT || hst[0] == QPAT_EBREAKDOWN) return pcg_status(hst[0], "pcg32");
-    }
-    M->stats.solves += R;
-    return QPAT_OK;
+        M->stats.solves += R;
+        return QPAT_OK;
+    };
+    const int rc = refine();
+    if (rc != QPAT_EBREAKDOWN && rc != QPAT_ENOCONV) return rc;
+    M->stats.fp64_fallbacks += 1;
+    SolveOpts s64 = so;
+    s64.precision = 0;
+    return solve(M, st, s64, R, B, X, s, X0);
 }
 
 }  // namespace qpat
@@ -595,6 +644,8 @@ int qpat_mesh_stats(qpat_mesh_t M, int64_t* out4) {
     out4[3] = M->stats.launches;
     return QPAT_OK;
 }
+
+int64_t qpat_mesh_fp64_fallbacks(qpat_mesh_t M) { return M ? M->stats.fp64_fallbacks : -1; }
 
 int qpat_mesh_reset_stats(qpat_mesh_t M) {
     if (!M) return fail(QPAT_EINVAL, "qpat_mesh_reset_stats: NULL mesh");

@@ -27,6 +27,7 @@ struct SolveStats {
     int64_t pcg_iters = 0;
     int64_t solves = 0;
     int64_t refinements = 0;
+    int64_t fp64_fallbacks = 0;     // mixed-precision solves redone in FP64
     int64_t launches = 0;
 };
 
@@ -54,6 +55,7 @@ struct SolveOpts {
     int max_sweeps = 30;
     int fp32_assembled = 0;   // FP32 inner operator: 0 matrix-free elements, 1 assembled values
     int pcg_variant = 0;      // assembled operators: 0 (= 1) two reductions, 2 one reduction, 3 bulk-copy ring
+    int mixed_restart = 0;    // precision 1: 0 reliable updates (keep the direction), 1 restart every sweep
 };
 
 struct DeviceGuard {

@@ -73,6 +73,11 @@ struct PcgWork {
     void* p1;
     void* q;
     void* z = nullptr;  // optional N x R: D^-1 r kept by the owner (saves a multiply per halo node)
+    // optional resume state of the two-reduction kernel (reliable updates):
+    // resume_gamma (R, NULL = fresh start), rz_state (R), pbuf (1); see pcg.cu
+    const double* resume_gamma = nullptr;
+    double* rz_state = nullptr;
+    int* pbuf = nullptr;
     // extra vectors of the single-reduction variant (see pcg.cu)
     void* r1 = nullptr;
     void* s0 = nullptr;

@@ -144,6 +144,7 @@ SolveOpts solve_opts(const qpat_params* prm) {
     so.maxit = p->max_pcg_iter > 0 ? p->max_pcg_iter : 20000;
     so.fp32_assembled = p->fp32_operator == 1 ? 1 : 0;
     so.pcg_variant = p->pcg_variant;
+    so.mixed_restart = p->mixed_restart ? 1 : 0;
     return so;
 }
 

@@ -50,6 +50,13 @@ struct PcgArgs {
     int maxit;
     long long spin_limit;
     T* z;   // optional: z = D^-1 r stored by the owner (two-reduction kernel)
+    // optional resume of a previous run (two-reduction kernel, reliable
+    // updates): gamma[r] rescales the previous direction to this run's RHS
+    // scaling; rz_state[r] and *pbuf carry r.z of the previous direction and
+    // the buffer (p0/p1) holding it, and are rewritten at exit
+    const double* resume_gamma;
+    double* rz_state;
+    int* pbuf;
     T* r1;  // single-reduction variant
     T* s0;
     T* s1;
@@ -303,7 +310,7 @@ __device__ __forceinline__ void pcg_body(const PcgArgs<T>& a, const int cta, con
     }
     __shared__ double scratch[(kThreads / 32) * kMaxNS];
     __shared__ double red[kMaxNS];
-    __shared__ double bb[R], rz[R], rz_old[R], rr[R], alpha[R], beta[R];
+    __shared__ double bb[R], rz[R], rz_old[R], rr[R], alpha[R], beta[R], zcoef[R];
     __shared__ int s_flag;
 
     const MeshDev& m = a.m;
@@ -311,6 +318,9 @@ __device__ __forceinline__ void pcg_body(const PcgArgs<T>& a, const int cta, con
     const int part = threadIdx.x % NP;  // this thread's RHS block [part*VW, part*VW + VW)
     const int r0 = part * VW;
     const bool zs = a.z != nullptr;
+    const bool resumed = a.resume_gamma != nullptr;
+    const int pb_in = a.pbuf ? *a.pbuf : 0;
+    const int off = resumed ? (pb_in == 0 ? 1 : 0) : 0;  // iteration 0 reads p_old from buffer pb_in
     int red_id = 0;
 
     // ---- initial residual r = b (x0 = 0)
@@ -347,7 +357,10 @@ __device__ __forceinline__ void pcg_body(const PcgArgs<T>& a, const int cta, con
             bb[threadIdx.x] = red[threadIdx.x];
             rz[threadIdx.x] = red[R + threadIdx.x];
             rr[threadIdx.x] = red[2 * R + threadIdx.x];
-            rz_old[threadIdx.x] = 1.0;
+            // resumed: the previous direction's r.z in this run's scaling
+            rz_old[threadIdx.x] = resumed ? a.resume_gamma[threadIdx.x] * a.resume_gamma[threadIdx.x] *
+                                                a.rz_state[threadIdx.x]
+                                          : 1.0;
         }
         __syncthreads();
     }
@@ -366,18 +379,28 @@ __device__ __forceinline__ void pcg_body(const PcgArgs<T>& a, const int cta, con
             if (cta == 0 && threadIdx.x == 0) atomicCAS(a.status, 0, QPAT_ENOCONV);
             break;
         }
+        const bool prev = it > 0 || resumed;  // a previous direction exists
         if (threadIdx.x < R) {
             const int r = threadIdx.x;
             const bool act = rr[r] > a.rtol2 * bb[r];
-            beta[r] = (it == 0 || !act) ? 0.0 : rz[r] / rz_old[r];
+            double b_ = (!prev || !act || !(rz_old[r] > 0.0)) ? 0.0 : rz[r] / rz_old[r];
+            // resumed run, first step: p = z + beta (gamma p_prev)
+            if (it == 0 && resumed) b_ *= a.resume_gamma[r];
+            // a converged (frozen) RHS keeps its last direction unchanged, so
+            // that a resumed run continues from a conjugate direction
+            beta[r] = act ? b_ : (prev ? 1.0 : 0.0);
+            zcoef[r] = act ? 1.0 : 0.0;
         }
         __syncthreads();
 
-        T* pc = (it & 1) ? a.p1 : a.p0;
-        const T* pp = (it & 1) ? a.p0 : a.p1;
-        T bt[VW];
+        T* pc = ((it + off) & 1) ? a.p1 : a.p0;
+        const T* pp = ((it + off) & 1) ? a.p0 : a.p1;
+        T bt[VW], zc[VW];
 #pragma unroll
-        for (int c = 0; c < VW; ++c) bt[c] = T(beta[r0 + c]);
+        for (int c = 0; c < VW; ++c) {
+            bt[c] = T(beta[r0 + c]);
+            zc[c] = T(zcoef[r0 + c]);
+        }
 
         // ---- phase A: p = D^-1 r + beta p_old on touched nodes, q = A p on owned nodes
         T accA[1][VW];
@@ -403,14 +426,14 @@ __device__ __forceinline__ void pcg_body(const PcgArgs<T>& a, const int cta, con
                         vld_cg(a.r + e, rv[u]);
                         dinv_vec<T, VW, OP>(a.invdiag, g, r0, d[u]);
                     }
-                    if (it > 0) vld_cg(pp + e, po[u]);
+                    if (prev) vld_cg(pp + e, po[u]);
                 }
 #pragma unroll
                 for (int u = 0; u < kUnroll; ++u) {
                     T pv[VW];
 #pragma unroll
                     for (int c = 0; c < VW; ++c)
-                        pv[c] = (zs ? rv[u][c] : d[u][c] * rv[u][c]) + (it > 0 ? bt[c] * po[u][c] : T(0));
+                        pv[c] = zc[c] * (zs ? rv[u][c] : d[u][c] * rv[u][c]) + (prev ? bt[c] * po[u][c] : T(0));
                     if (u == 0 || i0 + u * int(blockDim.x) < nt * NP) vst(s.xin + li[u] * R + r0, pv);
                 }
             }
@@ -519,7 +542,11 @@ __device__ __forceinline__ void pcg_body(const PcgArgs<T>& a, const int cta, con
     if (cta == 0 && threadIdx.x < R) {
         a.stats[threadIdx.x] = rr[threadIdx.x];
         a.stats[R + threadIdx.x] = bb[threadIdx.x];
-        if (threadIdx.x == 0) *a.iters = it;
+        if (a.rz_state) a.rz_state[threadIdx.x] = rz_old[threadIdx.x];  // r.z that formed the last p
+        if (threadIdx.x == 0) {
+            *a.iters = it;
+            if (a.pbuf && it > 0) *a.pbuf = (it - 1 + off) & 1;
+        }
     }
 }
 
@@ -1352,6 +1379,9 @@ cudaError_t launch_pcg_t(const MeshDev& m, const OpParams<T>& op, const T* invdi
     a.maxit = maxit;
     a.spin_limit = 40000000LL;  // about 2 s of __nanosleep(32) spins
     a.z = static_cast<T*>(w.z);
+    a.resume_gamma = w.resume_gamma;
+    a.rz_state = w.rz_state;
+    a.pbuf = w.pbuf;
     a.r1 = static_cast<T*>(w.r1);
     a.s0 = static_cast<T*>(w.s0);
     a.s1 = static_cast<T*>(w.s1);

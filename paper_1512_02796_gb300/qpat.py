@@ -30,7 +30,8 @@ class qpat_params(ctypes.Structure):
         ("max_lsqr", ctypes.c_int), ("fixed_counts", ctypes.c_int), ("precision", ctypes.c_int),
         ("max_pcg_iter", ctypes.c_int), ("pcg_rtol", ctypes.c_double), ("fit_grid", ctypes.c_int),
         ("fit_gn_steps", ctypes.c_int), ("patch_nodes", ctypes.c_int), ("fp32_operator", ctypes.c_int),
-        ("pcg_variant", ctypes.c_int), ("prior", ctypes.c_int), ("reserved", ctypes.c_int * 4),
+        ("pcg_variant", ctypes.c_int), ("prior", ctypes.c_int), ("mixed_restart", ctypes.c_int),
+        ("reserved", ctypes.c_int * 3),
         ("prior_q", ctypes.c_double),
     ]
 
@@ -87,6 +88,7 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
         "qpat_mesh_faces": (ctypes.c_int, [vp, _c_int32_p]),
         "qpat_mesh_permutation": (ctypes.c_int, [vp, _c_int32_p]),
         "qpat_mesh_stats": (ctypes.c_int, [vp, _c_int64_p]),
+        "qpat_mesh_fp64_fallbacks": (ctypes.c_int64, [vp]),
         "qpat_mesh_reset_stats": (ctypes.c_int, [vp]),
         "qpat_mesh_set_timing": (ctypes.c_int, [vp, ctypes.c_int]),
         "qpat_mesh_pcg_time": (ctypes.c_int, [vp, _c_double_p]),
@@ -156,7 +158,8 @@ def exported_names() -> Sequence[str]:
         "qpat_default_params", "qpat_last_error", "qpat_launch_count", "qpat_mesh", "qpat_mesh_ex", "qpat_mesh_free",
         "qpat_mesh_host_info", "qpat_mesh_num_nodes", "qpat_mesh_num_tets", "qpat_mesh_num_faces", "qpat_mesh_num_patches",
         "qpat_mesh_num_entries",
-        "qpat_mesh_faces", "qpat_mesh_permutation", "qpat_mesh_stats", "qpat_mesh_reset_stats",
+        "qpat_mesh_faces", "qpat_mesh_permutation", "qpat_mesh_stats", "qpat_mesh_fp64_fallbacks",
+        "qpat_mesh_reset_stats",
         "qpat_mesh_set_timing", "qpat_mesh_pcg_time",
         "qpat_flux_patch", "qpat_flux_side", "qpat_apply_K_dev", "qpat_forward", "qpat_forward_dev", "qpat_forward_noalloc_dev",
         "qpat_forward_guess_dev",
@@ -344,7 +347,7 @@ class Mesh:
         out = np.zeros(4, dtype=np.int64)
         _check(load().qpat_mesh_stats(self.handle, out.ctypes.data_as(_c_int64_p)))
         return {"pcg_iters": int(out[0]), "solves": int(out[1]), "refinements": int(out[2]),
-                "launches": int(out[3])}
+                "launches": int(out[3]), "fp64_fallbacks": int(load().qpat_mesh_fp64_fallbacks(self.handle))}
 
     def reset_stats(self):
         _check(load().qpat_mesh_reset_stats(self.handle))

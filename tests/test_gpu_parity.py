@@ -203,3 +203,30 @@ def test_prior_parameter_checks(case):
     with pytest.raises(Q.QpatError):
         Q.qpat_prior_solve(case.lib, np.zeros(case.N), np.zeros(case.N), np.ones(2 * case.N),
                            _params(0, prior=1, prior_q=2.5))
+
+
+def test_mixed_precision_falls_back_to_fp64_outside_fp32_range(case):
+    """kappa and mu scaled by 1e40 (beyond the FP32 range; K = 1e40 (S + M)
+    up to the Robin term, still well conditioned in FP64) make the FP32
+    operator infinite: the inner PCG reports a breakdown and the solve is
+    redone by the FP64 PCG, so the mixed path returns the FP64 answer."""
+    kap, mu = case.kappa * 1e40, case.mu * 1e40
+    ref, _ = Q.qpat_forward(case.lib, kap, mu, case.flux, _params(0))
+    case.lib.reset_stats()
+    out, _ = Q.qpat_forward(case.lib, kap, mu, case.flux, _params(1, fp32_operator=1))
+    assert case.lib.stats()["fp64_fallbacks"] >= 1
+    assert rel(out, ref) < 1e-10
+
+
+@pytest.mark.parametrize("restart", [0, 1])
+def test_mixed_precision_reliable_updates_and_restarts(case, restart):
+    """Both forms of the FP32 + FP64 refinement solve (reliable updates that
+    keep the FP32 search direction, or a fresh inner PCG per sweep) reach the
+    FP64 answer: forward and the pair of J products."""
+    p = _params(1, fp32_operator=1, mixed_restart=restart)
+    phi, h = Q.qpat_forward(case.lib, case.kappa, case.mu, case.flux, p)
+    assert rel(phi, case.phi) < 1e-10
+    rng = np.random.default_rng(12)
+    s = rng.standard_normal(2 * case.N)
+    out = Q.qpat_jvp(case.lib, case.kappa, case.mu, case.phi, s, case.w, p)
+    assert rel(out, O.jvp(case.om, case.kappa, case.mu, case.phi, s, case.w, case.fac)) < 1e-10
