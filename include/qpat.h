@@ -335,6 +335,14 @@ int qpat_conv3d_bf16_dev(const void* in, int Cin, const void* w, const float* bi
 int qpat_conv3d_bf16_wgrad_dev(const void* in, int Cin, const void* dy, int Cout, int n,
                                float* dw, float* db, float* partial, void* stream);
 int64_t qpat_conv3d_bf16_wgrad_scratch(int n, int Cin, int Cout);
+/* Convolution engine of qpat_conv3d_bf16_dev and of the U-Net (process-wide):
+ * 0 (default) = tcgen05 tensor cores with a tensor-memory accumulator where
+ * the shape allows (Cout % 16 == 0, 16 <= Cout <= 256), else mma.sync;
+ * 1 = mma.sync only.  QPAT_EINVAL for other values.  Not in the paper. */
+int qpat_conv3d_set_engine(int engine);
+/* Bounded waits of the tcgen05 convolution that gave up since the library
+ * was loaded (their tiles are written as NaN); 0 in normal operation. */
+int qpat_conv3d_tc_timeouts(void);
 
 /* ---------------------------------------------------------- autotuner */
 

@@ -428,6 +428,14 @@ int qpat_conv3d_bf16_wgrad_dev(const void* in, int Cin, const void* dy, int Cout
     return QPAT_OK;
 }
 
+int qpat_conv3d_set_engine(int engine) {
+    if (engine != 0 && engine != 1) return fail(QPAT_EINVAL, "qpat_conv3d_set_engine: engine must be 0 or 1");
+    unet::set_conv_engine(engine);
+    return QPAT_OK;
+}
+
+int qpat_conv3d_tc_timeouts(void) { return unet::tc_timeouts(); }
+
 int64_t qpat_conv3d_bf16_wgrad_scratch(int n, int Cin, int Cout) {
     return int64_t(unet::wgrad_chunks(n)) * 27 * Cin * Cout;
 }

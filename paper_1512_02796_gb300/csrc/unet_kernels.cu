@@ -333,9 +333,15 @@ int grid1d(int64_t n) {
 
 }  // namespace
 
+static int g_conv_engine = 0;
+void set_conv_engine(int engine) { g_conv_engine = engine; }
+int conv_engine() { return g_conv_engine; }
+
 cudaError_t conv3d_fwd(const bf16* in, int Cin, const bf16* w, const float* bias, int Cout, int relu, bf16* out,
                        float* out32, int n, cudaStream_t s) {
     if (Cin % 16 || Cout % 8 || n % 2) return cudaErrorInvalidValue;
+    if (g_conv_engine == 0 && conv3d_fwd_tc_supported(Cin, Cout))
+        return conv3d_fwd_tc(in, Cin, w, bias, Cout, relu, out, out32, n, s);
     switch (Cout / 8) {
         case 1: return conv_fwd_t<1>(in, Cin, w, bias, Cout, relu, out, out32, n, s);
         case 2: return conv_fwd_t<2>(in, Cin, w, bias, Cout, relu, out, out32, n, s);

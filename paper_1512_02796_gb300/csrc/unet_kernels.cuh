@@ -5,7 +5,9 @@
 // Activations are channels-last bf16 tensors [voxel][C] of one n^3 grid;
 // convolutions are 3x3x3 with zero padding, written as implicit GEMMs
 // (rows = voxels, columns = output channels, reduction = 27 taps x input
-// channels) on mma.sync m16n8k16 bf16 -> fp32.  Weights are stored
+// channels): the forward convolution on tcgen05.mma with a tensor-memory
+// accumulator (unet_tc.cu) where the shape allows, else mma.sync m16n8k16
+// bf16 -> fp32; the weight gradient on mma.sync.  Weights are stored
 // [tap][c_out][c_in] (c_in fastest), tap = (dz + 1) * 9 + (dy + 1) * 3 + dx + 1.
 #pragma once
 
@@ -23,6 +25,15 @@ namespace unet {
 
 cudaError_t conv3d_fwd(const __nv_bfloat16* in, int Cin, const __nv_bfloat16* w, const float* bias, int Cout,
                        int relu, __nv_bfloat16* out, float* out_f32, int n, cudaStream_t s);
+// the same convolution on tcgen05 tensor cores with a TMEM accumulator
+// (unet_tc.cu); shapes: Cin % 16 == 0, Cout % 16 == 0, 16 <= Cout <= 256
+bool conv3d_fwd_tc_supported(int Cin, int Cout);
+cudaError_t conv3d_fwd_tc(const __nv_bfloat16* in, int Cin, const __nv_bfloat16* w, const float* bias, int Cout,
+                          int relu, __nv_bfloat16* out, float* out_f32, int n, cudaStream_t s);
+int tc_timeouts();  // bounded waits of the tcgen05 kernel that gave up (device counter)
+// convolution engine: 0 = tcgen05 where the shape allows, else mma.sync; 1 = mma.sync only
+void set_conv_engine(int engine);
+int conv_engine();
 // weight gradient (fp32, [tap][c_out][c_in]) of a conv whose input was `in`
 // and whose output gradient (already masked by the ReLU) is `dy`; `partial`
 // must hold chunks(n) * 27 * Cout * Cin floats

@@ -137,6 +137,8 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
         "qpat_conv3d_bf16_wgrad_dev": (ctypes.c_int, [vp, ctypes.c_int, vp, ctypes.c_int, ctypes.c_int, vp, vp, vp,
                                                       vp]),
         "qpat_conv3d_bf16_wgrad_scratch": (ctypes.c_int64, [ctypes.c_int, ctypes.c_int, ctypes.c_int]),
+        "qpat_conv3d_set_engine": (ctypes.c_int, [ctypes.c_int]),
+        "qpat_conv3d_tc_timeouts": (ctypes.c_int, []),
         "qpat_autotune": (ctypes.c_int, [_c_double_p, ctypes.c_int64, _c_int32_p, ctypes.c_int64, _c_double_p,
                                          _c_double_p, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
                                          ctypes.POINTER(ctypes.c_int), _c_double_p, ctypes.POINTER(ctypes.c_int)]),
@@ -170,6 +172,7 @@ def exported_names() -> Sequence[str]:
         "qpat_unet_create", "qpat_unet_free", "qpat_unet_num_params", "qpat_unet_get_params", "qpat_unet_set_params",
         "qpat_unet_features_dev", "qpat_unet_predict_dev", "qpat_unet_train_dev", "qpat_unet_to_double_dev",
         "qpat_conv3d_bf16_dev", "qpat_conv3d_bf16_wgrad_dev", "qpat_conv3d_bf16_wgrad_scratch",
+        "qpat_conv3d_set_engine", "qpat_conv3d_tc_timeouts",
     ]
 
 
@@ -236,6 +239,15 @@ def qpat_unet_features_dev(mesh: Mesh, kappa, mu, flux, h: float, x):
 def qpat_unet_to_double_dev(y, out):
     _check(load().qpat_unet_to_double_dev(_tpf(y), int(y.numel()), _tp(out), _stream()))
     return out
+
+
+def qpat_conv3d_set_engine(engine: int):
+    """0: tcgen05 tensor cores where the shape allows (default); 1: mma.sync only."""
+    _check(load().qpat_conv3d_set_engine(int(engine)))
+
+
+def qpat_conv3d_tc_timeouts() -> int:
+    return int(load().qpat_conv3d_tc_timeouts())
 
 
 def qpat_conv3d_bf16_dev(x, w, bias, cout: int, relu: bool, n: int, out, out_f32=None):

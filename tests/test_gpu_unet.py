@@ -144,3 +144,29 @@ def test_training_lowers_loss_and_guess_saves_iterations():
     finally:
         net.close()
         mesh.close()
+
+
+@pytest.mark.parametrize("n,cin,cout", [(8, 16, 16), (16, 192, 64), (8, 64, 192), (16, 48, 32)])
+def test_tcgen05_and_mma_sync_engines_agree(n, cin, cout):
+    """The tcgen05 (tensor-memory accumulator) and mma.sync convolutions give
+    the same FP32 result up to summation order, and no bounded wait of the
+    tcgen05 kernel gave up."""
+    _need()
+    rng = np.random.default_rng(cin * 7 + cout)
+    x = UO.to_bf16(rng.standard_normal((n ** 3, cin)))
+    w = UO.to_bf16(rng.standard_normal((27, cout, cin)) / np.sqrt(27 * cin))
+    b = torch.tensor(rng.standard_normal(cout).astype(np.float32), device="cuda")
+    res = []
+    try:
+        for engine in (0, 1):
+            Q.qpat_conv3d_set_engine(engine)
+            out = torch.empty((n ** 3, cout), dtype=torch.bfloat16, device="cuda")
+            o32 = torch.empty((n ** 3, cout), dtype=torch.float32, device="cuda")
+            Q.qpat_conv3d_bf16_dev(_bf(x), _bf(w), b, cout, True, n, out, o32)
+            torch.cuda.synchronize()
+            res.append(o32.cpu().numpy())
+    finally:
+        Q.qpat_conv3d_set_engine(0)
+    scale = np.abs(res[1]).max()
+    assert np.abs(res[0] - res[1]).max() <= 1e-5 * scale
+    assert Q.qpat_conv3d_tc_timeouts() == 0
