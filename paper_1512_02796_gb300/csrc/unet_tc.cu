@@ -95,11 +95,11 @@ __global__ void __launch_bounds__(kTcThreads) k_conv_fwd_tc(const bf16* __restri
                                                             bf16* __restrict__ out, float* __restrict__ out32,
                                                             int n) {
     extern __shared__ __align__(128) unsigned char tc_smem[];
-    __shared__ uint64_t mbar;
+    __shared__ uint64_t mbar[2];
     __shared__ uint32_t tmem_base_s;
     __shared__ int s_ok;
-    unsigned char* sA = tc_smem;                                       // 128 x Cin bf16
-    unsigned char* sB = tc_smem + size_t(kTcRows) * Cin * 2;           // Cout x Cin bf16
+    // two stages (taps alternate): A 128 x Cin bf16, then B Cout x Cin bf16
+    const size_t a_bytes = size_t(kTcRows) * Cin * 2, stage_bytes = a_bytes + size_t(Cout) * Cin * 2;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int v0 = blockIdx.x * kTcRows;
     const int nvox = n * n * n;
@@ -111,7 +111,8 @@ __global__ void __launch_bounds__(kTcThreads) k_conv_fwd_tc(const bf16* __restri
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
     if (threadIdx.x == 0) {
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(s_addr(&mbar)) : "memory");
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(s_addr(&mbar[0])) : "memory");
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(s_addr(&mbar[1])) : "memory");
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         s_ok = 1;
     }
@@ -121,9 +122,17 @@ __global__ void __launch_bounds__(kTcThreads) k_conv_fwd_tc(const bf16* __restri
     const uint32_t tmem = tmem_base_s;
     const uint32_t idesc = instr_desc(kTcRows, Cout);
     const int kc = Cin / 8;  // 16-byte chunks per row
+    // completion of tap t's MMAs: phase (t / 2) of mbar[t % 2]
+    auto wait_tap = [&](int t) { return mbar_wait_parity(&mbar[t & 1], uint32_t((t >> 1) & 1)); };
 
     int tap = 0;
     for (; tap < 27; ++tap) {
+        unsigned char* sA = tc_smem + size_t(tap & 1) * stage_bytes;
+        unsigned char* sB = sA + a_bytes;
+        // the stage is rewritten only after the MMAs of tap - 2 have read it
+        if (tap >= 2 && !wait_tap(tap - 2)) s_ok = 0;
+        __syncthreads();
+        if (!s_ok) break;
         // ---- stage A_tap (own row: one voxel's neighbour) and B_tap
         {
             const int v = v0 + threadIdx.x;
@@ -158,18 +167,19 @@ __global__ void __launch_bounds__(kTcThreads) k_conv_fwd_tc(const bf16* __restri
                     : "memory");
             }
             asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                             s_addr(&mbar))
+                             s_addr(&mbar[tap & 1]))
                          : "memory");
         }
-        // the tile buffers are reused by the next tap only after the MMAs read them
-        if (!mbar_wait_parity(&mbar, uint32_t(tap & 1))) s_ok = 0;
-        __syncthreads();
-        if (!s_ok) break;
     }
-    if (!s_ok) {
-        // the wait of tap `tap` gave up: give its MMAs in flight one more
-        // bounded wait before TMEM is read and freed
-        mbar_wait_parity(&mbar, uint32_t(tap & 1));
+    // the last two taps' MMAs (or, after a give-up, those in flight) finish
+    // before TMEM is read and freed; each wait is bounded
+    {
+        const int last = s_ok ? 26 : tap - 1;
+        bool fin = true;
+        if (last >= 1 && !wait_tap(last - 1)) fin = false;
+        if (last >= 0 && !wait_tap(last)) fin = false;
+        if (!fin) s_ok = 0;
+        __syncthreads();
     }
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 
@@ -222,7 +232,7 @@ __global__ void __launch_bounds__(kTcThreads) k_conv_fwd_tc(const bf16* __restri
 template <int NCOLS>
 cudaError_t conv_fwd_tc_t(const bf16* in, int Cin, const bf16* w, const float* bias, int Cout, int relu, bf16* out,
                           float* out32, int n, cudaStream_t s) {
-    const size_t smem = size_t(kTcRows) * Cin * 2 + size_t(Cout) * Cin * 2;
+    const size_t smem = 2 * (size_t(kTcRows) * Cin * 2 + size_t(Cout) * Cin * 2);
     cudaError_t e = cudaFuncSetAttribute(k_conv_fwd_tc<NCOLS>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
     if (e != cudaSuccess) return e;
     const int nvox = n * n * n;
@@ -237,7 +247,7 @@ cudaError_t conv_fwd_tc_t(const bf16* in, int Cin, const bf16* w, const float* b
 bool conv3d_fwd_tc_supported(int Cin, int Cout) {
     // M = 128 needs N = Cout a multiple of 16 in [16, 256]; K steps of 16
     return Cin % 16 == 0 && Cout % 16 == 0 && Cout >= 16 && Cout <= 256 &&
-           size_t(kTcRows) * Cin * 2 + size_t(Cout) * Cin * 2 <= 200 * 1024;
+           2 * (size_t(kTcRows) * Cin * 2 + size_t(Cout) * Cin * 2) <= 200 * 1024;
 }
 
 cudaError_t conv3d_fwd_tc(const bf16* in, int Cin, const bf16* w, const float* bias, int Cout, int relu, bf16* out,
