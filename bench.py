@@ -42,11 +42,12 @@ def env_rank():
 
 
 def kernel_source_sha1() -> str:
-    """Hash of the PCG kernel sources (a stored ncu traffic figure is only
-    reported while these are unchanged)."""
+    """Hash of the PCG kernel sources and of the code that lays out their
+    operands (a stored ncu traffic figure is only reported while these are
+    unchanged)."""
     import hashlib
     h = hashlib.sha1()
-    for f in ("pcg.cu", "fem.cuh"):
+    for f in ("pcg.cu", "fem.cuh", "mesh.cpp", "kernels.cu"):
         with open(os.path.join(ROOT, "paper_1512_02796_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()
@@ -263,9 +264,9 @@ def run_ours(args):
         bpi_pair = pcg_bytes_per_iter(N, d["E"], R, 4)
     else:
         bpi_pair = pcg_asm_bytes_per_iter(N, mesh.entries, R, s_bytes, 1)
-    bpi_prior = pcg_asm_bytes_per_iter(N, mesh.entries, 2, 8, 2)
+    bpi_prior = pcg_asm_bytes_per_iter(N, mesh.prior_entries, 2, 8, 2)
     fpi_pair = pcg_asm_flops_per_iter(N, mesh.entries, R)
-    fpi_prior = pcg_asm_flops_per_iter(N, mesh.entries, 2)
+    fpi_prior = pcg_asm_flops_per_iter(N, mesh.prior_entries, 2)
     kernels = {
         "pair": {"kernel": f"k_pcg<{'float' if precision == 1 else 'double'}, {R}, "
                            f"{0 if (precision == 1 and args.fp32_operator == 0) else 2}> (J s + J^T w, {R} RHS)",

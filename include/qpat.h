@@ -139,11 +139,14 @@ int qpat_mesh_ex(const double* xyz, int64_t N, const int32_t* tets, int64_t E,
 void qpat_mesh_free(qpat_mesh_t mesh);
 
 /* Host-only preparation check (needs no GPU): builds the mesh structures of
- * qpat_mesh_ex and verifies them.  info8 receives F, patches, max touched
- * nodes per patch, max owned nodes, max tets per patch, max faces per patch,
- * total patch-tet entries (>= E; the excess is the tets duplicated on patch
- * borders) and total patch-face entries.  faces (F x 3) and perm (N) are
- * filled when not NULL.  Returns QPAT_EINVAL with a message if a check fails. */
+ * qpat_mesh_ex and verifies them.  info8 (10 entries) receives F, patches,
+ * max touched nodes per patch, max owned nodes, max tets per patch, max faces
+ * per patch, total patch-tet entries (>= E; the excess is the tets duplicated
+ * on patch borders), total patch-face entries, the stored nonzeros of the
+ * assembled K pattern and those of the prior's stiffness-only pattern (pairs
+ * with a non-zero gradient coupling in a shared tet).  faces (F x 3) and perm
+ * (N) are filled when not NULL.  Returns QPAT_EINVAL with a message if a
+ * check fails. */
 int qpat_mesh_host_info(const double* xyz, int64_t N, const int32_t* tets, int64_t E,
                         int patch_nodes, int64_t* info8, int32_t* faces, int32_t* perm);
 
@@ -170,6 +173,10 @@ int64_t qpat_mesh_num_patches(qpat_mesh_t mesh);
 /* Stored entries of the assembled operators (node pairs sharing a tet,
  * the diagonal included), without the sliced-ELLPACK padding. */
 int64_t qpat_mesh_num_entries(qpat_mesh_t mesh);
+/* Stored entries of each assembled prior block (M(u) of Eq. (14) plus
+ * delta I): the node pairs whose gradient coupling is non-zero in a shared
+ * tet, the diagonal included (7 per interior row on Kuhn meshes). */
+int64_t qpat_mesh_num_prior_entries(qpat_mesh_t mesh);
 
 /* Boundary faces in canonical order (F x 3 caller node ids, ascending). */
 int qpat_mesh_faces(qpat_mesh_t mesh, int32_t* faces);

@@ -3,6 +3,7 @@
 // prior entry points.  Algorithm 1 lives in recon.cu.
 #include <algorithm>
 #include <atomic>
+#include <set>
 #include <cmath>
 #include <cstring>
 #include <map>
@@ -192,12 +193,12 @@ int prepare_prior(qpat_mesh_s* M, const double* kt_l, const double* mt_l, double
     st.inv64 = M->ws.get<double>("opP.inv64", 2 * N, s, &e);
     st.inv32 = M->ws.get<float>("opP.inv32", 2 * N, s, &e);
     st.nv = 2;
-    st.v64[0] = M->ws.get<double>("opP.v64a", M->d.sell_entries, s, &e);
-    st.v64[1] = M->ws.get<double>("opP.v64b", M->d.sell_entries, s, &e);
+    st.v64[0] = M->ws.get<double>("opP.v64a", M->dp.sell_entries, s, &e);
+    st.v64[1] = M->ws.get<double>("opP.v64b", M->dp.sell_entries, s, &e);
     if (e != cudaSuccess) return cuda_fail(e, "workspace");
     if ((e = launch_cast_d2f(N, kt_l, st.c1_32, s)) != cudaSuccess) return cuda_fail(e, "cast");
     if ((e = launch_cast_d2f(N, mt_l, st.c2_32, s)) != cudaSuccess) return cuda_fail(e, "cast");
-    if ((e = launch_assemble_prior(M->d, kt_l, mt_l, st.inv_T2, kind, q, b_over_a, delta, st.v64[0], st.v64[1],
+    if ((e = launch_assemble_prior(M->dp, kt_l, mt_l, st.inv_T2, kind, q, b_over_a, delta, st.v64[0], st.v64[1],
                                    st.inv64, st.inv32, s)) != cudaSuccess)
         return cuda_fail(e, "assemble_prior");
     return QPAT_OK;
@@ -208,7 +209,7 @@ int prepare_prior(qpat_mesh_s* M, const double* kt_l, const double* mt_l, double
 // element recomputation is kept for FP32 only).
 static cudaError_t apply_op64(qpat_mesh_s* M, const OpState& st, int R, const double* x, double* y,
                               cudaStream_t s) {
-    return launch_apply_csr<double>(M->d, st.nv, R, st.v64[0], st.v64[1], x, y, s);
+    return launch_apply_csr<double>(st.kind == OP_PRIOR ? M->dp : M->d, st.nv, R, st.v64[0], st.v64[1], x, y, s);
 }
 
 static int pcg_status(int st, const char* what) {
@@ -231,6 +232,8 @@ int solve(qpat_mesh_s* M, const OpState& st, const SolveOpts& so_in, int R, cons
     // solve can resolve, so refinement would not contract.
     SolveOpts so = so_in;
     if (st.kind == OP_PRIOR) so.precision = 0;
+    // the prior's assembled blocks live in the stiffness-only pattern
+    const MeshDev& md = st.kind == OP_PRIOR ? M->dp : M->d;
     const int64_t N = M->h.N;
     const int64_t n = N * R;
     cudaError_t e = cudaSuccess;
@@ -297,11 +300,11 @@ int solve(qpat_mesh_s* M, const OpState& st, const SolveOpts& so_in, int R, cons
         OpParams<double> op{st.c1_64, st.c2_64, st.inv_T2, st.scale1, st.delta, 1, st.v64[0], st.v64[1]};
         if (M->timing) cudaEventRecord(M->ev0, s);
         e = cudaErrorNotSupported;
-        if (ring) e = launch_pcg_ring<double>(M->d, OP, R, op, st.inv64, w, so.rtol, so.maxit, s, nullptr);
+        if (ring) e = launch_pcg_ring<double>(md, OP, R, op, st.inv64, w, so.rtol, so.maxit, s, nullptr);
         if (e == cudaErrorNotSupported) {
             if (so.pcg_variant == 3) return fail(QPAT_EINVAL, "pcg: the bulk-copy ring does not fit this mesh");
-            e = single ? launch_pcg1<double>(M->d, OP, R, op, st.inv64, w, so.rtol, so.maxit, s, nullptr)
-                       : launch_pcg<double>(M->d, OP, R, op, st.inv64, w, so.rtol, so.maxit, s, nullptr);
+            e = single ? launch_pcg1<double>(md, OP, R, op, st.inv64, w, so.rtol, so.maxit, s, nullptr)
+                       : launch_pcg<double>(md, OP, R, op, st.inv64, w, so.rtol, so.maxit, s, nullptr);
         }
         if (e != cudaSuccess) return cuda_fail(e, "pcg launch");
         if (M->timing) cudaEventRecord(M->ev1, s);
@@ -507,7 +510,7 @@ static int mesh_create(const double* xyz, int64_t N, const int32_t* tets, int64_
 }
 
 int qpat_mesh_host_info(const double* xyz, int64_t N, const int32_t* tets, int64_t E, int patch_nodes,
-                        int64_t* info8, int32_t* faces, int32_t* perm) {
+                        int64_t* info8, int32_t* faces, int32_t* perm) {  // info8: 10 entries
     if (!info8) return fail(QPAT_EINVAL, "qpat_mesh_host_info: info is NULL");
     HostMesh h;
     std::string msg = build_host_mesh(xyz, N, tets, E, patch_nodes, 0, h);
@@ -546,6 +549,35 @@ int qpat_mesh_host_info(const double* xyz, int64_t N, const int32_t* tets, int64
     info8[5] = h.max_pfaces;
     info8[6] = dup;  // sum over patches of listed tets (>= E; the excess is border duplication)
     info8[7] = int64_t(h.face_ptr[h.P]);
+    // the prior's stiffness-only pattern: a subset of the full pattern, with
+    // every diagonal, symmetric in global ids
+    {
+        std::set<std::pair<int, int>> full, sub;
+        int64_t nfull = 0, nsub = 0;
+        for (int p = 0; p < h.P; ++p) {
+            const int nb = h.node_ptr[p];
+            for (int g = h.own_begin[p]; g < h.own_begin[p + 1]; ++g) {
+                const int64_t b0 = h.sell_ptr[g >> 5] * 32 + (g & 31), b1 = h.psell_ptr[g >> 5] * 32 + (g & 31);
+                for (int k = 0; k < h.sell_len[g]; ++k) full.insert({g, h.nodes[nb + h.sell_col[b0 + int64_t(k) * 32]]});
+                bool diag = false;
+                for (int k = 0; k < h.psell_len[g]; ++k) {
+                    const int j = h.nodes[nb + h.psell_col[b1 + int64_t(k) * 32]];
+                    sub.insert({g, j});
+                    diag |= j == g;
+                }
+                if (!diag || h.psell_col[b1 + int64_t(h.psell_diag[g]) * 32] != g - h.own_begin[p])
+                    return fail(QPAT_EINVAL, "host check: stiffness pattern diagonal");
+                nfull += h.sell_len[g];
+                nsub += h.psell_len[g];
+            }
+        }
+        for (const auto& e : sub) {
+            if (!full.count(e)) return fail(QPAT_EINVAL, "host check: stiffness pattern not a subset");
+            if (!sub.count({e.second, e.first})) return fail(QPAT_EINVAL, "host check: stiffness pattern not symmetric");
+        }
+        info8[8] = nfull;
+        info8[9] = nsub;
+    }
     if (faces) std::memcpy(faces, h.faces_caller.data(), sizeof(int32_t) * 3 * h.F);
     if (perm) std::memcpy(perm, h.perm.data(), sizeof(int32_t) * h.N);
     // every tet must be listed once per distinct patch owning one of its
@@ -621,6 +653,13 @@ int64_t qpat_mesh_num_entries(qpat_mesh_t M) {
     if (!M) return -1;
     int64_t n = 0;
     for (uint8_t l : M->h.sell_len) n += l;
+    return n;
+}
+
+int64_t qpat_mesh_num_prior_entries(qpat_mesh_t M) {
+    if (!M) return -1;
+    int64_t n = 0;
+    for (uint8_t l : M->h.psell_len) n += l;
     return n;
 }
 

@@ -76,6 +76,7 @@ struct DeviceGuard {
 struct qpat_mesh_s {
     qpat::HostMesh h;
     qpat::MeshDev d{};
+    qpat::MeshDev dp{};  // d with the stiffness-only pattern of the prior operators (psell)
     std::vector<void*> dev_allocs;
     int device = 0;
     cudaStream_t stream = nullptr;   // used by the host-pointer entry points

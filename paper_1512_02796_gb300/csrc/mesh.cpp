@@ -182,7 +182,8 @@ std::string build_host_mesh(const double* xyz, int64_t N, const int32_t* tets,
     m.face_ptr.assign(1, 0);
     std::vector<int32_t> tet_stamp(E, -1), face_stamp(m.F, -1), node_local(N, -1);
     std::vector<int32_t> ptets, pfaces, halo;
-    std::vector<std::vector<uint16_t>> rows(N);  // local column ids of every row
+    std::vector<std::vector<uint16_t>> rows(N);   // local column ids of every row
+    std::vector<std::vector<uint16_t>> srows(N);  // the subset with a non-zero gradient coupling
     for (int p = 0; p < P; ++p) {
         const int32_t b = m.own_begin[p], e = m.own_begin[p + 1];
         const int nown = e - b;
@@ -226,15 +227,42 @@ std::string build_host_mesh(const double* xyz, int64_t N, const int32_t* tets,
                 lv[k] = node_local[m.tets[4 * t + k]];
                 m.tet_loc.push_back(uint16_t(lv[k]));
             }
+            // gradient couplings of the tet: cofactor vectors c_k (grad lambda_k
+            // times the determinant); a pair couples in a stiffness operator iff
+            // c_a . c_b is not zero up to rounding
+            double cof[4][3];
+            {
+                const double* q0 = &m.xyz[3 * m.tets[4 * t]];
+                double ed[3][3];
+                for (int k = 1; k < 4; ++k)
+                    for (int d = 0; d < 3; ++d) ed[k - 1][d] = m.xyz[3 * m.tets[4 * t + k] + d] - q0[d];
+                auto cross = [](const double* x, const double* y, double* z) {
+                    z[0] = x[1] * y[2] - x[2] * y[1];
+                    z[1] = x[2] * y[0] - x[0] * y[2];
+                    z[2] = x[0] * y[1] - x[1] * y[0];
+                };
+                cross(ed[1], ed[2], cof[1]);
+                cross(ed[2], ed[0], cof[2]);
+                cross(ed[0], ed[1], cof[3]);
+                for (int d = 0; d < 3; ++d) cof[0][d] = -(cof[1][d] + cof[2][d] + cof[3][d]);
+            }
             for (int a = 0; a < 4; ++a)
                 if (lv[a] < nown)
-                    for (int c = 0; c < 4; ++c) rows[b + lv[a]].push_back(uint16_t(lv[c]));
+                    for (int c = 0; c < 4; ++c) {
+                        rows[b + lv[a]].push_back(uint16_t(lv[c]));
+                        const double dot = cof[a][0] * cof[c][0] + cof[a][1] * cof[c][1] + cof[a][2] * cof[c][2];
+                        const double na = std::sqrt(cof[a][0] * cof[a][0] + cof[a][1] * cof[a][1] + cof[a][2] * cof[a][2]);
+                        const double nc = std::sqrt(cof[c][0] * cof[c][0] + cof[c][1] * cof[c][1] + cof[c][2] * cof[c][2]);
+                        if (a == c || std::fabs(dot) > 1e-12 * na * nc) srows[b + lv[a]].push_back(uint16_t(lv[c]));
+                    }
         }
         for (int32_t g = b; g < e; ++g) {
-            auto& r = rows[g];
-            std::sort(r.begin(), r.end());
-            r.erase(std::unique(r.begin(), r.end()), r.end());
-            if (r.size() > 255) return "qpat_mesh: a node has more than 254 neighbours";
+            for (auto* rp : {&rows[g], &srows[g]}) {
+                auto& r = *rp;
+                std::sort(r.begin(), r.end());
+                r.erase(std::unique(r.begin(), r.end()), r.end());
+            }
+            if (rows[g].size() > 255) return "qpat_mesh: a node has more than 254 neighbours";
         }
         for (int32_t f : pfaces) {
             for (int k = 0; k < 3; ++k) m.face_loc.push_back(uint16_t(node_local[m.faces_lib[3 * f + k]]));
@@ -252,38 +280,47 @@ std::string build_host_mesh(const double* xyz, int64_t N, const int32_t* tets,
         for (int32_t g : halo) node_local[g] = -1;
     }
 
-    // ---- sliced ELLPACK pattern (slices never straddle patches: patch_nodes % 32 == 0)
+    // ---- sliced ELLPACK patterns (slices never straddle patches: patch_nodes % 32 == 0)
     m.nslices = (N + 31) / 32;
-    m.sell_ptr.assign(m.nslices + 1, 0);
-    m.sell_len.assign(size_t(32) * m.nslices, 0);
-    m.sell_diag.resize(N);
-    for (int64_t s = 0; s < m.nslices; ++s) {
-        size_t w = 0;
-        for (int64_t g = 32 * s; g < std::min<int64_t>(N, 32 * s + 32); ++g) w = std::max(w, rows[g].size());
-        m.sell_ptr[s + 1] = m.sell_ptr[s] + int64_t(w);
-        m.sell_wmax = std::max(m.sell_wmax, int(w));
-    }
-    m.sell_col.assign(size_t(32) * m.sell_ptr[m.nslices], 0);
-    for (int64_t s = 0; s < m.nslices; ++s) {
-        const int64_t w = m.sell_ptr[s + 1] - m.sell_ptr[s];
-        for (int lane = 0; lane < 32; ++lane) {
-            const int64_t g = 32 * s + lane;
-            uint16_t self = 0;
-            if (g < N) {
-                const int p = m.patch_of_slice[g >> 5];
-                self = uint16_t(g - m.own_begin[p]);
-                m.sell_len[g] = uint8_t(rows[g].size());
-                m.sell_diag[g] = -1;
-            }
-            for (int64_t k = 0; k < w; ++k) {
-                uint16_t c = self;
-                if (g < N && k < int64_t(rows[g].size())) c = rows[g][k];
-                m.sell_col[(m.sell_ptr[s] + k) * 32 + lane] = c;
-                if (g < N && k < int64_t(rows[g].size()) && c == self) m.sell_diag[g] = int32_t(k);
-            }
-            if (g < N && m.sell_diag[g] < 0) return "qpat_mesh: a node belongs to no tetrahedron";
+    auto build_sell = [&](const std::vector<std::vector<uint16_t>>& rr, std::vector<int64_t>& ptr,
+                          std::vector<uint16_t>& col, std::vector<uint8_t>& len, std::vector<int32_t>& diag,
+                          int& wmax) -> const char* {
+        ptr.assign(m.nslices + 1, 0);
+        len.assign(size_t(32) * m.nslices, 0);
+        diag.resize(N);
+        wmax = 0;
+        for (int64_t s = 0; s < m.nslices; ++s) {
+            size_t w = 0;
+            for (int64_t g = 32 * s; g < std::min<int64_t>(N, 32 * s + 32); ++g) w = std::max(w, rr[g].size());
+            ptr[s + 1] = ptr[s] + int64_t(w);
+            wmax = std::max(wmax, int(w));
         }
-    }
+        col.assign(size_t(32) * ptr[m.nslices], 0);
+        for (int64_t s = 0; s < m.nslices; ++s) {
+            const int64_t w = ptr[s + 1] - ptr[s];
+            for (int lane = 0; lane < 32; ++lane) {
+                const int64_t g = 32 * s + lane;
+                uint16_t self = 0;
+                if (g < N) {
+                    const int p = m.patch_of_slice[g >> 5];
+                    self = uint16_t(g - m.own_begin[p]);
+                    len[g] = uint8_t(rr[g].size());
+                    diag[g] = -1;
+                }
+                for (int64_t k = 0; k < w; ++k) {
+                    uint16_t c = self;
+                    if (g < N && k < int64_t(rr[g].size())) c = rr[g][k];
+                    col[(ptr[s] + k) * 32 + lane] = c;
+                    if (g < N && k < int64_t(rr[g].size()) && c == self) diag[g] = int32_t(k);
+                }
+                if (g < N && diag[g] < 0) return "qpat_mesh: a node belongs to no tetrahedron";
+            }
+        }
+        return nullptr;
+    };
+    if (const char* err = build_sell(rows, m.sell_ptr, m.sell_col, m.sell_len, m.sell_diag, m.sell_wmax)) return err;
+    if (const char* err = build_sell(srows, m.psell_ptr, m.psell_col, m.psell_len, m.psell_diag, m.psell_wmax))
+        return err;
     return "";
 }
 

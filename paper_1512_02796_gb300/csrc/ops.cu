@@ -127,6 +127,14 @@ int upload_mesh(qpat_mesh_s* M) {
     const uint16_t* fl = nullptr;
     if ((rc = up(M, h.face_loc, &fl))) return rc;
     d.face_loc = reinterpret_cast<const ushort4*>(fl);
+    // the prior's view: everything as d, but the stiffness-only pattern
+    MeshDev& dp = M->dp;
+    dp = d;
+    if ((rc = up(M, h.psell_ptr, &dp.sell_ptr)) || (rc = up(M, h.psell_col, &dp.sell_col)) ||
+        (rc = up(M, h.psell_len, &dp.sell_len)) || (rc = up(M, h.psell_diag, &dp.sell_diag)))
+        return rc;
+    dp.sell_entries = int64_t(h.psell_col.size());
+    dp.sell_wmax = h.psell_wmax;
     if ((e = cudaStreamCreateWithFlags(&M->stream, cudaStreamNonBlocking)) != cudaSuccess)
         return cuda_fail(e, "qpat_mesh: stream");
     if ((e = cudaMallocHost(&M->host_scratch, 256 * sizeof(double))) != cudaSuccess)

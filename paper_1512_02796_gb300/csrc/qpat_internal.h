@@ -56,6 +56,16 @@ struct HostMesh {
     std::vector<uint8_t> sell_len;      // row lengths (32 * nslices; 0 past row N - 1)
     std::vector<int32_t> sell_diag;     // k of the diagonal entry of each row (N)
     int sell_wmax = 0;                  // widest slice (entries per row)
+    // The same layout for the pure stiffness operators of the prior
+    // (M(u), Eq. (14)): only pairs whose gradient coupling grad(lambda_a) .
+    // grad(lambda_b) is non-zero in some tet they share.  On Kuhn meshes the
+    // face- and body-diagonal edges couple with exactly zero (7 of the 15
+    // entries per row remain); on general meshes the pattern equals the full one.
+    std::vector<int64_t> psell_ptr;
+    std::vector<uint16_t> psell_col;
+    std::vector<uint8_t> psell_len;
+    std::vector<int32_t> psell_diag;
+    int psell_wmax = 0;
 };
 
 // Builds a HostMesh; returns "" on success or an error message.

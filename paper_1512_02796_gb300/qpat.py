@@ -85,6 +85,7 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
         "qpat_mesh_num_faces": (ctypes.c_int64, [vp]),
         "qpat_mesh_num_patches": (ctypes.c_int64, [vp]),
         "qpat_mesh_num_entries": (ctypes.c_int64, [vp]),
+        "qpat_mesh_num_prior_entries": (ctypes.c_int64, [vp]),
         "qpat_mesh_faces": (ctypes.c_int, [vp, _c_int32_p]),
         "qpat_mesh_permutation": (ctypes.c_int, [vp, _c_int32_p]),
         "qpat_mesh_stats": (ctypes.c_int, [vp, _c_int64_p]),
@@ -159,7 +160,7 @@ def exported_names() -> Sequence[str]:
     return [
         "qpat_default_params", "qpat_last_error", "qpat_launch_count", "qpat_mesh", "qpat_mesh_ex", "qpat_mesh_free",
         "qpat_mesh_host_info", "qpat_mesh_num_nodes", "qpat_mesh_num_tets", "qpat_mesh_num_faces", "qpat_mesh_num_patches",
-        "qpat_mesh_num_entries",
+        "qpat_mesh_num_entries", "qpat_mesh_num_prior_entries",
         "qpat_mesh_faces", "qpat_mesh_permutation", "qpat_mesh_stats", "qpat_mesh_fp64_fallbacks",
         "qpat_mesh_reset_stats",
         "qpat_mesh_set_timing", "qpat_mesh_pcg_time",
@@ -333,6 +334,7 @@ class Mesh:
         self.F = int(lib.qpat_mesh_num_faces(h))
         self.P = int(lib.qpat_mesh_num_patches(h))
         self.entries = int(lib.qpat_mesh_num_entries(h))
+        self.prior_entries = int(lib.qpat_mesh_num_prior_entries(h))
 
     def close(self):
         if getattr(self, "handle", None):
@@ -383,7 +385,7 @@ def qpat_mesh_host_info(xyz, tets, patch_nodes: int = 512):
     """Host-only mesh preparation check; returns (info dict, faces, perm)."""
     xyz = _f64(xyz)
     tets = np.ascontiguousarray(tets, dtype=np.int32)
-    info = np.zeros(8, dtype=np.int64)
+    info = np.zeros(10, dtype=np.int64)
     lib = load()
     # first call sizes the face array
     _check(lib.qpat_mesh_host_info(_dp(xyz), xyz.shape[0], tets.ctypes.data_as(_c_int32_p), tets.shape[0],
@@ -393,7 +395,8 @@ def qpat_mesh_host_info(xyz, tets, patch_nodes: int = 512):
     _check(lib.qpat_mesh_host_info(_dp(xyz), xyz.shape[0], tets.ctypes.data_as(_c_int32_p), tets.shape[0],
                                    patch_nodes, info.ctypes.data_as(_c_int64_p), faces.ctypes.data_as(_c_int32_p),
                                    perm.ctypes.data_as(_c_int32_p)))
-    keys = ["F", "P", "max_touched", "max_own", "max_ptets", "max_pfaces", "patch_tets", "patch_faces"]
+    keys = ["F", "P", "max_touched", "max_own", "max_ptets", "max_pfaces", "patch_tets", "patch_faces",
+            "nnz", "prior_nnz"]
     return dict(zip(keys, (int(v) for v in info))), faces, perm
 
 
