@@ -26,6 +26,7 @@ __all__ = [
     "spheres_phantom", "blob_phantom", "config", "noise_draws",
     "random_vector", "kappa_from_optics", "CONFIG_NAMES",
     "cylinder_mesh", "SideIllumination", "CylinderConfig", "cylinder_config",
+    "wavelength_optics",
 ]
 
 
@@ -399,3 +400,24 @@ def cylinder_config(n: int, nz: int, R: float, H: float, K: int, seed: int) -> C
                               mus=2.0 if i == 0 else None))
     ill = [SideIllumination(theta0=(k % 4) * np.pi / 2) for k in range(K)]
     return CylinderConfig(f"cyl{n}x{nz}_K{K}", n, nz, R, H, ill, spheres, seed=seed)
+
+
+# ------------------------------------------------------------------ several wavelengths
+
+def wavelength_optics(cfg, xyz: np.ndarray, wavelengths_nm: Sequence[float], seed: int = 0):
+    """Nodal (kappa, mu) of the phantom at several wavelengths (the paper's
+    remark that the extension to multiple wavelengths is straightforward):
+    absorption mu_a(x) scaled by a seeded smooth spectrum per wavelength
+    (factors in [0.5, 1.5]), reduced scattering mu_s'(x) following the
+    usual power law (lambda / 800 nm)^(-1.2).  Returns a list of (kappa, mu)
+    pairs, one per wavelength."""
+    rng = np.random.default_rng(seed)
+    mua, mus = cfg.optics(xyz)
+    c = rng.uniform(0.0, 2 * np.pi, size=2)
+    out = []
+    for lam in wavelengths_nm:
+        a = 1.0 + 0.5 * np.sin(c[0] + lam / 60.0) * np.cos(c[1] + lam / 170.0)
+        s = (lam / 800.0) ** (-1.2)
+        mua_l, mus_l = mua * a, mus * s
+        out.append((kappa_from_optics(mua_l, mus_l), mua_l))
+    return out

@@ -65,3 +65,41 @@ def test_autotune_picks_a_measured_candidate():
     finite = {k: v for k, v in table.items() if np.isfinite(v)}
     assert len(finite) >= 6
     assert (pn, op) in finite and finite[(pn, op)] == min(finite.values())
+
+
+def test_several_wavelengths_on_one_mesh_in_one_launch():
+    """Several wavelengths (independent optical problems on one mesh, the
+    paper's straightforward extension) as one batched launch: the same mesh
+    handle once per wavelength, each solve equal to its own FP64 forward and,
+    for one wavelength, to the oracle."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    cfg = S.small_config(12, 20.0, 3, 41)
+    xyz, tets = cfg.mesh()
+    lams = [700.0, 760.0, 830.0, 900.0]
+    optics = S.wavelength_optics(cfg, xyz, lams, seed=5)
+    m = Q.qpat_mesh(xyz, tets, patch_nodes=64)
+    flux = np.stack([Q.qpat_flux_patch(m, p.center, p.normal, p.half_w, p.amp) for p in cfg.patches])
+    batch = Q.qpat_batch_create([m] * len(lams), [cfg.K] * len(lams))
+    try:
+        for j, (kap, mu) in enumerate(optics):
+            k, m_, f = batch.inputs(j)
+            k.copy_(torch.tensor(kap))
+            m_.copy_(torch.tensor(mu))
+            f.copy_(torch.tensor(flux))
+        batch.forward()
+        torch.cuda.synchronize()
+        st, _, _ = batch.status()
+        assert all(s == 0 for s in st), st
+        phis = [batch.phi(j).cpu().numpy() for j in range(len(lams))]
+        for j, (kap, mu) in enumerate(optics):
+            ref, _ = Q.qpat_forward(m, kap, mu, flux)
+            assert rel(phis[j], ref) < 1e-10
+        om = O.Mesh(xyz, tets)
+        phi_o, _ = O.forward(om, optics[2][0], optics[2][1], flux)
+        assert rel(phis[2], phi_o) < 1e-10
+        # the wavelengths really differ
+        assert rel(phis[0], phis[3]) > 1e-3
+    finally:
+        batch.close()
+        m.close()
