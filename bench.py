@@ -129,14 +129,20 @@ def pcg_asm_bytes_per_iter(N: int, entries: int, R: int, s: int, nv: int) -> flo
     return entries * (nv * s + 2.0) + nv * s * N + 6.0 * s * R * N
 
 
-def pcg_asm_flops_per_iter(N: int, entries: int, R: int) -> float:
+def pcg_asm_flops_per_iter(N: int, entries: int, R: int, deg: int = 0, local_entries: int = 0) -> float:
     """Algorithmic floating-point operations of one PCG iteration with an
     assembled operator of `entries` stored nonzeros per value set, R
     right-hand sides (for the two-block prior R = 2, one value set each):
     2 per nonzero per RHS for q = A p, and per node per RHS 13 for the vector
     work (z = D^-1 r: 1; p = z + beta p, x += alpha p, r -= alpha q: 2 each;
-    the dot products p.q, r.z, r.r: 2 each)."""
-    return 2.0 * entries * R + 13.0 * R * N
+    the dot products p.q, r.z, r.r: 2 each).  A patch-local Chebyshev
+    preconditioner of degree deg adds per RHS one scaling a_deg v (1 per
+    node) and deg Horner steps w = a_j v + D^-1 (A_pp w): 2 per local
+    nonzero and 3 per node."""
+    f = 2.0 * entries * R + 13.0 * R * N
+    if deg > 0:
+        f += R * N + deg * (2.0 * local_entries * R + 3.0 * R * N)
+    return f
 
 
 def fp64_peak_tflops(sm_mhz: float, nsm: int) -> float:
@@ -188,6 +194,10 @@ def run_ours(args):
     torch.cuda.set_device(local)
     precision = 1 if args.precision == "mixed" else 0
     prm = Q.qpat_default_params(precision=precision, fp32_operator=args.fp32_operator)
+    if args.poly is not None:
+        prm.poly_degree = args.poly
+    if args.prior_poly is not None:
+        prm.prior_poly_degree = args.prior_poly
     d = setup_problem(Q, torch, precision)
     mesh = d["mesh"]
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")  # 256 MB > L2
@@ -265,14 +275,18 @@ def run_ours(args):
     else:
         bpi_pair = pcg_asm_bytes_per_iter(N, mesh.entries, R, s_bytes, 1)
     bpi_prior = pcg_asm_bytes_per_iter(N, mesh.prior_entries, 2, 8, 2)
-    fpi_pair = pcg_asm_flops_per_iter(N, mesh.entries, R)
-    fpi_prior = pcg_asm_flops_per_iter(N, mesh.prior_entries, 2)
+    pair_deg = prm.poly_degree if (precision == 0 or args.fp32_operator == 1) else 0
+    fpi_pair = pcg_asm_flops_per_iter(N, mesh.entries, R, pair_deg, mesh.local_entries)
+    fpi_prior = pcg_asm_flops_per_iter(N, mesh.prior_entries, 2, prm.prior_poly_degree, mesh.prior_local_entries)
     kernels = {
         "pair": {"kernel": f"k_pcg<{'float' if precision == 1 else 'double'}, {R}, "
-                           f"{0 if (precision == 1 and args.fp32_operator == 0) else 2}> (J s + J^T w, {R} RHS)",
+                           f"{0 if (precision == 1 and args.fp32_operator == 0) else 2}"
+                           f"{', true' if pair_deg else ''}> (J s + J^T w, {R} RHS"
+                           f"{f', degree-{pair_deg} patch-local Chebyshev' if pair_deg else ', Jacobi'})",
                  "ms": pair_ms, "iters": pair_iters, "launches": pair_launches, "bytes_per_iter": bpi_pair,
                  "flops_per_iter": fpi_pair, "arith": "fp32" if precision == 1 else "fp64"},
-        "prior": {"kernel": "k_pcg<double, 2, 3> (M_delta^-1, two blocks)",
+        "prior": {"kernel": f"k_pcg<double, 2, 3{', true' if prm.prior_poly_degree else ''}> (M_delta^-1, two blocks"
+                            f"{f', degree-{prm.prior_poly_degree} patch-local Chebyshev' if prm.prior_poly_degree else ', Jacobi'})",
                   "ms": prior_ms, "iters": prior_iters, "launches": prior_launches, "bytes_per_iter": bpi_prior,
                   "flops_per_iter": fpi_prior, "arith": "fp64"},
     }
@@ -322,6 +336,9 @@ def run_ours(args):
         "dtype": "f32+f64-refine" if precision == 1 else "f64", "data": "synthetic",
         "config": {"workload": WORKLOAD, "nodes": N, "tets": d["E"], "illuminations": K,
                    "pair_rhs": R, "precision": args.precision, "pcg_rtol": prm.pcg_rtol,
+                   "preconditioner": {"K": f"patch-local Chebyshev, degree {pair_deg}" if pair_deg else "Jacobi",
+                                      "M_delta": (f"patch-local Chebyshev, degree {prm.prior_poly_degree}"
+                                                  if prm.prior_poly_degree else "Jacobi")},
                    "l2": "flushed between steps (256 MB write outside the per-step events)",
                    "parallelism": "replicas" if world > 1 else "single"},
         "e2e": {"value": e2e_steps / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
@@ -353,7 +370,7 @@ def run_ours(args):
 def uneven_batch_leg(Q, torch, reps: int = 5):
     """32 forward problems on cubes of 16^3-48^3 nodes with 1-4 illuminations:
     one batched cooperative launch replayed as a CUDA graph, against the same
-    solves issued one mesh after the other (FP64, rtol 1e-13 both)."""
+    solves issued one mesh after the other (FP64, rtol 1e-13, Jacobi both)."""
     cfgs = S.uneven_batch(32)
     meshes, ins = [], []
     for cfg in cfgs:
@@ -363,7 +380,10 @@ def uneven_batch_leg(Q, torch, reps: int = 5):
         flux = np.stack([Q.qpat_flux_patch(m, p.center, p.normal, p.half_w, p.amp) for p in cfg.patches])
         meshes.append(m)
         ins.append(tuple(torch.tensor(a, device="cuda") for a in (kap, mu, flux)))
-    batch = Q.qpat_batch_create(meshes, [c.K for c in cfgs])
+    # Jacobi on both sides: on these small meshes (256-node patches, many per
+    # CTA) the patch-local sweeps cost more than the iterations they save
+    p0 = Q.qpat_default_params(precision=0, poly_degree=0)
+    batch = Q.qpat_batch_create(meshes, [c.K for c in cfgs], p0)
     for j, (k, mu, f) in enumerate(ins):
         bk, bm, bf = batch.inputs(j)
         bk.copy_(k)
@@ -381,7 +401,6 @@ def uneven_batch_leg(Q, torch, reps: int = 5):
     st, it, ct = batch.status()
     outs = [torch.empty((c.K, m.N), dtype=torch.float64, device="cuda") for c, m in zip(cfgs, meshes)]
     hs = [torch.empty_like(o) for o in outs]
-    p0 = Q.qpat_default_params(precision=0)
     for j, (k, mu, f) in enumerate(ins):
         Q.qpat_forward_dev(meshes[j], k, mu, f, outs[j], hs[j], p0)
     torch.cuda.synchronize()
@@ -645,6 +664,10 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--poly", type=int, default=None,
+                    help="degree of the patch-local Chebyshev preconditioner of the K solves (library default)")
+    ap.add_argument("--prior-poly", type=int, default=None,
+                    help="the same for the M_delta solves (library default)")
     ap.add_argument("--fp32-operator", type=int, default=1, choices=[0, 1],
                     help="FP32 inner operator: 0 matrix-free elements, 1 assembled values")
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")

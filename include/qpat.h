@@ -93,7 +93,18 @@ typedef struct {
                               continues the previous search direction, rescaled,
                               after r is replaced by the true FP64 residual);
                               1 = restart the inner PCG at every refinement sweep */
-    int reserved[3];
+    int poly_degree;       /* preconditioner of the K solves on assembled operators
+                              with pcg_variant 0/1: 0 = Jacobi (D^-1); 1..8 = block
+                              Jacobi over the CTA patches, each block's inverse
+                              approximated by a Chebyshev polynomial of this degree
+                              in D^-1 A_pp (A_pp: the couplings among the patch's
+                              owned nodes), on [hi / 50, hi] with hi the Gershgorin
+                              bound of D^-1 A.  A fixed symmetric positive definite
+                              operator, so PCG converges to the same solution in
+                              fewer (and costlier) iterations.  Other variants and
+                              the matrix-free FP32 operator use Jacobi.  Default 2. */
+    int prior_poly_degree; /* the same for the M_delta solves (default 2) */
+    int reserved[1];
     double prior_q;        /* q of prior 1, in (0, 2] */
 } qpat_params;
 
@@ -177,6 +188,12 @@ int64_t qpat_mesh_num_entries(qpat_mesh_t mesh);
  * delta I): the node pairs whose gradient coupling is non-zero in a shared
  * tet, the diagonal included (7 per interior row on Kuhn meshes). */
 int64_t qpat_mesh_num_prior_entries(qpat_mesh_t mesh);
+
+/* Stored nonzeros that couple two nodes owned by the same patch, in the K
+ * pattern (prior = 0) or the prior pattern (prior = 1): the entries the
+ * patch-local Chebyshev preconditioner applies (poly_degree).  -1 if mesh
+ * is NULL. */
+int64_t qpat_mesh_num_local_entries(qpat_mesh_t mesh, int prior);
 
 /* Boundary faces in canonical order (F x 3 caller node ids, ascending). */
 int qpat_mesh_faces(qpat_mesh_t mesh, int32_t* faces);
@@ -375,7 +392,8 @@ int qpat_autotune(const double* xyz, int64_t N, const int32_t* tets, int64_t E,
  * sequence (layout changes, assembly of K, load vectors, the batched PCG,
  * the output layout) is recorded into a CUDA graph on the first
  * qpat_batch_forward and replayed afterwards.  Illuminations are padded to
- * a common R = K_max rounded up to 1, 2, 4 or 8 (K_j <= 8).  Stacked
+ * a common R = K_max rounded up to 1, 2, 4 or 8 (K_j <= 8).  FP64 PCG to
+ * pcg_rtol with prm->poly_degree's preconditioner (Jacobi if 0).  Stacked
  * illuminations follow Sec. 4; the solve is the Appendix's K^-1 f.
  * Ownership: the batch allocates (at creation) and owns per problem j the
  * device buffers kappa_j, mu_j (N_j), flux_j (K_j x F_j, canonical faces)

@@ -165,10 +165,11 @@ int prepare_K(qpat_mesh_s* M, const double* kap_l, const double* mu_l, OpState& 
     st.nv = 1;
     st.v64[0] = M->ws.get<double>(t + ".v64", M->d.sell_entries, s, &e);
     st.v32[0] = M->ws.get<float>(t + ".v32", M->d.sell_entries, s, &e);
+    st.gbound = M->ws.get<double>(t + ".gb", 1, s, &e);
     if (e != cudaSuccess) return cuda_fail(e, "workspace");
     if ((e = launch_cast_d2f(N, kap_l, st.c1_32, s)) != cudaSuccess) return cuda_fail(e, "cast");
     if ((e = launch_cast_d2f(N, mu_l, st.c2_32, s)) != cudaSuccess) return cuda_fail(e, "cast");
-    if ((e = launch_assemble_K(M->d, kap_l, mu_l, st.v64[0], st.inv64, st.inv32, s)) != cudaSuccess)
+    if ((e = launch_assemble_K(M->d, kap_l, mu_l, st.v64[0], st.inv64, st.inv32, s, st.gbound)) != cudaSuccess)
         return cuda_fail(e, "assemble_K");
     if ((e = launch_cast_vals(M->d.sell_entries, st.v64[0], st.v32[0], s)) != cudaSuccess)
         return cuda_fail(e, "cast");
@@ -195,11 +196,12 @@ int prepare_prior(qpat_mesh_s* M, const double* kt_l, const double* mt_l, double
     st.nv = 2;
     st.v64[0] = M->ws.get<double>("opP.v64a", M->dp.sell_entries, s, &e);
     st.v64[1] = M->ws.get<double>("opP.v64b", M->dp.sell_entries, s, &e);
+    st.gbound = M->ws.get<double>("opP.gb", 1, s, &e);
     if (e != cudaSuccess) return cuda_fail(e, "workspace");
     if ((e = launch_cast_d2f(N, kt_l, st.c1_32, s)) != cudaSuccess) return cuda_fail(e, "cast");
     if ((e = launch_cast_d2f(N, mt_l, st.c2_32, s)) != cudaSuccess) return cuda_fail(e, "cast");
     if ((e = launch_assemble_prior(M->dp, kt_l, mt_l, st.inv_T2, kind, q, b_over_a, delta, st.v64[0], st.v64[1],
-                                   st.inv64, st.inv32, s)) != cudaSuccess)
+                                   st.inv64, st.inv32, s, st.gbound)) != cudaSuccess)
         return cuda_fail(e, "assemble_prior");
     return QPAT_OK;
 }
@@ -254,6 +256,11 @@ int solve(qpat_mesh_s* M, const OpState& st, const SolveOpts& so_in, int R, cons
     const bool assembled = so.precision == 0 || so.fp32_assembled;
     const bool single = assembled && so.pcg_variant == 2;
     const bool ring = assembled && so.pcg_variant == 3;
+    // patch-local Chebyshev preconditioner: two-reduction kernel, assembled values
+    if (assembled && !single && !ring && st.gbound) {
+        w.poly_deg = st.kind == OP_PRIOR ? so.poly_prior : so.poly_k;
+        w.poly_hi = st.gbound;
+    }
     if (single) {
         w.r1 = M->ws.get_bytes(nm("r1"), n * esz, s, &e);
         w.s0 = M->ws.get_bytes(nm("s0"), n * esz, s, &e);
@@ -337,6 +344,11 @@ int solve(qpat_mesh_s* M, const OpState& st, const SolveOpts& so_in, int R, cons
         if (e != cudaSuccess) return cuda_fail(e, "workspace");
         w.b = b32;
         w.x = x32;
+        if (w.poly_deg > 0) {
+            // the polynomial preconditioner keeps z by the owner
+            w.z = M->ws.get_bytes(nm("z32"), n * esz, s, &e);
+            if (e != cudaSuccess) return cuda_fail(e, "workspace");
+        }
         const int OP = so.fp32_assembled ? OP_CSR1 : OP_K;
         OpParams<float> op{st.c1_32, st.c2_32, float(st.inv_T2), float(st.scale1), float(st.delta), 1, st.v32[0],
                            nullptr};
@@ -488,6 +500,8 @@ void qpat_default_params(qpat_params* p) {
     p->patch_nodes = 0;
     p->prior = 0;
     p->prior_q = 1.0;
+    p->poly_degree = 2;        // fastest measured on a 64^3 cube (GB300)
+    p->prior_poly_degree = 2;
 }
 
 static int mesh_create(const double* xyz, int64_t N, const int32_t* tets, int64_t E, int patch_nodes,
@@ -660,6 +674,23 @@ int64_t qpat_mesh_num_prior_entries(qpat_mesh_t M) {
     if (!M) return -1;
     int64_t n = 0;
     for (uint8_t l : M->h.psell_len) n += l;
+    return n;
+}
+
+int64_t qpat_mesh_num_local_entries(qpat_mesh_t M, int prior) {
+    if (!M) return -1;
+    const HostMesh& h = M->h;
+    const auto& ptr = prior ? h.psell_ptr : h.sell_ptr;
+    const auto& col = prior ? h.psell_col : h.sell_col;
+    const auto& len = prior ? h.psell_len : h.sell_len;
+    int64_t n = 0;
+    for (int64_t g = 0; g < h.N; ++g) {
+        const int p = h.patch_of_slice[size_t(g >> 5)];
+        const int nown = h.own_begin[size_t(p) + 1] - h.own_begin[size_t(p)];
+        const int64_t base = ptr[size_t(g >> 5)] * 32 + (g & 31);
+        for (int k = 0; k < len[size_t(g)]; ++k)
+            if (col[size_t(base + int64_t(k) * 32)] < nown) ++n;
+    }
     return n;
 }
 

@@ -43,6 +43,7 @@ struct OpState {
     int prior_kind = 0;             // r(t) of the prior (prior_weight in fem.cuh)
     double prior_q = 1;
     int nv = 1;                     // assembled value sets (1: K, 2: prior blocks)
+    double* gbound = nullptr;       // Gershgorin bound of D^-1 A over the value sets (1 double)
     double* v64[2] = {nullptr, nullptr};  // assembled FP64 values (sliced ELLPACK)
     float* v32[2] = {nullptr, nullptr};   // FP32 copy (K only)
 };
@@ -56,6 +57,8 @@ struct SolveOpts {
     int fp32_assembled = 0;   // FP32 inner operator: 0 matrix-free elements, 1 assembled values
     int pcg_variant = 0;      // assembled operators: 0 (= 1) two reductions, 2 one reduction, 3 bulk-copy ring
     int mixed_restart = 0;    // precision 1: 0 reliable updates (keep the direction), 1 restart every sweep
+    int poly_k = 0;           // patch-local Chebyshev degree of the K preconditioner (0 Jacobi)
+    int poly_prior = 0;       // the same for M_delta
 };
 
 struct DeviceGuard {

@@ -22,11 +22,13 @@ struct qpat_batch_s {
         double *kl = nullptr, *ml = nullptr, *vals = nullptr, *inv = nullptr;     // library layout
         double *f = nullptr, *x = nullptr, *r = nullptr, *p0 = nullptr, *p1 = nullptr, *q = nullptr;
         double *partials = nullptr, *ctl = nullptr;
+        double *z = nullptr, *gb = nullptr;  // patch-local Chebyshev preconditioner
     };
     int device = 0;
     int R = 0;
     double rtol = 1e-13;
     int maxit = 20000;
+    int poly_deg = 0;
     std::vector<Prob> probs;
     std::vector<void*> allocs;
     qpat::PcgBatchPlan plan;
@@ -66,7 +68,8 @@ int batch_sequence(qpat_batch_s* B, cudaStream_t s) {
         if ((e = launch_to_lib<double, double>(m, 1, 1, P.kappa, P.kl, s)) != cudaSuccess ||
             (e = launch_to_lib<double, double>(m, 1, 1, P.mu, P.ml, s)) != cudaSuccess)
             return cuda_fail(e, "qpat_batch_forward: to_lib");
-        if ((e = launch_assemble_K(m, P.kl, P.ml, P.vals, P.inv, nullptr, s)) != cudaSuccess)
+        if ((e = launch_assemble_K(m, P.kl, P.ml, P.vals, P.inv, nullptr, s, B->poly_deg > 0 ? P.gb : nullptr)) !=
+            cudaSuccess)
             return cuda_fail(e, "qpat_batch_forward: assemble");
         if ((e = cudaMemsetAsync(P.f, 0, sizeof(double) * N * B->R, s)) != cudaSuccess)
             return cuda_fail(e, "qpat_batch_forward: memset");
@@ -103,6 +106,7 @@ int qpat_batch_create(int nprob, const qpat_mesh_t* meshes, const int* K, const 
     const SolveOpts so = solve_opts(prm);
     B->rtol = so.rtol;
     B->maxit = so.maxit;
+    B->poly_deg = so.poly_k;
     DeviceGuard dg(B->device);
     std::vector<PcgBatchProblem> pp;
     int rc = QPAT_OK;
@@ -120,6 +124,7 @@ int qpat_batch_create(int nprob, const qpat_mesh_t* meshes, const int* K, const 
             (rc = batch_alloc(B, &P.p1, N * R)) || (rc = batch_alloc(B, &P.q, N * R)) ||
             (rc = batch_alloc(B, &P.partials, pcg_partials_doubles())) || (rc = batch_alloc(B, &P.ctl, 64)))
             break;
+        if (B->poly_deg > 0 && ((rc = batch_alloc(B, &P.z, N * R)) || (rc = batch_alloc(B, &P.gb, 1)))) break;
         PcgBatchProblem q;
         q.m = P.mesh->d;
         q.vals = P.vals;
@@ -135,6 +140,9 @@ int qpat_batch_create(int nprob, const qpat_mesh_t* meshes, const int* K, const 
         q.w.status = reinterpret_cast<int*>(P.ctl + 1);
         q.w.iters = reinterpret_cast<int*>(P.ctl + 2);
         q.w.stats = P.ctl + 8;
+        q.w.z = P.z;
+        q.w.poly_deg = B->poly_deg;
+        q.w.poly_hi = P.gb;
         q.rtol = B->rtol;
         q.maxit = B->maxit;
         pp.push_back(q);

@@ -249,17 +249,36 @@ __global__ void __launch_bounds__(kThreads) k_assemble_prior(MeshDev m, const do
     }
 }
 
-// val_r[diag] += shift ; inv[g * NV + r] = 1 / val_r[diag]  (FP64, optional FP32 copy)
-__global__ void k_diag_csr(MeshDev m, int NV, double shift, double* val0, double* val1, double* inv64, float* inv32) {
+// val_r[diag] += shift ; inv[g * NV + r] = 1 / val_r[diag]  (FP64, optional FP32 copy).
+// gbound (optional, zeroed by the caller): max over rows of sum_j |a_ij| / a_ii
+// (Gershgorin: every eigenvalue of D^-1 A, and of D^-1 A_pp for a principal
+// block, lies in [0, gbound] when A is symmetric positive definite).
+__global__ void k_diag_csr(MeshDev m, int NV, double shift, double* val0, double* val1, double* inv64, float* inv32,
+                           double* gbound) {
+    double gmax = 0.0;
     for (int64_t g = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; g < m.N; g += int64_t(gridDim.x) * blockDim.x) {
-        const int64_t idx = (m.sell_ptr[g >> 5] + m.sell_diag[g]) * 32 + (g & 31);
+        const int64_t base = m.sell_ptr[g >> 5] * 32 + (g & 31);
+        const int dk = m.sell_diag[g];
+        const int64_t idx = base + int64_t(dk) * 32;
         for (int r = 0; r < NV; ++r) {
             double* v = r == 0 ? val0 : val1;
             const double d = v[idx] + shift;
             v[idx] = d;
             inv64[g * NV + r] = 1.0 / d;
             if (inv32) inv32[g * NV + r] = float(1.0 / d);
+            if (gbound) {
+                double off = 0.0;
+                for (int k = 0; k < m.sell_len[g]; ++k)
+                    if (k != dk) off += fabs(v[base + int64_t(k) * 32]);
+                gmax = fmax(gmax, 1.0 + off / d);
+            }
         }
+    }
+    if (gbound) {
+        for (int o = 16; o > 0; o >>= 1) gmax = fmax(gmax, __shfl_xor_sync(0xffffffffu, gmax, o));
+        // non-negative doubles order like their bit patterns
+        if ((threadIdx.x & 31) == 0 && gmax > 0.0)
+            atomicMax(reinterpret_cast<unsigned long long*>(gbound), (unsigned long long)__double_as_longlong(gmax));
     }
 }
 
@@ -522,7 +541,7 @@ cudaError_t launch_invdiag_prior(const MeshDev& m, const double* u1, const doubl
 }
 
 cudaError_t launch_assemble_K(const MeshDev& m, const double* kappa, const double* mu, double* val, double* inv64,
-                              float* inv32, cudaStream_t s) {
+                              float* inv32, cudaStream_t s, double* gbound) {
     cudaError_t e = cudaMemsetAsync(val, 0, sizeof(double) * m.sell_entries, s);
     if (e != cudaSuccess) return e;
     const size_t smem = PatchSmem<double, 1>::bytes(m.max_touched, m.max_own);
@@ -530,14 +549,15 @@ cudaError_t launch_assemble_K(const MeshDev& m, const double* kappa, const doubl
     if (e != cudaSuccess) return e;
     qpat::note_launch(1);
     k_assemble_K<<<m.P, kThreads, smem, s>>>(m, kappa, mu, val);
+    if (gbound && (e = cudaMemsetAsync(gbound, 0, sizeof(double), s)) != cudaSuccess) return e;
     qpat::note_launch(1);
-    k_diag_csr<<<grid_for(m.N), 256, 0, s>>>(m, 1, 0.0, val, nullptr, inv64, inv32);
+    k_diag_csr<<<grid_for(m.N), 256, 0, s>>>(m, 1, 0.0, val, nullptr, inv64, inv32, gbound);
     return cudaGetLastError();
 }
 
 cudaError_t launch_assemble_prior(const MeshDev& m, const double* u1, const double* u2, double inv_T2, int kind,
                                   double q, double scale1, double delta, double* val0, double* val1, double* inv64,
-                                  float* inv32, cudaStream_t s) {
+                                  float* inv32, cudaStream_t s, double* gbound) {
     cudaError_t e = cudaMemsetAsync(val0, 0, sizeof(double) * m.sell_entries, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(val1, 0, sizeof(double) * m.sell_entries, s);
     if (e != cudaSuccess) return e;
@@ -546,8 +566,9 @@ cudaError_t launch_assemble_prior(const MeshDev& m, const double* u1, const doub
     if (e != cudaSuccess) return e;
     qpat::note_launch(1);
     k_assemble_prior<<<m.P, kThreads, smem, s>>>(m, u1, u2, inv_T2, kind, q, scale1, val0, val1);
+    if (gbound && (e = cudaMemsetAsync(gbound, 0, sizeof(double), s)) != cudaSuccess) return e;
     qpat::note_launch(1);
-    k_diag_csr<<<grid_for(m.N), 256, 0, s>>>(m, 2, delta, val0, val1, inv64, inv32);
+    k_diag_csr<<<grid_for(m.N), 256, 0, s>>>(m, 2, delta, val0, val1, inv64, inv32, gbound);
     return cudaGetLastError();
 }
 

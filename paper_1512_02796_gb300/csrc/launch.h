@@ -29,11 +29,14 @@ cudaError_t launch_invdiag_prior(const MeshDev& m, const double* u1, const doubl
 // Assembly of K (FP64 values in the sliced-ELLPACK pattern; val must hold
 // m.sell_entries) and of the two prior blocks with delta on the diagonal;
 // both also write the inverse diagonal (FP64 and, if not null, FP32).
+// gbound (optional, one double): receives max over rows and value sets of
+// sum_j |a_ij| / a_ii, a Gershgorin bound of the spectrum of D^-1 A (and of
+// D^-1 A_pp for every principal block A_pp).
 cudaError_t launch_assemble_K(const MeshDev& m, const double* kappa, const double* mu, double* val, double* inv64,
-                              float* inv32, cudaStream_t s);
+                              float* inv32, cudaStream_t s, double* gbound = nullptr);
 cudaError_t launch_assemble_prior(const MeshDev& m, const double* u1, const double* u2, double inv_T2, int kind,
                                   double q, double scale1, double delta, double* val0, double* val1, double* inv64,
-                                  float* inv32, cudaStream_t s);
+                                  float* inv32, cudaStream_t s, double* gbound = nullptr);
 cudaError_t launch_cast_vals(int64_t n, const double* in, float* out, cudaStream_t s);
 // y = A x with an assembled operator (NV = 1: one value set for R RHS; NV = 2: the prior, R = 2)
 template <typename T>
@@ -65,6 +68,9 @@ cudaError_t launch_sub(int64_t n, const double* a, const double* b, double* out,
 cudaError_t launch_cast_d2f(int64_t n, const double* in, float* out, cudaStream_t s);
 
 // ---------------------------------------------------------------- pcg.cu
+// largest degree of the patch-local Chebyshev preconditioner (see pcg.cu)
+constexpr int kMaxPolyDegree = 8;
+
 struct PcgWork {
     void* b;  // N x R (T)
     void* x;
@@ -83,6 +89,11 @@ struct PcgWork {
     void* s0 = nullptr;
     void* s1 = nullptr;
     void* w1 = nullptr;
+    // patch-local Chebyshev preconditioner (two-reduction kernel on assembled
+    // operators, needs z): degree 0 = Jacobi; poly_hi = device pointer to an
+    // upper bound of the spectrum of D^-1 A
+    int poly_deg = 0;
+    const double* poly_hi = nullptr;
     double* partials;   // 2 x max_grid x 3R
     unsigned* bar;      // 2
     int* status;        // 1
@@ -124,6 +135,7 @@ struct PcgBatchPlan {
     int* dev_cta_begin = nullptr;
     int R = 0, nprob = 0, grid = 0;
     size_t smem = 0;
+    bool poly = false;  // patch-local Chebyshev preconditioner (every problem has z, poly_deg, poly_hi)
     std::vector<int> cta_count;
 };
 cudaError_t pcg_batch_prepare(int R, const std::vector<PcgBatchProblem>& probs, PcgBatchPlan& plan);

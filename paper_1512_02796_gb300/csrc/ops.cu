@@ -153,6 +153,8 @@ SolveOpts solve_opts(const qpat_params* prm) {
     so.fp32_assembled = p->fp32_operator == 1 ? 1 : 0;
     so.pcg_variant = p->pcg_variant;
     so.mixed_restart = p->mixed_restart ? 1 : 0;
+    so.poly_k = p->poly_degree;
+    so.poly_prior = p->prior_poly_degree;
     return so;
 }
 
@@ -163,6 +165,9 @@ static int check_params(const qpat_params* prm, const char* who) {
     if (prm->pcg_variant < 0 || prm->pcg_variant > 3)
         return fail(QPAT_EINVAL, std::string(who) + ": pcg_variant must be 0, 1, 2 or 3");
     if (prm->prior != 0 && prm->prior != 1) return fail(QPAT_EINVAL, std::string(who) + ": prior must be 0 or 1");
+    if (prm->poly_degree < 0 || prm->poly_degree > kMaxPolyDegree || prm->prior_poly_degree < 0 ||
+        prm->prior_poly_degree > kMaxPolyDegree)
+        return fail(QPAT_EINVAL, std::string(who) + ": poly_degree and prior_poly_degree must lie in [0, 8]");
     if (prm->prior == 1 && !(prm->prior_q > 0.0 && prm->prior_q <= 2.0))
         return fail(QPAT_EINVAL, std::string(who) + ": prior_q must lie in (0, 2]");
     return QPAT_OK;

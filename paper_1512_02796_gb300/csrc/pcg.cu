@@ -61,6 +61,11 @@ struct PcgArgs {
     T* s0;
     T* s1;
     T* w1;
+    // patch-local Chebyshev preconditioner (two-reduction kernel on assembled
+    // operators with z stored): degree (0 = Jacobi) and a device pointer to
+    // an upper bound of the spectrum of D^-1 A
+    int poly_deg = 0;
+    const double* poly_hi = nullptr;
 };
 
 constexpr int kMaxGrid = 152 * 8;
@@ -143,9 +148,12 @@ __device__ __forceinline__ void dinv_vec(const T* invdiag, int g, int r0, T (&d)
 // entry).  Entries past the row length are not loaded.
 constexpr int kChunk = 8;
 constexpr int kUnroll = 2;  // touched nodes a thread stages at once
-template <typename T, int R, int VW, int OP>
+//
+// kLocal: only the couplings among the patch's owned nodes (local column ids
+// below nloc; the owned nodes come first in a patch's node list) take part.
+template <typename T, int R, int VW, int OP, bool kLocal = false>
 __device__ __forceinline__ void sell_row(const MeshDev& m, const OpParams<T>& op, const T* xs, int g, int r0,
-                                         T (&acc)[VW]) {
+                                         T (&acc)[VW], int nloc = 0) {
     constexpr int NL = OP == OP_CSR2 ? VW : 1;  // distinct value sets this thread reads
     const int64_t base = m.sell_ptr[g >> 5] * 32 + (g & 31);
     const int len = m.sell_len[g];
@@ -164,6 +172,15 @@ __device__ __forceinline__ void sell_row(const MeshDev& m, const OpParams<T>& op
             col[j] = ok ? int(__ldg(m.sell_col + idx)) : 0;
 #pragma unroll
             for (int q = 0; q < NL; ++q) v[j][q] = ok ? __ldg(vp[q] + idx) : T(0);
+        }
+        if constexpr (kLocal) {
+#pragma unroll
+            for (int j = 0; j < kChunk; ++j) {
+                const bool in = col[j] < nloc;
+                col[j] = in ? col[j] : 0;
+#pragma unroll
+                for (int q = 0; q < NL; ++q) v[j][q] = in ? v[j][q] : T(0);
+            }
         }
 #pragma unroll
         for (int j = 0; j < kChunk; ++j) {
@@ -295,8 +312,81 @@ __device__ __forceinline__ bool grid_reduce(T (&acc)[NQ][VW], double* scratch, d
     return true;
 }
 
+// ---------------------------------------------------------------- preconditioner
+// Patch-local Chebyshev preconditioner: block Jacobi over the CTA patches,
+// each block A_pp (the couplings among a patch's owned nodes) inverted
+// approximately by the polynomial of `deg` steps of the Chebyshev iteration
+// for A_pp z = r with diagonal scaling, from z = 0, on the interval
+// [lo, hi] of B = D^-1 A_pp:  z = p(B) v with v = D^-1 r and p of degree
+// deg.  M^-1 = p(B) D^-1 is symmetric (D^-1/2 p(D^-1/2 A_pp D^-1/2) D^-1/2
+// per block) and positive definite whenever hi bounds the spectrum (the
+// Chebyshev residual polynomial 1 - x p(x) stays inside (-1, 1) on (0, hi]),
+// so ordinary PCG applies.  p is evaluated in Horner form,
+//   w = a_deg v ;  w = a_j v + B w  (j = deg-1 .. 0) ;  z = w,
+// one local operator sweep and two FP64 operations per row and step (FP64
+// issue slots are the scarce resource on GB300), and no grid barrier.
+constexpr double kPolyRatio = 50.0;  // lo = hi / kPolyRatio
+
+// Monomial coefficients a_0..a_deg of p.  With polynomials in x standing for
+// the vectors of the iteration applied to v: the scaled residual
+// S_0 = 1, the step D_0 = 1/theta, the iterate P_0 = D_0, and per step
+//   S_{k+1} = S_k - x D_k ;  D_{k+1} = rho_{k+1} rho_k D_k + (2 rho_{k+1} / delta) S_{k+1} ;
+//   P_{k+1} = P_k + D_{k+1},
+// where theta, delta are the centre and half width of [lo, hi],
+// rho_0 = delta / theta and rho_{k+1} = 1 / (2 theta / delta - rho_k).
+__device__ __forceinline__ void cheb_coeffs(double hi, int deg, double* acoef) {
+    if (!(hi > 0.0) || !isfinite(hi)) hi = 2.0;
+    hi *= 1.01;  // margin over the FP64 rounding of the bound
+    const double lo = hi / kPolyRatio;
+    const double th = 0.5 * (hi + lo), dl = 0.5 * (hi - lo), sg = th / dl;
+    double S[kMaxPolyDegree + 2] = {}, D[kMaxPolyDegree + 2] = {}, P[kMaxPolyDegree + 2] = {};
+    S[0] = 1.0;
+    D[0] = 1.0 / th;
+    P[0] = D[0];
+    double rho = 1.0 / sg;
+    for (int k = 0; k < deg; ++k) {
+        for (int j = k + 1; j >= 1; --j) S[j] -= D[j - 1];  // S -= x D (D has degree k)
+        const double rn = 1.0 / (2.0 * sg - rho);
+        const double c1 = rn * rho, c2 = 2.0 * rn / dl;
+        for (int j = 0; j <= k + 1; ++j) {
+            D[j] = c1 * D[j] + c2 * S[j];
+            P[j] += D[j];
+        }
+        rho = rn;
+    }
+    for (int j = 0; j <= deg; ++j) acoef[j] = P[j];
+}
+
+// The deg Horner steps on one patch.  On entry every thread has written, for
+// its owned rows (offset li * R + r0), cV = v = D^-1 r and cW0 = a_deg v; on
+// exit the returned buffer holds z.  Block-wide barriers separate the steps.
+template <typename T, int R, int VW, int NP, int OP>
+__device__ __forceinline__ T* cheb_patch(const PcgArgs<T>& a, int ob, int nown, int r0, int deg, const double* acoef,
+                                         const T* cV, T* cW0, T* cW1) {
+    for (int s = 0; s < deg; ++s) {
+        const T* src = (s & 1) ? cW1 : cW0;
+        T* dst = (s & 1) ? cW0 : cW1;
+        const T aj = T(acoef[deg - 1 - s]);
+        __syncthreads();  // w complete
+        for (int i = threadIdx.x; i < nown * NP; i += blockDim.x) {
+            const int li = i / NP;
+            const int g = ob + li;
+            const int o = li * R + r0;
+            T y[VW], vv[VW], d[VW];
+            sell_row<T, R, VW, OP, true>(a.m, a.op, src, g, r0, y, nown);
+            vld(cV + o, vv);
+            dinv_vec<T, VW, OP>(a.invdiag, g, r0, d);
+#pragma unroll
+            for (int c = 0; c < VW; ++c) y[c] = aj * vv[c] + d[c] * y[c];
+            vst(dst + o, y);
+        }
+    }
+    __syncthreads();  // nobody reads this patch's buffers any more
+    return (deg & 1) ? cW1 : cW0;
+}
+
 // ---------------------------------------------------------------- the solver
-template <typename T, int R, int OP>
+template <typename T, int R, int OP, bool kPoly = false>
 __device__ __forceinline__ void pcg_body(const PcgArgs<T>& a, const int cta, const int ncta) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     constexpr bool kCsr = (OP == OP_CSR1 || OP == OP_CSR2);
@@ -323,6 +413,22 @@ __device__ __forceinline__ void pcg_body(const PcgArgs<T>& a, const int cta, con
     const int off = resumed ? (pb_in == 0 ? 1 : 0) : 0;  // iteration 0 reads p_old from buffer pb_in
     int red_id = 0;
 
+    // patch-local Chebyshev preconditioner: its four owned-row vectors
+    // overlay the staged p (phase A is over whenever they are in use)
+    const int deg = (kPoly && kCsr && zs) ? a.poly_deg : 0;  // kPoly: a separate instantiation keeps
+                                                              // the Jacobi kernel's registers unchanged
+    __shared__ double pco[kMaxPolyDegree + 1];
+    T *cV = nullptr, *cW0 = nullptr, *cW1 = nullptr;
+    if (deg > 0) {
+        const size_t stride = size_t(m.max_own) * R;
+        cV = reinterpret_cast<T*>(smem_raw);
+        cW0 = cV + stride;
+        cW1 = cW0 + stride;
+        if (threadIdx.x == 0) cheb_coeffs(__ldcg(a.poly_hi), deg, pco);
+        __syncthreads();
+    }
+    const T a_top = deg > 0 ? T(pco[deg]) : T(1);
+
     // ---- initial residual r = b (x0 = 0)
     {
         T acc[3][VW];
@@ -341,11 +447,31 @@ __device__ __forceinline__ void pcg_body(const PcgArgs<T>& a, const int cta, con
                     zero[c] = T(0);
                     zv[c] = d[c] * bv[c];
                     acc[0][c] += bv[c] * bv[c];
-                    acc[1][c] += bv[c] * zv[c];
+                    if (deg == 0) acc[1][c] += bv[c] * zv[c];
                 }
                 vst(a.x + e, zero);
                 vst(a.r + e, bv);
-                if (a.z) vst(a.z + e, zv);
+                if (deg > 0) {
+                    const int o = (i / NP) * R + r0;
+                    vst(cV + o, zv);
+#pragma unroll
+                    for (int c = 0; c < VW; ++c) zv[c] *= a_top;
+                    vst(cW0 + o, zv);
+                } else if (a.z) {
+                    vst(a.z + e, zv);
+                }
+            }
+            if (deg > 0) {
+                const T* zw = cheb_patch<T, R, VW, NP, OP>(a, ob, nown, r0, deg, pco, cV, cW0, cW1);
+                for (int i = threadIdx.x; i < nown * NP; i += blockDim.x) {
+                    const size_t e = size_t(ob + i / NP) * R + r0;
+                    T bv[VW], zv[VW];
+                    vld(a.b + e, bv);
+                    vld(zw + (i / NP) * R + r0, zv);
+#pragma unroll
+                    for (int c = 0; c < VW; ++c) acc[1][c] += bv[c] * zv[c];
+                    vst(a.z + e, zv);
+                }
             }
         }
 #pragma unroll
@@ -515,12 +641,32 @@ __device__ __forceinline__ void pcg_body(const PcgArgs<T>& a, const int cta, con
                         xv[c] += al[c] * pv[c];
                         rv[c] -= al[c] * qv[c];
                         zv[c] = d[c] * rv[c];
-                        accB[0][c] += rv[c] * zv[c];
+                        if (deg == 0) accB[0][c] += rv[c] * zv[c];
                         accB[1][c] += rv[c] * rv[c];
                     }
                     vst(a.x + e, xv);
                     vst(a.r + e, rv);
-                    if (zs) vst(a.z + e, zv);
+                    if (deg > 0) {
+                        const int o = (i / NP) * R + r0;
+                        vst(cV + o, zv);
+#pragma unroll
+                        for (int c = 0; c < VW; ++c) zv[c] *= a_top;
+                        vst(cW0 + o, zv);
+                    } else if (zs) {
+                        vst(a.z + e, zv);
+                    }
+                }
+                if (deg > 0) {
+                    const T* zw = cheb_patch<T, R, VW, NP, OP>(a, ob, nown, r0, deg, pco, cV, cW0, cW1);
+                    for (int i = threadIdx.x; i < nown * NP; i += blockDim.x) {
+                        const size_t e = size_t(ob + i / NP) * R + r0;
+                        T rv[VW], zv[VW];
+                        vld(a.r + e, rv);  // written by this thread above
+                        vld(zw + (i / NP) * R + r0, zv);
+#pragma unroll
+                        for (int c = 0; c < VW; ++c) accB[0][c] += rv[c] * zv[c];
+                        vst(a.z + e, zv);
+                    }
                 }
             }
         }
@@ -557,9 +703,9 @@ constexpr int min_ctas() {
     return (OP == OP_CSR1 || OP == OP_CSR2) ? 4 : 1;
 }
 
-template <typename T, int R, int OP>
+template <typename T, int R, int OP, bool kPoly = false>
 __global__ void __launch_bounds__(kThreads) k_pcg(PcgArgs<T> a) {
-    pcg_body<T, R, OP>(a, blockIdx.x, gridDim.x);
+    pcg_body<T, R, OP, kPoly>(a, blockIdx.x, gridDim.x);
 }
 
 // ---------------------------------------------------------------- single-reduction variant
@@ -1227,7 +1373,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_pcg_ring(PcgArgs<T> a, RingLayo
 // Independent problems (meshes of different sizes) in one cooperative
 // launch: CTAs [cta_begin[j], cta_begin[j+1]) solve problem j, and each
 // problem's barriers and reductions involve only its own CTAs.
-template <typename T, int R, int OP>
+template <typename T, int R, int OP, bool kPoly = false>
 __global__ void __launch_bounds__(kThreads) k_pcg_batch(const PcgArgs<T>* __restrict__ probs,
                                                         const int* __restrict__ cta_begin, int nprob) {
     int lo = 0, hi = nprob - 1;
@@ -1240,14 +1386,21 @@ __global__ void __launch_bounds__(kThreads) k_pcg_batch(const PcgArgs<T>* __rest
     }
     const int b0 = cta_begin[lo];
     const PcgArgs<T> a = probs[lo];
-    pcg_body<T, R, OP>(a, int(blockIdx.x) - b0, cta_begin[lo + 1] - b0);
+    pcg_body<T, R, OP, kPoly>(a, int(blockIdx.x) - b0, cta_begin[lo + 1] - b0);
 }
 
 template <int R>
 cudaError_t batch_prepare_t(const std::vector<PcgBatchProblem>& probs, PcgBatchPlan& plan) {
+    // the patch-local Chebyshev preconditioner when every problem asks for it
+    bool poly = !probs.empty();
+    for (const auto& p : probs) poly = poly && p.w.poly_deg > 0 && p.w.z && p.w.poly_hi;
     size_t smem = 0;
-    for (const auto& p : probs) smem = std::max(smem, sizeof(double) * size_t(p.m.max_touched) * R);
-    auto kern = k_pcg_batch<double, R, OP_CSR1>;
+    for (const auto& p : probs) {
+        if (p.w.poly_deg < 0 || p.w.poly_deg > kMaxPolyDegree) return cudaErrorInvalidValue;
+        smem = std::max(smem, sizeof(double) * size_t(p.m.max_touched) * R);
+        if (poly) smem = std::max(smem, 3 * sizeof(double) * size_t(p.m.max_own) * R);
+    }
+    auto kern = poly ? k_pcg_batch<double, R, OP_CSR1, true> : k_pcg_batch<double, R, OP_CSR1>;
     cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
     if (err != cudaSuccess) return err;
     int dev = 0, nsm = 0, per_sm = 0;
@@ -1307,6 +1460,11 @@ cudaError_t batch_prepare_t(const std::vector<PcgBatchProblem>& probs, PcgBatchP
         a.rtol2 = p.rtol * p.rtol;
         a.maxit = p.maxit;
         a.spin_limit = 40000000LL;
+        if (poly) {
+            a.z = static_cast<double*>(p.w.z);
+            a.poly_deg = p.w.poly_deg;
+            a.poly_hi = p.w.poly_hi;
+        }
     }
     if ((err = cudaMalloc(&plan.dev_args, sizeof(PcgArgs<double>) * nprob)) != cudaSuccess) return err;
     if ((err = cudaMalloc(reinterpret_cast<void**>(&plan.dev_cta_begin), sizeof(int) * (nprob + 1))) != cudaSuccess)
@@ -1321,13 +1479,14 @@ cudaError_t batch_prepare_t(const std::vector<PcgBatchProblem>& probs, PcgBatchP
     plan.nprob = nprob;
     plan.grid = begin[nprob];
     plan.smem = smem;
+    plan.poly = poly;
     plan.cta_count = cnt;
     return cudaSuccess;
 }
 
 template <int R>
 cudaError_t batch_launch_t(const PcgBatchPlan& plan, cudaStream_t s) {
-    auto kern = k_pcg_batch<double, R, OP_CSR1>;
+    auto kern = plan.poly ? k_pcg_batch<double, R, OP_CSR1, true> : k_pcg_batch<double, R, OP_CSR1>;
     const PcgArgs<double>* pa = static_cast<const PcgArgs<double>*>(plan.dev_args);
     const int* cb = plan.dev_cta_begin;
     int np = plan.nprob;
@@ -1339,13 +1498,19 @@ cudaError_t batch_launch_t(const PcgBatchPlan& plan, cudaStream_t s) {
 template <typename T, int R, int OP, bool kSingle = false>
 cudaError_t launch_pcg_t(const MeshDev& m, const OpParams<T>& op, const T* invdiag, const PcgWork& w,
                          double rtol, int maxit, cudaStream_t s, int* grid_used) {
-    const size_t smem = (OP == OP_CSR1 || OP == OP_CSR2) ? sizeof(T) * size_t(m.max_touched) * R
-                                                         : PatchSmem<T, R>::bytes(m.max_touched, m.max_own);
+    constexpr bool kCsr = OP == OP_CSR1 || OP == OP_CSR2;
+    const int deg = (kCsr && !kSingle && w.z) ? w.poly_deg : 0;
+    if (w.poly_deg < 0 || w.poly_deg > kMaxPolyDegree || (deg > 0 && !w.poly_hi)) return cudaErrorInvalidValue;
+    size_t smem = kCsr ? sizeof(T) * size_t(m.max_touched) * R : PatchSmem<T, R>::bytes(m.max_touched, m.max_own);
+    if (deg > 0) smem = std::max(smem, 3 * sizeof(T) * size_t(m.max_own) * R);
     void (*kern)(PcgArgs<T>) = nullptr;
-    if constexpr (kSingle)
+    if constexpr (kSingle) {
         kern = k_pcg1<T, R, OP>;
-    else
+    } else if constexpr (kCsr) {
+        kern = deg > 0 ? k_pcg<T, R, OP, true> : k_pcg<T, R, OP>;
+    } else {
         kern = k_pcg<T, R, OP>;
+    }
     cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
     if (err != cudaSuccess) return err;
     int dev = 0, nsm = 0, per_sm = 0;
@@ -1386,6 +1551,8 @@ cudaError_t launch_pcg_t(const MeshDev& m, const OpParams<T>& op, const T* invdi
     a.s0 = static_cast<T*>(w.s0);
     a.s1 = static_cast<T*>(w.s1);
     a.w1 = static_cast<T*>(w.w1);
+    a.poly_deg = deg;
+    a.poly_hi = w.poly_hi;
     if (kSingle && !(a.r1 && a.s0 && a.s1 && a.w1)) return cudaErrorInvalidValue;
     err = cudaMemsetAsync(w.bar, 0, 2 * sizeof(unsigned), s);
     if (err != cudaSuccess) return err;

@@ -31,7 +31,7 @@ class qpat_params(ctypes.Structure):
         ("max_pcg_iter", ctypes.c_int), ("pcg_rtol", ctypes.c_double), ("fit_grid", ctypes.c_int),
         ("fit_gn_steps", ctypes.c_int), ("patch_nodes", ctypes.c_int), ("fp32_operator", ctypes.c_int),
         ("pcg_variant", ctypes.c_int), ("prior", ctypes.c_int), ("mixed_restart", ctypes.c_int),
-        ("reserved", ctypes.c_int * 3),
+        ("poly_degree", ctypes.c_int), ("prior_poly_degree", ctypes.c_int), ("reserved", ctypes.c_int * 1),
         ("prior_q", ctypes.c_double),
     ]
 
@@ -86,6 +86,7 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
         "qpat_mesh_num_patches": (ctypes.c_int64, [vp]),
         "qpat_mesh_num_entries": (ctypes.c_int64, [vp]),
         "qpat_mesh_num_prior_entries": (ctypes.c_int64, [vp]),
+        "qpat_mesh_num_local_entries": (ctypes.c_int64, [vp, ctypes.c_int]),
         "qpat_mesh_faces": (ctypes.c_int, [vp, _c_int32_p]),
         "qpat_mesh_permutation": (ctypes.c_int, [vp, _c_int32_p]),
         "qpat_mesh_stats": (ctypes.c_int, [vp, _c_int64_p]),
@@ -160,7 +161,7 @@ def exported_names() -> Sequence[str]:
     return [
         "qpat_default_params", "qpat_last_error", "qpat_launch_count", "qpat_mesh", "qpat_mesh_ex", "qpat_mesh_free",
         "qpat_mesh_host_info", "qpat_mesh_num_nodes", "qpat_mesh_num_tets", "qpat_mesh_num_faces", "qpat_mesh_num_patches",
-        "qpat_mesh_num_entries", "qpat_mesh_num_prior_entries",
+        "qpat_mesh_num_entries", "qpat_mesh_num_prior_entries", "qpat_mesh_num_local_entries",
         "qpat_mesh_faces", "qpat_mesh_permutation", "qpat_mesh_stats", "qpat_mesh_fp64_fallbacks",
         "qpat_mesh_reset_stats",
         "qpat_mesh_set_timing", "qpat_mesh_pcg_time",
@@ -335,6 +336,9 @@ class Mesh:
         self.P = int(lib.qpat_mesh_num_patches(h))
         self.entries = int(lib.qpat_mesh_num_entries(h))
         self.prior_entries = int(lib.qpat_mesh_num_prior_entries(h))
+        # couplings inside a patch (what the patch-local preconditioner applies)
+        self.local_entries = int(lib.qpat_mesh_num_local_entries(h, 0))
+        self.prior_local_entries = int(lib.qpat_mesh_num_local_entries(h, 1))
 
     def close(self):
         if getattr(self, "handle", None):

@@ -34,6 +34,8 @@ def test_default_params_follow_the_paper():
     p = Q.qpat_default_params()
     assert p.T == 5e-3 and p.delta == 1e-6 and p.b_over_a == 1.0
     assert p.m0 == 10 and p.tau == 1e-2
+    # library choices, not the paper's: degree-2 patch-local Chebyshev preconditioners
+    assert p.poly_degree == 2 and p.prior_poly_degree == 2
 
 
 @pytest.mark.parametrize("n,L,pn", [(2, 1.0, 32), (5, 2.0, 32), (11, 20.0, 64), (11, 20.0, 512), (17, 4.0, 96)])

@@ -16,7 +16,10 @@ pytestmark = pytest.mark.gpu
 SIZES = [(5, 1), (9, 3), (12, 2), (7, 4), (16, 1), (10, 4), (13, 3)]
 
 
-def test_uneven_batch_matches_single_solves():
+@pytest.mark.parametrize("deg", [0, 2])
+def test_uneven_batch_matches_single_solves(deg):
+    """Jacobi (deg 0) or the patch-local Chebyshev preconditioner in the
+    batched launch: every problem equals its single-mesh solve and the oracle."""
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
     cfgs = [S.small_config(n, 2.0 * n, K, 100 + i) for i, (n, K) in enumerate(SIZES)]
@@ -28,7 +31,7 @@ def test_uneven_batch_matches_single_solves():
         flux = np.stack([Q.qpat_flux_patch(m, p.center, p.normal, p.half_w, p.amp) for p in cfg.patches])
         meshes.append(m)
         data.append((xyz, tets, kap, mu, flux))
-    batch = Q.qpat_batch_create(meshes, [c.K for c in cfgs])
+    batch = Q.qpat_batch_create(meshes, [c.K for c in cfgs], Q.qpat_default_params(poly_degree=deg))
     try:
         for rep in range(3):
             scale = 1.0 + 0.1 * rep          # new inputs on every replay of the same graph

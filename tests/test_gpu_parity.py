@@ -230,3 +230,81 @@ def test_mixed_precision_reliable_updates_and_restarts(case, restart):
     s = rng.standard_normal(2 * case.N)
     out = Q.qpat_jvp(case.lib, case.kappa, case.mu, case.phi, s, case.w, p)
     assert rel(out, O.jvp(case.om, case.kappa, case.mu, case.phi, s, case.w, case.fac)) < 1e-10
+
+
+@pytest.mark.parametrize("deg", [1, 2, 4, 8])
+def test_prior_solve_poly_preconditioner(case, deg):
+    """The patch-local Chebyshev preconditioner (block Jacobi over the CTA
+    patches, a degree-deg polynomial per block) changes the iteration, not
+    the solution: the M_delta solve meets the Jacobi bars, and on Kuhn cubes
+    of a few hundred nodes or more it needs no more iterations than Jacobi."""
+    rng = np.random.default_rng(13)
+    N = case.N
+    kt = 0.3 * rng.standard_normal(N)
+    mt = np.log(case.mu / case.mu.mean())
+    rhs = rng.standard_normal(2 * N)
+    T, ba, delta = 1e-2, 0.7, 1e-6
+    Md = O.prior_matrix(case.om, kt, mt, T, ba, delta)
+    ref = O.Factor(Md).solve(rhs)
+    iters = {}
+    for d in (0, deg):
+        case.lib.reset_stats()
+        out = Q.qpat_prior_solve(case.lib, kt, mt, rhs,
+                                 _params(0, T=T, b_over_a=ba, delta=delta, pcg_rtol=1e-13, prior_poly_degree=d))
+        iters[d] = case.lib.stats()["pcg_iters"]
+        Anorm = abs(Md).sum(axis=0).max()
+        eta = np.linalg.norm(Md @ out - rhs, 1) / (Anorm * np.linalg.norm(out, 1) + np.linalg.norm(rhs, 1))
+        assert eta < 1e-13
+        if N <= 800:
+            ev = np.linalg.eigvalsh(Md.toarray())
+            tol = 10 * (ev[-1] / ev[0]) * 1e-13
+        else:
+            tol = 1e-4
+        assert rel(out, ref) < max(tol, 1e-10)
+    # on a handful of nodes CG needs only a few steps either way; on the
+    # mapped cylinder mesh the stiffness has positive off-diagonal entries,
+    # the Gershgorin interval is wider and a low degree may not pay
+    if N > 400 and not hasattr(case.cfg, "illuminations"):
+        assert iters[deg] <= iters[0]
+
+
+@pytest.mark.parametrize("precision,fp32_op,variant", [(0, 0, 1), (0, 0, 2), (1, 1, 1), (1, 0, 1)])
+@pytest.mark.parametrize("deg", [0, 1, 3])
+def test_forward_and_pair_poly_preconditioner(case, precision, fp32_op, variant, deg):
+    """K solves with Jacobi (deg 0) or the patch-local Chebyshev
+    preconditioner (FP64 PCG and the FP32 inner PCG of the refinement;
+    variants and operators without it fall back to Jacobi) reach the
+    oracle's forward field and J products."""
+    p = _params(precision, fp32_operator=fp32_op, pcg_variant=variant, poly_degree=deg)
+    phi, h = Q.qpat_forward(case.lib, case.kappa, case.mu, case.flux, p)
+    assert rel(phi, case.phi) < 1e-10
+    assert rel(h, case.h) < 1e-10
+    rng = np.random.default_rng(14)
+    s = rng.standard_normal(2 * case.N)
+    t = rng.standard_normal((case.K, case.N))
+    oj = Q.qpat_jvp(case.lib, case.kappa, case.mu, case.phi, s, case.w, p)
+    assert rel(oj, O.jvp(case.om, case.kappa, case.mu, case.phi, s, case.w, case.fac)) < 1e-10
+    ov = Q.qpat_vjp(case.lib, case.kappa, case.mu, case.phi, t, case.w, p)
+    assert rel(ov, O.vjp(case.om, case.kappa, case.mu, case.phi, t, case.w, case.fac)) < 1e-10
+
+
+def test_poly_degree_checks(case):
+    for kw in ({"poly_degree": 9}, {"prior_poly_degree": -1}):
+        with pytest.raises(Q.QpatError):
+            Q.qpat_forward(case.lib, case.kappa, case.mu, case.flux, _params(0, **kw))
+
+
+def test_local_entry_counts(case):
+    """Couplings inside a patch (what the patch-local preconditioner applies)
+    are a subset of the stored entries; with the whole mesh in one patch
+    they are all of them."""
+    lib = case.lib
+    assert 0 < lib.local_entries <= lib.entries
+    assert 0 < lib.prior_local_entries <= lib.prior_entries
+    if case.N <= 1024:
+        one = Q.qpat_mesh(case.xyz, case.tets, patch_nodes=32 * (-(-case.N // 32)))
+        try:
+            assert one.local_entries == one.entries
+            assert one.prior_local_entries == one.prior_entries
+        finally:
+            one.close()
