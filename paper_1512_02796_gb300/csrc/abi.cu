@@ -625,17 +625,20 @@ int qpat_mesh_host_info(const double* xyz, int64_t N, const int32_t* tets, int64
     return QPAT_OK;
 }
 
+static constexpr int kPatchesPerSm = 2;
+
 int qpat_mesh(const double* xyz, int64_t N, const int32_t* tets, int64_t E, qpat_mesh_t* out) {
     // default patching: at most 1024 owned nodes per patch and a patch count
-    // that is a multiple of 4 CTAs per SM, so that every resident CTA of the
-    // persistent solver owns the same number of patches
+    // that is a multiple of 2 CTAs per SM (the residency of the FP64 solver
+    // kernels), so that every resident CTA of the persistent solver owns the
+    // same number of patches
     int dev = 0, nsm = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) !=
                                                    cudaSuccess || nsm < 1) {
         (void)cudaGetLastError();
         nsm = 152;
     }
-    return mesh_create(xyz, N, tets, E, 1024, 4 * nsm, out);
+    return mesh_create(xyz, N, tets, E, 1024, kPatchesPerSm * nsm, out);
 }
 
 int qpat_mesh_ex(const double* xyz, int64_t N, const int32_t* tets, int64_t E, int patch_nodes, qpat_mesh_t* out) {

@@ -145,8 +145,13 @@ __device__ __forceinline__ void dinv_vec(const T* invdiag, int g, int r0, T (&d)
 // are fetched kChunk at a time into registers before any is used, so that
 // kChunk independent loads per thread are in flight at once (a thread-per-row
 // loop that consumes each entry as it arrives waits one memory latency per
-// entry).  Entries past the row length are not loaded.
+// entry).  Entries past the row length are not loaded; their multiply-adds
+// run on zeros (predicating them off was measured slower).  Chunk widths: K
+// rows of Kuhn meshes hold 15 entries (two chunks of 8), the prior's
+// stiffness-only rows 7 (one chunk of 7, no wasted FP64 multiply-add; FP64
+// issue slots bound the assembled FP64 solves on GB300).
 constexpr int kChunk = 8;
+constexpr int kChunkPrior = 7;
 constexpr int kUnroll = 2;  // touched nodes a thread stages at once
 //
 // kLocal: only the couplings among the patch's owned nodes (local column ids
@@ -155,6 +160,7 @@ template <typename T, int R, int VW, int OP, bool kLocal = false>
 __device__ __forceinline__ void sell_row(const MeshDev& m, const OpParams<T>& op, const T* xs, int g, int r0,
                                          T (&acc)[VW], int nloc = 0) {
     constexpr int NL = OP == OP_CSR2 ? VW : 1;  // distinct value sets this thread reads
+    constexpr int CH = OP == OP_CSR2 ? kChunkPrior : kChunk;
     const int64_t base = m.sell_ptr[g >> 5] * 32 + (g & 31);
     const int len = m.sell_len[g];
     const T* vp[NL];
@@ -162,11 +168,11 @@ __device__ __forceinline__ void sell_row(const MeshDev& m, const OpParams<T>& op
     for (int q = 0; q < NL; ++q) vp[q] = (OP == OP_CSR2 && r0 + q == 1) ? op.v1 : op.v0;
 #pragma unroll
     for (int c = 0; c < VW; ++c) acc[c] = T(0);
-    for (int k0 = 0; k0 < len; k0 += kChunk) {
-        int col[kChunk];
-        T v[kChunk][NL];
+    for (int k0 = 0; k0 < len; k0 += CH) {
+        int col[CH];
+        T v[CH][NL];
 #pragma unroll
-        for (int j = 0; j < kChunk; ++j) {
+        for (int j = 0; j < CH; ++j) {
             const int64_t idx = base + int64_t(k0 + j) * 32;
             const bool ok = k0 + j < len;
             col[j] = ok ? int(__ldg(m.sell_col + idx)) : 0;
@@ -175,7 +181,7 @@ __device__ __forceinline__ void sell_row(const MeshDev& m, const OpParams<T>& op
         }
         if constexpr (kLocal) {
 #pragma unroll
-            for (int j = 0; j < kChunk; ++j) {
+            for (int j = 0; j < CH; ++j) {
                 const bool in = col[j] < nloc;
                 col[j] = in ? col[j] : 0;
 #pragma unroll
@@ -183,7 +189,7 @@ __device__ __forceinline__ void sell_row(const MeshDev& m, const OpParams<T>& op
             }
         }
 #pragma unroll
-        for (int j = 0; j < kChunk; ++j) {
+        for (int j = 0; j < CH; ++j) {
             T xv[VW];
             vld(xs + col[j] * R + r0, xv);
 #pragma unroll
