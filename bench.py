@@ -476,6 +476,72 @@ def recon_leg(Q, torch, n: int = 64, seed: int = 7, nlin: int = 5, nlsqr: int = 
     return out
 
 
+def illumination_study(Q, n: int = 38, seed: int = 17):
+    """The illumination-count study of Test 2 (Sec. 5) on its synthetic
+    stand-in (qpat_synth.Test2Config: 11 mm cube, shell/ball/cross target,
+    whole-face characteristic-function fluxes): Algorithm 1 with the
+    library's default parameters and the paper's stopping rules, for the
+    illumination sets the paper compares (one face; two adjacent; two
+    opposite; three around a corner; three spread).  Data: the library's own
+    FP64 forward on the nested (2n-1)^3 mesh, injected onto the coarse
+    nodes, plus seeded 1 % noise (sigma floor 1e-3 max|h|), one draw per
+    illumination shared by every set.  Reports the relative L2 errors of the
+    reconstruction and of the fitted constant background, linearisations,
+    LSQR rounds and wall time."""
+    faces = ("btm", "rgt", "top", "bck")
+    fine = S.Test2Config(2 * n - 1, faces)
+    xf, tf = fine.mesh()
+    mf = Q.qpat_mesh(xf, tf)
+    kf, muf = fine.coefficients(xf)
+    flf = np.stack([Q.qpat_flux_patch(mf, p.center, p.normal, p.half_w, p.amp) for p in fine.patches])
+    _, hf = Q.qpat_forward(mf, kf, muf, flf, Q.qpat_default_params(precision=0))
+    mf.close()
+    h = hf[:, S.fine_to_coarse_index(n)]
+    sig = 0.01 * np.abs(h) + 1e-3 * np.abs(h).max()
+    chi = h + sig * S.noise_draws(seed, h.shape)
+    coarse = S.Test2Config(n, faces)
+    xyz, tets = coarse.mesh()
+    kap_t, mu_t = coarse.coefficients(xyz)
+    mesh = Q.qpat_mesh(xyz, tets)
+    flux = np.stack([Q.qpat_flux_patch(mesh, p.center, p.normal, p.half_w, p.amp) for p in coarse.patches])
+    rel = lambda a, b: float(np.linalg.norm(a - b) / np.linalg.norm(b))
+    Q.qpat_reconstruct(mesh, flux[:1], chi[:1], sig[:1],
+                       Q.qpat_default_params(precision=0, max_lin=1, max_lsqr=2, fixed_counts=1))  # warm-up
+    bnd = np.zeros(mesh.N, dtype=bool)
+    bnd[np.unique(mesh.faces())] = True
+    inner = ~bnd
+    out = {"study": "illuminations (Test 2 stand-in)", "n": n, "nodes": mesh.N, "fine_nodes": fine.N,
+           "noise": "1 % + floor 1e-3 max|h|", "params": "library defaults (paper's stopping rules), FP64",
+           "runs": {}}
+    for label, cap in (("lsqr cap 50 (default)", 50), ("lsqr cap 20", 20)):
+        res = {}
+        for st in (("btm",), ("btm", "rgt"), ("btm", "top"), ("btm", "rgt", "bck"), ("btm", "top", "bck")):
+            ix = [faces.index(f) for f in st]
+            t0 = time.perf_counter()
+            try:
+                kap, mu, rep = Q.qpat_reconstruct(mesh, flux[ix], chi[ix], sig[ix],
+                                                  Q.qpat_default_params(precision=0, max_lsqr=cap))
+            except Q.QpatError as e:   # e.g. a K solve at an iterate with exp(30)-scale kappa jumps
+                res["+".join(st)] = {"failed": str(e), "wall_s": time.perf_counter() - t0}
+                continue
+            dt = time.perf_counter() - t0
+            kt = np.log(kap / rep.kappa0)
+            res["+".join(st)] = {
+                "e_kappa": rel(kap, kap_t), "e_mu": rel(mu, mu_t),
+                "e_kappa_interior": rel(kap[inner], kap_t[inner]), "e_mu_interior": rel(mu[inner], mu_t[inner]),
+                "e_kappa_background": rel(np.full_like(kap_t, rep.kappa0), kap_t),
+                "e_mu_background": rel(np.full_like(mu_t, rep.mu0), mu_t),
+                "max_abs_log_kappa_ratio": {"interior": float(np.abs(kt[inner]).max()),
+                                            "boundary": float(np.abs(kt[bnd]).max())},
+                "kappa0": float(rep.kappa0), "mu0": float(rep.mu0),
+                "linearisations": int(rep.linearisations), "accepted_last": bool(rep.accepted_last),
+                "lsqr_rounds": [int(v) for v in rep.lsqr_iters[:rep.linearisations]],
+                "wall_s": dt}
+        out["runs"][label] = res
+    mesh.close()
+    return out
+
+
 def learned_leg(Q, torch, n: int = 32, train_phantoms: int = 18, steps: int = 150):
     """Learned initial guess: the BF16 U-Net trained on the library's own
     FP32 + refinement forward solves of `train_phantoms` seeded phantoms on an
@@ -659,6 +725,9 @@ def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--profile-case", action="store_true",
                     help="run the fixed solve sequence used for ncu captures and exit")
+    ap.add_argument("--illumination-study", action="store_true",
+                    help="run the Test 2 illumination-count study on its synthetic stand-in and exit")
+    ap.add_argument("--study-n", type=int, default=38, help="nodes per side of the study's coarse mesh")
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
@@ -678,6 +747,10 @@ def main():
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
+    if args.illumination_study:
+        import paper_1512_02796_gb300 as Q
+        print(json.dumps(illumination_study(Q, n=args.study_n)), flush=True)
+        return
     if args.profile_case:
         run_profile_case(args)
     elif args.impl == "reference":

@@ -291,6 +291,75 @@ def uneven_batch(count: int = 32, seed: int = 3000, nmin: int = 16, nmax: int = 
     return out
 
 
+# ---------------------------------------------------------------- Test 2 stand-in
+
+TEST2_FACES = {"btm": (2, 0), "top": (2, 1), "rgt": (0, 1), "bck": (1, 1)}
+
+
+def test2_phantom(xyz: np.ndarray, L: float = 11.0, half_thick: float = 0.5, half_width: float = 1.0):
+    """Nodal (kappa, mu) of the Test 2 target of Sec. 5 on the cube [0, L]^3
+    (the paper centres it at the origin; here centre = (L/2, L/2, L/2)).
+
+    mu: background 0.015, a spherical shell 4 <= r <= 5 at 0.02, and a
+    cross-shaped inclusion lying along the plane z = x at 0.01 (the cross
+    wins where they meet).  kappa: background 0.3, a ball r <= 3 at 0.2, and
+    a cross along the plane z = -x at 0.4 (the cross wins).  The paper shows
+    the crosses only in figures; here a cross is a plus sign of two bars,
+    half width `half_width`, lying in its plane (one along y, one along the
+    in-plane diagonal, both through the centre and across the cube), with
+    half thickness `half_thick` normal to the plane.
+    """
+    p = np.asarray(xyz, dtype=np.float64) - L / 2.0
+    x, y, z = p[:, 0], p[:, 1], p[:, 2]
+    r = np.sqrt(x * x + y * y + z * z)
+    s2 = np.sqrt(2.0)
+
+    def cross(normal_dist, inplane):
+        return (np.abs(normal_dist) <= half_thick) & ((np.abs(inplane) <= half_width) | (np.abs(y) <= half_width))
+
+    cross_mu = cross((z - x) / s2, (x + z) / s2)     # plane z = x
+    cross_kappa = cross((z + x) / s2, (x - z) / s2)  # plane z = -x
+    mu = np.full(p.shape[0], 0.015)
+    mu[(r >= 4.0) & (r <= 5.0)] = 0.02
+    mu[cross_mu] = 0.01
+    kappa = np.full(p.shape[0], 0.3)
+    kappa[r <= 3.0] = 0.2
+    kappa[cross_kappa] = 0.4
+    return kappa, mu
+
+
+@dataclasses.dataclass
+class Test2Config:
+    """Test 2 of Sec. 5 on a Kuhn cube of n^3 nodes over [0, 11]^3 mm, lit
+    through whole faces (characteristic functions, amplitude 1): any subset
+    of btm (z = 0), top (z = L), rgt (x = L) and bck (y = L)."""
+    n: int
+    illum: Tuple[str, ...] = ("btm",)
+    L: float = 11.0
+
+    @property
+    def name(self) -> str:
+        return f"test2_n{self.n}_" + "+".join(self.illum)
+
+    @property
+    def N(self) -> int:
+        return self.n ** 3
+
+    @property
+    def K(self) -> int:
+        return len(self.illum)
+
+    @property
+    def patches(self) -> List[Patch]:
+        return _face_patches(self.L, self.L / 2.0, [TEST2_FACES[f] for f in self.illum])
+
+    def mesh(self):
+        return kuhn_cube(self.n, self.L)
+
+    def coefficients(self, xyz: np.ndarray):
+        return test2_phantom(xyz, self.L)
+
+
 def noise_draws(seed: int, shape) -> np.ndarray:
     """Standard normal draws for the measurement noise eta (Sec. 5, Test 1):
     chi = h + 0.01 |h| * xi with xi from here."""
