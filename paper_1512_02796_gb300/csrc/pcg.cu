@@ -360,12 +360,17 @@ __device__ __forceinline__ void cheb_coeffs(double hi, int deg, double* acoef) {
         }
         rho = rn;
     }
-    for (int j = 0; j <= deg; ++j) acoef[j] = P[j];
+    // p / |a_deg| instead of p: a positive factor in M^-1 leaves the PCG
+    // iterates x unchanged (beta is a ratio of r.z values, alpha absorbs the
+    // scale of the direction), and the Horner start w = +-v then needs no
+    // multiply.  acoef[deg] = +-1 carries the sign of a_deg.
+    for (int j = 0; j <= deg; ++j) acoef[j] = P[j] / fabs(P[deg]);
 }
 
 // The deg Horner steps on one patch.  On entry every thread has written, for
-// its owned rows (offset li * R + r0), cV = v = D^-1 r and cW0 = a_deg v; on
-// exit the returned buffer holds z.  Block-wide barriers separate the steps.
+// its owned rows (offset li * R + r0), cV = v = D^-1 r and cW0 = a_deg v
+// (a_deg = +-1 after the normalisation in cheb_coeffs); on exit the returned
+// buffer holds z.  Block-wide barriers separate the steps.
 template <typename T, int R, int VW, int NP, int OP>
 __device__ __forceinline__ T* cheb_patch(const PcgArgs<T>& a, int ob, int nown, int r0, int deg, const double* acoef,
                                          const T* cV, T* cW0, T* cW1) {
@@ -425,6 +430,7 @@ __device__ __forceinline__ void pcg_body(const PcgArgs<T>& a, const int cta, con
                                                               // the Jacobi kernel's registers unchanged
     __shared__ double pco[kMaxPolyDegree + 1];
     T *cV = nullptr, *cW0 = nullptr, *cW1 = nullptr;
+    bool top_neg = false;  // a_deg = -1: the Horner start is -v
     if (deg > 0) {
         const size_t stride = size_t(m.max_own) * R;
         cV = reinterpret_cast<T*>(smem_raw);
@@ -432,8 +438,8 @@ __device__ __forceinline__ void pcg_body(const PcgArgs<T>& a, const int cta, con
         cW1 = cW0 + stride;
         if (threadIdx.x == 0) cheb_coeffs(__ldcg(a.poly_hi), deg, pco);
         __syncthreads();
+        top_neg = pco[deg] < 0.0;
     }
-    const T a_top = deg > 0 ? T(pco[deg]) : T(1);
 
     // ---- initial residual r = b (x0 = 0)
     {
@@ -461,7 +467,7 @@ __device__ __forceinline__ void pcg_body(const PcgArgs<T>& a, const int cta, con
                     const int o = (i / NP) * R + r0;
                     vst(cV + o, zv);
 #pragma unroll
-                    for (int c = 0; c < VW; ++c) zv[c] *= a_top;
+                    for (int c = 0; c < VW; ++c) zv[c] = top_neg ? -zv[c] : zv[c];
                     vst(cW0 + o, zv);
                 } else if (a.z) {
                     vst(a.z + e, zv);
@@ -527,11 +533,12 @@ __device__ __forceinline__ void pcg_body(const PcgArgs<T>& a, const int cta, con
 
         T* pc = ((it + off) & 1) ? a.p1 : a.p0;
         const T* pp = ((it + off) & 1) ? a.p0 : a.p1;
-        T bt[VW], zc[VW];
+        T bt[VW];
+        bool zon[VW];  // a select, not an FP64 multiply by 0 / 1
 #pragma unroll
         for (int c = 0; c < VW; ++c) {
             bt[c] = T(beta[r0 + c]);
-            zc[c] = T(zcoef[r0 + c]);
+            zon[c] = zcoef[r0 + c] != 0.0;
         }
 
         // ---- phase A: p = D^-1 r + beta p_old on touched nodes, q = A p on owned nodes
@@ -565,7 +572,8 @@ __device__ __forceinline__ void pcg_body(const PcgArgs<T>& a, const int cta, con
                     T pv[VW];
 #pragma unroll
                     for (int c = 0; c < VW; ++c)
-                        pv[c] = zc[c] * (zs ? rv[u][c] : d[u][c] * rv[u][c]) + (prev ? bt[c] * po[u][c] : T(0));
+                        pv[c] = (zon[c] ? (zs ? rv[u][c] : d[u][c] * rv[u][c]) : T(0)) +
+                                (prev ? bt[c] * po[u][c] : T(0));
                     if (u == 0 || i0 + u * int(blockDim.x) < nt * NP) vst(s.xin + li[u] * R + r0, pv);
                 }
             }
@@ -656,7 +664,7 @@ __device__ __forceinline__ void pcg_body(const PcgArgs<T>& a, const int cta, con
                         const int o = (i / NP) * R + r0;
                         vst(cV + o, zv);
 #pragma unroll
-                        for (int c = 0; c < VW; ++c) zv[c] *= a_top;
+                        for (int c = 0; c < VW; ++c) zv[c] = top_neg ? -zv[c] : zv[c];
                         vst(cW0 + o, zv);
                     } else if (zs) {
                         vst(a.z + e, zv);
