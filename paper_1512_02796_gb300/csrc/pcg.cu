@@ -1,16 +1,17 @@
-// Persistent fused Jacobi-preconditioned conjugate gradients.
+// Persistent fused preconditioned conjugate gradients.
 //
 // The paper solves with K (Appendix) and with M_delta (Sec. 4, one solve per
 // LSQR round) but does not name a solver; both are symmetric positive
 // definite, so this library uses preconditioned conjugate gradients.  One
 // cooperative launch runs the whole iteration: every CTA owns a fixed set of
 // node patches and, per iteration,
-//   phase A: forms p = D^-1 r + beta p_old on its touched nodes in shared
-//            memory (the z = D^-1 r vector is never stored), writes p on its
-//            owned nodes, applies the operator and keeps q = A p on its
-//            owned nodes, accumulating p.q;
-//   phase B: x += alpha p, r -= alpha q on its owned nodes, accumulating
-//            r.D^-1 r and r.r.
+//   phase A: forms p = z + beta p_old on its touched nodes in shared memory
+//            (z = M^-1 r read from its owner, or D^-1 r formed on the fly),
+//            writes p on its owned nodes, applies the operator and keeps
+//            q = A p on its owned nodes, accumulating p.q;
+//   phase B: x += alpha p, r -= alpha q on its owned nodes, z = M^-1 r
+//            (Jacobi D^-1, or the patch-local Chebyshev polynomial below),
+//            accumulating r.z and r.r.
 // Each phase ends with a grid-wide reduction behind a bounded grid barrier:
 // every CTA writes its partial sums, the last CTA to arrive adds all of them
 // in a fixed order, publishes the totals and releases the others, so every
