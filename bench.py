@@ -41,6 +41,20 @@ def env_rank():
         os.environ.get("LOCAL_RANK", "0"))
 
 
+def whole_job_rate(local_ms: float, steps: int, world: int, device: str = "cuda"):
+    """Whole-job timing of the timed region: the maximum over ranks of each
+    rank's summed step time (all ranks wait for the slowest), and the
+    aggregate rate world * steps per second of that time (every rank does
+    the same per-rank work, weak scaling).  Returns (ms, steps per second)."""
+    tot_ms = float(local_ms)
+    if world > 1:
+        import torch
+        t = torch.tensor([tot_ms], dtype=torch.float64, device=device)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        tot_ms = float(t.item())
+    return tot_ms, world * steps / (tot_ms / 1e3)
+
+
 def kernel_source_sha1() -> str:
     """Hash of the PCG kernel sources and of the code that lays out their
     operands (a stored ncu traffic figure is only reported while these are
@@ -243,12 +257,7 @@ def run_ours(args):
     gpu_launches = Q.qpat_launch_count() - launches0   # library kernels launched in the timed region
     clocks = clk.stop()
     step_ms = [a.elapsed_time(b) for a, b in ev]
-    tot_ms = sum(step_ms)
-    if world > 1:
-        t = torch.tensor([tot_ms], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        tot_ms = float(t.item())
-    value = world * args.steps / (tot_ms / 1e3)
+    tot_ms, value = whole_job_rate(sum(step_ms), args.steps, world)
 
 
     # ---- end to end through the host-pointer ABI (copies inside the timed region)
