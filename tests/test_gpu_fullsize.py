@@ -89,3 +89,34 @@ def test_pair_adjoint_identity_full_size(big, precision):
     a = float(np.sum(oj.cpu().numpy() * t))
     b = float(s @ ov.cpu().numpy())
     assert abs(a - b) <= 1e-10 * abs(a)
+
+
+@pytest.mark.parametrize("deg", [0, 2])
+def test_prior_solve_full_size(big, deg):
+    """The M_delta solve as bench.py times it (two blocks, lagged weights of
+    log(kappa / median), log(mu / median), library T, b/a, delta; degree 2 is
+    the default, 0 Jacobi): normwise backward error against the oracle's
+    M_delta, and the two preconditioners agree within the conditioning of the
+    solve (they run the same system to the same residual)."""
+    N = big.N
+    kt = np.log(big.kappa / np.median(big.kappa))
+    mt = np.log(big.mu / np.median(big.mu))
+    rhs = np.random.default_rng(123).standard_normal(2 * N)
+    prm = Q.qpat_default_params(prior_poly_degree=deg)
+    out = torch.empty(2 * N, dtype=torch.float64, device="cuda")
+    big.lib.reset_stats()
+    Q.qpat_prior_solve_dev(big.lib, big.T(kt), big.T(mt), big.T(rhs), out, prm)
+    torch.cuda.synchronize()
+    iters = big.lib.stats()["pcg_iters"]
+    x = out.cpu().numpy()
+    Md = O.prior_matrix(big.om, kt, mt, prm.T, prm.b_over_a, prm.delta)
+    Anorm = abs(Md).sum(axis=0).max()
+    eta = np.linalg.norm(Md @ x - rhs, 1) / (Anorm * np.linalg.norm(x, 1) + np.linalg.norm(rhs, 1))
+    assert eta < 1e-13
+    if not hasattr(big, "prior_x"):
+        big.prior_x = {}
+    big.prior_x[deg] = (x, iters)
+    if len(big.prior_x) == 2:
+        (x0, it0), (x2, it2) = big.prior_x[0], big.prior_x[2]
+        assert rel(x2, x0) < 1e-8
+        assert it2 < 0.7 * it0   # the patch-local polynomial roughly halves the count (1400 -> 710)
