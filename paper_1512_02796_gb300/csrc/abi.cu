@@ -554,6 +554,29 @@ int qpat_mesh_host_info(const double* xyz, int64_t N, const int32_t* tets, int64
             if (!owned) return fail(QPAT_EINVAL, "host check: patch tet without owned node");
         }
         dup += h.tet_ptr[p + 1] - h.tet_ptr[p];
+        // colours: they tile the patch's tet (face) list in order, and no two
+        // elements of one colour share an owned vertex
+        auto check_colours = [&](const std::vector<int32_t>& beg, const std::vector<int32_t>& off,
+                                 const std::vector<int32_t>& ptr, const std::vector<uint16_t>& loc, int nv) -> bool {
+            const int j0 = beg[p], j1 = beg[p + 1];
+            if (j1 <= j0 || off[j0] != ptr[p] || off[j1 - 1] != ptr[p + 1]) return false;
+            std::vector<int> seen(size_t(oe - ob), -1);
+            for (int j = j0; j + 1 < j1; ++j) {
+                if (off[j + 1] < off[j]) return false;
+                for (int e = off[j]; e < off[j + 1]; ++e)
+                    for (int a = 0; a < nv; ++a) {
+                        const int li = loc[4 * size_t(e) + a];
+                        if (li < oe - ob) {
+                            if (seen[li] == j) return false;
+                            seen[li] = j;
+                        }
+                    }
+            }
+            return true;
+        };
+        if (!check_colours(h.tcol_beg, h.tcol_off, h.tet_ptr, h.tet_loc, 4) ||
+            !check_colours(h.fcol_beg, h.fcol_off, h.face_ptr, h.face_loc, 3))
+            return fail(QPAT_EINVAL, "host check: element colours");
     }
     info8[0] = h.F;
     info8[1] = h.P;

@@ -215,13 +215,40 @@ __device__ __forceinline__ void load_tet(const PatchSmem<T, R>& s, const ushort4
     }
 }
 
+// f(e) for every element of patch p, one colour after the other with a
+// block-wide barrier after each (beg / off: HostMesh's tcol_* or fcol_*).
+// Elements of one colour share no owned vertex, so the sums into owned rows
+// need no atomics and add up in the same order on every run.
+template <class F>
+__device__ __forceinline__ void for_each_coloured(const int* beg, const int* off, int p, F&& f) {
+    const int j0 = __ldg(beg + p), j1 = __ldg(beg + p + 1);
+    for (int j = j0; j + 1 < j1; ++j) {
+        const int e1 = __ldg(off + j + 1);
+        for (int e = __ldg(off + j) + threadIdx.x; e < e1; e += blockDim.x) f(e);
+        __syncthreads();
+    }
+}
+
+// y += v into an owned-row accumulator: plain in a coloured loop, atomic otherwise
+template <bool kColoured, typename T>
+__device__ __forceinline__ void acc_add(T* y, T v) {
+    if constexpr (kColoured) {
+        *y += v;
+    } else {
+        atomicAdd(y, v);
+    }
+}
+
 // Element loop of one patch: yout[owned] += (operator) xin.  xin, the
 // coordinates and the coefficients must be staged and yout zeroed.
-template <typename T, int R, int OP>
+// kColoured: colour by colour (run-to-run identical sums, a barrier per
+// colour); otherwise all elements at once with shared-memory atomics (the
+// matrix-free FP32 PCG, where a barrier per colour and iteration would cost
+// more than it buys).
+template <typename T, int R, int OP, bool kColoured = false>
 __device__ __forceinline__ void patch_elements(const MeshDev& m, int p, int nown, const PatchSmem<T, R>& s,
                                                const OpParams<T>& op) {
-    const int tb = __ldg(m.tet_ptr + p), te = __ldg(m.tet_ptr + p + 1);
-    for (int t = tb + threadIdx.x; t < te; t += blockDim.x) {
+    auto tet = [&](int t) {
         const ushort4 lv = m.tet_loc[t];
         const int v[4] = {lv.x, lv.y, lv.z, lv.w};
         T pc[4][3], c[4][3], ad;
@@ -247,7 +274,7 @@ __device__ __forceinline__ void patch_elements(const MeshDev& m, int p, int nown
                 mass_rows_add(mu, Sm, x, vm, y);
 #pragma unroll
                 for (int a = 0; a < 4; ++a)
-                    if (v[a] < nown) atomicAdd(&s.yout[v[a] * R + r], y[a]);
+                    if (v[a] < nown) acc_add<kColoured>(&s.yout[v[a] * R + r], y[a]);
             }
         } else {
             static_assert(R == 2, "the prior operator has two blocks");
@@ -270,14 +297,19 @@ __device__ __forceinline__ void patch_elements(const MeshDev& m, int p, int nown
                 stiff_rows(c, G, sk, y);
 #pragma unroll
                 for (int a = 0; a < 4; ++a)
-                    if (v[a] < nown) atomicAdd(&s.yout[v[a] * 2 + r], y[a]);
+                    if (v[a] < nown) acc_add<kColoured>(&s.yout[v[a] * 2 + r], y[a]);
             }
         }
+    };
+    if constexpr (kColoured) {
+        for_each_coloured(m.tcol_beg, m.tcol_off, p, tet);
+    } else {
+        const int tb = __ldg(m.tet_ptr + p), te = __ldg(m.tet_ptr + p + 1);
+        for (int t = tb + threadIdx.x; t < te; t += blockDim.x) tet(t);
     }
     if constexpr (OP == OP_K) {
         if (op.robin) {
-            const int fb = __ldg(m.face_ptr + p), fe = __ldg(m.face_ptr + p + 1);
-            for (int f = fb + threadIdx.x; f < fe; f += blockDim.x) {
+            auto face = [&](int f) {
                 const ushort4 lv = m.face_loc[f];
                 const int v[3] = {lv.x, lv.y, lv.z};
                 const T w = face_area_of<T>(m, f) / T(24);
@@ -289,8 +321,14 @@ __device__ __forceinline__ void patch_elements(const MeshDev& m, int p, int nown
                     const T Sx = x[0] + x[1] + x[2];
 #pragma unroll
                     for (int a = 0; a < 3; ++a)
-                        if (v[a] < nown) atomicAdd(&s.yout[v[a] * R + r], w * (Sx + x[a]));
+                        if (v[a] < nown) acc_add<kColoured>(&s.yout[v[a] * R + r], w * (Sx + x[a]));
                 }
+            };
+            if constexpr (kColoured) {
+                for_each_coloured(m.fcol_beg, m.fcol_off, p, face);
+            } else {
+                const int fb = __ldg(m.face_ptr + p), fe = __ldg(m.face_ptr + p + 1);
+                for (int f = fb + threadIdx.x; f < fe; f += blockDim.x) face(f);
             }
         }
     }

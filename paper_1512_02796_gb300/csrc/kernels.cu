@@ -28,7 +28,7 @@ __global__ void __launch_bounds__(kThreads) k_apply(MeshDev m, OpParams<T> op, T
     }
     for (int i = threadIdx.x; i < nown * R; i += blockDim.x) s.yout[i] = T(0);
     __syncthreads();
-    patch_elements<T, R, OP>(m, p, nown, s, op);
+    patch_elements<T, R, OP, true>(m, p, nown, s, op);  // coloured: run-to-run identical
     __syncthreads();
     for (int i = threadIdx.x; i < nown * R; i += blockDim.x) {
         T v = s.yout[i];
@@ -77,7 +77,8 @@ __global__ void __launch_bounds__(kThreads) k_diag_K(MeshDev m, const double* __
     stage_static<double, 1>(m, nb, nt, s, op);
     for (int i = threadIdx.x; i < nown; i += blockDim.x) s.yout[i] = 0.0;
     __syncthreads();
-    for (int t = m.tet_ptr[p] + threadIdx.x; t < m.tet_ptr[p + 1]; t += blockDim.x) {
+    // colour by colour: plain sums in a fixed order (see for_each_coloured)
+    for_each_coloured(m.tcol_beg, m.tcol_off, p, [&](int t) {
         const ushort4 lv = m.tet_loc[t];
         const int v[4] = {lv.x, lv.y, lv.z, lv.w};
         double pc[4][3], c[4][3], ad;
@@ -92,17 +93,16 @@ __global__ void __launch_bounds__(kThreads) k_diag_K(MeshDev m, const double* __
         for (int a = 0; a < 4; ++a)
             if (v[a] < nown) {
                 const double c2 = c[a][0] * c[a][0] + c[a][1] * c[a][1] + c[a][2] * c[a][2];
-                atomicAdd(&s.yout[v[a]], sk * c2 + vm * (2.0 * Sm + 4.0 * s.c2[v[a]]));
+                s.yout[v[a]] += sk * c2 + vm * (2.0 * Sm + 4.0 * s.c2[v[a]]);
             }
-    }
-    for (int f = m.face_ptr[p] + threadIdx.x; f < m.face_ptr[p + 1]; f += blockDim.x) {
+    });
+    for_each_coloured(m.fcol_beg, m.fcol_off, p, [&](int f) {
         const ushort4 lv = m.face_loc[f];
         const int v[3] = {lv.x, lv.y, lv.z};
         const double w = m.pface_area64[f] / 12.0;
         for (int a = 0; a < 3; ++a)
-            if (v[a] < nown) atomicAdd(&s.yout[v[a]], w);
-    }
-    __syncthreads();
+            if (v[a] < nown) s.yout[v[a]] += w;
+    });
     for (int i = threadIdx.x; i < nown; i += blockDim.x) {
         const double d = 1.0 / s.yout[i];
         inv64[ob + i] = d;
@@ -125,7 +125,7 @@ __global__ void __launch_bounds__(kThreads) k_diag_prior(MeshDev m, const double
     stage_static<double, 2>(m, nb, nt, s, op);
     for (int i = threadIdx.x; i < 2 * nown; i += blockDim.x) s.yout[i] = 0.0;
     __syncthreads();
-    for (int t = m.tet_ptr[p] + threadIdx.x; t < m.tet_ptr[p + 1]; t += blockDim.x) {
+    for_each_coloured(m.tcol_beg, m.tcol_off, p, [&](int t) {
         const ushort4 lv = m.tet_loc[t];
         const int v[4] = {lv.x, lv.y, lv.z, lv.w};
         double pc[4][3], c[4][3], ad;
@@ -140,11 +140,9 @@ __global__ void __launch_bounds__(kThreads) k_diag_prior(MeshDev m, const double
             const double cT = prior_weight<double>(kind, g2, inv_T2, q);
             const double sk = (r == 0 ? 1.0 : scale1) * cT / (6.0 * ad);
             for (int a = 0; a < 4; ++a)
-                if (v[a] < nown)
-                    atomicAdd(&s.yout[2 * v[a] + r], sk * (c[a][0] * c[a][0] + c[a][1] * c[a][1] + c[a][2] * c[a][2]));
+                if (v[a] < nown) s.yout[2 * v[a] + r] += sk * (c[a][0] * c[a][0] + c[a][1] * c[a][1] + c[a][2] * c[a][2]);
         }
-    }
-    __syncthreads();
+    });
     for (int i = threadIdx.x; i < 2 * nown; i += blockDim.x) {
         const double d = 1.0 / (s.yout[i] + delta);
         inv64[2 * ob + i] = d;
@@ -168,7 +166,9 @@ __global__ void __launch_bounds__(kThreads) k_assemble_K(MeshDev m, const double
     OpParams<double> op{kappa, mu, 0, 0, 0, 1};
     stage_static<double, 1>(m, nb, nt, s, op);
     __syncthreads();
-    for (int t = m.tet_ptr[p] + threadIdx.x; t < m.tet_ptr[p + 1]; t += blockDim.x) {
+    // colour by colour: each owned row takes one tet's terms at a time, plain
+    // adds in a fixed order (the values are identical on every run)
+    for_each_coloured(m.tcol_beg, m.tcol_off, p, [&](int t) {
         const ushort4 lv = m.tet_loc[t];
         const int v[4] = {lv.x, lv.y, lv.z, lv.w};
         double pc[4][3], c[4][3], ad;
@@ -187,11 +187,11 @@ __global__ void __launch_bounds__(kThreads) k_assemble_K(MeshDev m, const double
                 const double st = sk * (c[a][0] * c[b][0] + c[a][1] * c[b][1] + c[a][2] * c[b][2]);
                 const double ms = a == b ? 2.0 * Sm + 4.0 * s.c2[v[a]] : Sm + s.c2[v[a]] + s.c2[v[b]];
                 const int64_t idx = sell_slot(m, g, v[b]);
-                if (idx >= 0) atomicAdd(val + idx, st + vm * ms);
+                if (idx >= 0) val[idx] += st + vm * ms;
             }
         }
-    }
-    for (int f = m.face_ptr[p] + threadIdx.x; f < m.face_ptr[p + 1]; f += blockDim.x) {
+    });
+    for_each_coloured(m.fcol_beg, m.fcol_off, p, [&](int f) {
         const ushort4 lv = m.face_loc[f];
         const int v[3] = {lv.x, lv.y, lv.z};
         const double w = m.pface_area64[f] / 24.0;
@@ -199,10 +199,10 @@ __global__ void __launch_bounds__(kThreads) k_assemble_K(MeshDev m, const double
             if (v[a] >= nown) continue;
             for (int b = 0; b < 3; ++b) {
                 const int64_t idx = sell_slot(m, ob + v[a], v[b]);
-                if (idx >= 0) atomicAdd(val + idx, a == b ? 2.0 * w : w);
+                if (idx >= 0) val[idx] += a == b ? 2.0 * w : w;
             }
         }
-    }
+    });
 }
 
 // Prior blocks: A^r_ab = scale_r c_T(u_r) c_a.c_b / (6 |det|), c_T = r'(t)/t at t = |grad u_r| (prior_weight)
@@ -219,7 +219,7 @@ __global__ void __launch_bounds__(kThreads) k_assemble_prior(MeshDev m, const do
     OpParams<double> op{u1, u2, 0, 0, 0, 0};
     stage_static<double, 1>(m, nb, nt, s, op);
     __syncthreads();
-    for (int t = m.tet_ptr[p] + threadIdx.x; t < m.tet_ptr[p + 1]; t += blockDim.x) {
+    for_each_coloured(m.tcol_beg, m.tcol_off, p, [&](int t) {
         const ushort4 lv = m.tet_loc[t];
         const int v[4] = {lv.x, lv.y, lv.z, lv.w};
         double pc[4][3], c[4][3], ad;
@@ -241,12 +241,12 @@ __global__ void __launch_bounds__(kThreads) k_assemble_prior(MeshDev m, const do
                 const double cc = c[a][0] * c[b][0] + c[a][1] * c[b][1] + c[a][2] * c[b][2];
                 const int64_t idx = sell_slot(m, g, v[b]);
                 if (idx >= 0) {
-                    atomicAdd(val0 + idx, coef[0] * cc);
-                    atomicAdd(val1 + idx, coef[1] * cc);
+                    val0[idx] += coef[0] * cc;
+                    val1[idx] += coef[1] * cc;
                 }
             }
         }
-    }
+    });
 }
 
 // val_r[diag] += shift ; inv[g * NV + r] = 1 / val_r[diag]  (FP64, optional FP32 copy).
@@ -350,7 +350,8 @@ __global__ void __launch_bounds__(kThreads) k_vjp_accum(MeshDev m, const T* __re
     }
     for (int i = threadIdx.x; i < 2 * nown; i += blockDim.x) sy[i] = T(0);
     __syncthreads();
-    for (int t = m.tet_ptr[p] + threadIdx.x; t < m.tet_ptr[p + 1]; t += blockDim.x) {
+    // colour by colour: plain sums in a fixed order (run-to-run identical)
+    for_each_coloured(m.tcol_beg, m.tcol_off, p, [&](int t) {
         const ushort4 lv = m.tet_loc[t];
         const int v[4] = {lv.x, lv.y, lv.z, lv.w};
         T pc[4][3], c[4][3], ad;
@@ -376,11 +377,10 @@ __global__ void __launch_bounds__(kThreads) k_vjp_accum(MeshDev m, const T* __re
         g1 *= s1;
         for (int a = 0; a < 4; ++a)
             if (v[a] < nown) {
-                atomicAdd(&sy[2 * v[a]], -g1);
-                atomicAdd(&sy[2 * v[a] + 1], -m4[a]);
+                sy[2 * v[a]] -= g1;
+                sy[2 * v[a] + 1] -= m4[a];
             }
-    }
-    __syncthreads();
+    });
     for (int i = threadIdx.x; i < 2 * nown; i += blockDim.x) {
         T* dst = y + size_t(ob) * 2 + i;
         *dst = accumulate ? *dst + sy[i] : sy[i];
@@ -399,15 +399,20 @@ cudaError_t vjp_t(const MeshDev& m, const T* phi, const T* z, T* y, int ldk, int
 }
 
 // ---------------------------------------------------------------- load vector
-// f_i += 2 Phi_F |F| / 3 for the three vertices of every lit face
+// f_i += sum over the boundary faces F of node i of 2 Phi_F |F| / 3, gathered
+// per (node, illumination) over the node's faces in a fixed order
 __global__ void k_load(MeshDev m, int K, int R, const double* __restrict__ flux, double* f) {
-    const int64_t total = int64_t(m.F) * K;
+    const int64_t total = int64_t(m.N) * K;
     for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < total; i += int64_t(gridDim.x) * blockDim.x) {
-        const int k = int(i / m.F), fi = int(i % m.F);
-        const double v = flux[i];
-        if (v == 0.0) continue;
-        const double c = 2.0 * v * m.farea[fi] / 3.0;
-        for (int a = 0; a < 3; ++a) atomicAdd(&f[size_t(m.faces_lib[3 * fi + a]) * R + k], c);
+        const int g = int(i / K), k = int(i % K);
+        const int q0 = __ldg(m.nface_ptr + g), q1 = __ldg(m.nface_ptr + g + 1);
+        if (q0 == q1) continue;
+        double acc = 0.0;
+        for (int q = q0; q < q1; ++q) {
+            const int fi = __ldg(m.nface + q);
+            acc += 2.0 * __ldg(flux + size_t(k) * m.F + fi) * __ldg(m.farea + fi) / 3.0;
+        }
+        f[size_t(g) * R + k] += acc;
     }
 }
 
@@ -628,7 +633,7 @@ cudaError_t launch_vjp_accum(const MeshDev& m, int K, const T* phi, const T* z, 
 
 cudaError_t launch_load(const MeshDev& m, int K, int R, const double* flux, double* f, cudaStream_t s) {
     qpat::note_launch(1);
-    k_load<<<grid_for(int64_t(m.F) * K), 256, 0, s>>>(m, K, R, flux, f);
+    k_load<<<grid_for(int64_t(m.N) * K), 256, 0, s>>>(m, K, R, flux, f);
     return cudaGetLastError();
 }
 

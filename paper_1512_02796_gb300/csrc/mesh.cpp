@@ -161,6 +161,8 @@ std::string build_host_mesh(const double* xyz, int64_t N, const int32_t* tets,
         for (int64_t f = 0; f < m.F; ++f)
             for (int k = 0; k < 3; ++k) nf[fill[m.faces_lib[3 * f + k]]++] = int32_t(f);
     }
+    m.nface_ptr = nf_ptr;
+    m.nface = nf;
 
     // ---- patches: P balanced ranges of whole 32-node slices.  With
     // patch_multiple > 0 the count is rounded up to a multiple of it (the
@@ -180,6 +182,10 @@ std::string build_host_mesh(const double* xyz, int64_t N, const int32_t* tets,
     m.node_ptr.assign(1, 0);
     m.tet_ptr.assign(1, 0);
     m.face_ptr.assign(1, 0);
+    m.tcol_beg.assign(1, 0);
+    m.fcol_beg.assign(1, 0);
+    m.tcol_off.clear();
+    m.fcol_off.clear();
     std::vector<int32_t> tet_stamp(E, -1), face_stamp(m.F, -1), node_local(N, -1);
     std::vector<int32_t> ptets, pfaces, halo;
     std::vector<std::vector<uint16_t>> rows(N);   // local column ids of every row
@@ -221,6 +227,51 @@ std::string build_host_mesh(const double* xyz, int64_t N, const int32_t* tets,
         if (ntouch > 65535) return "qpat_mesh: a patch touches more than 65535 nodes";
         for (int32_t g = b; g < e; ++g) m.nodes.push_back(g);
         for (int32_t g : halo) m.nodes.push_back(g);
+        // greedy colours: a tet (face) takes the lowest colour that no earlier
+        // tet (face) sharing one of its owned vertices has; then the lists are
+        // sorted by colour (stable, so the order inside a colour is kept)
+        auto colour = [&](std::vector<int32_t>& items, int nv, const int32_t* conn, std::vector<int32_t>& beg,
+                          std::vector<int32_t>& off, int32_t base) -> int {
+            std::vector<std::array<uint64_t, 4>> used(size_t(nown), std::array<uint64_t, 4>{0, 0, 0, 0});
+            std::vector<int> col(items.size());
+            int ncol = 0;
+            for (size_t i = 0; i < items.size(); ++i) {
+                std::array<uint64_t, 4> u{0, 0, 0, 0};
+                for (int k = 0; k < nv; ++k) {
+                    const int32_t l = node_local[conn[size_t(nv) * items[i] + k]];
+                    if (l >= 0 && l < nown)
+                        for (int w = 0; w < 4; ++w) u[w] |= used[l][w];
+                }
+                int c = 0;
+                while (c < 256 && ((u[c >> 6] >> (c & 63)) & 1u)) ++c;
+                if (c == 256) return -1;
+                col[i] = c;
+                ncol = std::max(ncol, c + 1);
+                for (int k = 0; k < nv; ++k) {
+                    const int32_t l = node_local[conn[size_t(nv) * items[i] + k]];
+                    if (l >= 0 && l < nown) used[l][c >> 6] |= uint64_t(1) << (c & 63);
+                }
+            }
+            std::vector<int32_t> sorted;
+            sorted.reserve(items.size());
+            int32_t pos = base;
+            for (int c = 0; c < ncol; ++c) {
+                off.push_back(pos);
+                for (size_t i = 0; i < items.size(); ++i)
+                    if (col[i] == c) {
+                        sorted.push_back(items[i]);
+                        ++pos;
+                    }
+            }
+            off.push_back(pos);
+            beg.push_back(int32_t(off.size()));
+            items.swap(sorted);
+            return ncol;
+        };
+        const int ntc = colour(ptets, 4, m.tets.data(), m.tcol_beg, m.tcol_off, int32_t(m.tet_loc.size() / 4));
+        const int nfc = colour(pfaces, 3, m.faces_lib.data(), m.fcol_beg, m.fcol_off, int32_t(m.face_loc.size() / 4));
+        if (ntc < 0 || nfc < 0) return "qpat_mesh: more than 256 element colours in a patch";
+        m.max_tcolors = std::max(m.max_tcolors, ntc);
         for (int32_t t : ptets) {
             int32_t lv[4];
             for (int k = 0; k < 4; ++k) {

@@ -114,7 +114,10 @@ int upload_mesh(qpat_mesh_s* M) {
         (rc = up(M, h.tet_ptr, &d.tet_ptr)) || (rc = up(M, h.face_ptr, &d.face_ptr)) ||
         (rc = up(M, h.pface_area, &d.pface_area64)) || (rc = up(M, pa32, &d.pface_area32)) ||
         (rc = up(M, h.faces_lib, &d.faces_lib)) || (rc = up(M, h.farea, &d.farea)) ||
-        (rc = up(M, h.perm, &d.perm)) || (rc = up(M, h.iperm, &d.iperm)))
+        (rc = up(M, h.perm, &d.perm)) || (rc = up(M, h.iperm, &d.iperm)) ||
+        (rc = up(M, h.tcol_beg, &d.tcol_beg)) || (rc = up(M, h.tcol_off, &d.tcol_off)) ||
+        (rc = up(M, h.fcol_beg, &d.fcol_beg)) || (rc = up(M, h.fcol_off, &d.fcol_off)) ||
+        (rc = up(M, h.nface_ptr, &d.nface_ptr)) || (rc = up(M, h.nface, &d.nface)))
         return rc;
     if ((rc = up(M, h.sell_ptr, &d.sell_ptr)) || (rc = up(M, h.sell_col, &d.sell_col)) ||
         (rc = up(M, h.sell_len, &d.sell_len)) || (rc = up(M, h.sell_diag, &d.sell_diag)))

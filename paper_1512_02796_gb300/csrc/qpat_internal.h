@@ -43,6 +43,17 @@ struct HostMesh {
     std::vector<int32_t> face_ptr;
     std::vector<uint16_t> face_loc;     // 4 per patch face: 3 local ids + 0 pad
     std::vector<double> pface_area;     // per patch face
+    // Colours of each patch's tets and faces: within a colour no two share an
+    // owned vertex, and each patch's list is sorted by colour.  Colour c of
+    // patch p spans tets [tcol_off[j], tcol_off[j + 1]) with j = tcol_beg[p] + c,
+    // j + 1 < tcol_beg[p + 1] (faces likewise with fcol_*).  Element kernels
+    // run the colours one after the other, so their sums into owned rows need
+    // no atomics and add up in a fixed order (run-to-run identical results).
+    std::vector<int32_t> tcol_beg, tcol_off, fcol_beg, fcol_off;
+    int max_tcolors = 0;
+    // boundary faces of each node (library order, CSR): the load vector is
+    // gathered per node in a fixed order
+    std::vector<int32_t> nface_ptr, nface;
     int max_touched = 0, max_own = 0, max_ptets = 0, max_pfaces = 0;
     double extent = 0.0;                // largest bounding-box side
     // Assembled-operator pattern in sliced ELLPACK form (slices of 32
@@ -92,6 +103,12 @@ struct MeshDev {
     const ushort4* tet_loc;
     const int* face_ptr;        // P + 1
     const ushort4* face_loc;
+    const int* tcol_beg;        // P + 1 (see HostMesh)
+    const int* tcol_off;
+    const int* fcol_beg;        // P + 1
+    const int* fcol_off;
+    const int* nface_ptr;       // N + 1: boundary faces of each node
+    const int* nface;
     const double* pface_area64;
     const float* pface_area32;
     const int* faces_lib;       // F x 3 canonical order

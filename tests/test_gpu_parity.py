@@ -308,3 +308,35 @@ def test_local_entry_counts(case):
             assert one.prior_local_entries == one.prior_entries
         finally:
             one.close()
+
+
+def test_runs_are_bit_identical(case):
+    """The element kernels sum colour by colour and the PCG reduces in a
+    fixed order, so repeated calls (and a second mesh handle built from the
+    same input) give bit-identical fields and the same iteration counts."""
+    rng = np.random.default_rng(15)
+    N = case.N
+    s = rng.standard_normal(2 * N)
+    t = rng.standard_normal((case.K, N))
+    kt = 0.3 * rng.standard_normal(N)
+    mt = np.log(case.mu / case.mu.mean())
+    rhs = rng.standard_normal(2 * N)
+    other = Q.qpat_mesh(case.xyz, case.tets, patch_nodes=64 if case.N > 64 else 32)
+    try:
+        runs = []
+        for lib in (case.lib, case.lib, other):
+            lib.reset_stats()
+            out = []
+            for prec in (0, 1):
+                p = _params(prec, fp32_operator=1)
+                out += list(Q.qpat_forward(lib, case.kappa, case.mu, case.flux, p))
+                out.append(Q.qpat_jvp(lib, case.kappa, case.mu, case.phi, s, case.w, p))
+                out.append(Q.qpat_vjp(lib, case.kappa, case.mu, case.phi, t, case.w, p))
+            out.append(Q.qpat_prior_solve(lib, kt, mt, rhs, _params(0, T=1e-2, b_over_a=0.7)))
+            runs.append((out, lib.stats()["pcg_iters"]))
+        for out, iters in runs[1:]:
+            assert iters == runs[0][1]
+            for a, b in zip(out, runs[0][0]):
+                np.testing.assert_array_equal(a, b)
+    finally:
+        other.close()
