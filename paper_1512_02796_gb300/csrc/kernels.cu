@@ -166,8 +166,11 @@ __global__ void __launch_bounds__(kThreads) k_assemble_K(MeshDev m, const double
     OpParams<double> op{kappa, mu, 0, 0, 0, 1};
     stage_static<double, 1>(m, nb, nt, s, op);
     __syncthreads();
-    // colour by colour: each owned row takes one tet's terms at a time, plain
-    // adds in a fixed order (the values are identical on every run)
+    // colour by colour: within a colour each owned row takes one tet's terms,
+    // and the barrier between colours orders the additions to an entry, so
+    // the sums run in a fixed order (identical values on every run).  The
+    // additions are fire-and-forget reductions into global memory (no load
+    // round trip per entry); the barrier waits for them once per colour.
     for_each_coloured(m.tcol_beg, m.tcol_off, p, [&](int t) {
         const ushort4 lv = m.tet_loc[t];
         const int v[4] = {lv.x, lv.y, lv.z, lv.w};
@@ -187,7 +190,7 @@ __global__ void __launch_bounds__(kThreads) k_assemble_K(MeshDev m, const double
                 const double st = sk * (c[a][0] * c[b][0] + c[a][1] * c[b][1] + c[a][2] * c[b][2]);
                 const double ms = a == b ? 2.0 * Sm + 4.0 * s.c2[v[a]] : Sm + s.c2[v[a]] + s.c2[v[b]];
                 const int64_t idx = sell_slot(m, g, v[b]);
-                if (idx >= 0) val[idx] += st + vm * ms;
+                if (idx >= 0) atomicAdd(val + idx, st + vm * ms);
             }
         }
     });
@@ -199,7 +202,7 @@ __global__ void __launch_bounds__(kThreads) k_assemble_K(MeshDev m, const double
             if (v[a] >= nown) continue;
             for (int b = 0; b < 3; ++b) {
                 const int64_t idx = sell_slot(m, ob + v[a], v[b]);
-                if (idx >= 0) val[idx] += a == b ? 2.0 * w : w;
+                if (idx >= 0) atomicAdd(val + idx, a == b ? 2.0 * w : w);
             }
         }
     });
@@ -219,6 +222,7 @@ __global__ void __launch_bounds__(kThreads) k_assemble_prior(MeshDev m, const do
     OpParams<double> op{u1, u2, 0, 0, 0, 0};
     stage_static<double, 1>(m, nb, nt, s, op);
     __syncthreads();
+    // colour by colour, ordered reductions as in k_assemble_K
     for_each_coloured(m.tcol_beg, m.tcol_off, p, [&](int t) {
         const ushort4 lv = m.tet_loc[t];
         const int v[4] = {lv.x, lv.y, lv.z, lv.w};
@@ -241,8 +245,8 @@ __global__ void __launch_bounds__(kThreads) k_assemble_prior(MeshDev m, const do
                 const double cc = c[a][0] * c[b][0] + c[a][1] * c[b][1] + c[a][2] * c[b][2];
                 const int64_t idx = sell_slot(m, g, v[b]);
                 if (idx >= 0) {
-                    val0[idx] += coef[0] * cc;
-                    val1[idx] += coef[1] * cc;
+                    atomicAdd(val0 + idx, coef[0] * cc);
+                    atomicAdd(val1 + idx, coef[1] * cc);
                 }
             }
         }
