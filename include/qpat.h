@@ -150,13 +150,15 @@ int qpat_mesh_ex(const double* xyz, int64_t N, const int32_t* tets, int64_t E,
 void qpat_mesh_free(qpat_mesh_t mesh);
 
 /* Host-only preparation check (needs no GPU): builds the mesh structures of
- * qpat_mesh_ex and verifies them.  info8 (10 entries) receives F, patches,
+ * qpat_mesh_ex and verifies them.  info8 (11 entries) receives F, patches,
  * max touched nodes per patch, max owned nodes, max tets per patch, max faces
  * per patch, total patch-tet entries (>= E; the excess is the tets duplicated
  * on patch borders), total patch-face entries, the stored nonzeros of the
- * assembled K pattern and those of the prior's stiffness-only pattern (pairs
- * with a non-zero gradient coupling in a shared tet).  faces (F x 3) and perm
- * (N) are filled when not NULL.  Returns QPAT_EINVAL with a message if a
+ * assembled K pattern, those of the prior's stiffness-only pattern (pairs
+ * with a non-zero gradient coupling in a shared tet), and the largest number
+ * of tet colours in a patch (the element kernels sum colour by colour; no two
+ * tets of a colour share an owned node, which is checked).  faces (F x 3) and
+ * perm (N) are filled when not NULL.  Returns QPAT_EINVAL with a message if a
  * check fails. */
 int qpat_mesh_host_info(const double* xyz, int64_t N, const int32_t* tets, int64_t E,
                         int patch_nodes, int64_t* info8, int32_t* faces, int32_t* perm);

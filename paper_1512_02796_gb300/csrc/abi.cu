@@ -524,7 +524,7 @@ static int mesh_create(const double* xyz, int64_t N, const int32_t* tets, int64_
 }
 
 int qpat_mesh_host_info(const double* xyz, int64_t N, const int32_t* tets, int64_t E, int patch_nodes,
-                        int64_t* info8, int32_t* faces, int32_t* perm) {  // info8: 10 entries
+                        int64_t* info8, int32_t* faces, int32_t* perm) {  // info8: 11 entries
     if (!info8) return fail(QPAT_EINVAL, "qpat_mesh_host_info: info is NULL");
     HostMesh h;
     std::string msg = build_host_mesh(xyz, N, tets, E, patch_nodes, 0, h);
@@ -586,6 +586,7 @@ int qpat_mesh_host_info(const double* xyz, int64_t N, const int32_t* tets, int64
     info8[5] = h.max_pfaces;
     info8[6] = dup;  // sum over patches of listed tets (>= E; the excess is border duplication)
     info8[7] = int64_t(h.face_ptr[h.P]);
+    info8[10] = h.max_tcolors;
     // the prior's stiffness-only pattern: a subset of the full pattern, with
     // every diagonal, symmetric in global ids
     {

@@ -389,7 +389,7 @@ def qpat_mesh_host_info(xyz, tets, patch_nodes: int = 512):
     """Host-only mesh preparation check; returns (info dict, faces, perm)."""
     xyz = _f64(xyz)
     tets = np.ascontiguousarray(tets, dtype=np.int32)
-    info = np.zeros(10, dtype=np.int64)
+    info = np.zeros(11, dtype=np.int64)
     lib = load()
     # first call sizes the face array
     _check(lib.qpat_mesh_host_info(_dp(xyz), xyz.shape[0], tets.ctypes.data_as(_c_int32_p), tets.shape[0],
@@ -400,7 +400,7 @@ def qpat_mesh_host_info(xyz, tets, patch_nodes: int = 512):
                                    patch_nodes, info.ctypes.data_as(_c_int64_p), faces.ctypes.data_as(_c_int32_p),
                                    perm.ctypes.data_as(_c_int32_p)))
     keys = ["F", "P", "max_touched", "max_own", "max_ptets", "max_pfaces", "patch_tets", "patch_faces",
-            "nnz", "prior_nnz"]
+            "nnz", "prior_nnz", "max_tet_colours"]
     return dict(zip(keys, (int(v) for v in info))), faces, perm
 
 

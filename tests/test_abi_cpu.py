@@ -49,6 +49,12 @@ def test_host_mesh_faces_match_oracle_and_patches_verify(n, L, pn):
     assert info["P"] == -(-n ** 3 // pn)
     assert info["patch_tets"] >= 6 * (n - 1) ** 3
     assert info["max_own"] <= pn + 32     # balanced whole 32-node slices
+    # element colours (checked inside: no two tets of a colour share an owned
+    # node): at least the 6 tets around the cube diagonal, at least the 24 around
+    # an interior node once a patch owns one, few enough for one barrier each
+    assert 6 <= info["max_tet_colours"] <= 64
+    if n >= 5:
+        assert info["max_tet_colours"] >= 24
 
 
 @pytest.mark.parametrize("n,nz,pn", [(5, 4, 32), (9, 6, 64), (17, 9, 256)])
