@@ -263,16 +263,17 @@ def run_ours(args):
     # ---- end to end through the host-pointer ABI (copies inside the timed region)
     H = d["host"]
     e2e_steps = max(1, min(args.steps, 5))
-    hk = H["kappa"]
+    # one untimed call first: the host-call staging buffers are allocated once
+    Q.qpat_jvp_vjp_pair(mesh, H["kappa"], H["mu"], H["phi"], H["s"], H["t"], H["w"], prm)
+    Q.qpat_prior_solve(mesh, H["kt"], H["mt"], H["prior_rhs"], prm)
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
-        oj = Q.qpat_jvp(mesh, H["kappa"], H["mu"], H["phi"], H["s"], H["w"], prm)
-        ov = Q.qpat_vjp(mesh, H["kappa"], H["mu"], H["phi"], H["t"], H["w"], prm)
+        oj, ov = Q.qpat_jvp_vjp_pair(mesh, H["kappa"], H["mu"], H["phi"], H["s"], H["t"], H["w"], prm)
         op = Q.qpat_prior_solve(mesh, H["kt"], H["mt"], H["prior_rhs"], prm)
     e2e_s = time.perf_counter() - t0
     N, K = d["N"], d["K"]
-    # inputs of qpat_jvp (kappa, mu, phi, w, s), qpat_vjp (kappa, mu, phi, w, t), qpat_prior_solve (kt, mt, rhs)
-    h2d = 8 *((N + N + K * N + K * N + 2 * N) + (N + N + K * N + K * N + K * N) + (N + N + 2 * N))
+    # inputs of qpat_jvp_vjp_pair (kappa, mu, phi, w, s, t) and qpat_prior_solve (kt, mt, rhs)
+    h2d = 8 * ((N + N + K * N + K * N + 2 * N + K * N) + (N + N + 2 * N))
     d2h = 8 * (K * N + 2 * N + 2 * N)
 
     # ---- roofline of the dominant kernel: the fused PCG launch (pair or prior)

@@ -314,6 +314,12 @@ int qpat_jvp_vjp_pair_dev(qpat_mesh_t mesh, const qpat_params* prm,
                           const double* phi, const double* w, const double* s,
                           const double* t, double* out_jv, double* out_vjp,
                           void* stream);
+/* The same with host pointers (copied to and from the device on the mesh's
+ * stream; returns when out_jv and out_vjp are written).  K in [1, 8]. */
+int qpat_jvp_vjp_pair(qpat_mesh_t mesh, const qpat_params* prm,
+                      const double* kappa, const double* mu, int K,
+                      const double* phi, const double* w, const double* s,
+                      const double* t, double* out_jv, double* out_vjp);
 
 /* ------------------------------------------------ learned initial guess */
 

@@ -502,6 +502,28 @@ int qpat_jvp_vjp_pair_dev(qpat_mesh_t M, const qpat_params* prm, const double* k
     return QPAT_OK;
 }
 
+int qpat_jvp_vjp_pair(qpat_mesh_t M, const qpat_params* prm, const double* kappa, const double* mu, int K,
+                      const double* phi, const double* w, const double* sv, const double* t, double* out_jv,
+                      double* out_vjp) {
+    if (!M) return fail(QPAT_EINVAL, "qpat_jvp_vjp_pair: NULL mesh");
+    DeviceGuard dg(M->device);
+    const size_t N = M->h.N;
+    int rc = QPAT_OK;
+    HostCall hc(M);
+    double* dk = hc.in(kappa, N, &rc);
+    double* dm = hc.in(mu, N, &rc);
+    double* dp = hc.in(phi, size_t(K) * N, &rc);
+    double* dw = hc.in(w, size_t(K) * N, &rc);
+    double* ds = hc.in(sv, 2 * N, &rc);
+    double* dt = hc.in(t, size_t(K) * N, &rc);
+    double* dj = hc.out(size_t(K) * N, &rc);
+    double* dv = hc.out(2 * N, &rc);
+    if (rc) return rc;
+    if ((rc = qpat_jvp_vjp_pair_dev(M, prm, dk, dm, K, dp, dw, ds, dt, dj, dv, M->stream))) return rc;
+    if ((rc = hc.back(out_jv, dj, size_t(K) * N)) || (rc = hc.back(out_vjp, dv, 2 * N))) return rc;
+    return hc.sync();
+}
+
 int qpat_prior_solve_dev(qpat_mesh_t M, const qpat_params* prm, const double* kt, const double* mt,
                          const double* rhs, double* out, void* stream) {
     if (!M || !kt || !mt || !rhs || !out) return fail(QPAT_EINVAL, "qpat_prior_solve: NULL argument");

@@ -114,6 +114,9 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
         "qpat_vjp_dev": (ctypes.c_int, [vp, ctypes.POINTER(qpat_params), vp, vp, ctypes.c_int, vp, vp, vp, vp, vp]),
         "qpat_jvp_vjp_pair_dev": (ctypes.c_int, [vp, ctypes.POINTER(qpat_params), vp, vp, ctypes.c_int, vp, vp, vp,
                                                  vp, vp, vp, vp]),
+        "qpat_jvp_vjp_pair": (ctypes.c_int, [vp, ctypes.POINTER(qpat_params), _c_double_p, _c_double_p, ctypes.c_int,
+                                             _c_double_p, _c_double_p, _c_double_p, _c_double_p, _c_double_p,
+                                             _c_double_p]),
         "qpat_prior_solve": (ctypes.c_int, [vp, ctypes.POINTER(qpat_params), _c_double_p, _c_double_p, _c_double_p,
                                             _c_double_p]),
         "qpat_batch_create": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(vp), ctypes.POINTER(ctypes.c_int),
@@ -168,7 +171,7 @@ def exported_names() -> Sequence[str]:
         "qpat_flux_patch", "qpat_flux_side", "qpat_apply_K_dev", "qpat_forward", "qpat_forward_dev", "qpat_forward_noalloc_dev",
         "qpat_forward_guess_dev",
         "qpat_jvp", "qpat_jvp_dev",
-        "qpat_vjp", "qpat_vjp_dev", "qpat_jvp_vjp_pair_dev", "qpat_prior_solve", "qpat_prior_solve_dev",
+        "qpat_vjp", "qpat_vjp_dev", "qpat_jvp_vjp_pair_dev", "qpat_jvp_vjp_pair", "qpat_prior_solve", "qpat_prior_solve_dev",
         "qpat_batch_create", "qpat_batch_buffers", "qpat_batch_forward", "qpat_batch_status", "qpat_batch_free",
         "qpat_autotune", "qpat_reconstruct",
         "qpat_unet_create", "qpat_unet_free", "qpat_unet_num_params", "qpat_unet_get_params", "qpat_unet_set_params",
@@ -457,6 +460,20 @@ def qpat_vjp(mesh: Mesh, kappa, mu, phi, t, w=None, params: Optional[qpat_params
     _check(load().qpat_vjp(mesh.handle, _pp(params), _dp(_f64(kappa)), _dp(_f64(mu)), K, _dp(phi), _dp(w),
                            _dp(t), _dp(out)))
     return out
+
+
+def qpat_jvp_vjp_pair(mesh: Mesh, kappa, mu, phi, s, t, w=None, params: Optional[qpat_params] = None):
+    """One J s and one J^T t (host arrays) as a single 2K-RHS block solve;
+    returns (w o J s (K x N), J^T (w o t) (2N))."""
+    phi = _f64(np.atleast_2d(phi))
+    K = phi.shape[0]
+    t = _f64(np.broadcast_to(t, phi.shape))
+    w = None if w is None else _f64(np.broadcast_to(w, phi.shape))
+    oj = np.empty((K, mesh.N))
+    ov = np.empty(2 * mesh.N)
+    _check(load().qpat_jvp_vjp_pair(mesh.handle, _pp(params), _dp(_f64(kappa)), _dp(_f64(mu)), K, _dp(phi), _dp(w),
+                                    _dp(_f64(s)), _dp(t), _dp(oj), _dp(ov)))
+    return oj, ov
 
 
 def qpat_prior_solve(mesh: Mesh, kt, mt, rhs, params: Optional[qpat_params] = None):

@@ -340,3 +340,18 @@ def test_runs_are_bit_identical(case):
                 np.testing.assert_array_equal(a, b)
     finally:
         other.close()
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_pair_host_entry(case, precision):
+    """qpat_jvp_vjp_pair (host pointers, one 2K-RHS block solve) against the
+    oracle's J s and J^T t."""
+    if case.K > 8:
+        pytest.skip("the pair takes K <= 8")
+    rng = np.random.default_rng(16)
+    s = rng.standard_normal(2 * case.N)
+    t = rng.standard_normal((case.K, case.N))
+    oj, ov = Q.qpat_jvp_vjp_pair(case.lib, case.kappa, case.mu, case.phi, s, t, case.w,
+                                 _params(precision, fp32_operator=1))
+    assert rel(oj, O.jvp(case.om, case.kappa, case.mu, case.phi, s, case.w, case.fac)) < 1e-10
+    assert rel(ov, O.vjp(case.om, case.kappa, case.mu, case.phi, t, case.w, case.fac)) < 1e-10
