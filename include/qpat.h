@@ -447,6 +447,25 @@ int qpat_reconstruct(qpat_mesh_t mesh, const qpat_params* prm, int K,
                      const double* sigma, const double* kappa0_mu0,
                      double* kappa, double* mu, qpat_report* rep);
 
+/* Checkpoint / resume of Algorithm 1.  The state between linearisations is
+ * the background pair (kappa_0, mu_0), beta^(l) = (kappa_tilde, mu_tilde) and
+ * the count l (step 1 of Algorithm 1 restarts from beta^(l) alone).
+ * beta_out (2N, caller order: kappa_tilde then mu_tilde; may be NULL)
+ * receives the final beta; with beta_in == NULL this is qpat_reconstruct.
+ * With beta_in != NULL the run resumes at step 1 from beta^(l) = beta_in
+ * after lin_done >= 1 linearisations (step 0 counted), kappa0_mu0 required,
+ * and continues until max_lin or a rejected step; rep->linearisations then
+ * counts from lin_done, and rep->residuals[0] is the residual at beta_in.
+ * Everything on the device sums in a fixed order, so a run stopped at
+ * max_lin = l and resumed from its kappa0/mu0, beta_out and
+ * rep->linearisations gives the same bits as one uninterrupted run.
+ * QPAT_EINVAL if beta_in is given without kappa0_mu0 or with lin_done < 1. */
+int qpat_reconstruct_ex(qpat_mesh_t mesh, const qpat_params* prm, int K,
+                        const double* flux_face, const double* chi,
+                        const double* sigma, const double* kappa0_mu0,
+                        const double* beta_in, int lin_done, double* kappa,
+                        double* mu, double* beta_out, qpat_report* rep);
+
 #ifdef __cplusplus
 }
 #endif

@@ -619,19 +619,26 @@ class ReconReport:
     lsqr_phibar: List[List[float]]
     linearisations: int
     accepted_last: bool
+    beta: Optional[np.ndarray] = None  # final beta^(l) = [kappa_tilde, mu_tilde]
 
 
 def reconstruct(mesh: Mesh, flux, chi, sigma, params: QpatParams,
-                kappa0_mu0=None):
+                kappa0_mu0=None, beta_in=None, lin_done: int = 0):
     """Algorithm 1 with step 0 (Sec. 5, Test 1) for K stacked illuminations.
 
     flux: K x F, chi and sigma: K x N (Gamma = diag(sigma^2), so
     Gamma^{-1/2} = diag(1/sigma)).  Linearisations are counted as in Sec. 5
-    (step 0 is the first).  Returns (kappa, mu, report)."""
+    (step 0 is the first).  Returns (kappa, mu, report); report.beta is the
+    final beta^(l).  Resume: step 1 of Algorithm 1 starts from beta^(l)
+    alone, so with beta_in (needs kappa0_mu0 and lin_done >= 1) the
+    initialisation and step 0 are skipped and the loop continues from
+    beta^(l) = beta_in with lin_done linearisations counted."""
     chi = np.atleast_2d(chi)
     w = 1.0 / np.atleast_2d(sigma)
     K, N = chi.shape
     P = params
+    if beta_in is not None and (kappa0_mu0 is None or lin_done < 1):
+        raise ValueError("resuming needs kappa0_mu0 and lin_done >= 1")
     if kappa0_mu0 is None:
         k0, m0_ = fit_background(mesh, flux, chi, w, P.fit_grid, P.fit_gn_steps)
     else:
@@ -640,33 +647,37 @@ def reconstruct(mesh: Mesh, flux, chi, sigma, params: QpatParams,
     def coeffs(beta):
         return k0 * np.exp(beta[:N]), m0_ * np.exp(beta[N:])
 
-    # initialisation
-    ones = np.ones(N)
-    fac0 = Factor(system_matrix(mesh, k0 * ones, m0_ * ones))
-    phi0, _ = forward(mesh, k0 * ones, m0_ * ones, flux, fac0)
-    mt = init_mu(chi, phi0, m0_)
-    kt = np.zeros(N)
-
     rep = ReconReport(k0, m0_, [], [], [], 0, True)
+    if beta_in is not None:
+        # resume at step 1 from beta^(l)
+        beta = np.array(beta_in, dtype=np.float64)
+        rep.linearisations = int(lin_done)
+    else:
+        # initialisation
+        ones = np.ones(N)
+        fac0 = Factor(system_matrix(mesh, k0 * ones, m0_ * ones))
+        phi0, _ = forward(mesh, k0 * ones, m0_ * ones, flux, fac0)
+        mt = init_mu(chi, phi0, m0_)
+        kt = np.zeros(N)
 
-    # step 0: LSQR for kappa only, prior M_delta(kt_init)
-    kap, mu = k0 * np.exp(kt), m0_ * np.exp(mt)
-    fac = Factor(system_matrix(mesh, kap, mu))
-    phi, h = forward(mesh, kap, mu, flux, fac)
-    zeros = np.zeros(N)
-    yhat = (w * (chi - h)).ravel()          # J kt_init = 0 as kt_init = 0
-    Mk = Factor(assemble_stiffness(mesh, lagged_weights(mesh, kt, P.T, P.prior, P.prior_q))
-                + P.delta * sp.identity(N, format="csr"))
-    A0 = lambda v: jvp(mesh, kap, mu, phi, np.concatenate([v, zeros]), w, fac).ravel()
-    AT0 = lambda u: vjp(mesh, kap, mu, phi, u.reshape(K, N), w, fac)[:N]
-    res0 = lsqr_prior(A0, AT0, Mk.solve, yhat, P.max_lsqr, P.m0, P.tau, P.fixed_counts)
-    kt = kt + res0.x
-    rep.lsqr_iters.append(res0.iters)
-    rep.lsqr_phibar.append(res0.phibar)
-    rep.linearisations = 1
-    beta = np.concatenate([kt, mt])
+        # step 0: LSQR for kappa only, prior M_delta(kt_init)
+        kap, mu = k0 * np.exp(kt), m0_ * np.exp(mt)
+        fac = Factor(system_matrix(mesh, kap, mu))
+        phi, h = forward(mesh, kap, mu, flux, fac)
+        zeros = np.zeros(N)
+        yhat = (w * (chi - h)).ravel()          # J kt_init = 0 as kt_init = 0
+        Mk = Factor(assemble_stiffness(mesh, lagged_weights(mesh, kt, P.T, P.prior, P.prior_q))
+                    + P.delta * sp.identity(N, format="csr"))
+        A0 = lambda v: jvp(mesh, kap, mu, phi, np.concatenate([v, zeros]), w, fac).ravel()
+        AT0 = lambda u: vjp(mesh, kap, mu, phi, u.reshape(K, N), w, fac)[:N]
+        res0 = lsqr_prior(A0, AT0, Mk.solve, yhat, P.max_lsqr, P.m0, P.tau, P.fixed_counts)
+        kt = kt + res0.x
+        rep.lsqr_iters.append(res0.iters)
+        rep.lsqr_phibar.append(res0.phibar)
+        rep.linearisations = 1
+        beta = np.concatenate([kt, mt])
 
-    # step 1 needs h(beta^(0))
+    # step 1 needs h(beta^(l))
     kap, mu = coeffs(beta)
     fac = Factor(system_matrix(mesh, kap, mu))
     phi, h = forward(mesh, kap, mu, flux, fac)
@@ -698,4 +709,5 @@ def reconstruct(mesh: Mesh, flux, chi, sigma, params: QpatParams,
         beta, kap, mu, fac, phi, h, r_cur = beta_new, kap_n, mu_n, fac_n, phi_n, h_n, r_new
         rep.residuals.append(r_cur)
     kap, mu = coeffs(beta)
+    rep.beta = beta
     return kap, mu, rep

@@ -158,6 +158,14 @@ __global__ void k_xw(int64_t n, const double* S, const double* v, double* x, dou
 }
 
 // beta_new = beta_old + x (kappa block only when kappa_only)
+// beta (interleaved per node) from its two blocks
+__global__ void k_pack_beta(int64_t N, const double* s1, const double* s2, double* beta) {
+    FOR_I(N) {
+        beta[2 * i] = s1[i];
+        beta[2 * i + 1] = s2[i];
+    }
+}
+
 __global__ void k_add_beta(int64_t N, const double* x, int kappa_only, double* beta) {
     FOR_I(N) {
         beta[2 * i] += x[2 * i];
@@ -316,10 +324,16 @@ int lsqr(Recon& rc, LinState& L, const OpState& P, const double* b, int kappa_on
 
 using namespace qpat;
 
-extern "C" int qpat_reconstruct(qpat_mesh_t M, const qpat_params* prm_in, int K, const double* flux_face,
-                                const double* chi, const double* sigma, const double* kappa0_mu0, double* kappa,
-                                double* mu, qpat_report* rep) {
+// Algorithm 1.  beta_in (2N, caller order: kappa_tilde then mu_tilde) resumes
+// a stopped run at step 1 with beta^(l) = beta_in after lin_done
+// linearisations (the background constants must then be given); beta_out
+// (optional) receives the final beta^(l).
+static int reconstruct_impl(qpat_mesh_t M, const qpat_params* prm_in, int K, const double* flux_face,
+                            const double* chi, const double* sigma, const double* kappa0_mu0, const double* beta_in,
+                            int lin_done, double* kappa, double* mu, double* beta_out, qpat_report* rep) {
     if (!M || !flux_face || !chi || !sigma || !kappa || !mu) return fail(QPAT_EINVAL, "qpat_reconstruct: NULL argument");
+    if (beta_in && (!kappa0_mu0 || lin_done < 1))
+        return fail(QPAT_EINVAL, "qpat_reconstruct_ex: resuming needs kappa0_mu0 and lin_done >= 1");
     if (K < 1 || round_rhs(K) < 0) return fail(QPAT_EINVAL, "qpat_reconstruct: K must be in [1, 16]");
     qpat_params prm;
     qpat_default_params(&prm);
@@ -390,6 +404,10 @@ extern "C" int qpat_reconstruct(qpat_mesh_t M, const qpat_params* prm_in, int K,
             return rc.residual(L);
         };
 
+        double* ktmp = rc.buf("ktv", N);
+        double* mtmp = rc.buf("mtv", N);
+        OpState P;
+        std::vector<double> hist;
         // ---- (kappa_0, mu_0): given, or the reading of Algorithm 1's preamble
         double k0, m0;
         if (kappa0_mu0) {
@@ -450,6 +468,16 @@ extern "C" int qpat_reconstruct(qpat_mesh_t M, const qpat_params* prm_in, int K,
         report.kappa0 = k0;
         report.mu0 = m0;
 
+        if (beta_in) {
+        // ---- resume: beta^(l) given, continue at step 1
+        double* hb = rc.buf("hbeta", 2 * N);
+        rc.ck(cudaMemcpyAsync(hb, beta_in, 2 * N * sizeof(double), cudaMemcpyHostToDevice, s), "H2D");
+        rc.ck(launch_to_lib<double, double>(M->d, 1, 1, hb, ktmp, s), "to_lib");
+        rc.ck(launch_to_lib<double, double>(M->d, 1, 1, hb + N, mtmp, s), "to_lib");
+        qpat::note_launch(1);
+        k_pack_beta<<<GS(N)>>>(N, ktmp, mtmp, beta);
+        report.linearisations = lin_done;
+        } else {
         // ---- initialisation: phi0 at the constants, mu_tilde_init, kappa_tilde_init = 0
         forward_const(k0, m0, LA, kapA, muA, phiA);
         qpat::note_launch(1);
@@ -464,18 +492,15 @@ extern "C" int qpat_reconstruct(qpat_mesh_t M, const qpat_params* prm_in, int K,
         rc.ckq(forward_lib(M, rc.so, LA, rc.flux, s));
         qpat::note_launch(1);
         k_wresid<<<GS(N * R)>>>(N, R, rc.w, rc.chi, LA.mu, LA.phi, nullptr, ytil);
-        double* ktmp = rc.buf("ktv", N);
-        double* mtmp = rc.buf("mtv", N);
         qpat::note_launch(1);
         k_unpack_beta<<<GS(N)>>>(N, beta, 0, ktmp, mtmp);
-        OpState P;
         rc.ckq(prepare_prior(M, ktmp, mtmp, prm.T, prm.prior, prm.prior_q, prm.b_over_a, prm.delta, P, s));
-        std::vector<double> hist;
         int it0 = lsqr(rc, LA, P, ytil, 1, prm, xls, hist);
         qpat::note_launch(1);
         k_add_beta<<<GS(N)>>>(N, xls, 1, beta);
         report.lsqr_iters[0] = it0;
         report.linearisations = 1;
+        }
 
         // ---- h(beta^(0))
         qpat::note_launch(1);
@@ -544,6 +569,14 @@ extern "C" int qpat_reconstruct(qpat_mesh_t M, const qpat_params* prm_in, int K,
         rc.ck(launch_from_lib<double, double>(M->d, 1, 1, s2, outm, s), "from_lib");
         rc.ck(cudaMemcpyAsync(kappa, outk, N * sizeof(double), cudaMemcpyDeviceToHost, s), "D2H");
         rc.ck(cudaMemcpyAsync(mu, outm, N * sizeof(double), cudaMemcpyDeviceToHost, s), "D2H");
+        if (beta_out) {
+            double* ob = rc.buf("outb", 2 * N);
+            qpat::note_launch(1);
+            k_unpack_beta<<<GS(N)>>>(N, beta, 0, s1, s2);
+            rc.ck(launch_from_lib<double, double>(M->d, 1, 1, s1, ob, s), "from_lib");
+            rc.ck(launch_from_lib<double, double>(M->d, 1, 1, s2, ob + N, s), "from_lib");
+            rc.ck(cudaMemcpyAsync(beta_out, ob, 2 * N * sizeof(double), cudaMemcpyDeviceToHost, s), "D2H");
+        }
         rc.ck(cudaStreamSynchronize(s), "sync");
         (void)kapC;
         (void)muC;
@@ -561,4 +594,18 @@ extern "C" int qpat_reconstruct(qpat_mesh_t M, const qpat_params* prm_in, int K,
         std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
     if (rep) *rep = report;
     return QPAT_OK;
+}
+
+extern "C" int qpat_reconstruct(qpat_mesh_t M, const qpat_params* prm, int K, const double* flux_face,
+                                const double* chi, const double* sigma, const double* kappa0_mu0, double* kappa,
+                                double* mu, qpat_report* rep) {
+    return reconstruct_impl(M, prm, K, flux_face, chi, sigma, kappa0_mu0, nullptr, 0, kappa, mu, nullptr, rep);
+}
+
+extern "C" int qpat_reconstruct_ex(qpat_mesh_t M, const qpat_params* prm, int K, const double* flux_face,
+                                   const double* chi, const double* sigma, const double* kappa0_mu0,
+                                   const double* beta_in, int lin_done, double* kappa, double* mu, double* beta_out,
+                                   qpat_report* rep) {
+    return reconstruct_impl(M, prm, K, flux_face, chi, sigma, kappa0_mu0, beta_in, lin_done, kappa, mu, beta_out,
+                            rep);
 }

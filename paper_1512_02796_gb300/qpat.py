@@ -151,6 +151,9 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
         "qpat_reconstruct": (ctypes.c_int, [vp, ctypes.POINTER(qpat_params), ctypes.c_int, _c_double_p,
                                             _c_double_p, _c_double_p, _c_double_p, _c_double_p, _c_double_p,
                                             ctypes.POINTER(qpat_report)]),
+        "qpat_reconstruct_ex": (ctypes.c_int, [vp, ctypes.POINTER(qpat_params), ctypes.c_int, _c_double_p,
+                                               _c_double_p, _c_double_p, _c_double_p, _c_double_p, ctypes.c_int,
+                                               _c_double_p, _c_double_p, _c_double_p, ctypes.POINTER(qpat_report)]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -173,7 +176,7 @@ def exported_names() -> Sequence[str]:
         "qpat_jvp", "qpat_jvp_dev",
         "qpat_vjp", "qpat_vjp_dev", "qpat_jvp_vjp_pair_dev", "qpat_jvp_vjp_pair", "qpat_prior_solve", "qpat_prior_solve_dev",
         "qpat_batch_create", "qpat_batch_buffers", "qpat_batch_forward", "qpat_batch_status", "qpat_batch_free",
-        "qpat_autotune", "qpat_reconstruct",
+        "qpat_autotune", "qpat_reconstruct", "qpat_reconstruct_ex",
         "qpat_unet_create", "qpat_unet_free", "qpat_unet_num_params", "qpat_unet_get_params", "qpat_unet_set_params",
         "qpat_unet_features_dev", "qpat_unet_predict_dev", "qpat_unet_train_dev", "qpat_unet_to_double_dev",
         "qpat_conv3d_bf16_dev", "qpat_conv3d_bf16_wgrad_dev", "qpat_conv3d_bf16_wgrad_scratch",
@@ -481,6 +484,25 @@ def qpat_prior_solve(mesh: Mesh, kt, mt, rhs, params: Optional[qpat_params] = No
     _check(load().qpat_prior_solve(mesh.handle, _pp(params), _dp(_f64(kt)), _dp(_f64(mt)), _dp(_f64(rhs)),
                                    _dp(out)))
     return out
+
+
+def qpat_reconstruct_ex(mesh: Mesh, flux, chi, sigma, params: Optional[qpat_params] = None, kappa0_mu0=None,
+                        beta_in=None, lin_done: int = 0):
+    """Algorithm 1 with checkpoint / resume: returns (kappa, mu, beta, report);
+    beta_in / lin_done resume a run at step 1 (see include/qpat.h)."""
+    flux = _f64(np.atleast_2d(flux))
+    K = flux.shape[0]
+    chi = _f64(np.atleast_2d(chi))
+    sigma = _f64(np.broadcast_to(sigma, chi.shape))
+    k0 = None if kappa0_mu0 is None else _f64(kappa0_mu0)
+    b_in = None if beta_in is None else _f64(beta_in)
+    kappa = np.empty(mesh.N)
+    mu = np.empty(mesh.N)
+    beta = np.empty(2 * mesh.N)
+    rep = qpat_report()
+    _check(load().qpat_reconstruct_ex(mesh.handle, _pp(params), K, _dp(flux), _dp(chi), _dp(sigma), _dp(k0),
+                                      _dp(b_in), int(lin_done), _dp(kappa), _dp(mu), _dp(beta), ctypes.byref(rep)))
+    return kappa, mu, beta, rep
 
 
 def qpat_reconstruct(mesh: Mesh, flux, chi, sigma, params: Optional[qpat_params] = None, kappa0_mu0=None):

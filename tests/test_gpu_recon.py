@@ -137,3 +137,47 @@ def test_reconstruct_with_tvq_prior_matches_oracle(c0, q, nlin, nlsqr):
                                       Q.qpat_default_params(T=1e-2, max_lin=nlin, max_lsqr=nlsqr,
                                                             fixed_counts=1, precision=0), k0m0)
     assert rel(kap_pm, kap_g) > 1e-6
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_reconstruct_resume_is_bit_identical(precision):
+    """Checkpoint / resume on the GPU: a run stopped at max_lin = 2 and
+    resumed from its (kappa_0, mu_0), beta and linearisation count gives the
+    same bits as one 4-linearisation run (every device sum runs in a fixed
+    order); resuming without the background constants is refused.  Case: the
+    7^3 cube with two patches whose first steps are accepted (the oracle's
+    resume pin uses the same data)."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    cfg = S.small_config(7, 12.0, 2, 9)
+    xyz, tets = cfg.mesh()
+    om = O.Mesh(xyz, tets)
+    kap_t, mu_t = cfg.coefficients(xyz)
+    fl = np.stack([O.flux_patch(om, p.center, p.normal, p.half_w) for p in cfg.patches])
+    h = O.measure(om, kap_t, mu_t, fl)
+    sig = 0.01 * np.abs(h) + 1e-12
+    chi = h + sig * S.noise_draws(1, h.shape)
+    k0m0 = (float(np.median(kap_t)), float(np.median(mu_t)))
+    lib = Q.qpat_mesh(xyz, tets, patch_nodes=64)
+    try:
+        # (the assembled FP32 operator: the matrix-free one sums with atomics)
+        common = dict(T=1e-3, max_lsqr=8, fixed_counts=1, precision=precision, fp32_operator=1)
+        kp, mp, bp, rp = Q.qpat_reconstruct_ex(lib, fl, chi, sig, Q.qpat_default_params(max_lin=2, **common), k0m0)
+        assert rp.linearisations == 2 and rp.accepted_last
+        kf, mf, bf, rf = Q.qpat_reconstruct_ex(lib, fl, chi, sig, Q.qpat_default_params(max_lin=4, **common), k0m0)
+        kr, mr, br, rr = Q.qpat_reconstruct_ex(lib, fl, chi, sig, Q.qpat_default_params(max_lin=4, **common), k0m0,
+                                               beta_in=bp, lin_done=rp.linearisations)
+        assert rr.linearisations == rf.linearisations
+        np.testing.assert_array_equal(kr, kf)
+        np.testing.assert_array_equal(mr, mf)
+        np.testing.assert_array_equal(br, bf)
+        # the plain entry point is the same run; beta is log(kappa / kappa_0), log(mu / mu_0)
+        kq, mq, _ = Q.qpat_reconstruct(lib, fl, chi, sig, Q.qpat_default_params(max_lin=4, **common), k0m0)
+        np.testing.assert_array_equal(kq, kf)
+        np.testing.assert_array_equal(mq, mf)
+        np.testing.assert_allclose(np.log(kf / rf.kappa0), bf[:om.N], rtol=0, atol=1e-12)
+        with pytest.raises(Q.QpatError):
+            Q.qpat_reconstruct_ex(lib, fl, chi, sig, Q.qpat_default_params(max_lin=4, **common), None,
+                                  beta_in=bp, lin_done=2)
+    finally:
+        lib.close()

@@ -490,3 +490,31 @@ def test_reconstruct_decreases_residual_and_error():
     e_mu = np.linalg.norm(mu - mu_t) / np.linalg.norm(mu_t)
     e_mu0 = np.linalg.norm(k0m0[1] - mu_t) / np.linalg.norm(mu_t)
     assert e_mu < e_mu0
+
+
+def test_reconstruct_resume_equals_one_run():
+    """Checkpoint / resume of Algorithm 1: step 1 restarts from beta^(l)
+    alone, so stopping after l linearisations and resuming from (kappa_0,
+    mu_0, beta^(l), l) reproduces the uninterrupted run exactly; resuming
+    without the background constants is refused."""
+    cfg = S.small_config(7, 12.0, 2, 9)
+    xyz, tets = cfg.mesh()
+    m = O.Mesh(xyz, tets)
+    kap_t, mu_t = cfg.coefficients(xyz)
+    fl = np.stack([O.flux_patch(m, p.center, p.normal, p.half_w) for p in cfg.patches])
+    h = O.measure(m, kap_t, mu_t, fl)
+    sig = 0.01 * np.abs(h) + 1e-12
+    chi = h + sig * S.noise_draws(1, h.shape)
+    k0m0 = (float(np.median(kap_t)), float(np.median(mu_t)))
+    full = O.reconstruct(m, fl, chi, sig, O.QpatParams(T=1e-3, max_lin=4, max_lsqr=8, fixed_counts=True), k0m0)
+    part = O.reconstruct(m, fl, chi, sig, O.QpatParams(T=1e-3, max_lin=2, max_lsqr=8, fixed_counts=True), k0m0)
+    assert part[2].linearisations == 2 and part[2].accepted_last
+    rest = O.reconstruct(m, fl, chi, sig, O.QpatParams(T=1e-3, max_lin=4, max_lsqr=8, fixed_counts=True), k0m0,
+                         beta_in=part[2].beta, lin_done=part[2].linearisations)
+    assert rest[2].linearisations == full[2].linearisations
+    np.testing.assert_array_equal(rest[0], full[0])
+    np.testing.assert_array_equal(rest[1], full[1])
+    np.testing.assert_array_equal(rest[2].beta, full[2].beta)
+    assert rest[2].residuals == full[2].residuals[1:]   # continues the history after beta^(2)
+    with pytest.raises(ValueError):
+        O.reconstruct(m, fl, chi, sig, O.QpatParams(), None, beta_in=part[2].beta, lin_done=2)
