@@ -104,7 +104,11 @@ typedef struct {
                               fewer (and costlier) iterations.  Other variants and
                               the matrix-free FP32 operator use Jacobi.  Default 2. */
     int prior_poly_degree; /* the same for the M_delta solves (default 2) */
-    int reserved[1];
+    int step_halvings;     /* Algorithm 1, not in the paper (default 0 = the
+                              paper's rule): before rejecting a step in step 4,
+                              try beta + 2^-j (beta_new - beta), j = 1..this;
+                              step 0's update is then kept only if one of
+                              x, x/2, ... lowers the residual.  In [0, 16]. */
     double prior_q;        /* q of prior 1, in (0, 2] */
 } qpat_params;
 

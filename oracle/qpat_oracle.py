@@ -519,6 +519,11 @@ class QpatParams:
     fit_gn_steps: int = 10
     prior: int = 0            # 0: Perona-Malik (Eq. (10)); 1: smoothed TV^q (tvq_r)
     prior_q: float = 1.0
+    # Not in the paper (an option, off by default): before rejecting a step
+    # in step 4, try beta + 2^-j (beta_new - beta) for j = 1..step_halvings;
+    # step 0's update is then also accepted only if it lowers the residual
+    # (first of x, x/2, ...; otherwise kappa_tilde_init is kept).
+    step_halvings: int = 0
 
 
 def nonlinear_residual(chi, h, w) -> float:
@@ -671,10 +676,23 @@ def reconstruct(mesh: Mesh, flux, chi, sigma, params: QpatParams,
         A0 = lambda v: jvp(mesh, kap, mu, phi, np.concatenate([v, zeros]), w, fac).ravel()
         AT0 = lambda u: vjp(mesh, kap, mu, phi, u.reshape(K, N), w, fac)[:N]
         res0 = lsqr_prior(A0, AT0, Mk.solve, yhat, P.max_lsqr, P.m0, P.tau, P.fixed_counts)
-        kt = kt + res0.x
         rep.lsqr_iters.append(res0.iters)
         rep.lsqr_phibar.append(res0.phibar)
         rep.linearisations = 1
+        if P.step_halvings > 0:
+            # option: keep the first of x, x/2, ... that lowers the residual at beta_init
+            r_init = nonlinear_residual(chi, h, w)
+            kt_acc = kt
+            for j in range(P.step_halvings + 1):
+                kt_c = kt + res0.x if j == 0 else kt + res0.x * 0.5 ** j
+                kc, mc = k0 * np.exp(kt_c), m0_ * np.exp(mt)
+                _, hc = forward(mesh, kc, mc, flux, Factor(system_matrix(mesh, kc, mc)))
+                if nonlinear_residual(chi, hc, w) < r_init:
+                    kt_acc = kt_c
+                    break
+            kt = kt_acc
+        else:
+            kt = kt + res0.x
         beta = np.concatenate([kt, mt])
 
     # step 1 needs h(beta^(l))
@@ -698,11 +716,17 @@ def reconstruct(mesh: Mesh, flux, chi, sigma, params: QpatParams,
         rep.lsqr_phibar.append(res.phibar)
         rep.linearisations += 1
         beta_new = res.x
-        # step 4: accept only if the nonlinear residual decreased
-        kap_n, mu_n = coeffs(beta_new)
-        fac_n = Factor(system_matrix(mesh, kap_n, mu_n))
-        phi_n, h_n = forward(mesh, kap_n, mu_n, flux, fac_n)
-        r_new = nonlinear_residual(chi, h_n, w)
+        # step 4: accept only if the nonlinear residual decreased (option:
+        # first try the shorter steps beta + 2^-j (beta_new - beta))
+        for j in range(P.step_halvings + 1):
+            cand = beta_new if j == 0 else beta + (beta_new - beta) * 0.5 ** j
+            kap_n, mu_n = coeffs(cand)
+            fac_n = Factor(system_matrix(mesh, kap_n, mu_n))
+            phi_n, h_n = forward(mesh, kap_n, mu_n, flux, fac_n)
+            r_new = nonlinear_residual(chi, h_n, w)
+            if r_new < r_cur:
+                beta_new = cand
+                break
         if r_new >= r_cur:
             rep.accepted_last = False
             break

@@ -158,6 +158,13 @@ __global__ void k_xw(int64_t n, const double* S, const double* v, double* x, dou
 }
 
 // beta_new = beta_old + x (kappa block only when kappa_only)
+__global__ void k_halve(int64_t n, double* x) { FOR_I(n) x[i] *= 0.5; }
+
+// out = beta + t (beta_new - beta) over the 2N entries (shortened step)
+__global__ void k_beta_step(int64_t n, double t, const double* beta, const double* beta_new, double* out) {
+    FOR_I(n) out[i] = beta[i] + (beta_new[i] - beta[i]) * t;
+}
+
 // beta (interleaved per node) from its two blocks
 __global__ void k_pack_beta(int64_t N, const double* s1, const double* s2, double* beta) {
     FOR_I(N) {
@@ -346,6 +353,8 @@ static int reconstruct_impl(qpat_mesh_t M, const qpat_params* prm_in, int K, con
         return fail(QPAT_EINVAL, "qpat_reconstruct: max_lin must be in [1, 32], max_lsqr >= 0, m0 >= 1");
     if (!(prm.T > 0) || !(prm.delta > 0) || !(prm.b_over_a > 0))
         return fail(QPAT_EINVAL, "qpat_reconstruct: T, delta, b/a must be positive");
+    if (prm.step_halvings < 0 || prm.step_halvings > 16)
+        return fail(QPAT_EINVAL, "qpat_reconstruct: step_halvings must lie in [0, 16]");
     DeviceGuard dg(M->device);
     const auto t0 = std::chrono::steady_clock::now();
     Recon rc{};
@@ -496,8 +505,36 @@ static int reconstruct_impl(qpat_mesh_t M, const qpat_params* prm_in, int K, con
         k_unpack_beta<<<GS(N)>>>(N, beta, 0, ktmp, mtmp);
         rc.ckq(prepare_prior(M, ktmp, mtmp, prm.T, prm.prior, prm.prior_q, prm.b_over_a, prm.delta, P, s));
         int it0 = lsqr(rc, LA, P, ytil, 1, prm, xls, hist);
-        qpat::note_launch(1);
-        k_add_beta<<<GS(N)>>>(N, xls, 1, beta);
+        if (prm.step_halvings > 0) {
+            // option: keep the first of x, x/2, ... that lowers the residual at beta_init
+            const double r_init = rc.residual(LA);
+            double* binit = rc.buf("binit", 2 * N);
+            double* bcand = rc.buf("bcand", 2 * N);
+            rc.ck(cudaMemcpyAsync(binit, beta, 2 * N * sizeof(double), cudaMemcpyDeviceToDevice, s), "copy");
+            bool kept = false;
+            for (int j = 0; j <= prm.step_halvings && !kept; ++j) {
+                rc.ck(cudaMemcpyAsync(bcand, binit, 2 * N * sizeof(double), cudaMemcpyDeviceToDevice, s), "copy");
+                if (j > 0) {
+                    qpat::note_launch(1);
+                    k_halve<<<GS(2 * N)>>>(2 * N, xls);  // x / 2^j (exact: powers of two)
+                }
+                qpat::note_launch(1);
+                k_add_beta<<<GS(N)>>>(N, xls, 1, bcand);
+                qpat::note_launch(1);
+                k_coef_from_beta<<<GS(N)>>>(N, 0, k0, bcand, kapB);
+                qpat::note_launch(1);
+                k_coef_from_beta<<<GS(N)>>>(N, 1, m0, bcand, muB);
+                rc.lin(LB, kapB, muB, phiB, "rKB");
+                rc.ckq(forward_lib(M, rc.so, LB, rc.flux, s));
+                if (rc.residual(LB) < r_init) {
+                    rc.ck(cudaMemcpyAsync(beta, bcand, 2 * N * sizeof(double), cudaMemcpyDeviceToDevice, s), "copy");
+                    kept = true;
+                }
+            }
+        } else {
+            qpat::note_launch(1);
+            k_add_beta<<<GS(N)>>>(N, xls, 1, beta);
+        }
         report.lsqr_iters[0] = it0;
         report.linearisations = 1;
         }
@@ -537,14 +574,31 @@ static int reconstruct_impl(qpat_mesh_t M, const qpat_params* prm_in, int K, con
             const int it = lsqr(rc, *cur, P, ytil, 0, prm, betaN, hist);
             report.lsqr_iters[report.linearisations] = it;
             report.linearisations += 1;
-            // step 4: accept only if the nonlinear residual decreased
-            qpat::note_launch(1);
-            k_coef_from_beta<<<GS(N)>>>(N, 0, k0, betaN, kapN);
-            qpat::note_launch(1);
-            k_coef_from_beta<<<GS(N)>>>(N, 1, m0, betaN, muN);
-            rc.lin(*nxt, kapN, muN, phiN, tagN);
-            rc.ckq(forward_lib(M, rc.so, *nxt, rc.flux, s));
-            const double r_new = rc.residual(*nxt);
+            // step 4: accept only if the nonlinear residual decreased (option:
+            // first try the shorter steps beta + 2^-j (beta_new - beta))
+            double r_new = INFINITY;
+            for (int j = 0; j <= prm.step_halvings; ++j) {
+                const double* cand = betaN;
+                if (j > 0) {
+                    double* bc = rc.buf("bstep", 2 * N);
+                    qpat::note_launch(1);
+                    k_beta_step<<<GS(2 * N)>>>(2 * N, std::ldexp(1.0, -j), beta, betaN, bc);
+                    cand = bc;
+                }
+                qpat::note_launch(1);
+                k_coef_from_beta<<<GS(N)>>>(N, 0, k0, cand, kapN);
+                qpat::note_launch(1);
+                k_coef_from_beta<<<GS(N)>>>(N, 1, m0, cand, muN);
+                rc.lin(*nxt, kapN, muN, phiN, tagN);
+                rc.ckq(forward_lib(M, rc.so, *nxt, rc.flux, s));
+                r_new = rc.residual(*nxt);
+                if (r_new < r_cur) {
+                    if (j > 0)
+                        rc.ck(cudaMemcpyAsync(betaN, cand, 2 * N * sizeof(double), cudaMemcpyDeviceToDevice, s),
+                              "copy");
+                    break;
+                }
+            }
             if (!(r_new < r_cur)) {
                 report.accepted_last = 0;
                 break;

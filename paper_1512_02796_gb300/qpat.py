@@ -31,7 +31,7 @@ class qpat_params(ctypes.Structure):
         ("max_pcg_iter", ctypes.c_int), ("pcg_rtol", ctypes.c_double), ("fit_grid", ctypes.c_int),
         ("fit_gn_steps", ctypes.c_int), ("patch_nodes", ctypes.c_int), ("fp32_operator", ctypes.c_int),
         ("pcg_variant", ctypes.c_int), ("prior", ctypes.c_int), ("mixed_restart", ctypes.c_int),
-        ("poly_degree", ctypes.c_int), ("prior_poly_degree", ctypes.c_int), ("reserved", ctypes.c_int * 1),
+        ("poly_degree", ctypes.c_int), ("prior_poly_degree", ctypes.c_int), ("step_halvings", ctypes.c_int),
         ("prior_q", ctypes.c_double),
     ]
 

@@ -518,3 +518,41 @@ def test_reconstruct_resume_equals_one_run():
     assert rest[2].residuals == full[2].residuals[1:]   # continues the history after beta^(2)
     with pytest.raises(ValueError):
         O.reconstruct(m, fl, chi, sig, O.QpatParams(), None, beta_in=part[2].beta, lin_done=2)
+
+
+def test_reconstruct_step_halving_option():
+    """The step-halving option (not in the paper; off by default) only
+    changes what happens to a step that Algorithm 1 would reject: the accepted
+    prefix of a default run is reproduced exactly, every accepted step lowers
+    the residual, and on the Test 2 stand-in (two opposite illuminations),
+    where the default run's kappa-only step 0 diverges, it stays bounded and
+    fits the data to the noise level."""
+    cfg = S.small_config(7, 12.0, 2, 9)
+    xyz, tets = cfg.mesh()
+    m = O.Mesh(xyz, tets)
+    kap_t, mu_t = cfg.coefficients(xyz)
+    fl = np.stack([O.flux_patch(m, p.center, p.normal, p.half_w) for p in cfg.patches])
+    h = O.measure(m, kap_t, mu_t, fl)
+    sig = 0.01 * np.abs(h) + 1e-12
+    chi = h + sig * S.noise_draws(1, h.shape)
+    k0m0 = (float(np.median(kap_t)), float(np.median(mu_t)))
+    d = O.reconstruct(m, fl, chi, sig, O.QpatParams(T=1e-3, max_lin=5, max_lsqr=50), k0m0)[2]
+    hv = O.reconstruct(m, fl, chi, sig, O.QpatParams(T=1e-3, max_lin=5, max_lsqr=50, step_halvings=4), k0m0)[2]
+    assert not d.accepted_last                                  # the default run stops at a rejected step
+    assert hv.residuals[:len(d.residuals)] == d.residuals        # same accepted prefix, bit for bit
+    assert hv.linearisations > d.linearisations
+    assert all(b < a for a, b in zip(hv.residuals, hv.residuals[1:]))
+
+    co = S.Test2Config(9, ("btm", "top"))
+    x2, t2 = co.mesh()
+    m2 = O.Mesh(x2, t2)
+    k2, mu2 = co.coefficients(x2)
+    fl2 = np.stack([O.flux_patch(m2, p.center, p.normal, p.half_w, p.amp) for p in co.patches])
+    h2 = O.measure(m2, k2, mu2, fl2)
+    s2 = 0.01 * np.abs(h2) + 1e-3 * np.abs(h2).max()
+    c2 = h2 + s2 * S.noise_draws(3, h2.shape)
+    kd, _, rd = O.reconstruct(m2, fl2, c2, s2, O.QpatParams())
+    kh, _, rh = O.reconstruct(m2, fl2, c2, s2, O.QpatParams(step_halvings=6))
+    assert np.abs(np.log(kd / rd.kappa0)).max() > 20          # default: step 0 diverges
+    assert np.abs(np.log(kh / rh.kappa0)).max() < 2
+    assert rh.residuals[-1] < 1.5 * np.sqrt(h2.size)           # whitened noise level sqrt(K N)
