@@ -523,14 +523,16 @@ def illumination_study(Q, n: int = 38, seed: int = 17):
     out = {"study": "illuminations (Test 2 stand-in)", "n": n, "nodes": mesh.N, "fine_nodes": fine.N,
            "noise": "1 % + floor 1e-3 max|h|", "params": "library defaults (paper's stopping rules), FP64",
            "runs": {}}
-    for label, cap in (("lsqr cap 50 (default)", 50), ("lsqr cap 20", 20)):
+    for label, cap, halvings in (("lsqr cap 50 (default)", 50, 0), ("lsqr cap 20", 20, 0),
+                                 ("step halving 6 (option, not in the paper)", 50, 6)):
         res = {}
         for st in (("btm",), ("btm", "rgt"), ("btm", "top"), ("btm", "rgt", "bck"), ("btm", "top", "bck")):
             ix = [faces.index(f) for f in st]
             t0 = time.perf_counter()
             try:
                 kap, mu, rep = Q.qpat_reconstruct(mesh, flux[ix], chi[ix], sig[ix],
-                                                  Q.qpat_default_params(precision=0, max_lsqr=cap))
+                                                  Q.qpat_default_params(precision=0, max_lsqr=cap,
+                                                                        step_halvings=halvings))
             except Q.QpatError as e:   # e.g. a K solve at an iterate with exp(30)-scale kappa jumps
                 res["+".join(st)] = {"failed": str(e), "wall_s": time.perf_counter() - t0}
                 continue
