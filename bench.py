@@ -166,8 +166,8 @@ def fp64_peak_tflops(sm_mhz: float, nsm: int) -> float:
     return 4.0 * nsm * sm_mhz * 1e6 / 1e12
 
 
-def setup_problem(Q, torch, precision: int):
-    cfg = S.config(WORKLOAD)
+def setup_problem(Q, torch, precision: int, workload: str = None):
+    cfg = S.config(workload or WORKLOAD)
     xyz, tets = cfg.mesh()
     kappa, mu = cfg.coefficients(xyz)
     mesh = Q.qpat_mesh(xyz, tets)
@@ -212,7 +212,7 @@ def run_ours(args):
         prm.poly_degree = args.poly
     if args.prior_poly is not None:
         prm.prior_poly_degree = args.prior_poly
-    d = setup_problem(Q, torch, precision)
+    d = setup_problem(Q, torch, precision, args.workload)
     mesh = d["mesh"]
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")  # 256 MB > L2
 
@@ -344,7 +344,7 @@ def run_ours(args):
         "warmup": args.warmup, "ms_per_step": tot_ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None,   # replicas: per-GPU work fixed as N grows
         "dtype": "f32+f64-refine" if precision == 1 else "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "nodes": N, "tets": d["E"], "illuminations": K,
+        "config": {"workload": args.workload, "nodes": N, "tets": d["E"], "illuminations": K,
                    "pair_rhs": R, "precision": args.precision, "pcg_rtol": prm.pcg_rtol,
                    "preconditioner": {"K": f"patch-local Chebyshev, degree {pair_deg}" if pair_deg else "Jacobi",
                                       "M_delta": (f"patch-local Chebyshev, degree {prm.prior_poly_degree}"
@@ -706,7 +706,7 @@ def run_reference(args):
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None,
-        "dtype": "f64", "data": "synthetic", "config": {"workload": WORKLOAD, "sample": sample},
+        "dtype": "f64", "data": "synthetic", "config": {"workload": args.workload, "sample": sample},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }), flush=True)
@@ -741,6 +741,7 @@ def main():
     ap.add_argument("--illumination-study", action="store_true",
                     help="run the Test 2 illumination-count study on its synthetic stand-in and exit")
     ap.add_argument("--study-n", type=int, default=38, help="nodes per side of the study's coarse mesh")
+    ap.add_argument("--workload", default=WORKLOAD, choices=list(S.CONFIG_NAMES[1:]))
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)

@@ -110,6 +110,21 @@ typedef struct {
                               step 0's update is then kept only if one of
                               x, x/2, ... lowers the residual.  In [0, 16]. */
     double prior_q;        /* q of prior 1, in (0, 2] */
+    int lsqr_reorth;       /* LSQR of Algorithm 1 (step 0 and step 3): 1 (default) =
+                              with full reorthogonalisation of both Golub-Kahan
+                              bases (classical Gram-Schmidt, twice), which gives
+                              the iterates of exact arithmetic to rounding;
+                              0 = the plain recurrence.  The same method in exact
+                              arithmetic; in floating point the plain recurrence
+                              loses orthogonality after a few tens of rounds (the
+                              1/delta mode of M_delta^-1 re-enters), and one
+                              50-round sweep then moves by percents under 1e-13
+                              perturbations of the solves.  Keeps
+                              (max_lsqr + 1) x (K N + 4 N) doubles on the device. */
+    int64_t barrier_spin_limit; /* bounded grid-barrier waits of the persistent
+                              PCG kernels: polls (each ~32 ns of sleep) before a
+                              waiting CTA gives up with QPAT_ETIMEOUT;
+                              0 = library default (about 2 s). */
 } qpat_params;
 
 /* Report of qpat_reconstruct (Algorithm 1). */
@@ -263,14 +278,14 @@ int qpat_forward_guess_dev(qpat_mesh_t mesh, const qpat_params* prm, const doubl
                            const double* phi0, double* phi, double* h, void* stream);
 
 /* Allocation-free forward solve, for callers that cannot allocate device
- * memory when they need the solve (code issued during CUDA graph capture,
- * real-time pipelines that forbid allocator calls after start-up, hosts that
- * budget every byte of GPU memory themselves).  The paper has no
- * counterpart; it computes the same phi = K^-1 f and h = mu * phi as
- * qpat_forward_dev in FP64 (matrix-free operator, Jacobi PCG to a relative
- * residual rtol, at most max_iter iterations), with every scratch vector in
- * one fixed file-scope device array of 4,835,488 doubles (about 39 MB) that
- * each GPU using the library keeps until the process exits.
+ * memory when they need a solve: real-time pipelines that forbid allocator
+ * calls after start-up (cudaMalloc may block on the driver), and hosts that
+ * budget every byte of GPU memory themselves.  The paper has no counterpart;
+ * it computes the same phi = K^-1 f and h = mu * phi as qpat_forward_dev in
+ * FP64 (matrix-free operator, Jacobi PCG to a relative residual rtol, at most
+ * max_iter iterations), with every scratch vector in one fixed file-scope
+ * device array of 4,835,488 doubles (about 39 MB) that each GPU using the
+ * library keeps until the process exits.
  *  - Limit: N x R <= 524,288, R = K rounded up to 1, 2, 4, 8 or 16;
  *    larger problems return QPAT_EINVAL without touching the GPU.
  *  - kappa, mu: N; flux_face: K x F; phi, h: K x N (either may be NULL);
@@ -278,12 +293,13 @@ int qpat_forward_guess_dev(qpat_mesh_t mesh, const qpat_params* prm, const doubl
  *  - The mesh handle must already exist (qpat_mesh allocates).
  *  - The first call on a device looks up the array's device address
  *    (cudaGetSymbolAddress, with that device current; the driver may load
- *    the library's device code then) -- make that first call before any
+ *    the library's device code then); make that first call before any
  *    stream capture.  No call allocates or frees device memory.
- *  - Every call shares the one array: calls that overlap on the GPU (other
- *    streams, other threads, other meshes) race and must be serialised by
- *    the caller.  The call synchronises the stream before returning (it
- *    reads the solver status). */
+ *  - Every call shares the one array, which keeps the last call's contents
+ *    (the call zeroes what must start at zero): calls that overlap on the
+ *    GPU (other streams, other threads, other meshes) race and must be
+ *    serialised by the caller.  The call synchronises the stream before
+ *    returning (it reads the solver status). */
 int qpat_forward_noalloc_dev(qpat_mesh_t mesh, const double* kappa, const double* mu,
                              int K, const double* flux_face, double rtol, int max_iter,
                              double* phi, double* h, void* stream);

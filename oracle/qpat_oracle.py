@@ -40,6 +40,7 @@ __all__ = [
     "assemble_robin", "load_vector", "load_vector_nodal", "flux_patch", "flux_side", "system_matrix", "Factor",
     "forward", "G1_matrix", "G2_matrix", "jvp", "vjp", "lagged_weights", "tvq_r", "tvq_rprime",
     "prior_matrix", "prior_solve", "lsqr_prior", "fit_background", "init_mu",
+    "linearised_data", "step_zero", "linearisation_step",
     "reconstruct", "measure", "nonlinear_residual", "simulate_data",
 ]
 
@@ -427,6 +428,9 @@ def prior_solve(mesh: Mesh, kt, mt, rhs, T: float, b_over_a: float = 1.0,
 # Priorconditioned LSQR (Eqs. (21)-(22))
 # --------------------------------------------------------------------------
 
+BREAKDOWN = 1e-12   # relative size below which a Golub-Kahan direction counts as zero
+
+
 @dataclasses.dataclass
 class LsqrResult:
     x: np.ndarray
@@ -437,7 +441,7 @@ class LsqrResult:
 
 def lsqr_prior(A: Callable, AT: Callable, Pinv: Callable, b: np.ndarray,
                max_iter: int, m0: int = 10, tau: float = 1e-2,
-               fixed_counts: bool = False) -> LsqrResult:
+               fixed_counts: bool = False, reorth: bool = False) -> LsqrResult:
     """LSQR for min |A L^{-1} xt - b|, x = L^{-1} xt, L^T L = P, started from
     xt = 0 and carried out in x-space so that only P^{-1} = M_delta^{-1} is
     applied, once per round (Eq. (21), Sec. 4).
@@ -449,7 +453,17 @@ def lsqr_prior(A: Callable, AT: Callable, Pinv: Callable, b: np.ndarray,
     bidiagonal matrix, giving |A x_m - b| = phibar_m.
     Stops when r_m = 1 - phibar_m / phibar_{m-m0} <= tau for m > m0
     (Eq. (22)), or after max_iter rounds; with fixed_counts it always runs
-    max_iter rounds.  phibar is the residual estimate of Eq. (22)."""
+    max_iter rounds.  phibar is the residual estimate of Eq. (22).
+
+    reorth: full reorthogonalisation (a numerical realisation of the same
+    method, not a change of it).  In exact arithmetic the u's are
+    orthonormal and the v's are P-orthonormal (v_i . P v_j = delta_ij, with
+    q_j = P v_j), so subtracting their components again changes nothing; in
+    floating point it stops the loss of orthogonality that otherwise lets
+    the 1/delta mode of M_delta^-1 re-enter every few rounds.  Each new
+    u-hat is projected off all earlier u's and each new p off all earlier
+    v's (p -= (v_j . p) q_j, which P-orthogonalises z = P^-1 p), both by
+    classical Gram-Schmidt applied twice."""
     beta = np.linalg.norm(b)
     if beta == 0.0:
         return LsqrResult(np.zeros_like(np.asarray(AT(b))), [0.0], 0, False)
@@ -468,20 +482,45 @@ def lsqr_prior(A: Callable, AT: Callable, Pinv: Callable, b: np.ndarray,
     hist = [phibar]
     m = 0
     stopped = False
+    U, V, Qb = [u], [v], [q]
     while m < max_iter:
         m += 1
-        uh = A(v) - alpha * u
+        av = A(v)
+        uh = av - alpha * u
+        if reorth:
+            for _ in range(2):
+                uh = uh - np.stack(U, axis=1) @ (np.stack(U, axis=0) @ uh)
         beta = np.linalg.norm(uh)
-        u = uh / beta if beta > 0 else uh
-        p = AT(u) - beta * q
-        z = Pinv(p)
-        alpha = math.sqrt(max(float(p @ z), 0.0))
-        if alpha > 0:
-            v = z / alpha
-            q = p / alpha
+        # breakdown: a new direction that vanishes against the scale of the
+        # product that made it ends the bidiagonalisation; the rotation
+        # below then completes the exact least-squares solution over the
+        # Krylov space and the iteration stops
+        done = beta <= BREAKDOWN * np.linalg.norm(av)
+        if done:
+            beta = 0.0
+            alpha = 0.0
         else:
-            v = z
-            q = p
+            u = uh / beta
+            atu = AT(u)
+            p = atu - beta * q
+            if reorth:
+                for _ in range(2):
+                    p = p - np.stack(Qb, axis=1) @ (np.stack(V, axis=0) @ p)
+            if np.linalg.norm(p) <= BREAKDOWN * np.linalg.norm(atu):
+                done = True
+                alpha = 0.0
+            else:
+                z = Pinv(p)
+                alpha = math.sqrt(max(float(p @ z), 0.0))
+                if alpha > 0:
+                    v = z / alpha
+                    q = p / alpha
+                else:
+                    done = True
+        if reorth:
+            U.append(u)
+            V.append(v)
+            Qb.append(q)
         rho = math.hypot(rhobar, beta)
         c = rhobar / rho
         s = beta / rho
@@ -492,6 +531,8 @@ def lsqr_prior(A: Callable, AT: Callable, Pinv: Callable, b: np.ndarray,
         x = x + (phi_m / rho) * wd
         wd = v - (theta / rho) * wd
         hist.append(phibar)
+        if done:
+            break
         if not fixed_counts and m > m0:
             r_m = 1.0 - hist[m] / hist[m - m0]
             if r_m <= tau:
@@ -524,6 +565,12 @@ class QpatParams:
     # step 0's update is then also accepted only if it lowers the residual
     # (first of x, x/2, ...; otherwise kappa_tilde_init is kept).
     step_halvings: int = 0
+    # LSQR with full reorthogonalisation (lsqr_prior, reorth): the iterates of
+    # exact arithmetic, to rounding (the reading of step 3's LSQR).  False
+    # runs the plain recurrence, which loses orthogonality after a few tens
+    # of rounds: on the 11^3 cube one 50-round sweep then moves by 1e-2 - 6e-2
+    # under 1e-13 perturbations of the solves (reorthogonalised: ~1e-12).
+    lsqr_reorth: bool = True
 
 
 def nonlinear_residual(chi, h, w) -> float:
@@ -627,6 +674,46 @@ class ReconReport:
     beta: Optional[np.ndarray] = None  # final beta^(l) = [kappa_tilde, mu_tilde]
 
 
+def linearised_data(chi, h, Jbeta, w) -> np.ndarray:
+    """y~ = Gamma^{-1/2} (chi - h(beta^(l)) + J^(l) beta^(l)), stacked over the
+    illuminations (Algorithm 1, step 1; the y^(l) of Eq. (11)).  chi, h, Jbeta
+    and the whitening w = diag(Gamma^{-1/2}) are K x N; returns K N."""
+    return (w * (chi - h + Jbeta)).ravel()
+
+
+def step_zero(mesh: Mesh, kap, mu, phi, h, fac, chi, w, kt, P: QpatParams) -> LsqrResult:
+    """Step 0 of Sec. 5 (Test 1): with J_kappa the Jacobian w.r.t. kappa_tilde
+    alone at (kappa_tilde_init, mu_tilde_init), y^ = Gamma^{-1/2}(chi - h +
+    J_kappa kappa_tilde_init) and the prior M_delta(kappa_tilde_init) =
+    M(kappa_tilde_init) + delta I of the kappa block only, LSQR from zero.
+    kap, mu, phi, h and the factor of K belong to beta_init.  Returns the LSQR
+    result; its x is the new kappa_tilde_init."""
+    K, N = np.atleast_2d(chi).shape
+    zeros = np.zeros(N)
+    Jk = jvp(mesh, kap, mu, phi, np.concatenate([kt, zeros]), None, fac)
+    yhat = linearised_data(chi, h, Jk, w)
+    Mk = Factor(assemble_stiffness(mesh, lagged_weights(mesh, kt, P.T, P.prior, P.prior_q))
+                + P.delta * sp.identity(N, format="csr"))
+    A0 = lambda v: jvp(mesh, kap, mu, phi, np.concatenate([v, zeros]), w, fac).ravel()
+    AT0 = lambda u: vjp(mesh, kap, mu, phi, u.reshape(K, N), w, fac)[:N]
+    return lsqr_prior(A0, AT0, Mk.solve, yhat, P.max_lsqr, P.m0, P.tau, P.fixed_counts, P.lsqr_reorth)
+
+
+def linearisation_step(mesh: Mesh, kap, mu, phi, h, fac, chi, w, beta, P: QpatParams) -> LsqrResult:
+    """Steps 1-3 of Algorithm 1 at beta^(l) (kap, mu, phi, h and the factor of
+    K belong to beta^(l)): y~ of step 1, M_delta = blkdiag(M(kappa_tilde^(l)),
+    (b/a) M(mu_tilde^(l))) + delta I of step 2 (Eqs. (16), (19)), and the
+    priorconditioned LSQR of step 3 from zero (Eqs. (21)-(22)).  Returns the
+    LSQR result; its x is the candidate beta^(l+1) that step 4 tests."""
+    K, N = np.atleast_2d(chi).shape
+    Jb = jvp(mesh, kap, mu, phi, beta, None, fac)
+    ytil = linearised_data(chi, h, Jb, w)
+    Pfac = Factor(prior_matrix(mesh, beta[:N], beta[N:], P.T, P.b_over_a, P.delta, P.prior, P.prior_q))
+    A = lambda v: jvp(mesh, kap, mu, phi, v, w, fac).ravel()
+    AT = lambda u: vjp(mesh, kap, mu, phi, u.reshape(K, N), w, fac)
+    return lsqr_prior(A, AT, Pfac.solve, ytil, P.max_lsqr, P.m0, P.tau, P.fixed_counts, P.lsqr_reorth)
+
+
 def reconstruct(mesh: Mesh, flux, chi, sigma, params: QpatParams,
                 kappa0_mu0=None, beta_in=None, lin_done: int = 0):
     """Algorithm 1 with step 0 (Sec. 5, Test 1) for K stacked illuminations.
@@ -669,13 +756,7 @@ def reconstruct(mesh: Mesh, flux, chi, sigma, params: QpatParams,
         kap, mu = k0 * np.exp(kt), m0_ * np.exp(mt)
         fac = Factor(system_matrix(mesh, kap, mu))
         phi, h = forward(mesh, kap, mu, flux, fac)
-        zeros = np.zeros(N)
-        yhat = (w * (chi - h)).ravel()          # J kt_init = 0 as kt_init = 0
-        Mk = Factor(assemble_stiffness(mesh, lagged_weights(mesh, kt, P.T, P.prior, P.prior_q))
-                    + P.delta * sp.identity(N, format="csr"))
-        A0 = lambda v: jvp(mesh, kap, mu, phi, np.concatenate([v, zeros]), w, fac).ravel()
-        AT0 = lambda u: vjp(mesh, kap, mu, phi, u.reshape(K, N), w, fac)[:N]
-        res0 = lsqr_prior(A0, AT0, Mk.solve, yhat, P.max_lsqr, P.m0, P.tau, P.fixed_counts)
+        res0 = step_zero(mesh, kap, mu, phi, h, fac, chi, w, kt, P)
         rep.lsqr_iters.append(res0.iters)
         rep.lsqr_phibar.append(res0.phibar)
         rep.linearisations = 1
@@ -703,15 +784,8 @@ def reconstruct(mesh: Mesh, flux, chi, sigma, params: QpatParams,
     rep.residuals.append(r_cur)
 
     while rep.linearisations < P.max_lin:
-        # step 1: h, J and y-tilde = Gamma^{-1/2}(chi - h + J beta)
-        Jb = jvp(mesh, kap, mu, phi, beta, None, fac)
-        ytil = (w * (chi - h + Jb)).ravel()
-        # step 2: M_delta from the current iterate
-        Pfac = Factor(prior_matrix(mesh, beta[:N], beta[N:], P.T, P.b_over_a, P.delta, P.prior, P.prior_q))
-        # step 3: priorconditioned LSQR from zero
-        A = lambda v: jvp(mesh, kap, mu, phi, v, w, fac).ravel()
-        AT = lambda u: vjp(mesh, kap, mu, phi, u.reshape(K, N), w, fac)
-        res = lsqr_prior(A, AT, Pfac.solve, ytil, P.max_lsqr, P.m0, P.tau, P.fixed_counts)
+        # steps 1-3: linearise at beta^(l), lagged M_delta, priorconditioned LSQR
+        res = linearisation_step(mesh, kap, mu, phi, h, fac, chi, w, beta, P)
         rep.lsqr_iters.append(res.iters)
         rep.lsqr_phibar.append(res.phibar)
         rep.linearisations += 1

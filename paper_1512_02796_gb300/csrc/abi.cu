@@ -98,6 +98,16 @@ __global__ void k_jt_out(int64_t N, int R, const double* kappa, const double* mu
     }
 }
 
+// Columns [r0, r0 + Rh) of an N x R node-major block to an N x Rh block and back.
+__global__ void k_take_rhs(int64_t N, int R, int r0, int Rh, const double* x, double* xh) {
+    for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < N * Rh; i += int64_t(gridDim.x) * blockDim.x)
+        xh[i] = x[(i / Rh) * R + r0 + (i % Rh)];
+}
+__global__ void k_put_rhs(int64_t N, int R, int r0, int Rh, const double* xh, double* x) {
+    for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < N * Rh; i += int64_t(gridDim.x) * blockDim.x)
+        x[(i / Rh) * R + r0 + (i % Rh)] = xh[i];
+}
+
 __global__ void k_sqrt_vec(int n, const double* in, double* out) {
     if (threadIdx.x < n) out[threadIdx.x] = sqrt(in[threadIdx.x]);
 }
@@ -239,6 +249,42 @@ int solve(qpat_mesh_s* M, const OpState& st, const SolveOpts& so_in, int R, cons
     const int64_t N = M->h.N;
     const int64_t n = N * R;
     cudaError_t e = cudaSuccess;
+    {
+        // More right-hand sides than one launch's shared memory holds on
+        // this mesh's patches (e.g. 16 FP64 RHS on ~1000-node patches): the
+        // block is solved as two halves of R/2, each RHS with the same
+        // arithmetic as in one launch.
+        const bool asm_ = so.precision == 0 || so.fp32_assembled;
+        const bool poly_ok = asm_ && so.pcg_variant != 2 && so.pcg_variant != 3 && st.gbound;
+        const int deg = poly_ok ? (st.kind == OP_PRIOR ? so.poly_prior : so.poly_k) : 0;
+        const int op64 = st.kind == OP_K ? OP_CSR1 : OP_CSR2;
+        bool fits = pcg_fits<double>(md, op64, R, deg) && (!X0 || apply_csr_fits<double>(md, R));
+        if (fits && so.precision == 1)
+            fits = pcg_fits<float>(md, so.fp32_assembled ? OP_CSR1 : OP_K, R, deg) && apply_csr_fits<double>(md, R);
+        if (!fits && R > 1) {
+            const int Rh = R / 2;
+            const std::string tag = "split" + std::to_string(R);
+            double* Bh = M->ws.get<double>(tag + ".b", N * Rh, s, &e);
+            double* Xh = M->ws.get<double>(tag + ".x", N * Rh, s, &e);
+            double* X0h = X0 ? M->ws.get<double>(tag + ".x0", N * Rh, s, &e) : nullptr;
+            if (e != cudaSuccess) return cuda_fail(e, "workspace");
+            for (int half = 0; half < 2; ++half) {
+                qpat::note_launch(1);
+                k_take_rhs<<<grid_of(N * Rh), 256, 0, s>>>(N, R, half * Rh, Rh, B, Bh);
+                if (X0) {
+                    qpat::note_launch(1);
+                    k_take_rhs<<<grid_of(N * Rh), 256, 0, s>>>(N, R, half * Rh, Rh, X0, X0h);
+                }
+                if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "split");
+                const int rc = solve(M, st, so_in, Rh, Bh, Xh, s, X0h);
+                if (rc != QPAT_OK) return rc;
+                qpat::note_launch(1);
+                k_put_rhs<<<grid_of(N * Rh), 256, 0, s>>>(N, R, half * Rh, Rh, Xh, X);
+                if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "split");
+            }
+            return QPAT_OK;
+        }
+    }
     PcgWork w{};
     const char* pfx = st.kind == OP_K ? "pcg" : "pcgP";
     auto nm = [&](const char* a) { return std::string(pfx) + "." + a; };
@@ -252,6 +298,7 @@ int solve(qpat_mesh_s* M, const OpState& st, const SolveOpts& so_in, int R, cons
     w.status = M->ws.get<int>("pcg.status", 1, s, &e);
     w.iters = M->ws.get<int>("pcg.iters", 1, s, &e);
     w.stats = M->ws.get<double>("pcg.stats", 32, s, &e);
+    w.spin_limit = so.spin_limit;
     // PCG variant on the assembled operators (the matrix-free FP32 operator has one)
     const bool assembled = so.precision == 0 || so.fp32_assembled;
     const bool single = assembled && so.pcg_variant == 2;
@@ -502,6 +549,7 @@ void qpat_default_params(qpat_params* p) {
     p->prior_q = 1.0;
     p->poly_degree = 2;        // fastest measured on a 64^3 cube (GB300)
     p->prior_poly_degree = 2;
+    p->lsqr_reorth = 1;        // exact-arithmetic LSQR iterates (see qpat.h)
 }
 
 static int mesh_create(const double* xyz, int64_t N, const int32_t* tets, int64_t E, int patch_nodes,

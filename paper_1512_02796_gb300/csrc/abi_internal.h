@@ -59,6 +59,7 @@ struct SolveOpts {
     int mixed_restart = 0;    // precision 1: 0 reliable updates (keep the direction), 1 restart every sweep
     int poly_k = 0;           // patch-local Chebyshev degree of the K preconditioner (0 Jacobi)
     int poly_prior = 0;       // the same for M_delta
+    long long spin_limit = 0; // grid-barrier polls before a timeout (0 = default)
 };
 
 struct DeviceGuard {

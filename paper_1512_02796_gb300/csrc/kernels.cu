@@ -604,6 +604,21 @@ cudaError_t launch_apply_csr(const MeshDev& m, int NV, int R, const T* v0, const
     }
 }
 
+// Whether k_apply_csr for R right-hand sides fits the device's per-block
+// shared memory (the input vector is staged on the patch's touched nodes).
+template <typename T>
+bool apply_csr_fits(const MeshDev& m, int R) {
+    int dev = 0, optin = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return true;
+    }
+    return sizeof(T) * size_t(m.max_touched) * size_t(R) <= size_t(optin);
+}
+template bool apply_csr_fits<double>(const MeshDev&, int);
+template bool apply_csr_fits<float>(const MeshDev&, int);
+
 template cudaError_t launch_apply_csr<double>(const MeshDev&, int, int, const double*, const double*, const double*,
                                               double*, cudaStream_t);
 template cudaError_t launch_apply_csr<float>(const MeshDev&, int, int, const float*, const float*, const float*,

@@ -71,6 +71,15 @@ cudaError_t launch_cast_d2f(int64_t n, const double* in, float* out, cudaStream_
 // largest degree of the patch-local Chebyshev preconditioner (see pcg.cu)
 constexpr int kMaxPolyDegree = 8;
 
+// Bounds of the persistent PCG kernels' grid reductions: at most kMaxGrid
+// CTAs, each contributing kMaxNS doubles (3 quantities x 16 RHS).  The
+// partials buffer holds 2 x kMaxGrid x kMaxNS + 2 x kMaxNS doubles
+// (pcg_partials_doubles).
+constexpr int kMaxGrid = 152 * 8;
+constexpr int kMaxNS = 48;
+// Default bound of a grid-barrier wait: polls of ~32 ns sleep (about 2 s).
+constexpr long long kDefaultSpinLimit = 40000000LL;
+
 struct PcgWork {
     void* b;  // N x R (T)
     void* x;
@@ -99,6 +108,7 @@ struct PcgWork {
     int* status;        // 1
     int* iters;         // 1
     double* stats;      // 2R: final r.r, b.b
+    long long spin_limit = 0;  // grid-barrier polls before QPAT_ETIMEOUT (0 = default, about 2 s)
 };
 
 // Persistent fused Jacobi-PCG on R right-hand sides (see pcg.cu).  b is
@@ -142,6 +152,12 @@ cudaError_t pcg_batch_prepare(int R, const std::vector<PcgBatchProblem>& probs, 
 cudaError_t pcg_batch_launch(const PcgBatchPlan& plan, cudaStream_t s);
 void pcg_batch_release(PcgBatchPlan& plan);
 
+// Shared-memory fit of the PCG kernel (launch_pcg) and of k_apply_csr for R
+// right-hand sides on this mesh's patches (false: split the RHS).
+template <typename T>
+bool pcg_fits(const MeshDev& m, int OP, int R, int deg);
+template <typename T>
+bool apply_csr_fits(const MeshDev& m, int R);
 int pcg_max_grid();            // upper bound of the cooperative grid
 size_t pcg_partials_doubles();  // size of PcgWork::partials (per-CTA partials + totals)
 

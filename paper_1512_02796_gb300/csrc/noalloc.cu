@@ -1,9 +1,10 @@
 // Allocation-free forward solve.
 //
 // Some callers cannot allocate device memory at the time they need a solve:
-// code running while a CUDA graph is being captured for replay, real-time
-// or embedded pipelines that forbid allocator calls after start-up, and
-// hosts that manage every byte of GPU memory themselves.  For them,
+// real-time or embedded pipelines that forbid allocator calls after start-up
+// (a cudaMalloc can block on the driver and stall the pipeline), and hosts
+// that budget every byte of GPU memory themselves (an allocation inside a
+// library call would break their budget).  For them,
 // qpat_forward_noalloc_dev runs the forward solve phi = K^-1 f (FP64
 // matrix-free PCG, the same kernel as the FP64 path) with all its scratch in
 // one file-scope device array of fixed size, so that the call itself never
@@ -22,8 +23,11 @@ constexpr int64_t kNoallocMaxNR = int64_t(1) << 19;
 // Scratch layout in doubles: kappa, mu, inverse diagonal (N each, N <= max),
 // then six N x R vectors (f, x, r, p0, p1, q), two reduction buffers and a
 // small control block (barrier, status, iteration count, statistics).
-constexpr int64_t kPartials = int64_t(2) * 1216 * 48 + 2 * 48;
+constexpr int64_t kPartials = int64_t(2) * kMaxGrid * kMaxNS + 2 * kMaxNS;  // = pcg_partials_doubles()
 constexpr int64_t kCtl = 64;
+// control block: barrier and status words in ctl[0..2], then 2 x 16 doubles
+// of solver statistics from ctl[8]
+static_assert(8 + 2 * 16 <= kCtl, "control block too small for the solver statistics");
 constexpr int64_t kNoallocDoubles = 3 * kNoallocMaxNR + 6 * kNoallocMaxNR + kPartials + kCtl;
 
 __device__ __align__(256) double g_noalloc_scratch[kNoallocDoubles];
@@ -97,7 +101,8 @@ extern "C" int qpat_forward_noalloc_dev(qpat_mesh_t M, const double* kappa, cons
     if ((e = launch_to_lib<double, double>(M->d, 1, 1, kappa, kl, s)) != cudaSuccess ||
         (e = launch_to_lib<double, double>(M->d, 1, 1, mu, ml, s)) != cudaSuccess)
         return cuda_fail(e, "qpat_forward_noalloc_dev: to_lib");
-    // the load vector accumulates with atomics: it must start at zero
+    // launch_load adds each node's face sums into f and leaves the padded
+    // columns (K <= r < R) untouched: f must start at zero
     if ((e = cudaMemsetAsync(f, 0, sizeof(double) * n, s)) != cudaSuccess)
         return cuda_fail(e, "qpat_forward_noalloc_dev: memset");
     if ((e = launch_load(M->d, K, R, flux_face, f, s)) != cudaSuccess)
@@ -111,6 +116,7 @@ extern "C" int qpat_forward_noalloc_dev(qpat_mesh_t M, const double* kappa, cons
         return cuda_fail(e, "qpat_forward_noalloc_dev: from_lib");
     if (h) {
         k_rowscale_launch(N, R, ml, x, r, s);  // r is free once the solve is done
+        if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "qpat_forward_noalloc_dev: rowscale");
         if ((e = launch_from_lib<double, double>(M->d, K, R, r, h, s)) != cudaSuccess)
             return cuda_fail(e, "qpat_forward_noalloc_dev: from_lib");
     }

@@ -158,6 +158,7 @@ SolveOpts solve_opts(const qpat_params* prm) {
     so.mixed_restart = p->mixed_restart ? 1 : 0;
     so.poly_k = p->poly_degree;
     so.poly_prior = p->prior_poly_degree;
+    so.spin_limit = p->barrier_spin_limit > 0 ? p->barrier_spin_limit : 0;
     return so;
 }
 
@@ -173,6 +174,9 @@ static int check_params(const qpat_params* prm, const char* who) {
         return fail(QPAT_EINVAL, std::string(who) + ": poly_degree and prior_poly_degree must lie in [0, 8]");
     if (prm->prior == 1 && !(prm->prior_q > 0.0 && prm->prior_q <= 2.0))
         return fail(QPAT_EINVAL, std::string(who) + ": prior_q must lie in (0, 2]");
+    if (prm->barrier_spin_limit < 0) return fail(QPAT_EINVAL, std::string(who) + ": barrier_spin_limit must be >= 0");
+    if (prm->lsqr_reorth != 0 && prm->lsqr_reorth != 1)
+        return fail(QPAT_EINVAL, std::string(who) + ": lsqr_reorth must be 0 or 1");
     return QPAT_OK;
 }
 
@@ -230,6 +234,39 @@ int vjp_lib(qpat_mesh_s* M, const SolveOpts& so, LinState& L, const double* t, d
     return QPAT_OK;
 }
 
+namespace {
+// flag = 1 if some a[i] (or b[i]) is not finite, or (positive) not > 0
+__global__ void k_check_coeffs(int64_t n, const double* a, const double* b, int positive, int* flag) {
+    for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x) {
+        const double x = a[i], y = b ? b[i] : 1.0;
+        const bool bad = positive ? !(x > 0.0 && isfinite(x) && y > 0.0 && isfinite(y)) : !(isfinite(x) && isfinite(y));
+        if (bad) *flag = 1;
+    }
+}
+}  // namespace
+
+// Rejects coefficient inputs the operators are not defined for (Eq. (1) needs
+// kappa, mu in L^inf_+: positive and finite; log parameters must be finite)
+// before any assembly: QPAT_EINVAL with `what` in the message.  Reads one
+// flag back (synchronises the stream).
+int check_coeffs(qpat_mesh_s* M, int64_t n, const double* a, const double* b, int positive, const char* what,
+                 cudaStream_t s) {
+    cudaError_t e = cudaSuccess;
+    int* flag = M->ws.get<int>("chk.flag", 1, s, &e);
+    if (e != cudaSuccess) return cuda_fail(e, "workspace");
+    if ((e = cudaMemsetAsync(flag, 0, sizeof(int), s)) != cudaSuccess) return cuda_fail(e, "memset");
+    const int64_t g = std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 152 * 8));
+    qpat::note_launch(1);
+    k_check_coeffs<<<int(g), 256, 0, s>>>(n, a, b, positive, flag);
+    int* hf = reinterpret_cast<int*>(M->host_scratch + 210);
+    if ((e = cudaGetLastError()) != cudaSuccess ||
+        (e = cudaMemcpyAsync(hf, flag, sizeof(int), cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
+        (e = cudaStreamSynchronize(s)) != cudaSuccess)
+        return cuda_fail(e, "coefficient check");
+    if (*hf) return fail(QPAT_EINVAL, std::string(what) + (positive ? " must be positive and finite" : " must be finite"));
+    return QPAT_OK;
+}
+
 // Upload caller-order device inputs into a LinState (library order).
 static int lin_from_caller(qpat_mesh_s* M, const double* kappa, const double* mu, int K, const double* phi,
                            const double* w, LinState& L, cudaStream_t s) {
@@ -245,6 +282,8 @@ static int lin_from_caller(qpat_mesh_s* M, const double* kappa, const double* mu
     if ((e = launch_to_lib<double, double>(M->d, 1, 1, kappa, L.kap, s)) != cudaSuccess ||
         (e = launch_to_lib<double, double>(M->d, 1, 1, mu, L.mu, s)) != cudaSuccess)
         return cuda_fail(e, "to_lib");
+    int rc = check_coeffs(M, N, L.kap, L.mu, 1, "kappa and mu", s);
+    if (rc != QPAT_OK) return rc;
     if (phi && (e = launch_to_lib<double, double>(M->d, K, L.R, phi, L.phi, s)) != cudaSuccess)
         return cuda_fail(e, "to_lib");
     if (w && (e = launch_to_lib<double, double>(M->d, K, L.R, w, L.w, s)) != cudaSuccess)
@@ -547,6 +586,7 @@ int qpat_prior_solve_dev(qpat_mesh_t M, const qpat_params* prm, const double* kt
         (e = launch_to_lib<double, double>(M->d, 1, 1, mt, mtl, s)) != cudaSuccess ||
         (e = launch_to_lib<double, double>(M->d, 2, 2, rhs, bl, s)) != cudaSuccess)
         return cuda_fail(e, "to_lib");
+    if ((rc = check_coeffs(M, N, ktl, mtl, 0, "qpat_prior_solve: kt and mt", s))) return rc;
     OpState st;
     if ((rc = prepare_prior(M, ktl, mtl, p->T, p->prior, p->prior_q, p->b_over_a, p->delta, st, s))) return rc;
     if ((rc = solve(M, st, solve_opts(prm), 2, bl, xl, s))) return rc;

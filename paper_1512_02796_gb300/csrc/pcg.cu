@@ -69,8 +69,7 @@ struct PcgArgs {
     const double* poly_hi = nullptr;
 };
 
-constexpr int kMaxGrid = 152 * 8;
-constexpr int kMaxNS = 48;  // largest reduction: 3 quantities x 16 RHS
+// kMaxGrid, kMaxNS and kDefaultSpinLimit: launch.h
 
 // ---------------------------------------------------------------- vectors
 template <typename T, int VW>
@@ -1474,7 +1473,7 @@ cudaError_t batch_prepare_t(const std::vector<PcgBatchProblem>& probs, PcgBatchP
         a.stats = p.w.stats;
         a.rtol2 = p.rtol * p.rtol;
         a.maxit = p.maxit;
-        a.spin_limit = 40000000LL;
+        a.spin_limit = p.w.spin_limit > 0 ? p.w.spin_limit : kDefaultSpinLimit;
         if (poly) {
             a.z = static_cast<double*>(p.w.z);
             a.poly_deg = p.w.poly_deg;
@@ -1557,7 +1556,7 @@ cudaError_t launch_pcg_t(const MeshDev& m, const OpParams<T>& op, const T* invdi
     a.stats = w.stats;
     a.rtol2 = rtol * rtol;
     a.maxit = maxit;
-    a.spin_limit = 40000000LL;  // about 2 s of __nanosleep(32) spins
+    a.spin_limit = w.spin_limit > 0 ? w.spin_limit : kDefaultSpinLimit;
     a.z = static_cast<T*>(w.z);
     a.resume_gamma = w.resume_gamma;
     a.rz_state = w.rz_state;
@@ -1627,7 +1626,7 @@ cudaError_t launch_pcg_ring_t(const MeshDev& m, const OpParams<T>& op, const T* 
     a.stats = w.stats;
     a.rtol2 = rtol * rtol;
     a.maxit = maxit;
-    a.spin_limit = 40000000LL;
+    a.spin_limit = w.spin_limit > 0 ? w.spin_limit : kDefaultSpinLimit;
     err = cudaMemsetAsync(w.bar, 0, 2 * sizeof(unsigned), s);
     if (err != cudaSuccess) return err;
     err = cudaMemsetAsync(w.status, 0, sizeof(int), s);
@@ -1722,6 +1721,60 @@ cudaError_t launch_pcg(const MeshDev& m, int OP, int R, const OpParams<T>& op, c
         default: return cudaErrorInvalidValue;
     }
 }
+
+// Whether the two-reduction PCG kernel that launch_pcg picks for (OP, R,
+// polynomial degree) fits the device's per-block shared memory: the staged
+// direction on the touched nodes, the preconditioner's three owned-row
+// vectors, or the matrix-free operator's patch geometry, plus the kernel's
+// static shared arrays.
+template <typename T, int R, int OP>
+bool pcg_fits_t(const MeshDev& m, int deg) {
+    constexpr bool kCsr = OP == OP_CSR1 || OP == OP_CSR2;
+    if (!kCsr) deg = 0;
+    size_t smem = kCsr ? sizeof(T) * size_t(m.max_touched) * R : PatchSmem<T, R>::bytes(m.max_touched, m.max_own);
+    if (deg > 0) smem = std::max(smem, 3 * sizeof(T) * size_t(m.max_own) * R);
+    void (*kern)(PcgArgs<T>) = nullptr;
+    if constexpr (kCsr) {
+        kern = deg > 0 ? k_pcg<T, R, OP, true> : k_pcg<T, R, OP>;
+    } else {
+        kern = k_pcg<T, R, OP>;
+    }
+    cudaFuncAttributes fa{};
+    int dev = 0, optin = 0;
+    cudaGetDevice(&dev);
+    if (cudaFuncGetAttributes(&fa, kern) != cudaSuccess ||
+        cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return true;  // let the launch report the error
+    }
+    return smem + fa.sharedSizeBytes <= size_t(optin);
+}
+
+template <typename T>
+bool pcg_fits(const MeshDev& m, int OP, int R, int deg) {
+    if (OP == OP_PRIOR) return R != 2 || pcg_fits_t<T, 2, OP_PRIOR>(m, deg);
+    if (OP == OP_CSR2) return R != 2 || pcg_fits_t<T, 2, OP_CSR2>(m, deg);
+    if (OP == OP_CSR1) {
+        switch (R) {
+            case 1: return pcg_fits_t<T, 1, OP_CSR1>(m, deg);
+            case 2: return pcg_fits_t<T, 2, OP_CSR1>(m, deg);
+            case 4: return pcg_fits_t<T, 4, OP_CSR1>(m, deg);
+            case 8: return pcg_fits_t<T, 8, OP_CSR1>(m, deg);
+            case 16: return pcg_fits_t<T, 16, OP_CSR1>(m, deg);
+            default: return true;
+        }
+    }
+    switch (R) {
+        case 1: return pcg_fits_t<T, 1, OP_K>(m, deg);
+        case 2: return pcg_fits_t<T, 2, OP_K>(m, deg);
+        case 4: return pcg_fits_t<T, 4, OP_K>(m, deg);
+        case 8: return pcg_fits_t<T, 8, OP_K>(m, deg);
+        case 16: return pcg_fits_t<T, 16, OP_K>(m, deg);
+        default: return true;
+    }
+}
+template bool pcg_fits<double>(const MeshDev&, int, int, int);
+template bool pcg_fits<float>(const MeshDev&, int, int, int);
 
 template <typename T>
 cudaError_t launch_pcg1(const MeshDev& m, int OP, int R, const OpParams<T>& op, const T* invdiag,

@@ -14,6 +14,7 @@
 #include <chrono>
 #include <cmath>
 #include <cstring>
+#include <initializer_list>
 #include <stdexcept>
 #include <string>
 #include <vector>
@@ -32,7 +33,66 @@ int gridn(int64_t n) {
 #define GS(n) gridn(n), 256, 0, s
 #define FOR_I(n) for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < (n); i += int64_t(gridDim.x) * blockDim.x)
 
-enum { S_ALPHA = 0, S_BETA, S_RHOBAR, S_PHIBAR, S_RHO, S_C, S_S, S_THETA, S_PHI, S_T0, S_T1, S_COUNT = 16 };
+enum { S_ALPHA = 0, S_BETA, S_RHOBAR, S_PHIBAR, S_RHO, S_C, S_S, S_THETA, S_PHI, S_T0, S_T1, S_T2, S_T3,
+       S_COUNT = 16 };
+
+// A Golub-Kahan direction whose norm falls below this fraction of the norm of
+// the product that made it counts as zero: the bidiagonalisation has
+// exhausted the Krylov space, the last rotation completes the exact
+// least-squares solution and LSQR stops (the oracle uses the same rule).
+constexpr double kBreakdown = 1e-12;
+
+// Full reorthogonalisation (qpat_params.lsqr_reorth): projections against
+// the stored bases, two passes of classical Gram-Schmidt.  Partial dot
+// products over kChunks slices of each stored vector, then a fixed-order sum
+// per vector, so the coefficients are the same from run to run.
+constexpr int kChunks = 64;
+
+// part[j * kChunks + c] = sum over slice c of B_j . x   (B_j = B + j * n)
+__global__ void k_mdot_partial(int64_t n, const double* __restrict__ B, const double* __restrict__ x,
+                               double* __restrict__ part) {
+    const int c = blockIdx.x, j = blockIdx.y;
+    const int64_t len = (n + kChunks - 1) / kChunks;
+    const int64_t b = int64_t(c) * len, e = b + len < n ? b + len : n;
+    const double* Bj = B + int64_t(j) * n;
+    double a = 0.0;
+    for (int64_t i = b + threadIdx.x; i < e; i += blockDim.x) a += Bj[i] * x[i];
+    __shared__ double sh[256 / 32];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = a;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < int(blockDim.x >> 5); ++w) t += sh[w];
+        part[j * kChunks + c] = t;
+    }
+}
+
+// coef[j] = sum_c part[j * kChunks + c], one warp per stored vector
+__global__ void k_mdot_final(int m, const double* __restrict__ part, double* __restrict__ coef) {
+    const int j = blockIdx.x;
+    if (j >= m) return;
+    double a = 0.0;
+    for (int c = threadIdx.x; c < kChunks; c += 32) a += part[j * kChunks + c];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+    if (threadIdx.x == 0) coef[j] = a;
+}
+
+// y -= sum_j coef[j] C_j   (C_j = C + j * n), j = 0 .. m-1 in order
+__global__ void k_msub(int64_t n, int m, const double* __restrict__ C, const double* __restrict__ coef,
+                       double* __restrict__ y) {
+    FOR_I(n) {
+        double a = y[i];
+        for (int j = 0; j < m; ++j) a -= coef[j] * C[int64_t(j) * n + i];
+        y[i] = a;
+    }
+}
+
+__global__ void k_set_scalar(double* S, int idx, double v) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) S[idx] = v;
+}
 
 __global__ void k_fill(int64_t n, double v, double* out) { FOR_I(n) out[i] = v; }
 
@@ -104,15 +164,17 @@ __global__ void k_p_update(int64_t N, const double* o1, const double* o2, const 
     }
 }
 
-// v = z / alpha, q = p / alpha ; on the first round also w_d = v, x = 0
+// v = z / alpha, q = p / alpha ; on the first round also w_d = v, x = 0.
+// alpha = 0 (breakdown) leaves v and q as they are.
 __global__ void k_vq(int64_t n, const double* z, const double* p, const double* S, double* v, double* q, int first,
                      double* wd, double* x) {
     const double a = S[S_ALPHA];
-    const double inv = a > 0.0 ? 1.0 / a : 0.0;
+    if (!(a > 0.0)) return;
+    const double inv = 1.0 / a;
     FOR_I(n) {
-        const double vi = a > 0.0 ? z[i] * inv : z[i];
+        const double vi = z[i] * inv;
         v[i] = vi;
-        q[i] = a > 0.0 ? p[i] * inv : p[i];
+        q[i] = p[i] * inv;
         if (first) {
             wd[i] = vi;
             x[i] = 0.0;
@@ -242,7 +304,11 @@ struct Recon {
 };
 
 // One priorconditioned LSQR sweep (oracle: lsqr_prior).  b: N x R data
-// vector; x: N x 2 result.  Returns rounds run.
+// vector; x: N x 2 result.  Returns rounds run.  With prm.lsqr_reorth the
+// u's (N x R) and the v's and q = M_delta v (N x 2) are kept and every new
+// u-hat and p is projected off them (two classical Gram-Schmidt passes).
+// A direction that vanishes against the product that made it (kBreakdown)
+// ends the sweep after its last rotation, as in the oracle.
 int lsqr(Recon& rc, LinState& L, const OpState& P, const double* b, int kappa_only, const qpat_params& prm,
          double* x, std::vector<double>& hist_out) {
     const int64_t N = rc.N, R = rc.R;
@@ -259,7 +325,38 @@ int lsqr(Recon& rc, LinState& L, const OpState& P, const double* b, int kappa_on
     double* o1 = rc.buf("o1", N);
     double* o2 = rc.buf("o2", N);
     double* S = rc.S;
+    double* hs = rc.M->host_scratch;
     const int maxit = std::max(0, prm.max_lsqr);
+    const bool reorth = prm.lsqr_reorth != 0;
+    const int64_t nu = N * R, nv = 2 * N;
+    double *Ub = nullptr, *Vb = nullptr, *Qb = nullptr, *cf = nullptr, *cpart = nullptr;
+    if (reorth) {
+        Ub = rc.buf("Ub", size_t(nu) * (maxit + 1));
+        Vb = rc.buf("Vb", size_t(nv) * (maxit + 1));
+        Qb = rc.buf("Qb", size_t(nv) * (maxit + 1));
+        cf = rc.buf("cf", maxit + 1);
+        cpart = rc.buf("cpart", size_t(maxit + 1) * kChunks);
+    }
+    // y -= Bsub (Bdot^T y) over the first m stored vectors, twice
+    auto project = [&](double* y, const double* Bdot, const double* Bsub, int64_t n, int m) {
+        for (int pass = 0; pass < 2; ++pass) {
+            qpat::note_launch(3);
+            k_mdot_partial<<<dim3(kChunks, m), 256, 0, s>>>(n, Bdot, y, cpart);
+            k_mdot_final<<<m, 32, 0, s>>>(m, cpart, cf);
+            k_msub<<<GS(n)>>>(n, m, Bsub, cf, y);
+        }
+    };
+    auto store = [&](int j) {
+        rc.ck(cudaMemcpyAsync(Ub + j * nu, u, nu * sizeof(double), cudaMemcpyDeviceToDevice, s), "copy");
+        rc.ck(cudaMemcpyAsync(Vb + j * nv, v, nv * sizeof(double), cudaMemcpyDeviceToDevice, s), "copy");
+        rc.ck(cudaMemcpyAsync(Qb + j * nv, q, nv * sizeof(double), cudaMemcpyDeviceToDevice, s), "copy");
+    };
+    // S[idx[k]] -> hs[k] (scalars the host needs for a decision)
+    auto readS = [&](std::initializer_list<int> idx) {
+        int k = 0;
+        for (int i : idx) rc.ck(cudaMemcpyAsync(hs + k++, S + i, sizeof(double), cudaMemcpyDeviceToHost, s), "copy");
+        rc.ck(cudaStreamSynchronize(s), "sync");
+    };
     hist_out.assign(1, 0.0);
     // beta u = b
     rc.ck(cudaMemcpyAsync(u, b, N * R * sizeof(double), cudaMemcpyDeviceToDevice, s), "copy");
@@ -278,45 +375,77 @@ int lsqr(Recon& rc, LinState& L, const OpState& P, const double* b, int kappa_on
     k_p_update<<<GS(N)>>>(N, o1, o2, q, S, 1, kappa_only, p);
     rc.ckq(solve(rc.M, P, rc.so, 2, p, z, s));
     rc.ck(launch_dots<double>(2 * N, 1, p, z, rc.dpart, S + S_T1, s), "dot");
+    readS({S_T1});
+    hist_out[0] = std::sqrt(bb);
+    if (!(hs[0] > 0.0)) {
+        rc.ck(cudaMemsetAsync(x, 0, 2 * N * sizeof(double), s), "memset");
+        return 0;
+    }
     qpat::note_launch(1);
     k_scal_set<<<1, 32, 0, s>>>(S, S_ALPHA, S_T1, 0);
     qpat::note_launch(1);
     k_vq<<<GS(2 * N)>>>(2 * N, z, p, S, v, q, 1, wd, x);
     qpat::note_launch(1);
     k_lsqr_init_scalars<<<1, 32, 0, s>>>(S, rc.hist);
-    hist_out[0] = std::sqrt(bb);
+    if (reorth) store(0);
     int m = 0;
     while (m < maxit) {
         ++m;
+        bool done = false;
         // u = (A v - alpha u) / beta
         qpat::note_launch(1);
         k_unpack_beta<<<GS(N)>>>(N, v, kappa_only, s1, s2);
         rc.ckq(jvp_lib(rc.M, rc.so, L, s1, s2, Av, s));
         qpat::note_launch(1);
         k_uh<<<GS(N * R)>>>(N * R, Av, S, u, 0);
+        if (reorth) project(u, Ub, Ub, nu, m);
         rc.ck(launch_dots<double>(N * R, 1, u, u, rc.dpart, S + S_T0, s), "dot");
-        qpat::note_launch(1);
-        k_scal_set<<<1, 32, 0, s>>>(S, S_BETA, S_T0, 0);
-        qpat::note_launch(1);
-        k_scale_inv<<<GS(N * R)>>>(N * R, S, S_BETA, u);
-        // p = A^T u - beta q ; z = P^-1 p ; alpha = sqrt(p.z) ; v = z/alpha ; q = p/alpha
-        rc.ckq(vjp_lib(rc.M, rc.so, L, u, o1, o2, s));
-        qpat::note_launch(1);
-        k_p_update<<<GS(N)>>>(N, o1, o2, q, S, 0, kappa_only, p);
-        rc.ckq(solve(rc.M, P, rc.so, 2, p, z, s));
-        rc.ck(launch_dots<double>(2 * N, 1, p, z, rc.dpart, S + S_T1, s), "dot");
-        qpat::note_launch(1);
-        k_scal_set<<<1, 32, 0, s>>>(S, S_ALPHA, S_T1, 0);
-        qpat::note_launch(1);
-        k_vq<<<GS(2 * N)>>>(2 * N, z, p, S, v, q, 0, wd, x);
+        rc.ck(launch_dots<double>(N * R, 1, Av, Av, rc.dpart, S + S_T2, s), "dot");
+        readS({S_T0, S_T2});
+        if (hs[0] <= kBreakdown * kBreakdown * hs[1]) {
+            done = true;
+            qpat::note_launch(2);
+            k_set_scalar<<<1, 32, 0, s>>>(S, S_BETA, 0.0);
+            k_set_scalar<<<1, 32, 0, s>>>(S, S_ALPHA, 0.0);
+        } else {
+            qpat::note_launch(1);
+            k_scal_set<<<1, 32, 0, s>>>(S, S_BETA, S_T0, 0);
+            qpat::note_launch(1);
+            k_scale_inv<<<GS(N * R)>>>(N * R, S, S_BETA, u);
+            // p = A^T u - beta q ; z = P^-1 p ; alpha = sqrt(p.z) ; v = z/alpha ; q = p/alpha
+            rc.ckq(vjp_lib(rc.M, rc.so, L, u, o1, o2, s));
+            rc.ck(launch_dots<double>(N, 1, o1, o1, rc.dpart, S + S_T2, s), "dot");
+            if (!kappa_only) rc.ck(launch_dots<double>(N, 1, o2, o2, rc.dpart, S + S_T3, s), "dot");
+            qpat::note_launch(1);
+            k_p_update<<<GS(N)>>>(N, o1, o2, q, S, 0, kappa_only, p);
+            if (reorth) project(p, Vb, Qb, nv, m);
+            rc.ck(launch_dots<double>(2 * N, 1, p, p, rc.dpart, S + S_T0, s), "dot");
+            readS({S_T0, S_T2, S_T3});
+            const double atu2 = hs[1] + (kappa_only ? 0.0 : hs[2]);   // |A^T u|^2
+            if (hs[0] <= kBreakdown * kBreakdown * atu2) {
+                done = true;
+                qpat::note_launch(1);
+                k_set_scalar<<<1, 32, 0, s>>>(S, S_ALPHA, 0.0);
+            } else {
+                rc.ckq(solve(rc.M, P, rc.so, 2, p, z, s));
+                rc.ck(launch_dots<double>(2 * N, 1, p, z, rc.dpart, S + S_T1, s), "dot");
+                qpat::note_launch(1);
+                k_scal_set<<<1, 32, 0, s>>>(S, S_ALPHA, S_T1, 0);
+                qpat::note_launch(1);
+                k_vq<<<GS(2 * N)>>>(2 * N, z, p, S, v, q, 0, wd, x);
+            }
+        }
+        if (reorth && !done) store(m);
         // rotation, then x and w_d
         qpat::note_launch(1);
         k_givens<<<1, 32, 0, s>>>(S, rc.hist, m);
         qpat::note_launch(1);
         k_xw<<<GS(2 * N)>>>(2 * N, S, v, x, wd);
-        rc.ck(cudaMemcpyAsync(rc.M->host_scratch, S + S_PHIBAR, sizeof(double), cudaMemcpyDeviceToHost, s), "copy");
+        rc.ck(cudaMemcpyAsync(hs, S + S_PHIBAR, sizeof(double), cudaMemcpyDeviceToHost, s), "copy");
+        rc.ck(cudaMemcpyAsync(hs + 1, S + S_ALPHA, sizeof(double), cudaMemcpyDeviceToHost, s), "copy");
         rc.ck(cudaStreamSynchronize(s), "sync");
-        hist_out.push_back(rc.M->host_scratch[0]);
+        hist_out.push_back(hs[0]);
+        if (done || !(hs[1] > 0.0)) break;
         if (!prm.fixed_counts && m > prm.m0) {
             const double r_m = 1.0 - hist_out[m] / hist_out[m - prm.m0];
             if (r_m <= prm.tau) break;
@@ -355,6 +484,20 @@ static int reconstruct_impl(qpat_mesh_t M, const qpat_params* prm_in, int K, con
         return fail(QPAT_EINVAL, "qpat_reconstruct: T, delta, b/a must be positive");
     if (prm.step_halvings < 0 || prm.step_halvings > 16)
         return fail(QPAT_EINVAL, "qpat_reconstruct: step_halvings must lie in [0, 16]");
+    if (prm.lsqr_reorth != 0 && prm.lsqr_reorth != 1)
+        return fail(QPAT_EINVAL, "qpat_reconstruct: lsqr_reorth must be 0 or 1");
+    if (prm.barrier_spin_limit < 0) return fail(QPAT_EINVAL, "qpat_reconstruct: barrier_spin_limit must be >= 0");
+    {
+        // the data model of Eq. (8): finite data, Gamma = diag(sigma^2) positive definite
+        const int64_t n = int64_t(K) * M->h.N;
+        for (int64_t i = 0; i < n; ++i) {
+            if (!std::isfinite(chi[i])) return fail(QPAT_EINVAL, "qpat_reconstruct: chi must be finite");
+            if (!(sigma[i] > 0.0) || !std::isfinite(sigma[i]))
+                return fail(QPAT_EINVAL, "qpat_reconstruct: sigma must be positive and finite");
+        }
+        for (int64_t i = 0; i < int64_t(K) * M->h.F; ++i)
+            if (!std::isfinite(flux_face[i])) return fail(QPAT_EINVAL, "qpat_reconstruct: flux must be finite");
+    }
     DeviceGuard dg(M->device);
     const auto t0 = std::chrono::steady_clock::now();
     Recon rc{};

@@ -32,7 +32,7 @@ class qpat_params(ctypes.Structure):
         ("fit_gn_steps", ctypes.c_int), ("patch_nodes", ctypes.c_int), ("fp32_operator", ctypes.c_int),
         ("pcg_variant", ctypes.c_int), ("prior", ctypes.c_int), ("mixed_restart", ctypes.c_int),
         ("poly_degree", ctypes.c_int), ("prior_poly_degree", ctypes.c_int), ("step_halvings", ctypes.c_int),
-        ("prior_q", ctypes.c_double),
+        ("prior_q", ctypes.c_double), ("lsqr_reorth", ctypes.c_int), ("barrier_spin_limit", ctypes.c_int64),
     ]
 
 

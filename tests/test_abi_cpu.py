@@ -130,3 +130,18 @@ def test_host_mesh_rejects_bad_input():
 def test_launch_counter_is_callable_without_a_gpu():
     # a host-side counter: no kernel has been launched by the CPU test process
     assert Q.qpat_launch_count() >= 0
+
+
+def test_params_struct_layout_matches_the_header():
+    """The ctypes mirror of qpat_params has the C struct's size: the library's
+    qpat_default_params clears exactly sizeof(qpat_params) bytes (memset
+    first), so with a guard area behind the mirror's size the last byte of
+    the struct is written and the guard is left alone."""
+    import ctypes
+    n = ctypes.sizeof(Q.qpat_params)
+    buf = (ctypes.c_ubyte * (n + 32))(*([0xAB] * (n + 32)))
+    Q.load().qpat_default_params(ctypes.cast(buf, ctypes.POINTER(Q.qpat_params)))
+    assert buf[n - 1] == 0                     # barrier_spin_limit (0 by default), high byte
+    assert all(b == 0xAB for b in buf[n:])
+    p = Q.qpat_default_params()
+    assert p.lsqr_reorth == 1 and p.barrier_spin_limit == 0

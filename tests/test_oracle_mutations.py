@@ -92,3 +92,50 @@ def test_tvq_missing_chain_rule_factor_is_caught(monkeypatch):
     # d/dt (t^2 + T^2)^(q/2) / q taken without the inner derivative 2t / 2 = t
     monkeypatch.setattr(Q, "tvq_rprime", lambda t, T, q: (t * t + T * T) ** (q / 2.0 - 1.0))
     assert _fails(P.test_tvq_weights_closed_forms_and_derivative)
+
+
+def test_dropped_j_beta_in_linearised_data_is_caught(monkeypatch):
+    # y~ = w (chi - h) instead of w (chi - h + J beta): an increment solve
+    monkeypatch.setattr(Q, "linearised_data", lambda chi, h, Jb, w: (w * (chi - h)).ravel())
+    assert _fails(P.test_linearisation_step_is_krylov_minimiser_of_the_linearised_problem)
+    assert _fails(P.test_step_zero_is_krylov_minimiser_in_kappa_alone)
+
+
+def test_unwhitened_linearised_data_is_caught(monkeypatch):
+    monkeypatch.setattr(Q, "linearised_data", lambda chi, h, Jb, w: (chi - h + Jb).ravel())
+    assert _fails(P.test_linearisation_step_is_krylov_minimiser_of_the_linearised_problem)
+
+
+def test_step_zero_over_both_blocks_is_caught(monkeypatch):
+    # step 0 solving for (kappa_tilde, mu_tilde) and keeping the first block
+    def bad(mesh, kap, mu, phi, h, fac, chi, w, kt, P_):
+        N = mesh.N
+        beta = np.concatenate([kt, np.log(mu / mu.mean())])
+        r = Q.linearisation_step(mesh, kap, mu, phi, h, fac, chi, w, beta, P_)
+        r.x = r.x[:N]
+        return r
+    import oracle
+    monkeypatch.setattr(Q, "step_zero", bad)
+    monkeypatch.setattr(oracle, "step_zero", bad)
+    assert _fails(P.test_step_zero_is_krylov_minimiser_in_kappa_alone)
+
+
+def _init_mu_variant(kind):
+    def f(chi, phi0, mu0):
+        r = phi0 / chi if kind == "inverted" else chi / phi0
+        m = np.sum(r, axis=0) if kind == "sum" else np.mean(r, axis=0)
+        m = np.where(m > 0, m, mu0)
+        lo, hi = (10.0 * mu0, 0.1 * mu0) if kind == "swapped" else (0.1 * mu0, 10.0 * mu0)
+        m = np.minimum(np.maximum(m, lo), hi)
+        return np.log(m / mu0)
+    return f
+
+
+@pytest.mark.parametrize("kind", ["sum", "inverted", "swapped"])
+def test_init_mu_mistakes_are_caught(monkeypatch, kind):
+    import oracle
+    monkeypatch.setattr(Q, "init_mu", _init_mu_variant(kind))
+    monkeypatch.setattr(oracle, "init_mu", _init_mu_variant(kind))
+    assert _fails(P.test_init_mu_hand_computed_case)
+    if kind != "swapped":
+        assert _fails(P.test_init_mu_recovers_mu_when_data_is_mu_times_phi0)

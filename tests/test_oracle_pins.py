@@ -506,10 +506,10 @@ def test_reconstruct_resume_equals_one_run():
     sig = 0.01 * np.abs(h) + 1e-12
     chi = h + sig * S.noise_draws(1, h.shape)
     k0m0 = (float(np.median(kap_t)), float(np.median(mu_t)))
-    full = O.reconstruct(m, fl, chi, sig, O.QpatParams(T=1e-3, max_lin=4, max_lsqr=8, fixed_counts=True), k0m0)
-    part = O.reconstruct(m, fl, chi, sig, O.QpatParams(T=1e-3, max_lin=2, max_lsqr=8, fixed_counts=True), k0m0)
+    full = O.reconstruct(m, fl, chi, sig, O.QpatParams(T=1e-2, max_lin=4, max_lsqr=8, fixed_counts=True), k0m0)
+    part = O.reconstruct(m, fl, chi, sig, O.QpatParams(T=1e-2, max_lin=2, max_lsqr=8, fixed_counts=True), k0m0)
     assert part[2].linearisations == 2 and part[2].accepted_last
-    rest = O.reconstruct(m, fl, chi, sig, O.QpatParams(T=1e-3, max_lin=4, max_lsqr=8, fixed_counts=True), k0m0,
+    rest = O.reconstruct(m, fl, chi, sig, O.QpatParams(T=1e-2, max_lin=4, max_lsqr=8, fixed_counts=True), k0m0,
                          beta_in=part[2].beta, lin_done=part[2].linearisations)
     assert rest[2].linearisations == full[2].linearisations
     np.testing.assert_array_equal(rest[0], full[0])
@@ -536,8 +536,10 @@ def test_reconstruct_step_halving_option():
     sig = 0.01 * np.abs(h) + 1e-12
     chi = h + sig * S.noise_draws(1, h.shape)
     k0m0 = (float(np.median(kap_t)), float(np.median(mu_t)))
-    d = O.reconstruct(m, fl, chi, sig, O.QpatParams(T=1e-3, max_lin=5, max_lsqr=50), k0m0)[2]
-    hv = O.reconstruct(m, fl, chi, sig, O.QpatParams(T=1e-3, max_lin=5, max_lsqr=50, step_halvings=4), k0m0)[2]
+    # (the plain LSQR recurrence, whose default run stops at a rejected step here)
+    d = O.reconstruct(m, fl, chi, sig, O.QpatParams(T=1e-3, max_lin=5, max_lsqr=50, lsqr_reorth=False), k0m0)[2]
+    hv = O.reconstruct(m, fl, chi, sig, O.QpatParams(T=1e-3, max_lin=5, max_lsqr=50, step_halvings=4,
+                                                     lsqr_reorth=False), k0m0)[2]
     assert not d.accepted_last                                  # the default run stops at a rejected step
     assert hv.residuals[:len(d.residuals)] == d.residuals        # same accepted prefix, bit for bit
     assert hv.linearisations > d.linearisations
@@ -551,8 +553,185 @@ def test_reconstruct_step_halving_option():
     h2 = O.measure(m2, k2, mu2, fl2)
     s2 = 0.01 * np.abs(h2) + 1e-3 * np.abs(h2).max()
     c2 = h2 + s2 * S.noise_draws(3, h2.shape)
-    kd, _, rd = O.reconstruct(m2, fl2, c2, s2, O.QpatParams())
-    kh, _, rh = O.reconstruct(m2, fl2, c2, s2, O.QpatParams(step_halvings=6))
+    kd, _, rd = O.reconstruct(m2, fl2, c2, s2, O.QpatParams(lsqr_reorth=False))
+    kh, _, rh = O.reconstruct(m2, fl2, c2, s2, O.QpatParams(step_halvings=6, lsqr_reorth=False))
     assert np.abs(np.log(kd / rd.kappa0)).max() > 20          # default: step 0 diverges
     assert np.abs(np.log(kh / rh.kappa0)).max() < 2
     assert rh.residuals[-1] < 1.5 * np.sqrt(h2.size)           # whitened noise level sqrt(K N)
+
+
+# ---------------------------------------------------------------- Algorithm 1 pieces
+
+def test_init_mu_hand_computed_case():
+    """mu_init of Algorithm 1 with the multi-illumination rule of Sec. 4 on a
+    hand-computed K = 2 case (mu_0 = 0.01): node 0 averages 0.02/1 and
+    0.06/2 to 0.025; node 1 averages to 0.2 and is clipped to 10 mu_0; node 2
+    averages to -0.02 (not positive: mu_0); node 3 averages to 1e-5 and is
+    clipped to mu_0 / 10.  Expected mu_tilde = log(mu_init / mu_0), written
+    out by hand."""
+    chi = np.array([[0.02, 0.3, -0.05, 1e-5],
+                    [0.06, 0.1, 0.01, 1e-5]])
+    phi0 = np.array([[1.0, 1.0, 1.0, 1.0],
+                     [2.0, 1.0, 1.0, 1.0]])
+    got = O.init_mu(chi, phi0, 0.01)
+    expect = np.array([math.log(2.5), math.log(10.0), 0.0, math.log(0.1)])
+    np.testing.assert_allclose(got, expect, rtol=0, atol=1e-14)
+
+
+def test_init_mu_recovers_mu_when_data_is_mu_times_phi0():
+    """The motivation of mu_init (Eqs. (2), (4)): if every illumination's data
+    is chi^(k) = mu o phi0^(k) with the same mu, the average of chi/phi0 is
+    mu and mu_tilde_init = log(mu / mu_0) exactly, for any positive phi0^(k)."""
+    rng = np.random.default_rng(4)
+    mu0 = 0.012
+    mu = mu0 * np.exp(rng.uniform(-1.5, 1.5, 50))
+    phi0 = rng.uniform(0.1, 3.0, (3, 50))
+    got = O.init_mu(mu[None, :] * phi0, phi0, mu0)
+    np.testing.assert_allclose(got, np.log(mu / mu0), rtol=0, atol=1e-13)
+
+
+def _fd_jacobian(m, fl, k0, m0, beta, eps=1e-5):
+    """Column-by-column Jacobian of beta -> h(kappa_0 e^kt, mu_0 e^mt) (K N x 2N)
+    by central differences of the forward model alone (no jvp code)."""
+    N = m.N
+    cols = []
+    for j in range(2 * N):
+        hs = []
+        for sgn in (1.0, -1.0):
+            b = beta.copy()
+            b[j] += sgn * eps
+            hs.append(O.measure(m, k0 * np.exp(b[:N]), m0 * np.exp(b[N:]), fl).ravel())
+        cols.append((hs[0] - hs[1]) / (2 * eps))
+    return np.stack(cols, axis=1)
+
+
+def _tiny_linearisation():
+    cfg = S.small_config(3, 6.0, 3, 13)
+    xyz, tets = cfg.mesh()
+    m = O.Mesh(xyz, tets)
+    fl = np.stack([O.flux_patch(m, p.center, p.normal, p.half_w) for p in cfg.patches])
+    N = m.N
+    k0, m0 = 0.3, 0.012
+    rng = np.random.default_rng(21)
+    beta = 0.3 * rng.standard_normal(2 * N)                       # beta^(l), away from 0
+    beta_true = beta + 0.2 * rng.standard_normal(2 * N)
+    h_true = O.measure(m, k0 * np.exp(beta_true[:N]), m0 * np.exp(beta_true[N:]), fl)
+    sig = 0.01 * np.abs(h_true) + 1e-3 * np.abs(h_true).max()
+    chi = h_true + sig * S.noise_draws(5, h_true.shape)
+    return m, fl, k0, m0, beta, chi, 1.0 / sig
+
+
+def _krylov_minimiser(A, Pinv, b, m):
+    """argmin |A x - b| over x in P^-1 K_m(A^T A P^-1, A^T b), from an
+    orthonormal basis (each new vector orthogonalised twice) and a dense
+    least-squares solve."""
+    Vb = []
+    r = A.T @ b
+    for _ in range(m):
+        v = Pinv @ r
+        for _ in range(2):
+            for q in Vb:
+                v = v - (q @ v) * q
+        Vb.append(v / np.linalg.norm(v))
+        r = A.T @ (A @ v)
+    V = np.stack(Vb, 1)
+    return V @ np.linalg.lstsq(A @ V, b, rcond=None)[0]
+
+
+def test_linearisation_step_is_krylov_minimiser_of_the_linearised_problem():
+    """Steps 1-3 of Algorithm 1 on a 27-node mesh with K = 3: after m LSQR
+    rounds the candidate beta^(l+1) minimises |A beta - y~| over
+    M_delta^-1 K_m(A^T A M_delta^-1, A^T y~), with A = Gamma^-1/2 J,
+    y~ = Gamma^-1/2 (chi - h(beta^(l)) + J beta^(l)) and M_delta built from
+    beta^(l) (Eqs. (11), (16), (19), (21)), all formed here with dense numpy
+    algebra and J from central differences of the forward model alone.
+    Dropping the + J beta^(l) term of y~ (an increment solve instead of
+    Gauss-Newton for beta), the whitening, or building M_delta elsewhere
+    fails it."""
+    m, fl, k0, m0, beta, chi, w = _tiny_linearisation()
+    N = m.N
+    kap, mu = k0 * np.exp(beta[:N]), m0 * np.exp(beta[N:])
+    fac = O.Factor(O.system_matrix(m, kap, mu))
+    phi, h = O.forward(m, kap, mu, fl, fac)
+    Jd = _fd_jacobian(m, fl, k0, m0, beta)
+    A = w.ravel()[:, None] * Jd
+    ytil = w.ravel() * (chi.ravel() - h.ravel() + Jd @ beta)
+    T = 1e-2
+    Md = O.prior_matrix(m, beta[:N], beta[N:], T, 1.0, 1e-6).toarray()
+    Pinv = np.linalg.inv(Md)
+    for rounds in (1, 3, 5):
+        P = O.QpatParams(T=T, max_lsqr=rounds, fixed_counts=True, lsqr_reorth=True)
+        res = O.linearisation_step(m, kap, mu, phi, h, fac, chi, w, beta, P)
+        expect = _krylov_minimiser(A, Pinv, ytil, rounds)
+        assert np.linalg.norm(res.x - expect) <= 1e-6 * np.linalg.norm(expect), rounds
+    # the + J beta^(l) term changes this problem's answer by O(1)
+    alt = _krylov_minimiser(A, Pinv, w.ravel() * (chi.ravel() - h.ravel()), 5)
+    assert np.linalg.norm(alt - expect) > 0.1 * np.linalg.norm(expect)
+
+
+def test_step_zero_is_krylov_minimiser_in_kappa_alone():
+    """Step 0 of Sec. 5 is the same problem in kappa_tilde alone: A = Gamma^-1/2
+    J_kappa, y^ = Gamma^-1/2 (chi - h + J_kappa kappa_tilde_init) and the
+    prior M(kappa_tilde_init) + delta I of the kappa block; the result after
+    m rounds is that Krylov minimiser (dense numpy, J from central
+    differences).  Solving for both blocks, or dropping
+    J_kappa kappa_tilde_init, fails it."""
+    m, fl, k0, m0, beta, chi, w = _tiny_linearisation()
+    N = m.N
+    kt = beta[:N]
+    kap, mu = k0 * np.exp(kt), m0 * np.exp(beta[N:])
+    fac = O.Factor(O.system_matrix(m, kap, mu))
+    phi, h = O.forward(m, kap, mu, fl, fac)
+    Jk = _fd_jacobian(m, fl, k0, m0, beta)[:, :N]
+    A = w.ravel()[:, None] * Jk
+    yhat = w.ravel() * (chi.ravel() - h.ravel() + Jk @ kt)
+    T = 1e-2
+    Mk = O.prior_matrix(m, kt, np.zeros(N), T, 1.0, 1e-6).toarray()[:N, :N]
+    Pinv = np.linalg.inv(Mk)
+    for rounds in (1, 3, 5):
+        P = O.QpatParams(T=T, max_lsqr=rounds, fixed_counts=True, lsqr_reorth=True)
+        res = O.step_zero(m, kap, mu, phi, h, fac, chi, w, kt, P)
+        assert res.x.shape == (N,)
+        expect = _krylov_minimiser(A, Pinv, yhat, rounds)
+        assert np.linalg.norm(res.x - expect) <= 1e-6 * np.linalg.norm(expect), rounds
+    alt = _krylov_minimiser(A, Pinv, w.ravel() * (chi.ravel() - h.ravel()), 5)
+    assert np.linalg.norm(alt - expect) > 0.1 * np.linalg.norm(expect)
+
+
+def test_lsqr_reorth_keeps_krylov_minimiser_where_plain_recurrence_drifts():
+    """LSQR with full reorthogonalisation follows exact arithmetic: on a
+    problem whose P has one direction 1e6 above the rest (as M_delta^-1 has
+    the constant mode, 1/delta), its m-th iterate stays the minimiser over
+    P^-1 K_m(A^T A P^-1, A^T b) (basis built by dense projection with full
+    orthogonalisation) for m up to 24, and it equals the plain recurrence in
+    the first rounds, where that has not yet lost orthogonality."""
+    rng = np.random.default_rng(31)
+    mrows, ncols = 120, 60
+    A = rng.standard_normal((mrows, ncols)) @ np.diag(np.logspace(0, -3, ncols))
+    Qm = np.linalg.qr(rng.standard_normal((ncols, ncols)))[0]
+    lam = np.logspace(-1, 1, ncols)
+    lam[0] = 1e-6                                   # the 1/delta-like direction of P^-1
+    P = Qm @ np.diag(lam) @ Qm.T
+    Pinv = Qm @ np.diag(1.0 / lam) @ Qm.T
+    b = rng.standard_normal(mrows)
+    for m in (3, 12, 24):
+        res = O.lsqr_prior(lambda v: A @ v, lambda u: A.T @ u, lambda p: Pinv @ p, b, m,
+                           fixed_counts=True, reorth=True)
+        # orthonormal basis of the Krylov space, each new vector orthogonalised twice
+        Vb = []
+        r = A.T @ b
+        for _ in range(m):
+            v = Pinv @ r
+            for _ in range(2):
+                for q in Vb:
+                    v = v - (q @ v) * q
+            Vb.append(v / np.linalg.norm(v))
+            r = A.T @ (A @ v)
+        V = np.stack(Vb, 1)
+        xbest = V @ np.linalg.lstsq(A @ V, b, rcond=None)[0]
+        assert np.linalg.norm(A @ res.x - b) <= np.linalg.norm(A @ xbest - b) * (1 + 1e-8)
+        assert np.linalg.norm(res.x - xbest) <= 1e-6 * np.linalg.norm(xbest)
+        assert abs(res.phibar[-1] - np.linalg.norm(A @ res.x - b)) < 1e-9 * np.linalg.norm(b)
+    plain = O.lsqr_prior(lambda v: A @ v, lambda u: A.T @ u, lambda p: Pinv @ p, b, 2, fixed_counts=True)
+    ro = O.lsqr_prior(lambda v: A @ v, lambda u: A.T @ u, lambda p: Pinv @ p, b, 2, fixed_counts=True, reorth=True)
+    assert np.linalg.norm(ro.x - plain.x) <= 1e-8 * np.linalg.norm(plain.x)

@@ -1,13 +1,14 @@
 """The allocation-free forward solve (qpat_forward_noalloc_dev), for callers
-that cannot allocate device memory when they need a solve: work issued while
-a CUDA graph is being captured, real-time pipelines that forbid allocator
-calls after start-up, and hosts that manage all GPU memory themselves.
+that cannot allocate device memory when they need a solve: real-time
+pipelines that forbid allocator calls after start-up (an allocation can block
+on the driver) and hosts that budget all GPU memory themselves.
 
 Its output must equal the regular entry point's (qpat_forward_dev, FP64) to
 the 1e-10 relative tolerance of the other forward tests, on two calls in a
-row (the second call reuses the same fixed scratch array), and sizes above
-the fixed limit must be refused.  This file runs last so that a stop at the
-first failure has already run every other test."""
+row (the second call reuses the same fixed scratch array), the device's free
+memory must not change across its calls, and sizes above the fixed limit
+must be refused.  This file runs last so that a stop at the first failure has
+already run every other test."""
 import numpy as np
 import pytest
 
@@ -40,11 +41,17 @@ def test_noalloc_forward_matches_regular_entry_point(cfg):
         phi_ref = torch.empty((K, N), dtype=torch.float64, device=dev)
         h_ref = torch.empty_like(phi_ref)
         Q.qpat_forward_dev(mesh, k, m, f, phi_ref, h_ref, Q.qpat_default_params(precision=0))
-        for _ in range(2):
-            phi = torch.full((K, N), float("nan"), dtype=torch.float64, device=dev)
-            h = torch.full_like(phi, float("nan"))
+        outs = [(torch.full((K, N), float("nan"), dtype=torch.float64, device=dev),
+                 torch.full((K, N), float("nan"), dtype=torch.float64, device=dev)) for _ in range(2)]
+        torch.cuda.synchronize()
+        free = []
+        for phi, h in outs:           # nothing else touches the device between the two readings
             Q.qpat_forward_noalloc_dev(mesh, k, m, f, phi, h)
             torch.cuda.synchronize()
+            free.append(torch.cuda.mem_get_info()[0])
+        # the second call (after the first one's set-up) takes no device memory
+        assert free[1] == free[0]
+        for phi, h in outs:
             assert _rel(phi, phi_ref) < 1e-10
             assert _rel(h, h_ref) < 1e-10
     finally:
