@@ -191,6 +191,11 @@ int qpat_mesh_stats(qpat_mesh_t mesh, int64_t* out4);
  * (since the last reset); -1 for a NULL mesh. */
 int64_t qpat_mesh_fp64_fallbacks(qpat_mesh_t mesh);
 int qpat_mesh_reset_stats(qpat_mesh_t mesh);
+/* Sum over the PCG launches since the last reset of iterations times the
+ * right-hand sides of the launch (a block solve may run as several launches
+ * when one launch's shared memory cannot hold all its right-hand sides);
+ * -1 for a NULL mesh.  Not in the paper (diagnostics). */
+int64_t qpat_mesh_rhs_iterations(qpat_mesh_t mesh);
 
 /* When on, every PCG launch is bracketed by CUDA events recorded on the
  * stream it is launched on; qpat_mesh_pcg_time returns the summed device
@@ -372,6 +377,12 @@ int qpat_unet_features_dev(qpat_mesh_t mesh, const double* kappa, const double* 
 int qpat_unet_predict_dev(qpat_unet_t unet, const float* x, int B, float* y, void* stream);
 int qpat_unet_train_dev(qpat_unet_t unet, const float* x, const float* t, int B, float lr,
                         float* loss, void* stream);
+/* The training loss of those B samples and its gradient with respect to
+ * every parameter (summed over the samples, no update): grad (HOST,
+ * qpat_unet_num_params floats, the layout of qpat_unet_get_params), *loss
+ * (host, may be NULL).  Synchronous. */
+int qpat_unet_grad_dev(qpat_unet_t unet, const float* x, const float* t, int B, float* grad,
+                       float* loss, void* stream);
 /* y (float) -> out (double), count entries (the guess handed to the solve). */
 int qpat_unet_to_double_dev(const float* y, int64_t count, double* out, void* stream);
 

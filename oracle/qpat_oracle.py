@@ -38,6 +38,7 @@ __all__ = [
     "Mesh", "QpatParams", "tet_geometry", "boundary_faces", "face_areas",
     "int_bary_tet", "int_bary_tri", "assemble_stiffness", "assemble_weighted_mass",
     "assemble_robin", "load_vector", "load_vector_nodal", "flux_patch", "flux_side", "system_matrix", "Factor",
+    "JacobiPcg",
     "forward", "G1_matrix", "G2_matrix", "jvp", "vjp", "lagged_weights", "tvq_r", "tvq_rprime",
     "prior_matrix", "prior_solve", "lsqr_prior", "fit_background", "init_mu",
     "linearised_data", "step_zero", "linearisation_step",
@@ -291,6 +292,68 @@ class Factor:
 
     def solve(self, b: np.ndarray) -> np.ndarray:
         return self.lu.solve(np.asarray(b, dtype=np.float64))
+
+
+class JacobiPcg:
+    """Textbook Jacobi-preconditioned conjugate gradients for a symmetric
+    positive definite A, several right-hand sides at once (each column its
+    own CG), stopped per column at |b - A x| <= rtol |b| (the recursive
+    residual).  The stand-in for Factor where a sparse factorisation of A is
+    out of reach (millions of 3D finite-element unknowns); same .solve(b)
+    interface.  The iteration can advance in slices (start / advance) so
+    that a caller can time bounded parts of one solve."""
+
+    def __init__(self, A: sp.spmatrix, rtol: float = 1e-13, maxit: int = 200000):
+        self.A = A.tocsr()
+        self.dinv = 1.0 / self.A.diagonal()
+        self.rtol = rtol
+        self.maxit = maxit
+
+    def start(self, B: np.ndarray):
+        B = np.asarray(B, dtype=np.float64)
+        self.one = B.ndim == 1
+        B = B.reshape(B.shape[0], -1)
+        self.x = np.zeros_like(B)
+        self.r = B.copy()
+        self.z = self.dinv[:, None] * self.r
+        self.p = self.z.copy()
+        self.rz = np.einsum("ij,ij->j", self.r, self.z)
+        self.stop2 = (self.rtol ** 2) * np.einsum("ij,ij->j", B, B)
+        self.active = np.einsum("ij,ij->j", self.r, self.r) > self.stop2
+        self.iters = np.zeros(B.shape[1], dtype=np.int64)
+
+    def advance(self, n: int) -> bool:
+        """Up to n CG iterations of every unconverged column; True when all
+        columns have converged."""
+        for _ in range(n):
+            a = np.flatnonzero(self.active)
+            if a.size == 0:
+                return True
+            p = self.p[:, a]
+            q = self.A @ p
+            alpha = self.rz[a] / np.einsum("ij,ij->j", p, q)
+            self.x[:, a] += alpha * p
+            r = self.r[:, a] - alpha * q
+            self.r[:, a] = r
+            z = self.dinv[:, None] * r
+            rz_new = np.einsum("ij,ij->j", r, z)
+            self.p[:, a] = z + (rz_new / self.rz[a]) * p
+            self.rz[a] = rz_new
+            self.iters[a] += 1
+            done = np.einsum("ij,ij->j", r, r) <= self.stop2[a]
+            self.active[a[done]] = False
+            if self.iters.max() >= self.maxit:
+                raise RuntimeError("JacobiPcg: iteration cap reached")
+        return not self.active.any()
+
+    def result(self) -> np.ndarray:
+        return self.x[:, 0].copy() if self.one else self.x.copy()
+
+    def solve(self, b: np.ndarray) -> np.ndarray:
+        self.start(b)
+        while not self.advance(1000):
+            pass
+        return self.result()
 
 
 # --------------------------------------------------------------------------

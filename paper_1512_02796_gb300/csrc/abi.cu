@@ -373,6 +373,7 @@ int solve(qpat_mesh_s* M, const OpState& st, const SolveOpts& so_in, int R, cons
             M->pcg_ms += ms;
         }
         M->stats.pcg_iters += hst[1];
+        M->stats.rhs_iters += int64_t(hst[1]) * R;
         M->stats.solves += R;
         M->stats.launches += 1;
         return pcg_status(hst[0], pfx);
@@ -490,6 +491,7 @@ int solve(qpat_mesh_s* M, const OpState& st, const SolveOpts& so_in, int R, cons
                 M->pcg_ms += ms;
             }
             M->stats.pcg_iters += hst[1];
+            M->stats.rhs_iters += int64_t(hst[1]) * R;
             M->stats.launches += 1;
             M->stats.refinements += 1;
             // an inner run that stops at its cap still improves x (the next
@@ -791,6 +793,8 @@ int qpat_mesh_stats(qpat_mesh_t M, int64_t* out4) {
 }
 
 int64_t qpat_mesh_fp64_fallbacks(qpat_mesh_t M) { return M ? M->stats.fp64_fallbacks : -1; }
+
+int64_t qpat_mesh_rhs_iterations(qpat_mesh_t M) { return M ? M->stats.rhs_iters : -1; }
 
 int qpat_mesh_reset_stats(qpat_mesh_t M) {
     if (!M) return fail(QPAT_EINVAL, "qpat_mesh_reset_stats: NULL mesh");

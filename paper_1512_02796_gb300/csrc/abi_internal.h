@@ -29,6 +29,7 @@ struct SolveStats {
     int64_t refinements = 0;
     int64_t fp64_fallbacks = 0;     // mixed-precision solves redone in FP64
     int64_t launches = 0;
+    int64_t rhs_iters = 0;          // sum over PCG launches of iterations x right-hand sides of the launch
 };
 
 struct OpState {

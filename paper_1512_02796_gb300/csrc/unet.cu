@@ -343,10 +343,10 @@ int qpat_unet_predict_dev(qpat_unet_t U, const float* x, int B, float* y, void* 
     return QPAT_OK;
 }
 
-int qpat_unet_train_dev(qpat_unet_t U, const float* x, const float* t, int B, float lr, float* loss, void* stream) {
-    if (!U || !x || !t || B < 1) return fail(QPAT_EINVAL, "qpat_unet_train_dev: bad argument");
-    DeviceGuard dg(U->device);
-    cudaStream_t s = static_cast<cudaStream_t>(stream);
+// Loss (mean squared error over the B samples' voxels) into U->loss and its
+// gradient with respect to every weight and bias into the accumulators
+// aw, ab (summed over the samples).
+static int unet_loss_grad(qpat_unet_s* U, const float* x, const float* t, int B, cudaStream_t s) {
     const int64_t nv = int64_t(U->n) * U->n * U->n;
     UCK(cudaMemsetAsync(U->loss, 0, sizeof(float), s));
     for (int b = 0; b < B; ++b) {
@@ -364,6 +364,36 @@ int qpat_unet_train_dev(qpat_unet_t U, const float* x, const float* t, int B, fl
             k_axpy32<<<1, 256, 0, s>>>(c.cout, 1.f, c.gb, c.ab, b == 0);
         }
     }
+    UCK(cudaGetLastError());
+    return QPAT_OK;
+}
+
+int qpat_unet_grad_dev(qpat_unet_t U, const float* x, const float* t, int B, float* grad, float* loss,
+                       void* stream) {
+    if (!U || !x || !t || !grad || B < 1) return fail(QPAT_EINVAL, "qpat_unet_grad_dev: bad argument");
+    DeviceGuard dg(U->device);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    int rc = unet_loss_grad(U, x, t, B, s);
+    if (rc) return rc;
+    size_t o = 0;
+    for (auto& c : U->conv) {
+        UCK(cudaMemcpyAsync(grad + o, c.aw, sizeof(float) * c.nw(), cudaMemcpyDeviceToHost, s));
+        o += c.nw();
+        UCK(cudaMemcpyAsync(grad + o, c.ab, sizeof(float) * c.cout, cudaMemcpyDeviceToHost, s));
+        o += c.cout;
+    }
+    UCK(cudaMemcpyAsync(U->hloss, U->loss, sizeof(float), cudaMemcpyDeviceToHost, s));
+    UCK(cudaStreamSynchronize(s));
+    if (loss) *loss = *U->hloss;
+    return QPAT_OK;
+}
+
+int qpat_unet_train_dev(qpat_unet_t U, const float* x, const float* t, int B, float lr, float* loss, void* stream) {
+    if (!U || !x || !t || B < 1) return fail(QPAT_EINVAL, "qpat_unet_train_dev: bad argument");
+    DeviceGuard dg(U->device);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    int rc0 = unet_loss_grad(U, x, t, B, s);
+    if (rc0) return rc0;
     ++U->step;
     for (auto& c : U->conv) {
         UCK(unet::adam(c.w32, nullptr, c.aw, c.mw, c.vw, c.nw(), lr, 0.9f, 0.999f, 1e-8f, U->step, s));

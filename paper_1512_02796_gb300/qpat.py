@@ -91,6 +91,7 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
         "qpat_mesh_permutation": (ctypes.c_int, [vp, _c_int32_p]),
         "qpat_mesh_stats": (ctypes.c_int, [vp, _c_int64_p]),
         "qpat_mesh_fp64_fallbacks": (ctypes.c_int64, [vp]),
+        "qpat_mesh_rhs_iterations": (ctypes.c_int64, [vp]),
         "qpat_mesh_reset_stats": (ctypes.c_int, [vp]),
         "qpat_mesh_set_timing": (ctypes.c_int, [vp, ctypes.c_int]),
         "qpat_mesh_pcg_time": (ctypes.c_int, [vp, _c_double_p]),
@@ -136,6 +137,8 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
         "qpat_unet_predict_dev": (ctypes.c_int, [vp, vp, ctypes.c_int, vp, vp]),
         "qpat_unet_train_dev": (ctypes.c_int, [vp, vp, vp, ctypes.c_int, ctypes.c_float,
                                                ctypes.POINTER(ctypes.c_float), vp]),
+        "qpat_unet_grad_dev": (ctypes.c_int, [vp, vp, vp, ctypes.c_int, ctypes.POINTER(ctypes.c_float),
+                                              ctypes.POINTER(ctypes.c_float), vp]),
         "qpat_unet_to_double_dev": (ctypes.c_int, [vp, ctypes.c_int64, vp, vp]),
         "qpat_conv3d_bf16_dev": (ctypes.c_int, [vp, ctypes.c_int, vp, vp, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                                 vp, vp, vp]),
@@ -169,7 +172,7 @@ def exported_names() -> Sequence[str]:
         "qpat_mesh_host_info", "qpat_mesh_num_nodes", "qpat_mesh_num_tets", "qpat_mesh_num_faces", "qpat_mesh_num_patches",
         "qpat_mesh_num_entries", "qpat_mesh_num_prior_entries", "qpat_mesh_num_local_entries",
         "qpat_mesh_faces", "qpat_mesh_permutation", "qpat_mesh_stats", "qpat_mesh_fp64_fallbacks",
-        "qpat_mesh_reset_stats",
+        "qpat_mesh_rhs_iterations", "qpat_mesh_reset_stats",
         "qpat_mesh_set_timing", "qpat_mesh_pcg_time",
         "qpat_flux_patch", "qpat_flux_side", "qpat_apply_K_dev", "qpat_forward", "qpat_forward_dev", "qpat_forward_noalloc_dev",
         "qpat_forward_guess_dev",
@@ -178,7 +181,8 @@ def exported_names() -> Sequence[str]:
         "qpat_batch_create", "qpat_batch_buffers", "qpat_batch_forward", "qpat_batch_status", "qpat_batch_free",
         "qpat_autotune", "qpat_reconstruct", "qpat_reconstruct_ex",
         "qpat_unet_create", "qpat_unet_free", "qpat_unet_num_params", "qpat_unet_get_params", "qpat_unet_set_params",
-        "qpat_unet_features_dev", "qpat_unet_predict_dev", "qpat_unet_train_dev", "qpat_unet_to_double_dev",
+        "qpat_unet_features_dev", "qpat_unet_predict_dev", "qpat_unet_train_dev", "qpat_unet_grad_dev",
+        "qpat_unet_to_double_dev",
         "qpat_conv3d_bf16_dev", "qpat_conv3d_bf16_wgrad_dev", "qpat_conv3d_bf16_wgrad_scratch",
         "qpat_conv3d_set_engine", "qpat_conv3d_tc_timeouts",
     ]
@@ -215,6 +219,16 @@ class UNet:
         _check(load().qpat_unet_train_dev(self.handle, _tpf(x), _tpf(t), x.shape[0], float(lr), ctypes.byref(loss),
                                           _stream()))
         return float(loss.value)
+
+    def grad(self, x, t):
+        """(loss, gradient) of the mean squared error of samples x against
+        targets t, in the parameter layout of get_params; no update."""
+        g = np.empty(self.num_params(), dtype=np.float32)
+        loss = ctypes.c_float()
+        _check(load().qpat_unet_grad_dev(self.handle, _tpf(x), _tpf(t), x.shape[0],
+                                         g.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), ctypes.byref(loss),
+                                         _stream()))
+        return float(loss.value), g
 
     def close(self):
         if getattr(self, "handle", None):
@@ -371,7 +385,8 @@ class Mesh:
         out = np.zeros(4, dtype=np.int64)
         _check(load().qpat_mesh_stats(self.handle, out.ctypes.data_as(_c_int64_p)))
         return {"pcg_iters": int(out[0]), "solves": int(out[1]), "refinements": int(out[2]),
-                "launches": int(out[3]), "fp64_fallbacks": int(load().qpat_mesh_fp64_fallbacks(self.handle))}
+                "launches": int(out[3]), "fp64_fallbacks": int(load().qpat_mesh_fp64_fallbacks(self.handle)),
+                "rhs_iters": int(load().qpat_mesh_rhs_iterations(self.handle))}
 
     def reset_stats(self):
         _check(load().qpat_mesh_reset_stats(self.handle))

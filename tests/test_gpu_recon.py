@@ -4,11 +4,14 @@ fixed counts, and the paper's stopping rules).
 
 The result of 5 x 50 nested Krylov rounds has no closed form, so the bar is
 the oracle's own sensitivity: the oracle is re-run with every linear solve
-perturbed by a relative 1e-13 (the solve accuracy of the GPU path), and the
+perturbed by a relative 1e-12 (the accuracy of the GPU path's K solves: PCG
+to a residual of 1e-13 with cond(K) ~ 30 on this cube), and the
 GPU result must lie within max(1e-10, 10 x that spread) of the oracle, per
 field (kappa, mu).  With the default, fully reorthogonalised LSQR that
-spread is ~1e-6 for the whole run and ~1e-12 per linearisation; the plain
+spread is ~1e-6 for the whole run and ~1e-11 per linearisation; the plain
 recurrence (lsqr_reorth = 0) loses orthogonality and spreads by ~0.4."""
+
+PERTURB = 1e-12
 import numpy as np
 import pytest
 
@@ -70,8 +73,10 @@ def test_reconstruct_fixed_counts_matches_oracle(c0, precision, nlin, nlsqr):
     par = O.QpatParams(T=1e-3, max_lin=nlin, max_lsqr=nlsqr, fixed_counts=True)
     k0m0 = (0.32, 0.011)
     kap_o, mu_o, rep_o = _oracle(c0, par, k0m0)
-    kap_p, mu_p, _ = _oracle(c0, par, k0m0, perturb=1e-13, seed=1)
-    floor = max(rel(kap_p, kap_o), rel(mu_p, mu_o))
+    floor = 0.0
+    for seed in (1, 2):
+        kap_p, mu_p, _ = _oracle(c0, par, k0m0, perturb=PERTURB, seed=seed)
+        floor = max(floor, rel(kap_p, kap_o), rel(mu_p, mu_o))
     prm = Q.qpat_default_params(T=1e-3, max_lin=nlin, max_lsqr=nlsqr, fixed_counts=1, precision=precision)
     kap_g, mu_g, rep = Q.qpat_reconstruct(c0["lib"], c0["flux"], c0["chi"], c0["sig"], prm, k0m0)
     tol = max(1e-10, 10 * floor)
@@ -117,14 +122,16 @@ def test_background_fit_matches_oracle(c0):
 def test_reconstruct_with_tvq_prior_matches_oracle(c0, q, nlin, nlsqr):
     """Algorithm 1 with the smoothed TV^q prior (the alternative r(t) of
     Sec. 3) instead of Perona-Malik, FP64, within max(1e-10, 10 x the
-    oracle's own spread under 1e-13 solve perturbations).  Short sweeps pin
+    oracle's own spread under 1e-12 solve perturbations).  Short sweeps pin
     the path tightly; at 3 x 3 the oracle's own spread is already ~3e-2 for
     kappa (TV^q weights up to T^(q-2) make M_delta far worse conditioned)."""
     par = O.QpatParams(T=1e-2, max_lin=nlin, max_lsqr=nlsqr, fixed_counts=True, prior=1, prior_q=q)
     k0m0 = (0.32, 0.011)
     kap_o, mu_o, _ = _oracle(c0, par, k0m0)
-    kap_p, mu_p, _ = _oracle(c0, par, k0m0, perturb=1e-13, seed=2)
-    floor = max(rel(kap_p, kap_o), rel(mu_p, mu_o))
+    floor = 0.0
+    for seed in (2, 3):
+        kap_p, mu_p, _ = _oracle(c0, par, k0m0, perturb=PERTURB, seed=seed)
+        floor = max(floor, rel(kap_p, kap_o), rel(mu_p, mu_o))
     prm = Q.qpat_default_params(T=1e-2, max_lin=nlin, max_lsqr=nlsqr, fixed_counts=1, precision=0, prior=1,
                                 prior_q=q)
     kap_g, mu_g, _ = Q.qpat_reconstruct(c0["lib"], c0["flux"], c0["chi"], c0["sig"], prm, k0m0)
@@ -136,7 +143,7 @@ def test_reconstruct_with_tvq_prior_matches_oracle(c0, q, nlin, nlsqr):
     kap_pm, _, _ = Q.qpat_reconstruct(c0["lib"], c0["flux"], c0["chi"], c0["sig"],
                                       Q.qpat_default_params(T=1e-2, max_lin=nlin, max_lsqr=nlsqr,
                                                             fixed_counts=1, precision=0), k0m0)
-    assert rel(kap_pm, kap_g) > 1e-6
+    assert rel(kap_pm, kap_g) > 10 * tol
 
 
 @pytest.mark.parametrize("precision", [0, 1])
@@ -188,7 +195,7 @@ def test_reconstruct_step_halving_matches_oracle():
     against the oracle: the same linearisations and accept / reject decisions
     (a halved step is accepted in linearisation 2, the next step is
     rejected), with residual history and fields within the oracle's own
-    spread under 1e-13 solve perturbations (x 100; Algorithm 1 amplifies
+    spread under 1e-12 solve perturbations (x 100; Algorithm 1 amplifies
     solve-level differences, ~1e-6 on this cube)."""
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
@@ -204,7 +211,7 @@ def test_reconstruct_step_halving_matches_oracle():
     par = O.QpatParams(T=1e-3, max_lin=4, max_lsqr=3, fixed_counts=True, step_halvings=4, lsqr_reorth=False)
     c = dict(om=om, flux=fl, chi=chi, sig=sig)
     ko, mo, ro = _oracle(c, par, k0m0)
-    kp, mp, rp = _oracle(c, par, k0m0, perturb=1e-13, seed=1)
+    kp, mp, rp = _oracle(c, par, k0m0, perturb=PERTURB, seed=1)
     floor = max(rel(kp, ko), rel(mp, mo), 1e-8)
     lib = Q.qpat_mesh(xyz, tets, patch_nodes=64)
     try:
@@ -223,11 +230,14 @@ def test_reconstruct_step_halving_matches_oracle():
 
 
 def _floor(c, par, k0m0, seed=1):
-    """The oracle's own spread: its result again with every linear solve
-    perturbed by a relative 1e-13 (the GPU solves' accuracy)."""
+    """The oracle's own spread: the largest change of its result over two
+    re-runs with every linear solve perturbed by a relative PERTURB."""
     ko, mo, ro = _oracle(c, par, k0m0)
-    kp, mp, _ = _oracle(c, par, k0m0, perturb=1e-13, seed=seed)
-    return ko, mo, ro, max(rel(kp, ko), rel(mp, mo))
+    f = 0.0
+    for sd in (seed, seed + 100):
+        kp, mp, _ = _oracle(c, par, k0m0, perturb=PERTURB, seed=sd)
+        f = max(f, rel(kp, ko), rel(mp, mo))
+    return ko, mo, ro, f
 
 
 @pytest.mark.parametrize("precision", [0, 1])
@@ -278,7 +288,7 @@ def test_reconstruct_steps_replayed_from_oracle_iterates(c0):
     """Each linearisation on its own: from the oracle's beta^(l) of Config
     0's 5 x 50 run (resume at step 1, qpat_reconstruct_ex), the GPU's next
     beta^(l+1) equals the oracle's, step by step, within max(1e-10, 10 x the
-    oracle's own one-step spread under 1e-13 solve perturbations), with the
+    oracle's own one-step spread under PERTURB solve perturbations), with the
     same accept / reject decision.  With reorthogonalised LSQR that spread is
     ~1e-12 per step (~1e-9 for step 0); the plain recurrence's is 1e-2 - 6e-2
     already within one 50-round sweep."""
@@ -303,7 +313,7 @@ def test_reconstruct_steps_replayed_from_oracle_iterates(c0):
 
     # step 0 (with the initialisation) from scratch
     r0 = oracle_step(0, None)
-    spread = rel(oracle_step(0, None, 1e-13).beta, r0.beta)
+    spread = rel(oracle_step(0, None, PERTURB).beta, r0.beta)
     prm = Q.qpat_default_params(T=1e-3, max_lin=1, max_lsqr=50, fixed_counts=1, lsqr_reorth=1)
     _, _, bg, _ = Q.qpat_reconstruct_ex(c0["lib"], c0["flux"], c0["chi"], c0["sig"], prm, k0m0)
     print(f"step 0: spread {spread:.1e} diff {rel(bg, r0.beta):.1e}")
@@ -311,7 +321,7 @@ def test_reconstruct_steps_replayed_from_oracle_iterates(c0):
     beta, lin, checked = r0.beta, 1, 0
     while lin < 5:
         ro = oracle_step(lin, beta)
-        spread = rel(oracle_step(lin, beta, 1e-13).beta, ro.beta)
+        spread = rel(oracle_step(lin, beta, PERTURB).beta, ro.beta)
         prm = Q.qpat_default_params(T=1e-3, max_lin=lin + 1, max_lsqr=50, fixed_counts=1, lsqr_reorth=1)
         _, _, bg, rg = Q.qpat_reconstruct_ex(c0["lib"], c0["flux"], c0["chi"], c0["sig"], prm, k0m0,
                                              beta_in=beta, lin_done=lin)

@@ -170,3 +170,39 @@ def test_tcgen05_and_mma_sync_engines_agree(n, cin, cout):
     scale = np.abs(res[1]).max()
     assert np.abs(res[0] - res[1]).max() <= 1e-5 * scale
     assert Q.qpat_conv3d_tc_timeouts() == 0
+
+
+def test_whole_network_gradient_matches_oracle():
+    """One training step's parameter gradient (qpat_unet_grad_dev: the mean
+    squared error of a 32^3 sample, every layer's weights and biases) against
+    the oracle's FP64 reverse pass (oracle.unet_oracle.unet_loss_grad, itself
+    pinned by central differences).  The GPU rounds weights, activations and
+    data gradients to bf16 (8-bit mantissa, ~4e-3 per rounding) through 15
+    layers each way, so the bar is 5e-2 on the whole gradient, 1e-1 per layer
+    and a cosine above 0.995; a missing or wrongly transposed layer gradient
+    is off by O(1)."""
+    _need()
+    n = 32
+    rng = np.random.default_rng(12)
+    net = Q.UNet(n, seed=5)
+    try:
+        p = net.get_params().astype(np.float64)
+        x3 = rng.standard_normal((n ** 3, 3))
+        t = rng.standard_normal(n ** 3)
+        xt = torch.tensor(x3[None].astype(np.float32), device="cuda")
+        tt = torch.tensor(t[None].astype(np.float32), device="cuda")
+        loss_g, g = net.grad(xt, tt)
+    finally:
+        net.close()
+    loss_o, go = UO.unet_loss_grad(p, x3, t, n)
+    g = g.astype(np.float64)
+    sizes = [27 * co * ci + co for ci, co, _, _ in UO.SPEC]
+    offs = np.concatenate([[0], np.cumsum(sizes)])
+    per_layer = [float(np.linalg.norm(g[a:b] - go[a:b]) / np.linalg.norm(go[a:b])) for a, b in zip(offs, offs[1:])]
+    whole = float(np.linalg.norm(g - go) / np.linalg.norm(go))
+    cos = float(g @ go / (np.linalg.norm(g) * np.linalg.norm(go)))
+    print(f"loss {loss_g:.6f} vs {loss_o:.6f}; gradient rel {whole:.2e} cos {cos:.6f}; per layer "
+          f"{['%.1e' % v for v in per_layer]}")
+    assert abs(loss_g - loss_o) <= 2e-2 * loss_o
+    assert whole < 5e-2 and cos > 0.995
+    assert max(per_layer) < 1e-1

@@ -735,3 +735,34 @@ def test_lsqr_reorth_keeps_krylov_minimiser_where_plain_recurrence_drifts():
     plain = O.lsqr_prior(lambda v: A @ v, lambda u: A.T @ u, lambda p: Pinv @ p, b, 2, fixed_counts=True)
     ro = O.lsqr_prior(lambda v: A @ v, lambda u: A.T @ u, lambda p: Pinv @ p, b, 2, fixed_counts=True, reorth=True)
     assert np.linalg.norm(ro.x - plain.x) <= 1e-8 * np.linalg.norm(plain.x)
+
+
+def test_jacobi_pcg_matches_sparse_lu():
+    """The oracle's iterative stand-in for large meshes: Jacobi PCG to a
+    relative residual of 1e-13 agrees with the SuperLU solve within the
+    residual bound (cond x 1e-13) on the system matrix K and on M_delta, for
+    several right-hand sides at once, and in slices of iterations."""
+    cfg = S.small_config(9, 10.0, 3, 2)
+    xyz, tets = cfg.mesh()
+    m = O.Mesh(xyz, tets)
+    kap, mu = cfg.coefficients(xyz)
+    rng = np.random.default_rng(5)
+    A = O.system_matrix(m, kap, mu)
+    B = rng.standard_normal((m.N, 3))
+    X = O.JacobiPcg(A).solve(B)
+    Xd = np.stack([O.Factor(A).solve(B[:, j]) for j in range(3)], 1)
+    assert np.linalg.norm(X - Xd) <= 1e-10 * np.linalg.norm(Xd)
+    assert np.linalg.norm(B - A @ X) <= 1.01e-13 * np.linalg.norm(B) * np.sqrt(3)
+    kt, mt = 0.2 * rng.standard_normal(m.N), 0.2 * rng.standard_normal(m.N)
+    P = O.prior_matrix(m, kt, mt, 1e-2, 1.0, 1e-6)
+    b = rng.standard_normal(2 * m.N)
+    cg = O.JacobiPcg(P)
+    cg.start(b)
+    n = 0
+    while not cg.advance(7):
+        n += 1
+    x = cg.result()
+    lam = np.linalg.eigvalsh(P.toarray())
+    xd = O.Factor(P).solve(b)
+    assert n > 3 and x.shape == b.shape
+    assert np.linalg.norm(x - xd) <= 1e-13 * (lam[-1] / lam[0]) * np.linalg.norm(xd) * 10

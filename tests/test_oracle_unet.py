@@ -65,3 +65,40 @@ def test_bf16_rounding_ties_to_even():
     assert r[2] == 1.0 + 2.0 ** -6                # halfway -> even mantissa
     assert r[3] == 1.0 + 2.0 ** -7 and r[4] == -2.5
     assert abs(r[5] / 3.0e-3 - 1) < 2.0 ** -8
+
+
+def _random_net(seed, n):
+    rng = np.random.default_rng(seed)
+    parts = []
+    for ci, co, _, _ in U.SPEC:
+        parts.append(rng.standard_normal(27 * co * ci) * np.sqrt(2.0 / (27 * ci)))
+        parts.append(0.05 * rng.standard_normal(co))
+    p = np.concatenate(parts)
+    x3 = rng.standard_normal((n ** 3, 3))
+    t = rng.standard_normal(n ** 3)
+    return p, x3, t
+
+
+def test_unet_gradient_matches_central_differences():
+    """The whole-network reverse pass of unet_loss_grad against central
+    differences of the FP64 loss along random directions (8^3 grid: levels 8,
+    4, 2, 1), each direction also restricted to one layer so that a wrong or
+    missing layer gradient shows; and the plain loss equals the one the
+    gradient routine reports."""
+    n = 8
+    p, x3, t = _random_net(3, n)
+    loss, g = U.unet_loss_grad(p, x3, t, n)
+    assert abs(loss - U.unet_loss(p, x3, t, n)) <= 1e-14 * loss
+    rng = np.random.default_rng(4)
+    sizes = [27 * co * ci + co for ci, co, _, _ in U.SPEC]
+    offs = np.concatenate([[0], np.cumsum(sizes)])
+    dirs = [rng.standard_normal(p.size)]
+    for layer in (0, 6, 8, 12, 14):
+        d = np.zeros(p.size)
+        d[offs[layer]:offs[layer + 1]] = rng.standard_normal(sizes[layer])
+        dirs.append(d)
+    for d in dirs:
+        d = d / np.linalg.norm(d)
+        eps = 1e-6
+        fd = (U.unet_loss(p + eps * d, x3, t, n) - U.unet_loss(p - eps * d, x3, t, n)) / (2 * eps)
+        assert abs(fd - g @ d) <= 1e-6 * max(abs(fd), 1e-3 * np.linalg.norm(g))
