@@ -397,7 +397,7 @@ __device__ __forceinline__ T* cheb_patch(const PcgArgs<T>& a, int ob, int nown, 
 }
 
 // ---------------------------------------------------------------- the solver
-template <typename T, int R, int OP, bool kPoly = false>
+template <typename T, int R, int OP, bool kPoly = false, int NT = kThreads>
 __device__ __forceinline__ void pcg_body(const PcgArgs<T>& a, const int cta, const int ncta) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     constexpr bool kCsr = (OP == OP_CSR1 || OP == OP_CSR2);
@@ -409,7 +409,7 @@ __device__ __forceinline__ void pcg_body(const PcgArgs<T>& a, const int cta, con
     } else {
         s.carve(reinterpret_cast<T*>(smem_raw), a.m.max_touched, a.m.max_own);
     }
-    __shared__ double scratch[(kThreads / 32) * kMaxNS];
+    __shared__ double scratch[(NT / 32) * kMaxNS];
     __shared__ double red[kMaxNS];
     __shared__ double bb[R], rz[R], rz_old[R], rr[R], alpha[R], beta[R], zcoef[R];
     __shared__ int s_flag;
@@ -720,6 +720,16 @@ constexpr int min_ctas() {
 template <typename T, int R, int OP, bool kPoly = false>
 __global__ void __launch_bounds__(kThreads) k_pcg(PcgArgs<T> a) {
     pcg_body<T, R, OP, kPoly>(a, blockIdx.x, gridDim.x);
+}
+
+// The same solver with kWideThreads threads per CTA, for the launches whose
+// shared memory (the staged direction or the preconditioner's owned-row
+// vectors of many RHS on large patches) leaves room for one CTA per SM only:
+// twice the warps per SM to hide the shared-memory and FP64 latencies.
+constexpr int kWideThreads = 2 * kThreads;
+template <typename T, int R, int OP, bool kPoly = false>
+__global__ void __launch_bounds__(kWideThreads) k_pcg_wide(PcgArgs<T> a) {
+    pcg_body<T, R, OP, kPoly, kWideThreads>(a, blockIdx.x, gridDim.x);
 }
 
 // ---------------------------------------------------------------- single-reduction variant
@@ -1533,6 +1543,22 @@ cudaError_t launch_pcg_t(const MeshDev& m, const OpParams<T>& op, const T* invdi
     err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, smem);
     if (err != cudaSuccess) return err;
     if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    int nthreads = kThreads;
+    if constexpr (kCsr && !kSingle && R >= 4) {
+        if (per_sm == 1 && !w.force_narrow) {
+            // one CTA per SM: the wide variant, if it keeps one resident CTA
+            void (*wk)(PcgArgs<T>) = deg > 0 ? k_pcg_wide<T, R, OP, true> : k_pcg_wide<T, R, OP>;
+            int pw = 0;
+            if (cudaFuncSetAttribute(wk, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)) == cudaSuccess &&
+                cudaOccupancyMaxActiveBlocksPerMultiprocessor(&pw, wk, kWideThreads, smem) == cudaSuccess &&
+                pw >= 1) {
+                kern = wk;
+                nthreads = kWideThreads;
+                per_sm = pw;
+            }
+            (void)cudaGetLastError();
+        }
+    }
     int maxres = per_sm * nsm;
     if (maxres > kMaxGrid) maxres = kMaxGrid;
     // equal patch counts per CTA: k = ceil(P / resident), grid = ceil(P / k)
@@ -1574,7 +1600,7 @@ cudaError_t launch_pcg_t(const MeshDev& m, const OpParams<T>& op, const T* invdi
     if (err != cudaSuccess) return err;
     void* args[] = {&a};
     qpat::note_launch(1);
-    return cudaLaunchCooperativeKernel((void*)kern, dim3(grid), dim3(kThreads), args, smem, s);
+    return cudaLaunchCooperativeKernel((void*)kern, dim3(grid), dim3(nthreads), args, smem, s);
 }
 
 // Ring variant: picks the most slots (<= kMaxSlots) that keep min(4, P / SMs)
