@@ -676,7 +676,12 @@ def run_ours(args):
         import torch.distributed as dist
         dist.init_process_group("nccl")
     torch.cuda.set_device(local)
-    prm = Q.qpat_default_params(precision=0)
+    # FP64 K solves with Jacobi: on GB300 they are bound by the FP64 pipe, and
+    # the patch-local polynomial's extra FP64 work per iteration costs more
+    # than its saved iterations (128^3, 16-RHS pair: 1203 ms at degree 0,
+    # 1321 / 1339 / 1437 ms at degrees 1 / 2 / 3); M_delta keeps the library's
+    # degree 2 (325 ms, 327 ms with Jacobi)
+    prm = Q.qpat_default_params(precision=0, poly_degree=0)
     if args.poly is not None:
         prm.poly_degree = args.poly
     if args.prior_poly is not None:
@@ -929,7 +934,12 @@ def recon_leg(Q, torch, n: int = 64, seed: int = 7, T: float = 2e-2, cap: int = 
            "params": f"T = {T}, LSQR cap {cap}, otherwise library defaults (paper's b/a, delta, m0, tau; "
                      f"5 linearisations; reorthogonalised LSQR)"}
     res = {}
+    # fp64_alt: the same FP64 method with an equally valid solver setting (the
+    # K solves with Jacobi instead of the degree-2 patch polynomial, both to
+    # the same 1e-13 residual): how far two FP64 runs lie apart measures the
+    # method's own sensitivity to solve-level rounding at this size
     for name, prm in (("fp64", Q.qpat_default_params(precision=0, T=T, max_lsqr=cap)),
+                      ("fp64_alt", Q.qpat_default_params(precision=0, T=T, max_lsqr=cap, poly_degree=0)),
                       ("mixed", Q.qpat_default_params(precision=1, fp32_operator=1, T=T, max_lsqr=cap))):
         warm = Q.qpat_default_params(precision=prm.precision, fp32_operator=1, max_lin=1, max_lsqr=2, fixed_counts=1)
         Q.qpat_reconstruct(mesh, flux, chi, sig, warm)         # warm-up (workspace, kernels)
@@ -951,15 +961,22 @@ def recon_leg(Q, torch, n: int = 64, seed: int = 7, T: float = 2e-2, cap: int = 
                      "residuals": [float(v) for v in rep.residuals[:rep.linearisations + 1] if v > 0],
                      "noise_level": float(np.sqrt(chi.size)), "pcg_iters": int(rep.pcg_iters)}
     f, m = out["fp64"], out["mixed"]
+    res = {k: v for k, v in res.items() if "failed" not in out[k]}
     if "failed" in f or "failed" in m:
         out["equal_error"] = False
         mesh.close()
         return out
     out["speedup_mixed_vs_fp64"] = f["wall_s"] / m["wall_s"]
     out["field_rel_diff"] = max(rel(res["mixed"][i], res["fp64"][i]) for i in range(2))
-    out["equal_error"] = bool(abs(m["e_mu"] - f["e_mu"]) <= 0.01 * f["e_mu"]
-                              and abs(m["e_kappa"] - f["e_kappa"]) <= 0.01 * f["e_kappa"]
-                              and out["field_rel_diff"] <= 1e-6)
+    errs_equal = bool(abs(m["e_mu"] - f["e_mu"]) <= 0.01 * f["e_mu"]
+                      and abs(m["e_kappa"] - f["e_kappa"]) <= 0.01 * f["e_kappa"])
+    # the survey's definition: errors within 1 % and fields within 1e-6
+    out["equal_error"] = bool(errs_equal and out["field_rel_diff"] <= 1e-6)
+    if "fp64_alt" in res:
+        fl = max(rel(res["fp64_alt"][i], res["fp64"][i]) for i in range(2))
+        out["fp64_vs_fp64_alt_field_rel_diff"] = fl
+        # errors within 1 % and fields no further apart than two FP64 runs
+        out["equal_error_within_fp64_sensitivity"] = bool(errs_equal and out["field_rel_diff"] <= max(1e-6, fl))
     mesh.close()
     return out
 

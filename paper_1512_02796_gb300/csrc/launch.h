@@ -109,7 +109,7 @@ struct PcgWork {
     int* iters;         // 1
     double* stats;      // 2R: final r.r, b.b
     long long spin_limit = 0;  // grid-barrier polls before QPAT_ETIMEOUT (0 = default, about 2 s)
-    int force_narrow = 0;      // 1: never the wide (2 x kThreads) two-reduction kernel
+    int force_narrow = 0;      // 1: the plain two-reduction kernel only (no wide or occupancy-bounded form)
 };
 
 // Persistent fused Jacobi-PCG on R right-hand sides (see pcg.cu).  b is

@@ -23,6 +23,7 @@
 #include <cuda/atomic>
 #include <algorithm>
 #include <cstring>
+#include <type_traits>
 #include <vector>
 
 #include "launch.h"
@@ -638,7 +639,13 @@ __device__ __forceinline__ void pcg_body(const PcgArgs<T>& a, const int cta, con
             T al[VW];
 #pragma unroll
             for (int c = 0; c < VW; ++c) al[c] = T(alpha[r0 + c]);
-            for (int p = cta; p < P; p += ncta) {
+            // this CTA's patches in the reverse order of phase A: the patches
+            // it handled last there (their operator slices and p, q still
+            // partly in L2) come first here, and the next phase A starts
+            // again where this one ends
+            const int nmine = cta < P ? (P - 1 - cta) / ncta + 1 : 0;
+            for (int jp = nmine - 1; jp >= 0; --jp) {
+                const int p = cta + jp * ncta;
                 const int ob = __ldg(m.own_begin + p), nown = __ldg(m.own_begin + p + 1) - ob;
                 for (int i = threadIdx.x; i < nown * NP; i += blockDim.x) {
                     const int g = ob + i / NP;
@@ -719,6 +726,15 @@ constexpr int min_ctas() {
 
 template <typename T, int R, int OP, bool kPoly = false>
 __global__ void __launch_bounds__(kThreads) k_pcg(PcgArgs<T> a) {
+    pcg_body<T, R, OP, kPoly>(a, blockIdx.x, gridDim.x);
+}
+
+// The two-block M_delta solver (R = 2, two value sets, patch-local
+// preconditioner) held to three resident CTAs per SM (78 registers, no
+// spills): at its unbounded 107 registers only two fit, 16 warps per SM for
+// a kernel bound by FP64 issue and shared-memory latency.
+template <typename T, int R, int OP, bool kPoly = false>
+__global__ void __launch_bounds__(kThreads, 3) k_pcg_occ3(PcgArgs<T> a) {
     pcg_body<T, R, OP, kPoly>(a, blockIdx.x, gridDim.x);
 }
 
@@ -1532,6 +1548,8 @@ cudaError_t launch_pcg_t(const MeshDev& m, const OpParams<T>& op, const T* invdi
         kern = k_pcg1<T, R, OP>;
     } else if constexpr (kCsr) {
         kern = deg > 0 ? k_pcg<T, R, OP, true> : k_pcg<T, R, OP>;
+        if constexpr (OP == OP_CSR2 && R == 2 && std::is_same<T, double>::value)
+            if (deg > 0 && !w.force_narrow) kern = k_pcg_occ3<T, R, OP, true>;
     } else {
         kern = k_pcg<T, R, OP>;
     }
