@@ -7,6 +7,7 @@
 #include <cmath>
 #include <cstring>
 #include <map>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -521,6 +522,29 @@ using namespace qpat;
 
 namespace qpat {
 static std::atomic<long long> g_launches{0};
+
+cudaError_t allow_smem(const void* func, size_t smem) {
+    static std::mutex mu;
+    static std::map<std::pair<int, const void*>, size_t> raised;  // (device, kernel) -> allowed bytes
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    std::lock_guard<std::mutex> lk(mu);
+    auto key = std::make_pair(dev, func);
+    auto it = raised.find(key);
+    if (it == raised.end()) {
+        int optin = 0;
+        cudaFuncAttributes fa{};
+        if ((e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev)) != cudaSuccess ||
+            (e = cudaFuncGetAttributes(&fa, func)) != cudaSuccess)
+            return e;
+        const size_t lim = size_t(optin) > fa.sharedSizeBytes ? size_t(optin) - fa.sharedSizeBytes : 0;
+        if ((e = cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, int(lim))) != cudaSuccess)
+            return e;
+        it = raised.emplace(key, lim).first;
+    }
+    return smem <= it->second ? cudaSuccess : cudaErrorInvalidValue;
+}
 void note_launch(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 }  // namespace qpat
 

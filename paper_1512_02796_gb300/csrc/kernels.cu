@@ -44,7 +44,7 @@ cudaError_t apply_t(const MeshDev& m, const OpParams<T>& op, T sign, const T* x,
                     cudaStream_t st) {
     const size_t smem = PatchSmem<T, R>::bytes(m.max_touched, m.max_own);
     auto kern = k_apply<T, R, OP>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+    cudaError_t e = qpat::allow_smem((const void*)kern, size_t(smem));
     if (e != cudaSuccess) return e;
     qpat::note_launch(1);
     kern<<<m.P, kThreads, smem, st>>>(m, op, sign, x, y, ldx, c0);
@@ -314,7 +314,7 @@ template <typename T, int R, int NV>
 cudaError_t apply_csr_t(const MeshDev& m, const T* v0, const T* v1, const T* x, T* y, cudaStream_t st) {
     const size_t smem = sizeof(T) * size_t(m.max_touched) * R;
     auto kern = k_apply_csr<T, R, NV>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+    cudaError_t e = qpat::allow_smem((const void*)kern, size_t(smem));
     if (e != cudaSuccess) return e;
     qpat::note_launch(1);
     kern<<<m.P, kThreads, smem, st>>>(m, v0, v1, x, y);
@@ -395,7 +395,7 @@ template <typename T, int K>
 cudaError_t vjp_t(const MeshDev& m, const T* phi, const T* z, T* y, int ldk, int c0, int acc, cudaStream_t st) {
     const size_t smem = sizeof(T) * (size_t(m.max_touched) * (3 + 2 * K) + size_t(m.max_own) * 2);
     auto kern = k_vjp_accum<T, K>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+    cudaError_t e = qpat::allow_smem((const void*)kern, size_t(smem));
     if (e != cudaSuccess) return e;
     qpat::note_launch(1);
     kern<<<m.P, kThreads, smem, st>>>(m, phi, z, y, ldk, c0, acc);
@@ -531,7 +531,7 @@ cudaError_t launch_apply_prior(const MeshDev& m, const T* u1, const T* u2, T inv
 cudaError_t launch_invdiag_K(const MeshDev& m, const double* kappa, const double* mu, double* inv64, float* inv32,
                              cudaStream_t s) {
     const size_t smem = PatchSmem<double, 1>::bytes(m.max_touched, m.max_own);
-    cudaError_t e = cudaFuncSetAttribute(k_diag_K, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+    cudaError_t e = qpat::allow_smem((const void*)k_diag_K, size_t(smem));
     if (e != cudaSuccess) return e;
     qpat::note_launch(1);
     k_diag_K<<<m.P, kThreads, smem, s>>>(m, kappa, mu, inv64, inv32);
@@ -542,7 +542,7 @@ cudaError_t launch_invdiag_prior(const MeshDev& m, const double* u1, const doubl
                                  double q, double scale1, double delta, double* inv64, float* inv32,
                                  cudaStream_t s) {
     const size_t smem = PatchSmem<double, 2>::bytes(m.max_touched, m.max_own);
-    cudaError_t e = cudaFuncSetAttribute(k_diag_prior, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+    cudaError_t e = qpat::allow_smem((const void*)k_diag_prior, size_t(smem));
     if (e != cudaSuccess) return e;
     qpat::note_launch(1);
     k_diag_prior<<<m.P, kThreads, smem, s>>>(m, u1, u2, inv_T2, kind, q, scale1, delta, inv64, inv32);
@@ -554,7 +554,7 @@ cudaError_t launch_assemble_K(const MeshDev& m, const double* kappa, const doubl
     cudaError_t e = cudaMemsetAsync(val, 0, sizeof(double) * m.sell_entries, s);
     if (e != cudaSuccess) return e;
     const size_t smem = PatchSmem<double, 1>::bytes(m.max_touched, m.max_own);
-    e = cudaFuncSetAttribute(k_assemble_K, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+    e = qpat::allow_smem((const void*)k_assemble_K, size_t(smem));
     if (e != cudaSuccess) return e;
     qpat::note_launch(1);
     k_assemble_K<<<m.P, kThreads, smem, s>>>(m, kappa, mu, val);
@@ -571,7 +571,7 @@ cudaError_t launch_assemble_prior(const MeshDev& m, const double* u1, const doub
     if (e == cudaSuccess) e = cudaMemsetAsync(val1, 0, sizeof(double) * m.sell_entries, s);
     if (e != cudaSuccess) return e;
     const size_t smem = PatchSmem<double, 1>::bytes(m.max_touched, m.max_own);
-    e = cudaFuncSetAttribute(k_assemble_prior, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+    e = qpat::allow_smem((const void*)k_assemble_prior, size_t(smem));
     if (e != cudaSuccess) return e;
     qpat::note_launch(1);
     k_assemble_prior<<<m.P, kThreads, smem, s>>>(m, u1, u2, inv_T2, kind, q, scale1, val0, val1);

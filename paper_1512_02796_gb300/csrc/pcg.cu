@@ -1441,7 +1441,7 @@ cudaError_t batch_prepare_t(const std::vector<PcgBatchProblem>& probs, PcgBatchP
         if (poly) smem = std::max(smem, 3 * sizeof(double) * size_t(p.m.max_own) * R);
     }
     auto kern = poly ? k_pcg_batch<double, R, OP_CSR1, true> : k_pcg_batch<double, R, OP_CSR1>;
-    cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+    cudaError_t err = qpat::allow_smem((const void*)kern, size_t(smem));
     if (err != cudaSuccess) return err;
     int dev = 0, nsm = 0, per_sm = 0;
     cudaGetDevice(&dev);
@@ -1553,7 +1553,7 @@ cudaError_t launch_pcg_t(const MeshDev& m, const OpParams<T>& op, const T* invdi
     } else {
         kern = k_pcg<T, R, OP>;
     }
-    cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+    cudaError_t err = qpat::allow_smem((const void*)kern, size_t(smem));
     if (err != cudaSuccess) return err;
     int dev = 0, nsm = 0, per_sm = 0;
     cudaGetDevice(&dev);
@@ -1567,7 +1567,7 @@ cudaError_t launch_pcg_t(const MeshDev& m, const OpParams<T>& op, const T* invdi
             // one CTA per SM: the wide variant, if it keeps one resident CTA
             void (*wk)(PcgArgs<T>) = deg > 0 ? k_pcg_wide<T, R, OP, true> : k_pcg_wide<T, R, OP>;
             int pw = 0;
-            if (cudaFuncSetAttribute(wk, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)) == cudaSuccess &&
+            if (qpat::allow_smem((const void*)wk, size_t(smem)) == cudaSuccess &&
                 cudaOccupancyMaxActiveBlocksPerMultiprocessor(&pw, wk, kWideThreads, smem) == cudaSuccess &&
                 pw >= 1) {
                 kern = wk;
@@ -1635,7 +1635,7 @@ cudaError_t launch_pcg_ring_t(const MeshDev& m, const OpParams<T>& op, const T* 
     cudaError_t err = cudaFuncGetAttributes(&fa, kern);
     if (err != cudaSuccess) return err;
     const int dyn_max = smem_optin - int(fa.sharedSizeBytes);  // static + dynamic <= opt-in limit
-    err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn_max);
+    err = qpat::allow_smem((const void*)kern, size_t(dyn_max));
     if (err != cudaSuccess) return err;
     const int want = std::max(1, std::min(4, (m.P + nsm - 1) / nsm));
     RingLayout L{};

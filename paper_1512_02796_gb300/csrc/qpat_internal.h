@@ -16,6 +16,14 @@ namespace qpat {
 // replayed CUDA graph counts its kernel nodes); read by qpat_launch_count.
 void note_launch(int n = 1);
 
+// Lets kernel `func` launch with `smem` bytes of dynamic shared memory.  The
+// attribute this sets is one value per kernel for the whole process, so it is
+// raised once to everything the device allows beside the kernel's static
+// shared memory (never lowered): concurrent launches of the same kernel from
+// several host threads with different sizes then cannot undo each other.
+// cudaErrorInvalidValue if `smem` exceeds that limit.
+cudaError_t allow_smem(const void* func, size_t smem);
+
 // Host-side mesh after preparation.  Node ids inside are LIBRARY ids: nodes
 // are sorted by the Morton code of their coordinates, so that a contiguous
 // range of library ids is a spatially compact block.  The ranges of

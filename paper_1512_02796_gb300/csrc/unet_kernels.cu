@@ -110,7 +110,7 @@ template <int NT>
 cudaError_t conv_fwd_t(const bf16* in, int Cin, const bf16* w, const float* bias, int Cout, int relu, bf16* out,
                        float* out32, int n, cudaStream_t s) {
     const size_t smem = sizeof(uint32_t) * size_t(Cout) * ((Cin + 8) / 2);
-    cudaError_t e = cudaFuncSetAttribute(k_conv_fwd<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+    cudaError_t e = qpat::allow_smem((const void*)k_conv_fwd<NT>, size_t(smem));
     if (e != cudaSuccess) return e;
     const int nvox = n * n * n;
     const int grid = (nvox + 16 * kConvWarps - 1) / (16 * kConvWarps);

@@ -15,6 +15,7 @@
 
 namespace qpat {
 void note_launch(int n);  // launch counter (abi.cu)
+cudaError_t allow_smem(const void* func, size_t smem);  // dynamic shared memory permission (abi.cu)
 }
 #include <cuda_runtime.h>
 

@@ -233,7 +233,7 @@ template <int NCOLS>
 cudaError_t conv_fwd_tc_t(const bf16* in, int Cin, const bf16* w, const float* bias, int Cout, int relu, bf16* out,
                           float* out32, int n, cudaStream_t s) {
     const size_t smem = 2 * (size_t(kTcRows) * Cin * 2 + size_t(Cout) * Cin * 2);
-    cudaError_t e = cudaFuncSetAttribute(k_conv_fwd_tc<NCOLS>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+    cudaError_t e = qpat::allow_smem((const void*)k_conv_fwd_tc<NCOLS>, size_t(smem));
     if (e != cudaSuccess) return e;
     const int nvox = n * n * n;
     qpat::note_launch(1);

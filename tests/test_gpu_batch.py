@@ -106,3 +106,38 @@ def test_several_wavelengths_on_one_mesh_in_one_launch():
     finally:
         batch.close()
         m.close()
+
+
+def test_concurrent_reconstructions_match_sequential():
+    """Independent reconstructions (Algorithm 1) on meshes of different sizes
+    run concurrently, one host thread and one mesh stream each (the library
+    call releases the interpreter), give bit for bit the results of the same
+    reconstructions run one after the other: every device sum has a fixed
+    order, whatever else runs on the GPU."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from concurrent.futures import ThreadPoolExecutor
+    probs = []
+    for i, (n, K) in enumerate([(7, 1), (9, 2), (11, 3), (8, 4)]):
+        cfg = S.small_config(n, 2.0 * n, K, 300 + i)
+        xyz, tets = cfg.mesh()
+        kap, mu = cfg.coefficients(xyz)
+        m = Q.qpat_mesh(xyz, tets, patch_nodes=64)
+        flux = np.stack([Q.qpat_flux_patch(m, p.center, p.normal, p.half_w, p.amp) for p in cfg.patches])
+        _, h = Q.qpat_forward(m, kap, mu, flux)
+        sig = 0.01 * np.abs(h) + 1e-3 * np.abs(h).max()
+        chi = h + sig * S.noise_draws(40 + i, h.shape)
+        probs.append((m, flux, chi, sig, (float(np.median(kap)), float(np.median(mu)))))
+    prm = Q.qpat_default_params(T=1e-2, max_lin=3, max_lsqr=6, fixed_counts=1)
+    run = lambda p: Q.qpat_reconstruct(p[0], p[1], p[2], p[3], prm, p[4])
+    try:
+        seq = [run(p) for p in probs]
+        with ThreadPoolExecutor(max_workers=4) as ex:
+            con = list(ex.map(run, probs))
+        for (ks, ms, rs), (kc, mc, rc) in zip(seq, con):
+            np.testing.assert_array_equal(kc, ks)
+            np.testing.assert_array_equal(mc, ms)
+            assert rc.linearisations == rs.linearisations
+    finally:
+        for p in probs:
+            p[0].close()
