@@ -887,47 +887,63 @@ def uneven_batch_leg(Q, torch, reps: int = 5):
     return res
 
 
-def concurrent_recon_leg(Q, torch, count: int = 32, threads: int = 8):
+def concurrent_recon_leg(Q, torch, count: int = 32, threads: int = 16, patch_nodes: int = 1024):
     """Config 3: `count` independent reconstructions (Algorithm 1, FP64) on
-    cubes of 16^3-48^3 nodes with 1-4 illuminations and 2-5 inclusions, run
-    one after the other and then concurrently (`threads` host threads, each
-    problem on its mesh's own stream, so the small solves of several
-    problems share the GPU).  Settings: T = 2e-2, 3 linearisations x 10 LSQR
-    rounds with fixed counts (the same work in both runs).  Data: the
-    library's forward on the same mesh plus seeded 1 % noise (a throughput
-    leg).  Reports both wall times and that the results are bit-identical."""
+    cubes of 16^3-48^3 nodes with 1-4 illuminations and 2-5 inclusions.
+    Three runs: one after the other on the default patching (every solve
+    spreads over the whole GPU), one after the other on patches of
+    `patch_nodes` owned nodes (a solve then holds one CTA per patch, 4-108
+    CTAs), and concurrently on those meshes (`threads` host threads, each
+    problem on its mesh's own stream, so that several problems' solves share
+    the GPU).  Settings: T = 2e-2, 3 linearisations x 10 LSQR rounds with
+    fixed counts (the same work in every run).  Data: the library's forward
+    on the same mesh plus seeded 1 % noise (a throughput leg).  Reports the
+    wall times and that concurrent and sequential runs on the same meshes
+    give identical bits."""
     from concurrent.futures import ThreadPoolExecutor
     cfgs = S.uneven_batch(count)
-    probs = []
+    sets = {"default": [], "patched": []}
     for i, cfg in enumerate(cfgs):
         xyz, tets = cfg.mesh()
         kap, mu = cfg.coefficients(xyz)
-        m = Q.qpat_mesh(xyz, tets)
-        flux = np.stack([Q.qpat_flux_patch(m, p.center, p.normal, p.half_w, p.amp) for p in cfg.patches])
-        _, h = Q.qpat_forward(m, kap, mu, flux, Q.qpat_default_params(precision=0))
-        sig = 0.01 * np.abs(h) + 1e-3 * np.abs(h).max()
-        chi = h + sig * S.noise_draws(cfg.seed + 7, h.shape)
-        probs.append((m, flux, chi, sig, (float(np.median(kap)), float(np.median(mu)))))
+        for key, pn in (("default", None), ("patched", patch_nodes)):
+            m = Q.qpat_mesh(xyz, tets, patch_nodes=pn)
+            flux = np.stack([Q.qpat_flux_patch(m, p.center, p.normal, p.half_w, p.amp) for p in cfg.patches])
+            if key == "default":
+                _, h = Q.qpat_forward(m, kap, mu, flux, Q.qpat_default_params(precision=0))
+                sig = 0.01 * np.abs(h) + 1e-3 * np.abs(h).max()
+                chi = h + sig * S.noise_draws(cfg.seed + 7, h.shape)
+            sets[key].append((m, flux, chi, sig, (float(np.median(kap)), float(np.median(mu)))))
     prm = Q.qpat_default_params(precision=0, T=2e-2, max_lin=3, max_lsqr=10, fixed_counts=1)
     run = lambda p: Q.qpat_reconstruct(p[0], p[1], p[2], p[3], prm, p[4])
+    rel = lambda a, b: float(np.linalg.norm(a - b) / np.linalg.norm(b))
     try:
-        run(probs[0])                                 # warm-up
+        run(sets["default"][0])                       # warm-up
+        run(sets["patched"][0])
         t0 = time.perf_counter()
-        seq = [run(p) for p in probs]
+        seq = [run(p) for p in sets["default"]]
         t_seq = time.perf_counter() - t0
         t0 = time.perf_counter()
+        seqp = [run(p) for p in sets["patched"]]
+        t_seqp = time.perf_counter() - t0
+        t0 = time.perf_counter()
         with ThreadPoolExecutor(max_workers=threads) as ex:
-            con = list(ex.map(run, probs))
+            con = list(ex.map(run, sets["patched"]))
         t_con = time.perf_counter() - t0
-        same = all(np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1]) for a, b in zip(seq, con))
-        return {"problems": count, "nodes_total": int(sum(p[0].N for p in probs)),
+        same = all(np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1]) for a, b in zip(seqp, con))
+        diff = max(max(rel(a[0], b[0]), rel(a[1], b[1])) for a, b in zip(seq, con))
+        return {"problems": count, "nodes_total": int(sum(p[0].N for p in sets["default"])),
                 "illuminations_total": int(sum(c.K for c in cfgs)), "threads": threads,
+                "patch_nodes": patch_nodes,
                 "settings": "FP64, T = 2e-2, 3 linearisations x 10 LSQR rounds, fixed counts",
-                "sequential_s": t_seq, "concurrent_s": t_con, "speedup": t_seq / t_con,
-                "reconstructions_per_s": count / t_con, "bit_identical": bool(same)}
+                "sequential_default_patching_s": t_seq, "sequential_patched_s": t_seqp,
+                "concurrent_patched_s": t_con, "speedup_vs_sequential_default": t_seq / t_con,
+                "reconstructions_per_s": count / t_con, "concurrent_bit_identical_to_sequential": bool(same),
+                "max_field_rel_diff_vs_default_patching": diff}
     finally:
-        for p in probs:
-            p[0].close()
+        for v in sets.values():
+            for p in v:
+                p[0].close()
 
 
 def autotune_leg(Q):
@@ -1282,19 +1298,30 @@ def run_reference(args):
 
 def run_profile_case(args):
     """Fixed sequence for ncu captures of the PCG kernels on the workload:
-    one FP64 pair, one M_delta solve, one mixed-precision pair (no timing, no
-    output but a status line)."""
+    the set-up forward solve, one FP64 pair (the bench's FP64 arm: Jacobi K
+    solves), one M_delta solve and one mixed-precision pair.  No timing;
+    prints the PCG launches and iterations of each call (deterministic, so a
+    plain run gives the per-launch iterations of a captured launch)."""
     import torch
     import paper_1512_02796_gb300 as Q
     d = setup_problem(Q, torch, args.workload, args.patch_nodes)
     mesh = d["mesh"]
-    for prm in (Q.qpat_default_params(precision=0), Q.qpat_default_params(precision=1, fp32_operator=1)):
-        Q.qpat_jvp_vjp_pair_dev(mesh, d["kappa"], d["mu"], d["phi"], d["w"], d["s"], d["t"], d["oj"], d["ov"], prm)
-        if prm.precision == 0:
+    calls = []
+    for name, prm in (("pair_fp64", Q.qpat_default_params(precision=0, poly_degree=0)),
+                      ("prior_fp64", Q.qpat_default_params(precision=0)),
+                      ("pair_fp32", Q.qpat_default_params(precision=1, fp32_operator=1))):
+        mesh.reset_stats()
+        if name == "prior_fp64":
             Q.qpat_prior_solve_dev(mesh, d["kt"], d["mt"], d["prior_rhs"], d["op"], prm)
-    torch.cuda.synchronize()
+        else:
+            Q.qpat_jvp_vjp_pair_dev(mesh, d["kappa"], d["mu"], d["phi"], d["w"], d["s"], d["t"], d["oj"],
+                                    d["ov"], prm)
+        torch.cuda.synchronize()
+        st = mesh.stats()
+        calls.append({"call": name, "launches": st["launches"], "pcg_iters": st["pcg_iters"],
+                      "rhs_iters": st["rhs_iters"]})
     mesh.close()
-    print("profile case ok", flush=True)
+    print(json.dumps({"profile_case": args.workload, "calls": calls}), flush=True)
 
 
 def main():
@@ -1332,7 +1359,8 @@ def main():
                     help="train and test the learned initial guess on the 128^3 workload and exit")
     ap.add_argument("--concurrent-study", action="store_true",
                     help="run the Config 3 leg (32 reconstructions, sequential vs concurrent) and exit")
-    ap.add_argument("--study-threads", type=int, default=8)
+    ap.add_argument("--study-threads", type=int, default=16)
+    ap.add_argument("--study-patch-nodes", type=int, default=1024)
     ap.add_argument("--study-phantoms", type=int, default=48)
     ap.add_argument("--study-steps", type=int, default=600)
     args = ap.parse_args()
@@ -1341,7 +1369,8 @@ def main():
     if args.concurrent_study:
         import torch
         import paper_1512_02796_gb300 as Q
-        print(json.dumps(concurrent_recon_leg(Q, torch, threads=args.study_threads)), flush=True)
+        print(json.dumps(concurrent_recon_leg(Q, torch, threads=args.study_threads,
+                                              patch_nodes=args.study_patch_nodes)), flush=True)
         return
     if args.learned_study:
         import torch
