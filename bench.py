@@ -1170,7 +1170,7 @@ def learned_leg(Q, torch, n: int = 32, train_phantoms: int = 18, steps: int = 15
 
 
 def learned_study(Q, torch, workload: str = "c4_cube128", phantoms: int = 48, held_out: int = 2,
-                  steps: int = 600, batch: int = 2, lr: float = 2e-3):
+                  steps: int = 600, batch: int = 2, lr: float = 2e-3, log_floor: float = 0.0):
     """Config 4's learned initial guess at full size: the BF16 U-Net (4
     levels, 16 base channels) trained on the library's own FP32 + refinement
     forward solves of `phantoms` seeded log-normal blob fields x 8
@@ -1184,6 +1184,8 @@ def learned_study(Q, torch, workload: str = "c4_cube128", phantoms: int = 48, he
     xyz, tets = cfgs[0].mesh()
     mesh = Q.qpat_mesh(xyz, tets)
     net = Q.UNet(cfgs[0].n, seed=1)
+    if log_floor > 0:
+        net.set_log_output(log_floor)
     t0 = time.perf_counter()
     with ThreadPoolExecutor(max_workers=8) as ex:     # numpy releases the GIL in the blob sums
         coefs = list(ex.map(lambda c: c.coefficients(xyz), cfgs))
@@ -1235,6 +1237,7 @@ def learned_study(Q, torch, workload: str = "c4_cube128", phantoms: int = 48, he
                          "guess_rel_error": float(torch.linalg.norm(phi0 - pa) / torch.linalg.norm(pa)),
                          "solution_rel_diff": float(torch.linalg.norm(pb - pa) / torch.linalg.norm(pa))})
         return {"study": "learned initial guess (Config 4)", "n": cfgs[0].n, "illuminations": int(flux.shape[0]),
+                "output": f"log(max(phi, {log_floor}))" if log_floor > 0 else "phi",
                 "train_phantoms": phantoms, "train_solves": phantoms * int(flux.shape[0]), "adam_steps": steps,
                 "batch": batch, "phantom_generation_s": t_gen, "training_solves_s": t_solves, "train_s": train_s,
                 "loss_first": float(np.mean(losses[:10])), "loss_last": float(np.mean(losses[-10:])),
@@ -1363,6 +1366,8 @@ def main():
     ap.add_argument("--study-patch-nodes", type=int, default=1024)
     ap.add_argument("--study-phantoms", type=int, default=48)
     ap.add_argument("--study-steps", type=int, default=600)
+    ap.add_argument("--study-log-floor", type=float, default=0.0,
+                    help="> 0: the network learns log(max(phi, floor)) (qpat_unet_set_log_output)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -1375,7 +1380,8 @@ def main():
     if args.learned_study:
         import torch
         import paper_1512_02796_gb300 as Q
-        print(json.dumps(learned_study(Q, torch, phantoms=args.study_phantoms, steps=args.study_steps)), flush=True)
+        print(json.dumps(learned_study(Q, torch, phantoms=args.study_phantoms, steps=args.study_steps,
+                                       log_floor=args.study_log_floor)), flush=True)
         return
     if args.illumination_study:
         import paper_1512_02796_gb300 as Q

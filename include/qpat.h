@@ -377,6 +377,12 @@ int qpat_unet_features_dev(qpat_mesh_t mesh, const double* kappa, const double* 
 int qpat_unet_predict_dev(qpat_unet_t unet, const float* x, int B, float* y, void* stream);
 int qpat_unet_train_dev(qpat_unet_t unet, const float* x, const float* t, int B, float lr,
                         float* loss, void* stream);
+/* Output mode: floor > 0 makes the network learn log(max(phi, floor)) of its
+ * targets (training loss in log space) and predict the exponential of its
+ * output, so that fields spanning decades are fitted relative to their size;
+ * floor = 0 (default) fits and predicts phi itself.  QPAT_EINVAL for a NULL
+ * network or a negative or non-finite floor. */
+int qpat_unet_set_log_output(qpat_unet_t unet, double floor);
 /* The training loss of those B samples and its gradient with respect to
  * every parameter (summed over the samples, no update): grad (HOST,
  * qpat_unet_num_params floats, the layout of qpat_unet_get_params), *loss

@@ -51,17 +51,22 @@ __global__ void k_pack_input(int64_t nvox, const float* x, bf16* xin) {
     }
 }
 
-__global__ void k_take_channel0(int64_t nvox, const float* y32, float* y) {
+// channel 0 of the output; in log mode (log_floor > 0) the network's output
+// is log(phi) and the prediction is its exponential
+__global__ void k_take_channel0(int64_t nvox, const float* y32, float* y, float log_floor) {
     for (int64_t v = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; v < nvox; v += int64_t(gridDim.x) * blockDim.x)
-        y[v] = y32[v * 16];
+        y[v] = log_floor > 0.f ? expf(y32[v * 16]) : y32[v * 16];
 }
 
-// mean-squared error of channel 0 and its gradient (bf16, 16 channels)
-__global__ void k_mse(int64_t nvox, const float* y32, const float* t, float scale, bf16* dy, float* loss) {
+// mean-squared error of channel 0 and its gradient (bf16, 16 channels); in
+// log mode against log(max(t, log_floor))
+__global__ void k_mse(int64_t nvox, const float* y32, const float* t, float scale, bf16* dy, float* loss,
+                      float log_floor) {
     __shared__ float red[256];
     float s = 0.f;
     for (int64_t v = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; v < nvox; v += int64_t(gridDim.x) * blockDim.x) {
-        const float d = y32[v * 16] - t[v];
+        const float tv = log_floor > 0.f ? logf(fmaxf(t[v], log_floor)) : t[v];
+        const float d = y32[v * 16] - tv;
         s += d * d;
         dy[v * 16] = __float2bfloat16(2.f * d * scale);
         for (int c = 1; c < 16; ++c) dy[v * 16 + c] = __float2bfloat16(0.f);
@@ -102,6 +107,7 @@ struct qpat_unet_s {
     bf16 *g_y, *g_d0, *g_a6, *g_cat0, *g_d1, *g_s0, *g_a5, *g_cat1, *g_d2, *g_s1, *g_a4, *g_cat2, *g_bt, *g_s2, *g_a3,
         *g_p2, *g_a2, *g_p1, *g_a1, *g_p0, *g_a0;
     float* y32 = nullptr;
+    float log_floor = 0.f;  // > 0: the network learns log(max(phi, log_floor)) (qpat_unet_set_log_output)
     float* partial = nullptr;
     float* loss = nullptr;
     float* hloss = nullptr;
@@ -337,7 +343,7 @@ int qpat_unet_predict_dev(qpat_unet_t U, const float* x, int B, float* y, void* 
         int rc = unet_forward(U, s);
         if (rc) return rc;
         qpat::note_launch(1);
-        k_take_channel0<<<g1(nv), 256, 0, s>>>(nv, U->y32, y + b * nv);
+        k_take_channel0<<<g1(nv), 256, 0, s>>>(nv, U->y32, y + b * nv, U->log_floor);
     }
     UCK(cudaGetLastError());
     return QPAT_OK;
@@ -355,7 +361,7 @@ static int unet_loss_grad(qpat_unet_s* U, const float* x, const float* t, int B,
         int rc = unet_forward(U, s);
         if (rc) return rc;
         qpat::note_launch(1);
-        k_mse<<<g1(nv), 256, 0, s>>>(nv, U->y32, t + b * nv, 1.f / float(nv * B), U->g_y, U->loss);
+        k_mse<<<g1(nv), 256, 0, s>>>(nv, U->y32, t + b * nv, 1.f / float(nv * B), U->g_y, U->loss, U->log_floor);
         if ((rc = unet_backward(U, s))) return rc;
         for (auto& c : U->conv) {
             qpat::note_launch(1);
@@ -385,6 +391,13 @@ int qpat_unet_grad_dev(qpat_unet_t U, const float* x, const float* t, int B, flo
     UCK(cudaMemcpyAsync(U->hloss, U->loss, sizeof(float), cudaMemcpyDeviceToHost, s));
     UCK(cudaStreamSynchronize(s));
     if (loss) *loss = *U->hloss;
+    return QPAT_OK;
+}
+
+int qpat_unet_set_log_output(qpat_unet_t U, double floor) {
+    if (!U || !(floor >= 0.0) || !std::isfinite(floor))
+        return fail(QPAT_EINVAL, "qpat_unet_set_log_output: NULL network or bad floor");
+    U->log_floor = float(floor);
     return QPAT_OK;
 }
 

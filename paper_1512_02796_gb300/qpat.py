@@ -137,6 +137,7 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
         "qpat_unet_predict_dev": (ctypes.c_int, [vp, vp, ctypes.c_int, vp, vp]),
         "qpat_unet_train_dev": (ctypes.c_int, [vp, vp, vp, ctypes.c_int, ctypes.c_float,
                                                ctypes.POINTER(ctypes.c_float), vp]),
+        "qpat_unet_set_log_output": (ctypes.c_int, [vp, ctypes.c_double]),
         "qpat_unet_grad_dev": (ctypes.c_int, [vp, vp, vp, ctypes.c_int, ctypes.POINTER(ctypes.c_float),
                                               ctypes.POINTER(ctypes.c_float), vp]),
         "qpat_unet_to_double_dev": (ctypes.c_int, [vp, ctypes.c_int64, vp, vp]),
@@ -182,6 +183,7 @@ def exported_names() -> Sequence[str]:
         "qpat_autotune", "qpat_reconstruct", "qpat_reconstruct_ex",
         "qpat_unet_create", "qpat_unet_free", "qpat_unet_num_params", "qpat_unet_get_params", "qpat_unet_set_params",
         "qpat_unet_features_dev", "qpat_unet_predict_dev", "qpat_unet_train_dev", "qpat_unet_grad_dev",
+        "qpat_unet_set_log_output",
         "qpat_unet_to_double_dev",
         "qpat_conv3d_bf16_dev", "qpat_conv3d_bf16_wgrad_dev", "qpat_conv3d_bf16_wgrad_scratch",
         "qpat_conv3d_set_engine", "qpat_conv3d_tc_timeouts",
@@ -219,6 +221,10 @@ class UNet:
         _check(load().qpat_unet_train_dev(self.handle, _tpf(x), _tpf(t), x.shape[0], float(lr), ctypes.byref(loss),
                                           _stream()))
         return float(loss.value)
+
+    def set_log_output(self, floor: float):
+        """floor > 0: learn log(max(phi, floor)) and predict exp of the output."""
+        _check(load().qpat_unet_set_log_output(self.handle, float(floor)))
 
     def grad(self, x, t):
         """(loss, gradient) of the mean squared error of samples x against

@@ -1,11 +1,16 @@
-"""Parity at the benchmark's full size (40 mm cube, 64^3 nodes, 4 illuminations)
-in the launch configuration bench.py times.  The oracle's sparse
-factorisation is too slow here, so each result is checked through a property
-that holds at any size, using only the oracle's assembled matrices:
-  K x against the oracle CSR product (sampled rows and the full vector),
+"""Parity at the benchmark's full sizes -- the 64^3 cube (Config 1, 4
+illuminations) and the bench's 128^3 workload (Config 4, 8 illuminations,
+the 16-RHS pair) -- in the launch configurations bench.py times.  The
+oracle's sparse factorisation is too slow here, so each result is checked
+through a property that holds at any size, using only the oracle's assembled
+matrices:
+  K x against the oracle CSR product,
   the forward residual |K phi - f| / |f| with the oracle K and f,
   the J s solve residual |K x - (G1 kappa s1 + G2 mu s2)| with the oracle G,
-  and the adjoint identity <J s, t> = <s, J^T t> of the paired launch.
+  the adjoint identity <J s, t> = <s, J^T t> of the paired launch,
+  the M_delta solve's normwise backward error against the oracle's M_delta.
+The linearisation point phi handed to J s and J^T t is a seeded smooth
+positive field (the formulas hold for any phi), not a GPU result.
 """
 import numpy as np
 import pytest
@@ -20,16 +25,32 @@ Q = pytest.importorskip("paper_1512_02796_gb300")
 pytestmark = pytest.mark.gpu
 
 
-@pytest.fixture(scope="module")
-def big():
+def smooth_phi(xyz, K, L, seed):
+    """K seeded smooth positive fields on the nodes (decaying away from a
+    random face, with a gentle random modulation)."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for _ in range(K):
+        ax, side = int(rng.integers(0, 3)), int(rng.integers(0, 2))
+        d = xyz[:, ax] if side == 0 else L - xyz[:, ax]
+        mod = 1.0 + 0.2 * np.sin(2 * np.pi * xyz @ rng.uniform(-1, 1, 3) / L)
+        out.append(np.exp(-d / (0.2 * L)) * mod + 1e-3)
+    return np.stack(out)
+
+
+@pytest.fixture(scope="module", params=["c1_cube64", "c4_cube128"])
+def big(request):
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
-    c = Case(S.config("c1_cube64"), solve=False)
+    c = Case(S.config(request.param), solve=False)
+    c.name = request.param
     c.lib = Q.qpat_mesh(c.xyz, c.tets)
     dev = torch.device("cuda")
     c.T = lambda a: torch.tensor(np.ascontiguousarray(a), device=dev)
-    phi, _ = Q.qpat_forward(c.lib, c.kappa, c.mu, c.flux)
-    c.phi = phi
+    c.phi = smooth_phi(c.xyz, c.K, c.cfg.L, 5)
+    # the bench's FP64 arm runs its K solves with Jacobi; the mixed arm the library default
+    c.prm = {0: Q.qpat_default_params(precision=0, poly_degree=0),
+             1: Q.qpat_default_params(precision=1, fp32_operator=1)}
     yield c
     c.lib.close()
 
@@ -48,15 +69,13 @@ def test_forward_residual_full_size(big, precision):
     dev = "cuda"
     phi = torch.empty((big.K, big.N), dtype=torch.float64, device=dev)
     h = torch.empty_like(phi)
-    Q.qpat_forward_dev(big.lib, big.T(big.kappa), big.T(big.mu), big.T(big.flux), phi, h,
-                       Q.qpat_default_params(precision=precision))
+    Q.qpat_forward_dev(big.lib, big.T(big.kappa), big.T(big.mu), big.T(big.flux), phi, h, big.prm[precision])
     torch.cuda.synchronize()
     ph = phi.cpu().numpy()
     for k in range(big.K):
         f = O.load_vector(big.om, big.flux[k])
         assert np.linalg.norm(big.Kmat @ ph[k] - f) / np.linalg.norm(f) < 1e-12
     np.testing.assert_allclose(h.cpu().numpy(), big.mu * ph, rtol=1e-15)
-    assert rel(ph, big.phi) < 1e-10
 
 
 def test_jvp_solve_residual_full_size(big):
@@ -64,10 +83,10 @@ def test_jvp_solve_residual_full_size(big):
     s = 0.1 * rng.standard_normal(2 * big.N)
     N = big.N
     out = torch.empty((big.K, N), dtype=torch.float64, device="cuda")
-    Q.qpat_jvp_dev(big.lib, big.T(big.kappa), big.T(big.mu), big.T(big.phi), None, big.T(s), out)
+    Q.qpat_jvp_dev(big.lib, big.T(big.kappa), big.T(big.mu), big.T(big.phi), None, big.T(s), out, big.prm[0])
     torch.cuda.synchronize()
     Js = out.cpu().numpy()
-    for k in range(big.K):
+    for k in sorted({0, big.K - 1}):
         x = (Js[k] - big.phi[k] * big.mu * s[N:]) / big.mu
         rhs = (O.G1_matrix(big.om, big.phi[k]) @ (big.kappa * s[:N])
                + O.G2_matrix(big.om, big.phi[k]) @ (big.mu * s[N:]))
@@ -84,7 +103,7 @@ def test_pair_adjoint_identity_full_size(big, precision):
     oj = torch.empty((big.K, N), dtype=torch.float64, device="cuda")
     ov = torch.empty(2 * N, dtype=torch.float64, device="cuda")
     Q.qpat_jvp_vjp_pair_dev(big.lib, big.T(big.kappa), big.T(big.mu), big.T(big.phi), big.T(w), big.T(s), big.T(t),
-                            oj, ov, Q.qpat_default_params(precision=precision))
+                            oj, ov, big.prm[precision])
     torch.cuda.synchronize()
     a = float(np.sum(oj.cpu().numpy() * t))
     b = float(s @ ov.cpu().numpy())
@@ -119,4 +138,4 @@ def test_prior_solve_full_size(big, deg):
     if len(big.prior_x) == 2:
         (x0, it0), (x2, it2) = big.prior_x[0], big.prior_x[2]
         assert rel(x2, x0) < 1e-8
-        assert it2 < 0.7 * it0   # the patch-local polynomial roughly halves the count (1400 -> 710)
+        assert it2 < 0.7 * it0   # the patch-local polynomial roughly halves the count (64^3: 1400 -> 680)

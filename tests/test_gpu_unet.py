@@ -208,3 +208,31 @@ def test_whole_network_gradient_matches_oracle():
     assert abs(loss_g - loss_o) <= 2e-2 * loss_o
     assert whole < 5e-2 and cos > 0.995
     assert max(per_layer) < 2.5e-1
+
+
+def test_log_output_mode():
+    """qpat_unet_set_log_output: the prediction is the exponential of the
+    network output (the same output as without the mode), and training in
+    log space lowers the loss on a field spanning several decades; a
+    negative floor is refused."""
+    _need()
+    n = 32
+    net = Q.UNet(n, seed=7)
+    try:
+        rng = np.random.default_rng(8)
+        x = torch.tensor(rng.normal(0, 0.3, (1, n ** 3, 3)).astype(np.float32), device="cuda")
+        y0 = torch.empty((1, n ** 3), dtype=torch.float32, device="cuda")
+        y1 = torch.empty_like(y0)
+        net.predict(x, y0)
+        net.set_log_output(1e-6)
+        net.predict(x, y1)
+        torch.cuda.synchronize()
+        np.testing.assert_allclose(y1.cpu().numpy(), np.exp(y0.cpu().numpy()), rtol=1e-5)
+        z = np.arange(n ** 3) // (n * n)
+        t = torch.tensor(np.exp(-z / 4.0)[None].astype(np.float32), device="cuda")   # 8 decades
+        losses = [net.train_step(x, t, 3e-3) for _ in range(60)]
+        assert losses[-1] < 0.3 * losses[0]
+        with pytest.raises(Q.QpatError):
+            net.set_log_output(-1.0)
+    finally:
+        net.close()
