@@ -153,6 +153,7 @@ __device__ __forceinline__ void dinv_vec(const T* invdiag, int g, int r0, T (&d)
 // issue slots bound the assembled FP64 solves on GB300).
 constexpr int kChunk = 8;
 constexpr int kChunkPrior = 7;
+constexpr int kChunkK64 = 15;  // FP64 K rows: one chunk of 15 (no multiply-add on padding)
 constexpr int kUnroll = 2;  // touched nodes a thread stages at once
 //
 // kLocal: only the couplings among the patch's owned nodes (local column ids
@@ -161,7 +162,7 @@ template <typename T, int R, int VW, int OP, bool kLocal = false>
 __device__ __forceinline__ void sell_row(const MeshDev& m, const OpParams<T>& op, const T* xs, int g, int r0,
                                          T (&acc)[VW], int nloc = 0) {
     constexpr int NL = OP == OP_CSR2 ? VW : 1;  // distinct value sets this thread reads
-    constexpr int CH = OP == OP_CSR2 ? kChunkPrior : kChunk;
+    constexpr int CH = OP == OP_CSR2 ? kChunkPrior : (sizeof(T) == 8 ? kChunkK64 : kChunk);
     const int64_t base = m.sell_ptr[g >> 5] * 32 + (g & 31);
     const int len = m.sell_len[g];
     const T* vp[NL];
