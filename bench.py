@@ -1110,9 +1110,10 @@ def illumination_study(Q, n: int = 38, seed: int = 17):
 
 
 def learned_leg(Q, torch, n: int = 32, train_phantoms: int = 18, steps: int = 150):
-    """Learned initial guess: the BF16 U-Net trained on the library's own
-    FP32 + refinement forward solves of `train_phantoms` seeded phantoms on an
-    n^3 cube (1 illumination each), then FP64 forward solves of held-out
+    """Learned initial guess: the BF16 U-Net (log-fluence output) trained on
+    the library's own FP32 + refinement forward solves of `train_phantoms`
+    seeded phantoms on an n^3 cube (1 illumination each), then FP64 forward
+    solves of held-out
     phantoms from zero and from the network's guess, both to the same
     tolerance: PCG iterations, device time (CUDA events) and the difference
     of the two solutions."""
@@ -1121,6 +1122,7 @@ def learned_leg(Q, torch, n: int = 32, train_phantoms: int = 18, steps: int = 15
     xyz, tets = cfgs[0].mesh()
     mesh = Q.qpat_mesh(xyz, tets)
     net = Q.UNet(n, seed=1)
+    net.set_log_output(1e-6)   # learn log(phi): the field spans decades
     try:
         X, T = [], []
         for cfg in cfgs[:train_phantoms]:
@@ -1170,7 +1172,7 @@ def learned_leg(Q, torch, n: int = 32, train_phantoms: int = 18, steps: int = 15
 
 
 def learned_study(Q, torch, workload: str = "c4_cube128", phantoms: int = 48, held_out: int = 2,
-                  steps: int = 600, batch: int = 2, lr: float = 2e-3, log_floor: float = 0.0):
+                  steps: int = 600, batch: int = 2, lr: float = 2e-3, log_floor: float = 1e-6):
     """Config 4's learned initial guess at full size: the BF16 U-Net (4
     levels, 16 base channels) trained on the library's own FP32 + refinement
     forward solves of `phantoms` seeded log-normal blob fields x 8
@@ -1366,7 +1368,7 @@ def main():
     ap.add_argument("--study-patch-nodes", type=int, default=1024)
     ap.add_argument("--study-phantoms", type=int, default=48)
     ap.add_argument("--study-steps", type=int, default=600)
-    ap.add_argument("--study-log-floor", type=float, default=0.0,
+    ap.add_argument("--study-log-floor", type=float, default=1e-6,
                     help="> 0: the network learns log(max(phi, floor)) (qpat_unet_set_log_output)")
     args = ap.parse_args()
     if args.warmup < 3:
