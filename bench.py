@@ -526,8 +526,13 @@ def setup_problem(Q, torch, workload: str, patch_nodes: int = 0):
     d["oj"] = torch.empty((cfg.K, mesh.N), dtype=torch.float64, device=dev)
     d["ov"] = torch.empty(2 * mesh.N, dtype=torch.float64, device=dev)
     d["op"] = torch.empty(2 * mesh.N, dtype=torch.float64, device=dev)
-    d["host"] = {k: np.ascontiguousarray(d[k].cpu().numpy()) for k in
-                 ("kappa", "mu", "phi", "w", "s", "t", "kt", "mt", "prior_rhs")}
+    # host copies of the inputs and host outputs in pinned memory (the e2e leg
+    # copies them in and out every step)
+    pin = lambda t: t.cpu().pin_memory().numpy()
+    d["host"] = {k: pin(d[k]) for k in ("kappa", "mu", "phi", "w", "s", "t", "kt", "mt", "prior_rhs")}
+    d["host"]["oj"] = pin(torch.empty((cfg.K, mesh.N), dtype=torch.float64))
+    d["host"]["ov"] = pin(torch.empty(2 * mesh.N, dtype=torch.float64))
+    d["host"]["op"] = pin(torch.empty(2 * mesh.N, dtype=torch.float64))
     return d
 
 
@@ -706,12 +711,14 @@ def run_ours(args):
     # ---- end to end through the host-pointer ABI (copies inside the timed region)
     H = d["host"]
     e2e_steps = max(1, min(args.steps, 5))
-    Q.qpat_jvp_vjp_pair(mesh, H["kappa"], H["mu"], H["phi"], H["s"], H["t"], H["w"], prm)   # sizes staging
-    Q.qpat_prior_solve(mesh, H["kt"], H["mt"], H["prior_rhs"], prm)
+    def e2e_step():
+        Q.qpat_jvp_vjp_pair(mesh, H["kappa"], H["mu"], H["phi"], H["s"], H["t"], H["w"], prm,
+                            out_jv=H["oj"], out_vjp=H["ov"])
+        Q.qpat_prior_solve(mesh, H["kt"], H["mt"], H["prior_rhs"], prm, out=H["op"])
+    e2e_step()                                   # sizes the staging buffers
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
-        Q.qpat_jvp_vjp_pair(mesh, H["kappa"], H["mu"], H["phi"], H["s"], H["t"], H["w"], prm)
-        Q.qpat_prior_solve(mesh, H["kt"], H["mt"], H["prior_rhs"], prm)
+        e2e_step()
     e2e_s = time.perf_counter() - t0
     h2d = 8 * ((N + N + K * N + K * N + 2 * N + K * N) + (N + N + 2 * N))
     d2h = 8 * (K * N + 2 * N + 2 * N)

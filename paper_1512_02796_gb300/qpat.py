@@ -486,22 +486,29 @@ def qpat_vjp(mesh: Mesh, kappa, mu, phi, t, w=None, params: Optional[qpat_params
     return out
 
 
-def qpat_jvp_vjp_pair(mesh: Mesh, kappa, mu, phi, s, t, w=None, params: Optional[qpat_params] = None):
+def qpat_jvp_vjp_pair(mesh: Mesh, kappa, mu, phi, s, t, w=None, params: Optional[qpat_params] = None,
+                      out_jv=None, out_vjp=None):
     """One J s and one J^T t (host arrays) as a single 2K-RHS block solve;
-    returns (w o J s (K x N), J^T (w o t) (2N))."""
+    returns (w o J s (K x N), J^T (w o t) (2N)), written into out_jv / out_vjp
+    when given (contiguous float64 host arrays, e.g. pinned)."""
     phi = _f64(np.atleast_2d(phi))
     K = phi.shape[0]
     t = _f64(np.broadcast_to(t, phi.shape))
     w = None if w is None else _f64(np.broadcast_to(w, phi.shape))
-    oj = np.empty((K, mesh.N))
-    ov = np.empty(2 * mesh.N)
+    oj = np.empty((K, mesh.N)) if out_jv is None else out_jv
+    ov = np.empty(2 * mesh.N) if out_vjp is None else out_vjp
+    if oj.shape != (K, mesh.N) or ov.shape != (2 * mesh.N,) or oj.dtype != np.float64 or ov.dtype != np.float64 \
+            or not (oj.flags.c_contiguous and ov.flags.c_contiguous and oj.flags.writeable and ov.flags.writeable):
+        raise ValueError("qpat_jvp_vjp_pair: out_jv must be K x N and out_vjp 2N contiguous float64")
     _check(load().qpat_jvp_vjp_pair(mesh.handle, _pp(params), _dp(_f64(kappa)), _dp(_f64(mu)), K, _dp(phi), _dp(w),
                                     _dp(_f64(s)), _dp(t), _dp(oj), _dp(ov)))
     return oj, ov
 
 
-def qpat_prior_solve(mesh: Mesh, kt, mt, rhs, params: Optional[qpat_params] = None):
-    out = np.empty(2 * mesh.N)
+def qpat_prior_solve(mesh: Mesh, kt, mt, rhs, params: Optional[qpat_params] = None, out=None):
+    out = np.empty(2 * mesh.N) if out is None else out
+    if out.shape != (2 * mesh.N,) or out.dtype != np.float64 or not (out.flags.c_contiguous and out.flags.writeable):
+        raise ValueError("qpat_prior_solve: out must be a contiguous float64 array of 2N")
     _check(load().qpat_prior_solve(mesh.handle, _pp(params), _dp(_f64(kt)), _dp(_f64(mt)), _dp(_f64(rhs)),
                                    _dp(out)))
     return out

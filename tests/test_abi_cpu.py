@@ -145,3 +145,24 @@ def test_params_struct_layout_matches_the_header():
     assert all(b == 0xAB for b in buf[n:])
     p = Q.qpat_default_params()
     assert p.lsqr_reorth == 1 and p.barrier_spin_limit == 0
+
+
+def test_host_output_arrays_are_checked_before_any_call():
+    """Caller-supplied host outputs (e.g. pinned buffers) must be contiguous,
+    writable float64 of the right shape; the binding refuses others before it
+    reaches the library."""
+    import types
+    m = types.SimpleNamespace(N=4, handle=None)
+    x = np.zeros(4)
+    for bad in (np.empty(7), np.empty(8, dtype=np.float32), np.empty(16)[::2]):
+        with pytest.raises(ValueError):
+            Q.qpat_prior_solve(m, x, x, np.zeros(8), out=bad)
+    ro = np.empty(8)
+    ro.flags.writeable = False
+    with pytest.raises(ValueError):
+        Q.qpat_prior_solve(m, x, x, np.zeros(8), out=ro)
+    phi = np.ones((2, 4))
+    with pytest.raises(ValueError):
+        Q.qpat_jvp_vjp_pair(m, x, x, phi, np.zeros(8), phi, None, out_jv=np.empty((3, 4)), out_vjp=np.empty(8))
+    with pytest.raises(ValueError):
+        Q.qpat_jvp_vjp_pair(m, x, x, phi, np.zeros(8), phi, None, out_jv=np.empty((2, 4)), out_vjp=np.empty(4))
