@@ -125,6 +125,32 @@ typedef struct {
                               PCG kernels: polls (each ~32 ns of sleep) before a
                               waiting CTA gives up with QPAT_ETIMEOUT;
                               0 = library default (about 2 s). */
+    int multigrid;         /* preconditioner of the K and M_delta solves (not in the
+                              paper, which prescribes no linear solver; every choice
+                              reaches the same pcg_rtol):
+                              0 = the persistent PCG above (poly_degree,
+                              prior_poly_degree);
+                              1 = conjugate gradients with one V-cycle of
+                              smoothed-aggregation algebraic multigrid per
+                              iteration (Vanek, Mandel, Brezina 1996: aggregates
+                              of the matrix graph, P = (I - 4/(3 hi) D^-1 A) P_tent,
+                              Galerkin coarse operators P^T A P, Chebyshev
+                              smoothing in D^-1 A, an exact dense solve on the
+                              coarsest level of <= 128 rows), all in FP64; the K
+                              solves then run FP64 iterates whatever `precision`
+                              says;
+                              2 = as 1 with the V-cycle of the K solves in FP32
+                              (the CG iterates stay FP64 and take the flexible
+                              beta = r.(z - z_old) / (r.z)_old); M_delta keeps the
+                              FP64 cycle.
+                              The hierarchy's patterns are built on the host on the
+                              first such solve of a mesh (seconds at 2 M nodes),
+                              its values on the device once per prepared operator. */
+    int mg_degree;         /* Chebyshev degree of each multigrid smoothing, 1..8
+                              (0 = 2) */
+    double mg_ratio;       /* the smoothing polynomial targets [hi / mg_ratio, hi] of
+                              the spectrum of D^-1 A, hi its Gershgorin bound
+                              (> 1; 0 = 30) */
 } qpat_params;
 
 /* Report of qpat_reconstruct (Algorithm 1). */
@@ -182,6 +208,17 @@ void qpat_mesh_free(qpat_mesh_t mesh);
 int qpat_mesh_host_info(const double* xyz, int64_t N, const int32_t* tets, int64_t E,
                         int patch_nodes, int64_t* info8, int32_t* faces, int32_t* perm);
 
+/* Host-only check (needs no GPU) of the multigrid hierarchy that
+ * qpat_params.multigrid builds for the K pattern (prior = 0) or the prior's
+ * pattern (prior = 1) of the mesh qpat_mesh_ex would prepare: builds the
+ * aggregates, the level patterns and the index plans of the device set-up
+ * and verifies every invariant the device relies on (P rows, R = P^T, the
+ * slots of A P and P^T A P, symmetric coarse patterns, a coarsest level of
+ * at most 128 rows).  Writes the rows of each level (finest first, up to
+ * max_levels) and returns the level count, or QPAT_EINVAL with a message. */
+int qpat_multigrid_host_info(const double* xyz, int64_t N, const int32_t* tets, int64_t E,
+                             int patch_nodes, int prior, int64_t* rows, int max_levels);
+
 /* Counters of the linear solves run with this mesh since creation or the
  * last reset: out4 = {PCG iterations, solves (RHS), FP64 refinement sweeps,
  * PCG launches}. */
@@ -196,6 +233,12 @@ int qpat_mesh_reset_stats(qpat_mesh_t mesh);
  * when one launch's shared memory cannot hold all its right-hand sides);
  * -1 for a NULL mesh.  Not in the paper (diagnostics). */
 int64_t qpat_mesh_rhs_iterations(qpat_mesh_t mesh);
+
+/* Rows of every level of the multigrid hierarchy built for the K pattern
+ * (prior = 0) or the prior's pattern (prior = 1), finest first, into rows
+ * (up to max_levels); returns the number of levels (0 before the first
+ * multigrid solve of that kind).  Not in the paper (diagnostics). */
+int qpat_mesh_multigrid_levels(qpat_mesh_t mesh, int prior, int64_t* rows, int max_levels);
 
 /* When on, every PCG launch is bracketed by CUDA events recorded on the
  * stream it is launched on; qpat_mesh_pcg_time returns the summed device

@@ -12,6 +12,7 @@
 #include <vector>
 
 #include "abi_internal.h"
+#include "amg.h"
 
 namespace qpat {
 
@@ -160,6 +161,11 @@ void k_jt_out_launch(int64_t N, int R, const double* kappa, const double* mu, co
 // Linear-solve drivers
 // --------------------------------------------------------------------------
 
+uint64_t next_op_stamp() {
+    static std::atomic<uint64_t> counter{0};
+    return counter.fetch_add(1, std::memory_order_relaxed) + 1;
+}
+
 // Operator state of one K(kappa, mu) or M_delta(kt, mt), library order.
 int prepare_K(qpat_mesh_s* M, const double* kap_l, const double* mu_l, OpState& st, cudaStream_t s,
               const char* tag) {
@@ -167,6 +173,7 @@ int prepare_K(qpat_mesh_s* M, const double* kap_l, const double* mu_l, OpState& 
     cudaError_t e = cudaSuccess;
     const std::string t(tag);
     st.kind = OP_K;
+    st.stamp = next_op_stamp();
     st.c1_64 = kap_l;
     st.c2_64 = mu_l;
     st.c1_32 = M->ws.get<float>(t + ".c1_32", N, s, &e);
@@ -193,6 +200,7 @@ int prepare_prior(qpat_mesh_s* M, const double* kt_l, const double* mt_l, double
     const int64_t N = M->h.N;
     cudaError_t e = cudaSuccess;
     st.kind = OP_PRIOR;
+    st.stamp = next_op_stamp();
     st.c1_64 = kt_l;
     st.c2_64 = mt_l;
     st.inv_T2 = 1.0 / (T * T);
@@ -245,6 +253,8 @@ int solve(qpat_mesh_s* M, const OpState& st, const SolveOpts& so_in, int R, cons
     // solve can resolve, so refinement would not contract.
     SolveOpts so = so_in;
     if (st.kind == OP_PRIOR) so.precision = 0;
+    // multigrid-preconditioned CG (FP64 iterates whatever the precision mode)
+    if (so.multigrid) return amg_solve(M, st, so, R, B, X, s, X0);
     // the prior's assembled blocks live in the stiffness-only pattern
     const MeshDev& md = st.kind == OP_PRIOR ? M->dp : M->d;
     const int64_t N = M->h.N;
@@ -576,6 +586,9 @@ void qpat_default_params(qpat_params* p) {
     p->poly_degree = 2;        // fastest measured on a 64^3 cube (GB300)
     p->prior_poly_degree = 2;
     p->lsqr_reorth = 1;        // exact-arithmetic LSQR iterates (see qpat.h)
+    p->multigrid = 0;
+    p->mg_degree = 2;
+    p->mg_ratio = 30.0;
 }
 
 static int mesh_create(const double* xyz, int64_t N, const int32_t* tets, int64_t E, int patch_nodes,
@@ -595,6 +608,20 @@ static int mesh_create(const double* xyz, int64_t N, const int32_t* tets, int64_
     }
     *out = M;
     return QPAT_OK;
+}
+
+int qpat_multigrid_host_info(const double* xyz, int64_t N, const int32_t* tets, int64_t E, int patch_nodes,
+                             int prior, int64_t* rows, int max_levels) {
+    if (max_levels < 0 || (max_levels > 0 && !rows)) return fail(QPAT_EINVAL, "qpat_multigrid_host_info: bad argument");
+    HostMesh h;
+    std::string msg = build_host_mesh(xyz, N, tets, E, patch_nodes, 0, h);
+    if (!msg.empty()) return fail(QPAT_EINVAL, msg);
+    const AmgPlan plan = amg_build_plan(amg_fine_pattern(h, prior ? 1 : 0));
+    msg = amg_check_plan(plan);
+    if (!msg.empty()) return fail(QPAT_EINVAL, "multigrid plan: " + msg);
+    const int L = int(plan.levels.size());
+    for (int l = 0; l < std::min(L, max_levels); ++l) rows[l] = plan.levels[size_t(l)].A.n;
+    return L;
 }
 
 int qpat_mesh_host_info(const double* xyz, int64_t N, const int32_t* tets, int64_t E, int patch_nodes,
@@ -749,6 +776,7 @@ void qpat_mesh_free(qpat_mesh_t M) {
     cudaGetDevice(&cur);
     cudaSetDevice(M->device);
     if (M->stream) cudaStreamSynchronize(M->stream);
+    qpat::amg_release(M);
     M->ws.release();
     if (M->ev0) cudaEventDestroy(M->ev0);
     if (M->ev1) cudaEventDestroy(M->ev1);
@@ -819,6 +847,11 @@ int qpat_mesh_stats(qpat_mesh_t M, int64_t* out4) {
 int64_t qpat_mesh_fp64_fallbacks(qpat_mesh_t M) { return M ? M->stats.fp64_fallbacks : -1; }
 
 int64_t qpat_mesh_rhs_iterations(qpat_mesh_t M) { return M ? M->stats.rhs_iters : -1; }
+
+int qpat_mesh_multigrid_levels(qpat_mesh_t M, int prior, int64_t* rows, int max_levels) {
+    if (!M || (max_levels > 0 && !rows) || max_levels < 0) return qpat::fail(QPAT_EINVAL, "qpat_mesh_multigrid_levels: bad argument");
+    return qpat::amg_levels(M, prior, rows, max_levels);
+}
 
 int qpat_mesh_reset_stats(qpat_mesh_t M) {
     if (!M) return fail(QPAT_EINVAL, "qpat_mesh_reset_stats: NULL mesh");

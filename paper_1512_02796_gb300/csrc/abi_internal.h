@@ -47,6 +47,7 @@ struct OpState {
     double* gbound = nullptr;       // Gershgorin bound of D^-1 A over the value sets (1 double)
     double* v64[2] = {nullptr, nullptr};  // assembled FP64 values (sliced ELLPACK)
     float* v32[2] = {nullptr, nullptr};   // FP32 copy (K only)
+    uint64_t stamp = 0;             // new for every preparation (keys values derived from the operator)
 };
 
 struct SolveOpts {
@@ -61,6 +62,9 @@ struct SolveOpts {
     int poly_k = 0;           // patch-local Chebyshev degree of the K preconditioner (0 Jacobi)
     int poly_prior = 0;       // the same for M_delta
     long long spin_limit = 0; // grid-barrier polls before a timeout (0 = default)
+    int multigrid = 0;        // 1: CG with the smoothed-aggregation V-cycle (FP64); 2: its K cycle in FP32
+    int mg_degree = 2;        // Chebyshev degree of each smoothing
+    double mg_ratio = 30.0;   // smoothing interval [hi / mg_ratio, hi] of D^-1 A
 };
 
 struct DeviceGuard {
@@ -75,6 +79,8 @@ struct DeviceGuard {
         if (cur != prev) cudaSetDevice(prev);
     }
 };
+
+struct AmgState;  // smoothed-aggregation hierarchy of a mesh (amg.cu)
 
 }  // namespace qpat
 
@@ -92,6 +98,7 @@ struct qpat_mesh_s {
     int timing = 0;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     double pcg_ms = 0.0;
+    qpat::AmgState* amg = nullptr;   // built on the first multigrid solve
 };
 
 namespace qpat {
@@ -112,6 +119,16 @@ int prepare_prior(qpat_mesh_s* M, const double* kt_l, const double* mt_l, double
 int solve(qpat_mesh_s* M, const OpState& st, const SolveOpts& so, int R, const double* B, double* X,
           cudaStream_t s, const double* X0 = nullptr);
 cudaError_t launch_add(int64_t n, const double* a, double* y, cudaStream_t s);  // y += a
+uint64_t next_op_stamp();
+// CG with one smoothed-aggregation V-cycle per iteration as the
+// preconditioner (amg.cu); X0 as in solve().  The hierarchy's patterns are
+// built on the first call per mesh and matrix pattern, its values once per
+// prepared operator.
+int amg_solve(qpat_mesh_s* M, const OpState& st, const SolveOpts& so, int R, const double* B, double* X,
+              cudaStream_t s, const double* X0 = nullptr);
+// rows of each level of the hierarchy of the K (prior = 0) or prior pattern; returns the level count
+int amg_levels(qpat_mesh_s* M, int prior, int64_t* rows, int max_levels);
+void amg_release(qpat_mesh_s* M);
 SolveOpts solve_opts(const qpat_params* prm);
 
 // node-major caller layout (x[c*R + r], r < R) <-> library N x Rp (zero padding)

@@ -1,0 +1,1125 @@
+// Device side of the smoothed-aggregation multigrid preconditioner (see
+// amg.h): the numeric set-up of the hierarchy from the assembled FP64
+// operator, the V-cycle, and the conjugate-gradient driver that uses it.
+//
+// Layout: vectors are node-major with R right-hand sides interleaved
+// (x[i * R + r]), as everywhere in the library.  The K operator has one value
+// set for all right-hand sides; M_delta has two (its blocks, R = 2, column r
+// uses set r), and every level of its hierarchy keeps two sets over one
+// pattern.  All sums run in a fixed order: results are identical from run
+// to run.
+#include <algorithm>
+#include <array>
+#include <cmath>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <string>
+#include <type_traits>
+#include <vector>
+
+#include "abi_internal.h"
+#include "amg.h"
+
+namespace qpat {
+
+struct SellDev {
+    int64_t n = 0;
+    const int64_t* ptr = nullptr;
+    const int32_t* col = nullptr;
+    const uint16_t* len = nullptr;
+    int64_t entries = 0;
+    int maxlen = 0;
+};
+
+struct LevelDev {
+    SellDev A;
+    const int32_t* diag = nullptr;
+    int64_t nc = 0;
+    SellDev P;
+    const uint16_t* a2p = nullptr;
+    const uint16_t* pself = nullptr;
+    const int64_t* ap_ptr = nullptr;
+    const int32_t* ap_col = nullptr;
+    const int64_t* ap_sptr = nullptr;
+    const uint16_t* ap_slot = nullptr;
+    int64_t ap_nnz = 0;
+    SellDev R;
+    const int64_t* r_src = nullptr;
+    const int64_t* g_ptr = nullptr;
+    const uint16_t* g_slot = nullptr;
+};
+
+namespace {
+
+__device__ __forceinline__ int64_t spos(const SellDev& S, int64_t row, int k) {
+    return (S.ptr[row >> 5] + k) * 32 + (row & 31);
+}
+
+// ---------------------------------------------------------------- set-up kernels
+
+// Inverse diagonal (n x NV, interleaved) and the Gershgorin bound
+// max_i sum_j |a_ij| / a_ii of D^-1 A per value set (hi must start at 0; the
+// bound is >= 1, so the bits of the positive doubles order like integers).
+template <int NV>
+__global__ void k_dinv_hi(SellDev A, const int32_t* diag, const double* v0, const double* v1, double* dinv,
+                          double* hi) {
+    const int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+    if (i >= A.n) return;
+    const int L = A.len[i];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+        const double* val = v == 0 ? v0 : v1;
+        double s = 0.0;
+        for (int k = 0; k < L; ++k) s += fabs(val[spos(A, i, k)]);
+        const double d = val[spos(A, i, diag[i])];
+        dinv[i * NV + v] = 1.0 / d;
+        const double ratio = s / fabs(d);
+        atomicMax(reinterpret_cast<unsigned long long*>(hi + v), __double_as_longlong(ratio));
+    }
+}
+
+// P = (I - omega D^-1 A) P_tent, omega = 4 / (3 hi): row i of P from row i of A.
+template <int NV>
+__global__ void k_prolong(SellDev A, SellDev P, const uint16_t* a2p, const uint16_t* pself, const double* v0,
+                          const double* v1, const double* dinv, const double* hi, double* p0, double* p1) {
+    const int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+    if (i >= A.n) return;
+    const int L = A.len[i], LP = P.len[i];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+        const double* val = v == 0 ? v0 : v1;
+        double* pv = v == 0 ? p0 : p1;
+        const double w = (4.0 / 3.0) / hi[v] * dinv[i * NV + v];
+        for (int k = 0; k < LP; ++k) pv[spos(P, i, k)] = 0.0;
+        pv[spos(P, i, pself[i])] = 1.0;
+        for (int k = 0; k < L; ++k) {
+            const int64_t at = spos(A, i, k);
+            pv[spos(P, i, a2p[at])] -= w * val[at];
+        }
+    }
+}
+
+// Row i of A P = sum over the entries a_ij of row i of A of a_ij (row j of P).
+template <int NV>
+__global__ void k_ap(SellDev A, SellDev P, const int64_t* ap_ptr, const int64_t* ap_sptr, const uint16_t* ap_slot,
+                     int64_t ap_nnz, const double* v0, const double* v1, const double* p0, const double* p1,
+                     double* ap) {
+    const int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+    if (i >= A.n) return;
+    const int L = A.len[i];
+    const int64_t b = ap_ptr[i], e = ap_ptr[i + 1];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+        const double* val = v == 0 ? v0 : v1;
+        const double* pv = v == 0 ? p0 : p1;
+        double* out = ap + v * ap_nnz;
+        for (int64_t t = b; t < e; ++t) out[t] = 0.0;
+        int64_t o = ap_sptr[i];
+        for (int k = 0; k < L; ++k) {
+            const int64_t at = spos(A, i, k);
+            const int64_t j = A.col[at];
+            const double a = val[at];
+            const int LPj = P.len[j];
+            for (int kk = 0; kk < LPj; ++kk) out[b + ap_slot[o++]] += a * pv[spos(P, j, kk)];
+        }
+    }
+}
+
+// R = P^T values gathered from P (padding 0).
+template <int NV>
+__global__ void k_rvals(int64_t entries, const int64_t* r_src, const double* p0, const double* p1, double* r0,
+                        double* r1) {
+    const int64_t e = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+    if (e >= entries) return;
+    const int64_t s = r_src[e];
+    r0[e] = s >= 0 ? p0[s] : 0.0;
+    if (NV == 2) r1[e] = s >= 0 ? p1[s] : 0.0;
+}
+
+// Coarse row I of P^T (A P), one warp per row and value set: the R entries
+// (fine rows i, ascending) are taken one after the other and the lanes add
+// the entries of row i of A P into the row's shared accumulator; within one
+// fine row the columns differ, so no two lanes meet on a slot and every
+// coarse value is summed in the same order on every run.
+template <int NV>
+__global__ void k_galerkin(SellDev R, SellDev C, const int64_t* r_src, const int64_t* ap_ptr, const int64_t* g_ptr,
+                           const uint16_t* g_slot, int64_t ap_nnz, const double* p0, const double* p1,
+                           const double* ap, double* c0, double* c1) {
+    extern __shared__ double acc_all[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int wpb = blockDim.x >> 5;
+    const int64_t task = blockIdx.x * int64_t(wpb) + warp;
+    if (task >= C.n * NV) return;
+    const int64_t I = task / NV;
+    const int v = int(task % NV);
+    double* acc = acc_all + int64_t(warp) * C.maxlen;
+    const double* pv = v == 0 ? p0 : p1;
+    const double* apv = ap + v * ap_nnz;
+    double* out = v == 0 ? c0 : c1;
+    const int LC = C.len[I], LR = R.len[I];
+    for (int k = lane; k < LC; k += 32) acc[k] = 0.0;
+    __syncwarp();
+    int64_t o = g_ptr[I];
+    for (int k = 0; k < LR; ++k) {
+        const int64_t at = spos(R, I, k);
+        const int64_t i = R.col[at];
+        const double p = pv[r_src[at]];
+        const int64_t b = ap_ptr[i], cnt = ap_ptr[i + 1] - b;
+        for (int64_t t = lane; t < cnt; t += 32) acc[g_slot[o + t]] += p * apv[b + t];
+        o += cnt;
+        __syncwarp();
+    }
+    for (int k = lane; k < LC; k += 32) out[spos(C, I, k)] = acc[k];
+}
+
+// In-place Gauss-Jordan inversion of the (symmetric positive definite)
+// coarsest operator, one CTA per value set, without pivoting: the pivots of
+// an SPD matrix are its positive Schur complements.
+template <int NV>
+__global__ void k_dense_inv(SellDev A, const double* v0, const double* v1, double* inv) {
+    extern __shared__ double a[];
+    const int n = int(A.n);
+    const int v = blockIdx.x;
+    const double* val = v == 0 ? v0 : v1;
+    double* fcol = a + n * n;
+    for (int t = threadIdx.x; t < n * n; t += blockDim.x) a[t] = 0.0;
+    __syncthreads();
+    for (int i = threadIdx.x; i < n; i += blockDim.x)
+        for (int k = 0; k < A.len[i]; ++k) {
+            const int64_t at = spos(A, i, k);
+            a[i * n + A.col[at]] += val[at];
+        }
+    __syncthreads();
+    for (int k = 0; k < n; ++k) {
+        const double rp = 1.0 / a[k * n + k];
+        __syncthreads();
+        for (int j = threadIdx.x; j < n; j += blockDim.x) a[k * n + j] = j == k ? rp : a[k * n + j] * rp;
+        for (int i = threadIdx.x; i < n; i += blockDim.x) fcol[i] = a[i * n + k];
+        __syncthreads();
+        for (int t = threadIdx.x; t < n * n; t += blockDim.x) {
+            const int i = t / n, j = t % n;
+            if (i == k) continue;
+            a[t] = j == k ? -fcol[i] * a[k * n + k] : a[t] - fcol[i] * a[k * n + j];
+        }
+        __syncthreads();
+    }
+    for (int t = threadIdx.x; t < n * n; t += blockDim.x) inv[int64_t(v) * n * n + t] = a[t];
+}
+
+__global__ void k_d2f(int64_t n, const double* in, float* out) {
+    const int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+    if (i < n) out[i] = float(in[i]);
+}
+
+}  // namespace
+
+namespace {
+
+// ---------------------------------------------------------------- solve kernels
+
+constexpr int kRedMaxGrid = 1024;  // blocks of the reducing vector kernels
+
+template <typename T, int R>
+__device__ __forceinline__ void ldR(const T* p, T* v) {
+    if constexpr (std::is_same<T, double>::value && R % 2 == 0) {
+#pragma unroll
+        for (int r = 0; r < R; r += 2) {
+            const double2 t = *reinterpret_cast<const double2*>(p + r);
+            v[r] = t.x;
+            v[r + 1] = t.y;
+        }
+    } else if constexpr (std::is_same<T, float>::value && R % 4 == 0) {
+#pragma unroll
+        for (int r = 0; r < R; r += 4) {
+            const float4 t = *reinterpret_cast<const float4*>(p + r);
+            v[r] = t.x;
+            v[r + 1] = t.y;
+            v[r + 2] = t.z;
+            v[r + 3] = t.w;
+        }
+    } else if constexpr (std::is_same<T, float>::value && R == 2) {
+        const float2 t = *reinterpret_cast<const float2*>(p);
+        v[0] = t.x;
+        v[1] = t.y;
+    } else {
+#pragma unroll
+        for (int r = 0; r < R; ++r) v[r] = p[r];
+    }
+}
+
+template <typename T, int R>
+__device__ __forceinline__ void stR(T* p, const T* v) {
+    if constexpr (std::is_same<T, double>::value && R % 2 == 0) {
+#pragma unroll
+        for (int r = 0; r < R; r += 2) *reinterpret_cast<double2*>(p + r) = make_double2(v[r], v[r + 1]);
+    } else if constexpr (std::is_same<T, float>::value && R % 4 == 0) {
+#pragma unroll
+        for (int r = 0; r < R; r += 4) *reinterpret_cast<float4*>(p + r) = make_float4(v[r], v[r + 1], v[r + 2], v[r + 3]);
+    } else {
+#pragma unroll
+        for (int r = 0; r < R; ++r) p[r] = v[r];
+    }
+}
+
+// acc = (A x)_i for the R columns of row i (NV = 2: column r uses value set r).
+template <typename T, int R, int NV>
+__device__ __forceinline__ void row_apply(const SellDev& A, const T* v0, const T* v1, const T* x, int64_t i, T* acc) {
+#pragma unroll
+    for (int r = 0; r < R; ++r) acc[r] = T(0);
+    const int L = A.len[i];
+    int64_t at = A.ptr[i >> 5] * 32 + (i & 31);
+    for (int k = 0; k < L; ++k, at += 32) {
+        const int64_t c = A.col[at];
+        T xv[R];
+        ldR<T, R>(x + c * R, xv);
+        if constexpr (NV == 1) {
+            const T a = v0[at];
+#pragma unroll
+            for (int r = 0; r < R; ++r) acc[r] = fma(a, xv[r], acc[r]);
+        } else {
+            acc[0] = fma(v0[at], xv[0], acc[0]);
+            acc[1] = fma(v1[at], xv[1], acc[1]);
+        }
+    }
+}
+
+// MODE 0: y = A x;  1: y = b - A x;  2: y = b + A x (b may be y).
+template <typename T, int R, int NV, int MODE>
+__global__ void __launch_bounds__(256) k_spmv(SellDev A, const T* v0, const T* v1, const T* x, const T* b, T* y) {
+    const int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+    if (i >= A.n) return;
+    T acc[R];
+    row_apply<T, R, NV>(A, v0, v1, x, i, acc);
+    if constexpr (MODE != 0) {
+        T bv[R];
+        ldR<T, R>(b + i * R, bv);
+#pragma unroll
+        for (int r = 0; r < R; ++r) acc[r] = MODE == 1 ? bv[r] - acc[r] : bv[r] + acc[r];
+    }
+    stR<T, R>(y + i * R, acc);
+}
+
+// Chebyshev smoothing step k (of a polynomial in D^-1 A on [hi / ratio, hi]):
+//   res = b - A x_in  (FIRST: x_in = 0, res = b),
+//   d = c_d d + c_r D^-1 res,  x_out = x_in + d,
+// with the coefficients of the three-term recurrence (Saad, Iterative
+// Methods for Sparse Linear Systems, Alg. 12.1): theta, delta the centre and
+// half-width of the interval, sigma = theta / delta, rho_0 = 1 / sigma,
+// rho_k = 1 / (2 sigma - rho_{k-1}); step 0: c_d = 0, c_r = 1 / theta;
+// step k: c_d = rho_k rho_{k-1}, c_r = 2 rho_k / delta.
+template <typename T, int R, int NV, bool FIRST>
+__global__ void __launch_bounds__(256) k_cheb(SellDev A, const T* v0, const T* v1, const T* dinv, const double* hi,
+                                              double ratio, int k, const T* x_in, T* x_out, T* d, const T* b) {
+    const int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+    if (i >= A.n) return;
+    T cd[NV], cr[NV];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+        const double h = hi[v], lo = h / ratio;
+        const double theta = 0.5 * (h + lo), delta = 0.5 * (h - lo), sigma = theta / delta;
+        double rho_prev = 1.0 / sigma, rho = rho_prev;
+        for (int j = 1; j <= k; ++j) {
+            rho_prev = rho;
+            rho = 1.0 / (2.0 * sigma - rho_prev);
+        }
+        cd[v] = k == 0 ? T(0) : T(rho * rho_prev);
+        cr[v] = k == 0 ? T(1.0 / theta) : T(2.0 * rho / delta);
+    }
+    T res[R], bv[R], dv[R], xv[R];
+    ldR<T, R>(b + i * R, bv);
+    if constexpr (FIRST) {
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            res[r] = bv[r];
+            xv[r] = T(0);
+        }
+    } else {
+        row_apply<T, R, NV>(A, v0, v1, x_in, i, res);
+        ldR<T, R>(x_in + i * R, xv);
+#pragma unroll
+        for (int r = 0; r < R; ++r) res[r] = bv[r] - res[r];
+    }
+    if (k > 0) ldR<T, R>(d + i * R, dv);
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const int v = NV == 2 ? r : 0;
+        const T di = dinv[i * NV + v];
+        const T upd = cr[v] * di * res[r];
+        dv[r] = k > 0 ? fma(cd[v], dv[r], upd) : upd;
+        xv[r] += dv[r];
+    }
+    stR<T, R>(d + i * R, dv);
+    stR<T, R>(x_out + i * R, xv);
+}
+
+// x = A^-1 b on the coarsest level (dense inverse, n <= kAmgCoarsest).
+template <typename T, int R, int NV>
+__global__ void k_dense_apply(int n, const T* inv, const T* b, T* x) {
+    for (int t = threadIdx.x; t < n * R; t += blockDim.x) {
+        const int i = t / R, r = t % R;
+        const T* row = inv + int64_t(NV == 2 ? r : 0) * n * n + int64_t(i) * n;
+        T s = T(0);
+        for (int j = 0; j < n; ++j) s = fma(row[j], b[j * R + r], s);
+        x[t] = s;
+    }
+}
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Block totals of Q per-thread values, in a fixed order, to part[blockIdx * Q + q].
+template <int Q>
+__device__ __forceinline__ void block_partials(double* v, double* part) {
+    __shared__ double red[8][Q];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+#pragma unroll
+    for (int q = 0; q < Q; ++q) {
+        const double t = warp_sum(v[q]);
+        if (lane == 0) red[warp][q] = t;
+    }
+    __syncthreads();
+    if (threadIdx.x < Q) {
+        double s = 0.0;
+        for (int w = 0; w < int(blockDim.x >> 5); ++w) s += red[w][threadIdx.x];
+        part[int64_t(blockIdx.x) * Q + threadIdx.x] = s;
+    }
+}
+
+// Total of quantity q over G block partials (a full warp calls it; every lane gets it).
+__device__ __forceinline__ double total_of(const double* part, int G, int Q, int q) {
+    double s = 0.0;
+    for (int g = threadIdx.x & 31; g < G; g += 32) s += part[int64_t(g) * Q + q];
+    return warp_sum(s);
+}
+
+// ---- conjugate gradients (FP64), R right-hand sides; ctl[0] status, ctl[1] RHS still running
+
+// x = 0, r = b, partials of b.b
+template <int R>
+__global__ void __launch_bounds__(256) k_cg_init(int64_t n, const double* b, double* x, double* r, double* part) {
+    double acc[R];
+#pragma unroll
+    for (int q = 0; q < R; ++q) acc[q] = 0.0;
+    for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x) {
+        double bv[R], z[R];
+        ldR<double, R>(b + i * R, bv);
+#pragma unroll
+        for (int q = 0; q < R; ++q) {
+            acc[q] = fma(bv[q], bv[q], acc[q]);
+            z[q] = 0.0;
+        }
+        stR<double, R>(r + i * R, bv);
+        stR<double, R>(x + i * R, z);
+    }
+    block_partials<R>(acc, part);
+}
+
+// x = x0, r = b - A x0, partials of b.b (the stopping target stays rtol |b|)
+template <int R, int NV>
+__global__ void __launch_bounds__(256) k_cg_init_x0(SellDev A, const double* v0, const double* v1, const double* b,
+                                                    const double* x0, double* x, double* r, double* part) {
+    double acc[R];
+#pragma unroll
+    for (int q = 0; q < R; ++q) acc[q] = 0.0;
+    for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < A.n; i += int64_t(gridDim.x) * blockDim.x) {
+        double bv[R], av[R], xv[R];
+        row_apply<double, R, NV>(A, v0, v1, x0, i, av);
+        ldR<double, R>(b + i * R, bv);
+        ldR<double, R>(x0 + i * R, xv);
+#pragma unroll
+        for (int q = 0; q < R; ++q) {
+            acc[q] = fma(bv[q], bv[q], acc[q]);
+            av[q] = bv[q] - av[q];
+        }
+        stR<double, R>(r + i * R, av);
+        stR<double, R>(x + i * R, xv);
+    }
+    block_partials<R>(acc, part);
+}
+
+// bb = totals; a right-hand side with b = 0 is solved by x = 0 and never runs
+template <int R>
+__global__ void k_cg_start(const double* part, int G, double* bb, int* active, int* ctl) {
+    const int r = threadIdx.x >> 5;
+    const double t = total_of(part, G, R, r);
+    if ((threadIdx.x & 31) == 0) {
+        bb[r] = t;
+        active[r] = t > 0.0 ? 1 : 0;
+        if (!isfinite(t)) atomicExch(ctl, int(QPAT_EINVAL));
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int c = 0;
+        for (int q = 0; q < R; ++q) c += active[q];
+        ctl[1] = c;
+    }
+}
+
+// q = A p and partials of p.q
+template <int R, int NV>
+__global__ void __launch_bounds__(256) k_cg_apply(SellDev A, const double* v0, const double* v1, const double* p,
+                                                  double* q, double* part) {
+    double acc[R];
+#pragma unroll
+    for (int t = 0; t < R; ++t) acc[t] = 0.0;
+    for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < A.n; i += int64_t(gridDim.x) * blockDim.x) {
+        double qv[R], pv[R];
+        row_apply<double, R, NV>(A, v0, v1, p, i, qv);
+        ldR<double, R>(p + i * R, pv);
+#pragma unroll
+        for (int t = 0; t < R; ++t) acc[t] = fma(pv[t], qv[t], acc[t]);
+        stR<double, R>(q + i * R, qv);
+    }
+    block_partials<R>(acc, part);
+}
+
+// alpha = r.z / p.q on the running right-hand sides (0 on the others)
+template <int R>
+__global__ void k_cg_alpha(const double* part, int G, const double* rz, const int* active, double* alpha, int* ctl) {
+    const int r = threadIdx.x >> 5;
+    const double pq = total_of(part, G, R, r);
+    if ((threadIdx.x & 31) == 0) {
+        double a = 0.0;
+        if (active[r]) {
+            if (!(pq > 0.0) || !isfinite(pq) || !isfinite(rz[r]))
+                atomicExch(ctl, int(QPAT_EBREAKDOWN));
+            else
+                a = rz[r] / pq;
+        }
+        alpha[r] = a;
+    }
+}
+
+// x += alpha p, r -= alpha q, partials of r.r
+template <int R>
+__global__ void __launch_bounds__(256) k_cg_update(int64_t n, const double* alpha, const double* p, const double* q,
+                                                   double* x, double* r, double* part) {
+    double al[R], acc[R];
+#pragma unroll
+    for (int t = 0; t < R; ++t) {
+        al[t] = alpha[t];
+        acc[t] = 0.0;
+    }
+    for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x) {
+        double pv[R], qv[R], xv[R], rv[R];
+        ldR<double, R>(p + i * R, pv);
+        ldR<double, R>(q + i * R, qv);
+        ldR<double, R>(x + i * R, xv);
+        ldR<double, R>(r + i * R, rv);
+#pragma unroll
+        for (int t = 0; t < R; ++t) {
+            xv[t] = fma(al[t], pv[t], xv[t]);
+            rv[t] = fma(-al[t], qv[t], rv[t]);
+            acc[t] = fma(rv[t], rv[t], acc[t]);
+        }
+        stR<double, R>(x + i * R, xv);
+        stR<double, R>(r + i * R, rv);
+    }
+    block_partials<R>(acc, part);
+}
+
+// a right-hand side stops once |r| <= rtol |b|
+template <int R>
+__global__ void k_cg_check(const double* part, int G, const double* bb, double rtol2, int* active, double* rr,
+                           int* ctl) {
+    const int r = threadIdx.x >> 5;
+    const double t = total_of(part, G, R, r);
+    if ((threadIdx.x & 31) == 0) {
+        rr[r] = t;
+        if (!isfinite(t)) atomicExch(ctl, int(QPAT_EBREAKDOWN));
+        if (active[r] && t <= rtol2 * bb[r]) active[r] = 0;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int c = 0;
+        for (int q = 0; q < R; ++q) c += active[q];
+        ctl[1] = c;
+    }
+}
+
+// partials of r.z (and, FLEX, of r.z_old)
+template <int R, bool FLEX>
+__global__ void __launch_bounds__(256) k_cg_dots(int64_t n, const double* r, const double* z, const double* zo,
+                                                 double* part) {
+    constexpr int Q = FLEX ? 2 * R : R;
+    double acc[Q];
+#pragma unroll
+    for (int t = 0; t < Q; ++t) acc[t] = 0.0;
+    for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x) {
+        double rv[R], zv[R];
+        ldR<double, R>(r + i * R, rv);
+        ldR<double, R>(z + i * R, zv);
+#pragma unroll
+        for (int t = 0; t < R; ++t) acc[t] = fma(rv[t], zv[t], acc[t]);
+        if constexpr (FLEX) {
+            ldR<double, R>(zo + i * R, zv);
+#pragma unroll
+            for (int t = 0; t < R; ++t) acc[R + t] = fma(rv[t], zv[t], acc[R + t]);
+        }
+    }
+    block_partials<Q>(acc, part);
+}
+
+// beta = r.z / (r.z)_old (FLEX: (r.z - r.z_old) / (r.z)_old, the form that
+// tolerates a preconditioner that varies slightly between applications);
+// FIRST: beta = 0.  rz <- r.z.
+template <int R, bool FLEX>
+__global__ void k_cg_beta(const double* part, int G, int first, double* rz, const int* active, double* beta,
+                          int* ctl) {
+    constexpr int Q = FLEX ? 2 * R : R;
+    const int r = threadIdx.x >> 5;
+    const double t = total_of(part, G, Q, r);
+    const double to = FLEX ? total_of(part, G, Q, R + r) : 0.0;
+    if ((threadIdx.x & 31) == 0) {
+        double b = 0.0;
+        if (!first && active[r]) b = (t - to) / rz[r];
+        if (active[r] && (!isfinite(t) || !(t > 0.0))) atomicExch(ctl, int(QPAT_EBREAKDOWN));
+        beta[r] = b;
+        rz[r] = t;
+    }
+}
+
+// p = z + beta p
+template <int R>
+__global__ void __launch_bounds__(256) k_cg_dir(int64_t n, const double* beta, const double* z, double* p) {
+    double be[R];
+#pragma unroll
+    for (int t = 0; t < R; ++t) be[t] = beta[t];
+    for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x) {
+        double zv[R], pv[R];
+        ldR<double, R>(z + i * R, zv);
+        ldR<double, R>(p + i * R, pv);
+#pragma unroll
+        for (int t = 0; t < R; ++t) pv[t] = fma(be[t], pv[t], zv[t]);
+        stR<double, R>(p + i * R, pv);
+    }
+}
+
+__global__ void k_d2f_vec(int64_t n, const double* in, float* out) {
+    for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x)
+        out[i] = float(in[i]);
+}
+__global__ void k_f2d_vec(int64_t n, const float* in, double* out) {
+    for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x)
+        out[i] = double(in[i]);
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------- host side
+
+struct AmgHierDev {
+    bool tried = false;
+    std::string error;
+    std::vector<LevelDev> lv;
+    std::vector<void*> allocs;
+};
+
+struct AmgValues {
+    uint64_t stamp = 0;
+    bool valid = false;
+    bool has32 = false;
+    std::vector<std::array<double*, 2>> A, P, R;  // A[0] unused (the operator's own values)
+    std::vector<double*> AP, dinv;
+    double* hi = nullptr;   // 2 per level
+    double* inv = nullptr;  // coarsest inverse, NV x n x n
+    std::vector<std::array<float*, 2>> A32, P32, R32;  // A32[0]: FP32 copy of the operator
+    std::vector<float*> dinv32;
+    float* inv32 = nullptr;
+    std::vector<void*> allocs;
+};
+
+struct AmgVecs {
+    std::vector<void*> b, xa, xb, d, r;
+    std::vector<void*> allocs;
+};
+
+struct AmgCg {
+    double *r = nullptr, *p = nullptr, *q = nullptr, *z[2] = {nullptr, nullptr}, *part = nullptr;
+    double *bb = nullptr, *rz = nullptr, *alpha = nullptr, *beta = nullptr, *rr = nullptr;
+    int* ctl = nullptr;     // [0] status, [1] right-hand sides still running
+    int* active = nullptr;  // 16
+    std::vector<void*> allocs;
+};
+
+struct AmgState {
+    AmgHierDev hier[2];  // 0: the K pattern, 1: the prior's stiffness-only pattern
+    std::map<const void*, AmgValues> vals;
+    std::map<std::pair<int, int>, AmgVecs> vecs;  // (pattern * 64 + R, FP32 V-cycle)
+    std::map<int, AmgCg> cg;                       // R
+};
+
+namespace {
+
+template <typename T>
+T* dalloc(std::vector<void*>& list, size_t count, cudaError_t& e) {
+    if (e != cudaSuccess) return nullptr;
+    void* p = nullptr;
+    e = cudaMalloc(&p, std::max<size_t>(count, 1) * sizeof(T));
+    if (e != cudaSuccess) return nullptr;
+    list.push_back(p);
+    return static_cast<T*>(p);
+}
+
+template <typename T>
+const T* upload(std::vector<void*>& list, const std::vector<T>& h, cudaError_t& e) {
+    T* d = dalloc<T>(list, h.size(), e);
+    if (e == cudaSuccess && !h.empty()) e = cudaMemcpy(d, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice);
+    return d;
+}
+
+SellDev upload_sell(std::vector<void*>& list, const SellPattern& S, cudaError_t& e) {
+    SellDev d;
+    d.n = S.n;
+    d.ptr = upload(list, S.ptr, e);
+    d.col = upload(list, S.col, e);
+    d.len = upload(list, S.len, e);
+    d.entries = S.entries();
+    d.maxlen = S.maxlen;
+    return d;
+}
+
+inline int blocks_of(int64_t n, int per = 256) { return int(std::max<int64_t>(1, (n + per - 1) / per)); }
+
+int build_hier(qpat_mesh_s* M, int prior, AmgHierDev& H) {
+    H.tried = true;
+    const AmgPlan plan = amg_build_plan(amg_fine_pattern(M->h, prior));
+    if (!plan.error.empty()) {
+        H.error = plan.error;
+        return fail(QPAT_EINVAL, plan.error);
+    }
+    cudaError_t e = cudaSuccess;
+    for (const AmgLevelPlan& L : plan.levels) {
+        LevelDev d;
+        d.A = upload_sell(H.allocs, L.A, e);
+        d.diag = upload(H.allocs, L.diag, e);
+        d.nc = L.nc;
+        if (L.nc > 0) {
+            d.P = upload_sell(H.allocs, L.P, e);
+            d.a2p = upload(H.allocs, L.a2p, e);
+            d.pself = upload(H.allocs, L.pself, e);
+            d.ap_ptr = upload(H.allocs, L.ap_ptr, e);
+            d.ap_col = upload(H.allocs, L.ap_col, e);
+            d.ap_sptr = upload(H.allocs, L.ap_sptr, e);
+            d.ap_slot = upload(H.allocs, L.ap_slot, e);
+            d.ap_nnz = int64_t(L.ap_col.size());
+            d.R = upload_sell(H.allocs, L.R, e);
+            d.r_src = upload(H.allocs, L.r_src, e);
+            d.g_ptr = upload(H.allocs, L.g_ptr, e);
+            d.g_slot = upload(H.allocs, L.g_slot, e);
+        }
+        H.lv.push_back(d);
+    }
+    if (e != cudaSuccess) {
+        H.error = std::string("multigrid upload: ") + cudaGetErrorString(e);
+        return cuda_fail(e, "multigrid upload");
+    }
+    return QPAT_OK;
+}
+
+template <int NV>
+cudaError_t numeric_levels(const AmgHierDev& H, const OpState& st, AmgValues& V, cudaStream_t s) {
+    const int L = int(H.lv.size());
+    cudaError_t e = cudaMemsetAsync(V.hi, 0, sizeof(double) * 2 * L, s);
+    if (e != cudaSuccess) return e;
+    for (int l = 0; l < L; ++l) {
+        const LevelDev& d = H.lv[size_t(l)];
+        const double* a0 = l == 0 ? st.v64[0] : V.A[size_t(l)][0];
+        const double* a1 = l == 0 ? st.v64[1] : V.A[size_t(l)][1];
+        note_launch(1);
+        k_dinv_hi<NV><<<blocks_of(d.A.n), 256, 0, s>>>(d.A, d.diag, a0, a1, V.dinv[size_t(l)], V.hi + 2 * l);
+        if (l + 1 == L) break;
+        const auto& Pv = V.P[size_t(l)];
+        const auto& Rv = V.R[size_t(l)];
+        note_launch(4);
+        k_prolong<NV><<<blocks_of(d.A.n), 256, 0, s>>>(d.A, d.P, d.a2p, d.pself, a0, a1, V.dinv[size_t(l)],
+                                                        V.hi + 2 * l, Pv[0], Pv[1]);
+        k_rvals<NV><<<blocks_of(d.R.entries), 256, 0, s>>>(d.R.entries, d.r_src, Pv[0], Pv[1], Rv[0], Rv[1]);
+        k_ap<NV><<<blocks_of(d.A.n, 128), 128, 0, s>>>(d.A, d.P, d.ap_ptr, d.ap_sptr, d.ap_slot, d.ap_nnz, a0, a1,
+                                                        Pv[0], Pv[1], V.AP[size_t(l)]);
+        const LevelDev& c = H.lv[size_t(l + 1)];
+        int wpb = 8;
+        while (wpb > 1 && size_t(wpb) * size_t(c.A.maxlen) * sizeof(double) > 96 * 1024) wpb >>= 1;
+        const size_t smem = size_t(wpb) * size_t(c.A.maxlen) * sizeof(double);
+        if ((e = allow_smem(reinterpret_cast<const void*>(&k_galerkin<NV>), smem)) != cudaSuccess) return e;
+        k_galerkin<NV><<<blocks_of(c.A.n * NV, wpb), 32 * wpb, smem, s>>>(
+            d.R, c.A, d.r_src, d.ap_ptr, d.g_ptr, d.g_slot, d.ap_nnz, Pv[0], Pv[1], V.AP[size_t(l)],
+            V.A[size_t(l + 1)][0], V.A[size_t(l + 1)][1]);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    const LevelDev& c = H.lv[size_t(L - 1)];
+    const int n = int(c.A.n);
+    const size_t smem = size_t(n) * size_t(n + 1) * sizeof(double);
+    if ((e = allow_smem(reinterpret_cast<const void*>(&k_dense_inv<NV>), smem)) != cudaSuccess) return e;
+    const double* a0 = L == 1 ? st.v64[0] : V.A[size_t(L - 1)][0];
+    const double* a1 = L == 1 ? st.v64[1] : V.A[size_t(L - 1)][1];
+    note_launch(1);
+    k_dense_inv<NV><<<NV, 256, smem, s>>>(c.A, a0, a1, V.inv);
+    return cudaGetLastError();
+}
+
+cudaError_t cast_to_f32(const double* in, float* out, int64_t n, cudaStream_t s) {
+    note_launch(1);
+    k_d2f<<<blocks_of(n), 256, 0, s>>>(n, in, out);
+    return cudaGetLastError();
+}
+
+// Values of the hierarchy for the operator st (allocated once per operator
+// buffer, recomputed when st was prepared again).
+int numeric(qpat_mesh_s* M, const AmgHierDev& H, const OpState& st, AmgValues& V, bool need32, cudaStream_t s) {
+    const int L = int(H.lv.size());
+    const int NV = st.nv;
+    cudaError_t e = cudaSuccess;
+    if (V.A.empty()) {
+        V.A.assign(size_t(L), {nullptr, nullptr});
+        V.P.assign(size_t(L), {nullptr, nullptr});
+        V.R.assign(size_t(L), {nullptr, nullptr});
+        V.AP.assign(size_t(L), nullptr);
+        V.dinv.assign(size_t(L), nullptr);
+        for (int l = 0; l < L; ++l) {
+            const LevelDev& d = H.lv[size_t(l)];
+            for (int v = 0; v < NV; ++v) {
+                if (l > 0) V.A[size_t(l)][size_t(v)] = dalloc<double>(V.allocs, size_t(d.A.entries), e);
+                if (l + 1 < L) {
+                    V.P[size_t(l)][size_t(v)] = dalloc<double>(V.allocs, size_t(d.P.entries), e);
+                    V.R[size_t(l)][size_t(v)] = dalloc<double>(V.allocs, size_t(d.R.entries), e);
+                }
+            }
+            if (l + 1 < L) V.AP[size_t(l)] = dalloc<double>(V.allocs, size_t(d.ap_nnz) * NV, e);
+            V.dinv[size_t(l)] = dalloc<double>(V.allocs, size_t(d.A.n) * NV, e);
+        }
+        V.hi = dalloc<double>(V.allocs, size_t(2 * L), e);
+        const int64_t nco = H.lv.back().A.n;
+        V.inv = dalloc<double>(V.allocs, size_t(NV * nco * nco), e);
+        if (e != cudaSuccess) return cuda_fail(e, "multigrid workspace");
+        // P and A P padding entries are never written: keep them 0
+        for (int l = 0; l + 1 < L; ++l)
+            for (int v = 0; v < NV; ++v)
+                if ((e = cudaMemsetAsync(V.P[size_t(l)][size_t(v)], 0, sizeof(double) * H.lv[size_t(l)].P.entries, s)) !=
+                    cudaSuccess)
+                    return cuda_fail(e, "multigrid memset");
+    }
+    if (need32 && !V.has32) {
+        V.A32.assign(size_t(L), {nullptr, nullptr});
+        V.P32.assign(size_t(L), {nullptr, nullptr});
+        V.R32.assign(size_t(L), {nullptr, nullptr});
+        V.dinv32.assign(size_t(L), nullptr);
+        for (int l = 0; l < L; ++l) {
+            const LevelDev& d = H.lv[size_t(l)];
+            for (int v = 0; v < NV; ++v) {
+                V.A32[size_t(l)][size_t(v)] = dalloc<float>(V.allocs, size_t(d.A.entries), e);
+                if (l + 1 < L) {
+                    V.P32[size_t(l)][size_t(v)] = dalloc<float>(V.allocs, size_t(d.P.entries), e);
+                    V.R32[size_t(l)][size_t(v)] = dalloc<float>(V.allocs, size_t(d.R.entries), e);
+                }
+            }
+            V.dinv32[size_t(l)] = dalloc<float>(V.allocs, size_t(d.A.n) * NV, e);
+        }
+        const int64_t nco = H.lv.back().A.n;
+        V.inv32 = dalloc<float>(V.allocs, size_t(NV * nco * nco), e);
+        if (e != cudaSuccess) return cuda_fail(e, "multigrid workspace");
+        V.has32 = true;
+        V.valid = false;
+    }
+    if (V.valid && V.stamp == st.stamp) return QPAT_OK;
+    e = NV == 1 ? numeric_levels<1>(H, st, V, s) : numeric_levels<2>(H, st, V, s);
+    if (e != cudaSuccess) return cuda_fail(e, "multigrid set-up");
+    if (V.has32) {
+        for (int l = 0; l < L && e == cudaSuccess; ++l) {
+            const LevelDev& d = H.lv[size_t(l)];
+            for (int v = 0; v < NV && e == cudaSuccess; ++v) {
+                const double* a = l == 0 ? st.v64[v] : V.A[size_t(l)][size_t(v)];
+                e = cast_to_f32(a, V.A32[size_t(l)][size_t(v)], d.A.entries, s);
+                if (e == cudaSuccess && l + 1 < L) e = cast_to_f32(V.P[size_t(l)][size_t(v)], V.P32[size_t(l)][size_t(v)], d.P.entries, s);
+                if (e == cudaSuccess && l + 1 < L) e = cast_to_f32(V.R[size_t(l)][size_t(v)], V.R32[size_t(l)][size_t(v)], d.R.entries, s);
+            }
+            if (e == cudaSuccess) e = cast_to_f32(V.dinv[size_t(l)], V.dinv32[size_t(l)], d.A.n * NV, s);
+        }
+        const int64_t nco = H.lv.back().A.n;
+        if (e == cudaSuccess) e = cast_to_f32(V.inv, V.inv32, NV * nco * nco, s);
+        if (e != cudaSuccess) return cuda_fail(e, "multigrid set-up");
+    }
+    V.stamp = st.stamp;
+    V.valid = true;
+    (void)M;
+    return QPAT_OK;
+}
+
+}  // namespace
+
+namespace {
+
+// One V-cycle x = B b on level l and below (pre-smoothing from x = 0,
+// residual, restriction, the coarser cycle, prolongation, post-smoothing
+// with the same polynomial: B is symmetric).
+template <typename T, int R, int NV>
+struct VCycle {
+    const AmgHierDev& H;
+    const AmgValues& V;
+    AmgVecs& W;
+    const OpState& st;
+    int deg;
+    double ratio;
+    cudaStream_t s;
+
+    static constexpr bool F64 = std::is_same<T, double>::value;
+    const T* av(int l, int v) const {
+        if constexpr (F64)
+            return l == 0 ? st.v64[v] : V.A[size_t(l)][size_t(v)];
+        else
+            return V.A32[size_t(l)][size_t(v)];
+    }
+    const T* pv(int l, int v) const {
+        if constexpr (F64) return V.P[size_t(l)][size_t(v)];
+        else return V.P32[size_t(l)][size_t(v)];
+    }
+    const T* rv(int l, int v) const {
+        if constexpr (F64) return V.R[size_t(l)][size_t(v)];
+        else return V.R32[size_t(l)][size_t(v)];
+    }
+    const T* dinv(int l) const {
+        if constexpr (F64) return V.dinv[size_t(l)];
+        else return V.dinv32[size_t(l)];
+    }
+    const T* inv() const {
+        if constexpr (F64) return V.inv;
+        else return V.inv32;
+    }
+
+    const T* run(int l, const T* b) {
+        const LevelDev& d = H.lv[size_t(l)];
+        const int L = int(H.lv.size());
+        T* x = static_cast<T*>(W.xa[size_t(l)]);
+        T* y = static_cast<T*>(W.xb[size_t(l)]);
+        T* dd = static_cast<T*>(W.d[size_t(l)]);
+        if (l == L - 1) {
+            note_launch(1);
+            k_dense_apply<T, R, NV><<<1, 256, 0, s>>>(int(d.A.n), inv(), b, x);
+            return x;
+        }
+        const int g = blocks_of(d.A.n);
+        const double* hi = V.hi + 2 * l;
+        const T *a0 = av(l, 0), *a1 = av(l, 1);
+        note_launch(1);
+        k_cheb<T, R, NV, true><<<g, 256, 0, s>>>(d.A, a0, a1, dinv(l), hi, ratio, 0, nullptr, x, dd, b);
+        for (int k = 1; k < deg; ++k) {
+            note_launch(1);
+            k_cheb<T, R, NV, false><<<g, 256, 0, s>>>(d.A, a0, a1, dinv(l), hi, ratio, k, x, y, dd, b);
+            std::swap(x, y);
+        }
+        T* res = static_cast<T*>(W.r[size_t(l)]);
+        T* bc = static_cast<T*>(W.b[size_t(l + 1)]);
+        note_launch(2);
+        k_spmv<T, R, NV, 1><<<g, 256, 0, s>>>(d.A, a0, a1, x, b, res);
+        k_spmv<T, R, NV, 0><<<blocks_of(d.R.n), 256, 0, s>>>(d.R, rv(l, 0), rv(l, 1), res, nullptr, bc);
+        const T* xc = run(l + 1, bc);
+        note_launch(1);
+        k_spmv<T, R, NV, 2><<<g, 256, 0, s>>>(d.P, pv(l, 0), pv(l, 1), xc, x, x);
+        for (int k = 0; k < deg; ++k) {
+            note_launch(1);
+            k_cheb<T, R, NV, false><<<g, 256, 0, s>>>(d.A, a0, a1, dinv(l), hi, ratio, k, x, y, dd, b);
+            std::swap(x, y);
+        }
+        return x;
+    }
+};
+
+template <int R, bool FLEX>
+void launch_dots_beta(const AmgCg& C, int64_t n, int G, const double* z, const double* zo, int first,
+                      cudaStream_t s) {
+    note_launch(2);
+    k_cg_dots<R, FLEX><<<G, 256, 0, s>>>(n, C.r, z, zo, C.part);
+    k_cg_beta<R, FLEX><<<1, 32 * R, 0, s>>>(C.part, G, first, C.rz, C.active, C.beta, C.ctl);
+}
+
+// Conjugate gradients on the fine operator with one V-cycle per iteration
+// as the preconditioner; X = 0 to start, each right-hand side stops at
+// |r| <= rtol |b| (the recursive residual, as the persistent PCG does).
+template <int R, int NV>
+int cg_solve(qpat_mesh_s* M, const OpState& st, const SolveOpts& so, const AmgHierDev& H, const AmgValues& V,
+             bool f32, AmgVecs& W, AmgCg& C, const double* B, double* X, const double* X0, cudaStream_t s,
+             int* iters) {
+    const LevelDev& d0 = H.lv[0];
+    const int64_t n = d0.A.n;
+    const int G = int(std::min<int64_t>(blocks_of(n), kRedMaxGrid));
+    const int deg = std::max(1, so.mg_degree);
+    int* hc = reinterpret_cast<int*>(M->host_scratch + 240);
+    cudaError_t e = cudaSuccess;
+    auto read_ctl = [&]() -> cudaError_t {
+        cudaError_t x = cudaMemcpyAsync(hc, C.ctl, 2 * sizeof(int), cudaMemcpyDeviceToHost, s);
+        if (x == cudaSuccess) x = cudaStreamSynchronize(s);
+        return x;
+    };
+    VCycle<double, R, NV> c64{H, V, W, st, deg, so.mg_ratio, s};
+    VCycle<float, R, NV> c32{H, V, W, st, deg, so.mg_ratio, s};
+    auto precond = [&](int it) -> const double* {
+        if (!f32) return c64.run(0, C.r);
+        float* b0 = static_cast<float*>(W.b[0]);
+        note_launch(1);
+        k_d2f_vec<<<G, 256, 0, s>>>(n * R, C.r, b0);
+        const float* x0 = c32.run(0, b0);
+        double* z = C.z[it & 1];
+        note_launch(1);
+        k_f2d_vec<<<G, 256, 0, s>>>(n * R, x0, z);
+        return z;
+    };
+    if ((e = cudaMemsetAsync(C.ctl, 0, 2 * sizeof(int), s)) != cudaSuccess) return cuda_fail(e, "memset");
+    note_launch(2);
+    if (X0)
+        k_cg_init_x0<R, NV><<<G, 256, 0, s>>>(d0.A, st.v64[0], st.v64[1], B, X0, X, C.r, C.part);
+    else
+        k_cg_init<R><<<G, 256, 0, s>>>(n, B, X, C.r, C.part);
+    k_cg_start<R><<<1, 32 * R, 0, s>>>(C.part, G, C.bb, C.active, C.ctl);
+    if ((e = read_ctl()) != cudaSuccess) return cuda_fail(e, "multigrid cg");
+    if (hc[0] != QPAT_OK) return fail(hc[0], "multigrid cg: right-hand side not finite");
+    *iters = 0;
+    if (hc[1] == 0) return QPAT_OK;
+    const double* z = precond(0);
+    if (f32)
+        launch_dots_beta<R, true>(C, n, G, z, z, 1, s);
+    else
+        launch_dots_beta<R, false>(C, n, G, z, z, 1, s);
+    if ((e = cudaMemcpyAsync(C.p, z, sizeof(double) * n * R, cudaMemcpyDeviceToDevice, s)) != cudaSuccess)
+        return cuda_fail(e, "copy");
+    const double rtol2 = so.rtol * so.rtol;
+    for (int it = 1; it <= so.maxit; ++it) {
+        note_launch(4);
+        k_cg_apply<R, NV><<<G, 256, 0, s>>>(d0.A, st.v64[0], st.v64[1], C.p, C.q, C.part);
+        k_cg_alpha<R><<<1, 32 * R, 0, s>>>(C.part, G, C.rz, C.active, C.alpha, C.ctl);
+        k_cg_update<R><<<G, 256, 0, s>>>(n, C.alpha, C.p, C.q, X, C.r, C.part);
+        k_cg_check<R><<<1, 32 * R, 0, s>>>(C.part, G, C.bb, rtol2, C.active, C.rr, C.ctl);
+        if ((e = read_ctl()) != cudaSuccess) return cuda_fail(e, "multigrid cg");
+        *iters = it;
+        if (hc[0] != QPAT_OK) return fail(hc[0], "multigrid cg: breakdown (p.Ap <= 0 or not finite)");
+        if (hc[1] == 0) return QPAT_OK;
+        const double* zo = z;
+        z = precond(it);
+        if (f32)
+            launch_dots_beta<R, true>(C, n, G, z, zo, 0, s);
+        else
+            launch_dots_beta<R, false>(C, n, G, z, zo, 0, s);
+        note_launch(1);
+        k_cg_dir<R><<<G, 256, 0, s>>>(n, C.beta, z, C.p);
+    }
+    return fail(QPAT_ENOCONV, "multigrid cg: iteration cap reached");
+}
+
+template <int NV>
+int dispatch(int R, qpat_mesh_s* M, const OpState& st, const SolveOpts& so, const AmgHierDev& H, const AmgValues& V,
+             bool f32, AmgVecs& W, AmgCg& C, const double* B, double* X, const double* X0, cudaStream_t s,
+             int* iters) {
+    if constexpr (NV == 2) {
+        return cg_solve<2, 2>(M, st, so, H, V, f32, W, C, B, X, X0, s, iters);
+    } else {
+        switch (R) {
+            case 1: return cg_solve<1, 1>(M, st, so, H, V, f32, W, C, B, X, X0, s, iters);
+            case 2: return cg_solve<2, 1>(M, st, so, H, V, f32, W, C, B, X, X0, s, iters);
+            case 4: return cg_solve<4, 1>(M, st, so, H, V, f32, W, C, B, X, X0, s, iters);
+            case 8: return cg_solve<8, 1>(M, st, so, H, V, f32, W, C, B, X, X0, s, iters);
+            default: return cg_solve<16, 1>(M, st, so, H, V, f32, W, C, B, X, X0, s, iters);
+        }
+    }
+}
+
+}  // namespace
+
+int amg_solve(qpat_mesh_s* M, const OpState& st, const SolveOpts& so, int R, const double* B, double* X,
+              cudaStream_t s, const double* X0) {
+    if (R != 1 && R != 2 && R != 4 && R != 8 && R != 16) return fail(QPAT_EINVAL, "multigrid: R must be 1, 2, 4, 8 or 16");
+    if (st.nv == 2 && R != 2) return fail(QPAT_EINVAL, "multigrid: M_delta is solved as 2 right-hand sides");
+    if (!(so.mg_ratio > 1.0) || so.mg_degree < 1 || so.mg_degree > 8)
+        return fail(QPAT_EINVAL, "multigrid: mg_degree must lie in [1, 8] and mg_ratio exceed 1");
+    if (!M->amg) M->amg = new AmgState();
+    AmgState& A = *M->amg;
+    const int pat = st.kind == OP_PRIOR ? 1 : 0;
+    AmgHierDev& H = A.hier[pat];
+    if (!H.tried) {
+        const int rc = build_hier(M, pat, H);
+        if (rc != QPAT_OK) return rc;
+    } else if (!H.error.empty()) {
+        return fail(QPAT_EINVAL, H.error);
+    }
+    const bool f32 = so.multigrid == 2 && st.kind == OP_K;
+    AmgValues& V = A.vals[st.v64[0]];
+    int rc = numeric(M, H, st, V, f32, s);
+    if (rc != QPAT_OK) return rc;
+    cudaError_t e = cudaSuccess;
+    AmgVecs& W = A.vecs[{pat * 64 + R, f32 ? 1 : 0}];
+    if (W.xa.empty()) {
+        const size_t esz = f32 ? sizeof(float) : sizeof(double);
+        for (const LevelDev& d : H.lv) {
+            const size_t cnt = size_t(d.A.n) * R * esz;
+            W.b.push_back(dalloc<char>(W.allocs, cnt, e));
+            W.xa.push_back(dalloc<char>(W.allocs, cnt, e));
+            W.xb.push_back(dalloc<char>(W.allocs, cnt, e));
+            W.d.push_back(dalloc<char>(W.allocs, cnt, e));
+            W.r.push_back(dalloc<char>(W.allocs, cnt, e));
+        }
+        if (e != cudaSuccess) return cuda_fail(e, "multigrid workspace");
+    }
+    AmgCg& C = A.cg[R];
+    if (!C.r) {
+        const size_t nR = size_t(M->h.N) * R;
+        C.r = dalloc<double>(C.allocs, nR, e);
+        C.p = dalloc<double>(C.allocs, nR, e);
+        C.q = dalloc<double>(C.allocs, nR, e);
+        C.z[0] = dalloc<double>(C.allocs, nR, e);
+        C.z[1] = dalloc<double>(C.allocs, nR, e);
+        C.part = dalloc<double>(C.allocs, size_t(kRedMaxGrid) * 32, e);
+        double* sc = dalloc<double>(C.allocs, 5 * 16, e);
+        C.ctl = dalloc<int>(C.allocs, 2 + 16, e);
+        if (e != cudaSuccess) return cuda_fail(e, "multigrid workspace");
+        C.bb = sc;
+        C.rz = sc + 16;
+        C.alpha = sc + 32;
+        C.beta = sc + 48;
+        C.rr = sc + 64;
+        C.active = C.ctl + 2;
+    }
+    if (M->timing) cudaEventRecord(M->ev0, s);
+    int iters = 0;
+    rc = st.nv == 2 ? dispatch<2>(R, M, st, so, H, V, f32, W, C, B, X, X0, s, &iters)
+                    : dispatch<1>(R, M, st, so, H, V, f32, W, C, B, X, X0, s, &iters);
+    if ((e = cudaGetLastError()) != cudaSuccess && rc == QPAT_OK) rc = cuda_fail(e, "multigrid launch");
+    if (M->timing) {
+        cudaEventRecord(M->ev1, s);
+        cudaEventSynchronize(M->ev1);
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, M->ev0, M->ev1);
+        M->pcg_ms += ms;
+    }
+    M->stats.pcg_iters += iters;
+    M->stats.rhs_iters += int64_t(iters) * R;
+    M->stats.solves += R;
+    M->stats.launches += 1;
+    return rc;
+}
+
+int amg_levels(qpat_mesh_s* M, int prior, int64_t* rows, int max_levels) {
+    if (!M->amg) return 0;
+    const AmgHierDev& H = M->amg->hier[prior ? 1 : 0];
+    const int L = int(H.lv.size());
+    for (int l = 0; l < std::min(L, max_levels); ++l) rows[l] = H.lv[size_t(l)].A.n;
+    return L;
+}
+
+void amg_release(qpat_mesh_s* M) {
+    if (!M->amg) return;
+    AmgState& A = *M->amg;
+    for (auto& H : A.hier)
+        for (void* p : H.allocs) cudaFree(p);
+    for (auto& kv : A.vals)
+        for (void* p : kv.second.allocs) cudaFree(p);
+    for (auto& kv : A.vecs)
+        for (void* p : kv.second.allocs) cudaFree(p);
+    for (auto& kv : A.cg)
+        for (void* p : kv.second.allocs) cudaFree(p);
+    delete M->amg;
+    M->amg = nullptr;
+}
+
+}  // namespace qpat

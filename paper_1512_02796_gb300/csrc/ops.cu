@@ -159,6 +159,9 @@ SolveOpts solve_opts(const qpat_params* prm) {
     so.poly_k = p->poly_degree;
     so.poly_prior = p->prior_poly_degree;
     so.spin_limit = p->barrier_spin_limit > 0 ? p->barrier_spin_limit : 0;
+    so.multigrid = p->multigrid;
+    so.mg_degree = p->mg_degree > 0 ? p->mg_degree : 2;
+    so.mg_ratio = p->mg_ratio > 0 ? p->mg_ratio : 30.0;
     return so;
 }
 
@@ -177,6 +180,10 @@ static int check_params(const qpat_params* prm, const char* who) {
     if (prm->barrier_spin_limit < 0) return fail(QPAT_EINVAL, std::string(who) + ": barrier_spin_limit must be >= 0");
     if (prm->lsqr_reorth != 0 && prm->lsqr_reorth != 1)
         return fail(QPAT_EINVAL, std::string(who) + ": lsqr_reorth must be 0 or 1");
+    if (prm->multigrid < 0 || prm->multigrid > 2)
+        return fail(QPAT_EINVAL, std::string(who) + ": multigrid must be 0, 1 or 2");
+    if (prm->mg_degree < 0 || prm->mg_degree > 8 || prm->mg_ratio < 0 || (prm->mg_ratio > 0 && prm->mg_ratio <= 1))
+        return fail(QPAT_EINVAL, std::string(who) + ": mg_degree must lie in [0, 8] and mg_ratio be 0 or above 1");
     return QPAT_OK;
 }
 

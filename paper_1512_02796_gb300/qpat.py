@@ -33,6 +33,7 @@ class qpat_params(ctypes.Structure):
         ("pcg_variant", ctypes.c_int), ("prior", ctypes.c_int), ("mixed_restart", ctypes.c_int),
         ("poly_degree", ctypes.c_int), ("prior_poly_degree", ctypes.c_int), ("step_halvings", ctypes.c_int),
         ("prior_q", ctypes.c_double), ("lsqr_reorth", ctypes.c_int), ("barrier_spin_limit", ctypes.c_int64),
+        ("multigrid", ctypes.c_int), ("mg_degree", ctypes.c_int), ("mg_ratio", ctypes.c_double),
     ]
 
 
@@ -92,6 +93,9 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
         "qpat_mesh_stats": (ctypes.c_int, [vp, _c_int64_p]),
         "qpat_mesh_fp64_fallbacks": (ctypes.c_int64, [vp]),
         "qpat_mesh_rhs_iterations": (ctypes.c_int64, [vp]),
+        "qpat_mesh_multigrid_levels": (ctypes.c_int, [vp, ctypes.c_int, _c_int64_p, ctypes.c_int]),
+        "qpat_multigrid_host_info": (ctypes.c_int, [_c_double_p, ctypes.c_int64, _c_int32_p, ctypes.c_int64, ctypes.c_int,
+                                                    ctypes.c_int, _c_int64_p, ctypes.c_int]),
         "qpat_mesh_reset_stats": (ctypes.c_int, [vp]),
         "qpat_mesh_set_timing": (ctypes.c_int, [vp, ctypes.c_int]),
         "qpat_mesh_pcg_time": (ctypes.c_int, [vp, _c_double_p]),
@@ -173,7 +177,7 @@ def exported_names() -> Sequence[str]:
         "qpat_mesh_host_info", "qpat_mesh_num_nodes", "qpat_mesh_num_tets", "qpat_mesh_num_faces", "qpat_mesh_num_patches",
         "qpat_mesh_num_entries", "qpat_mesh_num_prior_entries", "qpat_mesh_num_local_entries",
         "qpat_mesh_faces", "qpat_mesh_permutation", "qpat_mesh_stats", "qpat_mesh_fp64_fallbacks",
-        "qpat_mesh_rhs_iterations", "qpat_mesh_reset_stats",
+        "qpat_mesh_rhs_iterations", "qpat_mesh_multigrid_levels", "qpat_multigrid_host_info", "qpat_mesh_reset_stats",
         "qpat_mesh_set_timing", "qpat_mesh_pcg_time",
         "qpat_flux_patch", "qpat_flux_side", "qpat_apply_K_dev", "qpat_forward", "qpat_forward_dev", "qpat_forward_noalloc_dev",
         "qpat_forward_guess_dev",
@@ -397,6 +401,15 @@ class Mesh:
     def reset_stats(self):
         _check(load().qpat_mesh_reset_stats(self.handle))
 
+    def multigrid_levels(self, prior: bool = False) -> list:
+        """Rows of each level of the multigrid hierarchy of the K (or prior)
+        pattern, finest first; [] before the first multigrid solve."""
+        rows = np.zeros(16, dtype=np.int64)
+        n = load().qpat_mesh_multigrid_levels(self.handle, 1 if prior else 0, rows.ctypes.data_as(_c_int64_p), 16)
+        if n < 0:
+            _check(n)
+        return [int(r) for r in rows[:min(n, 16)]]
+
     def set_timing(self, on: bool = True):
         _check(load().qpat_mesh_set_timing(self.handle, 1 if on else 0))
 
@@ -429,6 +442,19 @@ def qpat_mesh_host_info(xyz, tets, patch_nodes: int = 512):
     keys = ["F", "P", "max_touched", "max_own", "max_ptets", "max_pfaces", "patch_tets", "patch_faces",
             "nnz", "prior_nnz", "max_tet_colours"]
     return dict(zip(keys, (int(v) for v in info))), faces, perm
+
+
+def qpat_multigrid_host_info(xyz, tets, prior: bool = False, patch_nodes: int = 512) -> list:
+    """Host-only check of the multigrid hierarchy's plan for the mesh's K (or
+    prior) pattern; returns the rows of each level, finest first."""
+    xyz = _f64(xyz)
+    tets = np.ascontiguousarray(tets, dtype=np.int32)
+    rows = np.zeros(16, dtype=np.int64)
+    n = load().qpat_multigrid_host_info(_dp(xyz), xyz.shape[0], tets.ctypes.data_as(_c_int32_p), tets.shape[0],
+                                        patch_nodes, 1 if prior else 0, rows.ctypes.data_as(_c_int64_p), 16)
+    if n < 0:
+        _check(n)
+    return [int(r) for r in rows[:min(n, 16)]]
 
 
 def qpat_flux_side(mesh: Mesh, center, axis, ref, radius: float, theta0: float, half_w: float = math.pi / 8,

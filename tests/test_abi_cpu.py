@@ -141,10 +141,12 @@ def test_params_struct_layout_matches_the_header():
     n = ctypes.sizeof(Q.qpat_params)
     buf = (ctypes.c_ubyte * (n + 32))(*([0xAB] * (n + 32)))
     Q.load().qpat_default_params(ctypes.cast(buf, ctypes.POINTER(Q.qpat_params)))
-    assert buf[n - 1] == 0                     # barrier_spin_limit (0 by default), high byte
+    import struct
+    assert bytes(buf[n - 8:n]) == struct.pack("<d", 30.0)   # mg_ratio, the last field
     assert all(b == 0xAB for b in buf[n:])
     p = Q.qpat_default_params()
     assert p.lsqr_reorth == 1 and p.barrier_spin_limit == 0
+    assert p.multigrid == 0 and p.mg_degree == 2 and p.mg_ratio == 30.0
 
 
 def test_host_output_arrays_are_checked_before_any_call():
@@ -166,3 +168,26 @@ def test_host_output_arrays_are_checked_before_any_call():
         Q.qpat_jvp_vjp_pair(m, x, x, phi, np.zeros(8), phi, None, out_jv=np.empty((3, 4)), out_vjp=np.empty(8))
     with pytest.raises(ValueError):
         Q.qpat_jvp_vjp_pair(m, x, x, phi, np.zeros(8), phi, None, out_jv=np.empty((2, 4)), out_vjp=np.empty(4))
+
+
+@pytest.mark.parametrize("n,prior", [(6, 0), (11, 0), (11, 1), (17, 0), (17, 1), (24, 1)])
+def test_multigrid_plan_invariants_on_cubes(n, prior):
+    """The smoothed-aggregation plan (aggregates, P, R = P^T, the slots of
+    A P and P^T A P, symmetric coarse patterns) passes the library's own
+    invariant check, coarsens by a clear factor per level and ends at <= 128
+    rows."""
+    xyz, tets = S.kuhn_cube(n, 10.0)
+    rows = Q.qpat_multigrid_host_info(xyz, tets, prior=bool(prior))
+    assert rows[0] == n ** 3
+    assert rows[-1] <= 128
+    for a, b in zip(rows, rows[1:]):
+        assert b <= a / 4
+
+
+def test_multigrid_plan_on_cylinder_and_tiny_meshes():
+    xyz, tets = S.cylinder_mesh(9, 6, 5.0, 10.0)
+    for prior in (False, True):
+        rows = Q.qpat_multigrid_host_info(xyz, tets, prior=prior)
+        assert rows[0] == xyz.shape[0] and rows[-1] <= 128
+    xyz, tets = S.kuhn_cube(3, 1.0)          # 27 nodes: the fine level is the coarsest
+    assert Q.qpat_multigrid_host_info(xyz, tets) == [27]
