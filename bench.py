@@ -75,13 +75,17 @@ def whole_job_rate(local_ms: float, steps: int, world: int, device: str = "cuda"
 
 
 
-def kernel_source_sha1() -> str:
-    """Hash of the PCG kernel sources and of the code that lays out their
-    operands (a stored ncu traffic figure is only reported while these are
+PCG_SOURCES = ("pcg.cu", "fem.cuh", "mesh.cpp", "kernels.cu")
+MG_SOURCES = ("amg.cu", "amg_setup.cpp", "amg.h", "fem.cuh", "mesh.cpp", "kernels.cu")
+
+
+def kernel_source_sha1(files=PCG_SOURCES) -> str:
+    """Hash of a kernel's sources and of the code that lays out its operands
+    (a stored ncu traffic figure is only reported while these are
     unchanged)."""
     import hashlib
     h = hashlib.sha1()
-    for f in ("pcg.cu", "fem.cuh", "mesh.cpp", "kernels.cu"):
+    for f in files:
         with open(os.path.join(ROOT, "paper_1512_02796_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()
@@ -557,7 +561,8 @@ def time_steps(Q, torch, d, prm, steps: int, warmup: int, clocks: bool = False, 
     torch.cuda.synchronize()
     mesh.set_timing(True)
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
-    acc = {k: {"ms": 0.0, "iters": 0, "rhs_iters": 0, "launches": 0} for k in ("pair", "prior")}
+    acc = {k: {"ms": 0.0, "iters": 0, "rhs_iters": 0, "launches": 0, "fine_ms": 0.0, "fine_launches": 0}
+           for k in ("pair", "prior")}
     clk = ClockSampler(local) if clocks else None
     if world > 1:
         torch.distributed.barrier()
@@ -578,6 +583,9 @@ def time_steps(Q, torch, d, prm, steps: int, warmup: int, clocks: bool = False, 
             acc[kind]["iters"] += st["pcg_iters"]
             acc[kind]["rhs_iters"] += st["rhs_iters"]
             acc[kind]["launches"] += st["launches"]
+            fm, fl = mesh.multigrid_fine_time()
+            acc[kind]["fine_ms"] += fm
+            acc[kind]["fine_launches"] += fl
         b.record()
     torch.cuda.synchronize()
     wall = time.perf_counter() - wall0
@@ -632,6 +640,81 @@ def kernel_table(d, prm, precision: int, acc, sm_mhz: float, nsm: int, hbm_peak:
     return kern, f64_peak
 
 
+def mg_kernel_table(d, prm, acc, sm_mhz: float, nsm: int, hbm_peak: float, step_ms_total: float):
+    """The multigrid-preconditioned solves of a timed region: per solve kind
+    the whole CG solve (events around it) and its dominant kernel, the fine-
+    level Chebyshev smoothing step (events around each launch), with that
+    kernel's algorithmic work per launch:
+      flops  2 nnz R + 6 N R   (the SpMV of b - A x, then d = c_d d + c_r D^-1 res, x += d)
+      bytes  (s + 4) nnz nv + 2 N + 5 s R N + s N nv   (values and column ids, row lengths,
+             b, x_in, d read, d and x_out written, D^-1)
+    with s the value size and nv the value sets (1 for K, 2 for M_delta)."""
+    mesh, N, K = d["mesh"], d["N"], d["K"]
+    R = 2 * (1 << max(0, math.ceil(math.log2(K))))
+    f32 = prm.multigrid == 2
+    s = 4 if f32 else 8
+    kern = {
+        "pair": {"kernel": f"k_cheb<{'float' if f32 else 'double'}, {R}, 1, false, 1> (fine-level Chebyshev "
+                           f"smoothing step of the multigrid V-cycle of the J s + J^T w solve, {R} RHS)",
+                 "flops_per_launch": 2.0 * mesh.entries * R + 6.0 * N * R,
+                 "bytes_per_launch": (s + 4.0) * mesh.entries + 2.0 * N + 5.0 * s * R * N + s * N,
+                 "arith": "fp32" if f32 else "fp64"},
+        "prior": {"kernel": "k_cheb<double, 2, 2, false, 1> (fine-level Chebyshev smoothing step of the multigrid "
+                            "V-cycle of the M_delta solve, two blocks)",
+                  "flops_per_launch": 2.0 * mesh.prior_entries * 2 + 6.0 * N * 2,
+                  "bytes_per_launch": (2 * 8 + 4.0) * mesh.prior_entries + 2.0 * N + 5.0 * 8 * 2 * N + 16.0 * N,
+                  "arith": "fp64"},
+    }
+    f64_peak = fp64_peak_tflops(sm_mhz, nsm)
+    for k, v in kern.items():
+        v.update(acc[k])
+        sec = v["fine_ms"] / 1e3
+        n = max(v["fine_launches"], 1)
+        v["us_per_launch"] = 1e3 * v["fine_ms"] / n
+        v["achieved_tflops"] = v["flops_per_launch"] * v["fine_launches"] / sec / 1e12 if sec > 0 else 0.0
+        v["achieved_gbs"] = v["bytes_per_launch"] * v["fine_launches"] / sec / 1e9 if sec > 0 else 0.0
+        v["share_of_step"] = v["fine_ms"] / step_ms_total if step_ms_total > 0 else None
+        v["cg_share_of_step"] = v["ms"] / step_ms_total if step_ms_total > 0 else None
+        v["hbm_frac"] = v["achieved_gbs"] / hbm_peak
+        if v["arith"] == "fp64":
+            v["fp64_frac"] = v["achieved_tflops"] / f64_peak
+    return kern, f64_peak
+
+
+def mg_roofline(kern, dom, f64_peak, hbm_peak, hbm_kind, sm_mhz, nsm, workload):
+    """Roofline object of the multigrid cycle's dominant kernel (FP64: against
+    the FP64 pipe; FP32: against the measured HBM copy bandwidth), `traffic`
+    from the committed ncu capture of that kernel on this workload while its
+    sources are unchanged."""
+    k = kern[dom]
+    if k["arith"] == "fp64":
+        out = {"bound": "alu", "achieved": k["achieved_tflops"], "peak": f64_peak, "unit": "TFLOP/s",
+               "peak_kind": f"derived: 2 FP64 FMA per SM per cycle x {nsm} SMs x {sm_mhz:.0f} MHz "
+                            f"(median sampled SM clock)"}
+    else:
+        out = {"bound": "hbm", "achieved": k["achieved_gbs"], "peak": hbm_peak, "unit": "GB/s",
+               "peak_kind": f"{hbm_kind} (MEASURED_PEAKS.json hbm_gbs, STREAM-style copy)" if hbm_kind == "measured"
+               else "fallback 6.8 TB/s"}
+    out["frac"] = out["achieved"] / out["peak"] if out["peak"] else None
+    out["kernel"] = k["kernel"]
+    out["flops_per_launch"] = k["flops_per_launch"]
+    out["bytes_per_launch"] = k["bytes_per_launch"]
+    out["us_per_launch"] = k["us_per_launch"]
+    out["launches"] = k["fine_launches"]
+    out["hbm_peak_gbs"] = hbm_peak
+    out["traffic"] = None
+    tf = os.path.join(ROOT, "profiles", f"k_cheb_{workload}_traffic.json")
+    if os.path.exists(tf):
+        try:
+            tr = json.load(open(tf))
+            ent = tr.get("kernels", {}).get(f"{dom}_{k['arith']}")
+            if ent and tr.get("source_sha1") == kernel_source_sha1(MG_SOURCES):
+                out["traffic"] = ent.get("dram_bytes_per_launch")
+        except Exception:
+            out["traffic"] = None
+    return out
+
+
 def roofline_of(kern, dom, f64_peak, hbm_peak, hbm_kind, sm_mhz, nsm, workload):
     """The roofline object of the dominant kernel: FP64 kernels against the
     FP64 pipe (GB300 issues 2 FP64 FMA per SM per cycle; ncu shows them FP64-
@@ -681,32 +764,46 @@ def run_ours(args):
         import torch.distributed as dist
         dist.init_process_group("nccl")
     torch.cuda.set_device(local)
-    # FP64 K solves with Jacobi: on GB300 they are bound by the FP64 pipe, and
-    # the patch-local polynomial's extra FP64 work per iteration costs more
-    # than its saved iterations (128^3, 16-RHS pair: 1203 ms at degree 0,
-    # 1321 / 1339 / 1437 ms at degrees 1 / 2 / 3); M_delta keeps the library's
-    # degree 2 (325 ms, 327 ms with Jacobi)
-    prm = Q.qpat_default_params(precision=0, poly_degree=0)
-    if args.poly is not None:
-        prm.poly_degree = args.poly
-    if args.prior_poly is not None:
-        prm.prior_poly_degree = args.prior_poly
+    # Headline: every K and M_delta solve by FP64 conjugate gradients with one
+    # smoothed-aggregation multigrid V-cycle (FP64) per iteration.
+    prm = Q.qpat_default_params(precision=0, multigrid=args.multigrid)
+    if not prm.multigrid:
+        # persistent PCG: Jacobi for the FP64 K solves (bound by the FP64 pipe,
+        # the patch-local polynomial's extra FP64 work costs more than its
+        # saved iterations); M_delta with the library's degree 2
+        prm.poly_degree = 0 if args.poly is None else args.poly
+        if args.prior_poly is not None:
+            prm.prior_poly_degree = args.prior_poly
     d = setup_problem(Q, torch, args.workload, args.patch_nodes)
     mesh, N, K = d["mesh"], d["N"], d["K"]
     nsm = torch.cuda.get_device_properties(local).multi_processor_count
     hbm_peak, hbm_kind = load_peaks()
 
-    # ---- headline: FP64 PCG (the paper's arithmetic)
     r = time_steps(Q, torch, d, prm, args.steps, args.warmup, clocks=True, local=local, world=world)
     tot_ms, value = whole_job_rate(sum(r["step_ms"]), args.steps, world)
     clocks = r["clocks"]
     sm_mhz = clocks["sm_mhz"] if clocks else 2070.0
-    kern, f64_peak = kernel_table(d, prm, 0, r["kernels"], sm_mhz, nsm, hbm_peak, sum(r["step_ms"]))
-    dom = max(kern, key=lambda k: kern[k]["ms"])
-    roof = roofline_of(kern, dom, f64_peak, hbm_peak, hbm_kind, sm_mhz, nsm, args.workload)
+    if prm.multigrid:
+        kern, f64_peak = mg_kernel_table(d, prm, r["kernels"], sm_mhz, nsm, hbm_peak, sum(r["step_ms"]))
+        dom = max(kern, key=lambda k: kern[k]["fine_ms"])
+        roof = mg_roofline(kern, dom, f64_peak, hbm_peak, hbm_kind, sm_mhz, nsm, args.workload)
+        roof["note"] = ("achieved = algorithmic work per launch x launches / CUDA-event time of the fine-level "
+                        "smoothing launches (events around each launch on its stream, timed region only); "
+                        "kernels[*].ms = the whole multigrid-CG solves")
+        precond = {"K": f"smoothed-aggregation multigrid V-cycle ({'FP32' if prm.multigrid == 2 else 'FP64'}), "
+                        f"Chebyshev degree {prm.mg_degree} on [hi/{prm.mg_ratio:g}, hi]",
+                   "M_delta": f"smoothed-aggregation multigrid V-cycle (FP64), Chebyshev degree {prm.mg_degree}",
+                   "levels_K": mesh.multigrid_levels(), "levels_M_delta": mesh.multigrid_levels(True)}
+    else:
+        kern, f64_peak = kernel_table(d, prm, 0, r["kernels"], sm_mhz, nsm, hbm_peak, sum(r["step_ms"]))
+        dom = max(kern, key=lambda k: kern[k]["ms"])
+        roof = roofline_of(kern, dom, f64_peak, hbm_peak, hbm_kind, sm_mhz, nsm, args.workload)
+        roof["note"] = ("achieved = algorithmic work per PCG iteration x iterations / CUDA-event time of the "
+                        "launches (events on the launching stream, timed region only)")
+        precond = {"K": f"patch-local Chebyshev, degree {prm.poly_degree}" if prm.poly_degree else "Jacobi",
+                   "M_delta": (f"patch-local Chebyshev, degree {prm.prior_poly_degree}"
+                               if prm.prior_poly_degree else "Jacobi")}
     roof["kernels"] = kern
-    roof["note"] = ("achieved = algorithmic work per PCG iteration x iterations / CUDA-event time of the "
-                    "launches (events on the launching stream, timed region only)")
 
     # ---- end to end through the host-pointer ABI (copies inside the timed region)
     H = d["host"]
@@ -727,13 +824,10 @@ def run_ours(args):
         "metric": metric_name(args.workload), "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": tot_ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None,   # replicas: per-GPU work fixed as N grows
-        "dtype": "f64", "data": "synthetic",
+        "dtype": "f64" if prm.multigrid != 2 else "f64+f32-multigrid", "data": "synthetic",
         "config": {"workload": args.workload, "nodes": N, "tets": d["E"], "illuminations": K,
                    "pair_rhs": 2 * K, "precision": "fp64", "pcg_rtol": prm.pcg_rtol,
-                   "patches": mesh.P, "preconditioner": {
-                       "K": f"patch-local Chebyshev, degree {prm.poly_degree}" if prm.poly_degree else "Jacobi",
-                       "M_delta": (f"patch-local Chebyshev, degree {prm.prior_poly_degree}"
-                                   if prm.prior_poly_degree else "Jacobi")},
+                   "patches": mesh.P, "preconditioner": precond,
                    "l2": "flushed between steps (256 MB write outside the per-step events); inputs > L2",
                    "parallelism": "replicas" if world > 1 else "single"},
         "e2e": {"value": e2e_steps / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
@@ -743,16 +837,38 @@ def run_ours(args):
         "wall_s": r["wall_s"],
     }
 
-    # ---- the same step in mixed precision (FP32 PCG inside FP64 refinement)
+    # ---- the same step with the persistent Jacobi / patch-local PCG (FP64)
+    if args.pcg_steps > 0 and prm.multigrid:
+        pp = Q.qpat_default_params(precision=0, poly_degree=0)
+        rp = time_steps(Q, torch, d, pp, args.pcg_steps, 3)
+        kp, _ = kernel_table(d, pp, 0, rp["kernels"], sm_mhz, nsm, hbm_peak, sum(rp["step_ms"]))
+        dp = max(kp, key=lambda k: kp[k]["ms"])
+        out["fp64_pcg"] = {"value": args.pcg_steps / (sum(rp["step_ms"]) / 1e3), "unit": UNIT,
+                           "ms_per_step": sum(rp["step_ms"]) / args.pcg_steps, "steps": args.pcg_steps,
+                           "dtype": "f64", "gpu_launches": rp["gpu_launches"],
+                           "preconditioner": {"K": "Jacobi", "M_delta": "patch-local Chebyshev, degree 2"},
+                           "roofline": roofline_of(kp, dp, f64_peak, hbm_peak, hbm_kind, sm_mhz, nsm, args.workload),
+                           "kernels": kp}
+    # ---- mixed precision: FP64 CG with the K solves' V-cycle in FP32
     if args.mixed_steps > 0:
-        pm = Q.qpat_default_params(precision=1, fp32_operator=1)
+        pm = Q.qpat_default_params(precision=0, multigrid=2)
         rm = time_steps(Q, torch, d, pm, args.mixed_steps, 3)
-        km, _ = kernel_table(d, pm, 1, rm["kernels"], sm_mhz, nsm, hbm_peak, sum(rm["step_ms"]))
+        km, _ = mg_kernel_table(d, pm, rm["kernels"], sm_mhz, nsm, hbm_peak, sum(rm["step_ms"]))
         out["mixed"] = {"value": args.mixed_steps / (sum(rm["step_ms"]) / 1e3), "unit": UNIT,
                         "ms_per_step": sum(rm["step_ms"]) / args.mixed_steps, "steps": args.mixed_steps,
-                        "dtype": "f32+f64-refine", "gpu_launches": rm["gpu_launches"],
-                        "roofline": roofline_of(km, "pair", f64_peak, hbm_peak, hbm_kind, sm_mhz, nsm, args.workload),
+                        "dtype": "f64 CG + f32 multigrid cycle (K)", "gpu_launches": rm["gpu_launches"],
+                        "roofline": mg_roofline(km, "pair", f64_peak, hbm_peak, hbm_kind, sm_mhz, nsm, args.workload),
                         "kernels": km}
+        # and FP32 PCG inside FP64 refinement (persistent kernels)
+        pr = Q.qpat_default_params(precision=1, fp32_operator=1)
+        rr = time_steps(Q, torch, d, pr, args.mixed_steps, 3)
+        kr, _ = kernel_table(d, pr, 1, rr["kernels"], sm_mhz, nsm, hbm_peak, sum(rr["step_ms"]))
+        out["mixed_pcg"] = {"value": args.mixed_steps / (sum(rr["step_ms"]) / 1e3), "unit": UNIT,
+                            "ms_per_step": sum(rr["step_ms"]) / args.mixed_steps, "steps": args.mixed_steps,
+                            "dtype": "f32+f64-refine", "gpu_launches": rr["gpu_launches"],
+                            "roofline": roofline_of(kr, "pair", f64_peak, hbm_peak, hbm_kind, sm_mhz, nsm,
+                                                    args.workload),
+                            "kernels": kr}
     mesh.close()
     del d
     torch.cuda.empty_cache()
@@ -774,18 +890,29 @@ def run_ours(args):
 
 def c2_leg(Q, torch, nsm, hbm_peak, hbm_kind, sm_mhz, steps: int = 5):
     """Config 2 (96^3 nodes, 8 illuminations): each pair's J s and J^T w run
-    as one 16-RHS block in FP32 PCG with FP64 refinement (to the same 1e-13
-    residuals), plus the FP64 M_delta solve."""
+    as one 16-RHS block, plus the M_delta solve; FP64 multigrid-preconditioned
+    CG (the value) and FP32 PCG with FP64 refinement (to the same 1e-13
+    residuals)."""
     d = setup_problem(Q, torch, "c2_cube96")
     try:
+        pg = Q.qpat_default_params(precision=0, multigrid=1)
+        rg = time_steps(Q, torch, d, pg, steps, 3)
+        kg, f64_peak = mg_kernel_table(d, pg, rg["kernels"], sm_mhz, nsm, hbm_peak, sum(rg["step_ms"]))
         pm = Q.qpat_default_params(precision=1, fp32_operator=1)
         r = time_steps(Q, torch, d, pm, steps, 3)
         km, f64_peak = kernel_table(d, pm, 1, r["kernels"], sm_mhz, nsm, hbm_peak, sum(r["step_ms"]))
-        return {"value": steps / (sum(r["step_ms"]) / 1e3), "unit": UNIT, "steps": steps,
-                "ms_per_step": sum(r["step_ms"]) / steps, "nodes": d["N"], "tets": d["E"], "illuminations": d["K"],
-                "dtype": "f32+f64-refine", "gpu_launches": r["gpu_launches"],
-                "roofline": roofline_of(km, "pair", f64_peak, hbm_peak, hbm_kind, sm_mhz, nsm, "c2_cube96"),
-                "kernels": km}
+        return {"value": steps / (sum(rg["step_ms"]) / 1e3), "unit": UNIT, "steps": steps,
+                "ms_per_step": sum(rg["step_ms"]) / steps, "nodes": d["N"], "tets": d["E"], "illuminations": d["K"],
+                "dtype": "f64", "preconditioner": "smoothed-aggregation multigrid V-cycle (FP64)",
+                "gpu_launches": rg["gpu_launches"],
+                "roofline": mg_roofline(kg, "pair", f64_peak, hbm_peak, hbm_kind, sm_mhz, nsm, "c2_cube96"),
+                "kernels": kg,
+                "mixed_pcg": {"value": steps / (sum(r["step_ms"]) / 1e3), "unit": UNIT,
+                              "ms_per_step": sum(r["step_ms"]) / steps, "dtype": "f32+f64-refine",
+                              "gpu_launches": r["gpu_launches"],
+                              "roofline": roofline_of(km, "pair", f64_peak, hbm_peak, hbm_kind, sm_mhz, nsm,
+                                                      "c2_cube96"),
+                              "kernels": km}}
     finally:
         d["mesh"].close()
         del d
@@ -1007,8 +1134,11 @@ def recon_leg(Q, torch, n: int = 64, seed: int = 7, T: float = 2e-2, cap: int = 
     # method's own sensitivity to solve-level rounding at this size
     for name, prm in (("fp64", Q.qpat_default_params(precision=0, T=T, max_lsqr=cap)),
                       ("fp64_alt", Q.qpat_default_params(precision=0, T=T, max_lsqr=cap, poly_degree=0)),
-                      ("mixed", Q.qpat_default_params(precision=1, fp32_operator=1, T=T, max_lsqr=cap))):
-        warm = Q.qpat_default_params(precision=prm.precision, fp32_operator=1, max_lin=1, max_lsqr=2, fixed_counts=1)
+                      ("mixed", Q.qpat_default_params(precision=1, fp32_operator=1, T=T, max_lsqr=cap)),
+                      ("fp64_mg", Q.qpat_default_params(precision=0, T=T, max_lsqr=cap, multigrid=1)),
+                      ("mixed_mg", Q.qpat_default_params(precision=0, T=T, max_lsqr=cap, multigrid=2))):
+        warm = Q.qpat_default_params(precision=prm.precision, fp32_operator=1, max_lin=1, max_lsqr=2, fixed_counts=1,
+                                     multigrid=prm.multigrid)
         Q.qpat_reconstruct(mesh, flux, chi, sig, warm)         # warm-up (workspace, kernels)
         t0 = time.perf_counter()
         try:
@@ -1039,11 +1169,23 @@ def recon_leg(Q, torch, n: int = 64, seed: int = 7, T: float = 2e-2, cap: int = 
                       and abs(m["e_kappa"] - f["e_kappa"]) <= 0.01 * f["e_kappa"])
     # equal error: both errors within 1 % and the fields within 1e-6
     out["equal_error"] = bool(errs_equal and out["field_rel_diff"] <= 1e-6)
+    fl = None
     if "fp64_alt" in res:
         fl = max(rel(res["fp64_alt"][i], res["fp64"][i]) for i in range(2))
         out["fp64_vs_fp64_alt_field_rel_diff"] = fl
         # errors within 1 % and fields no further apart than two FP64 runs
         out["equal_error_within_fp64_sensitivity"] = bool(errs_equal and out["field_rel_diff"] <= max(1e-6, fl))
+    # the multigrid forms against the FP64 persistent-PCG form, by the same rules
+    out["forms_vs_fp64"] = {}
+    for name in ("mixed", "fp64_mg", "mixed_mg"):
+        if name not in res:
+            continue
+        g = out[name]
+        eq = bool(abs(g["e_mu"] - f["e_mu"]) <= 0.01 * f["e_mu"] and abs(g["e_kappa"] - f["e_kappa"]) <= 0.01 * f["e_kappa"])
+        diff = max(rel(res[name][i], res["fp64"][i]) for i in range(2))
+        out["forms_vs_fp64"][name] = {"speedup": f["wall_s"] / g["wall_s"], "field_rel_diff": diff,
+                                      "errors_within_1pct": eq,
+                                      "equal_error_within_fp64_sensitivity": bool(eq and diff <= max(1e-6, fl or 0.0))}
     mesh.close()
     return out
 
@@ -1354,6 +1496,11 @@ def main():
                     help="degree of the patch-local Chebyshev preconditioner of the K solves (library default)")
     ap.add_argument("--prior-poly", type=int, default=None,
                     help="the same for the M_delta solves (library default)")
+    ap.add_argument("--multigrid", type=int, default=1, choices=[0, 1, 2],
+                    help="preconditioner of the headline: 1 FP64 multigrid (default), 2 its K cycle in FP32, "
+                         "0 the persistent Jacobi / patch-local PCG")
+    ap.add_argument("--pcg-steps", type=int, default=10,
+                    help="timed steps of the persistent-PCG FP64 comparison arm (0 = skip)")
     ap.add_argument("--mixed-steps", type=int, default=10,
                     help="timed steps of the mixed-precision arm (0: skip)")
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")

@@ -147,7 +147,10 @@ typedef struct {
                               first such solve of a mesh (seconds at 2 M nodes),
                               its values on the device once per prepared operator. */
     int mg_degree;         /* Chebyshev degree of each multigrid smoothing, 1..8
-                              (0 = 2) */
+                              (default and 0: 1, i.e. one damped-Jacobi step
+                              before and after each coarse correction; on GB300
+                              every fine-level step is an FP64 sparse product,
+                              and degree 1 was the fastest measured) */
     double mg_ratio;       /* the smoothing polynomial targets [hi / mg_ratio, hi] of
                               the spectrum of D^-1 A, hi its Gershgorin bound
                               (> 1; 0 = 30) */
@@ -239,6 +242,12 @@ int64_t qpat_mesh_rhs_iterations(qpat_mesh_t mesh);
  * (up to max_levels); returns the number of levels (0 before the first
  * multigrid solve of that kind).  Not in the paper (diagnostics). */
 int qpat_mesh_multigrid_levels(qpat_mesh_t mesh, int prior, int64_t* rows, int max_levels);
+
+/* With timing on (qpat_mesh_set_timing): the summed device time (ms) and
+ * the count of the fine-level Chebyshev smoothing launches of the multigrid
+ * cycles since the last reset (the cycle's dominant kernel; each launch
+ * bracketed by CUDA events on its stream).  Not in the paper (diagnostics). */
+int qpat_mesh_multigrid_fine_time(qpat_mesh_t mesh, double* ms, int64_t* launches);
 
 /* When on, every PCG launch is bracketed by CUDA events recorded on the
  * stream it is launched on; qpat_mesh_pcg_time returns the summed device

@@ -63,7 +63,7 @@ struct SolveOpts {
     int poly_prior = 0;       // the same for M_delta
     long long spin_limit = 0; // grid-barrier polls before a timeout (0 = default)
     int multigrid = 0;        // 1: CG with the smoothed-aggregation V-cycle (FP64); 2: its K cycle in FP32
-    int mg_degree = 2;        // Chebyshev degree of each smoothing
+    int mg_degree = 1;        // Chebyshev degree of each smoothing
     double mg_ratio = 30.0;   // smoothing interval [hi / mg_ratio, hi] of D^-1 A
 };
 
@@ -99,6 +99,8 @@ struct qpat_mesh_s {
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     double pcg_ms = 0.0;
     qpat::AmgState* amg = nullptr;   // built on the first multigrid solve
+    double mg_fine_ms = 0.0;         // with timing on: fine-level smoothing launches of the multigrid cycle
+    int64_t mg_fine_launches = 0;
 };
 
 namespace qpat {

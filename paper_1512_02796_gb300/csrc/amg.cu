@@ -30,6 +30,7 @@ struct SellDev {
     const uint16_t* len = nullptr;
     int64_t entries = 0;
     int maxlen = 0;
+    int group = 1;  // lanes per row of the SpMV kernels (1, or 8 for long rows)
 };
 
 struct LevelDev {
@@ -44,6 +45,7 @@ struct LevelDev {
     const int64_t* ap_sptr = nullptr;
     const uint16_t* ap_slot = nullptr;
     int64_t ap_nnz = 0;
+    int ap_maxlen = 0;
     SellDev R;
     const int64_t* r_src = nullptr;
     const int64_t* g_ptr = nullptr;
@@ -100,30 +102,40 @@ __global__ void k_prolong(SellDev A, SellDev P, const uint16_t* a2p, const uint1
     }
 }
 
-// Row i of A P = sum over the entries a_ij of row i of A of a_ij (row j of P).
+// Row i of A P = sum over the entries a_ij of row i of A of a_ij (row j of
+// P), one warp per row and value set: the entries of row i of A are taken
+// one after the other and the lanes add a_ij P[j, :] into the row's shared
+// accumulator; the columns of one P row differ, so no two lanes meet on a
+// slot and every value is summed in the same order on every run.
 template <int NV>
 __global__ void k_ap(SellDev A, SellDev P, const int64_t* ap_ptr, const int64_t* ap_sptr, const uint16_t* ap_slot,
-                     int64_t ap_nnz, const double* v0, const double* v1, const double* p0, const double* p1,
-                     double* ap) {
-    const int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
-    if (i >= A.n) return;
+                     int64_t ap_nnz, int ap_maxlen, const double* v0, const double* v1, const double* p0,
+                     const double* p1, double* ap) {
+    extern __shared__ double acc_all[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t task = blockIdx.x * int64_t(blockDim.x >> 5) + warp;
+    if (task >= A.n * NV) return;
+    const int64_t i = task / NV;
+    const int v = int(task % NV);
+    double* acc = acc_all + int64_t(warp) * ap_maxlen;
+    const double* val = v == 0 ? v0 : v1;
+    const double* pv = v == 0 ? p0 : p1;
+    double* out = ap + v * ap_nnz;
+    const int64_t b = ap_ptr[i], cnt = ap_ptr[i + 1] - b;
+    for (int64_t t = lane; t < cnt; t += 32) acc[t] = 0.0;
+    __syncwarp();
+    int64_t o = ap_sptr[i];
     const int L = A.len[i];
-    const int64_t b = ap_ptr[i], e = ap_ptr[i + 1];
-#pragma unroll
-    for (int v = 0; v < NV; ++v) {
-        const double* val = v == 0 ? v0 : v1;
-        const double* pv = v == 0 ? p0 : p1;
-        double* out = ap + v * ap_nnz;
-        for (int64_t t = b; t < e; ++t) out[t] = 0.0;
-        int64_t o = ap_sptr[i];
-        for (int k = 0; k < L; ++k) {
-            const int64_t at = spos(A, i, k);
-            const int64_t j = A.col[at];
-            const double a = val[at];
-            const int LPj = P.len[j];
-            for (int kk = 0; kk < LPj; ++kk) out[b + ap_slot[o++]] += a * pv[spos(P, j, kk)];
-        }
+    for (int k = 0; k < L; ++k) {
+        const int64_t at = spos(A, i, k);
+        const int64_t j = A.col[at];
+        const double a = val[at];
+        const int LPj = P.len[j];
+        for (int kk = lane; kk < LPj; kk += 32) acc[ap_slot[o + kk]] += a * pv[spos(P, j, kk)];
+        o += LPj;
+        __syncwarp();
     }
+    for (int64_t t = lane; t < cnt; t += 32) out[b + t] = acc[t];
 }
 
 // R = P^T values gathered from P (padding 0).
@@ -262,14 +274,21 @@ __device__ __forceinline__ void stR(T* p, const T* v) {
     }
 }
 
-// acc = (A x)_i for the R columns of row i (NV = 2: column r uses value set r).
-template <typename T, int R, int NV>
-__device__ __forceinline__ void row_apply(const SellDev& A, const T* v0, const T* v1, const T* x, int64_t i, T* acc) {
+// acc = (A x)_i for the R columns of row i (NV = 2: column r uses value set
+// r).  G lanes share a row (G = 1: one thread per row; G = 8 for rows of a
+// few dozen entries and more): lane `sub` takes entries sub, sub + G, ...
+// and the group's sums are combined by a fixed xor tree, so every lane of
+// the group ends with the same, run-to-run identical, total.  Lanes past the
+// last row (valid = false) take part in the shuffles only.
+template <typename T, int R, int NV, int G>
+__device__ __forceinline__ void row_apply(const SellDev& A, const T* v0, const T* v1, const T* x, int64_t i, int sub,
+                                          bool valid, T* acc) {
 #pragma unroll
     for (int r = 0; r < R; ++r) acc[r] = T(0);
-    const int L = A.len[i];
-    int64_t at = A.ptr[i >> 5] * 32 + (i & 31);
-    for (int k = 0; k < L; ++k, at += 32) {
+    const int L = valid ? A.len[i] : 0;
+    const int64_t base = valid ? A.ptr[i >> 5] * 32 + (i & 31) : 0;
+    for (int k = sub; k < L; k += G) {
+        const int64_t at = base + int64_t(k) * 32;
         const int64_t c = A.col[at];
         T xv[R];
         ldR<T, R>(x + c * R, xv);
@@ -282,15 +301,25 @@ __device__ __forceinline__ void row_apply(const SellDev& A, const T* v0, const T
             acc[1] = fma(v1[at], xv[1], acc[1]);
         }
     }
+    if constexpr (G > 1) {
+#pragma unroll
+        for (int r = 0; r < R; ++r)
+#pragma unroll
+            for (int o = G / 2; o > 0; o >>= 1) acc[r] += __shfl_xor_sync(0xffffffffu, acc[r], o);
+    }
 }
 
 // MODE 0: y = A x;  1: y = b - A x;  2: y = b + A x (b may be y).
-template <typename T, int R, int NV, int MODE>
+template <typename T, int R, int NV, int MODE, int G>
 __global__ void __launch_bounds__(256) k_spmv(SellDev A, const T* v0, const T* v1, const T* x, const T* b, T* y) {
-    const int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
-    if (i >= A.n) return;
+    const int64_t t = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+    const int64_t i = t / G;
+    const int sub = int(t % G);
+    const bool valid = i < A.n;
+    if (G == 1 && !valid) return;
     T acc[R];
-    row_apply<T, R, NV>(A, v0, v1, x, i, acc);
+    row_apply<T, R, NV, G>(A, v0, v1, x, i, sub, valid, acc);
+    if (!valid || sub != 0) return;
     if constexpr (MODE != 0) {
         T bv[R];
         ldR<T, R>(b + i * R, bv);
@@ -308,11 +337,17 @@ __global__ void __launch_bounds__(256) k_spmv(SellDev A, const T* v0, const T* v
 // half-width of the interval, sigma = theta / delta, rho_0 = 1 / sigma,
 // rho_k = 1 / (2 sigma - rho_{k-1}); step 0: c_d = 0, c_r = 1 / theta;
 // step k: c_d = rho_k rho_{k-1}, c_r = 2 rho_k / delta.
-template <typename T, int R, int NV, bool FIRST>
+template <typename T, int R, int NV, bool FIRST, int G>
 __global__ void __launch_bounds__(256) k_cheb(SellDev A, const T* v0, const T* v1, const T* dinv, const double* hi,
                                               double ratio, int k, const T* x_in, T* x_out, T* d, const T* b) {
-    const int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
-    if (i >= A.n) return;
+    const int64_t t = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+    const int64_t i = t / G;
+    const int sub = int(t % G);
+    const bool valid = i < A.n;
+    if ((G == 1 || FIRST) && !valid) return;
+    T res[R];
+    if constexpr (!FIRST) row_apply<T, R, NV, G>(A, v0, v1, x_in, i, sub, valid, res);
+    if (!valid || sub != 0) return;
     T cd[NV], cr[NV];
 #pragma unroll
     for (int v = 0; v < NV; ++v) {
@@ -326,7 +361,7 @@ __global__ void __launch_bounds__(256) k_cheb(SellDev A, const T* v0, const T* v
         cd[v] = k == 0 ? T(0) : T(rho * rho_prev);
         cr[v] = k == 0 ? T(1.0 / theta) : T(2.0 * rho / delta);
     }
-    T res[R], bv[R], dv[R], xv[R];
+    T bv[R], dv[R], xv[R];
     ldR<T, R>(b + i * R, bv);
     if constexpr (FIRST) {
 #pragma unroll
@@ -335,7 +370,6 @@ __global__ void __launch_bounds__(256) k_cheb(SellDev A, const T* v0, const T* v
             xv[r] = T(0);
         }
     } else {
-        row_apply<T, R, NV>(A, v0, v1, x_in, i, res);
         ldR<T, R>(x_in + i * R, xv);
 #pragma unroll
         for (int r = 0; r < R; ++r) res[r] = bv[r] - res[r];
@@ -427,7 +461,7 @@ __global__ void __launch_bounds__(256) k_cg_init_x0(SellDev A, const double* v0,
     for (int q = 0; q < R; ++q) acc[q] = 0.0;
     for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < A.n; i += int64_t(gridDim.x) * blockDim.x) {
         double bv[R], av[R], xv[R];
-        row_apply<double, R, NV>(A, v0, v1, x0, i, av);
+        row_apply<double, R, NV, 1>(A, v0, v1, x0, i, 0, true, av);
         ldR<double, R>(b + i * R, bv);
         ldR<double, R>(x0 + i * R, xv);
 #pragma unroll
@@ -468,7 +502,7 @@ __global__ void __launch_bounds__(256) k_cg_apply(SellDev A, const double* v0, c
     for (int t = 0; t < R; ++t) acc[t] = 0.0;
     for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < A.n; i += int64_t(gridDim.x) * blockDim.x) {
         double qv[R], pv[R];
-        row_apply<double, R, NV>(A, v0, v1, p, i, qv);
+        row_apply<double, R, NV, 1>(A, v0, v1, p, i, 0, true, qv);
         ldR<double, R>(p + i * R, pv);
 #pragma unroll
         for (int t = 0; t < R; ++t) acc[t] = fma(pv[t], qv[t], acc[t]);
@@ -680,6 +714,9 @@ SellDev upload_sell(std::vector<void*>& list, const SellPattern& S, cudaError_t&
     d.len = upload(list, S.len, e);
     d.entries = S.entries();
     d.maxlen = S.maxlen;
+    int64_t stored = 0;
+    for (int64_t i = 0; i < S.n; ++i) stored += S.len[size_t(i)];
+    d.group = S.n > 0 && stored >= 24 * S.n ? 8 : 1;
     return d;
 }
 
@@ -707,6 +744,8 @@ int build_hier(qpat_mesh_s* M, int prior, AmgHierDev& H) {
             d.ap_sptr = upload(H.allocs, L.ap_sptr, e);
             d.ap_slot = upload(H.allocs, L.ap_slot, e);
             d.ap_nnz = int64_t(L.ap_col.size());
+            for (size_t i = 0; i + 1 < L.ap_ptr.size(); ++i)
+                d.ap_maxlen = std::max<int>(d.ap_maxlen, int(L.ap_ptr[i + 1] - L.ap_ptr[i]));
             d.R = upload_sell(H.allocs, L.R, e);
             d.r_src = upload(H.allocs, L.r_src, e);
             d.g_ptr = upload(H.allocs, L.g_ptr, e);
@@ -739,8 +778,15 @@ cudaError_t numeric_levels(const AmgHierDev& H, const OpState& st, AmgValues& V,
         k_prolong<NV><<<blocks_of(d.A.n), 256, 0, s>>>(d.A, d.P, d.a2p, d.pself, a0, a1, V.dinv[size_t(l)],
                                                         V.hi + 2 * l, Pv[0], Pv[1]);
         k_rvals<NV><<<blocks_of(d.R.entries), 256, 0, s>>>(d.R.entries, d.r_src, Pv[0], Pv[1], Rv[0], Rv[1]);
-        k_ap<NV><<<blocks_of(d.A.n, 128), 128, 0, s>>>(d.A, d.P, d.ap_ptr, d.ap_sptr, d.ap_slot, d.ap_nnz, a0, a1,
-                                                        Pv[0], Pv[1], V.AP[size_t(l)]);
+        {
+            int wpb = 8;
+            while (wpb > 1 && size_t(wpb) * size_t(d.ap_maxlen) * sizeof(double) > 96 * 1024) wpb >>= 1;
+            const size_t smem = size_t(wpb) * size_t(d.ap_maxlen) * sizeof(double);
+            if ((e = allow_smem(reinterpret_cast<const void*>(&k_ap<NV>), smem)) != cudaSuccess) return e;
+            k_ap<NV><<<blocks_of(d.A.n * NV, wpb), 32 * wpb, smem, s>>>(d.A, d.P, d.ap_ptr, d.ap_sptr, d.ap_slot,
+                                                                        d.ap_nnz, d.ap_maxlen, a0, a1, Pv[0], Pv[1],
+                                                                        V.AP[size_t(l)]);
+        }
         const LevelDev& c = H.lv[size_t(l + 1)];
         int wpb = 8;
         while (wpb > 1 && size_t(wpb) * size_t(c.A.maxlen) * sizeof(double) > 96 * 1024) wpb >>= 1;
@@ -853,6 +899,45 @@ int numeric(qpat_mesh_s* M, const AmgHierDev& H, const OpState& st, AmgValues& V
 
 namespace {
 
+// Optional CUDA-event timing of the fine-level smoothing launches (the
+// multigrid cycle's dominant kernel); the events of one cycle are read after
+// the next stream synchronisation of the CG loop.
+struct FineTimer {
+    bool on = false;
+    cudaStream_t s = nullptr;
+    std::vector<cudaEvent_t> ev;
+    int used = 0;
+    double ms = 0.0;
+    int64_t launches = 0;
+    void before() {
+        if (!on) return;
+        if (used + 2 > int(ev.size())) {
+            cudaEvent_t a, b;
+            cudaEventCreate(&a);
+            cudaEventCreate(&b);
+            ev.push_back(a);
+            ev.push_back(b);
+        }
+        cudaEventRecord(ev[size_t(used)], s);
+    }
+    void after() {
+        if (!on) return;
+        cudaEventRecord(ev[size_t(used + 1)], s);
+        used += 2;
+    }
+    void collect() {  // after a synchronisation of the stream
+        for (int k = 0; k < used; k += 2) {
+            float t = 0.f;
+            if (cudaEventElapsedTime(&t, ev[size_t(k)], ev[size_t(k + 1)]) == cudaSuccess) ms += t;
+            ++launches;
+        }
+        used = 0;
+    }
+    ~FineTimer() {
+        for (cudaEvent_t e : ev) cudaEventDestroy(e);
+    }
+};
+
 // One V-cycle x = B b on level l and below (pre-smoothing from x = 0,
 // residual, restriction, the coarser cycle, prolongation, post-smoothing
 // with the same polynomial: B is symmetric).
@@ -865,6 +950,7 @@ struct VCycle {
     int deg;
     double ratio;
     cudaStream_t s;
+    FineTimer* timer = nullptr;
 
     static constexpr bool F64 = std::is_same<T, double>::value;
     const T* av(int l, int v) const {
@@ -890,6 +976,24 @@ struct VCycle {
         else return V.inv32;
     }
 
+    template <int MODE>
+    void spmv(const SellDev& A, const T* a0, const T* a1, const T* x, const T* b, T* y) {
+        note_launch(1);
+        if (A.group == 8)
+            k_spmv<T, R, NV, MODE, 8><<<blocks_of(A.n * 8), 256, 0, s>>>(A, a0, a1, x, b, y);
+        else
+            k_spmv<T, R, NV, MODE, 1><<<blocks_of(A.n), 256, 0, s>>>(A, a0, a1, x, b, y);
+    }
+    void cheb(const SellDev& A, const T* a0, const T* a1, const T* di, const double* hi, int k, const T* x_in,
+              T* x_out, T* d, const T* b) {
+        note_launch(1);
+        if (A.group == 8)
+            k_cheb<T, R, NV, false, 8><<<blocks_of(A.n * 8), 256, 0, s>>>(A, a0, a1, di, hi, ratio, k, x_in, x_out, d,
+                                                                          b);
+        else
+            k_cheb<T, R, NV, false, 1><<<blocks_of(A.n), 256, 0, s>>>(A, a0, a1, di, hi, ratio, k, x_in, x_out, d, b);
+    }
+
     const T* run(int l, const T* b) {
         const LevelDev& d = H.lv[size_t(l)];
         const int L = int(H.lv.size());
@@ -901,27 +1005,27 @@ struct VCycle {
             k_dense_apply<T, R, NV><<<1, 256, 0, s>>>(int(d.A.n), inv(), b, x);
             return x;
         }
-        const int g = blocks_of(d.A.n);
         const double* hi = V.hi + 2 * l;
         const T *a0 = av(l, 0), *a1 = av(l, 1);
         note_launch(1);
-        k_cheb<T, R, NV, true><<<g, 256, 0, s>>>(d.A, a0, a1, dinv(l), hi, ratio, 0, nullptr, x, dd, b);
+        k_cheb<T, R, NV, true, 1><<<blocks_of(d.A.n), 256, 0, s>>>(d.A, a0, a1, dinv(l), hi, ratio, 0, nullptr, x,
+                                                                  dd, b);
         for (int k = 1; k < deg; ++k) {
-            note_launch(1);
-            k_cheb<T, R, NV, false><<<g, 256, 0, s>>>(d.A, a0, a1, dinv(l), hi, ratio, k, x, y, dd, b);
+            if (l == 0 && timer) timer->before();
+            cheb(d.A, a0, a1, dinv(l), hi, k, x, y, dd, b);
+            if (l == 0 && timer) timer->after();
             std::swap(x, y);
         }
         T* res = static_cast<T*>(W.r[size_t(l)]);
         T* bc = static_cast<T*>(W.b[size_t(l + 1)]);
-        note_launch(2);
-        k_spmv<T, R, NV, 1><<<g, 256, 0, s>>>(d.A, a0, a1, x, b, res);
-        k_spmv<T, R, NV, 0><<<blocks_of(d.R.n), 256, 0, s>>>(d.R, rv(l, 0), rv(l, 1), res, nullptr, bc);
+        spmv<1>(d.A, a0, a1, x, b, res);
+        spmv<0>(d.R, rv(l, 0), rv(l, 1), res, nullptr, bc);
         const T* xc = run(l + 1, bc);
-        note_launch(1);
-        k_spmv<T, R, NV, 2><<<g, 256, 0, s>>>(d.P, pv(l, 0), pv(l, 1), xc, x, x);
+        spmv<2>(d.P, pv(l, 0), pv(l, 1), xc, x, x);
         for (int k = 0; k < deg; ++k) {
-            note_launch(1);
-            k_cheb<T, R, NV, false><<<g, 256, 0, s>>>(d.A, a0, a1, dinv(l), hi, ratio, k, x, y, dd, b);
+            if (l == 0 && timer) timer->before();
+            cheb(d.A, a0, a1, dinv(l), hi, k, x, y, dd, b);
+            if (l == 0 && timer) timer->after();
             std::swap(x, y);
         }
         return x;
@@ -954,8 +1058,22 @@ int cg_solve(qpat_mesh_s* M, const OpState& st, const SolveOpts& so, const AmgHi
         if (x == cudaSuccess) x = cudaStreamSynchronize(s);
         return x;
     };
-    VCycle<double, R, NV> c64{H, V, W, st, deg, so.mg_ratio, s};
-    VCycle<float, R, NV> c32{H, V, W, st, deg, so.mg_ratio, s};
+    FineTimer timer;
+    timer.on = M->timing != 0;
+    timer.s = s;
+    VCycle<double, R, NV> c64{H, V, W, st, deg, so.mg_ratio, s, &timer};
+    VCycle<float, R, NV> c32{H, V, W, st, deg, so.mg_ratio, s, &timer};
+    struct Flush {  // fine-level smoothing time into the mesh's counters, on every exit
+        FineTimer& t;
+        qpat_mesh_s* M;
+        ~Flush() {
+            if (!t.on) return;
+            cudaStreamSynchronize(t.s);
+            t.collect();
+            M->mg_fine_ms += t.ms;
+            M->mg_fine_launches += t.launches;
+        }
+    } flush{timer, M};
     auto precond = [&](int it) -> const double* {
         if (!f32) return c64.run(0, C.r);
         float* b0 = static_cast<float*>(W.b[0]);
@@ -993,6 +1111,7 @@ int cg_solve(qpat_mesh_s* M, const OpState& st, const SolveOpts& so, const AmgHi
         k_cg_update<R><<<G, 256, 0, s>>>(n, C.alpha, C.p, C.q, X, C.r, C.part);
         k_cg_check<R><<<1, 32 * R, 0, s>>>(C.part, G, C.bb, rtol2, C.active, C.rr, C.ctl);
         if ((e = read_ctl()) != cudaSuccess) return cuda_fail(e, "multigrid cg");
+        timer.collect();
         *iters = it;
         if (hc[0] != QPAT_OK) return fail(hc[0], "multigrid cg: breakdown (p.Ap <= 0 or not finite)");
         if (hc[1] == 0) return QPAT_OK;

@@ -160,7 +160,7 @@ SolveOpts solve_opts(const qpat_params* prm) {
     so.poly_prior = p->prior_poly_degree;
     so.spin_limit = p->barrier_spin_limit > 0 ? p->barrier_spin_limit : 0;
     so.multigrid = p->multigrid;
-    so.mg_degree = p->mg_degree > 0 ? p->mg_degree : 2;
+    so.mg_degree = p->mg_degree > 0 ? p->mg_degree : 1;
     so.mg_ratio = p->mg_ratio > 0 ? p->mg_ratio : 30.0;
     return so;
 }

@@ -94,6 +94,7 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
         "qpat_mesh_fp64_fallbacks": (ctypes.c_int64, [vp]),
         "qpat_mesh_rhs_iterations": (ctypes.c_int64, [vp]),
         "qpat_mesh_multigrid_levels": (ctypes.c_int, [vp, ctypes.c_int, _c_int64_p, ctypes.c_int]),
+        "qpat_mesh_multigrid_fine_time": (ctypes.c_int, [vp, ctypes.POINTER(ctypes.c_double), _c_int64_p]),
         "qpat_multigrid_host_info": (ctypes.c_int, [_c_double_p, ctypes.c_int64, _c_int32_p, ctypes.c_int64, ctypes.c_int,
                                                     ctypes.c_int, _c_int64_p, ctypes.c_int]),
         "qpat_mesh_reset_stats": (ctypes.c_int, [vp]),
@@ -177,7 +178,7 @@ def exported_names() -> Sequence[str]:
         "qpat_mesh_host_info", "qpat_mesh_num_nodes", "qpat_mesh_num_tets", "qpat_mesh_num_faces", "qpat_mesh_num_patches",
         "qpat_mesh_num_entries", "qpat_mesh_num_prior_entries", "qpat_mesh_num_local_entries",
         "qpat_mesh_faces", "qpat_mesh_permutation", "qpat_mesh_stats", "qpat_mesh_fp64_fallbacks",
-        "qpat_mesh_rhs_iterations", "qpat_mesh_multigrid_levels", "qpat_multigrid_host_info", "qpat_mesh_reset_stats",
+        "qpat_mesh_rhs_iterations", "qpat_mesh_multigrid_levels", "qpat_mesh_multigrid_fine_time", "qpat_multigrid_host_info", "qpat_mesh_reset_stats",
         "qpat_mesh_set_timing", "qpat_mesh_pcg_time",
         "qpat_flux_patch", "qpat_flux_side", "qpat_apply_K_dev", "qpat_forward", "qpat_forward_dev", "qpat_forward_noalloc_dev",
         "qpat_forward_guess_dev",
@@ -400,6 +401,14 @@ class Mesh:
 
     def reset_stats(self):
         _check(load().qpat_mesh_reset_stats(self.handle))
+
+    def multigrid_fine_time(self):
+        """(ms, launches) of the fine-level smoothing launches of the
+        multigrid cycles since the last reset (timing on)."""
+        ms = ctypes.c_double()
+        n = np.zeros(1, dtype=np.int64)
+        _check(load().qpat_mesh_multigrid_fine_time(self.handle, ctypes.byref(ms), n.ctypes.data_as(_c_int64_p)))
+        return float(ms.value), int(n[0])
 
     def multigrid_levels(self, prior: bool = False) -> list:
         """Rows of each level of the multigrid hierarchy of the K (or prior)

@@ -146,7 +146,7 @@ def test_params_struct_layout_matches_the_header():
     assert all(b == 0xAB for b in buf[n:])
     p = Q.qpat_default_params()
     assert p.lsqr_reorth == 1 and p.barrier_spin_limit == 0
-    assert p.multigrid == 0 and p.mg_degree == 2 and p.mg_ratio == 30.0
+    assert p.multigrid == 0 and p.mg_degree == 1 and p.mg_ratio == 30.0
 
 
 def test_host_output_arrays_are_checked_before_any_call():

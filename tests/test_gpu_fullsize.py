@@ -48,9 +48,13 @@ def big(request):
     dev = torch.device("cuda")
     c.T = lambda a: torch.tensor(np.ascontiguousarray(a), device=dev)
     c.phi = smooth_phi(c.xyz, c.K, c.cfg.L, 5)
-    # the bench's FP64 arm runs its K solves with Jacobi; the mixed arm the library default
+    # the bench's headline: FP64 CG with the FP64 multigrid cycle ("mg1"); its
+    # other arms: the K cycle in FP32 ("mg2"), the persistent FP64 PCG with
+    # Jacobi K solves (0) and FP32 PCG inside FP64 refinement (1)
     c.prm = {0: Q.qpat_default_params(precision=0, poly_degree=0),
-             1: Q.qpat_default_params(precision=1, fp32_operator=1)}
+             1: Q.qpat_default_params(precision=1, fp32_operator=1),
+             "mg1": Q.qpat_default_params(precision=0, multigrid=1),
+             "mg2": Q.qpat_default_params(precision=0, multigrid=2)}
     yield c
     c.lib.close()
 
@@ -64,7 +68,7 @@ def test_apply_full_size(big):
     assert rel(y.cpu().numpy(), big.Kmat @ x) < 1e-13
 
 
-@pytest.mark.parametrize("precision", [0, 1])
+@pytest.mark.parametrize("precision", [0, 1, "mg1", "mg2"])
 def test_forward_residual_full_size(big, precision):
     dev = "cuda"
     phi = torch.empty((big.K, big.N), dtype=torch.float64, device=dev)
@@ -78,12 +82,13 @@ def test_forward_residual_full_size(big, precision):
     np.testing.assert_allclose(h.cpu().numpy(), big.mu * ph, rtol=1e-15)
 
 
-def test_jvp_solve_residual_full_size(big):
+@pytest.mark.parametrize("precision", [0, "mg1"])
+def test_jvp_solve_residual_full_size(big, precision):
     rng = np.random.default_rng(2)
     s = 0.1 * rng.standard_normal(2 * big.N)
     N = big.N
     out = torch.empty((big.K, N), dtype=torch.float64, device="cuda")
-    Q.qpat_jvp_dev(big.lib, big.T(big.kappa), big.T(big.mu), big.T(big.phi), None, big.T(s), out, big.prm[0])
+    Q.qpat_jvp_dev(big.lib, big.T(big.kappa), big.T(big.mu), big.T(big.phi), None, big.T(s), out, big.prm[precision])
     torch.cuda.synchronize()
     Js = out.cpu().numpy()
     for k in sorted({0, big.K - 1}):
@@ -93,7 +98,7 @@ def test_jvp_solve_residual_full_size(big):
         assert np.linalg.norm(big.Kmat @ x - rhs) / np.linalg.norm(rhs) < 1e-11
 
 
-@pytest.mark.parametrize("precision", [0, 1])
+@pytest.mark.parametrize("precision", [0, 1, "mg1", "mg2"])
 def test_pair_adjoint_identity_full_size(big, precision):
     rng = np.random.default_rng(3)
     N = big.N
@@ -139,3 +144,26 @@ def test_prior_solve_full_size(big, deg):
         (x0, it0), (x2, it2) = big.prior_x[0], big.prior_x[2]
         assert rel(x2, x0) < 1e-8
         assert it2 < 0.7 * it0   # the patch-local polynomial roughly halves the count (64^3: 1400 -> 680)
+
+
+def test_prior_solve_multigrid_full_size(big):
+    """The M_delta solve of the bench's headline (multigrid cycle, FP64):
+    normwise backward error against the oracle's M_delta, and the solution
+    of the persistent degree-2 PCG within the conditioning of the solve."""
+    N = big.N
+    kt = np.log(big.kappa / np.median(big.kappa))
+    mt = np.log(big.mu / np.median(big.mu))
+    rhs = np.random.default_rng(123).standard_normal(2 * N)
+    out = torch.empty(2 * N, dtype=torch.float64, device="cuda")
+    prm = big.prm["mg1"]
+    Q.qpat_prior_solve_dev(big.lib, big.T(kt), big.T(mt), big.T(rhs), out, prm)
+    torch.cuda.synchronize()
+    x = out.cpu().numpy()
+    Md = O.prior_matrix(big.om, kt, mt, prm.T, prm.b_over_a, prm.delta)
+    Anorm = abs(Md).sum(axis=0).max()
+    eta = np.linalg.norm(Md @ x - rhs, 1) / (Anorm * np.linalg.norm(x, 1) + np.linalg.norm(rhs, 1))
+    assert eta < 1e-13
+    ref = torch.empty_like(out)
+    Q.qpat_prior_solve_dev(big.lib, big.T(kt), big.T(mt), big.T(rhs), ref, Q.qpat_default_params())
+    torch.cuda.synchronize()
+    assert rel(x, ref.cpu().numpy()) < 1e-8
