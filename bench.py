@@ -1451,21 +1451,28 @@ def run_reference(args):
 
 
 def run_profile_case(args):
-    """Fixed sequence for ncu captures of the PCG kernels on the workload:
-    the set-up forward solve, one FP64 pair (the bench's FP64 arm: Jacobi K
-    solves), one M_delta solve and one mixed-precision pair.  No timing;
-    prints the PCG launches and iterations of each call (deterministic, so a
-    plain run gives the per-launch iterations of a captured launch)."""
+    """Fixed sequence for ncu captures of the solver kernels on the workload:
+    the set-up forward solve; the bench headline's pair and M_delta solve
+    (FP64 multigrid-preconditioned CG) and the pair with the FP32 cycle; then
+    one FP64 pair of the persistent PCG (Jacobi K solves), one M_delta solve
+    and one mixed-precision pair.  No timing; prints the launches and
+    iterations of each call and the multigrid levels (deterministic, so a
+    plain run locates a captured launch)."""
     import torch
     import paper_1512_02796_gb300 as Q
     d = setup_problem(Q, torch, args.workload, args.patch_nodes)
     mesh = d["mesh"]
-    calls = []
-    for name, prm in (("pair_fp64", Q.qpat_default_params(precision=0, poly_degree=0)),
+    torch.cuda.synchronize()
+    calls = [{"call": "setup", "lib_launches": Q.qpat_launch_count()}]
+    for name, prm in (("pair_mg64", Q.qpat_default_params(precision=0, multigrid=1)),
+                      ("prior_mg64", Q.qpat_default_params(precision=0, multigrid=1)),
+                      ("pair_mg32", Q.qpat_default_params(precision=0, multigrid=2)),
+                      ("pair_fp64", Q.qpat_default_params(precision=0, poly_degree=0)),
                       ("prior_fp64", Q.qpat_default_params(precision=0)),
                       ("pair_fp32", Q.qpat_default_params(precision=1, fp32_operator=1))):
         mesh.reset_stats()
-        if name == "prior_fp64":
+        n0 = Q.qpat_launch_count()
+        if name.startswith("prior"):
             Q.qpat_prior_solve_dev(mesh, d["kt"], d["mt"], d["prior_rhs"], d["op"], prm)
         else:
             Q.qpat_jvp_vjp_pair_dev(mesh, d["kappa"], d["mu"], d["phi"], d["w"], d["s"], d["t"], d["oj"],
@@ -1473,9 +1480,10 @@ def run_profile_case(args):
         torch.cuda.synchronize()
         st = mesh.stats()
         calls.append({"call": name, "launches": st["launches"], "pcg_iters": st["pcg_iters"],
-                      "rhs_iters": st["rhs_iters"]})
+                      "rhs_iters": st["rhs_iters"], "lib_launches": Q.qpat_launch_count() - n0})
+    levels = {"K": mesh.multigrid_levels(), "M_delta": mesh.multigrid_levels(True)}
     mesh.close()
-    print(json.dumps({"profile_case": args.workload, "calls": calls}), flush=True)
+    print(json.dumps({"profile_case": args.workload, "calls": calls, "multigrid_levels": levels}), flush=True)
 
 
 def main():

@@ -11,6 +11,7 @@
 #include <algorithm>
 #include <array>
 #include <cmath>
+#include <cstdio>
 #include <map>
 #include <memory>
 #include <mutex>
@@ -30,7 +31,7 @@ struct SellDev {
     const uint16_t* len = nullptr;
     int64_t entries = 0;
     int maxlen = 0;
-    int group = 1;  // lanes per row of the SpMV kernels (1, or 8 for long rows)
+    int rowmajor = 0;  // layout (see SellPattern); row-major rows are applied by 8 lanes each
 };
 
 struct LevelDev {
@@ -55,7 +56,7 @@ struct LevelDev {
 namespace {
 
 __device__ __forceinline__ int64_t spos(const SellDev& S, int64_t row, int k) {
-    return (S.ptr[row >> 5] + k) * 32 + (row & 31);
+    return S.rowmajor ? S.ptr[row] + k : (S.ptr[row >> 5] + k) * 32 + (row & 31);
 }
 
 // ---------------------------------------------------------------- set-up kernels
@@ -286,9 +287,10 @@ __device__ __forceinline__ void row_apply(const SellDev& A, const T* v0, const T
 #pragma unroll
     for (int r = 0; r < R; ++r) acc[r] = T(0);
     const int L = valid ? A.len[i] : 0;
-    const int64_t base = valid ? A.ptr[i >> 5] * 32 + (i & 31) : 0;
+    const int64_t base = !valid ? 0 : A.rowmajor ? A.ptr[i] : A.ptr[i >> 5] * 32 + (i & 31);
+    const int64_t stride = A.rowmajor ? 1 : 32;
     for (int k = sub; k < L; k += G) {
-        const int64_t at = base + int64_t(k) * 32;
+        const int64_t at = base + int64_t(k) * stride;
         const int64_t c = A.col[at];
         T xv[R];
         ldR<T, R>(x + c * R, xv);
@@ -475,9 +477,15 @@ __global__ void __launch_bounds__(256) k_cg_init_x0(SellDev A, const double* v0,
     block_partials<R>(acc, part);
 }
 
+// Control words of a CG solve (int ctl[]): [0] status, [1] right-hand sides
+// still running, [2] iterations done, [3] 1 before the first direction,
+// [4] iteration cap; the per-RHS running flags follow at ctl + kCtlActive.
+constexpr int kCtlActive = 8;
+
 // bb = totals; a right-hand side with b = 0 is solved by x = 0 and never runs
 template <int R>
-__global__ void k_cg_start(const double* part, int G, double* bb, int* active, int* ctl) {
+__global__ void k_cg_start(const double* part, int G, double* bb, int* ctl) {
+    int* active = ctl + kCtlActive;
     const int r = threadIdx.x >> 5;
     const double t = total_of(part, G, R, r);
     if ((threadIdx.x & 31) == 0) {
@@ -490,6 +498,8 @@ __global__ void k_cg_start(const double* part, int G, double* bb, int* active, i
         int c = 0;
         for (int q = 0; q < R; ++q) c += active[q];
         ctl[1] = c;
+        ctl[2] = 0;
+        ctl[3] = 1;
     }
 }
 
@@ -513,7 +523,8 @@ __global__ void __launch_bounds__(256) k_cg_apply(SellDev A, const double* v0, c
 
 // alpha = r.z / p.q on the running right-hand sides (0 on the others)
 template <int R>
-__global__ void k_cg_alpha(const double* part, int G, const double* rz, const int* active, double* alpha, int* ctl) {
+__global__ void k_cg_alpha(const double* part, int G, const double* rz, double* alpha, int* ctl) {
+    const int* active = ctl + kCtlActive;
     const int r = threadIdx.x >> 5;
     const double pq = total_of(part, G, R, r);
     if ((threadIdx.x & 31) == 0) {
@@ -529,49 +540,92 @@ __global__ void k_cg_alpha(const double* part, int G, const double* rz, const in
 }
 
 // x += alpha p, r -= alpha q, partials of r.r
+// The vector passes of the CG give each node's R values to R / C threads
+// of C right-hand sides each (C = 8 for R = 16): fewer live registers per
+// thread, more loads in flight for these memory-bound passes.
+template <int R>
+constexpr int kChunk = R > 8 ? 8 : R;
+
+// Block totals of per-thread partials over C right-hand sides when thread t
+// holds chunk t % (R / C): an xor tree over the lanes of the same chunk,
+// then the warps in order; part[blockIdx * R * NQ + q * R + r] for the NQ
+// quantities of acc (acc[q * C + j] belongs to right-hand side chunk * C + j).
+template <int R, int NQ>
+__device__ __forceinline__ void chunk_partials(const double* acc, double* part) {
+    constexpr int C = kChunk<R>, NCH = R / C;
+    __shared__ double red[8][NQ * R];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+#pragma unroll
+    for (int q = 0; q < NQ; ++q)
+#pragma unroll
+        for (int j = 0; j < C; ++j) {
+            double v = acc[q * C + j];
+#pragma unroll
+            for (int o = 16; o >= NCH; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+            if (lane < NCH) red[warp][q * R + lane * C + j] = v;
+        }
+    __syncthreads();
+    if (threadIdx.x < NQ * R) {
+        double t = 0.0;
+        for (int w = 0; w < int(blockDim.x >> 5); ++w) t += red[w][threadIdx.x];
+        part[int64_t(blockIdx.x) * NQ * R + threadIdx.x] = t;
+    }
+}
+
 template <int R>
 __global__ void __launch_bounds__(256) k_cg_update(int64_t n, const double* alpha, const double* p, const double* q,
                                                    double* x, double* r, double* part) {
-    double al[R], acc[R];
+    constexpr int C = kChunk<R>, NCH = R / C;
+    const int c0 = int(threadIdx.x % NCH) * C;
+    double al[C], acc[C];
 #pragma unroll
-    for (int t = 0; t < R; ++t) {
-        al[t] = alpha[t];
+    for (int t = 0; t < C; ++t) {
+        al[t] = alpha[c0 + t];
         acc[t] = 0.0;
     }
-    for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x) {
-        double pv[R], qv[R], xv[R], rv[R];
-        ldR<double, R>(p + i * R, pv);
-        ldR<double, R>(q + i * R, qv);
-        ldR<double, R>(x + i * R, xv);
-        ldR<double, R>(r + i * R, rv);
+    for (int64_t g = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; g < n * NCH;
+         g += int64_t(gridDim.x) * blockDim.x) {
+        const int64_t o = (g / NCH) * R + c0;
+        double pv[C], qv[C], xv[C], rv[C];
+        ldR<double, C>(p + o, pv);
+        ldR<double, C>(q + o, qv);
+        ldR<double, C>(x + o, xv);
+        ldR<double, C>(r + o, rv);
 #pragma unroll
-        for (int t = 0; t < R; ++t) {
+        for (int t = 0; t < C; ++t) {
             xv[t] = fma(al[t], pv[t], xv[t]);
             rv[t] = fma(-al[t], qv[t], rv[t]);
             acc[t] = fma(rv[t], rv[t], acc[t]);
         }
-        stR<double, R>(x + i * R, xv);
-        stR<double, R>(r + i * R, rv);
+        stR<double, C>(x + o, xv);
+        stR<double, C>(r + o, rv);
     }
-    block_partials<R>(acc, part);
+    chunk_partials<R, 1>(acc, part);
 }
 
-// a right-hand side stops once |r| <= rtol |b|
+// a right-hand side stops once |r| <= rtol |b|; one more iteration is done.
+// Inside a graph (use_graph) the kernel also sets the loop's condition: go
+// on while some right-hand side runs, the status is clean and the cap is not
+// reached (reaching it with a running right-hand side is QPAT_ENOCONV).
 template <int R>
-__global__ void k_cg_check(const double* part, int G, const double* bb, double rtol2, int* active, double* rr,
-                           int* ctl) {
+__global__ void k_cg_check(const double* part, int G, const double* bb, const double* rtol2, double* rr, int* ctl,
+                           cudaGraphConditionalHandle cond, int use_graph) {
+    int* active = ctl + kCtlActive;
     const int r = threadIdx.x >> 5;
     const double t = total_of(part, G, R, r);
     if ((threadIdx.x & 31) == 0) {
         rr[r] = t;
         if (!isfinite(t)) atomicExch(ctl, int(QPAT_EBREAKDOWN));
-        if (active[r] && t <= rtol2 * bb[r]) active[r] = 0;
+        if (active[r] && t <= *rtol2 * bb[r]) active[r] = 0;
     }
     __syncthreads();
     if (threadIdx.x == 0) {
         int c = 0;
         for (int q = 0; q < R; ++q) c += active[q];
         ctl[1] = c;
+        const int it = ++ctl[2];
+        if (c > 0 && it >= ctl[4] && ctl[0] == QPAT_OK) ctl[0] = QPAT_ENOCONV;
+        if (use_graph) cudaGraphSetConditional(cond, (c > 0 && ctl[0] == QPAT_OK) ? 1u : 0u);
     }
 }
 
@@ -579,32 +633,36 @@ __global__ void k_cg_check(const double* part, int G, const double* bb, double r
 template <int R, bool FLEX>
 __global__ void __launch_bounds__(256) k_cg_dots(int64_t n, const double* r, const double* z, const double* zo,
                                                  double* part) {
-    constexpr int Q = FLEX ? 2 * R : R;
-    double acc[Q];
+    constexpr int C = kChunk<R>, NCH = R / C, NQ = FLEX ? 2 : 1;
+    const int c0 = int(threadIdx.x % NCH) * C;
+    double acc[NQ * C];
 #pragma unroll
-    for (int t = 0; t < Q; ++t) acc[t] = 0.0;
-    for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x) {
-        double rv[R], zv[R];
-        ldR<double, R>(r + i * R, rv);
-        ldR<double, R>(z + i * R, zv);
+    for (int t = 0; t < NQ * C; ++t) acc[t] = 0.0;
+    for (int64_t g = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; g < n * NCH;
+         g += int64_t(gridDim.x) * blockDim.x) {
+        const int64_t o = (g / NCH) * R + c0;
+        double rv[C], zv[C];
+        ldR<double, C>(r + o, rv);
+        ldR<double, C>(z + o, zv);
 #pragma unroll
-        for (int t = 0; t < R; ++t) acc[t] = fma(rv[t], zv[t], acc[t]);
+        for (int t = 0; t < C; ++t) acc[t] = fma(rv[t], zv[t], acc[t]);
         if constexpr (FLEX) {
-            ldR<double, R>(zo + i * R, zv);
+            ldR<double, C>(zo + o, zv);
 #pragma unroll
-            for (int t = 0; t < R; ++t) acc[R + t] = fma(rv[t], zv[t], acc[R + t]);
+            for (int t = 0; t < C; ++t) acc[C + t] = fma(rv[t], zv[t], acc[C + t]);
         }
     }
-    block_partials<Q>(acc, part);
+    chunk_partials<R, NQ>(acc, part);
 }
 
 // beta = r.z / (r.z)_old (FLEX: (r.z - r.z_old) / (r.z)_old, the form that
 // tolerates a preconditioner that varies slightly between applications);
-// FIRST: beta = 0.  rz <- r.z.
+// 0 before the first direction (ctl[3], cleared here).  rz <- r.z.
 template <int R, bool FLEX>
-__global__ void k_cg_beta(const double* part, int G, int first, double* rz, const int* active, double* beta,
-                          int* ctl) {
+__global__ void k_cg_beta(const double* part, int G, double* rz, double* beta, int* ctl) {
     constexpr int Q = FLEX ? 2 * R : R;
+    const int* active = ctl + kCtlActive;
+    const int first = ctl[3];
     const int r = threadIdx.x >> 5;
     const double t = total_of(part, G, Q, r);
     const double to = FLEX ? total_of(part, G, Q, R + r) : 0.0;
@@ -615,21 +673,29 @@ __global__ void k_cg_beta(const double* part, int G, int first, double* rz, cons
         beta[r] = b;
         rz[r] = t;
     }
+    __syncthreads();
+    if (threadIdx.x == 0) ctl[3] = 0;
 }
 
-// p = z + beta p
-template <int R>
-__global__ void __launch_bounds__(256) k_cg_dir(int64_t n, const double* beta, const double* z, double* p) {
-    double be[R];
+// p = z + beta p (FLEX: and z_old = z for the next beta)
+template <int R, bool FLEX>
+__global__ void __launch_bounds__(256) k_cg_dir(int64_t n, const double* beta, const double* z, double* p,
+                                                double* zo) {
+    constexpr int C = kChunk<R>, NCH = R / C;
+    const int c0 = int(threadIdx.x % NCH) * C;
+    double be[C];
 #pragma unroll
-    for (int t = 0; t < R; ++t) be[t] = beta[t];
-    for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x) {
-        double zv[R], pv[R];
-        ldR<double, R>(z + i * R, zv);
-        ldR<double, R>(p + i * R, pv);
+    for (int t = 0; t < C; ++t) be[t] = beta[c0 + t];
+    for (int64_t g = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; g < n * NCH;
+         g += int64_t(gridDim.x) * blockDim.x) {
+        const int64_t o = (g / NCH) * R + c0;
+        double zv[C], pv[C];
+        ldR<double, C>(z + o, zv);
+        ldR<double, C>(p + o, pv);
 #pragma unroll
-        for (int t = 0; t < R; ++t) pv[t] = fma(be[t], pv[t], zv[t]);
-        stR<double, R>(p + i * R, pv);
+        for (int t = 0; t < C; ++t) pv[t] = fma(be[t], pv[t], zv[t]);
+        stR<double, C>(p + o, pv);
+        if constexpr (FLEX) stR<double, C>(zo + o, zv);
     }
 }
 
@@ -673,11 +739,19 @@ struct AmgVecs {
 };
 
 struct AmgCg {
-    double *r = nullptr, *p = nullptr, *q = nullptr, *z[2] = {nullptr, nullptr}, *part = nullptr;
-    double *bb = nullptr, *rz = nullptr, *alpha = nullptr, *beta = nullptr, *rr = nullptr;
-    int* ctl = nullptr;     // [0] status, [1] right-hand sides still running
-    int* active = nullptr;  // 16
+    double *x = nullptr, *r = nullptr, *p = nullptr, *q = nullptr, *z = nullptr, *zo = nullptr, *part = nullptr;
+    double *bb = nullptr, *rz = nullptr, *alpha = nullptr, *beta = nullptr, *rr = nullptr, *rtol2 = nullptr;
+    int* ctl = nullptr;  // control words (see k_cg_start)
     std::vector<void*> allocs;
+};
+
+// One CG iteration captured once as the body of a graph "while" node, per
+// operator values, right-hand-side count and cycle settings; the check
+// kernel of the body sets the loop condition on the device.
+struct AmgGraph {
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    int body_kernels = 0;
 };
 
 struct AmgState {
@@ -685,6 +759,8 @@ struct AmgState {
     std::map<const void*, AmgValues> vals;
     std::map<std::pair<int, int>, AmgVecs> vecs;  // (pattern * 64 + R, FP32 V-cycle)
     std::map<int, AmgCg> cg;                       // R
+    std::map<std::string, AmgGraph> graphs;
+    cudaStream_t capture = nullptr;                // a non-default stream to capture on
 };
 
 namespace {
@@ -714,9 +790,7 @@ SellDev upload_sell(std::vector<void*>& list, const SellPattern& S, cudaError_t&
     d.len = upload(list, S.len, e);
     d.entries = S.entries();
     d.maxlen = S.maxlen;
-    int64_t stored = 0;
-    for (int64_t i = 0; i < S.n; ++i) stored += S.len[size_t(i)];
-    d.group = S.n > 0 && stored >= 24 * S.n ? 8 : 1;
+    d.rowmajor = S.rowmajor ? 1 : 0;
     return d;
 }
 
@@ -979,7 +1053,7 @@ struct VCycle {
     template <int MODE>
     void spmv(const SellDev& A, const T* a0, const T* a1, const T* x, const T* b, T* y) {
         note_launch(1);
-        if (A.group == 8)
+        if (A.rowmajor)
             k_spmv<T, R, NV, MODE, 8><<<blocks_of(A.n * 8), 256, 0, s>>>(A, a0, a1, x, b, y);
         else
             k_spmv<T, R, NV, MODE, 1><<<blocks_of(A.n), 256, 0, s>>>(A, a0, a1, x, b, y);
@@ -987,7 +1061,7 @@ struct VCycle {
     void cheb(const SellDev& A, const T* a0, const T* a1, const T* di, const double* hi, int k, const T* x_in,
               T* x_out, T* d, const T* b) {
         note_launch(1);
-        if (A.group == 8)
+        if (A.rowmajor)
             k_cheb<T, R, NV, false, 8><<<blocks_of(A.n * 8), 256, 0, s>>>(A, a0, a1, di, hi, ratio, k, x_in, x_out, d,
                                                                           b);
         else
@@ -1032,114 +1106,173 @@ struct VCycle {
     }
 };
 
-template <int R, bool FLEX>
-void launch_dots_beta(const AmgCg& C, int64_t n, int G, const double* z, const double* zo, int first,
-                      cudaStream_t s) {
-    note_launch(2);
-    k_cg_dots<R, FLEX><<<G, 256, 0, s>>>(n, C.r, z, zo, C.part);
-    k_cg_beta<R, FLEX><<<1, 32 * R, 0, s>>>(C.part, G, first, C.rz, C.active, C.beta, C.ctl);
-}
-
 // Conjugate gradients on the fine operator with one V-cycle per iteration
-// as the preconditioner; X = 0 to start, each right-hand side stops at
+// as the preconditioner; X0 (or 0) to start, each right-hand side stops at
 // |r| <= rtol |b| (the recursive residual, as the persistent PCG does).
+// After the start, every iteration is
+//   z = B r, beta = r.z / (r.z)_old, p = z + beta p, q = A p,
+//   alpha = r.z / p.q, x += alpha p, r -= alpha q, check,
+// launched from the host one kernel at a time when the fine-level smoothing
+// is being timed, and otherwise replayed from a captured graph whose
+// "while" node runs on the device until the check ends it (no host round
+// trip per iteration).  Both forms launch the same kernels on the same data.
 template <int R, int NV>
-int cg_solve(qpat_mesh_s* M, const OpState& st, const SolveOpts& so, const AmgHierDev& H, const AmgValues& V,
-             bool f32, AmgVecs& W, AmgCg& C, const double* B, double* X, const double* X0, cudaStream_t s,
-             int* iters) {
-    const LevelDev& d0 = H.lv[0];
-    const int64_t n = d0.A.n;
-    const int G = int(std::min<int64_t>(blocks_of(n), kRedMaxGrid));
-    const int deg = std::max(1, so.mg_degree);
-    int* hc = reinterpret_cast<int*>(M->host_scratch + 240);
-    cudaError_t e = cudaSuccess;
-    auto read_ctl = [&]() -> cudaError_t {
-        cudaError_t x = cudaMemcpyAsync(hc, C.ctl, 2 * sizeof(int), cudaMemcpyDeviceToHost, s);
-        if (x == cudaSuccess) x = cudaStreamSynchronize(s);
-        return x;
-    };
-    FineTimer timer;
-    timer.on = M->timing != 0;
-    timer.s = s;
-    VCycle<double, R, NV> c64{H, V, W, st, deg, so.mg_ratio, s, &timer};
-    VCycle<float, R, NV> c32{H, V, W, st, deg, so.mg_ratio, s, &timer};
-    struct Flush {  // fine-level smoothing time into the mesh's counters, on every exit
-        FineTimer& t;
-        qpat_mesh_s* M;
-        ~Flush() {
-            if (!t.on) return;
-            cudaStreamSynchronize(t.s);
-            t.collect();
-            M->mg_fine_ms += t.ms;
-            M->mg_fine_launches += t.launches;
-        }
-    } flush{timer, M};
-    auto precond = [&](int it) -> const double* {
-        if (!f32) return c64.run(0, C.r);
-        float* b0 = static_cast<float*>(W.b[0]);
-        note_launch(1);
-        k_d2f_vec<<<G, 256, 0, s>>>(n * R, C.r, b0);
-        const float* x0 = c32.run(0, b0);
-        double* z = C.z[it & 1];
-        note_launch(1);
-        k_f2d_vec<<<G, 256, 0, s>>>(n * R, x0, z);
-        return z;
-    };
-    if ((e = cudaMemsetAsync(C.ctl, 0, 2 * sizeof(int), s)) != cudaSuccess) return cuda_fail(e, "memset");
-    note_launch(2);
-    if (X0)
-        k_cg_init_x0<R, NV><<<G, 256, 0, s>>>(d0.A, st.v64[0], st.v64[1], B, X0, X, C.r, C.part);
-    else
-        k_cg_init<R><<<G, 256, 0, s>>>(n, B, X, C.r, C.part);
-    k_cg_start<R><<<1, 32 * R, 0, s>>>(C.part, G, C.bb, C.active, C.ctl);
-    if ((e = read_ctl()) != cudaSuccess) return cuda_fail(e, "multigrid cg");
-    if (hc[0] != QPAT_OK) return fail(hc[0], "multigrid cg: right-hand side not finite");
-    *iters = 0;
-    if (hc[1] == 0) return QPAT_OK;
-    const double* z = precond(0);
-    if (f32)
-        launch_dots_beta<R, true>(C, n, G, z, z, 1, s);
-    else
-        launch_dots_beta<R, false>(C, n, G, z, z, 1, s);
-    if ((e = cudaMemcpyAsync(C.p, z, sizeof(double) * n * R, cudaMemcpyDeviceToDevice, s)) != cudaSuccess)
-        return cuda_fail(e, "copy");
-    const double rtol2 = so.rtol * so.rtol;
-    for (int it = 1; it <= so.maxit; ++it) {
-        note_launch(4);
-        k_cg_apply<R, NV><<<G, 256, 0, s>>>(d0.A, st.v64[0], st.v64[1], C.p, C.q, C.part);
-        k_cg_alpha<R><<<1, 32 * R, 0, s>>>(C.part, G, C.rz, C.active, C.alpha, C.ctl);
-        k_cg_update<R><<<G, 256, 0, s>>>(n, C.alpha, C.p, C.q, X, C.r, C.part);
-        k_cg_check<R><<<1, 32 * R, 0, s>>>(C.part, G, C.bb, rtol2, C.active, C.rr, C.ctl);
-        if ((e = read_ctl()) != cudaSuccess) return cuda_fail(e, "multigrid cg");
-        timer.collect();
-        *iters = it;
-        if (hc[0] != QPAT_OK) return fail(hc[0], "multigrid cg: breakdown (p.Ap <= 0 or not finite)");
-        if (hc[1] == 0) return QPAT_OK;
-        const double* zo = z;
-        z = precond(it);
-        if (f32)
-            launch_dots_beta<R, true>(C, n, G, z, zo, 0, s);
-        else
-            launch_dots_beta<R, false>(C, n, G, z, zo, 0, s);
-        note_launch(1);
-        k_cg_dir<R><<<G, 256, 0, s>>>(n, C.beta, z, C.p);
+struct CgSolve {
+    qpat_mesh_s* M;
+    const OpState& st;
+    const SolveOpts& so;
+    const AmgHierDev& H;
+    const AmgValues& V;
+    bool f32;
+    AmgVecs& W;
+    AmgCg& C;
+    cudaStream_t s;
+    FineTimer* timer;
+    int64_t n = 0;
+    int G = 0;
+
+    // kernels of one iteration: per level above the coarsest 2 deg + 3
+    // (smoothing, residual, restriction, prolongation), 1 on the coarsest,
+    // 2 casts for the FP32 cycle, 7 of the CG itself
+    int body_kernels() const {
+        const int deg = std::max(1, so.mg_degree);
+        return (int(H.lv.size()) - 1) * (2 * deg + 3) + 1 + (f32 ? 2 : 0) + 7;
     }
-    return fail(QPAT_ENOCONV, "multigrid cg: iteration cap reached");
-}
+
+    // one iteration on stream t; use_graph: the check sets the loop condition
+    void body(cudaStream_t t, cudaGraphConditionalHandle cond, int use_graph) {
+        const int deg = std::max(1, so.mg_degree);
+        const LevelDev& d0 = H.lv[0];
+        const double* z;
+        if (!f32) {
+            VCycle<double, R, NV> c{H, V, W, st, deg, so.mg_ratio, t, timer};
+            z = c.run(0, C.r);
+        } else {
+            VCycle<float, R, NV> c{H, V, W, st, deg, so.mg_ratio, t, timer};
+            float* b0 = static_cast<float*>(W.b[0]);
+            note_launch(1);
+            k_d2f_vec<<<G, 256, 0, t>>>(n * R, C.r, b0);
+            const float* x0 = c.run(0, b0);
+            note_launch(1);
+            k_f2d_vec<<<G, 256, 0, t>>>(n * R, x0, C.z);
+            z = C.z;
+        }
+        note_launch(7);
+        if (f32) {
+            k_cg_dots<R, true><<<G, 256, 0, t>>>(n, C.r, z, C.zo, C.part);
+            k_cg_beta<R, true><<<1, 32 * R, 0, t>>>(C.part, G, C.rz, C.beta, C.ctl);
+            k_cg_dir<R, true><<<G, 256, 0, t>>>(n, C.beta, z, C.p, C.zo);
+        } else {
+            k_cg_dots<R, false><<<G, 256, 0, t>>>(n, C.r, z, nullptr, C.part);
+            k_cg_beta<R, false><<<1, 32 * R, 0, t>>>(C.part, G, C.rz, C.beta, C.ctl);
+            k_cg_dir<R, false><<<G, 256, 0, t>>>(n, C.beta, z, C.p, nullptr);
+        }
+        k_cg_apply<R, NV><<<G, 256, 0, t>>>(d0.A, st.v64[0], st.v64[1], C.p, C.q, C.part);
+        k_cg_alpha<R><<<1, 32 * R, 0, t>>>(C.part, G, C.rz, C.alpha, C.ctl);
+        k_cg_update<R><<<G, 256, 0, t>>>(n, C.alpha, C.p, C.q, C.x, C.r, C.part);
+        k_cg_check<R><<<1, 32 * R, 0, t>>>(C.part, G, C.bb, C.rtol2, C.rr, C.ctl, cond, use_graph);
+    }
+
+    int run(AmgState& A, const std::string& key, const double* B, double* X, const double* X0, int* iters) {
+        const LevelDev& d0 = H.lv[0];
+        n = d0.A.n;
+        G = int(std::min<int64_t>(blocks_of(n), kRedMaxGrid));
+        int* hc = reinterpret_cast<int*>(M->host_scratch + 240);
+        cudaError_t e = cudaSuccess;
+        auto read_ctl = [&]() -> cudaError_t {
+            cudaError_t x = cudaMemcpyAsync(hc, C.ctl, 3 * sizeof(int), cudaMemcpyDeviceToHost, s);
+            if (x == cudaSuccess) x = cudaStreamSynchronize(s);
+            return x;
+        };
+        const double rtol2 = so.rtol * so.rtol;
+        const int cap[1] = {so.maxit};
+        if ((e = cudaMemsetAsync(C.ctl, 0, 8 * sizeof(int), s)) != cudaSuccess ||
+            (e = cudaMemcpyAsync(C.ctl + 4, cap, sizeof(int), cudaMemcpyHostToDevice, s)) != cudaSuccess ||
+            (e = cudaMemcpyAsync(C.rtol2, &rtol2, sizeof(double), cudaMemcpyHostToDevice, s)) != cudaSuccess ||
+            (e = cudaMemsetAsync(C.p, 0, sizeof(double) * n * R, s)) != cudaSuccess)
+            return cuda_fail(e, "multigrid start");
+        note_launch(2);
+        if (X0)
+            k_cg_init_x0<R, NV><<<G, 256, 0, s>>>(d0.A, st.v64[0], st.v64[1], B, X0, C.x, C.r, C.part);
+        else
+            k_cg_init<R><<<G, 256, 0, s>>>(n, B, C.x, C.r, C.part);
+        k_cg_start<R><<<1, 32 * R, 0, s>>>(C.part, G, C.bb, C.ctl);
+        if ((e = read_ctl()) != cudaSuccess) return cuda_fail(e, "multigrid cg");
+        if (hc[0] != QPAT_OK) return fail(hc[0], "multigrid cg: right-hand side not finite");
+        if (hc[1] > 0) {
+            if (!timer->on) {
+                AmgGraph& g = A.graphs[key];
+                if (!g.exec) {
+                    const int rc = capture(A, g);
+                    if (rc != QPAT_OK) return rc;
+                }
+                if ((e = cudaGraphLaunch(g.exec, s)) != cudaSuccess) return cuda_fail(e, "multigrid graph");
+                if ((e = read_ctl()) != cudaSuccess) return cuda_fail(e, "multigrid cg");
+                note_launch(hc[2] * g.body_kernels);
+            } else {
+                while (true) {
+                    body(s, 0, 0);
+                    if ((e = read_ctl()) != cudaSuccess) return cuda_fail(e, "multigrid cg");
+                    timer->collect();
+                    if (hc[0] != QPAT_OK || hc[1] == 0) break;
+                }
+            }
+        }
+        *iters = hc[2];
+        if (hc[0] == QPAT_ENOCONV) return fail(QPAT_ENOCONV, "multigrid cg: iteration cap reached");
+        if (hc[0] != QPAT_OK) return fail(hc[0], "multigrid cg: breakdown (p.Ap <= 0 or not finite)");
+        if ((e = cudaMemcpyAsync(X, C.x, sizeof(double) * n * R, cudaMemcpyDeviceToDevice, s)) != cudaSuccess)
+            return cuda_fail(e, "copy");
+        return QPAT_OK;
+    }
+
+    int capture(AmgState& A, AmgGraph& g) {
+        cudaError_t e = cudaSuccess;
+        if (!A.capture && (e = cudaStreamCreateWithFlags(&A.capture, cudaStreamNonBlocking)) != cudaSuccess)
+            return cuda_fail(e, "multigrid capture stream");
+        if ((e = cudaGraphCreate(&g.graph, 0)) != cudaSuccess) return cuda_fail(e, "multigrid graph");
+        cudaGraphConditionalHandle cond;
+        if ((e = cudaGraphConditionalHandleCreate(&cond, g.graph, 1, cudaGraphCondAssignDefault)) != cudaSuccess)
+            return cuda_fail(e, "multigrid graph");
+        cudaGraphNodeParams np = {};
+        np.type = cudaGraphNodeTypeConditional;
+        np.conditional.handle = cond;
+        np.conditional.type = cudaGraphCondTypeWhile;
+        np.conditional.size = 1;
+        cudaGraphNode_t node;
+        if ((e = cudaGraphAddNode(&node, g.graph, nullptr, nullptr, 0, &np)) != cudaSuccess)
+            return cuda_fail(e, "multigrid graph");
+        cudaGraph_t bodyg = np.conditional.phGraph_out[0];
+        if ((e = cudaStreamBeginCaptureToGraph(A.capture, bodyg, nullptr, nullptr, 0,
+                                               cudaStreamCaptureModeThreadLocal)) != cudaSuccess)
+            return cuda_fail(e, "multigrid capture");
+        body(A.capture, cond, 1);
+        g.body_kernels = body_kernels();
+        cudaGraph_t out = nullptr;
+        const cudaError_t e1 = cudaGetLastError();
+        e = cudaStreamEndCapture(A.capture, &out);
+        // capturing counted the body's launches once; replays are counted per iteration
+        note_launch(-g.body_kernels);
+        if (e1 != cudaSuccess) return cuda_fail(e1, "multigrid capture");
+        if (e != cudaSuccess) return cuda_fail(e, "multigrid capture");
+        if ((e = cudaGraphInstantiate(&g.exec, g.graph, 0)) != cudaSuccess) return cuda_fail(e, "multigrid graph");
+        return QPAT_OK;
+    }
+};
 
 template <int NV>
-int dispatch(int R, qpat_mesh_s* M, const OpState& st, const SolveOpts& so, const AmgHierDev& H, const AmgValues& V,
-             bool f32, AmgVecs& W, AmgCg& C, const double* B, double* X, const double* X0, cudaStream_t s,
-             int* iters) {
+int dispatch(int R, AmgState& A, const std::string& key, qpat_mesh_s* M, const OpState& st, const SolveOpts& so,
+             const AmgHierDev& H, const AmgValues& V, bool f32, AmgVecs& W, AmgCg& C, const double* B, double* X,
+             const double* X0, cudaStream_t s, FineTimer* timer, int* iters) {
     if constexpr (NV == 2) {
-        return cg_solve<2, 2>(M, st, so, H, V, f32, W, C, B, X, X0, s, iters);
+        return CgSolve<2, 2>{M, st, so, H, V, f32, W, C, s, timer}.run(A, key, B, X, X0, iters);
     } else {
         switch (R) {
-            case 1: return cg_solve<1, 1>(M, st, so, H, V, f32, W, C, B, X, X0, s, iters);
-            case 2: return cg_solve<2, 1>(M, st, so, H, V, f32, W, C, B, X, X0, s, iters);
-            case 4: return cg_solve<4, 1>(M, st, so, H, V, f32, W, C, B, X, X0, s, iters);
-            case 8: return cg_solve<8, 1>(M, st, so, H, V, f32, W, C, B, X, X0, s, iters);
-            default: return cg_solve<16, 1>(M, st, so, H, V, f32, W, C, B, X, X0, s, iters);
+            case 1: return CgSolve<1, 1>{M, st, so, H, V, f32, W, C, s, timer}.run(A, key, B, X, X0, iters);
+            case 2: return CgSolve<2, 1>{M, st, so, H, V, f32, W, C, s, timer}.run(A, key, B, X, X0, iters);
+            case 4: return CgSolve<4, 1>{M, st, so, H, V, f32, W, C, s, timer}.run(A, key, B, X, X0, iters);
+            case 8: return CgSolve<8, 1>{M, st, so, H, V, f32, W, C, s, timer}.run(A, key, B, X, X0, iters);
+            default: return CgSolve<16, 1>{M, st, so, H, V, f32, W, C, s, timer}.run(A, key, B, X, X0, iters);
         }
     }
 }
@@ -1183,26 +1316,41 @@ int amg_solve(qpat_mesh_s* M, const OpState& st, const SolveOpts& so, int R, con
     AmgCg& C = A.cg[R];
     if (!C.r) {
         const size_t nR = size_t(M->h.N) * R;
+        C.x = dalloc<double>(C.allocs, nR, e);
         C.r = dalloc<double>(C.allocs, nR, e);
         C.p = dalloc<double>(C.allocs, nR, e);
         C.q = dalloc<double>(C.allocs, nR, e);
-        C.z[0] = dalloc<double>(C.allocs, nR, e);
-        C.z[1] = dalloc<double>(C.allocs, nR, e);
+        C.z = dalloc<double>(C.allocs, nR, e);
+        C.zo = dalloc<double>(C.allocs, nR, e);
         C.part = dalloc<double>(C.allocs, size_t(kRedMaxGrid) * 32, e);
-        double* sc = dalloc<double>(C.allocs, 5 * 16, e);
-        C.ctl = dalloc<int>(C.allocs, 2 + 16, e);
+        double* sc = dalloc<double>(C.allocs, 5 * 16 + 1, e);
+        C.ctl = dalloc<int>(C.allocs, kCtlActive + 16, e);
         if (e != cudaSuccess) return cuda_fail(e, "multigrid workspace");
         C.bb = sc;
         C.rz = sc + 16;
         C.alpha = sc + 32;
         C.beta = sc + 48;
         C.rr = sc + 64;
-        C.active = C.ctl + 2;
+        C.rtol2 = sc + 80;
     }
+    // the captured iteration depends on these buffers and settings only
+    char key[256];
+    std::snprintf(key, sizeof key, "%d/%d/%d/%d/%d/%.17g/%p/%p/%p", pat, R, st.nv, int(f32), so.mg_degree, so.mg_ratio,
+                  static_cast<const void*>(&V), static_cast<const void*>(st.v64[0]),
+                  static_cast<const void*>(st.v64[1]));
+    FineTimer timer;
+    timer.on = M->timing != 0;
+    timer.s = s;
     if (M->timing) cudaEventRecord(M->ev0, s);
     int iters = 0;
-    rc = st.nv == 2 ? dispatch<2>(R, M, st, so, H, V, f32, W, C, B, X, X0, s, &iters)
-                    : dispatch<1>(R, M, st, so, H, V, f32, W, C, B, X, X0, s, &iters);
+    rc = st.nv == 2 ? dispatch<2>(R, A, key, M, st, so, H, V, f32, W, C, B, X, X0, s, &timer, &iters)
+                    : dispatch<1>(R, A, key, M, st, so, H, V, f32, W, C, B, X, X0, s, &timer, &iters);
+    if (timer.on) {
+        cudaStreamSynchronize(s);
+        timer.collect();
+        M->mg_fine_ms += timer.ms;
+        M->mg_fine_launches += timer.launches;
+    }
     if ((e = cudaGetLastError()) != cudaSuccess && rc == QPAT_OK) rc = cuda_fail(e, "multigrid launch");
     if (M->timing) {
         cudaEventRecord(M->ev1, s);
@@ -1237,6 +1385,11 @@ void amg_release(qpat_mesh_s* M) {
         for (void* p : kv.second.allocs) cudaFree(p);
     for (auto& kv : A.cg)
         for (void* p : kv.second.allocs) cudaFree(p);
+    for (auto& kv : A.graphs) {
+        if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
+        if (kv.second.graph) cudaGraphDestroy(kv.second.graph);
+    }
+    if (A.capture) cudaStreamDestroy(A.capture);
     delete M->amg;
     M->amg = nullptr;
 }

@@ -28,20 +28,34 @@
 
 namespace qpat {
 
-// A sliced-ELLPACK pattern with 32-row slices: entry k of row i sits at
-// (ptr[i / 32] + k) * 32 + i % 32; rows hold len[i] entries and padding
-// entries repeat the row's own id (value 0).  The patterns this file builds
-// keep each row sorted by column; the fine level keeps the mesh's order.
+// A sparse pattern in one of two layouts.  Sliced ELLPACK with 32-row
+// slices (rowmajor = false): entry k of row i sits at
+// (ptr[i / 32] + k) * 32 + i % 32, so the 32 rows of a warp read 32
+// consecutive entries; padding entries repeat the row's own id (value 0).
+// Row-major (rowmajor = true, for rows of a few dozen entries and more,
+// which several lanes share): entry k of row i sits at ptr[i] + k.  Rows
+// hold len[i] entries.  The patterns this file builds keep each row sorted
+// by column; the fine level keeps the mesh's SELL order.
 struct SellPattern {
     int64_t n = 0;         // rows
-    int64_t nslices = 0;
-    std::vector<int64_t> ptr;   // nslices + 1, in units of 32 entries
-    std::vector<int32_t> col;   // 32 * ptr[nslices]
-    std::vector<uint16_t> len;  // 32 * nslices (0 past row n - 1)
-    int64_t entries() const { return ptr.empty() ? 0 : 32 * ptr.back(); }
-    int64_t pos(int64_t row, int k) const { return (ptr[row / 32] + k) * 32 + row % 32; }
+    int64_t nslices = 0;   // SELL: slices of 32 rows
+    bool rowmajor = false;
+    std::vector<int64_t> ptr;   // SELL: nslices + 1, in units of 32 entries; row-major: n + 1
+    std::vector<int32_t> col;   // entries()
+    std::vector<uint16_t> len;  // SELL: 32 * nslices (0 past row n - 1); row-major: n
+    int64_t entries() const {
+        if (ptr.empty()) return 0;
+        return rowmajor ? ptr.back() : 32 * ptr.back();
+    }
+    int64_t pos(int64_t row, int k) const {
+        return rowmajor ? ptr[size_t(row)] + k : (ptr[size_t(row / 32)] + k) * 32 + row % 32;
+    }
     int maxlen = 0;
 };
+
+// Rows of at least this many entries on average are stored row-major and
+// applied by 8 lanes per row.
+constexpr int kAmgRowMajorLen = 24;
 
 // Host plan of one level: the level's operator pattern and, except on the
 // coarsest level, the transfer to the next one.

@@ -95,7 +95,27 @@ inline int slot_of(const int32_t* col, int64_t b, int64_t e, int32_t c) {
 }
 
 bool sell_from_csr(const Csr& c, SellPattern& s, std::string& err) {
+    if (c.n > 0 && c.ptr[size_t(c.n)] >= int64_t(kAmgRowMajorLen) * c.n) {
+        // long rows: row-major, so that the lanes sharing a row read consecutive entries
+        s.n = c.n;
+        s.nslices = 0;
+        s.rowmajor = true;
+        s.ptr = c.ptr;
+        s.col = c.col;
+        s.len.assign(size_t(c.n), 0);
+        s.maxlen = 0;
+        for (int64_t i = 0; i < c.n; ++i) {
+            if (c.len(i) > 65535) {
+                err = "multigrid: a row of a level holds more than 65535 entries";
+                return false;
+            }
+            s.len[size_t(i)] = uint16_t(c.len(i));
+            s.maxlen = std::max(s.maxlen, int(c.len(i)));
+        }
+        return true;
+    }
     s.n = c.n;
+    s.rowmajor = false;
     s.nslices = (c.n + 31) / 32;
     s.ptr.assign(size_t(s.nslices + 1), 0);
     s.len.assign(size_t(32 * s.nslices), 0);

@@ -117,3 +117,37 @@ def test_parameter_checks(case):
     for bad in (dict(multigrid=3), dict(multigrid=1, mg_degree=9), dict(multigrid=1, mg_ratio=0.5)):
         with pytest.raises(Q.QpatError):
             Q.qpat_forward(case.lib, case.kappa, case.mu, case.flux, Q.qpat_default_params(**bad))
+
+
+def test_graph_loop_equals_host_loop(case):
+    """Without timing the CG iterations run as a captured graph whose "while"
+    node is driven by the device; with timing on they are launched from the
+    host one by one.  The same kernels on the same data: the same bits and
+    the same iteration count."""
+    prm = _mg(1)
+    case.lib.reset_stats()
+    a, _ = Q.qpat_forward(case.lib, case.kappa, case.mu, case.flux, prm)
+    ia = case.lib.stats()["pcg_iters"]
+    case.lib.set_timing(True)
+    try:
+        case.lib.reset_stats()
+        b, _ = Q.qpat_forward(case.lib, case.kappa, case.mu, case.flux, prm)
+        ib = case.lib.stats()["pcg_iters"]
+        ms, launches = case.lib.multigrid_fine_time()
+    finally:
+        case.lib.set_timing(False)
+    np.testing.assert_array_equal(a, b)
+    assert ia == ib
+    if len(case.lib.multigrid_levels()) > 1:
+        assert launches == ib and ms > 0.0
+
+
+def test_iteration_cap_and_restart(case):
+    """A cap below the need ends the graph loop with QPAT_ENOCONV; the next
+    solve on the same handle is exact again."""
+    if case.N <= 128:
+        pytest.skip("one level: the exact coarse solve converges at once")
+    with pytest.raises(Q.QpatError):
+        Q.qpat_forward(case.lib, case.kappa, case.mu, case.flux, _mg(1, max_pcg_iter=1))
+    phi, _ = Q.qpat_forward(case.lib, case.kappa, case.mu, case.flux, _mg(1))
+    assert rel(phi, case.phi) < 1e-10
