@@ -65,20 +65,33 @@ __device__ __forceinline__ int64_t spos(const SellDev& S, int64_t row, int k) {
 // max_i sum_j |a_ij| / a_ii of D^-1 A per value set (hi must start at 0; the
 // bound is >= 1, so the bits of the positive doubles order like integers).
 template <int NV>
-__global__ void k_dinv_hi(SellDev A, const int32_t* diag, const double* v0, const double* v1, double* dinv,
-                          double* hi) {
+__global__ void __launch_bounds__(256) k_dinv_hi(SellDev A, const int32_t* diag, const double* v0, const double* v1,
+                                                 double* dinv, double* hi) {
+    __shared__ double bmax[NV][8];
     const int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
-    if (i >= A.n) return;
-    const int L = A.len[i];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 #pragma unroll
     for (int v = 0; v < NV; ++v) {
-        const double* val = v == 0 ? v0 : v1;
-        double s = 0.0;
-        for (int k = 0; k < L; ++k) s += fabs(val[spos(A, i, k)]);
-        const double d = val[spos(A, i, diag[i])];
-        dinv[i * NV + v] = 1.0 / d;
-        const double ratio = s / fabs(d);
-        atomicMax(reinterpret_cast<unsigned long long*>(hi + v), __double_as_longlong(ratio));
+        double ratio = 0.0;
+        if (i < A.n) {
+            const double* val = v == 0 ? v0 : v1;
+            const int L = A.len[i];
+            double s = 0.0;
+            for (int k = 0; k < L; ++k) s += fabs(val[spos(A, i, k)]);
+            const double d = val[spos(A, i, diag[i])];
+            dinv[i * NV + v] = 1.0 / d;
+            ratio = s / fabs(d);
+        }
+        // the largest ratio of the block (max is exact in any order), then one atomic per block
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) ratio = fmax(ratio, __shfl_xor_sync(0xffffffffu, ratio, o));
+        if (lane == 0) bmax[v][warp] = ratio;
+    }
+    __syncthreads();
+    if (threadIdx.x < NV) {
+        double m = 0.0;
+        for (int w = 0; w < int(blockDim.x >> 5); ++w) m = fmax(m, bmax[threadIdx.x][w]);
+        atomicMax(reinterpret_cast<unsigned long long*>(hi + threadIdx.x), __double_as_longlong(m));
     }
 }
 
@@ -104,39 +117,47 @@ __global__ void k_prolong(SellDev A, SellDev P, const uint16_t* a2p, const uint1
 }
 
 // Row i of A P = sum over the entries a_ij of row i of A of a_ij (row j of
-// P), one warp per row and value set: the entries of row i of A are taken
-// one after the other and the lanes add a_ij P[j, :] into the row's shared
-// accumulator; the columns of one P row differ, so no two lanes meet on a
-// slot and every value is summed in the same order on every run.
+// P), 8 lanes per row and value set (4 rows per warp): the entries of row i
+// of A are taken one after the other and the 8 lanes add a_ij P[j, :] into
+// the row's shared accumulator; the columns of one P row differ, so no two
+// lanes meet on a slot and every value is summed in the same order on every
+// run.
+constexpr int kApLanes = 8;
 template <int NV>
 __global__ void k_ap(SellDev A, SellDev P, const int64_t* ap_ptr, const int64_t* ap_sptr, const uint16_t* ap_slot,
                      int64_t ap_nnz, int ap_maxlen, const double* v0, const double* v1, const double* p0,
                      const double* p1, double* ap) {
     extern __shared__ double acc_all[];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int64_t task = blockIdx.x * int64_t(blockDim.x >> 5) + warp;
-    if (task >= A.n * NV) return;
-    const int64_t i = task / NV;
-    const int v = int(task % NV);
-    double* acc = acc_all + int64_t(warp) * ap_maxlen;
+    const int grp = threadIdx.x / kApLanes, sub = threadIdx.x % kApLanes;
+    const int64_t task = blockIdx.x * int64_t(blockDim.x / kApLanes) + grp;
+    const bool valid = task < A.n * NV;
+    const int64_t i = valid ? task / NV : 0;
+    const int v = valid ? int(task % NV) : 0;
+    double* acc = acc_all + int64_t(grp) * ap_maxlen;
     const double* val = v == 0 ? v0 : v1;
     const double* pv = v == 0 ? p0 : p1;
     double* out = ap + v * ap_nnz;
-    const int64_t b = ap_ptr[i], cnt = ap_ptr[i + 1] - b;
-    for (int64_t t = lane; t < cnt; t += 32) acc[t] = 0.0;
+    const int64_t b = valid ? ap_ptr[i] : 0, cnt = valid ? ap_ptr[i + 1] - b : 0;
+    for (int64_t t = sub; t < cnt; t += kApLanes) acc[t] = 0.0;
     __syncwarp();
-    int64_t o = ap_sptr[i];
-    const int L = A.len[i];
-    for (int k = 0; k < L; ++k) {
-        const int64_t at = spos(A, i, k);
-        const int64_t j = A.col[at];
-        const double a = val[at];
-        const int LPj = P.len[j];
-        for (int kk = lane; kk < LPj; kk += 32) acc[ap_slot[o + kk]] += a * pv[spos(P, j, kk)];
-        o += LPj;
+    int64_t o = valid ? ap_sptr[i] : 0;
+    const int L = valid ? A.len[i] : 0;
+    // the longest row of the warp sets the step count, so that every lane reaches each __syncwarp
+    int Lw = L;
+#pragma unroll
+    for (int s = 16; s > 0; s >>= 1) Lw = max(Lw, __shfl_xor_sync(0xffffffffu, Lw, s));
+    for (int k = 0; k < Lw; ++k) {
+        if (k < L) {
+            const int64_t at = spos(A, i, k);
+            const int64_t j = A.col[at];
+            const double a = val[at];
+            const int LPj = P.len[j];
+            for (int kk = sub; kk < LPj; kk += kApLanes) acc[ap_slot[o + kk]] += a * pv[spos(P, j, kk)];
+            o += LPj;
+        }
         __syncwarp();
     }
-    for (int64_t t = lane; t < cnt; t += 32) out[b + t] = acc[t];
+    for (int64_t t = sub; t < cnt; t += kApLanes) out[b + t] = acc[t];
 }
 
 // R = P^T values gathered from P (padding 0).
@@ -853,13 +874,14 @@ cudaError_t numeric_levels(const AmgHierDev& H, const OpState& st, AmgValues& V,
                                                         V.hi + 2 * l, Pv[0], Pv[1]);
         k_rvals<NV><<<blocks_of(d.R.entries), 256, 0, s>>>(d.R.entries, d.r_src, Pv[0], Pv[1], Rv[0], Rv[1]);
         {
-            int wpb = 8;
-            while (wpb > 1 && size_t(wpb) * size_t(d.ap_maxlen) * sizeof(double) > 96 * 1024) wpb >>= 1;
-            const size_t smem = size_t(wpb) * size_t(d.ap_maxlen) * sizeof(double);
+            int wpb = 8;  // warps per block, kApLanes lanes per row
+            const int rpw = 32 / kApLanes;
+            while (wpb > 1 && size_t(wpb * rpw) * size_t(d.ap_maxlen) * sizeof(double) > 96 * 1024) wpb >>= 1;
+            const size_t smem = size_t(wpb * rpw) * size_t(d.ap_maxlen) * sizeof(double);
             if ((e = allow_smem(reinterpret_cast<const void*>(&k_ap<NV>), smem)) != cudaSuccess) return e;
-            k_ap<NV><<<blocks_of(d.A.n * NV, wpb), 32 * wpb, smem, s>>>(d.A, d.P, d.ap_ptr, d.ap_sptr, d.ap_slot,
-                                                                        d.ap_nnz, d.ap_maxlen, a0, a1, Pv[0], Pv[1],
-                                                                        V.AP[size_t(l)]);
+            k_ap<NV><<<blocks_of(d.A.n * NV, wpb * rpw), 32 * wpb, smem, s>>>(
+                d.A, d.P, d.ap_ptr, d.ap_sptr, d.ap_slot, d.ap_nnz, d.ap_maxlen, a0, a1, Pv[0], Pv[1],
+                V.AP[size_t(l)]);
         }
         const LevelDev& c = H.lv[size_t(l + 1)];
         int wpb = 8;
