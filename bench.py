@@ -1066,7 +1066,26 @@ def concurrent_recon_leg(Q, torch, count: int = 32, threads: int = 16, patch_nod
         t_con = time.perf_counter() - t0
         same = all(np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1]) for a, b in zip(seqp, con))
         diff = max(max(rel(a[0], b[0]), rel(a[1], b[1])) for a, b in zip(seq, con))
+        # the same reconstructions with the multigrid-preconditioned solves
+        # (each mesh's hierarchy is built by a first, untimed run)
+        pmg = Q.qpat_default_params(precision=0, T=2e-2, max_lin=3, max_lsqr=10, fixed_counts=1, multigrid=1)
+        run_mg = lambda p: Q.qpat_reconstruct(p[0], p[1], p[2], p[3], pmg, p[4])
+        for p in sets["default"]:
+            run_mg(p)
+        t0 = time.perf_counter()
+        seq_mg = [run_mg(p) for p in sets["default"]]
+        t_seq_mg = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        with ThreadPoolExecutor(max_workers=threads) as ex:
+            con_mg = list(ex.map(run_mg, sets["default"]))
+        t_con_mg = time.perf_counter() - t0
+        same_mg = all(np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1]) for a, b in zip(seq_mg, con_mg))
+        diff_mg = max(max(rel(a[0], b[0]), rel(a[1], b[1])) for a, b in zip(seq, seq_mg))
         return {"problems": count, "nodes_total": int(sum(p[0].N for p in sets["default"])),
+                "multigrid": {"sequential_s": t_seq_mg, "concurrent_s": t_con_mg,
+                              "speedup_vs_sequential_default": t_seq / t_con_mg,
+                              "concurrent_bit_identical_to_sequential": bool(same_mg),
+                              "max_field_rel_diff_vs_persistent_pcg": diff_mg},
                 "illuminations_total": int(sum(c.K for c in cfgs)), "threads": threads,
                 "patch_nodes": patch_nodes,
                 "settings": "FP64, T = 2e-2, 3 linearisations x 10 LSQR rounds, fixed counts",
