@@ -1481,6 +1481,9 @@ def run_profile_case(args):
     import paper_1512_02796_gb300 as Q
     d = setup_problem(Q, torch, args.workload, args.patch_nodes)
     mesh = d["mesh"]
+    # timing on: the multigrid CG launches its kernels one by one from the host
+    # (ncu cannot profile kernel nodes of a graph with a conditional node)
+    mesh.set_timing(True)
     torch.cuda.synchronize()
     calls = [{"call": "setup", "lib_launches": Q.qpat_launch_count()}]
     for name, prm in (("pair_mg64", Q.qpat_default_params(precision=0, multigrid=1)),
