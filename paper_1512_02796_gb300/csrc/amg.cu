@@ -593,9 +593,24 @@ __device__ __forceinline__ void chunk_partials(const double* acc, double* part) 
     }
 }
 
-template <int R>
+// The next cycle's first fine-level smoothing step (from x = 0: x = d =
+// c_r D^-1 b with b = r, c_r = 1 / theta as in k_cheb), taken in the CG
+// update on the residual it has just written instead of by a separate pass
+// over r; for the FP32 cycle also the FP32 copy of r.  The same operations
+// in the same order as k_cheb's first step, so the results do not change.
+template <typename T, int NV>
+struct PreStep {
+    const T* dinv = nullptr;      // fine level, n x NV
+    const double* hi = nullptr;   // Gershgorin bounds of the fine level, per value set
+    double ratio = 30.0;
+    T* x = nullptr;               // the cycle's first fine-level buffer (x = d after the step)
+    T* d = nullptr;               // null when no later pre-smoothing step reads d (degree 1)
+    float* b32 = nullptr;         // FP32 cycle: the fine level's right-hand side
+};
+
+template <int R, int NV, typename T>
 __global__ void __launch_bounds__(256) k_cg_update(int64_t n, const double* alpha, const double* p, const double* q,
-                                                   double* x, double* r, double* part) {
+                                                   double* x, double* r, double* part, PreStep<T, NV> pre) {
     constexpr int C = kChunk<R>, NCH = R / C;
     const int c0 = int(threadIdx.x % NCH) * C;
     double al[C], acc[C];
@@ -604,9 +619,16 @@ __global__ void __launch_bounds__(256) k_cg_update(int64_t n, const double* alph
         al[t] = alpha[c0 + t];
         acc[t] = 0.0;
     }
+    T cr[NV];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+        const double h = pre.hi[v], lo = h / pre.ratio;
+        cr[v] = T(1.0 / (0.5 * (h + lo)));
+    }
     for (int64_t g = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; g < n * NCH;
          g += int64_t(gridDim.x) * blockDim.x) {
-        const int64_t o = (g / NCH) * R + c0;
+        const int64_t node = g / NCH;
+        const int64_t o = node * R + c0;
         double pv[C], qv[C], xv[C], rv[C];
         ldR<double, C>(p + o, pv);
         ldR<double, C>(q + o, qv);
@@ -620,6 +642,17 @@ __global__ void __launch_bounds__(256) k_cg_update(int64_t n, const double* alph
         }
         stR<double, C>(x + o, xv);
         stR<double, C>(r + o, rv);
+        T rc[C], up[C];
+#pragma unroll
+        for (int t = 0; t < C; ++t) {
+            const int v = NV == 2 ? c0 + t : 0;
+            rc[t] = T(rv[t]);
+            const T upd = cr[v] * pre.dinv[node * NV + v] * rc[t];
+            up[t] = T(0) + upd;
+        }
+        if constexpr (std::is_same<T, float>::value) stR<float, C>(pre.b32 + o, rc);
+        if (pre.d) stR<T, C>(pre.d + o, up);
+        stR<T, C>(pre.x + o, up);
     }
     chunk_partials<R, 1>(acc, part);
 }
@@ -1047,6 +1080,7 @@ struct VCycle {
     double ratio;
     cudaStream_t s;
     FineTimer* timer = nullptr;
+    bool pre_done = false;  // the fine level's first smoothing step was taken by the CG update
 
     static constexpr bool F64 = std::is_same<T, double>::value;
     const T* av(int l, int v) const {
@@ -1090,6 +1124,27 @@ struct VCycle {
             k_cheb<T, R, NV, false, 1><<<blocks_of(A.n), 256, 0, s>>>(A, a0, a1, di, hi, ratio, k, x_in, x_out, d, b);
     }
 
+    // the fine level's first smoothing step on b (before the first iteration)
+    void first_fine(const T* b) {
+        if (H.lv.size() < 2) return;
+        const LevelDev& d = H.lv[0];
+        note_launch(1);
+        k_cheb<T, R, NV, true, 1><<<blocks_of(d.A.n), 256, 0, s>>>(d.A, av(0, 0), av(0, 1), dinv(0), V.hi, ratio, 0,
+                                                                  nullptr, static_cast<T*>(W.xa[0]),
+                                                                  static_cast<T*>(W.d[0]), b);
+    }
+
+    PreStep<T, NV> pre_step(float* b32) const {
+        PreStep<T, NV> p;
+        p.dinv = dinv(0);
+        p.hi = V.hi;
+        p.ratio = ratio;
+        p.x = static_cast<T*>(W.xa[0]);
+        p.d = deg > 1 ? static_cast<T*>(W.d[0]) : nullptr;
+        p.b32 = b32;
+        return p;
+    }
+
     const T* run(int l, const T* b) {
         const LevelDev& d = H.lv[size_t(l)];
         const int L = int(H.lv.size());
@@ -1103,9 +1158,11 @@ struct VCycle {
         }
         const double* hi = V.hi + 2 * l;
         const T *a0 = av(l, 0), *a1 = av(l, 1);
-        note_launch(1);
-        k_cheb<T, R, NV, true, 1><<<blocks_of(d.A.n), 256, 0, s>>>(d.A, a0, a1, dinv(l), hi, ratio, 0, nullptr, x,
-                                                                  dd, b);
+        if (!(l == 0 && pre_done)) {
+            note_launch(1);
+            k_cheb<T, R, NV, true, 1><<<blocks_of(d.A.n), 256, 0, s>>>(d.A, a0, a1, dinv(l), hi, ratio, 0, nullptr,
+                                                                      x, dd, b);
+        }
         for (int k = 1; k < deg; ++k) {
             if (l == 0 && timer) timer->before();
             cheb(d.A, a0, a1, dinv(l), hi, k, x, y, dd, b);
@@ -1156,9 +1213,12 @@ struct CgSolve {
     // kernels of one iteration: per level above the coarsest 2 deg + 3
     // (smoothing, residual, restriction, prolongation), 1 on the coarsest,
     // 2 casts for the FP32 cycle, 7 of the CG itself
+    // (the fine level's first smoothing step, and for the FP32 cycle the cast
+    // of r, are taken by the CG update)
     int body_kernels() const {
         const int deg = std::max(1, so.mg_degree);
-        return (int(H.lv.size()) - 1) * (2 * deg + 3) + 1 + (f32 ? 2 : 0) + 7;
+        const int L = int(H.lv.size());
+        return (L - 1) * (2 * deg + 3) - (L > 1 ? 1 : 0) + 1 + (f32 ? 1 : 0) + 7;
     }
 
     // one iteration on stream t; use_graph: the check sets the loop condition
@@ -1166,15 +1226,13 @@ struct CgSolve {
         const int deg = std::max(1, so.mg_degree);
         const LevelDev& d0 = H.lv[0];
         const double* z;
+        const bool multi = H.lv.size() > 1;
         if (!f32) {
-            VCycle<double, R, NV> c{H, V, W, st, deg, so.mg_ratio, t, timer};
+            VCycle<double, R, NV> c{H, V, W, st, deg, so.mg_ratio, t, timer, multi};
             z = c.run(0, C.r);
         } else {
-            VCycle<float, R, NV> c{H, V, W, st, deg, so.mg_ratio, t, timer};
-            float* b0 = static_cast<float*>(W.b[0]);
-            note_launch(1);
-            k_d2f_vec<<<G, 256, 0, t>>>(n * R, C.r, b0);
-            const float* x0 = c.run(0, b0);
+            VCycle<float, R, NV> c{H, V, W, st, deg, so.mg_ratio, t, timer, multi};
+            const float* x0 = c.run(0, static_cast<float*>(W.b[0]));
             note_launch(1);
             k_f2d_vec<<<G, 256, 0, t>>>(n * R, x0, C.z);
             z = C.z;
@@ -1191,7 +1249,14 @@ struct CgSolve {
         }
         k_cg_apply<R, NV><<<G, 256, 0, t>>>(d0.A, st.v64[0], st.v64[1], C.p, C.q, C.part);
         k_cg_alpha<R><<<1, 32 * R, 0, t>>>(C.part, G, C.rz, C.alpha, C.ctl);
-        k_cg_update<R><<<G, 256, 0, t>>>(n, C.alpha, C.p, C.q, C.x, C.r, C.part);
+        if (!f32) {
+            VCycle<double, R, NV> c{H, V, W, st, deg, so.mg_ratio, t, timer};
+            k_cg_update<R, NV, double><<<G, 256, 0, t>>>(n, C.alpha, C.p, C.q, C.x, C.r, C.part, c.pre_step(nullptr));
+        } else {
+            VCycle<float, R, NV> c{H, V, W, st, deg, so.mg_ratio, t, timer};
+            float* b0 = static_cast<float*>(W.b[0]);
+            k_cg_update<R, NV, float><<<G, 256, 0, t>>>(n, C.alpha, C.p, C.q, C.x, C.r, C.part, c.pre_step(b0));
+        }
         k_cg_check<R><<<1, 32 * R, 0, t>>>(C.part, G, C.bb, C.rtol2, C.rr, C.ctl, cond, use_graph);
     }
 
@@ -1222,6 +1287,18 @@ struct CgSolve {
         if ((e = read_ctl()) != cudaSuccess) return cuda_fail(e, "multigrid cg");
         if (hc[0] != QPAT_OK) return fail(hc[0], "multigrid cg: right-hand side not finite");
         if (hc[1] > 0) {
+            // the first cycle's first fine smoothing step (later ones come with the CG update)
+            const int deg = std::max(1, so.mg_degree);
+            if (!f32) {
+                VCycle<double, R, NV> c{H, V, W, st, deg, so.mg_ratio, s, timer};
+                c.first_fine(C.r);
+            } else {
+                VCycle<float, R, NV> c{H, V, W, st, deg, so.mg_ratio, s, timer};
+                float* b0 = static_cast<float*>(W.b[0]);
+                note_launch(1);
+                k_d2f_vec<<<G, 256, 0, s>>>(n * R, C.r, b0);
+                c.first_fine(b0);
+            }
             if (!timer->on) {
                 AmgGraph& g = A.graphs[key];
                 if (!g.exec) {
