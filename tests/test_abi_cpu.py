@@ -191,3 +191,20 @@ def test_multigrid_plan_on_cylinder_and_tiny_meshes():
         assert rows[0] == xyz.shape[0] and rows[-1] <= 128
     xyz, tets = S.kuhn_cube(3, 1.0)          # 27 nodes: the fine level is the coarsest
     assert Q.qpat_multigrid_host_info(xyz, tets) == [27]
+
+
+def test_multigrid_plan_independent_of_caller_numbering():
+    """The library reorders nodes itself (Morton order), so the multigrid plan
+    of a randomly relabelled mesh with shuffled tet vertices has the same
+    level sizes as the original, and passes the same invariant checks."""
+    xyz, tets = S.kuhn_cube(14, 5.0)
+    rng = np.random.default_rng(4)
+    p = rng.permutation(xyz.shape[0])
+    inv = np.argsort(p)
+    tets2 = inv[tets]
+    for e in range(tets2.shape[0]):
+        tets2[e] = tets2[e][rng.permutation(4)]
+    for prior in (False, True):
+        a = Q.qpat_multigrid_host_info(xyz, tets, prior=prior)
+        b = Q.qpat_multigrid_host_info(xyz[p], tets2.astype(np.int32), prior=prior)
+        assert a == b and a[-1] <= 128 and len(a) >= 2
